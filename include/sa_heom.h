@@ -1,0 +1,262 @@
+/*
+ * sa_heom.h -- C ABI of the B300 (sm_103a) symmetry-adapted HEOM library.
+ *
+ * The library propagates the symmetry-adapted hierarchical equations of
+ * motion of Mondal & Huo (arXiv 2608.20657) for the Holstein-Tavis-Cummings
+ * model (N identical two-level molecules, one cavity mode, single-excitation
+ * manifold, Eq. HS), with independent identical local baths decomposed into
+ * m exponentials (Eq. BCF-exp) and hierarchy depth L (Eq. scaled-HEOM with a
+ * hard cutoff).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: 0 (SA_OK) on success, a negative SA_ERR_* code otherwise.
+ *    No exception, abort or exit crosses this boundary.  sa_heom_strerror()
+ *    names a code; sa_heom_last_error() gives a one-line detail of the most
+ *    recent failure on the calling thread.
+ *  - Handles are not thread-safe: one thread uses a handle at a time.
+ *  - "stream" arguments are cudaStream_t values passed as void*; NULL is the
+ *    legacy default stream.  Device pointers are plain CUDA device addresses
+ *    (for instance a torch tensor's data_ptr()); the library never frees
+ *    memory it did not allocate.
+ *  - Complex numbers are interleaved (re, im) pairs: double2 for SA_FP64,
+ *    float2 for the auxiliary variables of SA_FP32_AUX.
+ *  - State layout ("canonical layout"): instances one after another; inside
+ *    an instance the canonical patterns in the order tier ascending, then
+ *    their local-vector lists compared lexicographically with larger vectors
+ *    first (vectors ordered by |alpha| descending, then components
+ *    lexicographically descending).  Inside a pattern with G occupation
+ *    categories (distinct nonzero vectors in pattern order, then the zero
+ *    category when M_0 = N - r >= 1) the (G+1)^2 + h unique variables of
+ *    Eq. uvar-count are stored as
+ *        Z; X_1..X_G; Y_1..Y_G; P_1..P_G; S_{q,r} (q = 1..G, r != q,
+ *        row major); T_q for the categories with M_q >= 2, in order.
+ *    The physical density operator is the first pattern of each instance
+ *    (Z, X_0, Y_0, P_0[, T_0], Sec. IV.C).
+ *  - SA_FP32_AUX state buffers hold float2[n_vars_total], padded to 256
+ *    bytes, followed by double2[8 * n_instances]: slot 8*i + j holds
+ *    variable j of instance i's physical representative in FP64; the float2
+ *    copy of those variables mirrors it for readers in FP32.
+ */
+#ifndef SA_HEOM_H
+#define SA_HEOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SA_HEOM_MAXM 8  /* exponentials per local bath (static channel included) */
+#define SA_HEOM_MAXL 30 /* hierarchy depth */
+
+enum {
+    SA_OK = 0,
+    SA_ERR_INVALID_ARG = -1, /* N < 1, m outside 1..8, L outside 0..30, |c_k| = 0, non-finite input */
+    SA_ERR_UNSUPPORTED = -2, /* size beyond the 32-bit table indices, missing device */
+    SA_ERR_OOM = -3,         /* host or device allocation failed */
+    SA_ERR_CUDA = -4,        /* a CUDA runtime call failed; see sa_heom_last_error() */
+    SA_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait expired */
+    SA_ERR_NUMERIC = -6,     /* NaN or Inf in the observables */
+    SA_ERR_STATE = -7        /* handle built host-only, or wrong call order */
+};
+
+enum { SA_FP64 = 0, SA_FP32_AUX = 1 };                  /* precision */
+enum { SA_BUILD_DEVICE = 0, SA_BUILD_HOST_ONLY = 1 };   /* build flags */
+enum { SA_BATH_HIGH_T = 0, SA_BATH_MATSUBARA = 1, SA_BATH_PADE = 2 };
+
+/*
+ * One HTC + bath instance.  Units: any energy unit with hbar = 1.
+ *   N          molecules (1 .. 2^62); only multiplicities depend on it.
+ *   m, L       exponentials per local bath, hierarchy depth (Eq. n-label).
+ *   detuning   eps_x - omega_cav (the propagated frame has omega_cav = 0).
+ *   g          single-molecule coupling of Eq. HS (collective g*sqrt(N)).
+ *   kappa      photon population decay rate: -kappa/2 {|c><c|, .} on every
+ *              ADO (Lindblad on the cavity mode restricted to the manifold).
+ *   c, cc, nu  c_k, c-check_k, nu_k of Eq. BCF-exp, k < m.
+ */
+typedef struct sa_params {
+    int64_t N;
+    int32_t m;
+    int32_t L;
+    double detuning;
+    double g;
+    double kappa;
+    double c_re[SA_HEOM_MAXM], c_im[SA_HEOM_MAXM];
+    double cc_re[SA_HEOM_MAXM], cc_im[SA_HEOM_MAXM];
+    double nu_re[SA_HEOM_MAXM], nu_im[SA_HEOM_MAXM];
+} sa_params;
+
+/* Sizes of one instance or of a whole batch. */
+typedef struct sa_counts {
+    double log10_conventional_ados; /* log10 C(Nm+L, L), Eq. direct-ado-count */
+    int64_t n_vectors;              /* local vectors incl. the zero vector */
+    int64_t n_patterns;             /* canonical representatives, Eq. canonical-count-one */
+    int64_t n_vars;                 /* unique complex variables, Eq. Du-one */
+    int64_t n_categories;           /* sum over patterns of G */
+    int64_t n_records;              /* hierarchy connection records (pattern, category, k, +/-) */
+    int64_t n_terms;                /* per-variable hierarchy terms the records expand to */
+    int64_t state_bytes;            /* one state vector at the handle's precision */
+} sa_counts;
+
+typedef struct sa_heom sa_heom;
+
+/*
+ * sa_bath_drude_lorentz -- fill m, c, cc, nu of *p for the Drude-Lorentz
+ * density J(w) = 2 lambda gamma w / (w^2 + gamma^2) (Eq. Drude_Lorentz) in
+ * Eq. BCF-spectral, decomposed as Eq. BCF-exp:
+ *   SA_BATH_HIGH_T:    one term, c_0 = 2 lambda kT - i lambda gamma, nu_0 = gamma
+ *                      (n_poles ignored);
+ *   SA_BATH_MATSUBARA: gamma pole with cot(beta gamma/2) plus n_poles
+ *                      Matsubara poles nu_j = 2 pi j kT;
+ *   SA_BATH_PADE:      gamma pole plus n_poles poles of the [K-1/K] Pade
+ *                      approximant in x^2 of (coth x - 1/x)/x (K = n_poles);
+ *   sigma > 0 appends the static-disorder channel c = cc = sigma^2, nu = 0
+ *   (Eq. C_static).  Real rates give cc_k = conj(c_k) (text below Eq. BCF-exp).
+ * Other fields of *p are left untouched.  Errors: INVALID_ARG (non-positive
+ * lambda, gamma or kT, negative sigma, too many terms, n_poles > 12 for Pade).
+ */
+int sa_bath_drude_lorentz(double lambda, double gamma, double kT, int scheme, int n_poles,
+                          double sigma, sa_params* p);
+
+/*
+ * sa_heom_counts -- sizes of one instance without touching a device
+ * (canonical patterns of Eq. pattern-one, unique variables of Eq. uvar-count,
+ * connection records).  Pure host; builds the tables and drops them.
+ */
+int sa_heom_counts(const sa_params* p, sa_counts* out);
+
+/*
+ * sa_heom_build -- build the canonical patterns, categories, multiplicities
+ * (Eqs. Mq, M0), variable layout and the precomputed hierarchy connections
+ * (raw -> canonical targets with the aligned-target accessor resolved,
+ * Eqs. canonical-target-plus/minus, aligned-accessor, uvar-up, uvar-down) of
+ * `count` instances and, unless flags = SA_BUILD_HOST_ONLY, upload them to the
+ * current CUDA device and allocate the RK4 work buffers (two stage vectors
+ * and one accumulator, library-owned).  precision: SA_FP64 or SA_FP32_AUX.
+ * The handle owns everything it allocates until sa_heom_destroy.
+ * Errors: INVALID_ARG, UNSUPPORTED (more than 2^32 - 1 variables or records),
+ * OOM, CUDA.
+ */
+int sa_heom_build(const sa_params* params, int count, int precision, int flags, sa_heom** out);
+
+/* sa_heom_destroy -- free the handle and everything it owns; NULL is a no-op. */
+void sa_heom_destroy(sa_heom* h);
+
+/* sa_heom_info -- totals of the batch (inst = -1) or of instance inst. */
+int sa_heom_info(const sa_heom* h, int inst, sa_counts* out);
+
+/* sa_heom_var_offset -- first variable of instance inst in the batch vector. */
+int sa_heom_var_offset(const sa_heom* h, int inst, int64_t* out);
+
+/*
+ * Table dumps of instance inst (host copies, canonical order), for checking
+ * the builder against an independent implementation:
+ *   sa_heom_dump_vectors:   comp[n_vectors * m] local vectors (id 0 = zero).
+ *   sa_heom_dump_patterns:  per pattern tier, r (nonzero molecules), G, h,
+ *                           var_off (n_patterns + 1, instance-relative),
+ *                           cat_off (n_patterns + 1), ids[n_patterns * L]
+ *                           (vector ids padded with -1).
+ *   sa_heom_dump_categories: vector id and multiplicity M_q of each category.
+ *   sa_heom_dump_terms:     the per-variable hierarchy terms the records
+ *                           expand to: variable, source variable (both
+ *                           instance-relative), channel k, occupation n of
+ *                           the moved molecule before the move, dir (+1
+ *                           raise, -1 lower), side (0: row delta, 1: column
+ *                           delta of Eq. projector-commutator-element).  The
+ *                           exactly cancelling raise pair of P_q is omitted.
+ * Array sizes come from sa_heom_info.  Pointers may be NULL to skip a field.
+ */
+int sa_heom_dump_vectors(const sa_heom* h, int inst, uint8_t* comp);
+int sa_heom_dump_patterns(const sa_heom* h, int inst, int32_t* tier, int32_t* r, int32_t* G, int32_t* hcount,
+                          int64_t* var_off, int64_t* cat_off, int32_t* ids);
+int sa_heom_dump_categories(const sa_heom* h, int inst, int32_t* vec_id, int64_t* mult);
+int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, int32_t* k, int32_t* n,
+                       int32_t* dir, int32_t* side);
+
+/* sa_heom_state_bytes -- bytes of one state vector of the whole batch. */
+int sa_heom_state_bytes(const sa_heom* h, size_t* bytes);
+
+/*
+ * sa_heom_init_state -- factorised initial hierarchy (Eqs. factorized-
+ * initial-zero/higher): every ADO zero except the physical representative,
+ * set per instance from rho0[10 * i ..]: Z, X_0, Y_0, P_0, T_0 as (re, im)
+ * pairs (T_0 ignored for N = 1).  d_state: caller-owned device buffer of
+ * sa_heom_state_bytes bytes.  Asynchronous on `stream`.
+ */
+int sa_heom_init_state(const sa_heom* h, const double* rho0, void* d_state, void* stream);
+
+/*
+ * sa_heom_state_upload / sa_heom_state_download -- copy a full state between
+ * a host complex128 array in the canonical layout (n_vars_total complex
+ * values) and a device state buffer, converting to / from the handle's
+ * precision (the FP64 copies of the physical representative are exact).
+ * Synchronous with respect to the host.
+ */
+int sa_heom_state_upload(const sa_heom* h, const double* host_x, void* d_state, void* stream);
+int sa_heom_state_download(const sa_heom* h, const void* d_state, double* host_x, void* stream);
+
+/*
+ * sa_heom_rhs -- one evaluation of the matrix-free right-hand side
+ * dR/dt = M_u R (Eq. uvar-propagator; Hamiltonian terms from grouped sums,
+ * Eqs. grouped-row-sum, grouped-column-sum, HZ, HX and their Y, P, S, T
+ * counterparts; damping Gamma_Lambda; cavity loss; hierarchy terms of
+ * Eqs. uvar-up, uvar-down).  d_x, d_dx: device buffers of state layout
+ * (may not alias).  Asynchronous on `stream`.
+ */
+int sa_heom_rhs(sa_heom* h, const void* d_x, void* d_dx, void* stream);
+
+/*
+ * sa_heom_step -- one classical RK4 step of size dt (the integrator of
+ * Sec. V) on d_state, in place, as four fused right-hand-side + stage
+ * kernels.  Asynchronous on `stream`.
+ */
+int sa_heom_step(sa_heom* h, void* d_state, double dt, void* stream);
+
+/*
+ * sa_heom_propagate -- nsteps RK4 steps.  The steps run as a CUDA graph of
+ * obs_every steps (captured on first use for this state pointer, dt and
+ * obs_every, then replayed).  If h_obs is not NULL, the observables of
+ * sa_heom_observables are recorded for every instance before the first step
+ * and after every obs_every steps (and after the last step): h_obs receives
+ * rows * count * 8 doubles with rows = 1 + ceil(nsteps / obs_every).
+ * Returns when the work is done when h_obs is not NULL; otherwise
+ * asynchronous on `stream`.
+ */
+int sa_heom_propagate(sa_heom* h, void* d_state, double dt, int64_t nsteps, int64_t obs_every, double* h_obs,
+                      void* stream);
+
+/*
+ * sa_heom_observables -- Eqs. trace-uvar, Pcav-uvar, Pexc-uvar, PB-uvar,
+ * PD-uvar, Pplus-uvar, Pminus-uvar from the FP64 physical representative of
+ * every instance: out[8 * i ..] = Tr, P_cav, P_exc, P_B, P_D, P_+, P_-,
+ * max Hermiticity defect of rho_S.  theta from tan(2 theta) =
+ * Omega_R / Delta, Delta = omega_cav - eps_x, theta in [0, pi/2]
+ * (Eq. polariton-states).  Synchronous; returns NUMERIC if a value is not
+ * finite.
+ */
+int sa_heom_observables(sa_heom* h, const void* d_state, double* out, void* stream);
+
+/*
+ * Launch tuning.  block: threads per CTA (64..1024, multiple of 32);
+ * chunk: variables per work item (>= largest pattern, <= 4096); queue: 1 for
+ * the dynamic work queue, 0 for a static strided assignment.  Any argument
+ * <= 0 keeps its current value.  sa_heom_autotune times a few candidates of
+ * the RK4 stage kernel on d_state (which it leaves changed) and keeps the
+ * fastest; best[3] receives block, chunk, queue.
+ */
+int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue);
+int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best);
+
+/* Number of stage-kernel launches one RK4 step issues (for launch counting). */
+int sa_heom_launches_per_step(const sa_heom* h);
+
+const char* sa_heom_strerror(int code);
+const char* sa_heom_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SA_HEOM_H */

@@ -1,0 +1,296 @@
+"""Thin Python binding of the C ABI in ``include/sa_heom.h`` (ctypes).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of ``libsaheom.so``.  Device buffers are plain device pointers, in
+practice the ``data_ptr()`` of torch tensors, and streams are
+``torch.cuda.Stream.cuda_stream`` values; PyTorch is used for device memory
+and streams and nothing else.  If the shared library is missing, importing
+this module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsaheom.so")
+MAXM = 8
+
+SA_FP64, SA_FP32_AUX = 0, 1
+SA_BUILD_DEVICE, SA_BUILD_HOST_ONLY = 0, 1
+BATH_HIGH_T, BATH_MATSUBARA, BATH_PADE = 0, 1, 2
+ERRORS = {0: "SA_OK", -1: "SA_ERR_INVALID_ARG", -2: "SA_ERR_UNSUPPORTED", -3: "SA_ERR_OOM",
+          -4: "SA_ERR_CUDA", -5: "SA_ERR_TIMEOUT", -6: "SA_ERR_NUMERIC", -7: "SA_ERR_STATE"}
+
+
+class SaHeomError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({detail})")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    """sa_params of include/sa_heom.h."""
+    _fields_ = [
+        ("N", ctypes.c_int64), ("m", ctypes.c_int32), ("L", ctypes.c_int32),
+        ("detuning", ctypes.c_double), ("g", ctypes.c_double), ("kappa", ctypes.c_double),
+        ("c_re", ctypes.c_double * MAXM), ("c_im", ctypes.c_double * MAXM),
+        ("cc_re", ctypes.c_double * MAXM), ("cc_im", ctypes.c_double * MAXM),
+        ("nu_re", ctypes.c_double * MAXM), ("nu_im", ctypes.c_double * MAXM),
+    ]
+
+    def bath(self) -> dict:
+        m = self.m
+        return {"c": np.array([complex(self.c_re[k], self.c_im[k]) for k in range(m)]),
+                "cc": np.array([complex(self.cc_re[k], self.cc_im[k]) for k in range(m)]),
+                "nu": np.array([complex(self.nu_re[k], self.nu_im[k]) for k in range(m)])}
+
+
+class Counts(ctypes.Structure):
+    _fields_ = [("log10_conventional_ados", ctypes.c_double), ("n_vectors", ctypes.c_int64),
+                ("n_patterns", ctypes.c_int64), ("n_vars", ctypes.c_int64), ("n_categories", ctypes.c_int64),
+                ("n_records", ctypes.c_int64), ("n_terms", ctypes.c_int64), ("state_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"native library {LIB_PATH} is missing; run paper_2608_20657_b300._build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        P = ctypes.POINTER
+        sig = {
+            "sa_bath_drude_lorentz": [dbl, dbl, dbl, i32, i32, dbl, P(Params)],
+            "sa_heom_counts": [P(Params), P(Counts)],
+            "sa_heom_build": [P(Params), i32, i32, i32, P(vp)],
+            "sa_heom_info": [vp, i32, P(Counts)],
+            "sa_heom_var_offset": [vp, i32, P(i64)],
+            "sa_heom_dump_vectors": [vp, i32, vp],
+            "sa_heom_dump_patterns": [vp, i32, vp, vp, vp, vp, vp, vp, vp],
+            "sa_heom_dump_categories": [vp, i32, vp, vp],
+            "sa_heom_dump_terms": [vp, i32, vp, vp, vp, vp, vp, vp],
+            "sa_heom_state_bytes": [vp, P(ctypes.c_size_t)],
+            "sa_heom_init_state": [vp, vp, vp, vp],
+            "sa_heom_state_upload": [vp, vp, vp, vp],
+            "sa_heom_state_download": [vp, vp, vp, vp],
+            "sa_heom_rhs": [vp, vp, vp, vp],
+            "sa_heom_step": [vp, vp, dbl, vp],
+            "sa_heom_propagate": [vp, vp, dbl, i64, i64, vp, vp],
+            "sa_heom_observables": [vp, vp, vp, vp],
+            "sa_heom_set_tuning": [vp, i32, i32, i32],
+            "sa_heom_autotune": [vp, vp, vp, vp],
+            "sa_heom_launches_per_step": [vp],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = i32
+        L.sa_heom_destroy.argtypes = [vp]
+        L.sa_heom_destroy.restype = None
+        L.sa_heom_strerror.argtypes = [i32]
+        L.sa_heom_strerror.restype = ctypes.c_char_p
+        L.sa_heom_last_error.argtypes = []
+        L.sa_heom_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return ["sa_bath_drude_lorentz", "sa_heom_counts", "sa_heom_build", "sa_heom_destroy", "sa_heom_info",
+            "sa_heom_var_offset", "sa_heom_dump_vectors", "sa_heom_dump_patterns", "sa_heom_dump_categories",
+            "sa_heom_dump_terms", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_state_upload",
+            "sa_heom_state_download", "sa_heom_rhs", "sa_heom_step", "sa_heom_propagate", "sa_heom_observables",
+            "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_launches_per_step", "sa_heom_strerror",
+            "sa_heom_last_error"]
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise SaHeomError(rc, where, lib().sa_heom_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev(t) -> ctypes.c_void_p:
+    """Device pointer of a torch tensor (or an int address)."""
+    return ctypes.c_void_p(t if isinstance(t, int) else t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+
+
+def make_params(N, m=None, L=0, bath=None, detuning=0.0, g=0.0, kappa=0.0) -> Params:
+    """sa_params from a bath dict {c, cc, nu} (complex arrays of length m)."""
+    p = Params()
+    c = np.asarray(bath["c"], complex)
+    cc = np.asarray(bath["cc"], complex)
+    nu = np.asarray(bath["nu"], complex)
+    m = len(c) if m is None else m
+    p.N, p.m, p.L = int(N), int(m), int(L)
+    p.detuning, p.g, p.kappa = float(detuning), float(g), float(kappa)
+    for k in range(m):
+        p.c_re[k], p.c_im[k] = c[k].real, c[k].imag
+        p.cc_re[k], p.cc_im[k] = cc[k].real, cc[k].imag
+        p.nu_re[k], p.nu_im[k] = nu[k].real, nu[k].imag
+    return p
+
+
+def bath_drude_lorentz(lam, gam, kT, scheme=BATH_MATSUBARA, n_poles=1, sigma=0.0) -> dict:
+    """sa_bath_drude_lorentz: {c, cc, nu} of Eq. BCF-exp."""
+    p = Params()
+    _check(lib().sa_bath_drude_lorentz(lam, gam, kT, scheme, n_poles, sigma, ctypes.byref(p)), "sa_bath_drude_lorentz")
+    return p.bath()
+
+
+def counts(p: Params) -> dict:
+    c = Counts()
+    _check(lib().sa_heom_counts(ctypes.byref(p), ctypes.byref(c)), "sa_heom_counts")
+    return c.as_dict()
+
+
+class Heom:
+    """A built batch of instances (sa_heom handle)."""
+
+    def __init__(self, params, precision: int = SA_FP64, host_only: bool = False):
+        if isinstance(params, Params):
+            params = [params]
+        self.params = list(params)
+        arr = (Params * len(self.params))(*self.params)
+        h = ctypes.c_void_p()
+        _check(lib().sa_heom_build(arr, len(self.params), precision,
+                                   SA_BUILD_HOST_ONLY if host_only else SA_BUILD_DEVICE, ctypes.byref(h)),
+               "sa_heom_build")
+        self._h = h
+        self.count = len(self.params)
+        self.precision = precision
+        tot = self.info()
+        self.n_vars = tot["n_vars"]
+        self.n_patterns = tot["n_patterns"]
+        sb = ctypes.c_size_t()
+        _check(lib().sa_heom_state_bytes(self._h, ctypes.byref(sb)), "sa_heom_state_bytes")
+        self.state_bytes = int(sb.value)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sa_heom_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- tables ------------------------------------------------------
+    def info(self, inst: int = -1) -> dict:
+        c = Counts()
+        _check(lib().sa_heom_info(self._h, inst, ctypes.byref(c)), "sa_heom_info")
+        return c.as_dict()
+
+    def var_offset(self, inst: int) -> int:
+        v = ctypes.c_int64()
+        _check(lib().sa_heom_var_offset(self._h, inst, ctypes.byref(v)), "sa_heom_var_offset")
+        return v.value
+
+    def dump_vectors(self, inst: int = 0) -> np.ndarray:
+        i = self.info(inst)
+        out = np.zeros((i["n_vectors"], self.params[inst].m), np.uint8)
+        _check(lib().sa_heom_dump_vectors(self._h, inst, _ptr(out)), "sa_heom_dump_vectors")
+        return out
+
+    def dump_patterns(self, inst: int = 0) -> dict:
+        i = self.info(inst)
+        P, L = i["n_patterns"], self.params[inst].L
+        tier, r, G, h = (np.zeros(P, np.int32) for _ in range(4))
+        var_off = np.zeros(P + 1, np.int64)
+        cat_off = np.zeros(P + 1, np.int64)
+        ids = np.zeros((P, max(L, 1)), np.int32)
+        _check(lib().sa_heom_dump_patterns(self._h, inst, _ptr(tier), _ptr(r), _ptr(G), _ptr(h), _ptr(var_off),
+                                           _ptr(cat_off), _ptr(ids)), "sa_heom_dump_patterns")
+        nc = i["n_categories"]
+        vec_id = np.zeros(max(nc, 1), np.int32)
+        mult = np.zeros(max(nc, 1), np.int64)
+        _check(lib().sa_heom_dump_categories(self._h, inst, _ptr(vec_id), _ptr(mult)), "sa_heom_dump_categories")
+        return dict(tier=tier, r=r, G=G, h=h, var_off=var_off, cat_off=cat_off, ids=ids[:, :L],
+                    cat_id=vec_id[:nc], cat_M=mult[:nc])
+
+    def dump_terms(self, inst: int = 0) -> dict:
+        n = self.info(inst)["n_terms"]
+        var, src = np.zeros(n, np.int64), np.zeros(n, np.int64)
+        k, nn, d, s = (np.zeros(n, np.int32) for _ in range(4))
+        _check(lib().sa_heom_dump_terms(self._h, inst, _ptr(var), _ptr(src), _ptr(k), _ptr(nn), _ptr(d), _ptr(s)),
+               "sa_heom_dump_terms")
+        return dict(var=var, src=src, k=k, n=nn, dir=d, side=s)
+
+    # ---- device state -------------------------------------------------
+    def new_state(self, device="cuda"):
+        import torch
+
+        return torch.zeros(self.state_bytes, dtype=torch.uint8, device=device)
+
+    def init_state(self, state, rho0, stream=None):
+        """rho0: (count, 5) complex: Z, X_0, Y_0, P_0, T_0."""
+        r = np.zeros((self.count, 5), complex)
+        r[:] = np.asarray(rho0, complex).reshape(-1, 5) if np.ndim(rho0) > 1 else np.asarray(rho0, complex)
+        flat = np.ascontiguousarray(r.view(np.float64).reshape(-1))
+        _check(lib().sa_heom_init_state(self._h, _ptr(flat), _dev(state), _stream(stream)), "sa_heom_init_state")
+
+    def upload(self, state, x: np.ndarray, stream=None):
+        x = np.ascontiguousarray(x, np.complex128)
+        assert x.shape == (self.n_vars,)
+        _check(lib().sa_heom_state_upload(self._h, _ptr(x), _dev(state), _stream(stream)), "sa_heom_state_upload")
+
+    def download(self, state, stream=None) -> np.ndarray:
+        x = np.zeros(self.n_vars, np.complex128)
+        _check(lib().sa_heom_state_download(self._h, _dev(state), _ptr(x), _stream(stream)), "sa_heom_state_download")
+        return x
+
+    def rhs(self, x, dx, stream=None):
+        _check(lib().sa_heom_rhs(self._h, _dev(x), _dev(dx), _stream(stream)), "sa_heom_rhs")
+
+    def step(self, state, dt: float, stream=None):
+        _check(lib().sa_heom_step(self._h, _dev(state), float(dt), _stream(stream)), "sa_heom_step")
+
+    def propagate(self, state, dt: float, nsteps: int, obs_every: int = 0, observe: bool = True, stream=None):
+        if not observe:
+            _check(lib().sa_heom_propagate(self._h, _dev(state), float(dt), int(nsteps), int(obs_every), None,
+                                           _stream(stream)), "sa_heom_propagate")
+            return None
+        oe = obs_every if obs_every > 0 else max(nsteps, 1)
+        rows = 1 + (nsteps + oe - 1) // oe
+        out = np.zeros((rows, self.count, 8))
+        _check(lib().sa_heom_propagate(self._h, _dev(state), float(dt), int(nsteps), int(oe), _ptr(out),
+                                       _stream(stream)), "sa_heom_propagate")
+        return out
+
+    def observables(self, state, stream=None) -> np.ndarray:
+        out = np.zeros((self.count, 8))
+        _check(lib().sa_heom_observables(self._h, _dev(state), _ptr(out), _stream(stream)), "sa_heom_observables")
+        return out
+
+    def set_tuning(self, block=0, chunk=0, queue=-1):
+        _check(lib().sa_heom_set_tuning(self._h, int(block), int(chunk), int(queue)), "sa_heom_set_tuning")
+
+    def autotune(self, state, stream=None):
+        best = (ctypes.c_int * 3)()
+        _check(lib().sa_heom_autotune(self._h, _dev(state), _stream(stream), best), "sa_heom_autotune")
+        return tuple(best)
+
+    def launches_per_step(self) -> int:
+        return int(lib().sa_heom_launches_per_step(self._h))

@@ -1,0 +1,811 @@
+// api.cu -- the C ABI of include/sa_heom.h: batch assembly, device tables,
+// RK4 launch sequence, CUDA-graph capture of the step loop, observables,
+// state marshalling and the launch autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "sa_internal.h"
+
+namespace sa {
+cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, cudaStream_t st);
+cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm);
+cudaError_t launch_observables(const InstDev* inst, const double* theta, int ninst, const void* main64,
+                               const void* side64, double* out, cudaStream_t st);
+cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0, void* main64, void* main32,
+                             void* side64, cudaStream_t st);
+}  // namespace sa
+
+using namespace sa;
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char* where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return SA_ERR_CUDA;
+}
+#define CK(call)                                               \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+    } while (0)
+
+template <typename V>
+int upload(void** dptr, const std::vector<V>& h) {
+    size_t b = std::max<size_t>(h.size() * sizeof(V), 16);
+    cudaError_t e = cudaMalloc(dptr, b);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(table)");
+    if (!h.empty()) {
+        e = cudaMemcpy(*dptr, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(table)");
+    }
+    return SA_OK;
+}
+}  // namespace
+
+struct sa_heom {
+    int count = 0;
+    int precision = SA_FP64;
+    bool host_only = true;
+    std::vector<HostInstance> inst;
+    std::vector<uint64_t> var_begin;  // per instance + total
+    int64_t nvar = 0, npat = 0, ncat = 0, nrec = 0;
+    // batch tables (host)
+    std::vector<PatHdr> hdr;
+    std::vector<uint32_t> cat_word;
+    std::vector<double> catMd;
+    std::vector<float> catMf;
+    std::vector<double> gamma_d;
+    std::vector<float> gamma_f;
+    std::vector<Record> rec;
+    std::vector<InstDev> instdev;
+    std::vector<double> theta;
+    std::vector<double> coef_row_d, coef_col_d;
+    std::vector<float> coef_row_f, coef_col_f;
+    std::vector<uint16_t> lut;
+    std::vector<uint32_t> lut_off;
+    std::vector<uint32_t> chunk_begin;
+    int max_u = 0;
+    // tuning
+    int block = 256, chunk = 1024, use_queue = 1;
+    // device
+    int device = -1, num_sms = 0;
+    void *d_hdr = nullptr, *d_cat_word = nullptr, *d_catM = nullptr, *d_catMd = nullptr, *d_gamma = nullptr;
+    void *d_rec = nullptr, *d_inst = nullptr, *d_theta = nullptr, *d_coef_row = nullptr, *d_coef_col = nullptr;
+    void *d_coef_row_d = nullptr, *d_coef_col_d = nullptr, *d_lut = nullptr, *d_lut_off = nullptr;
+    void* d_chunk = nullptr;
+    void* d_work[3] = {nullptr, nullptr, nullptr};  // acc, xa, xb
+    unsigned int* d_queue = nullptr;
+    size_t queue_slots = 0;
+    double* d_obs = nullptr;
+    size_t obs_cap = 0;
+    double* d_rho0 = nullptr;
+    cudaStream_t cap = nullptr;
+    size_t state_bytes = 0, side_off = 0;
+    LaunchCfg cfg{256, 1024, 1, 1};
+    std::map<std::tuple<const void*, uint64_t, int64_t>, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+void build_lut(sa_heom* h) {
+    h->lut_off.assign(kMaxG + 2, 0);
+    h->lut.clear();
+    for (int G = 0; G <= kMaxG; ++G) {
+        h->lut_off[G] = uint32_t(h->lut.size());
+        for (int loc = 0; G > 0 && loc < (G + 1) * (G + 1); ++loc) {
+            int kind, q = 0, r = 0;
+            if (loc == 0) kind = 0;
+            else if (loc <= G) { kind = 1; q = loc; }
+            else if (loc <= 2 * G) { kind = 2; q = loc - G; }
+            else if (loc <= 3 * G) { kind = 3; q = loc - 2 * G; }
+            else {
+                kind = 4;
+                int s = loc - 3 * G - 1;
+                q = s / (G - 1) + 1;
+                r = s % (G - 1) + 1;
+                if (r >= q) ++r;
+            }
+            h->lut.push_back(uint16_t(kind | (q << 3) | (r << 8)));
+        }
+    }
+    h->lut_off[kMaxG + 1] = uint32_t(h->lut.size());
+}
+
+void build_chunks(sa_heom* h) {
+    h->chunk_begin.clear();
+    h->chunk_begin.push_back(0);
+    int64_t vars = 0, pats = 0;
+    for (int64_t p = 0; p < h->npat; ++p) {
+        int64_t u = int64_t(h->hdr[p + 1].var_off) - int64_t(h->hdr[p].var_off);
+        if (pats > 0 && (vars + u > h->chunk || pats >= kMaxPatPerChunk)) {
+            h->chunk_begin.push_back(uint32_t(p));
+            vars = 0;
+            pats = 0;
+        }
+        vars += u;
+        ++pats;
+    }
+    h->chunk_begin.push_back(uint32_t(h->npat));
+}
+
+int apply_tuning(sa_heom* h) {
+    build_chunks(h);
+    h->cfg.block = h->block;
+    h->cfg.chunk = h->chunk;
+    h->cfg.use_queue = h->use_queue;
+    const uint32_t nchunks = uint32_t(h->chunk_begin.size() - 1);
+    if (h->host_only) return SA_OK;
+    if (h->d_chunk) cudaFree(h->d_chunk);
+    h->d_chunk = nullptr;
+    int rc = upload(&h->d_chunk, h->chunk_begin);
+    if (rc) return rc;
+    int occ = 0;
+    CK(stage_occupancy(h->cfg, h->precision == SA_FP64, &occ));
+    if (occ < 1) return fail(SA_ERR_UNSUPPORTED, "stage kernel does not fit on an SM with this tuning");
+    h->cfg.grid = h->use_queue ? int(std::min<int64_t>(int64_t(h->num_sms) * occ, nchunks)) : int(nchunks);
+    if (h->cfg.grid < 1) h->cfg.grid = 1;
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    return SA_OK;
+}
+
+void free_device(sa_heom* h) {
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    void* ptrs[] = {h->d_hdr, h->d_cat_word, h->d_catM, h->d_catMd, h->d_gamma, h->d_rec, h->d_inst, h->d_theta,
+                    h->d_coef_row, h->d_coef_col, h->d_coef_row_d, h->d_coef_col_d, h->d_lut, h->d_lut_off,
+                    h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (h->cap) cudaStreamDestroy(h->cap);
+}
+
+int ensure_queue(sa_heom* h, size_t slots) {
+    if (slots <= h->queue_slots) return SA_OK;
+    if (h->d_queue) cudaFree(h->d_queue);
+    h->d_queue = nullptr;
+    size_t n = std::max<size_t>(slots, 64);
+    CK(cudaMalloc(&h->d_queue, n * sizeof(unsigned int)));
+    CK(cudaMemset(h->d_queue, 0, n * sizeof(unsigned int)));
+    h->queue_slots = n;
+    return SA_OK;
+}
+
+StageLaunch base_launch(const sa_heom* h) {
+    StageLaunch s{};
+    s.hdr = h->d_hdr;
+    s.cat_word = h->d_cat_word;
+    s.cat_M = h->d_catM;
+    s.gamma = h->d_gamma;
+    s.rec = h->d_rec;
+    s.chunk_begin = h->d_chunk;
+    s.inst = h->d_inst;
+    s.coef_row = h->d_coef_row;
+    s.coef_col = h->d_coef_col;
+    s.cat_Md = h->d_catMd;
+    s.coef_row_d = h->d_coef_row_d;
+    s.coef_col_d = h->d_coef_col_d;
+    s.lut = h->d_lut;
+    s.lut_off = h->d_lut_off;
+    s.nchunks = uint32_t(h->chunk_begin.size() - 1);
+    return s;
+}
+
+void* side(const sa_heom* h, const void* buf) {
+    if (h->precision == SA_FP64 || !buf) return nullptr;
+    return static_cast<char*>(const_cast<void*>(buf)) + h->side_off;
+}
+
+// The four fused RK4 stage launches of one step; slot: first queue counter.
+int enqueue_step(sa_heom* h, void* y, double dt, size_t slot, cudaStream_t st) {
+    void* acc = h->d_work[0];
+    void* xa = h->d_work[1];
+    void* xb = h->d_work[2];
+    const void* xin[4] = {y, xa, xb, xa};
+    void* xout[4] = {xa, xb, xa, nullptr};
+    for (int s = 0; s < 4; ++s) {
+        StageLaunch L = base_launch(h);
+        L.x_in = xin[s];
+        L.x_out = xout[s];
+        L.y = y;
+        L.acc = acc;
+        L.y_out = y;
+        L.xs_in = side(h, xin[s]);
+        L.xs_out = side(h, xout[s]);
+        L.ys = side(h, y);
+        L.accs = side(h, acc);
+        L.ys_out = side(h, y);
+        L.dt = dt;
+        L.stage = s;
+        L.queue = h->d_queue + slot + s;
+        CK(launch_stage(L, h->cfg, h->precision == SA_FP64, st));
+    }
+    return SA_OK;
+}
+
+int check_device(const sa_heom* h) {
+    if (!h) return fail(SA_ERR_INVALID_ARG, "null handle");
+    if (h->host_only) return fail(SA_ERR_STATE, "handle was built with SA_BUILD_HOST_ONLY");
+    return SA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sa_heom_strerror(int code) {
+    switch (code) {
+        case SA_OK: return "ok";
+        case SA_ERR_INVALID_ARG: return "invalid argument";
+        case SA_ERR_UNSUPPORTED: return "unsupported size or configuration";
+        case SA_ERR_OOM: return "out of memory";
+        case SA_ERR_CUDA: return "CUDA runtime error";
+        case SA_ERR_TIMEOUT: return "bounded device wait expired";
+        case SA_ERR_NUMERIC: return "non-finite observable";
+        case SA_ERR_STATE: return "invalid handle state";
+    }
+    return "unknown error";
+}
+
+const char* sa_heom_last_error(void) { return g_err.c_str(); }
+
+int sa_bath_drude_lorentz(double lambda, double gamma, double kT, int scheme, int n_poles, double sigma,
+                          sa_params* p) {
+    std::string err;
+    int rc = drude_lorentz(lambda, gamma, kT, scheme, n_poles, sigma, p, err);
+    if (rc) g_err = err;
+    return rc;
+}
+
+static void fill_counts(const HostInstance& hi, int precision, sa_counts* out) {
+    const double nm = double(hi.N) * hi.m;
+    out->log10_conventional_ados = (std::lgamma(nm + hi.L + 1.0) - std::lgamma(hi.L + 1.0) - std::lgamma(nm + 1.0)) /
+                                   std::log(10.0);
+    out->n_vectors = hi.V;
+    out->n_patterns = hi.P;
+    out->n_vars = int64_t(hi.var_off[hi.P]);
+    out->n_categories = int64_t(hi.cat_vec.size());
+    out->n_records = int64_t(hi.rec.size());
+    out->n_terms = hi.n_terms;
+    out->state_bytes = out->n_vars * (precision == SA_FP64 ? 16 : 8);
+}
+
+int sa_heom_counts(const sa_params* p, sa_counts* out) {
+    if (!p || !out) return fail(SA_ERR_INVALID_ARG, "null argument");
+    HostInstance hi;
+    std::string err;
+    int rc = build_instance(*p, hi, err);
+    if (rc) return fail(rc, err);
+    fill_counts(hi, SA_FP64, out);
+    return SA_OK;
+}
+
+int sa_heom_build(const sa_params* params, int count, int precision, int flags, sa_heom** out) {
+    if (!params || !out || count < 1 || count > 65535 || (precision != SA_FP64 && precision != SA_FP32_AUX))
+        return fail(SA_ERR_INVALID_ARG, "params, out, 1 <= count <= 65535 and a valid precision required");
+    *out = nullptr;
+    sa_heom* h = new (std::nothrow) sa_heom();
+    if (!h) return fail(SA_ERR_OOM, "handle");
+    h->count = count;
+    h->precision = precision;
+    h->host_only = (flags & SA_BUILD_HOST_ONLY) != 0;
+    h->inst.resize(count);
+    for (int i = 0; i < count; ++i) {
+        std::string err;
+        int rc = build_instance(params[i], h->inst[i], err);
+        if (rc) {
+            delete h;
+            return fail(rc, "instance " + std::to_string(i) + ": " + err);
+        }
+    }
+    // ---- batch assembly
+    h->var_begin.assign(count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+        const HostInstance& hi = h->inst[i];
+        h->var_begin[i + 1] = h->var_begin[i] + hi.var_off[hi.P];
+        h->npat += hi.P;
+        h->ncat += int64_t(hi.cat_vec.size());
+        h->nrec += int64_t(hi.rec.size());
+    }
+    h->nvar = int64_t(h->var_begin[count]);
+    if (h->nvar >= (int64_t(1) << 32) || h->nrec >= (int64_t(1) << 32) || h->ncat >= (int64_t(1) << 32)) {
+        delete h;
+        return fail(SA_ERR_UNSUPPORTED, "batch exceeds 32-bit table indices");
+    }
+    h->hdr.resize(h->npat + 1);
+    h->cat_word.reserve(h->ncat);
+    h->catMd.reserve(h->ncat);
+    h->catMf.reserve(h->ncat);
+    h->gamma_d.reserve(2 * h->npat);
+    h->gamma_f.reserve(2 * h->npat);
+    h->rec.reserve(h->nrec);
+    h->instdev.resize(count);
+    h->theta.resize(count);
+    h->coef_row_d.assign(size_t(2) * kCoefPerInst * count, 0.0);
+    h->coef_col_d.assign(size_t(2) * kCoefPerInst * count, 0.0);
+    int64_t pbase = 0;
+    for (int i = 0; i < count; ++i) {
+        const HostInstance& hi = h->inst[i];
+        const uint32_t vb = uint32_t(h->var_begin[i]);
+        const uint32_t rb = uint32_t(h->rec.size()), cb = uint32_t(h->cat_word.size());
+        for (int64_t p = 0; p < hi.P; ++p) {
+            PatHdr& H = h->hdr[pbase + p];
+            H.var_off = vb + uint32_t(hi.var_off[p]);
+            H.rec_off = rb + hi.rec_off[p];
+            H.cat_off = cb + hi.cat_off[p];
+            H.inst = uint16_t(i);
+            H.G = hi.G[p];
+            H.tier = hi.tier[p];
+            h->gamma_d.push_back(hi.gamma_re[p]);
+            h->gamma_d.push_back(hi.gamma_im[p]);
+            h->gamma_f.push_back(float(hi.gamma_re[p]));
+            h->gamma_f.push_back(float(hi.gamma_im[p]));
+            h->max_u = std::max<int>(h->max_u, int(hi.var_off[p + 1] - hi.var_off[p]));
+        }
+        for (size_t c = 0; c < hi.cat_vec.size(); ++c) {
+            h->cat_word.push_back(hi.cat_word[c]);
+            h->catMd.push_back(double(hi.cat_M[c]));
+            h->catMf.push_back(float(hi.cat_M[c]));
+        }
+        for (const Record& r : hi.rec) h->rec.push_back(Record{vb + r.target, r.packed});
+        InstDev& D = h->instdev[i];
+        D.g = hi.p.g;
+        D.detuning = hi.p.detuning;
+        D.kappa = hi.p.kappa;
+        D.N = double(hi.N);
+        D.gf = float(hi.p.g);
+        D.detf = float(hi.p.detuning);
+        D.kappaf = float(hi.p.kappa);
+        D.pad = 0;
+        D.coef_base = uint32_t(i) * kCoefPerInst;
+        D.side = uint32_t(i) * kSideSlots;
+        D.var_begin = vb;
+        D.n_rho0 = hi.N >= 2 ? 5u : 4u;
+        h->theta[i] = 0.5 * std::atan2(2.0 * hi.p.g * std::sqrt(double(hi.N)), -hi.p.detuning);
+        std::copy(hi.coef_row.begin(), hi.coef_row.end(), h->coef_row_d.begin() + size_t(2) * kCoefPerInst * i);
+        std::copy(hi.coef_col.begin(), hi.coef_col.end(), h->coef_col_d.begin() + size_t(2) * kCoefPerInst * i);
+        pbase += hi.P;
+    }
+    PatHdr& S = h->hdr[h->npat];  // sentinel
+    S.var_off = uint32_t(h->nvar);
+    S.rec_off = uint32_t(h->nrec);
+    S.cat_off = uint32_t(h->ncat);
+    S.inst = 0;
+    S.G = 0;
+    S.tier = 0;
+    h->coef_row_f.assign(h->coef_row_d.begin(), h->coef_row_d.end());
+    h->coef_col_f.assign(h->coef_col_d.begin(), h->coef_col_d.end());
+    build_lut(h);
+    h->chunk = std::max(1024, (h->max_u + 31) / 32 * 32);
+    // state layout
+    if (precision == SA_FP64) {
+        h->state_bytes = size_t(h->nvar) * 16;
+        h->side_off = 0;
+    } else {
+        h->side_off = (size_t(h->nvar) * 8 + 255) / 256 * 256;
+        h->state_bytes = h->side_off + size_t(count) * kSideSlots * 16;
+    }
+    if (h->host_only) {
+        build_chunks(h);
+        *out = h;
+        return SA_OK;
+    }
+    // ---- device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    h->device = dev;
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    int rc = SA_OK;
+    const bool f64 = precision == SA_FP64;
+    if (!rc) rc = upload(&h->d_hdr, h->hdr);
+    if (!rc) rc = upload(&h->d_cat_word, h->cat_word);
+    if (!rc) rc = f64 ? upload(&h->d_catM, h->catMd) : upload(&h->d_catM, h->catMf);
+    if (!rc) rc = upload(&h->d_catMd, h->catMd);
+    if (!rc) rc = f64 ? upload(&h->d_gamma, h->gamma_d) : upload(&h->d_gamma, h->gamma_f);
+    if (!rc) rc = upload(&h->d_rec, h->rec);
+    if (!rc) rc = upload(&h->d_inst, h->instdev);
+    if (!rc) rc = upload(&h->d_theta, h->theta);
+    if (!rc) rc = f64 ? upload(&h->d_coef_row, h->coef_row_d) : upload(&h->d_coef_row, h->coef_row_f);
+    if (!rc) rc = f64 ? upload(&h->d_coef_col, h->coef_col_d) : upload(&h->d_coef_col, h->coef_col_f);
+    if (!rc) rc = upload(&h->d_coef_row_d, h->coef_row_d);
+    if (!rc) rc = upload(&h->d_coef_col_d, h->coef_col_d);
+    if (!rc) rc = upload(&h->d_lut, h->lut);
+    if (!rc) rc = upload(&h->d_lut_off, h->lut_off);
+    for (int w = 0; w < 3 && !rc; ++w) {
+        e = cudaMalloc(&h->d_work[w], h->state_bytes);
+        if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? fail(SA_ERR_OOM, "RK4 work buffers")
+                                                                    : cuda_fail(e, "cudaMalloc(work)");
+        else {
+            e = cudaMemset(h->d_work[w], 0, h->state_bytes);
+            if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemset(work)");
+        }
+    }
+    if (!rc) {
+        e = cudaMalloc(&h->d_rho0, sizeof(double) * 10 * count);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(rho0)");
+    }
+    if (!rc) rc = ensure_queue(h, 64);
+    if (!rc) {
+        e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamCreate");
+    }
+    h->host_only = false;
+    if (!rc) rc = apply_tuning(h);
+    if (rc) {
+        free_device(h);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return SA_OK;
+}
+
+void sa_heom_destroy(sa_heom* h) {
+    if (!h) return;
+    if (!h->host_only) free_device(h);
+    delete h;
+}
+
+int sa_heom_info(const sa_heom* h, int inst, sa_counts* out) {
+    if (!h || !out || inst < -1 || inst >= h->count) return fail(SA_ERR_INVALID_ARG, "handle, instance, out");
+    if (inst >= 0) {
+        fill_counts(h->inst[inst], h->precision, out);
+        return SA_OK;
+    }
+    sa_counts t{};
+    double lmax = 0;
+    for (int i = 0; i < h->count; ++i) {
+        sa_counts c{};
+        fill_counts(h->inst[i], h->precision, &c);
+        t.n_vectors += c.n_vectors;
+        t.n_patterns += c.n_patterns;
+        t.n_vars += c.n_vars;
+        t.n_categories += c.n_categories;
+        t.n_records += c.n_records;
+        t.n_terms += c.n_terms;
+        lmax = std::max(lmax, c.log10_conventional_ados);
+    }
+    t.log10_conventional_ados = lmax;
+    t.state_bytes = int64_t(h->state_bytes);
+    *out = t;
+    return SA_OK;
+}
+
+int sa_heom_var_offset(const sa_heom* h, int inst, int64_t* out) {
+    if (!h || !out || inst < 0 || inst > h->count) return fail(SA_ERR_INVALID_ARG, "handle, instance, out");
+    *out = int64_t(h->var_begin[inst]);
+    return SA_OK;
+}
+
+int sa_heom_dump_vectors(const sa_heom* h, int inst, uint8_t* comp) {
+    if (!h || inst < 0 || inst >= h->count || !comp) return fail(SA_ERR_INVALID_ARG, "handle, instance, out");
+    const HostInstance& hi = h->inst[inst];
+    std::memcpy(comp, hi.comp.data(), hi.comp.size());
+    return SA_OK;
+}
+
+int sa_heom_dump_patterns(const sa_heom* h, int inst, int32_t* tier, int32_t* r, int32_t* G, int32_t* hcount,
+                          int64_t* var_off, int64_t* cat_off, int32_t* ids) {
+    if (!h || inst < 0 || inst >= h->count) return fail(SA_ERR_INVALID_ARG, "handle, instance");
+    const HostInstance& hi = h->inst[inst];
+    for (int64_t p = 0; p < hi.P; ++p) {
+        int rp = int(hi.id_off[p + 1] - hi.id_off[p]);
+        if (tier) tier[p] = hi.tier[p];
+        if (r) r[p] = rp;
+        if (G) G[p] = hi.G[p];
+        if (hcount) hcount[p] = hi.h[p];
+        if (var_off) var_off[p] = int64_t(hi.var_off[p]);
+        if (cat_off) cat_off[p] = int64_t(hi.cat_off[p]);
+        if (ids)
+            for (int a = 0; a < hi.L; ++a) ids[p * hi.L + a] = a < rp ? int32_t(hi.ids[hi.id_off[p] + a]) : -1;
+    }
+    if (var_off) var_off[hi.P] = int64_t(hi.var_off[hi.P]);
+    if (cat_off) cat_off[hi.P] = int64_t(hi.cat_off[hi.P]);
+    return SA_OK;
+}
+
+int sa_heom_dump_categories(const sa_heom* h, int inst, int32_t* vec_id, int64_t* mult) {
+    if (!h || inst < 0 || inst >= h->count) return fail(SA_ERR_INVALID_ARG, "handle, instance");
+    const HostInstance& hi = h->inst[inst];
+    for (size_t c = 0; c < hi.cat_vec.size(); ++c) {
+        if (vec_id) vec_id[c] = int32_t(hi.cat_vec[c]);
+        if (mult) mult[c] = hi.cat_M[c];
+    }
+    return SA_OK;
+}
+
+int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, int32_t* k, int32_t* n,
+                       int32_t* dir, int32_t* side_) {
+    if (!h || inst < 0 || inst >= h->count || !var || !src || !k || !n || !dir || !side_)
+        return fail(SA_ERR_INVALID_ARG, "handle, instance, outputs");
+    expand_terms(h->inst[inst], var, src, k, n, dir, side_);
+    return SA_OK;
+}
+
+int sa_heom_state_bytes(const sa_heom* h, size_t* bytes) {
+    if (!h || !bytes) return fail(SA_ERR_INVALID_ARG, "handle, out");
+    *bytes = h->state_bytes;
+    return SA_OK;
+}
+
+int sa_heom_init_state(const sa_heom* hc, const double* rho0, void* d_state, void* stream) {
+    sa_heom* h = const_cast<sa_heom*>(hc);
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!rho0 || !d_state) return fail(SA_ERR_INVALID_ARG, "rho0 and d_state required");
+    for (int i = 0; i < 10 * h->count; ++i)
+        if (!std::isfinite(rho0[i])) return fail(SA_ERR_INVALID_ARG, "non-finite rho0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaMemsetAsync(d_state, 0, h->state_bytes, st));
+    CK(cudaMemcpyAsync(h->d_rho0, rho0, sizeof(double) * 10 * h->count, cudaMemcpyHostToDevice, st));
+    if (h->precision == SA_FP64)
+        CK(launch_init_rho0(static_cast<const InstDev*>(h->d_inst), h->count, h->d_rho0, d_state, nullptr, nullptr, st));
+    else
+        CK(launch_init_rho0(static_cast<const InstDev*>(h->d_inst), h->count, h->d_rho0, nullptr, d_state,
+                            side(h, d_state), st));
+    return SA_OK;
+}
+
+int sa_heom_state_upload(const sa_heom* h, const double* host_x, void* d_state, void* stream) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!host_x || !d_state) return fail(SA_ERR_INVALID_ARG, "host_x and d_state required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (h->precision == SA_FP64) {
+        CK(cudaMemcpyAsync(d_state, host_x, size_t(h->nvar) * 16, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        return SA_OK;
+    }
+    std::vector<float> f(size_t(2) * h->nvar);
+    for (int64_t j = 0; j < 2 * h->nvar; ++j) f[j] = float(host_x[j]);
+    std::vector<double> s(size_t(2) * kSideSlots * h->count, 0.0);
+    for (int i = 0; i < h->count; ++i)
+        for (uint32_t j = 0; j < h->instdev[i].n_rho0; ++j) {
+            s[2 * (kSideSlots * i + j)] = host_x[2 * (h->var_begin[i] + j)];
+            s[2 * (kSideSlots * i + j) + 1] = host_x[2 * (h->var_begin[i] + j) + 1];
+        }
+    CK(cudaMemcpyAsync(d_state, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(side(h, d_state), s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return SA_OK;
+}
+
+int sa_heom_state_download(const sa_heom* h, const void* d_state, double* host_x, void* stream) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!host_x || !d_state) return fail(SA_ERR_INVALID_ARG, "host_x and d_state required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (h->precision == SA_FP64) {
+        CK(cudaMemcpyAsync(host_x, d_state, size_t(h->nvar) * 16, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return SA_OK;
+    }
+    std::vector<float> f(size_t(2) * h->nvar);
+    std::vector<double> s(size_t(2) * kSideSlots * h->count);
+    CK(cudaMemcpyAsync(f.data(), d_state, f.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s.data(), side(h, d_state), s.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int64_t j = 0; j < 2 * h->nvar; ++j) host_x[j] = double(f[j]);
+    for (int i = 0; i < h->count; ++i)
+        for (uint32_t j = 0; j < h->instdev[i].n_rho0; ++j) {
+            host_x[2 * (h->var_begin[i] + j)] = s[2 * (kSideSlots * i + j)];
+            host_x[2 * (h->var_begin[i] + j) + 1] = s[2 * (kSideSlots * i + j) + 1];
+        }
+    return SA_OK;
+}
+
+int sa_heom_rhs(sa_heom* h, const void* d_x, void* d_dx, void* stream) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!d_x || !d_dx || d_x == d_dx) return fail(SA_ERR_INVALID_ARG, "distinct d_x and d_dx required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int), st));
+    StageLaunch L = base_launch(h);
+    L.x_in = d_x;
+    L.x_out = d_dx;
+    L.xs_in = side(h, d_x);
+    L.xs_out = side(h, d_dx);
+    L.stage = -1;
+    L.queue = h->d_queue;
+    CK(launch_stage(L, h->cfg, h->precision == SA_FP64, st));
+    return SA_OK;
+}
+
+int sa_heom_step(sa_heom* h, void* d_state, double dt, void* stream) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!d_state || !std::isfinite(dt)) return fail(SA_ERR_INVALID_ARG, "d_state and finite dt required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaMemsetAsync(h->d_queue, 0, 4 * sizeof(unsigned int), st));
+    return enqueue_step(h, d_state, dt, 0, st);
+}
+
+static int graph_for(sa_heom* h, void* d_state, double dt, int64_t steps, cudaGraphExec_t* out) {
+    uint64_t dtb;
+    std::memcpy(&dtb, &dt, 8);
+    auto key = std::make_tuple(static_cast<const void*>(d_state), dtb, steps);
+    auto it = h->graphs.find(key);
+    if (it != h->graphs.end()) {
+        *out = it->second;
+        return SA_OK;
+    }
+    int rc = ensure_queue(h, size_t(4 * steps));
+    if (rc) return rc;
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int) * 4 * steps, h->cap);
+    for (int64_t s = 0; s < steps && e == cudaSuccess && rc == SA_OK; ++s) rc = enqueue_step(h, d_state, dt, 4 * s, h->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(queue) in capture");
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    if (h->graphs.size() > 16) {
+        for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+        h->graphs.clear();
+    }
+    h->graphs[key] = ex;
+    *out = ex;
+    return SA_OK;
+}
+
+static int run_steps(sa_heom* h, void* d_state, double dt, int64_t n, cudaStream_t st) {
+    const int64_t kGraphSteps = 64;
+    while (n > 0) {
+        int64_t s = std::min(n, kGraphSteps);
+        cudaGraphExec_t ex;
+        int rc = graph_for(h, d_state, dt, s, &ex);
+        if (rc) return rc;
+        CK(cudaGraphLaunch(ex, st));
+        n -= s;
+    }
+    return SA_OK;
+}
+
+int sa_heom_propagate(sa_heom* h, void* d_state, double dt, int64_t nsteps, int64_t obs_every, double* h_obs,
+                      void* stream) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!d_state || !std::isfinite(dt) || nsteps < 0) return fail(SA_ERR_INVALID_ARG, "d_state, dt, nsteps");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!h_obs) return run_steps(h, d_state, dt, nsteps, st);
+    if (obs_every <= 0) obs_every = std::max<int64_t>(nsteps, 1);
+    const int64_t rows = 1 + (nsteps + obs_every - 1) / obs_every;
+    const size_t need = size_t(rows) * h->count * 8;
+    if (need > h->obs_cap) {
+        if (h->d_obs) cudaFree(h->d_obs);
+        h->d_obs = nullptr;
+        CK(cudaMalloc(&h->d_obs, need * sizeof(double)));
+        h->obs_cap = need;
+    }
+    const void* m64 = h->precision == SA_FP64 ? d_state : nullptr;
+    const void* s64 = side(h, d_state);
+    const InstDev* di = static_cast<const InstDev*>(h->d_inst);
+    const double* th = static_cast<const double*>(h->d_theta);
+    CK(launch_observables(di, th, h->count, m64, s64, h->d_obs, st));
+    int64_t done = 0, row = 1;
+    while (done < nsteps) {
+        int64_t n = std::min(obs_every, nsteps - done);
+        rc = run_steps(h, d_state, dt, n, st);
+        if (rc) return rc;
+        CK(launch_observables(di, th, h->count, m64, s64, h->d_obs + size_t(row) * h->count * 8, st));
+        done += n;
+        ++row;
+    }
+    CK(cudaMemcpyAsync(h_obs, h->d_obs, need * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t j = 0; j < need; ++j)
+        if (!std::isfinite(h_obs[j])) return fail(SA_ERR_NUMERIC, "non-finite observable");
+    return SA_OK;
+}
+
+int sa_heom_observables(sa_heom* h, const void* d_state, double* out, void* stream) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!d_state || !out) return fail(SA_ERR_INVALID_ARG, "d_state and out required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t need = size_t(h->count) * 8;
+    if (need > h->obs_cap) {
+        if (h->d_obs) cudaFree(h->d_obs);
+        h->d_obs = nullptr;
+        CK(cudaMalloc(&h->d_obs, need * sizeof(double)));
+        h->obs_cap = need;
+    }
+    CK(launch_observables(static_cast<const InstDev*>(h->d_inst), static_cast<const double*>(h->d_theta), h->count,
+                          h->precision == SA_FP64 ? d_state : nullptr, side(h, d_state), h->d_obs, st));
+    CK(cudaMemcpyAsync(out, h->d_obs, need * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t j = 0; j < need; ++j)
+        if (!std::isfinite(out[j])) return fail(SA_ERR_NUMERIC, "non-finite observable");
+    return SA_OK;
+}
+
+int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue) {
+    if (!h) return fail(SA_ERR_INVALID_ARG, "null handle");
+    int nb = block > 0 ? block : h->block;
+    int nc = chunk > 0 ? chunk : h->chunk;
+    int nq = queue >= 0 ? queue : h->use_queue;
+    if (nb < 64 || nb > 256 || nb % 32) return fail(SA_ERR_INVALID_ARG, "block must be 64..256, multiple of 32");
+    if (nc % 32 || nc < h->max_u || nc > kMaxChunkVars)
+        return fail(SA_ERR_INVALID_ARG, "chunk must be a multiple of 32 between the largest pattern and 4096");
+    h->block = nb;
+    h->chunk = nc;
+    h->use_queue = nq ? 1 : 0;
+    return apply_tuning(h);
+}
+
+int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!d_state) return fail(SA_ERR_INVALID_ARG, "d_state required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int blocks[] = {128, 256};
+    const int chunks[] = {512, 1024, 2048};
+    float best_ms = 1e30f;
+    int bb = h->block, bc = h->chunk, bq = h->use_queue;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int q = 0; q < 2; ++q)
+        for (int b : blocks)
+            for (int c : chunks) {
+                if (c < h->max_u) continue;
+                if (sa_heom_set_tuning(h, b, c, q)) continue;
+                // warm-up + timed: two RK4 steps
+                for (int rep = 0; rep < 2; ++rep) {
+                    rc = sa_heom_step(h, d_state, 0.0, st);
+                    if (rc) return rc;
+                }
+                CK(cudaEventRecord(e0, st));
+                for (int rep = 0; rep < 3; ++rep) {
+                    rc = sa_heom_step(h, d_state, 0.0, st);
+                    if (rc) return rc;
+                }
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    bb = b;
+                    bc = c;
+                    bq = q;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    rc = sa_heom_set_tuning(h, bb, bc, bq);
+    if (rc) return rc;
+    if (best) {
+        best[0] = bb;
+        best[1] = bc;
+        best[2] = bq;
+    }
+    return SA_OK;
+}
+
+int sa_heom_launches_per_step(const sa_heom* h) { return h ? 4 : 0; }
+
+}  // extern "C"

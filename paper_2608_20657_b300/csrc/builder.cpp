@@ -1,0 +1,481 @@
+// builder.cpp -- host construction of the symmetry-adapted hierarchy tables.
+//
+// For one instance (N, m, L, bath, system parameters):
+//  1. local hierarchy vectors alpha in N0^m, |alpha| <= L (last paragraph of
+//     Sec. IV: a molecule carries a whole vector that moves as a unit);
+//  2. canonical occupation patterns (Eq. pattern-one generalised to vectors):
+//     multisets of nonzero vectors with total norm <= L and at most N
+//     members, enumerated tier by tier directly in canonical order;
+//  3. occupation categories, multiplicities M_q (Eqs. Mq, M0), T-ranks
+//     (Eq. h-Lambda) and the variable layout (Eq. uvar-count);
+//  4. damping rates Gamma_Lambda (Eq. tier-damping);
+//  5. connection records: for every (pattern, category, channel, raise /
+//     lower) the canonical target (Eqs. canonical-target-plus/minus) and the
+//     integer data that resolve the aligned accessor (Eq. aligned-accessor)
+//     for every variable of the source category -- "record the source, the
+//     target, the alignment, the multiplicity and the coefficient" of the
+//     precomputed matrix-free right-hand side (Sec. IV.B.4);
+//  6. the coefficient table of the hierarchy terms of Eqs. uvar-up and
+//     uvar-down generalised to channel k as in Eq. scaled-HEOM.
+// Every record is checked against the target's actual category vectors.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
+#include "sa_internal.h"
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace sa {
+
+namespace {
+
+// ---- local vectors ---------------------------------------------------------
+bool vec_before(const uint8_t* a, const uint8_t* b, int m) {
+    int na = 0, nb = 0;
+    for (int k = 0; k < m; ++k) {
+        na += a[k];
+        nb += b[k];
+    }
+    if (na != nb) return na > nb;
+    for (int k = 0; k < m; ++k)
+        if (a[k] != b[k]) return a[k] > b[k];
+    return false;
+}
+
+int64_t vcode(const uint8_t* a, int m, int L) {
+    int64_t c = 0;
+    for (int k = 0; k < m; ++k) c = c * (L + 1) + a[k];
+    return c;
+}
+
+void build_vectors(HostInstance& hi) {
+    const int m = hi.m, L = hi.L;
+    // all nonzero tuples with |alpha| <= L, generated by odometer
+    std::vector<std::vector<uint8_t>> vecs;
+    std::vector<uint8_t> t(m, 0);
+    while (true) {
+        int s = 0;
+        for (int k = 0; k < m; ++k) s += t[k];
+        if (s > 0 && s <= L) vecs.push_back(t);
+        int k = m - 1;
+        while (k >= 0) {
+            if (t[k] < L) {
+                ++t[k];
+                break;
+            }
+            t[k] = 0;
+            --k;
+        }
+        if (k < 0) break;
+    }
+    std::sort(vecs.begin(), vecs.end(),
+              [m](const std::vector<uint8_t>& a, const std::vector<uint8_t>& b) { return vec_before(a.data(), b.data(), m); });
+    hi.V = int(vecs.size()) + 1;
+    hi.comp.assign(size_t(hi.V) * m, 0);
+    hi.norm.assign(hi.V, 0);
+    for (int v = 1; v < hi.V; ++v) {
+        for (int k = 0; k < m; ++k) {
+            hi.comp[size_t(v) * m + k] = vecs[v - 1][k];
+            hi.norm[v] += vecs[v - 1][k];
+        }
+    }
+    int64_t total = 1;
+    for (int k = 0; k < m; ++k) total *= (L + 1);
+    hi.lut.assign(total, -1);
+    for (int v = 0; v < hi.V; ++v) hi.lut[vcode(&hi.comp[size_t(v) * m], m, L)] = v;
+}
+
+int shift_vec(const HostInstance& hi, int id, int k, int dir) {
+    uint8_t t[SA_HEOM_MAXM];
+    std::memcpy(t, &hi.comp[size_t(id) * hi.m], hi.m);
+    int v = int(t[k]) + dir;
+    if (v < 0 || v > hi.L) return -1;
+    t[k] = uint8_t(v);
+    return hi.lut[vcode(t, hi.m, hi.L)];
+}
+
+// ---- pattern enumeration ---------------------------------------------------
+struct Enum {
+    HostInstance& hi;
+    std::vector<uint32_t> cur;
+    int maxr;
+    std::vector<int> first_with_norm_le;  // smallest id whose norm <= n
+    void dfs(int start, int remaining, int tier) {
+        if (remaining == 0) {
+            hi.ids.insert(hi.ids.end(), cur.begin(), cur.end());
+            hi.id_off.push_back(uint32_t(hi.ids.size()));
+            hi.tier.push_back(uint8_t(tier));
+            return;
+        }
+        if (int(cur.size()) >= maxr) return;
+        int v0 = std::max(start, first_with_norm_le[remaining]);
+        for (int v = v0; v < hi.V; ++v) {
+            cur.push_back(uint32_t(v));
+            dfs(v, remaining - hi.norm[v], tier);
+            cur.pop_back();
+        }
+    }
+};
+
+// open-addressing map from an id sequence to its pattern index
+struct PatMap {
+    const HostInstance* hi;
+    std::vector<uint32_t> slot;  // pattern + 1, 0 = empty
+    uint64_t mask = 0;
+    static uint64_t hash(const uint32_t* a, int r) {
+        uint64_t h = 0x9e3779b97f4a7c15ull ^ uint64_t(r);
+        for (int i = 0; i < r; ++i) {
+            h ^= uint64_t(a[i]) + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+            h *= 0xbf58476d1ce4e5b9ull;
+        }
+        return h ^ (h >> 31);
+    }
+    void build(const HostInstance& H) {
+        hi = &H;
+        uint64_t cap = 16;
+        while (cap < uint64_t(H.P) * 2) cap <<= 1;
+        slot.assign(cap, 0);
+        mask = cap - 1;
+        for (int64_t i = 0; i < H.P; ++i) {
+            const uint32_t* a = &H.ids[H.id_off[i]];
+            int r = int(H.id_off[i + 1] - H.id_off[i]);
+            uint64_t s = hash(a, r) & mask;
+            while (slot[s]) s = (s + 1) & mask;
+            slot[s] = uint32_t(i + 1);
+        }
+    }
+    int64_t find(const uint32_t* a, int r) const {
+        uint64_t s = hash(a, r) & mask;
+        while (slot[s]) {
+            int64_t i = int64_t(slot[s]) - 1;
+            int ri = int(hi->id_off[i + 1] - hi->id_off[i]);
+            if (ri == r && std::equal(a, a + r, &hi->ids[hi->id_off[i]])) return i;
+            s = (s + 1) & mask;
+        }
+        return -1;
+    }
+};
+
+}  // namespace
+
+int build_instance(const sa_params& p, HostInstance& hi, std::string& err) {
+    if (p.N < 1 || p.m < 1 || p.m > SA_HEOM_MAXM || p.L < 0 || p.L > SA_HEOM_MAXL) {
+        err = "N >= 1, 1 <= m <= 8, 0 <= L <= 30 required";
+        return SA_ERR_INVALID_ARG;
+    }
+    const double scal[3] = {p.detuning, p.g, p.kappa};
+    for (double v : scal)
+        if (!std::isfinite(v)) {
+            err = "non-finite system parameter";
+            return SA_ERR_INVALID_ARG;
+        }
+    for (int k = 0; k < p.m; ++k) {
+        const double v[6] = {p.c_re[k], p.c_im[k], p.cc_re[k], p.cc_im[k], p.nu_re[k], p.nu_im[k]};
+        for (double x : v)
+            if (!std::isfinite(x)) {
+                err = "non-finite bath coefficient";
+                return SA_ERR_INVALID_ARG;
+            }
+        if (!(std::sqrt(p.c_re[k] * p.c_re[k] + p.c_im[k] * p.c_im[k]) > 0.0)) {
+            err = "|c_k| = 0 makes the scaled hierarchy singular (Eq. scaled-ADO)";
+            return SA_ERR_INVALID_ARG;
+        }
+    }
+    hi = HostInstance();
+    hi.p = p;
+    hi.m = p.m;
+    hi.L = p.L;
+    hi.N = p.N;
+    const int m = hi.m, L = hi.L;
+    build_vectors(hi);
+
+    // patterns, tier by tier, each tier in canonical (lexicographic) order
+    Enum en{hi, {}, int(std::min<int64_t>(L, p.N)), {}};
+    en.first_with_norm_le.assign(L + 1, hi.V);
+    for (int n = 0; n <= L; ++n) {
+        for (int v = 1; v < hi.V; ++v)
+            if (hi.norm[v] <= n) {
+                en.first_with_norm_le[n] = v;
+                break;
+            }
+    }
+    hi.id_off.push_back(0);
+    for (int t = 0; t <= L; ++t) en.dfs(1, t, t);
+    hi.P = int64_t(hi.tier.size());
+
+    // categories, multiplicities, layout, damping
+    hi.G.resize(hi.P);
+    hi.h.resize(hi.P);
+    hi.cat_off.assign(hi.P + 1, 0);
+    hi.var_off.assign(hi.P + 1, 0);
+    hi.gamma_re.resize(hi.P);
+    hi.gamma_im.resize(hi.P);
+    for (int64_t i = 0; i < hi.P; ++i) {
+        const uint32_t* a = &hi.ids[hi.id_off[i]];
+        int r = int(hi.id_off[i + 1] - hi.id_off[i]);
+        int G = 0;
+        hi.cat_off[i] = uint32_t(hi.cat_vec.size());
+        for (int j = 0; j < r; ++j) {
+            if (j == 0 || a[j] != a[j - 1]) {
+                hi.cat_vec.push_back(a[j]);
+                hi.cat_M.push_back(1);
+                ++G;
+            } else {
+                hi.cat_M.back() += 1;
+            }
+        }
+        if (p.N - r >= 1) {
+            hi.cat_vec.push_back(0);
+            hi.cat_M.push_back(p.N - r);
+            ++G;
+        }
+        if (G > kMaxG) {
+            err = "more than 31 occupation categories in a pattern";
+            return SA_ERR_UNSUPPORTED;
+        }
+        int h = 0;
+        double gre = 0, gim = 0;
+        for (int q = 0; q < G; ++q) {
+            int64_t M = hi.cat_M[hi.cat_off[i] + q];
+            hi.cat_trank.push_back(int8_t(M >= 2 ? h++ : -1));
+            uint32_t v = hi.cat_vec[hi.cat_off[i] + q];
+            for (int k = 0; k < m; ++k) {
+                double nk = double(hi.comp[size_t(v) * m + k]) * double(M);
+                gre += nk * p.nu_re[k];
+                gim += nk * p.nu_im[k];
+            }
+        }
+        hi.G[i] = uint8_t(G);
+        hi.h[i] = uint8_t(h);
+        hi.gamma_re[i] = gre;
+        hi.gamma_im[i] = gim;
+        hi.var_off[i + 1] = hi.var_off[i] + uint64_t((G + 1) * (G + 1) + h);
+    }
+    hi.cat_off[hi.P] = uint32_t(hi.cat_vec.size());
+
+    // coefficient table (Eqs. uvar-up, uvar-down with c_k, c-check_k of
+    // Eq. scaled-HEOM): raise: row -i sqrt((n+1)|c|), column +i sqrt((n+1)|c|);
+    // lower: row -i sqrt(n/|c|) c_k, column +i sqrt(n/|c|) c-check_k
+    hi.coef_row.assign(2 * kCoefPerInst, 0.0);
+    hi.coef_col.assign(2 * kCoefPerInst, 0.0);
+    for (int k = 0; k < m; ++k) {
+        double ac = std::sqrt(p.c_re[k] * p.c_re[k] + p.c_im[k] * p.c_im[k]);
+        for (int n = 0; n <= L && n < kCoefN; ++n) {
+            int up = coef_id(k, n, 1), dn = coef_id(k, n, 0);
+            double su = std::sqrt(double(n + 1) * ac);
+            hi.coef_row[2 * up] = 0.0;
+            hi.coef_row[2 * up + 1] = -su;
+            hi.coef_col[2 * up] = 0.0;
+            hi.coef_col[2 * up + 1] = su;
+            double sd = std::sqrt(double(n) / ac);
+            // -i sd c = sd (c_im - i c_re)
+            hi.coef_row[2 * dn] = sd * p.c_im[k];
+            hi.coef_row[2 * dn + 1] = -sd * p.c_re[k];
+            // +i sd cc = sd (-cc_im + i cc_re)
+            hi.coef_col[2 * dn] = -sd * p.cc_im[k];
+            hi.coef_col[2 * dn + 1] = sd * p.cc_re[k];
+        }
+    }
+
+    // connection records
+    PatMap pm;
+    pm.build(hi);
+    const int64_t P = hi.P;
+    std::vector<std::vector<Record>> per(P);
+    std::vector<std::vector<uint32_t>> words(P);
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : bad)
+    for (int64_t i = 0; i < P; ++i) {
+        const uint32_t* a = &hi.ids[hi.id_off[i]];
+        int r = int(hi.id_off[i + 1] - hi.id_off[i]);
+        int G = hi.G[i];
+        const uint32_t* cv = &hi.cat_vec[hi.cat_off[i]];
+        const int64_t* cM = &hi.cat_M[hi.cat_off[i]];
+        uint32_t key[SA_HEOM_MAXL + 2];
+        std::vector<Record>& out = per[i];
+        std::vector<uint32_t>& cw = words[i];
+        for (int q = 1; q <= G; ++q) {
+            int start = int(out.size());
+            uint32_t vq = cv[q - 1];
+            for (int k = 0; k < m; ++k) {
+                for (int dir = +1; dir >= -1; dir -= 2) {
+                    int n = hi.comp[size_t(vq) * m + k];
+                    if (dir > 0 && hi.tier[i] >= L) continue;   // Eq. hard-cutoff-factor
+                    if (dir < 0 && n == 0) continue;            // only occupied channels lower
+                    int w = shift_vec(hi, int(vq), k, dir);
+                    if (w < 0) {
+                        ++bad;
+                        continue;
+                    }
+                    // raw target as a multiset: one v_q replaced by w
+                    int nk = 0;
+                    bool dropped = (vq == 0);
+                    for (int j = 0; j < r; ++j) {
+                        if (!dropped && a[j] == vq) {
+                            dropped = true;
+                            continue;
+                        }
+                        key[nk++] = a[j];
+                    }
+                    if (w != 0) {
+                        int pos = nk;
+                        while (pos > 0 && key[pos - 1] > uint32_t(w)) {
+                            key[pos] = key[pos - 1];
+                            --pos;
+                        }
+                        key[pos] = uint32_t(w);
+                        ++nk;
+                    }
+                    int64_t t = pm.find(key, nk);
+                    if (t < 0) {
+                        ++bad;
+                        continue;
+                    }
+                    int del = cM[q - 1] == 1 ? 1 : 0;
+                    int s_merge = 0;
+                    for (int s = 1; s <= G; ++s)
+                        if (s != q && cv[s - 1] == uint32_t(w)) s_merge = s;
+                    int ins = s_merge ? 0 : 1;
+                    int ipos = G + 1;
+                    if (ins) {
+                        // first old category that sorts after w (zero vector sorts last)
+                        for (int s = 1; s <= G; ++s) {
+                            bool after = (cv[s - 1] == 0) ? (w != 0) : (w != 0 && cv[s - 1] > uint32_t(w));
+                            if (after) {
+                                ipos = s;
+                                break;
+                            }
+                        }
+                    }
+                    auto tau = [&](int rr) { return rr - ((del && rr > q) ? 1 : 0) + ((ins && rr >= ipos) ? 1 : 0); };
+                    int tstar = ins ? ipos - ((del && q < ipos) ? 1 : 0) : tau(s_merge);
+                    int Gp = hi.G[t];
+                    // verify the remap against the target's categories
+                    const uint32_t* tv = &hi.cat_vec[hi.cat_off[t]];
+                    if (Gp != G + ins - del || tstar < 1 || tstar > Gp || tv[tstar - 1] != uint32_t(w)) ++bad;
+                    for (int rr = 1; rr <= G; ++rr) {
+                        if (rr == q && del) continue;
+                        int tr = tau(rr);
+                        if (tr < 1 || tr > Gp || tv[tr - 1] != cv[rr - 1]) ++bad;
+                    }
+                    int trs = hi.cat_trank[hi.cat_off[t] + tstar - 1];
+                    Record rec;
+                    rec.target = uint32_t(hi.var_off[t]);
+                    rec.packed = pack_record(tstar, Gp, trs < 0 ? 0 : trs, trs >= 0 ? 1 : 0, ipos, ins, del,
+                                             coef_id(k, n, dir > 0 ? 1 : 0));
+                    out.push_back(rec);
+                }
+            }
+            cw.push_back(pack_cat(start, int(out.size()) - start, hi.cat_trank[hi.cat_off[i] + q - 1]));
+        }
+    }
+    if (bad) {
+        err = "internal: inconsistent connection record";
+        return SA_ERR_INVALID_ARG;
+    }
+    hi.rec_off.assign(P + 1, 0);
+    for (int64_t i = 0; i < P; ++i) hi.rec_off[i + 1] = hi.rec_off[i] + uint32_t(per[i].size());
+    hi.rec.resize(hi.rec_off[P]);
+    hi.cat_word.resize(hi.cat_vec.size());
+    for (int64_t i = 0; i < P; ++i) {
+        std::copy(per[i].begin(), per[i].end(), hi.rec.begin() + hi.rec_off[i]);
+        std::copy(words[i].begin(), words[i].end(), hi.cat_word.begin() + hi.cat_off[i]);
+    }
+    hi.n_terms = expand_terms(hi, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return SA_OK;
+}
+
+// Expand the records into per-variable hierarchy terms, with the same
+// integer resolution the kernels use.  Returns the number of terms; writes
+// them when the arrays are not NULL.
+int64_t expand_terms(const HostInstance& hi, int64_t* var, int64_t* src, int32_t* kk, int32_t* nn, int32_t* dd,
+                     int32_t* side) {
+    int64_t cnt = 0;
+    auto emit = [&](int64_t v, int64_t s, uint32_t packed, int sd) {
+        if (var) {
+            int cid = int(packed >> 23);
+            var[cnt] = v;
+            src[cnt] = s;
+            kk[cnt] = (cid >> 1) / kCoefN;
+            nn[cnt] = (cid >> 1) % kCoefN;
+            dd[cnt] = (cid & 1) ? +1 : -1;
+            side[cnt] = sd;
+        }
+        ++cnt;
+    };
+    for (int64_t i = 0; i < hi.P; ++i) {
+        int G = hi.G[i];
+        int64_t base = int64_t(hi.var_off[i]);
+        const uint32_t* cw = &hi.cat_word[hi.cat_off[i]];
+        const Record* R = &hi.rec[hi.rec_off[i]];
+        const int8_t* tr = &hi.cat_trank[hi.cat_off[i]];
+        auto target_index = [&](const Record& rc, int rowc, int colc, bool same) -> int64_t {
+            // rowc / colc: target category (0 = cavity); same: P entry
+            uint32_t pk = rc.packed;
+            int tstar = pk & 31, Gp = (pk >> 5) & 31, trs = (pk >> 10) & 31;
+            (void)tstar;
+            int64_t loc;
+            if (rowc == 0 && colc == 0) loc = loc_Z();
+            else if (colc == 0) loc = loc_X(Gp, rowc);
+            else if (rowc == 0) loc = loc_Y(Gp, colc);
+            else if (same) loc = loc_P(Gp, rowc);
+            else if (rowc != colc) loc = loc_S(Gp, rowc, colc);
+            else loc = loc_T(Gp, trs);
+            return int64_t(rc.target) + loc;
+        };
+        auto tau_of = [](uint32_t pk, int moved, int rr) {
+            int ipos = (pk >> 16) & 31, ins = (pk >> 21) & 1, del = (pk >> 22) & 1;
+            return rr - ((del && rr > moved) ? 1 : 0) + ((ins && rr >= ipos) ? 1 : 0);
+        };
+        // every variable: (kind, q, r) in canonical order
+        auto each_var = [&](int kind, int q, int r, int64_t loc) {
+            int row = 0, col = 0;
+            bool same = false;
+            if (kind == 1) row = q;
+            if (kind == 2) col = q;
+            if (kind == 3) { row = q; col = q; same = true; }
+            if (kind == 4) { row = q; col = r; }
+            if (kind == 5) { row = q; col = q; }
+            if (row) {
+                uint32_t w = cw[row - 1];
+                int rs = w & 1023, nr = (w >> 10) & 31;
+                for (int j = 0; j < nr; ++j) {
+                    const Record& rc = R[rs + j];
+                    bool raise = ((rc.packed >> 23) & 1) != 0;
+                    if (same && raise) continue;  // cancels against the column raise
+                    int tstar = rc.packed & 31;
+                    int cc = col == 0 ? 0 : (same ? tstar : tau_of(rc.packed, row, col));
+                    emit(base + loc, target_index(rc, tstar, cc, same), rc.packed, 0);
+                }
+            }
+            if (col) {
+                uint32_t w = cw[col - 1];
+                int rs = w & 1023, nr = (w >> 10) & 31;
+                for (int j = 0; j < nr; ++j) {
+                    const Record& rc = R[rs + j];
+                    bool raise = ((rc.packed >> 23) & 1) != 0;
+                    if (same && raise) continue;
+                    int tstar = rc.packed & 31;
+                    int rr = row == 0 ? 0 : (same ? tstar : tau_of(rc.packed, col, row));
+                    emit(base + loc, target_index(rc, rr, tstar, same), rc.packed, 1);
+                }
+            }
+        };
+        each_var(0, 0, 0, loc_Z());
+        for (int q = 1; q <= G; ++q) {
+            each_var(1, q, 0, loc_X(G, q));
+            each_var(2, q, 0, loc_Y(G, q));
+            each_var(3, q, 0, loc_P(G, q));
+            for (int r = 1; r <= G; ++r)
+                if (r != q) each_var(4, q, r, loc_S(G, q, r));
+            if (tr[q - 1] >= 0) each_var(5, q, 0, loc_T(G, tr[q - 1]));
+        }
+    }
+    return cnt;
+}
+
+}  // namespace sa

@@ -1,0 +1,138 @@
+// sa_internal.h -- host-side tables and device layout shared by the table
+// builder (builder.cpp), the bath helpers (bath.cpp), the kernels
+// (kernels.cu) and the C ABI (api.cu).  Library-internal.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/sa_heom.h"
+
+namespace sa {
+
+// ---- limits ---------------------------------------------------------------
+constexpr int kMaxG = 31;            // categories per pattern (5-bit fields)
+constexpr int kCoefN = 32;           // occupation slots per channel in the coefficient table
+constexpr int kCoefPerInst = SA_HEOM_MAXM * kCoefN * 2;
+constexpr int kMaxPatPerChunk = 256; // local pattern index is 8-bit
+constexpr int kSideSlots = 8;        // FP64 slots of the physical representative per instance
+constexpr int kMaxChunkVars = 4096;
+
+// ---- one hierarchy connection record ---------------------------------------
+// A record belongs to (pattern Lambda, category q, channel k, direction): the
+// molecule of category q whose local vector v_q becomes w = v_q +/- e_k.  The
+// raw target's canonical pattern Lambda' (Eqs. canonical-target-plus/minus)
+// has its categories in canonical order; an unmoved category r of Lambda
+// lands at
+//     tau(r) = r - [del && r > q] + [ins && r >= ipos]
+// and the moved molecule at tau_star.  del: category q vanishes (M_q = 1);
+// ins: w is a new category of Lambda' inserted before old category ipos
+// (otherwise w merges with an existing category).  Together with the
+// target's G' and the T-rank of tau_star this resolves every aligned-target
+// entry (Eq. aligned-accessor) with integer arithmetic.
+struct Record {
+    uint32_t target;   // first variable of Lambda' in the batch vector
+    uint32_t packed;   // see pack_record
+};
+
+inline uint32_t pack_record(int tau_star, int Gp, int trank_star, int has_t, int ipos, int ins, int del,
+                            int coef_id) {
+    return uint32_t(tau_star) | (uint32_t(Gp) << 5) | (uint32_t(trank_star) << 10) | (uint32_t(has_t) << 15) |
+           (uint32_t(ipos) << 16) | (uint32_t(ins) << 21) | (uint32_t(del) << 22) | (uint32_t(coef_id) << 23);
+}
+// coefficient id: ((k * kCoefN) + n) * 2 + (raise ? 1 : 0), n = v_q[k] before the move
+inline int coef_id(int k, int n, int raise) { return ((k * kCoefN) + n) * 2 + (raise ? 1 : 0); }
+
+// ---- per-pattern header on the device (16 bytes) --------------------------
+struct PatHdr {
+    uint32_t var_off;  // first variable (batch-global)
+    uint32_t rec_off;  // first record (batch-global)
+    uint32_t cat_off;  // first category (batch-global)
+    uint16_t inst;     // instance
+    uint8_t G;         // categories
+    uint8_t tier;      // |Lambda|
+};
+
+// per-category word: bits 0-9 first record (relative to rec_off),
+// 10-14 record count, 15-19 T-rank (31 = no T variable)
+inline uint32_t pack_cat(int rec_start, int nrec, int trank) {
+    return uint32_t(rec_start) | (uint32_t(nrec) << 10) | (uint32_t(trank < 0 ? 31 : trank) << 15);
+}
+
+// per-instance constants on the device
+struct InstDev {
+    double g, detuning, kappa, N;
+    float gf, detf, kappaf, pad;
+    uint32_t coef_base;  // into the coefficient tables
+    uint32_t side;       // first FP64 side slot
+    uint32_t var_begin;  // first variable
+    uint32_t n_rho0;     // variables of the physical representative (4 or 5)
+};
+
+// ---- host tables of one instance ------------------------------------------
+struct HostInstance {
+    sa_params p{};
+    int m = 0, L = 0;
+    int64_t N = 0;
+    // local vectors: id 0 = zero vector, then |alpha| descending, components
+    // lexicographically descending
+    int V = 0;
+    std::vector<uint8_t> comp;       // V * m
+    std::vector<int> norm;           // V
+    std::vector<int32_t> lut;        // mixed-radix code -> id
+    // canonical patterns
+    int64_t P = 0;
+    std::vector<uint32_t> id_off;    // P + 1
+    std::vector<uint32_t> ids;       // ascending vector ids
+    std::vector<uint8_t> tier;       // P
+    std::vector<uint8_t> G, h;       // P
+    std::vector<uint32_t> cat_off;   // P + 1
+    std::vector<uint32_t> cat_vec;   // vector id of each category
+    std::vector<int64_t> cat_M;      // multiplicity
+    std::vector<int8_t> cat_trank;   // T-rank or -1
+    std::vector<uint32_t> cat_word;  // pack_cat
+    std::vector<uint64_t> var_off;   // P + 1, instance-relative
+    std::vector<double> gamma_re, gamma_im;
+    std::vector<uint32_t> rec_off;   // P + 1, instance-relative
+    std::vector<Record> rec;         // target instance-relative until batch assembly
+    int64_t n_terms = 0;
+    // coefficient table: row and column coefficients, (re, im) pairs
+    std::vector<double> coef_row, coef_col;  // 2 * kCoefPerInst each
+};
+
+// launch description shared by api.cu and kernels.cu (type-erased pointers)
+struct LaunchCfg {
+    int block;      // threads per CTA
+    int chunk;      // variable capacity of one work item
+    int use_queue;  // 1: persistent grid + atomic work queue
+    int grid;       // CTAs
+};
+struct StageLaunch {
+    const void* hdr; const void* cat_word; const void* cat_M; const void* gamma; const void* rec;
+    const void* chunk_begin; const void* inst; const void* coef_row; const void* coef_col;
+    const void* cat_Md; const void* coef_row_d; const void* coef_col_d;
+    const void* lut; const void* lut_off;
+    uint32_t nchunks;
+    const void* x_in; void* x_out; const void* y; void* acc; void* y_out;
+    const void* xs_in; void* xs_out; const void* ys; void* accs; void* ys_out;
+    double dt; int stage; unsigned int* queue;
+};
+
+// builder.cpp
+int build_instance(const sa_params& p, HostInstance& out, std::string& err);
+int64_t expand_terms(const HostInstance& hi, int64_t* var, int64_t* src, int32_t* k, int32_t* n, int32_t* dir,
+                     int32_t* side);
+// bath.cpp
+int drude_lorentz(double lambda, double gamma, double kT, int scheme, int n_poles, double sigma, sa_params* p,
+                  std::string& err);
+
+// local index of a variable inside a pattern (canonical layout)
+inline int64_t loc_Z() { return 0; }
+inline int64_t loc_X(int G, int q) { return q; }
+inline int64_t loc_Y(int G, int q) { return G + q; }
+inline int64_t loc_P(int G, int q) { return 2 * G + q; }
+inline int64_t loc_S(int G, int q, int r) { return 3 * G + 1 + int64_t(q - 1) * (G - 1) + (r - 1) - (r > q ? 1 : 0); }
+inline int64_t loc_T(int G, int trank) { return int64_t(G + 1) * (G + 1) + trank; }
+
+}  // namespace sa

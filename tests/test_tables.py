@@ -1,0 +1,142 @@
+"""The library's host-built tables against the oracle's, bit for bit.
+
+Integer tables (local vectors, canonical patterns and their order, tiers,
+categories, multiplicities M_q, variable offsets) must be identical, and the
+hierarchy connections -- every (variable, source variable, channel, occupation,
+raise/lower, row/column) term of Eqs. uvar-up and uvar-down -- must be the
+same set.  The oracle lists the two raise terms of P_q, which cancel exactly
+(both deltas of Eq. projector-commutator-element name the same molecule); the
+library omits them.  No GPU is used: the handle is built host-only.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.bath as OB
+import paper_2608_20657_b300 as S
+import workloads as W
+
+
+def _oracle_bath(w):
+    if w["scheme"] == "high_t":
+        return OB.high_t(w["lam"], w["gam"], w["kT"], w["sigma"])
+    if w["scheme"] == "matsubara":
+        return OB.matsubara(w["lam"], w["gam"], w["kT"], w["poles"], w["sigma"])
+    return OB.pade(w["lam"], w["gam"], w["kT"], w["poles"], w["sigma"])
+
+
+def _pair(N, m, L, bath, **kw):
+    sa = oracle.SA(N, m, L, bath, **kw)
+    lib = S.Heom(S.make_params(N, m, L, bath, **kw), host_only=True)
+    return sa, lib
+
+
+def _generic_bath(m, seed):
+    rng = np.random.default_rng(seed)
+    return {"c": rng.uniform(0.1, 0.5, m) + 1j * rng.uniform(-0.4, 0.4, m),
+            "cc": rng.uniform(0.1, 0.5, m) + 1j * rng.uniform(-0.4, 0.4, m),
+            "nu": rng.uniform(0.2, 1.2, m) + 1j * rng.uniform(-0.3, 0.3, m)}
+
+
+CASES = [(1, 1, 3), (2, 1, 3), (3, 1, 0), (3, 2, 3), (4, 1, 5), (5, 2, 4), (10, 2, 6), (12, 3, 4), (7, 4, 3),
+         (100, 2, 8), (30, 1, 12), (1000000, 1, 9), (6, 5, 3), (2, 2, 6)]
+
+
+@pytest.mark.parametrize("N,m,L", CASES)
+def test_tables_bit_exact(N, m, L):
+    sa, lib = _pair(N, m, L, _generic_bath(m, N + 7 * m + L), detuning=0.1, g=0.2, kappa=0.05)
+    assert lib.n_patterns == sa.npat and lib.n_vars == sa.nvar
+    assert np.array_equal(lib.dump_vectors(0), sa.vectors())
+    a, b = lib.dump_patterns(0), sa.patterns()
+    for key in ("tier", "r", "G", "h", "var_off", "cat_off", "ids", "cat_id", "cat_M"):
+        assert np.array_equal(a[key], b[key]), key
+    lt, ot = lib.dump_terms(0), sa.terms()
+    lab = sa.var_labels()
+    # oracle: drop the cancelling raise pairs of P_q
+    isP = lab["kind"][ot["var"]] == 3
+    keep = ~(isP & (ot["dir"] == 1))
+    pairs = ot["var"][isP & (ot["dir"] == 1)]
+    # each dropped P raise term comes with its opposite-side twin
+    if pairs.size:
+        sub = {k: v[isP & (ot["dir"] == 1)] for k, v in ot.items()}
+        key = np.stack([sub["var"], sub["src"], sub["k"], sub["n"]], 1)
+        u, cnt = np.unique(key, axis=0, return_counts=True)
+        assert np.all(cnt == 2)
+        assert np.all(np.bincount(sub["side"]) == pairs.size // 2)
+    o = np.stack([ot[k][keep] for k in ("var", "src", "k", "n", "dir", "side")], 1)
+    l = np.stack([lt[k] for k in ("var", "src", "k", "n", "dir", "side")], 1)
+    o = o[np.lexsort(o.T[::-1])]
+    l = l[np.lexsort(l.T[::-1])]
+    assert o.shape == l.shape
+    assert np.array_equal(o, l)
+    assert oracle.errors() == 0
+
+
+@pytest.mark.parametrize("key", ["w1", "w2", "w3"])
+def test_workload_tables_bit_exact(key):
+    w = W.WORKLOADS[key]
+    bath = _oracle_bath(w)
+    N = w["N"]
+    sa = oracle.SA(N, len(bath["c"]), w["L"], bath, w["detuning"], w["gsn"] / np.sqrt(N), w["kappa"])
+    lib = S.Heom(S.params_from(w), host_only=True)
+    a, b = lib.dump_patterns(0), sa.patterns()
+    for k in ("tier", "r", "G", "h", "var_off", "cat_off", "ids", "cat_id", "cat_M"):
+        assert np.array_equal(a[k], b[k]), k
+    assert lib.info(0)["n_terms"] == sa.terms()["var"].size - int(
+        ((sa.var_labels()["kind"][sa.terms()["var"]] == 3) & (sa.terms()["dir"] == 1)).sum())
+
+
+def test_batch_offsets_and_counts():
+    """A batch is the instances' tables concatenated; per-instance counts
+    equal the stand-alone counts and offsets are prefix sums."""
+    ws = W.batch_w4(12)
+    ps = [S.params_from(w) for w in ws]
+    h = S.Heom(ps, precision=S.SA_FP32_AUX, host_only=True)
+    off = 0
+    for i, p in enumerate(ps):
+        c = S.counts(p)
+        assert h.var_offset(i) == off
+        assert h.info(i)["n_vars"] == c["n_vars"]
+        off += c["n_vars"]
+    assert h.n_vars == off
+    side = (off * 8 + 255) // 256 * 256
+    assert h.state_bytes == side + 12 * 8 * 16
+
+
+def test_saturation_in_library():
+    """Eqs. first-saturation / second-saturation hold for the library counts."""
+    bath = _generic_bath(2, 1)
+    L = 5
+    npat = [S.counts(S.make_params(N, 2, L, bath))["n_patterns"] for N in range(1, L + 5)]
+    nvar = [S.counts(S.make_params(N, 2, L, bath))["n_vars"] for N in range(1, L + 5)]
+    assert npat[L - 2] < npat[L - 1] == npat[-1]          # index N-1
+    assert nvar[L] < nvar[L + 1] == nvar[-1]
+
+
+@pytest.mark.parametrize("bad", [dict(N=0), dict(m=0), dict(m=9), dict(L=-1), dict(L=31)])
+def test_invalid_arguments_rejected(bad):
+    args = dict(N=3, m=1, L=2)
+    args.update(bad)
+    bath = {"c": np.ones(8) * 0.1, "cc": np.ones(8) * 0.1, "nu": np.ones(8)}
+    p = S.make_params(args["N"], min(max(args["m"], 1), 8), args["L"], bath)
+    p.m = args["m"]
+    with pytest.raises(S.SaHeomError) as e:
+        S.Heom(p, host_only=True)
+    assert e.value.code == -1
+
+
+def test_zero_coefficient_rejected():
+    bath = {"c": np.array([0j]), "cc": np.array([0j]), "nu": np.array([1.0])}
+    with pytest.raises(S.SaHeomError):
+        S.Heom(S.make_params(3, 1, 2, bath), host_only=True)
+    bath = {"c": np.array([np.nan + 0j]), "cc": np.array([0.1 + 0j]), "nu": np.array([1.0])}
+    with pytest.raises(S.SaHeomError):
+        S.Heom(S.make_params(3, 1, 2, bath), host_only=True)
+
+
+def test_host_only_handle_refuses_device_calls():
+    bath = {"c": np.array([0.1 + 0j]), "cc": np.array([0.1 + 0j]), "nu": np.array([1.0])}
+    h = S.Heom(S.make_params(3, 1, 2, bath), host_only=True)
+    with pytest.raises(S.SaHeomError) as e:
+        h.step(0, 0.1, stream=0)
+    assert e.value.code == -7
