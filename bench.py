@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark: unique variables updated per second by the symmetry-adapted
+HEOM RK4 step on B300.
+
+Workload (default): w4, a batch of 512 independent seeded instances with
+uneven N in 2..64, m in 1..2 plus the averaged static-disorder channel, L in
+3..8, FP32 auxiliary variables with an FP64 physical density matrix, dt =
+0.02.  One "step" is one classical RK4 step of the whole batch (four fused
+right-hand-side + stage kernels).  Inputs are synthetic (seeded) and resident
+in HBM; the four state-sized vectors (~0.6 GB) exceed the 126 MB L2, so no
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload w4|w5|w3]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own copy
+of the batch (weak scaling, no data-path collective); the time is the max
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "unique_vars_updated_per_s"
+UNIT = "unique-variable RK4 updates/s"
+FP32_BYTES_PER_VAR_STEP = 136    # 17 complex float accesses per variable per RK4 step
+FP64_BYTES_PER_VAR_STEP = 272
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return rank, world
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.strip()]
+        sm = [float(r[0]) for r in rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 8:
+                continue
+            for n, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _stage_sha() -> str:
+    src = open(os.path.join(ROOT, "paper_2608_20657_b300", "csrc", "kernels.cu"), "rb").read()
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
+def _traffic(workload: str):
+    """DRAM bytes per stage launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", f"stage_kernel_{workload}_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("kernel_sha") != _stage_sha():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def _params(workload):
+    import paper_2608_20657_b300 as S
+
+    if workload == "w4":
+        ws = W.batch_w4()
+        return ws, [S.params_from(w) for w in ws], S.SA_FP32_AUX, 0.02
+    w = W.WORKLOADS[workload]
+    return [w], [S.params_from(w)], S.SA_FP32_AUX, w["dt"]
+
+
+def _rho0(ws):
+    import paper_2608_20657_b300 as S
+
+    draws = W.random_rho_draws()
+    return np.stack([S.rho0_vars(w, draws) for w in ws])
+
+
+# ------------------------------------------------------------ CPU baseline
+
+def _oracle_sample(workload: str, budget_vars: int):
+    """A bounded sample of the workload for the oracle: the first instances
+    of the batch until budget_vars unique variables (w4), else the instance
+    itself."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from tests._helpers import oracle_rho0, oracle_sa
+
+    ws = W.batch_w4() if workload == "w4" else [W.WORKLOADS[workload]]
+    sample, total = [], 0
+    for w in ws:
+        sa = oracle_sa(w, cache=True)
+        x = sa.initial_state(*oracle_rho0(w, W.random_rho_draws()))
+        sample.append((sa, x))
+        total += sa.nvar
+        if total >= budget_vars:
+            break
+    return sample, total, len(ws)
+
+
+def cpu_baseline(workload: str, seconds: float = 15.0, dt: float = 0.02) -> dict:
+    import oracle
+
+    sample, total, n_all = _oracle_sample(workload, 400_000 if workload == "w4" else 10 ** 12)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        for sa, x in sample:
+            sa.rk4(x, dt, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (workload == "w5" and steps >= 1):
+            break
+    return {"value": total * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{len(sample)} of {n_all} instances ({total} unique variables), {steps} RK4 steps, "
+                      f"{el:.1f} s, FP64 C oracle with OpenMP over patterns"}
+
+
+def run_reference(args):
+    rank, world = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    sample, total, n_all = _oracle_sample(args.workload, 400_000 if args.workload == "w4" else 10 ** 12)
+    dt = 0.02
+    for _ in range(args.warmup):
+        for sa, x in sample:
+            sa.rk4(x, dt, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for sa, x in sample:
+            sa.rk4(x, dt, 1)
+    el = time.perf_counter() - t0
+    val = total * args.steps / el
+    cb = {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+          "sample": f"{len(sample)} of {n_all} instances ({total} unique variables) per step"}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": args.workload, "sample": cb["sample"]},
+                      "cpu_baseline": cb, "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                                   "d2h_bytes_per_step": 0}}))
+    return 0
+
+
+# ------------------------------------------------------------ GPU arm
+
+def run_ours(args):
+    import torch
+
+    import paper_2608_20657_b300 as S
+
+    rank, world = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    ws, ps, precision, dt = _params(args.workload)
+    h = S.Heom(ps, precision=precision)
+    st = h.new_state()
+    h.init_state(st, _rho0(ws))
+    stream = torch.cuda.current_stream()
+    best = h.autotune(st)
+    h.init_state(st, _rho0(ws))
+    torch.cuda.synchronize()
+
+    # warm-up (captures the CUDA graph)
+    h.propagate(st, dt, args.warmup, observe=False)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h.propagate(st, dt, args.steps, observe=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        dist.barrier()
+    ck = clocks.stop() if clocks else None
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    n_vars = h.n_vars
+    value = n_vars * world * args.steps / (ms / 1e3)
+
+    # roofline of the stage kernel (4 launches per step)
+    launch_ms = ms_step / 4.0
+    bytes_launch = FP32_BYTES_PER_VAR_STEP * n_vars / 4.0 if precision == S.SA_FP32_AUX else \
+        FP64_BYTES_PER_VAR_STEP * n_vars / 4.0
+    achieved = bytes_launch / (launch_ms / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": _traffic(args.workload), "peak_source": f"{peak_kind} hbm_gbs",
+            "kernel": "stage_kernel<float,true>", "bytes_per_launch": bytes_launch}
+
+    # end to end through the public API with host buffers: upload the state
+    # from pinned host memory, K steps with the observables of every step read
+    # back to the host, download the state
+    host_x = h.download(st)
+    pinned = torch.from_numpy(host_x.view(np.float64)).pin_memory()
+    hx = pinned.numpy().view(np.complex128)
+    k_e2e = max(1, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h.upload(st, hx)
+    obs = h.propagate(st, dt, k_e2e, 1)
+    back = h.download(st)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": n_vars * world * k_e2e / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(h.state_bytes / k_e2e),
+           "d2h_bytes_per_step": int((h.state_bytes + obs.size * 8) / k_e2e),
+           "steps": k_e2e, "note": "state upload + propagate with observables every step + state download"}
+    del back
+
+    # FP64 comparison on the same batch: time per step and the population
+    # error of the FP32-aux path against it
+    extra = {}
+    if rank == 0 and args.workload == "w4" and not args.no_fp64:
+        h64 = S.Heom(ps, precision=S.SA_FP64)
+        s64 = h64.new_state()
+        h64.autotune(s64)
+        h64.init_state(s64, _rho0(ws))
+        h64.propagate(s64, dt, 3, observe=False)
+        torch.cuda.synchronize()
+        k64 = max(3, min(args.steps, 20))
+        e0.record(stream)
+        h64.propagate(s64, dt, k64, observe=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        nerr = args.err_steps
+        a, b = h64.new_state(), h.new_state()
+        h64.init_state(a, _rho0(ws))
+        h.init_state(b, _rho0(ws))
+        o64 = h64.propagate(a, dt, nerr, max(1, nerr // 10))
+        o32 = h.propagate(b, dt, nerr, max(1, nerr // 10))
+        err = float(np.max(np.abs(o64[:, :, 1:7] - o32[:, :, 1:7])))
+        extra = {"fp64_ms_per_step": ms64, "fp32_over_fp64_speedup": ms64 / ms_step,
+                 "time_to_t_final_s": {"fp32_aux": ms_step * 10000 / 1e3, "fp64": ms64 * 10000 / 1e3,
+                                       "steps": 10000},
+                 "fp32_max_population_error_vs_fp64": err, "population_error_window_steps": nerr}
+        del h64, s64, a, b
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if precision == S.SA_FP32_AUX else "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload + (" (512 seeded instances, FP32-aux + FP64 rho_0)"
+                                                        if args.workload == "w4" else ""),
+                           "n_instances": h.count, "n_vars": n_vars, "n_patterns": h.n_patterns,
+                           "state_bytes": h.state_bytes, "l2": "inputs larger than L2 (4 vectors)",
+                           "tuning": {"block": best[0], "chunk": best[1], "queue": best[2]},
+                           "parallelism": f"replicas{world}"},
+                "roofline": roof, "gpu_launches": 4 * args.steps, "clocks": ck, "e2e": e2e}
+        line.update(extra)
+        if world == 1 and not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds, dt)
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="w4", choices=["w3", "w4", "w5"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--err-steps", type=int, default=2000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
