@@ -218,7 +218,11 @@ def run_ours(args):
     st = h.new_state()
     h.init_state(st, _rho0(ws))
     stream = torch.cuda.current_stream()
-    best = h.autotune(st)
+    if args.tune:
+        best = tuple(int(v) for v in args.tune.split(","))
+        h.set_tuning(*best)
+    else:
+        best = h.autotune(st)
     h.init_state(st, _rho0(ws))
     torch.cuda.synchronize()
 
@@ -261,22 +265,24 @@ def run_ours(args):
     # end to end through the public API with host buffers: upload the state
     # from pinned host memory, K steps with the observables of every step read
     # back to the host, download the state
-    host_x = h.download(st)
-    pinned = torch.from_numpy(host_x.view(np.float64)).pin_memory()
-    hx = pinned.numpy().view(np.complex128)
-    k_e2e = max(1, min(args.steps, 50))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    h.upload(st, hx)
-    obs = h.propagate(st, dt, k_e2e, 1)
-    back = h.download(st)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": n_vars * world * k_e2e / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(h.state_bytes / k_e2e),
-           "d2h_bytes_per_step": int((h.state_bytes + obs.size * 8) / k_e2e),
-           "steps": k_e2e, "note": "state upload + propagate with observables every step + state download"}
-    del back
+    e2e = None
+    if not args.no_e2e:
+        host_x = h.download(st)
+        pinned = torch.from_numpy(host_x.view(np.float64)).pin_memory()
+        hx = pinned.numpy().view(np.complex128)
+        k_e2e = max(1, min(args.steps, 50))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.upload(st, hx)
+        obs = h.propagate(st, dt, k_e2e, 1)
+        back = h.download(st)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": n_vars * world * k_e2e / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(h.state_bytes / k_e2e),
+               "d2h_bytes_per_step": int((h.state_bytes + obs.size * 8) / k_e2e),
+               "steps": k_e2e, "note": "state upload + propagate with observables every step + state download"}
+        del back
 
     # FP64 comparison on the same batch: time per step and the population
     # error of the FP32-aux path against it
@@ -339,6 +345,8 @@ def main():
     ap.add_argument("--err-steps", type=int, default=2000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", default="", help="block,chunk,queue (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
