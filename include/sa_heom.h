@@ -240,7 +240,7 @@ int sa_heom_observables(sa_heom* h, const void* d_state, double* out, void* stre
 
 /*
  * Launch tuning.  block: threads per CTA (64..1024, multiple of 32);
- * chunk: variables per work item (>= largest pattern, <= 4096); queue: 1 for
+ * chunk: variables per work item (>= largest pattern, <= 2048); queue: 1 for
  * the dynamic work queue, 0 for a static strided assignment.  Any argument
  * <= 0 keeps its current value.  sa_heom_autotune times a few candidates of
  * the RK4 stage kernel on d_state (which it leaves changed) and keeps the

@@ -77,6 +77,7 @@ struct sa_heom {
     std::vector<uint32_t> lut_off;
     std::vector<uint32_t> chunk_begin;
     int max_u = 0;
+    int rec_cap = 8;
     // tuning
     int block = 256, chunk = 1024, use_queue = 1;
     // device
@@ -93,7 +94,7 @@ struct sa_heom {
     double* d_rho0 = nullptr;
     cudaStream_t cap = nullptr;
     size_t state_bytes = 0, side_off = 0;
-    LaunchCfg cfg{256, 1024, 1, 1};
+    LaunchCfg cfg{256, 1024, 1, 1, 8};
     std::map<std::tuple<const void*, uint64_t, int64_t>, cudaGraphExec_t> graphs;
 };
 
@@ -138,6 +139,10 @@ void build_chunks(sa_heom* h) {
         ++pats;
     }
     h->chunk_begin.push_back(uint32_t(h->npat));
+    uint32_t cap = 8;
+    for (size_t c = 0; c + 1 < h->chunk_begin.size(); ++c)
+        cap = std::max(cap, h->hdr[h->chunk_begin[c + 1]].rec_off - h->hdr[h->chunk_begin[c]].rec_off);
+    h->rec_cap = int((cap + 7) / 8 * 8);
 }
 
 int apply_tuning(sa_heom* h) {
@@ -145,6 +150,7 @@ int apply_tuning(sa_heom* h) {
     h->cfg.block = h->block;
     h->cfg.chunk = h->chunk;
     h->cfg.use_queue = h->use_queue;
+    h->cfg.rec_cap = h->rec_cap;
     const uint32_t nchunks = uint32_t(h->chunk_begin.size() - 1);
     if (h->host_only) return SA_OK;
     if (h->d_chunk) cudaFree(h->d_chunk);
@@ -153,7 +159,7 @@ int apply_tuning(sa_heom* h) {
     if (rc) return rc;
     int occ = 0;
     CK(stage_occupancy(h->cfg, h->precision == SA_FP64, &occ));
-    if (occ < 1) return fail(SA_ERR_UNSUPPORTED, "stage kernel does not fit on an SM with this tuning");
+    if (occ < 1) return fail(SA_ERR_UNSUPPORTED, "stage kernel does not fit on an SM with this tuning (shared memory)");
     h->cfg.grid = h->use_queue ? int(std::min<int64_t>(int64_t(h->num_sms) * occ, nchunks)) : int(nchunks);
     if (h->cfg.grid < 1) h->cfg.grid = 1;
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
@@ -446,7 +452,14 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamCreate");
     }
     h->host_only = false;
-    if (!rc) rc = apply_tuning(h);
+    if (!rc) {
+        rc = apply_tuning(h);
+        // large m: shrink the work item until its shared-memory image fits
+        while (rc == SA_ERR_UNSUPPORTED && h->chunk / 2 >= h->max_u && h->chunk / 2 >= 64) {
+            h->chunk = (h->chunk / 2 + 31) / 32 * 32;
+            rc = apply_tuning(h);
+        }
+    }
     if (rc) {
         free_device(h);
         delete h;
@@ -749,7 +762,7 @@ int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue) {
     int nq = queue >= 0 ? queue : h->use_queue;
     if (nb < 64 || nb > 256 || nb % 32) return fail(SA_ERR_INVALID_ARG, "block must be 64..256, multiple of 32");
     if (nc % 32 || nc < h->max_u || nc > kMaxChunkVars)
-        return fail(SA_ERR_INVALID_ARG, "chunk must be a multiple of 32 between the largest pattern and 4096");
+        return fail(SA_ERR_INVALID_ARG, "chunk must be a multiple of 32 between the largest pattern and 2048");
     h->block = nb;
     h->chunk = nc;
     h->use_queue = nq ? 1 : 0;
@@ -763,6 +776,7 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int blocks[] = {128, 256};
     const int chunks[] = {512, 1024, 2048};
+    // (chunks above the shared-memory budget are skipped by set_tuning)
     float best_ms = 1e30f;
     int bb = h->block, bc = h->chunk, bq = h->use_queue;
     cudaEvent_t e0, e1;

@@ -301,8 +301,10 @@ int build_instance(const sa_params& p, HostInstance& hi, std::string& err) {
         for (int q = 1; q <= G; ++q) {
             int start = int(out.size());
             uint32_t vq = cv[q - 1];
-            for (int k = 0; k < m; ++k) {
-                for (int dir = +1; dir >= -1; dir -= 2) {
+            // raise records of every channel first, then the lower records
+            // (the P_q variables only need the lower ones)
+            for (int dir = +1; dir >= -1; dir -= 2) {
+                for (int k = 0; k < m; ++k) {
                     int n = hi.comp[size_t(vq) * m + k];
                     if (dir > 0 && hi.tier[i] >= L) continue;   // Eq. hard-cutoff-factor
                     if (dir < 0 && n == 0) continue;            // only occupied channels lower
@@ -365,12 +367,15 @@ int build_instance(const sa_params& p, HostInstance& hi, std::string& err) {
                     int trs = hi.cat_trank[hi.cat_off[t] + tstar - 1];
                     Record rec;
                     rec.target = uint32_t(hi.var_off[t]);
-                    rec.packed = pack_record(tstar, Gp, trs < 0 ? 0 : trs, trs >= 0 ? 1 : 0, ipos, ins, del,
-                                             coef_id(k, n, dir > 0 ? 1 : 0));
+                    // a merge record (ins = 0) keeps the merged source category
+                    // in the ipos field, which only inserts use
+                    rec.packed = pack_record(tstar, Gp, trs < 0 ? 0 : trs, trs >= 0 ? 1 : 0, ins ? ipos : s_merge,
+                                             ins, del, coef_id(k, n, dir > 0 ? 1 : 0));
                     out.push_back(rec);
                 }
             }
-            cw.push_back(pack_cat(start, int(out.size()) - start, hi.cat_trank[hi.cat_off[i] + q - 1]));
+            cw.push_back(pack_cat(start, int(out.size()) - start, hi.cat_trank[hi.cat_off[i] + q - 1],
+                                  hi.tier[i] < L ? m : 0));
         }
     }
     if (bad) {

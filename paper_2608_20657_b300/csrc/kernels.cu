@@ -28,6 +28,7 @@
 // mirror feeds the tier-1 readers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "sa_internal.h"
@@ -78,6 +79,7 @@ template <typename T> struct StageParams {
     const uint32_t* __restrict__ lut_off;   // per G
     uint32_t nchunks;
     int chunk;                              // variable capacity of the staged slice
+    int rec_cap;                            // record capacity of the staged slice
     const C* x_in;                          // stage input (gathered)
     C* x_out;                               // next stage input, or dR/dt (stage -1)
     const C* y;                             // state at the start of the step
@@ -106,9 +108,9 @@ __device__ __forceinline__ int tau_d(uint32_t pk, int moved, int r) {
 // the pattern's local variable l, gath(i) the batch-global variable i.
 template <typename A, typename T, class Own, class Gath>
 __device__ __forceinline__ typename Cx<A>::t var_rhs(const StageParams<T>& P, int kind, int q, int r, int G,
-                                                     const uint32_t* s_cw, const T* s_cM, const PatHdr& h,
-                                                     const InstDev& I, typename Cx<A>::t gam, Own own,
-                                                     Gath gath) {
+                                                     const uint32_t* s_cw, const T* s_cM, const uint2* s_rec,
+                                                     const PatHdr& h, const InstDev& I, typename Cx<A>::t gam,
+                                                     Own own, Gath gath) {
     using CA = typename Cx<A>::t;
     using C = typename Cx<T>::t;
     constexpr bool kMixed = sizeof(A) == 8 && sizeof(T) == 4;
@@ -158,73 +160,127 @@ __device__ __forceinline__ typename Cx<A>::t var_rhs(const StageParams<T>& P, in
         d = mk(g * t.y, -g * t.x);
         d = cfma(mk(-gam.x, -gam.y), v, d);
     }
-    // hierarchy terms
+    // hierarchy terms: the records of the row category (row delta of
+    // Eq. projector-commutator-element) and of the column category (column
+    // delta); gathers are issued four at a time before their products are
+    // accumulated
     const int row = (kind == KX || kind == KP || kind == KS || kind == KT) ? q : 0;
     const int col = (kind == KY) ? q : (kind == KS ? r : ((kind == KP || kind == KT) ? q : 0));
     const bool same = kind == KP;
-    const Record* R = P.rec + h.rec_off;
     auto crow = [&](int cid) -> CA {
         if constexpr (kMixed) return P.coef_row_d[I.coef_base + cid];
-        else return to_acc(P.coef_row[I.coef_base + cid], (CA*)nullptr);
+        else return to_acc(__ldg(P.coef_row + I.coef_base + cid), (CA*)nullptr);
     };
     auto ccol = [&](int cid) -> CA {
         if constexpr (kMixed) return P.coef_col_d[I.coef_base + cid];
-        else return to_acc(P.coef_col[I.coef_base + cid], (CA*)nullptr);
+        else return to_acc(__ldg(P.coef_col + I.coef_base + cid), (CA*)nullptr);
     };
-    if (row) {
-        const uint32_t w = s_cw[row - 1];
-        const int rs = w & 1023, nr = (w >> 10) & 31;
-        for (int j = 0; j < nr; ++j) {
-            const uint2 rc = __ldg(reinterpret_cast<const uint2*>(R + rs + j));
-            const uint32_t pk = rc.y;
-            const int cid = pk >> 23;
-            if (same && (cid & 1)) continue;  // the two raise terms of P_q cancel
-            const int ts = pk & 31, Gp = (pk >> 5) & 31;
-            int tl;
-            if (kind == KX) tl = ts;
-            else if (same) tl = 2 * Gp + ts;
-            else {
-                const int cc = tau_d(pk, row, col);
-                tl = (cc == ts) ? (Gp + 1) * (Gp + 1) + ((pk >> 10) & 31) : loc_S_d(Gp, ts, cc);
+    const uint32_t wr = row ? s_cw[row - 1] : 0u;
+    const uint32_t wc = (col && !same) ? s_cw[col - 1] : 0u;
+    // P_q: its two raise terms cancel, so only the lower records (which
+    // follow the raise records of the category) are read
+    const int skip = same ? int((wr >> 20) & 15) : 0;
+    const int nr = int((wr >> 10) & 31) - skip, nc = (wc >> 10) & 31;
+    const uint2* Rr = s_rec + (wr & 1023) + skip;
+    const uint2* Rc = s_rec + (wc & 1023);
+    const int ntot = nr + nc;
+    for (int i0 = 0; i0 < ntot; i0 += 4) {
+        CA val[4], cf[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u;
+            val[u] = mk(A(0), A(0));
+            cf[u] = mk(A(0), A(0));
+            if (i < ntot) {
+                const bool isrow = i < nr;
+                const uint2 rc = isrow ? Rr[i] : Rc[i - nr];
+                const uint32_t pk = rc.y;
+                const int cid = pk >> 23;
+                const int ts = pk & 31, Gp = (pk >> 5) & 31;
+                const int tT = (Gp + 1) * (Gp + 1) + ((pk >> 10) & 31);
+                int tl;
+                if (isrow) {
+                    if (kind == KX) tl = ts;
+                    else if (same) tl = 2 * Gp + ts;
+                    else {
+                        const int cc = tau_d(pk, row, col);
+                        tl = (cc == ts) ? tT : loc_S_d(Gp, ts, cc);
+                    }
+                } else {
+                    if (kind == KY) tl = Gp + ts;
+                    else {
+                        const int rr = tau_d(pk, col, row);
+                        tl = (rr == ts) ? tT : loc_S_d(Gp, rr, ts);
+                    }
+                }
+                val[u] = gath(rc.x + tl);
+                if (isrow) {
+                    cf[u] = crow(cid);
+                    if (same) cf[u] = cadd(cf[u], ccol(cid));
+                } else {
+                    cf[u] = ccol(cid);
+                }
             }
-            CA cf = crow(cid);
-            if (same) cf = cadd(cf, ccol(cid));
-            d = cfma(cf, gath(rc.x + tl), d);
         }
-    }
-    if (col && !same) {
-        const uint32_t w = s_cw[col - 1];
-        const int rs = w & 1023, nr = (w >> 10) & 31;
-        for (int j = 0; j < nr; ++j) {
-            const uint2 rc = __ldg(reinterpret_cast<const uint2*>(R + rs + j));
-            const uint32_t pk = rc.y;
-            const int cid = pk >> 23;
-            const int ts = pk & 31, Gp = (pk >> 5) & 31;
-            int tl;
-            if (kind == KY) tl = Gp + ts;
-            else {
-                const int rr = tau_d(pk, col, row);
-                tl = (rr == ts) ? (Gp + 1) * (Gp + 1) + ((pk >> 10) & 31) : loc_S_d(Gp, rr, ts);
-            }
-            d = cfma(ccol(cid), gath(rc.x + tl), d);
-        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d = cfma(cf[u], val[u], d);
     }
     return d;
+}
+
+// Shared-memory image of one work item (a chunk of consecutive patterns).
+template <typename T> struct ChunkSmem {
+    using C = typename Cx<T>::t;
+    C* x;            // stage input slice
+    C* R;            // grouped row sums R_q per category
+    C* Cs;           // grouped column sums C_q per category
+    C* Zs;           // sum_q M_q (X_q - Y_q) per pattern
+    C* crow;         // decoded record: row coefficient
+    C* ccol;         // decoded record: column coefficient
+    int4* dA;        // decoded record: X'-index, S'-row base, S'-column base, T'-index
+    uint32_t* dS;    // decoded record: small fields
+    uint2* rec;      // raw records (the FP64 physical-representative path)
+    PatHdr* hdr;
+    uint32_t* cw;
+    T* cM;
+    uint32_t* perm;  // work order: l | j << 11 | kind << 19 | q << 22 | r << 27
+    uint16_t* sb;
+    uint16_t* ob;
+};
+
+template <typename T>
+__device__ __forceinline__ ChunkSmem<T> carve(unsigned char* base, int chunk, int rec_cap) {
+    using C = typename Cx<T>::t;
+    ChunkSmem<T> S;
+    const int ncat = chunk / 4 + 8;
+    unsigned char* p = base;
+    S.x = reinterpret_cast<C*>(p);       p += sizeof(C) * chunk;
+    S.R = reinterpret_cast<C*>(p);       p += sizeof(C) * ncat;
+    S.Cs = reinterpret_cast<C*>(p);      p += sizeof(C) * ncat;
+    S.Zs = reinterpret_cast<C*>(p);      p += sizeof(C) * kMaxPatPerChunk;
+    S.crow = reinterpret_cast<C*>(p);    p += sizeof(C) * rec_cap;
+    S.ccol = reinterpret_cast<C*>(p);    p += sizeof(C) * rec_cap;
+    S.dA = reinterpret_cast<int4*>(p);   p += sizeof(int4) * rec_cap;
+    S.rec = reinterpret_cast<uint2*>(p); p += sizeof(uint2) * rec_cap;
+    S.dS = reinterpret_cast<uint32_t*>(p); p += sizeof(uint32_t) * rec_cap;
+    S.hdr = reinterpret_cast<PatHdr*>(p);  p += sizeof(PatHdr) * (kMaxPatPerChunk + 1);
+    S.cw = reinterpret_cast<uint32_t*>(p); p += sizeof(uint32_t) * ncat;
+    S.perm = reinterpret_cast<uint32_t*>(p); p += sizeof(uint32_t) * chunk;
+    S.cM = reinterpret_cast<T*>(p);      p += sizeof(T) * ncat;
+    S.sb = reinterpret_cast<uint16_t*>(p); p += sizeof(uint16_t) * kMaxPatPerChunk;
+    S.ob = reinterpret_cast<uint16_t*>(p);
+    return S;
 }
 
 template <typename T, bool FP64SIDE>
 __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem[];
-    // shared layout: x slice | headers | category words | multiplicities | local pattern ids
-    C* s_x = reinterpret_cast<C*>(smem);
-    PatHdr* s_hdr = reinterpret_cast<PatHdr*>(s_x + P.chunk);
-    uint32_t* s_cw = reinterpret_cast<uint32_t*>(s_hdr + kMaxPatPerChunk + 1);
-    T* s_cM = reinterpret_cast<T*>(s_cw + P.chunk / 4 + 8);
-    uint8_t* s_lp = reinterpret_cast<uint8_t*>(s_cM + P.chunk / 4 + 8);
-    __shared__ unsigned int s_c;
+    const ChunkSmem<T> S = carve<T>(smem, P.chunk, P.rec_cap);
+    __shared__ unsigned int s_c, s_nS;
 
     const T dtT = T(P.dt);
+    const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
     unsigned int iter = 0;
     for (;;) {
         unsigned int c;
@@ -239,95 +295,289 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
         if (c >= P.nchunks) break;
         const uint32_t p0 = __ldg(P.chunk_begin + c), p1 = __ldg(P.chunk_begin + c + 1);
         const int np = int(p1 - p0);
-        for (int j = threadIdx.x; j <= np; j += blockDim.x) s_hdr[j] = P.hdr[p0 + j];
-        __syncthreads();
-        const uint32_t v0 = s_hdr[0].var_off, nv = s_hdr[np].var_off - v0;
-        const uint32_t c0 = s_hdr[0].cat_off, ncat = s_hdr[np].cat_off - c0;
-        for (uint32_t l = threadIdx.x; l < nv; l += blockDim.x) s_x[l] = P.x_in[v0 + l];
+        // ---- phase 1: stage the chunk (every thread reads the ranges itself)
+        const PatHdr h0 = P.hdr[p0], h1 = P.hdr[p1];
+        const uint32_t v0 = h0.var_off, nv = h1.var_off - v0;
+        const uint32_t c0 = h0.cat_off, ncat = h1.cat_off - c0;
+        const uint32_t r0 = h0.rec_off, nrec = h1.rec_off - r0;
+        for (int j = threadIdx.x; j <= np; j += blockDim.x) S.hdr[j] = P.hdr[p0 + j];
+        for (uint32_t l = threadIdx.x; l < nv; l += blockDim.x) S.x[l] = P.x_in[v0 + l];
+        for (uint32_t l = threadIdx.x; l < nrec; l += blockDim.x)
+            S.rec[l] = __ldg(reinterpret_cast<const uint2*>(P.rec) + r0 + l);
         for (uint32_t l = threadIdx.x; l < ncat; l += blockDim.x) {
-            s_cw[l] = __ldg(P.cat_word + c0 + l);
-            s_cM[l] = __ldg(P.cat_M + c0 + l);
-        }
-        for (int j = threadIdx.x; j < np; j += blockDim.x) {
-            const uint32_t a = s_hdr[j].var_off - v0, b = s_hdr[j + 1].var_off - v0;
-            for (uint32_t l = a; l < b; ++l) s_lp[l] = uint8_t(j);
+            S.cw[l] = __ldg(P.cat_word + c0 + l);
+            S.cM[l] = __ldg(P.cat_M + c0 + l);
         }
         __syncthreads();
-        for (uint32_t l = threadIdx.x; l < nv; l += blockDim.x) {
-            const int j = s_lp[l];
-            const PatHdr h = s_hdr[j];
+        // ---- phase 2: warp 0 scans the work-order counts; the other threads
+        // take the categories: grouped sums R_q, C_q (Eqs. grouped-row-sum,
+        // grouped-column-sum) and the decoding of the category's records
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            const int per = (np + 31) / 32;
+            const int a = lane * per, b = min(np, a + per);
+            int ss = 0, so = 0;
+            for (int j = a; j < b; ++j) {
+                const int G = S.hdr[j].G;
+                const int u = int(S.hdr[j + 1].var_off - S.hdr[j].var_off);
+                ss += G * (G - 1);
+                so += u - G * (G - 1);
+            }
+            int is = ss, io = so;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int ts = __shfl_up_sync(0xffffffffu, is, off);
+                const int to = __shfl_up_sync(0xffffffffu, io, off);
+                if (lane >= off) {
+                    is += ts;
+                    io += to;
+                }
+            }
+            int bs = is - ss, bo = io - so;
+            for (int j = a; j < b; ++j) {
+                const int G = S.hdr[j].G;
+                const int u = int(S.hdr[j + 1].var_off - S.hdr[j].var_off);
+                S.sb[j] = uint16_t(bs);
+                S.ob[j] = uint16_t(bo);
+                bs += G * (G - 1);
+                bo += u - G * (G - 1);
+            }
+            if (lane == 31) s_nS = uint32_t(is);
+        } else {
+            for (uint32_t cl = threadIdx.x - 32; cl < ncat; cl += blockDim.x - 32) {
+                // owning pattern: last j with cat_off <= c0 + cl
+                int lo = 0, hi = np - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (S.hdr[mid].cat_off - c0 <= cl) lo = mid;
+                    else hi = mid - 1;
+                }
+                const PatHdr& h = S.hdr[lo];
+                const int G = h.G;
+                const int cb = int(h.cat_off - c0);
+                const int q = int(cl) - cb + 1;
+                const C* xp = S.x + (h.var_off - v0);
+                const uint32_t w = S.cw[cl];
+                const T Mq = S.cM[cl];
+                C Rs = xp[2 * G + q];
+                if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((w >> 15) & 31)], Rs);
+                C Cq = Rs;
+                for (int b = 1; b <= G; ++b) {
+                    if (b == q) continue;
+                    const T Mb = S.cM[cb + b - 1];
+                    Rs = caxpy(Mb, xp[loc_S_d(G, q, b)], Rs);
+                    Cq = caxpy(Mb, xp[loc_S_d(G, b, q)], Cq);
+                }
+                S.R[cl] = Rs;
+                S.Cs[cl] = Cq;
+                const InstDev& I = P.inst[h.inst];
+                const int nr = (w >> 10) & 31;
+                const int rl = int(h.rec_off - r0) + int(w & 1023);
+                for (int t = 0; t < nr; ++t) {
+                    const uint2 raw = S.rec[rl + t];
+                    const uint32_t pk = raw.y;
+                    const int ts = pk & 31, Gp = (pk >> 5) & 31, tr = (pk >> 10) & 31;
+                    const int ipos = (pk >> 16) & 31, ins = (pk >> 21) & 1, del = (pk >> 22) & 1;
+                    const int cid = pk >> 23;
+                    const int smerge = ins ? 63 : ipos;
+                    int4 A;
+                    A.x = int(raw.x) + ts;                                   // X'[tau*]
+                    A.y = int(raw.x) + 3 * Gp + (ts - 1) * (Gp - 1);         // S' row tau*
+                    A.z = int(raw.x) + 3 * Gp + ts;                          // S' column tau*
+                    A.w = int(raw.x) + (Gp + 1) * (Gp + 1) + tr;             // T'[tau*]
+                    S.dA[rl + t] = A;
+                    S.dS[rl + t] = uint32_t(del) | (uint32_t(ins) << 1) | (uint32_t(ipos) << 2) |
+                                   (uint32_t(ts) << 7) | (uint32_t(smerge) << 12) | (uint32_t(Gp) << 18);
+                    S.crow[rl + t] = __ldg(P.coef_row + I.coef_base + cid);
+                    S.ccol[rl + t] = __ldg(P.coef_col + I.coef_base + cid);
+                }
+            }
+        }
+        __syncthreads();
+        // ---- phase 3: pattern threads: work order (S variables first, then
+        // the rest, each in memory order) and the Z sums of Eq. HZ
+        {
+            const uint32_t nS = s_nS;
+            for (int j = threadIdx.x; j < np; j += blockDim.x) {
+                const PatHdr& h = S.hdr[j];
+                const int G = h.G;
+                const uint32_t a = h.var_off - v0;
+                const uint32_t ej = a | (uint32_t(j) << 11);
+                uint32_t* ps = S.perm + S.sb[j];
+                uint32_t* po = S.perm + nS + S.ob[j];
+                const int cb = int(h.cat_off - c0);
+                C zs = mk(T(0), T(0));
+                *po++ = ej | (uint32_t(KZ) << 19);
+                for (int q = 1; q <= G; ++q) {
+                    *po++ = (ej + q) | (uint32_t(KX) << 19) | (uint32_t(q) << 22);
+                    zs = caxpy(S.cM[cb + q - 1], csub(S.x[a + q], S.x[a + G + q]), zs);
+                }
+                for (int q = 1; q <= G; ++q) *po++ = (ej + G + q) | (uint32_t(KY) << 19) | (uint32_t(q) << 22);
+                for (int q = 1; q <= G; ++q) *po++ = (ej + 2 * G + q) | (uint32_t(KP) << 19) | (uint32_t(q) << 22);
+                uint32_t l = ej + 3 * G + 1;
+                for (int q = 1; q <= G; ++q)
+                    for (int r = 1; r <= G; ++r)
+                        if (r != q) *ps++ = (l++) | (uint32_t(KS) << 19) | (uint32_t(q) << 22) | (uint32_t(r) << 27);
+                for (int q = 1; q <= G; ++q) {
+                    const int tr = (S.cw[cb + q - 1] >> 15) & 31;
+                    if (tr != 31)
+                        *po++ = (ej + (G + 1) * (G + 1) + tr) | (uint32_t(KT) << 19) | (uint32_t(q) << 22);
+                }
+                S.Zs[j] = zs;
+            }
+        }
+        __syncthreads();
+        // ---- phase 4: one unique variable per thread
+        for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x) {
+            const uint32_t e = S.perm[i];
+            const uint32_t l = e & 2047u;
+            const int j = int((e >> 11) & 255u);
+            const int kind = int((e >> 19) & 7u);
+            const int q = int((e >> 22) & 31u);
+            const int r = int(e >> 27);
+            const uint32_t vg = v0 + l;
+            const PatHdr h = S.hdr[j];
             const int G = h.G;
             const int pl = int(h.var_off - v0);
-            const int loc = int(l) - pl;
-            int kind, q, r = 0;
-            if (loc < (G + 1) * (G + 1)) {
-                const uint32_t code = __ldg(P.lut + __ldg(P.lut_off + G) + loc);
-                kind = code & 7;
-                q = (code >> 3) & 31;
-                r = (code >> 8) & 31;
-            } else {
-                kind = KT;
-                const int t = loc - (G + 1) * (G + 1);
-                q = 1;
-                for (int a = 1; a <= G; ++a)
-                    if (((s_cw[h.cat_off - c0 + a - 1] >> 15) & 31) == uint32_t(t)) q = a;
-            }
+            const int cb = int(h.cat_off - c0);
             const InstDev& I = P.inst[h.inst];
-            const uint32_t* cw = s_cw + (h.cat_off - c0);
-            const T* cM = s_cM + (h.cat_off - c0);
-            const uint32_t vg = v0 + l;
             if (FP64SIDE && h.tier == 0) {
                 // physical representative: FP64 arithmetic and FP64 storage
                 const double2* xsin = P.xs_in + I.side;
-                auto own = [&](int i) { return xsin[i]; };
-                auto gath = [&](uint32_t i) { const C t = P.x_in[i]; return make_double2(t.x, t.y); };
+                auto own = [&](int ii) { return xsin[ii]; };
+                auto gath = [&](uint32_t ii) { const C t = __ldg(P.x_in + ii); return make_double2(t.x, t.y); };
                 const double2 gam = make_double2(P.gamma[p0 + j].x, P.gamma[p0 + j].y);
-                const double2 k = var_rhs<double>(P, kind, q, r, G, cw, cM, h, I, gam, own, gath);
+                const int loc = int(l) - pl;
+                const double2 k = var_rhs<double>(P, kind, q, r, G, S.cw + cb, S.cM + cb,
+                                                  S.rec + (h.rec_off - r0), h, I, gam, own, gath);
                 const double dt = P.dt;
                 const int si = int(I.side) + loc;
                 if (P.stage < 0) {
                     P.xs_out[si] = k;
                     P.x_out[vg] = mk(T(k.x), T(k.y));
                 } else if (P.stage == 3) {
-                    const double2 yv = P.ys[si], av = P.accs[si];
-                    const double2 yn = make_double2(yv.x + dt / 6.0 * (av.x + k.x), yv.y + dt / 6.0 * (av.y + k.y));
+                    const double2 ys = P.ys[si], as = P.accs[si];
+                    const double2 yn = make_double2(ys.x + dt / 6.0 * (as.x + k.x), ys.y + dt / 6.0 * (as.y + k.y));
                     P.ys_out[si] = yn;
                     P.y_out[vg] = mk(T(yn.x), T(yn.y));
                 } else {
-                    const double2 yv = P.ys[si];
-                    double2 av;
-                    if (P.stage == 0) av = k;
+                    const double2 ys = P.ys[si];
+                    double2 as;
+                    if (P.stage == 0) as = k;
                     else {
-                        av = P.accs[si];
-                        av.x += 2.0 * k.x;
-                        av.y += 2.0 * k.y;
+                        as = P.accs[si];
+                        as.x += 2.0 * k.x;
+                        as.y += 2.0 * k.y;
                     }
-                    P.accs[si] = av;
+                    P.accs[si] = as;
                     const double a = P.stage == 2 ? dt : 0.5 * dt;
-                    const double2 xn = make_double2(yv.x + a * k.x, yv.y + a * k.y);
+                    const double2 xn = make_double2(ys.x + a * k.x, ys.y + a * k.y);
                     P.xs_out[si] = xn;
                     P.x_out[vg] = mk(T(xn.x), T(xn.y));
                 }
                 continue;
             }
-            auto own = [&](int i) { return s_x[pl + i]; };
-            auto gath = [&](uint32_t i) { return P.x_in[i]; };
-            const C k = var_rhs<T>(P, kind, q, r, G, cw, cM, h, I, __ldg(P.gamma + p0 + j), own, gath);
+            // stream operands of the RK4 stage, issued before the derivative
+            C yv, av;
+            if (P.stage == 0) {
+                yv = S.x[l];
+            } else if (P.stage > 0) {
+                yv = P.y[vg];
+                av = P.acc[vg];
+            }
+            const T g = sizeof(T) == 8 ? T(I.g) : T(I.gf);
+            const T det = sizeof(T) == 8 ? T(I.detuning) : T(I.detf);
+            const T kap = sizeof(T) == 8 ? T(I.kappa) : T(I.kappaf);
+            const C gam = __ldg(P.gamma + p0 + j);
+            const C v = S.x[l];
+            const C* xp = S.x + pl;
+            // Hamiltonian, damping and loss (Eqs. HZ, HX and their Y, P, S, T
+            // counterparts), with the grouped sums of phases 2 and 3
+            C d;
+            if (kind == KZ) {
+                const C zs = S.Zs[j];
+                d = mk(g * zs.y, -g * zs.x);
+                d = cfma(mk(-(gam.x + kap), -gam.y), v, d);
+            } else if (kind == KX || kind == KY) {
+                const C Z = xp[0];
+                const C t = kind == KX ? csub(Z, S.R[cb + q - 1]) : csub(S.Cs[cb + q - 1], Z);
+                const T sd = kind == KX ? det : -det;
+                d = mk(sd * v.y + g * t.y, -sd * v.x - g * t.x);
+                d = cfma(mk(-(gam.x + T(0.5) * kap), -gam.y), v, d);
+            } else {
+                const C t = csub(xp[G + (kind == KS ? r : q)], xp[q]);
+                d = mk(g * t.y, -g * t.x);
+                d = cfma(mk(-gam.x, -gam.y), v, d);
+            }
+            // hierarchy terms (Eqs. uvar-up, uvar-down) from the decoded records
+            // of the row category and of the column category
+            const bool rowside = kind == KX || kind == KP || kind == KS || kind == KT;
+            const bool colside = kind == KY || kind == KS || kind == KT;
+            const int rcat = q;                       // row category (moved on the row side)
+            const int ccat = kind == KS ? r : q;      // column category (moved on the column side)
+            const uint32_t wr = rowside ? S.cw[cb + rcat - 1] : 0u;
+            const uint32_t wc = colside ? S.cw[cb + ccat - 1] : 0u;
+            const int skip = kind == KP ? int((wr >> 20) & 15) : 0;  // P_q: lower records only
+            const int nr = int((wr >> 10) & 31) - skip, nc = int((wc >> 10) & 31);
+            const int rb = int(h.rec_off - r0);
+            const int rr0 = rb + int(wr & 1023) + skip, rc0 = rb + int(wc & 1023);
+            const int colrow = q;                     // row category seen from the column side
+            const int rowcol = kind == KS ? r : q;    // column category seen from the row side
+            const int ntot = nr + nc;
+            for (int i0 = 0; i0 < ntot; i0 += 4) {
+                C val[4], cf[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int ii = i0 + u;
+                    val[u] = mk(T(0), T(0));
+                    cf[u] = mk(T(0), T(0));
+                    if (ii < ntot) {
+                        const bool isrow = ii < nr;
+                        const int rx = isrow ? rr0 + ii : rc0 + ii - nr;
+                        const int4 A = S.dA[rx];
+                        const uint32_t sm = S.dS[rx];
+                        const int Gp = int(sm >> 18) & 31;
+                        int idx;
+                        if (isrow) {
+                            if (kind == KX) idx = A.x;
+                            else if (kind == KP) idx = A.x + 2 * Gp;
+                            else {
+                                // S'[tau*, tau(b)] or T'[tau*], b = rowcol
+                                const int smerge = int(sm >> 12) & 63;
+                                const int b = rowcol;
+                                idx = A.y + b - (int(sm & 1u) && b > rcat ? 1 : 0) - (b > smerge ? 1 : 0);
+                                if (b == smerge) idx = A.w;
+                            }
+                            cf[u] = S.crow[rx];
+                            if (kind == KP) cf[u] = cadd(cf[u], S.ccol[rx]);
+                        } else {
+                            if (kind == KY) idx = A.x + Gp;
+                            else {
+                                // S'[tau(a), tau*] or T'[tau*], a = colrow
+                                const int a = colrow;
+                                const int ts = int(sm >> 7) & 31;
+                                const int ipos = int(sm >> 2) & 31;
+                                const int ta = a - ((sm & 1u) && a > ccat ? 1 : 0) + (((sm >> 1) & 1u) && a >= ipos ? 1 : 0);
+                                idx = (ta == ts) ? A.w : A.z + (ta - 1) * (Gp - 1) - (ts > ta ? 1 : 0);
+                            }
+                            cf[u] = S.ccol[rx];
+                        }
+                        val[u] = __ldg(P.x_in + idx);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) d = cfma(cf[u], val[u], d);
+            }
+            const C k = d;
             if (P.stage < 0) {
                 P.x_out[vg] = k;
             } else if (P.stage == 0) {
-                // x_in is y in the first stage
-                const C yv = s_x[l];
                 P.acc[vg] = k;
-                P.x_out[vg] = caxpy(T(0.5) * dtT, k, yv);
+                P.x_out[vg] = caxpy(aT, k, yv);
             } else if (P.stage == 3) {
-                const C yv = P.y[vg], av = P.acc[vg];
                 P.y_out[vg] = caxpy(dtT / T(6), cadd(av, k), yv);
             } else {
-                const C yv = P.y[vg];
-                const C av = P.acc[vg];
                 P.acc[vg] = caxpy(T(2), k, av);
-                P.x_out[vg] = caxpy(P.stage == 2 ? dtT : T(0.5) * dtT, k, yv);
+                P.x_out[vg] = caxpy(aT, k, yv);
             }
         }
         __syncthreads();
@@ -382,19 +632,21 @@ __global__ void init_rho0_kernel(const InstDev* __restrict__ inst, int ninst, co
 
 // ---- host launch wrappers (called from api.cu) -----------------------------
 
-size_t stage_smem_bytes(int chunk, bool fp64) {
+size_t stage_smem_bytes(int chunk, int rec_cap, bool fp64) {
     const size_t cs = fp64 ? 16 : 8, ts = fp64 ? 8 : 4;
-    size_t b = size_t(chunk) * cs;
+    const size_t ncat = size_t(chunk) / 4 + 8;
+    size_t b = cs * (size_t(chunk) + 2 * ncat + kMaxPatPerChunk + 2 * size_t(rec_cap));
+    b += (sizeof(int4) + sizeof(uint2) + sizeof(uint32_t)) * size_t(rec_cap);
     b += sizeof(PatHdr) * (kMaxPatPerChunk + 1);
-    b += sizeof(uint32_t) * (chunk / 4 + 8);
-    b += ts * (chunk / 4 + 8);
-    b += size_t(chunk);
-    return (b + 15) / 16 * 16;
+    b += sizeof(uint32_t) * (ncat + size_t(chunk));
+    b += ts * ncat;
+    b += 2 * sizeof(uint16_t) * kMaxPatPerChunk;
+    return (b + 15) / 16 * 16 + 16;
 }
 
 template <typename T, bool SIDE>
 static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, cudaStream_t st) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, sizeof(T) == 8);
+    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.rec_cap, sizeof(T) == 8);
     stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     return cudaGetLastError();
 }
@@ -419,6 +671,7 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.lut_off = static_cast<const uint32_t*>(s.lut_off);
     p.nchunks = s.nchunks;
     p.chunk = cfg.chunk;
+    p.rec_cap = cfg.rec_cap;
     p.x_in = static_cast<const C*>(s.x_in);
     p.x_out = static_cast<C*>(s.x_out);
     p.y = static_cast<const C*>(s.y);
@@ -444,8 +697,12 @@ cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, 
 // Sets the dynamic shared-memory limit once for the largest chunk (outside
 // any stream capture) and returns the CTAs per SM for this configuration.
 cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, fp64);
-    const int lim = int(stage_smem_bytes(kMaxChunkVars, fp64));
+    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.rec_cap, fp64);
+    const int lim = int(std::min<size_t>(stage_smem_bytes(kMaxChunkVars, kMaxChunkVars * 4, fp64), 227 * 1024));
+    if (sm > size_t(lim)) {
+        *blocks_per_sm = 0;
+        return cudaSuccess;
+    }
     cudaError_t e;
     if (fp64) {
         e = cudaFuncSetAttribute(stage_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);

@@ -17,7 +17,7 @@ constexpr int kCoefN = 32;           // occupation slots per channel in the coef
 constexpr int kCoefPerInst = SA_HEOM_MAXM * kCoefN * 2;
 constexpr int kMaxPatPerChunk = 256; // local pattern index is 8-bit
 constexpr int kSideSlots = 8;        // FP64 slots of the physical representative per instance
-constexpr int kMaxChunkVars = 4096;
+constexpr int kMaxChunkVars = 2048;   // 11-bit local variable index
 
 // ---- one hierarchy connection record ---------------------------------------
 // A record belongs to (pattern Lambda, category q, channel k, direction): the
@@ -27,8 +27,9 @@ constexpr int kMaxChunkVars = 4096;
 // lands at
 //     tau(r) = r - [del && r > q] + [ins && r >= ipos]
 // and the moved molecule at tau_star.  del: category q vanishes (M_q = 1);
-// ins: w is a new category of Lambda' inserted before old category ipos
-// (otherwise w merges with an existing category).  Together with the
+// ins: w is a new category of Lambda' inserted before old category ipos;
+// otherwise (ins = 0) w merges with the existing category s, and the ipos
+// field holds s.  Together with the
 // target's G' and the T-rank of tau_star this resolves every aligned-target
 // entry (Eq. aligned-accessor) with integer arithmetic.
 struct Record {
@@ -55,9 +56,11 @@ struct PatHdr {
 };
 
 // per-category word: bits 0-9 first record (relative to rec_off),
-// 10-14 record count, 15-19 T-rank (31 = no T variable)
-inline uint32_t pack_cat(int rec_start, int nrec, int trank) {
-    return uint32_t(rec_start) | (uint32_t(nrec) << 10) | (uint32_t(trank < 0 ? 31 : trank) << 15);
+// 10-14 record count, 15-19 T-rank (31 = no T variable), 20-23 raise
+// records (they come first, the lower records follow)
+inline uint32_t pack_cat(int rec_start, int nrec, int trank, int nup) {
+    return uint32_t(rec_start) | (uint32_t(nrec) << 10) | (uint32_t(trank < 0 ? 31 : trank) << 15) |
+           (uint32_t(nup) << 20);
 }
 
 // per-instance constants on the device
@@ -107,6 +110,7 @@ struct LaunchCfg {
     int chunk;      // variable capacity of one work item
     int use_queue;  // 1: persistent grid + atomic work queue
     int grid;       // CTAs
+    int rec_cap;    // most connection records in one work item
 };
 struct StageLaunch {
     const void* hdr; const void* cat_word; const void* cat_M; const void* gamma; const void* rec;
