@@ -698,7 +698,12 @@ cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, 
 // any stream capture) and returns the CTAs per SM for this configuration.
 cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm) {
     const size_t sm = stage_smem_bytes(cfg.chunk, cfg.rec_cap, fp64);
-    const int lim = int(std::min<size_t>(stage_smem_bytes(kMaxChunkVars, kMaxChunkVars * 4, fp64), 227 * 1024));
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // leave room for the kernel's static shared variables
+    const int lim = int(std::min<size_t>(stage_smem_bytes(kMaxChunkVars, kMaxChunkVars * 4, fp64),
+                                         size_t(std::max(optin - 1024, 0))));
     if (sm > size_t(lim)) {
         *blocks_per_sm = 0;
         return cudaSuccess;
