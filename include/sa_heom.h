@@ -33,7 +33,8 @@
  *        row major); T_q for the categories with M_q >= 2, in order.
  *    The physical density operator is the first pattern of each instance
  *    (Z, X_0, Y_0, P_0[, T_0], Sec. IV.C).
- *  - SA_FP32_AUX state buffers hold float2[n_vars_total], padded to 256
+ *  - SA_FP64 state buffers hold double2[n_vars_total] padded to 256 bytes.
+ *    SA_FP32_AUX state buffers hold float2[n_vars_total], padded to 256
  *    bytes, followed by double2[8 * n_instances]: slot 8*i + j holds
  *    variable j of instance i's physical representative in FP64; the float2
  *    copy of those variables mirrors it for readers in FP32.
@@ -251,6 +252,14 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best);
 
 /* Number of stage-kernel launches one RK4 step issues (for launch counting). */
 int sa_heom_launches_per_step(const sa_heom* h);
+
+/*
+ * sa_heom_device_error -- read the kernels' device error word (synchronises
+ * `stream`).  Returns SA_ERR_TIMEOUT if a stage kernel gave up a bounded
+ * wait on its bulk copies (the affected launch left its outputs incomplete);
+ * SA_OK otherwise.  sa_heom_propagate with observables checks it too.
+ */
+int sa_heom_device_error(sa_heom* h, void* stream);
 
 const char* sa_heom_strerror(int code);
 const char* sa_heom_last_error(void);

@@ -89,6 +89,7 @@ def lib() -> ctypes.CDLL:
             "sa_heom_set_tuning": [vp, i32, i32, i32],
             "sa_heom_autotune": [vp, vp, vp, vp],
             "sa_heom_launches_per_step": [vp],
+            "sa_heom_device_error": [vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -109,8 +110,8 @@ def exported_symbols() -> list[str]:
             "sa_heom_var_offset", "sa_heom_dump_vectors", "sa_heom_dump_patterns", "sa_heom_dump_categories",
             "sa_heom_dump_terms", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_state_upload",
             "sa_heom_state_download", "sa_heom_rhs", "sa_heom_step", "sa_heom_propagate", "sa_heom_observables",
-            "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_launches_per_step", "sa_heom_strerror",
-            "sa_heom_last_error"]
+            "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_launches_per_step", "sa_heom_device_error",
+            "sa_heom_strerror", "sa_heom_last_error"]
 
 
 def _check(rc: int, where: str):
@@ -291,6 +292,9 @@ class Heom:
         best = (ctypes.c_int * 3)()
         _check(lib().sa_heom_autotune(self._h, _dev(state), _stream(stream), best), "sa_heom_autotune")
         return tuple(best)
+
+    def device_error(self, stream=None):
+        _check(lib().sa_heom_device_error(self._h, _stream(stream)), "sa_heom_device_error")
 
     def launches_per_step(self) -> int:
         return int(lib().sa_heom_launches_per_step(self._h))

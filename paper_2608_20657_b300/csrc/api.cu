@@ -41,9 +41,11 @@ int cuda_fail(cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
     } while (0)
 
+// Tables get 64 bytes of padding: the stage kernel's bulk copies round each
+// range out to 16-byte boundaries.
 template <typename V>
 int upload(void** dptr, const std::vector<V>& h) {
-    size_t b = std::max<size_t>(h.size() * sizeof(V), 16);
+    size_t b = h.size() * sizeof(V) + 64;
     cudaError_t e = cudaMalloc(dptr, b);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(table)");
     if (!h.empty()) {
@@ -75,9 +77,9 @@ struct sa_heom {
     std::vector<float> coef_row_f, coef_col_f;
     std::vector<uint16_t> lut;
     std::vector<uint32_t> lut_off;
-    std::vector<uint32_t> chunk_begin;
+    std::vector<ChunkDesc> chunks;
     int max_u = 0;
-    int rec_cap = 8;
+    int rec_cap = 8, cat_cap = 8;
     // tuning
     int block = 256, chunk = 1024, use_queue = 1;
     // device
@@ -86,6 +88,7 @@ struct sa_heom {
     void *d_rec = nullptr, *d_inst = nullptr, *d_theta = nullptr, *d_coef_row = nullptr, *d_coef_col = nullptr;
     void *d_coef_row_d = nullptr, *d_coef_col_d = nullptr, *d_lut = nullptr, *d_lut_off = nullptr;
     void* d_chunk = nullptr;
+    unsigned int* d_err = nullptr;
     void* d_work[3] = {nullptr, nullptr, nullptr};  // acc, xa, xb
     unsigned int* d_queue = nullptr;
     size_t queue_slots = 0;
@@ -94,7 +97,7 @@ struct sa_heom {
     double* d_rho0 = nullptr;
     cudaStream_t cap = nullptr;
     size_t state_bytes = 0, side_off = 0;
-    LaunchCfg cfg{256, 1024, 1, 1, 8};
+    LaunchCfg cfg{256, 1024, 1, 1, 8, 8};
     std::map<std::tuple<const void*, uint64_t, int64_t>, cudaGraphExec_t> graphs;
 };
 
@@ -124,25 +127,41 @@ void build_lut(sa_heom* h) {
     h->lut_off[kMaxG + 1] = uint32_t(h->lut.size());
 }
 
+// Work items: runs of consecutive patterns with at most `chunk` variables and
+// kMaxPatPerChunk patterns, with the ranges the stage kernel stages.
 void build_chunks(sa_heom* h) {
-    h->chunk_begin.clear();
-    h->chunk_begin.push_back(0);
+    std::vector<uint32_t> begin{0};
     int64_t vars = 0, pats = 0;
     for (int64_t p = 0; p < h->npat; ++p) {
         int64_t u = int64_t(h->hdr[p + 1].var_off) - int64_t(h->hdr[p].var_off);
         if (pats > 0 && (vars + u > h->chunk || pats >= kMaxPatPerChunk)) {
-            h->chunk_begin.push_back(uint32_t(p));
+            begin.push_back(uint32_t(p));
             vars = 0;
             pats = 0;
         }
         vars += u;
         ++pats;
     }
-    h->chunk_begin.push_back(uint32_t(h->npat));
-    uint32_t cap = 8;
-    for (size_t c = 0; c + 1 < h->chunk_begin.size(); ++c)
-        cap = std::max(cap, h->hdr[h->chunk_begin[c + 1]].rec_off - h->hdr[h->chunk_begin[c]].rec_off);
-    h->rec_cap = int((cap + 7) / 8 * 8);
+    begin.push_back(uint32_t(h->npat));
+    h->chunks.clear();
+    uint32_t rcap = 8, ccap = 8;
+    for (size_t c = 0; c + 1 < begin.size(); ++c) {
+        const PatHdr &a = h->hdr[begin[c]], &b = h->hdr[begin[c + 1]];
+        ChunkDesc d;
+        d.p0 = begin[c];
+        d.np = begin[c + 1] - begin[c];
+        d.v0 = a.var_off;
+        d.nv = b.var_off - a.var_off;
+        d.c0 = a.cat_off;
+        d.ncat = b.cat_off - a.cat_off;
+        d.r0 = a.rec_off;
+        d.nrec = b.rec_off - a.rec_off;
+        rcap = std::max(rcap, d.nrec);
+        ccap = std::max(ccap, d.ncat);
+        h->chunks.push_back(d);
+    }
+    h->rec_cap = int((rcap + 7) / 8 * 8);
+    h->cat_cap = int((ccap + 7) / 8 * 8);
 }
 
 int apply_tuning(sa_heom* h) {
@@ -151,11 +170,12 @@ int apply_tuning(sa_heom* h) {
     h->cfg.chunk = h->chunk;
     h->cfg.use_queue = h->use_queue;
     h->cfg.rec_cap = h->rec_cap;
-    const uint32_t nchunks = uint32_t(h->chunk_begin.size() - 1);
+    h->cfg.cat_cap = h->cat_cap;
+    const uint32_t nchunks = uint32_t(h->chunks.size());
     if (h->host_only) return SA_OK;
     if (h->d_chunk) cudaFree(h->d_chunk);
     h->d_chunk = nullptr;
-    int rc = upload(&h->d_chunk, h->chunk_begin);
+    int rc = upload(&h->d_chunk, h->chunks);
     if (rc) return rc;
     int occ = 0;
     CK(stage_occupancy(h->cfg, h->precision == SA_FP64, &occ));
@@ -172,7 +192,8 @@ void free_device(sa_heom* h) {
     h->graphs.clear();
     void* ptrs[] = {h->d_hdr, h->d_cat_word, h->d_catM, h->d_catMd, h->d_gamma, h->d_rec, h->d_inst, h->d_theta,
                     h->d_coef_row, h->d_coef_col, h->d_coef_row_d, h->d_coef_col_d, h->d_lut, h->d_lut_off,
-                    h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0};
+                    h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0,
+                    h->d_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -196,7 +217,7 @@ StageLaunch base_launch(const sa_heom* h) {
     s.cat_M = h->d_catM;
     s.gamma = h->d_gamma;
     s.rec = h->d_rec;
-    s.chunk_begin = h->d_chunk;
+    s.desc = h->d_chunk;
     s.inst = h->d_inst;
     s.coef_row = h->d_coef_row;
     s.coef_col = h->d_coef_col;
@@ -205,7 +226,8 @@ StageLaunch base_launch(const sa_heom* h) {
     s.coef_col_d = h->d_coef_col_d;
     s.lut = h->d_lut;
     s.lut_off = h->d_lut_off;
-    s.nchunks = uint32_t(h->chunk_begin.size() - 1);
+    s.nchunks = uint32_t(h->chunks.size());
+    s.err = h->d_err;
     return s;
 }
 
@@ -238,6 +260,15 @@ int enqueue_step(sa_heom* h, void* y, double dt, size_t slot, cudaStream_t st) {
         L.queue = h->d_queue + slot + s;
         CK(launch_stage(L, h->cfg, h->precision == SA_FP64, st));
     }
+    return SA_OK;
+}
+
+// the kernels' error word: bit 0 = a bounded wait on a bulk copy expired
+int read_device_error(sa_heom* h, cudaStream_t st) {
+    unsigned int w = 0;
+    CK(cudaMemcpyAsync(&w, h->d_err, sizeof(w), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (w) return fail(SA_ERR_TIMEOUT, "a bounded device wait expired in the stage kernel");
     return SA_OK;
 }
 
@@ -397,7 +428,7 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     h->chunk = std::max(1024, (h->max_u + 31) / 32 * 32);
     // state layout
     if (precision == SA_FP64) {
-        h->state_bytes = size_t(h->nvar) * 16;
+        h->state_bytes = (size_t(h->nvar) * 16 + 255) / 256 * 256;
         h->side_off = 0;
     } else {
         h->side_off = (size_t(h->nvar) * 8 + 255) / 256 * 256;
@@ -447,6 +478,11 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(rho0)");
     }
     if (!rc) rc = ensure_queue(h, 64);
+    if (!rc) {
+        e = cudaMalloc(&h->d_err, 64);
+        if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, 64);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(error word)");
+    }
     if (!rc) {
         e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamCreate");
@@ -729,6 +765,8 @@ int sa_heom_propagate(sa_heom* h, void* d_state, double dt, int64_t nsteps, int6
     }
     CK(cudaMemcpyAsync(h_obs, h->d_obs, need * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    rc = read_device_error(h, st);
+    if (rc) return rc;
     for (size_t j = 0; j < need; ++j)
         if (!std::isfinite(h_obs[j])) return fail(SA_ERR_NUMERIC, "non-finite observable");
     return SA_OK;
@@ -821,5 +859,11 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
 }
 
 int sa_heom_launches_per_step(const sa_heom* h) { return h ? 4 : 0; }
+
+int sa_heom_device_error(sa_heom* h, void* stream) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    return read_device_error(h, static_cast<cudaStream_t>(stream));
+}
 
 }  // extern "C"

@@ -68,7 +68,7 @@ template <typename T> struct StageParams {
     const T* __restrict__ cat_M;
     const C* __restrict__ gamma;
     const Record* __restrict__ rec;
-    const uint32_t* __restrict__ chunk_begin;  // nchunks + 1
+    const ChunkDesc* __restrict__ desc;    // nchunks work items
     const InstDev* __restrict__ inst;
     const C* __restrict__ coef_row;
     const C* __restrict__ coef_col;
@@ -80,6 +80,7 @@ template <typename T> struct StageParams {
     uint32_t nchunks;
     int chunk;                              // variable capacity of the staged slice
     int rec_cap;                            // record capacity of the staged slice
+    int cat_cap;                            // category capacity of the staged slice
     const C* x_in;                          // stage input (gathered)
     C* x_out;                               // next stage input, or dR/dt (stage -1)
     const C* y;                             // state at the start of the step
@@ -94,6 +95,7 @@ template <typename T> struct StageParams {
     int stage;                              // -1: right-hand side only; 0..3: RK4 stage
     int use_queue;
     unsigned int* queue;
+    unsigned int* err;                      // device error word (bit 0: a bounded wait expired)
 };
 
 enum { KZ = 0, KX = 1, KY = 2, KP = 3, KS = 4, KT = 5 };
@@ -228,10 +230,74 @@ __device__ __forceinline__ typename Cx<A>::t var_rhs(const StageParams<T>& P, in
     return d;
 }
 
-// Shared-memory image of one work item (a chunk of consecutive patterns).
-template <typename T> struct ChunkSmem {
+// ---- TMA bulk copies and mbarriers (inline PTX) ----------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: about a second of SM clocks, then report failure
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (2LL << 30)) return false;
+    return true;
+}
+
+// A bulk copy must start on a 16-byte boundary and cover a multiple of 16
+// bytes: copy the enclosing aligned element range and remember how many
+// elements precede the first wanted one.  Tables and state buffers are
+// padded so that the rounded range stays inside the allocation.
+struct Span {
+    const char* src;
+    uint32_t bytes;
+    uint32_t skip;
+};
+__device__ __forceinline__ Span span(const void* base, uint32_t start, uint32_t count, uint32_t esz) {
+    const uint32_t per = esz >= 16 ? 1u : 16u / esz;
+    const uint32_t a = start - start % per;
+    const uint32_t e = (start + count + per - 1) / per * per;
+    Span sp;
+    sp.src = static_cast<const char*>(base) + size_t(a) * esz;
+    sp.bytes = count ? (e - a) * esz : 0u;
+    sp.skip = start - a;
+    return sp;
+}
+
+// Shared-memory image of one work item (double-buffered staging area plus
+// the per-item work arrays).
+template <typename T> struct StageBuf {
     using C = typename Cx<T>::t;
-    C* x;            // stage input slice
+    PatHdr* hdr;
+    C* x;
+    C* y;
+    C* acc;
+    uint2* rec;
+    uint32_t* cw;
+    T* cM;
+};
+template <typename T> struct StageWork {
+    using C = typename Cx<T>::t;
     C* R;            // grouped row sums R_q per category
     C* Cs;           // grouped column sums C_q per category
     C* Zs;           // sum_q M_q (X_q - Y_q) per pattern
@@ -239,156 +305,236 @@ template <typename T> struct ChunkSmem {
     C* ccol;         // decoded record: column coefficient
     int4* dA;        // decoded record: X'-index, S'-row base, S'-column base, T'-index
     uint32_t* dS;    // decoded record: small fields
-    uint2* rec;      // raw records (the FP64 physical-representative path)
-    PatHdr* hdr;
-    uint32_t* cw;
-    T* cM;
     uint32_t* perm;  // work order: l | j << 11 | kind << 19 | q << 22 | r << 27
     uint16_t* sb;
     uint16_t* ob;
 };
 
+__host__ __device__ __forceinline__ size_t al16(size_t b) { return (b + 15) / 16 * 16; }
+
 template <typename T>
-__device__ __forceinline__ ChunkSmem<T> carve(unsigned char* base, int chunk, int rec_cap) {
+__host__ __device__ __forceinline__ size_t buf_bytes(int chunk, int rec_cap, int cat_cap) {
+    const size_t cs = 2 * sizeof(T);
+    return al16(sizeof(PatHdr) * (kMaxPatPerChunk + 1)) + 3 * al16(cs * (chunk + 4)) + al16(8 * (rec_cap + 4)) +
+           al16(4 * (cat_cap + 8)) + al16(sizeof(T) * (cat_cap + 8));
+}
+template <typename T>
+__host__ __device__ __forceinline__ size_t work_bytes(int chunk, int rec_cap, int cat_cap) {
+    const size_t cs = 2 * sizeof(T);
+    return 2 * al16(cs * cat_cap) + al16(cs * kMaxPatPerChunk) + 2 * al16(cs * rec_cap) + al16(16 * rec_cap) +
+           al16(4 * rec_cap) + al16(4 * chunk) + 2 * al16(2 * kMaxPatPerChunk);
+}
+
+template <typename T>
+__device__ __forceinline__ StageBuf<T> carve_buf(unsigned char* p, int chunk, int rec_cap, int cat_cap) {
     using C = typename Cx<T>::t;
-    ChunkSmem<T> S;
-    const int ncat = chunk / 4 + 8;
-    unsigned char* p = base;
-    S.x = reinterpret_cast<C*>(p);       p += sizeof(C) * chunk;
-    S.R = reinterpret_cast<C*>(p);       p += sizeof(C) * ncat;
-    S.Cs = reinterpret_cast<C*>(p);      p += sizeof(C) * ncat;
-    S.Zs = reinterpret_cast<C*>(p);      p += sizeof(C) * kMaxPatPerChunk;
-    S.crow = reinterpret_cast<C*>(p);    p += sizeof(C) * rec_cap;
-    S.ccol = reinterpret_cast<C*>(p);    p += sizeof(C) * rec_cap;
-    S.dA = reinterpret_cast<int4*>(p);   p += sizeof(int4) * rec_cap;
-    S.rec = reinterpret_cast<uint2*>(p); p += sizeof(uint2) * rec_cap;
-    S.dS = reinterpret_cast<uint32_t*>(p); p += sizeof(uint32_t) * rec_cap;
-    S.hdr = reinterpret_cast<PatHdr*>(p);  p += sizeof(PatHdr) * (kMaxPatPerChunk + 1);
-    S.cw = reinterpret_cast<uint32_t*>(p); p += sizeof(uint32_t) * ncat;
-    S.perm = reinterpret_cast<uint32_t*>(p); p += sizeof(uint32_t) * chunk;
-    S.cM = reinterpret_cast<T*>(p);      p += sizeof(T) * ncat;
-    S.sb = reinterpret_cast<uint16_t*>(p); p += sizeof(uint16_t) * kMaxPatPerChunk;
-    S.ob = reinterpret_cast<uint16_t*>(p);
-    return S;
+    StageBuf<T> B;
+    B.hdr = reinterpret_cast<PatHdr*>(p); p += al16(sizeof(PatHdr) * (kMaxPatPerChunk + 1));
+    B.x = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * (chunk + 4));
+    B.y = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * (chunk + 4));
+    B.acc = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * (chunk + 4));
+    B.rec = reinterpret_cast<uint2*>(p);  p += al16(8 * (rec_cap + 4));
+    B.cw = reinterpret_cast<uint32_t*>(p); p += al16(4 * (cat_cap + 8));
+    B.cM = reinterpret_cast<T*>(p);
+    return B;
+}
+template <typename T>
+__device__ __forceinline__ StageWork<T> carve_work(unsigned char* p, int chunk, int rec_cap, int cat_cap) {
+    using C = typename Cx<T>::t;
+    StageWork<T> W;
+    W.R = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * cat_cap);
+    W.Cs = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * cat_cap);
+    W.Zs = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * kMaxPatPerChunk);
+    W.crow = reinterpret_cast<C*>(p);    p += al16(sizeof(C) * rec_cap);
+    W.ccol = reinterpret_cast<C*>(p);    p += al16(sizeof(C) * rec_cap);
+    W.dA = reinterpret_cast<int4*>(p);   p += al16(16 * rec_cap);
+    W.dS = reinterpret_cast<uint32_t*>(p); p += al16(4 * rec_cap);
+    W.perm = reinterpret_cast<uint32_t*>(p); p += al16(4 * chunk);
+    W.sb = reinterpret_cast<uint16_t*>(p); p += al16(2 * kMaxPatPerChunk);
+    W.ob = reinterpret_cast<uint16_t*>(p);
+    return W;
+}
+
+// element offsets of the staged slices inside a buffer (the "skip" of each span)
+struct Skips {
+    uint32_t x, y, acc, rec, cw, cM;
+};
+
+// Issue the bulk copies of work item d into buffer B (one thread).
+template <typename T>
+__device__ __forceinline__ Skips issue_item(const StageParams<T>& P, const ChunkDesc& d, const StageBuf<T>& B,
+                                            uint64_t* bar) {
+    using C = typename Cx<T>::t;
+    const uint32_t cs = sizeof(C);
+    const Span sh = span(P.hdr, d.p0, d.np + 1, sizeof(PatHdr));
+    const Span sx = span(P.x_in, d.v0, d.nv, cs);
+    const bool want_y = P.stage > 0, want_acc = P.stage > 0;
+    const Span sy = span(P.y, d.v0, want_y ? d.nv : 0u, cs);
+    const Span sa = span(P.acc, d.v0, want_acc ? d.nv : 0u, cs);
+    const Span sr = span(P.rec, d.r0, d.nrec, 8);
+    const Span sw = span(P.cat_word, d.c0, d.ncat, 4);
+    const Span sm = span(P.cat_M, d.c0, d.ncat, sizeof(T));
+    mbar_expect_tx(bar, sh.bytes + sx.bytes + sy.bytes + sa.bytes + sr.bytes + sw.bytes + sm.bytes);
+    bulk_g2s(B.hdr, sh.src, sh.bytes, bar);
+    if (sx.bytes) bulk_g2s(B.x, sx.src, sx.bytes, bar);
+    if (sy.bytes) bulk_g2s(B.y, sy.src, sy.bytes, bar);
+    if (sa.bytes) bulk_g2s(B.acc, sa.src, sa.bytes, bar);
+    if (sr.bytes) bulk_g2s(B.rec, sr.src, sr.bytes, bar);
+    if (sw.bytes) bulk_g2s(B.cw, sw.src, sw.bytes, bar);
+    if (sm.bytes) bulk_g2s(B.cM, sm.src, sm.bytes, bar);
+    return Skips{sx.skip, sy.skip, sa.skip, sr.skip, sw.skip, sm.skip};
 }
 
 template <typename T, bool FP64SIDE>
 __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem[];
-    const ChunkSmem<T> S = carve<T>(smem, P.chunk, P.rec_cap);
-    __shared__ unsigned int s_c, s_nS;
+    const size_t bb = buf_bytes<T>(P.chunk, P.rec_cap, P.cat_cap);
+    auto buf = [&](int which) { return carve_buf<T>(smem + (which ? bb : 0), P.chunk, P.rec_cap, P.cat_cap); };
+    const StageWork<T> W = carve_work<T>(smem + 2 * bb, P.chunk, P.rec_cap, P.cat_cap);
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ ChunkDesc s_desc[2];
+    __shared__ Skips s_skip[2];
+    __shared__ unsigned int s_item[2], s_nS;
+
+    const int tid = threadIdx.x;
+    const int producer = blockDim.x - 32;  // lane 0 of the last warp issues the copies
+    unsigned int iter = 0;
+    auto next_item = [&]() -> unsigned int {
+        if (P.use_queue) return atomicAdd(P.queue, 1u);
+        return blockIdx.x + (iter++) * gridDim.x;
+    };
+    if (tid == producer) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const unsigned int c = next_item();
+        s_item[0] = c;
+        if (c < P.nchunks) {
+            const ChunkDesc d = P.desc[c];
+            s_desc[0] = d;
+            s_skip[0] = issue_item(P, d, buf(0), &s_bar[0]);
+        }
+    }
+    __syncthreads();
 
     const T dtT = T(P.dt);
     const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
-    unsigned int iter = 0;
+    uint32_t parity0 = 0, parity1 = 0;
+    int b = 0;
     for (;;) {
-        unsigned int c;
-        if (P.use_queue) {
-            if (threadIdx.x == 0) s_c = atomicAdd(P.queue, 1u);
-            __syncthreads();
-            c = s_c;
-        } else {
-            c = blockIdx.x + iter * gridDim.x;
-            ++iter;
-        }
+        const unsigned int c = s_item[b];
         if (c >= P.nchunks) break;
-        const uint32_t p0 = __ldg(P.chunk_begin + c), p1 = __ldg(P.chunk_begin + c + 1);
-        const int np = int(p1 - p0);
-        // ---- phase 1: stage the chunk (every thread reads the ranges itself)
-        const PatHdr h0 = P.hdr[p0], h1 = P.hdr[p1];
-        const uint32_t v0 = h0.var_off, nv = h1.var_off - v0;
-        const uint32_t c0 = h0.cat_off, ncat = h1.cat_off - c0;
-        const uint32_t r0 = h0.rec_off, nrec = h1.rec_off - r0;
-        for (int j = threadIdx.x; j <= np; j += blockDim.x) S.hdr[j] = P.hdr[p0 + j];
-        for (uint32_t l = threadIdx.x; l < nv; l += blockDim.x) S.x[l] = P.x_in[v0 + l];
-        for (uint32_t l = threadIdx.x; l < nrec; l += blockDim.x)
-            S.rec[l] = __ldg(reinterpret_cast<const uint2*>(P.rec) + r0 + l);
-        for (uint32_t l = threadIdx.x; l < ncat; l += blockDim.x) {
-            S.cw[l] = __ldg(P.cat_word + c0 + l);
-            S.cM[l] = __ldg(P.cat_M + c0 + l);
+        // prefetch the next work item into the other buffer
+        if (tid == producer) {
+            const unsigned int c2 = next_item();
+            s_item[b ^ 1] = c2;
+            if (c2 < P.nchunks) {
+                const ChunkDesc d2 = P.desc[c2];
+                s_desc[b ^ 1] = d2;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                s_skip[b ^ 1] = issue_item(P, d2, buf(b ^ 1), &s_bar[b ^ 1]);
+            }
         }
-        __syncthreads();
+        const uint32_t par = b ? parity1 : parity0;
+        if (!mbar_wait(&s_bar[b], par)) {
+            // report, let a prefetch already in flight land (bounded), leave
+            atomicOr(P.err, 1u);
+            if (s_item[b ^ 1] < P.nchunks) mbar_wait(&s_bar[b ^ 1], b ? parity0 : parity1);
+            return;
+        }
+        if (b) parity1 ^= 1u;
+        else parity0 ^= 1u;
+
+        const StageBuf<T> B = buf(b);
+        const ChunkDesc d = s_desc[b];
+        const Skips sk = s_skip[b];
+        const int np = int(d.np);
+        const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0, ncat = d.ncat, r0 = d.r0;
+        const PatHdr* hdr = B.hdr;
+        const C* xs = B.x + sk.x;
+        const uint2* recs = B.rec + sk.rec;
+        const uint32_t* cwa = B.cw + sk.cw;
+        const T* cMa = B.cM + sk.cM;
         // ---- phase 2: warp 0 scans the work-order counts; the other threads
         // take the categories: grouped sums R_q, C_q (Eqs. grouped-row-sum,
         // grouped-column-sum) and the decoding of the category's records
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
+        if (tid < 32) {
+            const int lane = tid;
             const int per = (np + 31) / 32;
-            const int a = lane * per, b = min(np, a + per);
+            const int a = lane * per, e = min(np, a + per);
             int ss = 0, so = 0;
-            for (int j = a; j < b; ++j) {
-                const int G = S.hdr[j].G;
-                const int u = int(S.hdr[j + 1].var_off - S.hdr[j].var_off);
+            for (int j = a; j < e; ++j) {
+                const int G = hdr[j].G;
+                const int u = int(hdr[j + 1].var_off - hdr[j].var_off);
                 ss += G * (G - 1);
                 so += u - G * (G - 1);
             }
             int is = ss, io = so;
             for (int off = 1; off < 32; off <<= 1) {
-                const int ts = __shfl_up_sync(0xffffffffu, is, off);
-                const int to = __shfl_up_sync(0xffffffffu, io, off);
+                const int t1 = __shfl_up_sync(0xffffffffu, is, off);
+                const int t2 = __shfl_up_sync(0xffffffffu, io, off);
                 if (lane >= off) {
-                    is += ts;
-                    io += to;
+                    is += t1;
+                    io += t2;
                 }
             }
             int bs = is - ss, bo = io - so;
-            for (int j = a; j < b; ++j) {
-                const int G = S.hdr[j].G;
-                const int u = int(S.hdr[j + 1].var_off - S.hdr[j].var_off);
-                S.sb[j] = uint16_t(bs);
-                S.ob[j] = uint16_t(bo);
+            for (int j = a; j < e; ++j) {
+                const int G = hdr[j].G;
+                const int u = int(hdr[j + 1].var_off - hdr[j].var_off);
+                W.sb[j] = uint16_t(bs);
+                W.ob[j] = uint16_t(bo);
                 bs += G * (G - 1);
                 bo += u - G * (G - 1);
             }
             if (lane == 31) s_nS = uint32_t(is);
         } else {
-            for (uint32_t cl = threadIdx.x - 32; cl < ncat; cl += blockDim.x - 32) {
-                // owning pattern: last j with cat_off <= c0 + cl
-                int lo = 0, hi = np - 1;
+            for (uint32_t cl = tid - 32; cl < ncat; cl += blockDim.x - 32) {
+                int lo = 0, hi = np - 1;  // owning pattern: last j with cat_off <= c0 + cl
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (S.hdr[mid].cat_off - c0 <= cl) lo = mid;
+                    if (hdr[mid].cat_off - c0 <= cl) lo = mid;
                     else hi = mid - 1;
                 }
-                const PatHdr& h = S.hdr[lo];
+                const PatHdr h = hdr[lo];
                 const int G = h.G;
                 const int cb = int(h.cat_off - c0);
                 const int q = int(cl) - cb + 1;
-                const C* xp = S.x + (h.var_off - v0);
-                const uint32_t w = S.cw[cl];
-                const T Mq = S.cM[cl];
+                const C* xp = xs + (h.var_off - v0);
+                const uint32_t w = cwa[cl];
+                const T Mq = cMa[cl];
                 C Rs = xp[2 * G + q];
                 if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((w >> 15) & 31)], Rs);
                 C Cq = Rs;
-                for (int b = 1; b <= G; ++b) {
-                    if (b == q) continue;
-                    const T Mb = S.cM[cb + b - 1];
-                    Rs = caxpy(Mb, xp[loc_S_d(G, q, b)], Rs);
-                    Cq = caxpy(Mb, xp[loc_S_d(G, b, q)], Cq);
+                for (int e2 = 1; e2 <= G; ++e2) {
+                    if (e2 == q) continue;
+                    const T Mb = cMa[cb + e2 - 1];
+                    Rs = caxpy(Mb, xp[loc_S_d(G, q, e2)], Rs);
+                    Cq = caxpy(Mb, xp[loc_S_d(G, e2, q)], Cq);
                 }
-                S.R[cl] = Rs;
-                S.Cs[cl] = Cq;
+                W.R[cl] = Rs;
+                W.Cs[cl] = Cq;
                 const InstDev& I = P.inst[h.inst];
                 const int nr = (w >> 10) & 31;
                 const int rl = int(h.rec_off - r0) + int(w & 1023);
                 for (int t = 0; t < nr; ++t) {
-                    const uint2 raw = S.rec[rl + t];
+                    const uint2 raw = recs[rl + t];
                     const uint32_t pk = raw.y;
                     const int ts = pk & 31, Gp = (pk >> 5) & 31, tr = (pk >> 10) & 31;
                     const int ipos = (pk >> 16) & 31, ins = (pk >> 21) & 1, del = (pk >> 22) & 1;
                     const int cid = pk >> 23;
                     const int smerge = ins ? 63 : ipos;
                     int4 A;
-                    A.x = int(raw.x) + ts;                                   // X'[tau*]
-                    A.y = int(raw.x) + 3 * Gp + (ts - 1) * (Gp - 1);         // S' row tau*
-                    A.z = int(raw.x) + 3 * Gp + ts;                          // S' column tau*
-                    A.w = int(raw.x) + (Gp + 1) * (Gp + 1) + tr;             // T'[tau*]
-                    S.dA[rl + t] = A;
-                    S.dS[rl + t] = uint32_t(del) | (uint32_t(ins) << 1) | (uint32_t(ipos) << 2) |
-                                   (uint32_t(ts) << 7) | (uint32_t(smerge) << 12) | (uint32_t(Gp) << 18);
-                    S.crow[rl + t] = __ldg(P.coef_row + I.coef_base + cid);
-                    S.ccol[rl + t] = __ldg(P.coef_col + I.coef_base + cid);
+                    A.x = int(raw.x) + ts;                            // X'[tau*]
+                    A.y = int(raw.x) + 3 * Gp + (ts - 1) * (Gp - 1);  // S' row tau*
+                    A.z = int(raw.x) + 3 * Gp + ts;                   // S' column tau*
+                    A.w = int(raw.x) + (Gp + 1) * (Gp + 1) + tr;      // T'[tau*]
+                    W.dA[rl + t] = A;
+                    W.dS[rl + t] = uint32_t(del) | (uint32_t(ins) << 1) | (uint32_t(ipos) << 2) | (uint32_t(ts) << 7) |
+                                   (uint32_t(smerge) << 12) | (uint32_t(Gp) << 18);
+                    W.crow[rl + t] = __ldg(P.coef_row + I.coef_base + cid);
+                    W.ccol[rl + t] = __ldg(P.coef_col + I.coef_base + cid);
                 }
             }
         }
@@ -397,19 +543,19 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
         // the rest, each in memory order) and the Z sums of Eq. HZ
         {
             const uint32_t nS = s_nS;
-            for (int j = threadIdx.x; j < np; j += blockDim.x) {
-                const PatHdr& h = S.hdr[j];
+            for (int j = tid; j < np; j += blockDim.x) {
+                const PatHdr h = hdr[j];
                 const int G = h.G;
                 const uint32_t a = h.var_off - v0;
                 const uint32_t ej = a | (uint32_t(j) << 11);
-                uint32_t* ps = S.perm + S.sb[j];
-                uint32_t* po = S.perm + nS + S.ob[j];
+                uint32_t* ps = W.perm + W.sb[j];
+                uint32_t* po = W.perm + nS + W.ob[j];
                 const int cb = int(h.cat_off - c0);
                 C zs = mk(T(0), T(0));
                 *po++ = ej | (uint32_t(KZ) << 19);
                 for (int q = 1; q <= G; ++q) {
                     *po++ = (ej + q) | (uint32_t(KX) << 19) | (uint32_t(q) << 22);
-                    zs = caxpy(S.cM[cb + q - 1], csub(S.x[a + q], S.x[a + G + q]), zs);
+                    zs = caxpy(cMa[cb + q - 1], csub(xs[a + q], xs[a + G + q]), zs);
                 }
                 for (int q = 1; q <= G; ++q) *po++ = (ej + G + q) | (uint32_t(KY) << 19) | (uint32_t(q) << 22);
                 for (int q = 1; q <= G; ++q) *po++ = (ej + 2 * G + q) | (uint32_t(KP) << 19) | (uint32_t(q) << 22);
@@ -418,24 +564,26 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                     for (int r = 1; r <= G; ++r)
                         if (r != q) *ps++ = (l++) | (uint32_t(KS) << 19) | (uint32_t(q) << 22) | (uint32_t(r) << 27);
                 for (int q = 1; q <= G; ++q) {
-                    const int tr = (S.cw[cb + q - 1] >> 15) & 31;
+                    const int tr = (cwa[cb + q - 1] >> 15) & 31;
                     if (tr != 31)
                         *po++ = (ej + (G + 1) * (G + 1) + tr) | (uint32_t(KT) << 19) | (uint32_t(q) << 22);
                 }
-                S.Zs[j] = zs;
+                W.Zs[j] = zs;
             }
         }
         __syncthreads();
         // ---- phase 4: one unique variable per thread
-        for (uint32_t i = threadIdx.x; i < nv; i += blockDim.x) {
-            const uint32_t e = S.perm[i];
+        const C* ys = B.y + sk.y;
+        const C* as = B.acc + sk.acc;
+        for (uint32_t i = tid; i < nv; i += blockDim.x) {
+            const uint32_t e = W.perm[i];
             const uint32_t l = e & 2047u;
             const int j = int((e >> 11) & 255u);
             const int kind = int((e >> 19) & 7u);
             const int q = int((e >> 22) & 31u);
             const int r = int(e >> 27);
             const uint32_t vg = v0 + l;
-            const PatHdr h = S.hdr[j];
+            const PatHdr h = hdr[j];
             const int G = h.G;
             const int pl = int(h.var_off - v0);
             const int cb = int(h.cat_off - c0);
@@ -445,83 +593,73 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 const double2* xsin = P.xs_in + I.side;
                 auto own = [&](int ii) { return xsin[ii]; };
                 auto gath = [&](uint32_t ii) { const C t = __ldg(P.x_in + ii); return make_double2(t.x, t.y); };
-                const double2 gam = make_double2(P.gamma[p0 + j].x, P.gamma[p0 + j].y);
+                const double2 gam = make_double2(P.gamma[d.p0 + j].x, P.gamma[d.p0 + j].y);
                 const int loc = int(l) - pl;
-                const double2 k = var_rhs<double>(P, kind, q, r, G, S.cw + cb, S.cM + cb,
-                                                  S.rec + (h.rec_off - r0), h, I, gam, own, gath);
+                const double2 k = var_rhs<double>(P, kind, q, r, G, cwa + cb, cMa + cb, recs + (h.rec_off - r0), h, I,
+                                                  gam, own, gath);
                 const double dt = P.dt;
                 const int si = int(I.side) + loc;
                 if (P.stage < 0) {
                     P.xs_out[si] = k;
                     P.x_out[vg] = mk(T(k.x), T(k.y));
                 } else if (P.stage == 3) {
-                    const double2 ys = P.ys[si], as = P.accs[si];
-                    const double2 yn = make_double2(ys.x + dt / 6.0 * (as.x + k.x), ys.y + dt / 6.0 * (as.y + k.y));
+                    const double2 y6 = P.ys[si], a6 = P.accs[si];
+                    const double2 yn = make_double2(y6.x + dt / 6.0 * (a6.x + k.x), y6.y + dt / 6.0 * (a6.y + k.y));
                     P.ys_out[si] = yn;
                     P.y_out[vg] = mk(T(yn.x), T(yn.y));
                 } else {
-                    const double2 ys = P.ys[si];
-                    double2 as;
-                    if (P.stage == 0) as = k;
+                    const double2 y6 = P.ys[si];
+                    double2 a6;
+                    if (P.stage == 0) a6 = k;
                     else {
-                        as = P.accs[si];
-                        as.x += 2.0 * k.x;
-                        as.y += 2.0 * k.y;
+                        a6 = P.accs[si];
+                        a6.x += 2.0 * k.x;
+                        a6.y += 2.0 * k.y;
                     }
-                    P.accs[si] = as;
+                    P.accs[si] = a6;
                     const double a = P.stage == 2 ? dt : 0.5 * dt;
-                    const double2 xn = make_double2(ys.x + a * k.x, ys.y + a * k.y);
+                    const double2 xn = make_double2(y6.x + a * k.x, y6.y + a * k.y);
                     P.xs_out[si] = xn;
                     P.x_out[vg] = mk(T(xn.x), T(xn.y));
                 }
                 continue;
             }
-            // stream operands of the RK4 stage, issued before the derivative
-            C yv, av;
-            if (P.stage == 0) {
-                yv = S.x[l];
-            } else if (P.stage > 0) {
-                yv = P.y[vg];
-                av = P.acc[vg];
-            }
             const T g = sizeof(T) == 8 ? T(I.g) : T(I.gf);
             const T det = sizeof(T) == 8 ? T(I.detuning) : T(I.detf);
             const T kap = sizeof(T) == 8 ? T(I.kappa) : T(I.kappaf);
-            const C gam = __ldg(P.gamma + p0 + j);
-            const C v = S.x[l];
-            const C* xp = S.x + pl;
+            const C gam = __ldg(P.gamma + d.p0 + j);
+            const C v = xs[l];
+            const C* xp = xs + pl;
             // Hamiltonian, damping and loss (Eqs. HZ, HX and their Y, P, S, T
             // counterparts), with the grouped sums of phases 2 and 3
-            C d;
+            C dv;
             if (kind == KZ) {
-                const C zs = S.Zs[j];
-                d = mk(g * zs.y, -g * zs.x);
-                d = cfma(mk(-(gam.x + kap), -gam.y), v, d);
+                const C zs = W.Zs[j];
+                dv = mk(g * zs.y, -g * zs.x);
+                dv = cfma(mk(-(gam.x + kap), -gam.y), v, dv);
             } else if (kind == KX || kind == KY) {
                 const C Z = xp[0];
-                const C t = kind == KX ? csub(Z, S.R[cb + q - 1]) : csub(S.Cs[cb + q - 1], Z);
+                const C t = kind == KX ? csub(Z, W.R[cb + q - 1]) : csub(W.Cs[cb + q - 1], Z);
                 const T sd = kind == KX ? det : -det;
-                d = mk(sd * v.y + g * t.y, -sd * v.x - g * t.x);
-                d = cfma(mk(-(gam.x + T(0.5) * kap), -gam.y), v, d);
+                dv = mk(sd * v.y + g * t.y, -sd * v.x - g * t.x);
+                dv = cfma(mk(-(gam.x + T(0.5) * kap), -gam.y), v, dv);
             } else {
                 const C t = csub(xp[G + (kind == KS ? r : q)], xp[q]);
-                d = mk(g * t.y, -g * t.x);
-                d = cfma(mk(-gam.x, -gam.y), v, d);
+                dv = mk(g * t.y, -g * t.x);
+                dv = cfma(mk(-gam.x, -gam.y), v, dv);
             }
             // hierarchy terms (Eqs. uvar-up, uvar-down) from the decoded records
             // of the row category and of the column category
             const bool rowside = kind == KX || kind == KP || kind == KS || kind == KT;
             const bool colside = kind == KY || kind == KS || kind == KT;
-            const int rcat = q;                       // row category (moved on the row side)
-            const int ccat = kind == KS ? r : q;      // column category (moved on the column side)
-            const uint32_t wr = rowside ? S.cw[cb + rcat - 1] : 0u;
-            const uint32_t wc = colside ? S.cw[cb + ccat - 1] : 0u;
+            const int rcat = q;                     // row category (moved on the row side)
+            const int ccat = kind == KS ? r : q;    // column category (moved on the column side)
+            const uint32_t wr = rowside ? cwa[cb + rcat - 1] : 0u;
+            const uint32_t wc = colside ? cwa[cb + ccat - 1] : 0u;
             const int skip = kind == KP ? int((wr >> 20) & 15) : 0;  // P_q: lower records only
             const int nr = int((wr >> 10) & 31) - skip, nc = int((wc >> 10) & 31);
             const int rb = int(h.rec_off - r0);
             const int rr0 = rb + int(wr & 1023) + skip, rc0 = rb + int(wc & 1023);
-            const int colrow = q;                     // row category seen from the column side
-            const int rowcol = kind == KS ? r : q;    // column category seen from the row side
             const int ntot = nr + nc;
             for (int i0 = 0; i0 < ntot; i0 += 4) {
                 C val[4], cf[4];
@@ -533,54 +671,54 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                     if (ii < ntot) {
                         const bool isrow = ii < nr;
                         const int rx = isrow ? rr0 + ii : rc0 + ii - nr;
-                        const int4 A = S.dA[rx];
-                        const uint32_t sm = S.dS[rx];
+                        const int4 A = W.dA[rx];
+                        const uint32_t sm = W.dS[rx];
                         const int Gp = int(sm >> 18) & 31;
                         int idx;
                         if (isrow) {
                             if (kind == KX) idx = A.x;
                             else if (kind == KP) idx = A.x + 2 * Gp;
                             else {
-                                // S'[tau*, tau(b)] or T'[tau*], b = rowcol
+                                // S'[tau*, tau(c)] or T'[tau*]; c = r (S) or q (T)
                                 const int smerge = int(sm >> 12) & 63;
-                                const int b = rowcol;
-                                idx = A.y + b - (int(sm & 1u) && b > rcat ? 1 : 0) - (b > smerge ? 1 : 0);
-                                if (b == smerge) idx = A.w;
+                                const int cc = kind == KS ? r : q;
+                                idx = A.y + cc - ((sm & 1u) && cc > rcat ? 1 : 0) - (cc > smerge ? 1 : 0);
+                                if (cc == smerge) idx = A.w;
                             }
-                            cf[u] = S.crow[rx];
-                            if (kind == KP) cf[u] = cadd(cf[u], S.ccol[rx]);
+                            cf[u] = W.crow[rx];
+                            if (kind == KP) cf[u] = cadd(cf[u], W.ccol[rx]);
                         } else {
                             if (kind == KY) idx = A.x + Gp;
                             else {
-                                // S'[tau(a), tau*] or T'[tau*], a = colrow
-                                const int a = colrow;
+                                // S'[tau(q), tau*] or T'[tau*]
                                 const int ts = int(sm >> 7) & 31;
                                 const int ipos = int(sm >> 2) & 31;
-                                const int ta = a - ((sm & 1u) && a > ccat ? 1 : 0) + (((sm >> 1) & 1u) && a >= ipos ? 1 : 0);
+                                const int ta = q - ((sm & 1u) && q > ccat ? 1 : 0) +
+                                               (((sm >> 1) & 1u) && q >= ipos ? 1 : 0);
                                 idx = (ta == ts) ? A.w : A.z + (ta - 1) * (Gp - 1) - (ts > ta ? 1 : 0);
                             }
-                            cf[u] = S.ccol[rx];
+                            cf[u] = W.ccol[rx];
                         }
                         val[u] = __ldg(P.x_in + idx);
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) d = cfma(cf[u], val[u], d);
+                for (int u = 0; u < 4; ++u) dv = cfma(cf[u], val[u], dv);
             }
-            const C k = d;
             if (P.stage < 0) {
-                P.x_out[vg] = k;
+                P.x_out[vg] = dv;
             } else if (P.stage == 0) {
-                P.acc[vg] = k;
-                P.x_out[vg] = caxpy(aT, k, yv);
+                P.acc[vg] = dv;
+                P.x_out[vg] = caxpy(aT, dv, v);  // x_in is y in the first stage
             } else if (P.stage == 3) {
-                P.y_out[vg] = caxpy(dtT / T(6), cadd(av, k), yv);
+                P.y_out[vg] = caxpy(dtT / T(6), cadd(as[l], dv), ys[l]);
             } else {
-                P.acc[vg] = caxpy(T(2), k, av);
-                P.x_out[vg] = caxpy(aT, k, yv);
+                P.acc[vg] = caxpy(T(2), dv, as[l]);
+                P.x_out[vg] = caxpy(aT, dv, ys[l]);
             }
         }
         __syncthreads();
+        b ^= 1;
     }
 }
 
@@ -632,21 +770,14 @@ __global__ void init_rho0_kernel(const InstDev* __restrict__ inst, int ninst, co
 
 // ---- host launch wrappers (called from api.cu) -----------------------------
 
-size_t stage_smem_bytes(int chunk, int rec_cap, bool fp64) {
-    const size_t cs = fp64 ? 16 : 8, ts = fp64 ? 8 : 4;
-    const size_t ncat = size_t(chunk) / 4 + 8;
-    size_t b = cs * (size_t(chunk) + 2 * ncat + kMaxPatPerChunk + 2 * size_t(rec_cap));
-    b += (sizeof(int4) + sizeof(uint2) + sizeof(uint32_t)) * size_t(rec_cap);
-    b += sizeof(PatHdr) * (kMaxPatPerChunk + 1);
-    b += sizeof(uint32_t) * (ncat + size_t(chunk));
-    b += ts * ncat;
-    b += 2 * sizeof(uint16_t) * kMaxPatPerChunk;
-    return (b + 15) / 16 * 16 + 16;
+size_t stage_smem_bytes(int chunk, int rec_cap, int cat_cap, bool fp64) {
+    if (fp64) return 2 * buf_bytes<double>(chunk, rec_cap, cat_cap) + work_bytes<double>(chunk, rec_cap, cat_cap);
+    return 2 * buf_bytes<float>(chunk, rec_cap, cat_cap) + work_bytes<float>(chunk, rec_cap, cat_cap);
 }
 
 template <typename T, bool SIDE>
 static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, cudaStream_t st) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.rec_cap, sizeof(T) == 8);
+    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.rec_cap, cfg.cat_cap, sizeof(T) == 8);
     stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     return cudaGetLastError();
 }
@@ -660,7 +791,7 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.cat_M = static_cast<const T*>(s.cat_M);
     p.gamma = static_cast<const C*>(s.gamma);
     p.rec = static_cast<const Record*>(s.rec);
-    p.chunk_begin = static_cast<const uint32_t*>(s.chunk_begin);
+    p.desc = static_cast<const ChunkDesc*>(s.desc);
     p.inst = static_cast<const InstDev*>(s.inst);
     p.coef_row = static_cast<const C*>(s.coef_row);
     p.coef_col = static_cast<const C*>(s.coef_col);
@@ -672,6 +803,7 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.nchunks = s.nchunks;
     p.chunk = cfg.chunk;
     p.rec_cap = cfg.rec_cap;
+    p.cat_cap = cfg.cat_cap;
     p.x_in = static_cast<const C*>(s.x_in);
     p.x_out = static_cast<C*>(s.x_out);
     p.y = static_cast<const C*>(s.y);
@@ -686,6 +818,7 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.stage = s.stage;
     p.use_queue = cfg.use_queue;
     p.queue = s.queue;
+    p.err = s.err;
     return p;
 }
 
@@ -697,13 +830,12 @@ cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, 
 // Sets the dynamic shared-memory limit once for the largest chunk (outside
 // any stream capture) and returns the CTAs per SM for this configuration.
 cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.rec_cap, fp64);
+    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.rec_cap, cfg.cat_cap, fp64);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     // leave room for the kernel's static shared variables
-    const int lim = int(std::min<size_t>(stage_smem_bytes(kMaxChunkVars, kMaxChunkVars * 4, fp64),
-                                         size_t(std::max(optin - 1024, 0))));
+    const int lim = std::max(optin - 1024, 0);
     if (sm > size_t(lim)) {
         *blocks_per_sm = 0;
         return cudaSuccess;

@@ -104,6 +104,13 @@ struct HostInstance {
     std::vector<double> coef_row, coef_col;  // 2 * kCoefPerInst each
 };
 
+// one work item of the stage kernel: a run of consecutive patterns and the
+// ranges of their variables, categories and records (32 bytes, so that the
+// kernel's producer thread reads it with one load)
+struct ChunkDesc {
+    uint32_t p0, np, v0, nv, c0, ncat, r0, nrec;
+};
+
 // launch description shared by api.cu and kernels.cu (type-erased pointers)
 struct LaunchCfg {
     int block;      // threads per CTA
@@ -111,16 +118,17 @@ struct LaunchCfg {
     int use_queue;  // 1: persistent grid + atomic work queue
     int grid;       // CTAs
     int rec_cap;    // most connection records in one work item
+    int cat_cap;    // most categories in one work item
 };
 struct StageLaunch {
     const void* hdr; const void* cat_word; const void* cat_M; const void* gamma; const void* rec;
-    const void* chunk_begin; const void* inst; const void* coef_row; const void* coef_col;
+    const void* desc; const void* inst; const void* coef_row; const void* coef_col;
     const void* cat_Md; const void* coef_row_d; const void* coef_col_d;
     const void* lut; const void* lut_off;
     uint32_t nchunks;
     const void* x_in; void* x_out; const void* y; void* acc; void* y_out;
     const void* xs_in; void* xs_out; const void* ys; void* accs; void* ys_out;
-    double dt; int stage; unsigned int* queue;
+    double dt; int stage; unsigned int* queue; unsigned int* err;
 };
 
 // builder.cpp
