@@ -240,9 +240,10 @@ int sa_heom_propagate(sa_heom* h, void* d_state, double dt, int64_t nsteps, int6
 int sa_heom_observables(sa_heom* h, const void* d_state, double* out, void* stream);
 
 /*
- * Launch tuning.  block: threads per CTA (64..1024, multiple of 32);
- * chunk: variables per work item (>= largest pattern, <= 2048); queue: 1 for
- * the dynamic work queue, 0 for a static strided assignment.  Any argument
+ * Launch tuning.  block: threads per CTA (64..256, multiple of 32);
+ * chunk: variables per warp work item (>= largest pattern, <= 1024, multiple
+ * of 32); queue: 1 for the dynamic work queue over a persistent grid, 0 for
+ * one work item per warp.  Any argument
  * <= 0 keeps its current value.  sa_heom_autotune times a few candidates of
  * the RK4 stage kernel on d_state (which it leaves changed) and keeps the
  * fastest; best[3] receives block, chunk, queue.

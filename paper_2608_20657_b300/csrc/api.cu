@@ -77,17 +77,20 @@ struct sa_heom {
     std::vector<float> coef_row_f, coef_col_f;
     std::vector<uint16_t> lut;
     std::vector<uint32_t> lut_off;
-    std::vector<ChunkDesc> chunks;
+    std::vector<ItemDesc> items;
+    std::vector<uint32_t> vdesc;
+    std::vector<DRecA> drecA;
+    std::vector<uint32_t> drecS;
     int max_u = 0;
-    int rec_cap = 8, cat_cap = 8;
     // tuning
-    int block = 256, chunk = 1024, use_queue = 1;
+    int block = 256, chunk = 128, use_queue = 1;
     // device
     int device = -1, num_sms = 0;
     void *d_hdr = nullptr, *d_cat_word = nullptr, *d_catM = nullptr, *d_catMd = nullptr, *d_gamma = nullptr;
     void *d_rec = nullptr, *d_inst = nullptr, *d_theta = nullptr, *d_coef_row = nullptr, *d_coef_col = nullptr;
     void *d_coef_row_d = nullptr, *d_coef_col_d = nullptr, *d_lut = nullptr, *d_lut_off = nullptr;
     void* d_chunk = nullptr;
+    void *d_vdesc = nullptr, *d_drecA = nullptr, *d_drecS = nullptr;
     unsigned int* d_err = nullptr;
     void* d_work[3] = {nullptr, nullptr, nullptr};  // acc, xa, xb
     unsigned int* d_queue = nullptr;
@@ -97,7 +100,7 @@ struct sa_heom {
     double* d_rho0 = nullptr;
     cudaStream_t cap = nullptr;
     size_t state_bytes = 0, side_off = 0;
-    LaunchCfg cfg{256, 1024, 1, 1, 8, 8};
+    LaunchCfg cfg{256, 128, 1, 1};
     std::map<std::tuple<const void*, uint64_t, int64_t>, cudaGraphExec_t> graphs;
 };
 
@@ -127,14 +130,16 @@ void build_lut(sa_heom* h) {
     h->lut_off[kMaxG + 1] = uint32_t(h->lut.size());
 }
 
-// Work items: runs of consecutive patterns with at most `chunk` variables and
-// kMaxPatPerChunk patterns, with the ranges the stage kernel stages.
-void build_chunks(sa_heom* h) {
+// Work items (one warp each): runs of consecutive patterns with at most
+// `chunk` variables and kItemPats patterns.  vdesc gives each item's
+// variables in the order the warp's lanes take them -- S first, then T, P, X,
+// Y, Z, every kind in memory order -- with their local index and (kind, q, r).
+void build_items(sa_heom* h) {
     std::vector<uint32_t> begin{0};
     int64_t vars = 0, pats = 0;
     for (int64_t p = 0; p < h->npat; ++p) {
         int64_t u = int64_t(h->hdr[p + 1].var_off) - int64_t(h->hdr[p].var_off);
-        if (pats > 0 && (vars + u > h->chunk || pats >= kMaxPatPerChunk)) {
+        if (pats > 0 && (vars + u > h->chunk || pats >= kItemPats)) {
             begin.push_back(uint32_t(p));
             vars = 0;
             pats = 0;
@@ -143,44 +148,87 @@ void build_chunks(sa_heom* h) {
         ++pats;
     }
     begin.push_back(uint32_t(h->npat));
-    h->chunks.clear();
-    uint32_t rcap = 8, ccap = 8;
+    h->items.clear();
+    h->vdesc.assign(size_t(h->nvar), 0u);
     for (size_t c = 0; c + 1 < begin.size(); ++c) {
         const PatHdr &a = h->hdr[begin[c]], &b = h->hdr[begin[c + 1]];
-        ChunkDesc d;
+        ItemDesc d{};
         d.p0 = begin[c];
         d.np = begin[c + 1] - begin[c];
         d.v0 = a.var_off;
         d.nv = b.var_off - a.var_off;
         d.c0 = a.cat_off;
         d.ncat = b.cat_off - a.cat_off;
-        d.r0 = a.rec_off;
-        d.nrec = b.rec_off - a.rec_off;
-        rcap = std::max(rcap, d.nrec);
-        ccap = std::max(ccap, d.ncat);
-        h->chunks.push_back(d);
+        h->items.push_back(d);
+        uint32_t* out = &h->vdesc[d.v0];
+        auto put = [&](uint32_t l, uint32_t j, uint32_t kind, uint32_t q, uint32_t r) {
+            *out++ = l | (j << 10) | (kind << 15) | (q << 18) | (r << 23);
+        };
+        for (uint32_t j = 0; j < d.np; ++j) {  // S
+            const PatHdr& H = h->hdr[d.p0 + j];
+            const int G = H.G;
+            for (int q = 1; q <= G; ++q)
+                for (int r = 1; r <= G; ++r)
+                    if (r != q) put(uint32_t(H.var_off - d.v0 + loc_S(G, q, r)), j, 4, q, r);
+        }
+        for (uint32_t j = 0; j < d.np; ++j) {  // T
+            const PatHdr& H = h->hdr[d.p0 + j];
+            for (int q = 1; q <= H.G; ++q) {
+                const int tr = (h->cat_word[H.cat_off + q - 1] >> 15) & 31;
+                if (tr != 31) put(uint32_t(H.var_off - d.v0 + loc_T(H.G, tr)), j, 5, q, 0);
+            }
+        }
+        for (int kind : {3, 1, 2}) {  // P, X, Y
+            for (uint32_t j = 0; j < d.np; ++j) {
+                const PatHdr& H = h->hdr[d.p0 + j];
+                for (int q = 1; q <= H.G; ++q) {
+                    const int64_t loc = kind == 3 ? loc_P(H.G, q) : (kind == 1 ? loc_X(H.G, q) : loc_Y(H.G, q));
+                    put(uint32_t(H.var_off - d.v0 + loc), j, kind, q, 0);
+                }
+            }
+        }
+        for (uint32_t j = 0; j < d.np; ++j) put(h->hdr[d.p0 + j].var_off - d.v0, j, 0, 0, 0);  // Z
     }
-    h->rec_cap = int((rcap + 7) / 8 * 8);
-    h->cat_cap = int((ccap + 7) / 8 * 8);
+}
+
+// Decoded connection records: the batch-global indices the aligned accessor
+// resolves to for each kind of variable, and the small remap fields.
+void decode_records(sa_heom* h) {
+    h->drecA.resize(h->rec.size());
+    h->drecS.resize(h->rec.size());
+    for (size_t i = 0; i < h->rec.size(); ++i) {
+        const Record& R = h->rec[i];
+        const uint32_t pk = R.packed;
+        const int ts = pk & 31, Gp = (pk >> 5) & 31, tr = (pk >> 10) & 31;
+        const int ipos = (pk >> 16) & 31, ins = (pk >> 21) & 1, del = (pk >> 22) & 1;
+        const int cid = int(pk >> 23);
+        const int smerge = ins ? 63 : ipos;
+        const int t = int(R.target);
+        h->drecA[i] = {t + ts, t + 3 * Gp + (ts - 1) * (Gp - 1), t + 3 * Gp + ts, t + (Gp + 1) * (Gp + 1) + tr};
+        h->drecS[i] = uint32_t(del) | (uint32_t(ins) << 1) | (uint32_t(ipos) << 2) | (uint32_t(ts) << 7) |
+                      (uint32_t(smerge) << 12) | (uint32_t(Gp) << 18) | (uint32_t(cid) << 23);
+    }
 }
 
 int apply_tuning(sa_heom* h) {
-    build_chunks(h);
+    build_items(h);
     h->cfg.block = h->block;
     h->cfg.chunk = h->chunk;
     h->cfg.use_queue = h->use_queue;
-    h->cfg.rec_cap = h->rec_cap;
-    h->cfg.cat_cap = h->cat_cap;
-    const uint32_t nchunks = uint32_t(h->chunks.size());
+    const uint32_t nchunks = uint32_t(h->items.size());
     if (h->host_only) return SA_OK;
     if (h->d_chunk) cudaFree(h->d_chunk);
-    h->d_chunk = nullptr;
-    int rc = upload(&h->d_chunk, h->chunks);
+    if (h->d_vdesc) cudaFree(h->d_vdesc);
+    h->d_chunk = h->d_vdesc = nullptr;
+    int rc = upload(&h->d_chunk, h->items);
+    if (!rc) rc = upload(&h->d_vdesc, h->vdesc);
     if (rc) return rc;
     int occ = 0;
     CK(stage_occupancy(h->cfg, h->precision == SA_FP64, &occ));
     if (occ < 1) return fail(SA_ERR_UNSUPPORTED, "stage kernel does not fit on an SM with this tuning (shared memory)");
-    h->cfg.grid = h->use_queue ? int(std::min<int64_t>(int64_t(h->num_sms) * occ, nchunks)) : int(nchunks);
+    const int wpb = h->block / 32;
+    const int64_t blocks_needed = (int64_t(nchunks) + wpb - 1) / wpb;
+    h->cfg.grid = h->use_queue ? int(std::min<int64_t>(int64_t(h->num_sms) * occ, blocks_needed)) : int(blocks_needed);
     if (h->cfg.grid < 1) h->cfg.grid = 1;
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
@@ -193,7 +241,7 @@ void free_device(sa_heom* h) {
     void* ptrs[] = {h->d_hdr, h->d_cat_word, h->d_catM, h->d_catMd, h->d_gamma, h->d_rec, h->d_inst, h->d_theta,
                     h->d_coef_row, h->d_coef_col, h->d_coef_row_d, h->d_coef_col_d, h->d_lut, h->d_lut_off,
                     h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0,
-                    h->d_err};
+                    h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -217,7 +265,10 @@ StageLaunch base_launch(const sa_heom* h) {
     s.cat_M = h->d_catM;
     s.gamma = h->d_gamma;
     s.rec = h->d_rec;
-    s.desc = h->d_chunk;
+    s.items = h->d_chunk;
+    s.vdesc = h->d_vdesc;
+    s.drecA = h->d_drecA;
+    s.drecS = h->d_drecS;
     s.inst = h->d_inst;
     s.coef_row = h->d_coef_row;
     s.coef_col = h->d_coef_col;
@@ -226,7 +277,7 @@ StageLaunch base_launch(const sa_heom* h) {
     s.coef_col_d = h->d_coef_col_d;
     s.lut = h->d_lut;
     s.lut_off = h->d_lut_off;
-    s.nchunks = uint32_t(h->chunks.size());
+    s.nchunks = uint32_t(h->items.size());
     s.err = h->d_err;
     return s;
 }
@@ -357,7 +408,7 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
         h->nrec += int64_t(hi.rec.size());
     }
     h->nvar = int64_t(h->var_begin[count]);
-    if (h->nvar >= (int64_t(1) << 32) || h->nrec >= (int64_t(1) << 32) || h->ncat >= (int64_t(1) << 32)) {
+    if (h->nvar >= (int64_t(1) << 31) || h->nrec >= (int64_t(1) << 32) || h->ncat >= (int64_t(1) << 32)) {
         delete h;
         return fail(SA_ERR_UNSUPPORTED, "batch exceeds 32-bit table indices");
     }
@@ -425,7 +476,12 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     h->coef_row_f.assign(h->coef_row_d.begin(), h->coef_row_d.end());
     h->coef_col_f.assign(h->coef_col_d.begin(), h->coef_col_d.end());
     build_lut(h);
-    h->chunk = std::max(1024, (h->max_u + 31) / 32 * 32);
+    h->chunk = std::max(128, (h->max_u + 31) / 32 * 32);
+    if (h->chunk > kMaxItemVars) {
+        delete h;
+        return fail(SA_ERR_UNSUPPORTED, "a pattern has more than 1024 unique variables");
+    }
+    decode_records(h);
     // state layout
     if (precision == SA_FP64) {
         h->state_bytes = (size_t(h->nvar) * 16 + 255) / 256 * 256;
@@ -435,7 +491,7 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
         h->state_bytes = h->side_off + size_t(count) * kSideSlots * 16;
     }
     if (h->host_only) {
-        build_chunks(h);
+        build_items(h);
         *out = h;
         return SA_OK;
     }
@@ -463,6 +519,8 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     if (!rc) rc = upload(&h->d_coef_row_d, h->coef_row_d);
     if (!rc) rc = upload(&h->d_coef_col_d, h->coef_col_d);
     if (!rc) rc = upload(&h->d_lut, h->lut);
+    if (!rc) rc = upload(&h->d_drecA, h->drecA);
+    if (!rc) rc = upload(&h->d_drecS, h->drecS);
     if (!rc) rc = upload(&h->d_lut_off, h->lut_off);
     for (int w = 0; w < 3 && !rc; ++w) {
         e = cudaMalloc(&h->d_work[w], h->state_bytes);
@@ -490,9 +548,9 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     h->host_only = false;
     if (!rc) {
         rc = apply_tuning(h);
-        // large m: shrink the work item until its shared-memory image fits
-        while (rc == SA_ERR_UNSUPPORTED && h->chunk / 2 >= h->max_u && h->chunk / 2 >= 64) {
-            h->chunk = (h->chunk / 2 + 31) / 32 * 32;
+        // large items: fewer warps per block until the shared-memory image fits
+        while (rc == SA_ERR_UNSUPPORTED && h->block > 64) {
+            h->block /= 2;
             rc = apply_tuning(h);
         }
     }
@@ -799,8 +857,8 @@ int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue) {
     int nc = chunk > 0 ? chunk : h->chunk;
     int nq = queue >= 0 ? queue : h->use_queue;
     if (nb < 64 || nb > 256 || nb % 32) return fail(SA_ERR_INVALID_ARG, "block must be 64..256, multiple of 32");
-    if (nc % 32 || nc < h->max_u || nc > kMaxChunkVars)
-        return fail(SA_ERR_INVALID_ARG, "chunk must be a multiple of 32 between the largest pattern and 2048");
+    if (nc % 32 || nc < h->max_u || nc > kMaxItemVars)
+        return fail(SA_ERR_INVALID_ARG, "chunk must be a multiple of 32 between the largest pattern and 1024");
     h->block = nb;
     h->chunk = nc;
     h->use_queue = nq ? 1 : 0;
@@ -813,8 +871,9 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     if (!d_state) return fail(SA_ERR_INVALID_ARG, "d_state required");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int blocks[] = {128, 256};
-    const int chunks[] = {512, 1024, 2048};
-    // (chunks above the shared-memory budget are skipped by set_tuning)
+    const int chunks[] = {64, 96, 128, 192, 256};
+    // (items smaller than the largest pattern or above the shared-memory
+    // budget are skipped by set_tuning)
     float best_ms = 1e30f;
     int bb = h->block, bc = h->chunk, bq = h->use_queue;
     cudaEvent_t e0, e1;

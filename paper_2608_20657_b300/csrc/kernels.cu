@@ -68,7 +68,10 @@ template <typename T> struct StageParams {
     const T* __restrict__ cat_M;
     const C* __restrict__ gamma;
     const Record* __restrict__ rec;
-    const ChunkDesc* __restrict__ desc;    // nchunks work items
+    const ItemDesc* __restrict__ items;    // nchunks work items
+    const uint32_t* __restrict__ vdesc;    // per variable: item-local order and (kind, q, r)
+    const int4* __restrict__ drecA;        // decoded records: X'-index, S'-row base, S'-column base, T'-index
+    const uint32_t* __restrict__ drecS;    // decoded records: small fields and coefficient id
     const InstDev* __restrict__ inst;
     const C* __restrict__ coef_row;
     const C* __restrict__ coef_col;
@@ -78,9 +81,7 @@ template <typename T> struct StageParams {
     const uint16_t* __restrict__ lut;       // (kind | q << 3 | r << 8) per (G, local index)
     const uint32_t* __restrict__ lut_off;   // per G
     uint32_t nchunks;
-    int chunk;                              // variable capacity of the staged slice
-    int rec_cap;                            // record capacity of the staged slice
-    int cat_cap;                            // category capacity of the staged slice
+    int chunk;                              // variable capacity of one work item
     const C* x_in;                          // stage input (gathered)
     C* x_out;                               // next stage input, or dR/dt (stage -1)
     const C* y;                             // state at the start of the step
@@ -230,360 +231,140 @@ __device__ __forceinline__ typename Cx<A>::t var_rhs(const StageParams<T>& P, in
     return d;
 }
 
-// ---- TMA bulk copies and mbarriers (inline PTX) ----------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait: about a second of SM clocks, then report failure
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > (2LL << 30)) return false;
-    return true;
-}
-
-// A bulk copy must start on a 16-byte boundary and cover a multiple of 16
-// bytes: copy the enclosing aligned element range and remember how many
-// elements precede the first wanted one.  Tables and state buffers are
-// padded so that the rounded range stays inside the allocation.
-struct Span {
-    const char* src;
-    uint32_t bytes;
-    uint32_t skip;
-};
-__device__ __forceinline__ Span span(const void* base, uint32_t start, uint32_t count, uint32_t esz) {
-    const uint32_t per = esz >= 16 ? 1u : 16u / esz;
-    const uint32_t a = start - start % per;
-    const uint32_t e = (start + count + per - 1) / per * per;
-    Span sp;
-    sp.src = static_cast<const char*>(base) + size_t(a) * esz;
-    sp.bytes = count ? (e - a) * esz : 0u;
-    sp.skip = start - a;
-    return sp;
-}
-
-// Shared-memory image of one work item (double-buffered staging area plus
-// the per-item work arrays).
-template <typename T> struct StageBuf {
+// Per-warp shared-memory image of one work item.
+template <typename T> struct WarpSmem {
     using C = typename Cx<T>::t;
-    PatHdr* hdr;
-    C* x;
-    C* y;
-    C* acc;
-    uint2* rec;
+    C* x;        // stage input slice
+    C* y;        // RK4 state slice
+    C* acc;      // RK4 accumulator slice
+    C* R;        // grouped row sums R_q per category (Eq. grouped-row-sum)
+    C* Cs;       // grouped column sums C_q per category (Eq. grouped-column-sum)
+    C* Zs;       // sum_q M_q (X_q - Y_q) per pattern (Eq. HZ)
+    C* gam;      // Gamma_Lambda per pattern
+    PatHdr* ph;  // pattern headers (kItemPats + 1)
     uint32_t* cw;
     T* cM;
-};
-template <typename T> struct StageWork {
-    using C = typename Cx<T>::t;
-    C* R;            // grouped row sums R_q per category
-    C* Cs;           // grouped column sums C_q per category
-    C* Zs;           // sum_q M_q (X_q - Y_q) per pattern
-    C* crow;         // decoded record: row coefficient
-    C* ccol;         // decoded record: column coefficient
-    int4* dA;        // decoded record: X'-index, S'-row base, S'-column base, T'-index
-    uint32_t* dS;    // decoded record: small fields
-    uint32_t* perm;  // work order: l | j << 11 | kind << 19 | q << 22 | r << 27
-    uint16_t* sb;
-    uint16_t* ob;
 };
 
 __host__ __device__ __forceinline__ size_t al16(size_t b) { return (b + 15) / 16 * 16; }
 
 template <typename T>
-__host__ __device__ __forceinline__ size_t buf_bytes(int chunk, int rec_cap, int cat_cap) {
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int item) {
     const size_t cs = 2 * sizeof(T);
-    return al16(sizeof(PatHdr) * (kMaxPatPerChunk + 1)) + 3 * al16(cs * (chunk + 4)) + al16(8 * (rec_cap + 4)) +
-           al16(4 * (cat_cap + 8)) + al16(sizeof(T) * (cat_cap + 8));
-}
-template <typename T>
-__host__ __device__ __forceinline__ size_t work_bytes(int chunk, int rec_cap, int cat_cap) {
-    const size_t cs = 2 * sizeof(T);
-    return 2 * al16(cs * cat_cap) + al16(cs * kMaxPatPerChunk) + 2 * al16(cs * rec_cap) + al16(16 * rec_cap) +
-           al16(4 * rec_cap) + al16(4 * chunk) + 2 * al16(2 * kMaxPatPerChunk);
+    const size_t nc = size_t(item) / 4 + 8;
+    return 3 * al16(cs * item) + 2 * al16(cs * nc) + 2 * al16(cs * kItemPats) + al16(sizeof(PatHdr) * (kItemPats + 1)) +
+           al16(4 * nc) + al16(sizeof(T) * nc);
 }
 
 template <typename T>
-__device__ __forceinline__ StageBuf<T> carve_buf(unsigned char* p, int chunk, int rec_cap, int cat_cap) {
+__device__ __forceinline__ WarpSmem<T> carve_warp(unsigned char* p, int item) {
     using C = typename Cx<T>::t;
-    StageBuf<T> B;
-    B.hdr = reinterpret_cast<PatHdr*>(p); p += al16(sizeof(PatHdr) * (kMaxPatPerChunk + 1));
-    B.x = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * (chunk + 4));
-    B.y = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * (chunk + 4));
-    B.acc = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * (chunk + 4));
-    B.rec = reinterpret_cast<uint2*>(p);  p += al16(8 * (rec_cap + 4));
-    B.cw = reinterpret_cast<uint32_t*>(p); p += al16(4 * (cat_cap + 8));
-    B.cM = reinterpret_cast<T*>(p);
-    return B;
-}
-template <typename T>
-__device__ __forceinline__ StageWork<T> carve_work(unsigned char* p, int chunk, int rec_cap, int cat_cap) {
-    using C = typename Cx<T>::t;
-    StageWork<T> W;
-    W.R = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * cat_cap);
-    W.Cs = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * cat_cap);
-    W.Zs = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * kMaxPatPerChunk);
-    W.crow = reinterpret_cast<C*>(p);    p += al16(sizeof(C) * rec_cap);
-    W.ccol = reinterpret_cast<C*>(p);    p += al16(sizeof(C) * rec_cap);
-    W.dA = reinterpret_cast<int4*>(p);   p += al16(16 * rec_cap);
-    W.dS = reinterpret_cast<uint32_t*>(p); p += al16(4 * rec_cap);
-    W.perm = reinterpret_cast<uint32_t*>(p); p += al16(4 * chunk);
-    W.sb = reinterpret_cast<uint16_t*>(p); p += al16(2 * kMaxPatPerChunk);
-    W.ob = reinterpret_cast<uint16_t*>(p);
+    const int nc = item / 4 + 8;
+    WarpSmem<T> W;
+    W.x = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * item);
+    W.y = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * item);
+    W.acc = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * item);
+    W.R = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * nc);
+    W.Cs = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * nc);
+    W.Zs = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * kItemPats);
+    W.gam = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * kItemPats);
+    W.ph = reinterpret_cast<PatHdr*>(p);  p += al16(sizeof(PatHdr) * (kItemPats + 1));
+    W.cw = reinterpret_cast<uint32_t*>(p); p += al16(4 * nc);
+    W.cM = reinterpret_cast<T*>(p);
     return W;
 }
 
-// element offsets of the staged slices inside a buffer (the "skip" of each span)
-struct Skips {
-    uint32_t x, y, acc, rec, cw, cM;
-};
-
-// Issue the bulk copies of work item d into buffer B (one thread).
-template <typename T>
-__device__ __forceinline__ Skips issue_item(const StageParams<T>& P, const ChunkDesc& d, const StageBuf<T>& B,
-                                            uint64_t* bar) {
-    using C = typename Cx<T>::t;
-    const uint32_t cs = sizeof(C);
-    const Span sh = span(P.hdr, d.p0, d.np + 1, sizeof(PatHdr));
-    const Span sx = span(P.x_in, d.v0, d.nv, cs);
-    const bool want_y = P.stage > 0, want_acc = P.stage > 0;
-    const Span sy = span(P.y, d.v0, want_y ? d.nv : 0u, cs);
-    const Span sa = span(P.acc, d.v0, want_acc ? d.nv : 0u, cs);
-    const Span sr = span(P.rec, d.r0, d.nrec, 8);
-    const Span sw = span(P.cat_word, d.c0, d.ncat, 4);
-    const Span sm = span(P.cat_M, d.c0, d.ncat, sizeof(T));
-    mbar_expect_tx(bar, sh.bytes + sx.bytes + sy.bytes + sa.bytes + sr.bytes + sw.bytes + sm.bytes);
-    bulk_g2s(B.hdr, sh.src, sh.bytes, bar);
-    if (sx.bytes) bulk_g2s(B.x, sx.src, sx.bytes, bar);
-    if (sy.bytes) bulk_g2s(B.y, sy.src, sy.bytes, bar);
-    if (sa.bytes) bulk_g2s(B.acc, sa.src, sa.bytes, bar);
-    if (sr.bytes) bulk_g2s(B.rec, sr.src, sr.bytes, bar);
-    if (sw.bytes) bulk_g2s(B.cw, sw.src, sw.bytes, bar);
-    if (sm.bytes) bulk_g2s(B.cM, sm.src, sm.bytes, bar);
-    return Skips{sx.skip, sy.skip, sa.skip, sr.skip, sw.skip, sm.skip};
-}
-
+// One warp per work item (a run of consecutive patterns, at most `item`
+// variables and kItemPats patterns), with no block-wide barrier: the warp
+// stages its slices, forms the grouped sums, then each lane takes one
+// variable at a time in the host-made order (S variables first, then T, P,
+// X, Y, Z, so that the lanes of a warp run the same code path).
 template <typename T, bool FP64SIDE>
 __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem[];
-    const size_t bb = buf_bytes<T>(P.chunk, P.rec_cap, P.cat_cap);
-    auto buf = [&](int which) { return carve_buf<T>(smem + (which ? bb : 0), P.chunk, P.rec_cap, P.cat_cap); };
-    const StageWork<T> W = carve_work<T>(smem + 2 * bb, P.chunk, P.rec_cap, P.cat_cap);
-    __shared__ __align__(8) uint64_t s_bar[2];
-    __shared__ ChunkDesc s_desc[2];
-    __shared__ Skips s_skip[2];
-    __shared__ unsigned int s_item[2], s_nS;
-
-    const int tid = threadIdx.x;
-    const int producer = blockDim.x - 32;  // lane 0 of the last warp issues the copies
-    unsigned int iter = 0;
-    auto next_item = [&]() -> unsigned int {
-        if (P.use_queue) return atomicAdd(P.queue, 1u);
-        return blockIdx.x + (iter++) * gridDim.x;
-    };
-    if (tid == producer) {
-        mbar_init(&s_bar[0], 1);
-        mbar_init(&s_bar[1], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const unsigned int c = next_item();
-        s_item[0] = c;
-        if (c < P.nchunks) {
-            const ChunkDesc d = P.desc[c];
-            s_desc[0] = d;
-            s_skip[0] = issue_item(P, d, buf(0), &s_bar[0]);
-        }
-    }
-    __syncthreads();
-
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const WarpSmem<T> S = carve_warp<T>(smem + size_t(wib) * warp_smem_bytes<T>(P.chunk), P.chunk);
+    const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
+    unsigned int it = blockIdx.x * (blockDim.x >> 5) + wib;
     const T dtT = T(P.dt);
     const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
-    uint32_t parity0 = 0, parity1 = 0;
-    int b = 0;
     for (;;) {
-        const unsigned int c = s_item[b];
-        if (c >= P.nchunks) break;
-        // prefetch the next work item into the other buffer
-        if (tid == producer) {
-            const unsigned int c2 = next_item();
-            s_item[b ^ 1] = c2;
-            if (c2 < P.nchunks) {
-                const ChunkDesc d2 = P.desc[c2];
-                s_desc[b ^ 1] = d2;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                s_skip[b ^ 1] = issue_item(P, d2, buf(b ^ 1), &s_bar[b ^ 1]);
-            }
-        }
-        const uint32_t par = b ? parity1 : parity0;
-        if (!mbar_wait(&s_bar[b], par)) {
-            // report, let a prefetch already in flight land (bounded), leave
-            atomicOr(P.err, 1u);
-            if (s_item[b ^ 1] < P.nchunks) mbar_wait(&s_bar[b ^ 1], b ? parity0 : parity1);
-            return;
-        }
-        if (b) parity1 ^= 1u;
-        else parity0 ^= 1u;
-
-        const StageBuf<T> B = buf(b);
-        const ChunkDesc d = s_desc[b];
-        const Skips sk = s_skip[b];
-        const int np = int(d.np);
-        const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0, ncat = d.ncat, r0 = d.r0;
-        const PatHdr* hdr = B.hdr;
-        const C* xs = B.x + sk.x;
-        const uint2* recs = B.rec + sk.rec;
-        const uint32_t* cwa = B.cw + sk.cw;
-        const T* cMa = B.cM + sk.cM;
-        // ---- phase 2: warp 0 scans the work-order counts; the other threads
-        // take the categories: grouped sums R_q, C_q (Eqs. grouped-row-sum,
-        // grouped-column-sum) and the decoding of the category's records
-        if (tid < 32) {
-            const int lane = tid;
-            const int per = (np + 31) / 32;
-            const int a = lane * per, e = min(np, a + per);
-            int ss = 0, so = 0;
-            for (int j = a; j < e; ++j) {
-                const int G = hdr[j].G;
-                const int u = int(hdr[j + 1].var_off - hdr[j].var_off);
-                ss += G * (G - 1);
-                so += u - G * (G - 1);
-            }
-            int is = ss, io = so;
-            for (int off = 1; off < 32; off <<= 1) {
-                const int t1 = __shfl_up_sync(0xffffffffu, is, off);
-                const int t2 = __shfl_up_sync(0xffffffffu, io, off);
-                if (lane >= off) {
-                    is += t1;
-                    io += t2;
-                }
-            }
-            int bs = is - ss, bo = io - so;
-            for (int j = a; j < e; ++j) {
-                const int G = hdr[j].G;
-                const int u = int(hdr[j + 1].var_off - hdr[j].var_off);
-                W.sb[j] = uint16_t(bs);
-                W.ob[j] = uint16_t(bo);
-                bs += G * (G - 1);
-                bo += u - G * (G - 1);
-            }
-            if (lane == 31) s_nS = uint32_t(is);
+        unsigned int c;
+        if (P.use_queue) {
+            unsigned int t = 0;
+            if (lane == 0) t = atomicAdd(P.queue, 1u);
+            c = __shfl_sync(0xffffffffu, t, 0);
         } else {
-            for (uint32_t cl = tid - 32; cl < ncat; cl += blockDim.x - 32) {
-                int lo = 0, hi = np - 1;  // owning pattern: last j with cat_off <= c0 + cl
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (hdr[mid].cat_off - c0 <= cl) lo = mid;
-                    else hi = mid - 1;
-                }
-                const PatHdr h = hdr[lo];
-                const int G = h.G;
-                const int cb = int(h.cat_off - c0);
-                const int q = int(cl) - cb + 1;
-                const C* xp = xs + (h.var_off - v0);
-                const uint32_t w = cwa[cl];
-                const T Mq = cMa[cl];
-                C Rs = xp[2 * G + q];
-                if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((w >> 15) & 31)], Rs);
-                C Cq = Rs;
-                for (int e2 = 1; e2 <= G; ++e2) {
-                    if (e2 == q) continue;
-                    const T Mb = cMa[cb + e2 - 1];
-                    Rs = caxpy(Mb, xp[loc_S_d(G, q, e2)], Rs);
-                    Cq = caxpy(Mb, xp[loc_S_d(G, e2, q)], Cq);
-                }
-                W.R[cl] = Rs;
-                W.Cs[cl] = Cq;
-                const InstDev& I = P.inst[h.inst];
-                const int nr = (w >> 10) & 31;
-                const int rl = int(h.rec_off - r0) + int(w & 1023);
-                for (int t = 0; t < nr; ++t) {
-                    const uint2 raw = recs[rl + t];
-                    const uint32_t pk = raw.y;
-                    const int ts = pk & 31, Gp = (pk >> 5) & 31, tr = (pk >> 10) & 31;
-                    const int ipos = (pk >> 16) & 31, ins = (pk >> 21) & 1, del = (pk >> 22) & 1;
-                    const int cid = pk >> 23;
-                    const int smerge = ins ? 63 : ipos;
-                    int4 A;
-                    A.x = int(raw.x) + ts;                            // X'[tau*]
-                    A.y = int(raw.x) + 3 * Gp + (ts - 1) * (Gp - 1);  // S' row tau*
-                    A.z = int(raw.x) + 3 * Gp + ts;                   // S' column tau*
-                    A.w = int(raw.x) + (Gp + 1) * (Gp + 1) + tr;      // T'[tau*]
-                    W.dA[rl + t] = A;
-                    W.dS[rl + t] = uint32_t(del) | (uint32_t(ins) << 1) | (uint32_t(ipos) << 2) | (uint32_t(ts) << 7) |
-                                   (uint32_t(smerge) << 12) | (uint32_t(Gp) << 18);
-                    W.crow[rl + t] = __ldg(P.coef_row + I.coef_base + cid);
-                    W.ccol[rl + t] = __ldg(P.coef_col + I.coef_base + cid);
-                }
+            c = it;
+            it += nwarps;
+        }
+        if (c >= P.nchunks) break;
+        const ItemDesc d = P.items[c];
+        const int np = int(d.np);
+        const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0, ncat = d.ncat;
+        // ---- stage the item
+        for (uint32_t i = lane; i < nv; i += 32) {
+            S.x[i] = P.x_in[v0 + i];
+            if (P.stage > 0) {
+                S.y[i] = P.y[v0 + i];
+                S.acc[i] = P.acc[v0 + i];
             }
         }
-        __syncthreads();
-        // ---- phase 3: pattern threads: work order (S variables first, then
-        // the rest, each in memory order) and the Z sums of Eq. HZ
-        {
-            const uint32_t nS = s_nS;
-            for (int j = tid; j < np; j += blockDim.x) {
-                const PatHdr h = hdr[j];
-                const int G = h.G;
-                const uint32_t a = h.var_off - v0;
-                const uint32_t ej = a | (uint32_t(j) << 11);
-                uint32_t* ps = W.perm + W.sb[j];
-                uint32_t* po = W.perm + nS + W.ob[j];
-                const int cb = int(h.cat_off - c0);
-                C zs = mk(T(0), T(0));
-                *po++ = ej | (uint32_t(KZ) << 19);
-                for (int q = 1; q <= G; ++q) {
-                    *po++ = (ej + q) | (uint32_t(KX) << 19) | (uint32_t(q) << 22);
-                    zs = caxpy(cMa[cb + q - 1], csub(xs[a + q], xs[a + G + q]), zs);
-                }
-                for (int q = 1; q <= G; ++q) *po++ = (ej + G + q) | (uint32_t(KY) << 19) | (uint32_t(q) << 22);
-                for (int q = 1; q <= G; ++q) *po++ = (ej + 2 * G + q) | (uint32_t(KP) << 19) | (uint32_t(q) << 22);
-                uint32_t l = ej + 3 * G + 1;
-                for (int q = 1; q <= G; ++q)
-                    for (int r = 1; r <= G; ++r)
-                        if (r != q) *ps++ = (l++) | (uint32_t(KS) << 19) | (uint32_t(q) << 22) | (uint32_t(r) << 27);
-                for (int q = 1; q <= G; ++q) {
-                    const int tr = (cwa[cb + q - 1] >> 15) & 31;
-                    if (tr != 31)
-                        *po++ = (ej + (G + 1) * (G + 1) + tr) | (uint32_t(KT) << 19) | (uint32_t(q) << 22);
-                }
-                W.Zs[j] = zs;
-            }
+        for (int j = lane; j <= np; j += 32) S.ph[j] = P.hdr[d.p0 + j];
+        for (int j = lane; j < np; j += 32) S.gam[j] = __ldg(P.gamma + d.p0 + j);
+        for (uint32_t cl = lane; cl < ncat; cl += 32) {
+            S.cw[cl] = __ldg(P.cat_word + c0 + cl);
+            S.cM[cl] = __ldg(P.cat_M + c0 + cl);
         }
-        __syncthreads();
-        // ---- phase 4: one unique variable per thread
-        const C* ys = B.y + sk.y;
-        const C* as = B.acc + sk.acc;
-        for (uint32_t i = tid; i < nv; i += blockDim.x) {
-            const uint32_t e = W.perm[i];
-            const uint32_t l = e & 2047u;
-            const int j = int((e >> 11) & 255u);
-            const int kind = int((e >> 19) & 7u);
-            const int q = int((e >> 22) & 31u);
-            const int r = int(e >> 27);
+        __syncwarp();
+        // ---- grouped sums per category and per pattern
+        for (uint32_t cl = lane; cl < ncat; cl += 32) {
+            int lo = 0, hi = np - 1;  // owning pattern: last j with cat_off <= c0 + cl
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (S.ph[mid].cat_off - c0 <= cl) lo = mid;
+                else hi = mid - 1;
+            }
+            const PatHdr h = S.ph[lo];
+            const int G = h.G;
+            const int cb = int(h.cat_off - c0);
+            const int q = int(cl) - cb + 1;
+            const C* xp = S.x + (h.var_off - v0);
+            const T Mq = S.cM[cl];
+            C Rs = xp[2 * G + q];
+            if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((S.cw[cl] >> 15) & 31)], Rs);
+            C Cq = Rs;
+            for (int e2 = 1; e2 <= G; ++e2) {
+                if (e2 == q) continue;
+                const T Mb = S.cM[cb + e2 - 1];
+                Rs = caxpy(Mb, xp[loc_S_d(G, q, e2)], Rs);
+                Cq = caxpy(Mb, xp[loc_S_d(G, e2, q)], Cq);
+            }
+            S.R[cl] = Rs;
+            S.Cs[cl] = Cq;
+        }
+        for (int j = lane; j < np; j += 32) {
+            const PatHdr h = S.ph[j];
+            const int G = h.G;
+            const int cb = int(h.cat_off - c0);
+            const C* xp = S.x + (h.var_off - v0);
+            C zs = mk(T(0), T(0));
+            for (int q = 1; q <= G; ++q) zs = caxpy(S.cM[cb + q - 1], csub(xp[q], xp[G + q]), zs);
+            S.Zs[j] = zs;
+        }
+        __syncwarp();
+        // ---- one unique variable per lane
+        for (uint32_t i = lane; i < nv; i += 32) {
+            const uint32_t e = __ldg(P.vdesc + v0 + i);
+            const uint32_t l = e & 1023u;
+            const int j = int((e >> 10) & 31u);
+            const int kind = int((e >> 15) & 7u);
+            const int q = int((e >> 18) & 31u);
+            const int r = int((e >> 23) & 31u);
             const uint32_t vg = v0 + l;
-            const PatHdr h = hdr[j];
+            const PatHdr h = S.ph[j];
             const int G = h.G;
             const int pl = int(h.var_off - v0);
             const int cb = int(h.cat_off - c0);
@@ -593,10 +374,11 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 const double2* xsin = P.xs_in + I.side;
                 auto own = [&](int ii) { return xsin[ii]; };
                 auto gath = [&](uint32_t ii) { const C t = __ldg(P.x_in + ii); return make_double2(t.x, t.y); };
-                const double2 gam = make_double2(P.gamma[d.p0 + j].x, P.gamma[d.p0 + j].y);
+                const double2 gam = make_double2(S.gam[j].x, S.gam[j].y);
                 const int loc = int(l) - pl;
-                const double2 k = var_rhs<double>(P, kind, q, r, G, cwa + cb, cMa + cb, recs + (h.rec_off - r0), h, I,
-                                                  gam, own, gath);
+                const double2 k = var_rhs<double>(P, kind, q, r, G, S.cw + cb, S.cM + cb,
+                                                  reinterpret_cast<const uint2*>(P.rec) + h.rec_off, h, I, gam, own,
+                                                  gath);
                 const double dt = P.dt;
                 const int si = int(I.side) + loc;
                 if (P.stage < 0) {
@@ -627,19 +409,19 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
             const T g = sizeof(T) == 8 ? T(I.g) : T(I.gf);
             const T det = sizeof(T) == 8 ? T(I.detuning) : T(I.detf);
             const T kap = sizeof(T) == 8 ? T(I.kappa) : T(I.kappaf);
-            const C gam = __ldg(P.gamma + d.p0 + j);
-            const C v = xs[l];
-            const C* xp = xs + pl;
+            const C gam = S.gam[j];
+            const C v = S.x[l];
+            const C* xp = S.x + pl;
             // Hamiltonian, damping and loss (Eqs. HZ, HX and their Y, P, S, T
-            // counterparts), with the grouped sums of phases 2 and 3
+            // counterparts) with the grouped sums
             C dv;
             if (kind == KZ) {
-                const C zs = W.Zs[j];
+                const C zs = S.Zs[j];
                 dv = mk(g * zs.y, -g * zs.x);
                 dv = cfma(mk(-(gam.x + kap), -gam.y), v, dv);
             } else if (kind == KX || kind == KY) {
                 const C Z = xp[0];
-                const C t = kind == KX ? csub(Z, W.R[cb + q - 1]) : csub(W.Cs[cb + q - 1], Z);
+                const C t = kind == KX ? csub(Z, S.R[cb + q - 1]) : csub(S.Cs[cb + q - 1], Z);
                 const T sd = kind == KX ? det : -det;
                 dv = mk(sd * v.y + g * t.y, -sd * v.x - g * t.x);
                 dv = cfma(mk(-(gam.x + T(0.5) * kap), -gam.y), v, dv);
@@ -652,15 +434,15 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
             // of the row category and of the column category
             const bool rowside = kind == KX || kind == KP || kind == KS || kind == KT;
             const bool colside = kind == KY || kind == KS || kind == KT;
-            const int rcat = q;                     // row category (moved on the row side)
-            const int ccat = kind == KS ? r : q;    // column category (moved on the column side)
-            const uint32_t wr = rowside ? cwa[cb + rcat - 1] : 0u;
-            const uint32_t wc = colside ? cwa[cb + ccat - 1] : 0u;
+            const int ccat = kind == KS ? r : q;  // column category (moved on the column side)
+            const uint32_t wr = rowside ? S.cw[cb + q - 1] : 0u;
+            const uint32_t wc = colside ? S.cw[cb + ccat - 1] : 0u;
             const int skip = kind == KP ? int((wr >> 20) & 15) : 0;  // P_q: lower records only
             const int nr = int((wr >> 10) & 31) - skip, nc = int((wc >> 10) & 31);
-            const int rb = int(h.rec_off - r0);
-            const int rr0 = rb + int(wr & 1023) + skip, rc0 = rb + int(wc & 1023);
+            const uint32_t rr0 = h.rec_off + (wr & 1023) + skip, rc0 = h.rec_off + (wc & 1023);
             const int ntot = nr + nc;
+            const C* crow = P.coef_row + I.coef_base;
+            const C* ccol = P.coef_col + I.coef_base;
             for (int i0 = 0; i0 < ntot; i0 += 4) {
                 C val[4], cf[4];
 #pragma unroll
@@ -670,10 +452,11 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                     cf[u] = mk(T(0), T(0));
                     if (ii < ntot) {
                         const bool isrow = ii < nr;
-                        const int rx = isrow ? rr0 + ii : rc0 + ii - nr;
-                        const int4 A = W.dA[rx];
-                        const uint32_t sm = W.dS[rx];
+                        const uint32_t rx = isrow ? rr0 + ii : rc0 + (ii - nr);
+                        const int4 A = __ldg(P.drecA + rx);
+                        const uint32_t sm = __ldg(P.drecS + rx);
                         const int Gp = int(sm >> 18) & 31;
+                        const int cid = int(sm >> 23);
                         int idx;
                         if (isrow) {
                             if (kind == KX) idx = A.x;
@@ -682,11 +465,11 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                                 // S'[tau*, tau(c)] or T'[tau*]; c = r (S) or q (T)
                                 const int smerge = int(sm >> 12) & 63;
                                 const int cc = kind == KS ? r : q;
-                                idx = A.y + cc - ((sm & 1u) && cc > rcat ? 1 : 0) - (cc > smerge ? 1 : 0);
+                                idx = A.y + cc - ((sm & 1u) && cc > q ? 1 : 0) - (cc > smerge ? 1 : 0);
                                 if (cc == smerge) idx = A.w;
                             }
-                            cf[u] = W.crow[rx];
-                            if (kind == KP) cf[u] = cadd(cf[u], W.ccol[rx]);
+                            cf[u] = __ldg(crow + cid);
+                            if (kind == KP) cf[u] = cadd(cf[u], __ldg(ccol + cid));
                         } else {
                             if (kind == KY) idx = A.x + Gp;
                             else {
@@ -697,7 +480,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                                                (((sm >> 1) & 1u) && q >= ipos ? 1 : 0);
                                 idx = (ta == ts) ? A.w : A.z + (ta - 1) * (Gp - 1) - (ts > ta ? 1 : 0);
                             }
-                            cf[u] = W.ccol[rx];
+                            cf[u] = __ldg(ccol + cid);
                         }
                         val[u] = __ldg(P.x_in + idx);
                     }
@@ -711,14 +494,13 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 P.acc[vg] = dv;
                 P.x_out[vg] = caxpy(aT, dv, v);  // x_in is y in the first stage
             } else if (P.stage == 3) {
-                P.y_out[vg] = caxpy(dtT / T(6), cadd(as[l], dv), ys[l]);
+                P.y_out[vg] = caxpy(dtT / T(6), cadd(S.acc[l], dv), S.y[l]);
             } else {
-                P.acc[vg] = caxpy(T(2), dv, as[l]);
-                P.x_out[vg] = caxpy(aT, dv, ys[l]);
+                P.acc[vg] = caxpy(T(2), dv, S.acc[l]);
+                P.x_out[vg] = caxpy(aT, dv, S.y[l]);
             }
         }
-        __syncthreads();
-        b ^= 1;
+        __syncwarp();
     }
 }
 
@@ -770,14 +552,14 @@ __global__ void init_rho0_kernel(const InstDev* __restrict__ inst, int ninst, co
 
 // ---- host launch wrappers (called from api.cu) -----------------------------
 
-size_t stage_smem_bytes(int chunk, int rec_cap, int cat_cap, bool fp64) {
-    if (fp64) return 2 * buf_bytes<double>(chunk, rec_cap, cat_cap) + work_bytes<double>(chunk, rec_cap, cat_cap);
-    return 2 * buf_bytes<float>(chunk, rec_cap, cat_cap) + work_bytes<float>(chunk, rec_cap, cat_cap);
+size_t stage_smem_bytes(int item, int block, bool fp64) {
+    const size_t w = fp64 ? warp_smem_bytes<double>(item) : warp_smem_bytes<float>(item);
+    return w * size_t(block / 32);
 }
 
 template <typename T, bool SIDE>
 static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, cudaStream_t st) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.rec_cap, cfg.cat_cap, sizeof(T) == 8);
+    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, sizeof(T) == 8);
     stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     return cudaGetLastError();
 }
@@ -791,7 +573,10 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.cat_M = static_cast<const T*>(s.cat_M);
     p.gamma = static_cast<const C*>(s.gamma);
     p.rec = static_cast<const Record*>(s.rec);
-    p.desc = static_cast<const ChunkDesc*>(s.desc);
+    p.items = static_cast<const ItemDesc*>(s.items);
+    p.vdesc = static_cast<const uint32_t*>(s.vdesc);
+    p.drecA = static_cast<const int4*>(s.drecA);
+    p.drecS = static_cast<const uint32_t*>(s.drecS);
     p.inst = static_cast<const InstDev*>(s.inst);
     p.coef_row = static_cast<const C*>(s.coef_row);
     p.coef_col = static_cast<const C*>(s.coef_col);
@@ -802,8 +587,6 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.lut_off = static_cast<const uint32_t*>(s.lut_off);
     p.nchunks = s.nchunks;
     p.chunk = cfg.chunk;
-    p.rec_cap = cfg.rec_cap;
-    p.cat_cap = cfg.cat_cap;
     p.x_in = static_cast<const C*>(s.x_in);
     p.x_out = static_cast<C*>(s.x_out);
     p.y = static_cast<const C*>(s.y);
@@ -830,7 +613,7 @@ cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, 
 // Sets the dynamic shared-memory limit once for the largest chunk (outside
 // any stream capture) and returns the CTAs per SM for this configuration.
 cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.rec_cap, cfg.cat_cap, fp64);
+    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, fp64);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

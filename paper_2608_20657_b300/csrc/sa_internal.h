@@ -15,9 +15,7 @@ namespace sa {
 constexpr int kMaxG = 31;            // categories per pattern (5-bit fields)
 constexpr int kCoefN = 32;           // occupation slots per channel in the coefficient table
 constexpr int kCoefPerInst = SA_HEOM_MAXM * kCoefN * 2;
-constexpr int kMaxPatPerChunk = 256; // local pattern index is 8-bit
 constexpr int kSideSlots = 8;        // FP64 slots of the physical representative per instance
-constexpr int kMaxChunkVars = 2048;   // 11-bit local variable index
 
 // ---- one hierarchy connection record ---------------------------------------
 // A record belongs to (pattern Lambda, category q, channel k, direction): the
@@ -104,12 +102,17 @@ struct HostInstance {
     std::vector<double> coef_row, coef_col;  // 2 * kCoefPerInst each
 };
 
-// one work item of the stage kernel: a run of consecutive patterns and the
-// ranges of their variables, categories and records (32 bytes, so that the
-// kernel's producer thread reads it with one load)
-struct ChunkDesc {
-    uint32_t p0, np, v0, nv, c0, ncat, r0, nrec;
+struct DRecA {
+    int x, y, z, w;  // X'-index, S'-row base, S'-column base, T'-index (batch-global)
 };
+
+// one work item of the stage kernel (one warp): a run of consecutive
+// patterns and the ranges of their variables and categories
+struct ItemDesc {
+    uint32_t p0, np, v0, nv, c0, ncat, pad0, pad1;
+};
+constexpr int kItemPats = 32;     // patterns per work item (5-bit local index)
+constexpr int kMaxItemVars = 1024; // variables per work item (10-bit local index)
 
 // launch description shared by api.cu and kernels.cu (type-erased pointers)
 struct LaunchCfg {
@@ -117,12 +120,11 @@ struct LaunchCfg {
     int chunk;      // variable capacity of one work item
     int use_queue;  // 1: persistent grid + atomic work queue
     int grid;       // CTAs
-    int rec_cap;    // most connection records in one work item
-    int cat_cap;    // most categories in one work item
 };
 struct StageLaunch {
     const void* hdr; const void* cat_word; const void* cat_M; const void* gamma; const void* rec;
-    const void* desc; const void* inst; const void* coef_row; const void* coef_col;
+    const void* items; const void* vdesc; const void* drecA; const void* drecS;
+    const void* inst; const void* coef_row; const void* coef_col;
     const void* cat_Md; const void* coef_row_d; const void* coef_col_d;
     const void* lut; const void* lut_off;
     uint32_t nchunks;

@@ -159,8 +159,12 @@ def test_graph_equals_steps_and_tuning_invariance():
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     ref = h.download(a)
-    for blk, chk, q in [(128, 512, 0), (256, 2048, 1), (64, 1536, 1), (128, 1024, 0)]:
-        h.set_tuning(blk, chk, q)
+    for blk, chk, q in [(128, 128, 0), (256, 256, 1), (64, 160, 1), (128, 192, 0), (64, 1024, 1)]:
+        try:
+            h.set_tuning(blk, chk, q)
+        except S.SaHeomError as e:  # a tuning whose shared-memory image does not fit
+            assert e.code == -2
+            continue
         c = h.new_state()
         h.init_state(c, S.rho0_vars(w))
         h.propagate(c, 0.02, 70, observe=False)
