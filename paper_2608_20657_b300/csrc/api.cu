@@ -279,6 +279,7 @@ StageLaunch base_launch(const sa_heom* h) {
     s.lut_off = h->d_lut_off;
     s.nchunks = uint32_t(h->items.size());
     s.err = h->d_err;
+    s.ninst = h->count;
     return s;
 }
 
@@ -461,6 +462,7 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
         D.side = uint32_t(i) * kSideSlots;
         D.var_begin = vb;
         D.n_rho0 = hi.N >= 2 ? 5u : 4u;
+        D.pat_begin = uint32_t(pbase);
         h->theta[i] = 0.5 * std::atan2(2.0 * hi.p.g * std::sqrt(double(hi.N)), -hi.p.detuning);
         std::copy(hi.coef_row.begin(), hi.coef_row.end(), h->coef_row_d.begin() + size_t(2) * kCoefPerInst * i);
         std::copy(hi.coef_col.begin(), hi.coef_col.end(), h->coef_col_d.begin() + size_t(2) * kCoefPerInst * i);

@@ -231,6 +231,12 @@ __device__ __forceinline__ typename Cx<A>::t var_rhs(const StageParams<T>& P, in
     return d;
 }
 
+// Per-pattern constants staged with the work item.
+template <typename T> struct PatConst {
+    T g, det, kap;       // coupling, detuning, loss rate of the pattern's instance
+    uint32_t coef_base;  // the instance's coefficient table
+};
+
 // Per-warp shared-memory image of one work item.
 template <typename T> struct WarpSmem {
     using C = typename Cx<T>::t;
@@ -242,6 +248,7 @@ template <typename T> struct WarpSmem {
     C* Zs;       // sum_q M_q (X_q - Y_q) per pattern (Eq. HZ)
     C* gam;      // Gamma_Lambda per pattern
     PatHdr* ph;  // pattern headers (kItemPats + 1)
+    PatConst<T>* pc;
     uint32_t* cw;
     T* cM;
 };
@@ -253,7 +260,7 @@ __host__ __device__ __forceinline__ size_t warp_smem_bytes(int item) {
     const size_t cs = 2 * sizeof(T);
     const size_t nc = size_t(item) / 4 + 8;
     return 3 * al16(cs * item) + 2 * al16(cs * nc) + 2 * al16(cs * kItemPats) + al16(sizeof(PatHdr) * (kItemPats + 1)) +
-           al16(4 * nc) + al16(sizeof(T) * nc);
+           al16(sizeof(PatConst<T>) * kItemPats) + al16(4 * nc) + al16(sizeof(T) * nc);
 }
 
 template <typename T>
@@ -269,6 +276,7 @@ __device__ __forceinline__ WarpSmem<T> carve_warp(unsigned char* p, int item) {
     W.Zs = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * kItemPats);
     W.gam = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * kItemPats);
     W.ph = reinterpret_cast<PatHdr*>(p);  p += al16(sizeof(PatHdr) * (kItemPats + 1));
+    W.pc = reinterpret_cast<PatConst<T>*>(p); p += al16(sizeof(PatConst<T>) * kItemPats);
     W.cw = reinterpret_cast<uint32_t*>(p); p += al16(4 * nc);
     W.cM = reinterpret_cast<T*>(p);
     return W;
@@ -313,7 +321,16 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
             }
         }
         for (int j = lane; j <= np; j += 32) S.ph[j] = P.hdr[d.p0 + j];
-        for (int j = lane; j < np; j += 32) S.gam[j] = __ldg(P.gamma + d.p0 + j);
+        for (int j = lane; j < np; j += 32) {
+            S.gam[j] = __ldg(P.gamma + d.p0 + j);
+            const InstDev& I = P.inst[P.hdr[d.p0 + j].inst];
+            PatConst<T> pc;
+            pc.g = sizeof(T) == 8 ? T(I.g) : T(I.gf);
+            pc.det = sizeof(T) == 8 ? T(I.detuning) : T(I.detf);
+            pc.kap = sizeof(T) == 8 ? T(I.kappa) : T(I.kappaf);
+            pc.coef_base = I.coef_base;
+            S.pc[j] = pc;
+        }
         for (uint32_t cl = lane; cl < ncat; cl += 32) {
             S.cw[cl] = __ldg(P.cat_word + c0 + cl);
             S.cM[cl] = __ldg(P.cat_M + c0 + cl);
@@ -369,124 +386,94 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
             const int pl = int(h.var_off - v0);
             const int cb = int(h.cat_off - c0);
             const InstDev& I = P.inst[h.inst];
-            if (FP64SIDE && h.tier == 0) {
-                // physical representative: FP64 arithmetic and FP64 storage
-                const double2* xsin = P.xs_in + I.side;
-                auto own = [&](int ii) { return xsin[ii]; };
-                auto gath = [&](uint32_t ii) { const C t = __ldg(P.x_in + ii); return make_double2(t.x, t.y); };
-                const double2 gam = make_double2(S.gam[j].x, S.gam[j].y);
-                const int loc = int(l) - pl;
-                const double2 k = var_rhs<double>(P, kind, q, r, G, S.cw + cb, S.cM + cb,
-                                                  reinterpret_cast<const uint2*>(P.rec) + h.rec_off, h, I, gam, own,
-                                                  gath);
-                const double dt = P.dt;
-                const int si = int(I.side) + loc;
-                if (P.stage < 0) {
-                    P.xs_out[si] = k;
-                    P.x_out[vg] = mk(T(k.x), T(k.y));
-                } else if (P.stage == 3) {
-                    const double2 y6 = P.ys[si], a6 = P.accs[si];
-                    const double2 yn = make_double2(y6.x + dt / 6.0 * (a6.x + k.x), y6.y + dt / 6.0 * (a6.y + k.y));
-                    P.ys_out[si] = yn;
-                    P.y_out[vg] = mk(T(yn.x), T(yn.y));
-                } else {
-                    const double2 y6 = P.ys[si];
-                    double2 a6;
-                    if (P.stage == 0) a6 = k;
-                    else {
-                        a6 = P.accs[si];
-                        a6.x += 2.0 * k.x;
-                        a6.y += 2.0 * k.y;
-                    }
-                    P.accs[si] = a6;
-                    const double a = P.stage == 2 ? dt : 0.5 * dt;
-                    const double2 xn = make_double2(y6.x + a * k.x, y6.y + a * k.y);
-                    P.xs_out[si] = xn;
-                    P.x_out[vg] = mk(T(xn.x), T(xn.y));
-                }
-                continue;
-            }
-            const T g = sizeof(T) == 8 ? T(I.g) : T(I.gf);
-            const T det = sizeof(T) == 8 ? T(I.detuning) : T(I.detf);
-            const T kap = sizeof(T) == 8 ? T(I.kappa) : T(I.kappaf);
+            // SA_FP32_AUX: the physical representative is integrated in FP64 by
+            // rho0_kernel
+            if (FP64SIDE && h.tier == 0) continue;
+            const PatConst<T> pc = S.pc[j];
+            const T g = pc.g, det = pc.det, kap = pc.kap;
             const C gam = S.gam[j];
             const C v = S.x[l];
             const C* xp = S.x + pl;
-            // Hamiltonian, damping and loss (Eqs. HZ, HX and their Y, P, S, T
-            // counterparts) with the grouped sums
+            const C* __restrict__ crow = P.coef_row + pc.coef_base;
+            const C* __restrict__ ccol = P.coef_col + pc.coef_base;
+            const int4* __restrict__ dA = P.drecA;
+            const uint32_t* __restrict__ dS = P.drecS;
+            const C* __restrict__ X = P.x_in;
             C dv;
-            if (kind == KZ) {
-                const C zs = S.Zs[j];
-                dv = mk(g * zs.y, -g * zs.x);
-                dv = cfma(mk(-(gam.x + kap), -gam.y), v, dv);
+            // Hamiltonian, damping and loss (Eqs. HZ, HX and their Y, P, S, T
+            // counterparts) with the grouped sums, then the hierarchy terms of
+            // Eqs. uvar-up / uvar-down from the decoded records of the row
+            // category (row delta) and of the column category (column delta)
+            if (kind == KS || kind == KT) {
+                const int cc = kind == KS ? r : q;  // column category
+                const C t = csub(xp[G + cc], xp[q]);
+                dv = mk(g * t.y, -g * t.x);
+                dv = cfma(mk(-gam.x, -gam.y), v, dv);
+                const uint32_t wr = S.cw[cb + q - 1];
+                const uint32_t ra = h.rec_off + (wr & 1023);
+                const int nr = int((wr >> 10) & 31);
+#pragma unroll 2
+                for (int t2 = 0; t2 < nr; ++t2) {
+                    const int4 A = __ldg(dA + ra + t2);
+                    const uint32_t sm = __ldg(dS + ra + t2);
+                    const int smerge = int(sm >> 12) & 63;
+                    // S'[tau*, tau(cc)], or T'[tau*] when cc merges with the moved molecule
+                    int idx = A.y + cc - ((sm & 1u) && cc > q ? 1 : 0) - (cc > smerge ? 1 : 0);
+                    idx = cc == smerge ? A.w : idx;
+                    dv = cfma(__ldg(crow + (sm >> 23)), __ldg(X + idx), dv);
+                }
+                const uint32_t wc = S.cw[cb + cc - 1];
+                const uint32_t rc = h.rec_off + (wc & 1023);
+                const int nc = int((wc >> 10) & 31);
+#pragma unroll 2
+                for (int t2 = 0; t2 < nc; ++t2) {
+                    const int4 A = __ldg(dA + rc + t2);
+                    const uint32_t sm = __ldg(dS + rc + t2);
+                    const int ts = int(sm >> 7) & 31, ipos = int(sm >> 2) & 31, Gp = int(sm >> 18) & 31;
+                    // S'[tau(q), tau*], or T'[tau*]
+                    const int ta = q - ((sm & 1u) && q > cc ? 1 : 0) + (((sm >> 1) & 1u) && q >= ipos ? 1 : 0);
+                    const int idx = ta == ts ? A.w : A.z + (ta - 1) * (Gp - 1) - (ts > ta ? 1 : 0);
+                    dv = cfma(__ldg(ccol + (sm >> 23)), __ldg(X + idx), dv);
+                }
+            } else if (kind == KP) {
+                const C t = csub(xp[G + q], xp[q]);
+                dv = mk(g * t.y, -g * t.x);
+                dv = cfma(mk(-gam.x, -gam.y), v, dv);
+                // the two raise terms of P_q cancel: only the lower records, with
+                // the row and column coefficients combined
+                const uint32_t wr = S.cw[cb + q - 1];
+                const int nup = int((wr >> 20) & 15);
+                const uint32_t ra = h.rec_off + (wr & 1023) + nup;
+                const int nr = int((wr >> 10) & 31) - nup;
+#pragma unroll 2
+                for (int t2 = 0; t2 < nr; ++t2) {
+                    const int4 A = __ldg(dA + ra + t2);
+                    const uint32_t sm = __ldg(dS + ra + t2);
+                    const int Gp = int(sm >> 18) & 31;
+                    const C cf = cadd(__ldg(crow + (sm >> 23)), __ldg(ccol + (sm >> 23)));
+                    dv = cfma(cf, __ldg(X + A.x + 2 * Gp), dv);
+                }
             } else if (kind == KX || kind == KY) {
                 const C Z = xp[0];
                 const C t = kind == KX ? csub(Z, S.R[cb + q - 1]) : csub(S.Cs[cb + q - 1], Z);
                 const T sd = kind == KX ? det : -det;
                 dv = mk(sd * v.y + g * t.y, -sd * v.x - g * t.x);
                 dv = cfma(mk(-(gam.x + T(0.5) * kap), -gam.y), v, dv);
-            } else {
-                const C t = csub(xp[G + (kind == KS ? r : q)], xp[q]);
-                dv = mk(g * t.y, -g * t.x);
-                dv = cfma(mk(-gam.x, -gam.y), v, dv);
-            }
-            // hierarchy terms (Eqs. uvar-up, uvar-down) from the decoded records
-            // of the row category and of the column category
-            const bool rowside = kind == KX || kind == KP || kind == KS || kind == KT;
-            const bool colside = kind == KY || kind == KS || kind == KT;
-            const int ccat = kind == KS ? r : q;  // column category (moved on the column side)
-            const uint32_t wr = rowside ? S.cw[cb + q - 1] : 0u;
-            const uint32_t wc = colside ? S.cw[cb + ccat - 1] : 0u;
-            const int skip = kind == KP ? int((wr >> 20) & 15) : 0;  // P_q: lower records only
-            const int nr = int((wr >> 10) & 31) - skip, nc = int((wc >> 10) & 31);
-            const uint32_t rr0 = h.rec_off + (wr & 1023) + skip, rc0 = h.rec_off + (wc & 1023);
-            const int ntot = nr + nc;
-            const C* crow = P.coef_row + I.coef_base;
-            const C* ccol = P.coef_col + I.coef_base;
-            for (int i0 = 0; i0 < ntot; i0 += 4) {
-                C val[4], cf[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int ii = i0 + u;
-                    val[u] = mk(T(0), T(0));
-                    cf[u] = mk(T(0), T(0));
-                    if (ii < ntot) {
-                        const bool isrow = ii < nr;
-                        const uint32_t rx = isrow ? rr0 + ii : rc0 + (ii - nr);
-                        const int4 A = __ldg(P.drecA + rx);
-                        const uint32_t sm = __ldg(P.drecS + rx);
-                        const int Gp = int(sm >> 18) & 31;
-                        const int cid = int(sm >> 23);
-                        int idx;
-                        if (isrow) {
-                            if (kind == KX) idx = A.x;
-                            else if (kind == KP) idx = A.x + 2 * Gp;
-                            else {
-                                // S'[tau*, tau(c)] or T'[tau*]; c = r (S) or q (T)
-                                const int smerge = int(sm >> 12) & 63;
-                                const int cc = kind == KS ? r : q;
-                                idx = A.y + cc - ((sm & 1u) && cc > q ? 1 : 0) - (cc > smerge ? 1 : 0);
-                                if (cc == smerge) idx = A.w;
-                            }
-                            cf[u] = __ldg(crow + cid);
-                            if (kind == KP) cf[u] = cadd(cf[u], __ldg(ccol + cid));
-                        } else {
-                            if (kind == KY) idx = A.x + Gp;
-                            else {
-                                // S'[tau(q), tau*] or T'[tau*]
-                                const int ts = int(sm >> 7) & 31;
-                                const int ipos = int(sm >> 2) & 31;
-                                const int ta = q - ((sm & 1u) && q > ccat ? 1 : 0) +
-                                               (((sm >> 1) & 1u) && q >= ipos ? 1 : 0);
-                                idx = (ta == ts) ? A.w : A.z + (ta - 1) * (Gp - 1) - (ts > ta ? 1 : 0);
-                            }
-                            cf[u] = __ldg(ccol + cid);
-                        }
-                        val[u] = __ldg(P.x_in + idx);
-                    }
+                const uint32_t w = S.cw[cb + q - 1];
+                const uint32_t ra = h.rec_off + (w & 1023);
+                const int n = int((w >> 10) & 31);
+                const C* __restrict__ cft = kind == KX ? crow : ccol;
+#pragma unroll 2
+                for (int t2 = 0; t2 < n; ++t2) {
+                    const int4 A = __ldg(dA + ra + t2);
+                    const uint32_t sm = __ldg(dS + ra + t2);
+                    const int idx = kind == KX ? A.x : A.x + (int(sm >> 18) & 31);  // X'[tau*] or Y'[tau*]
+                    dv = cfma(__ldg(cft + (sm >> 23)), __ldg(X + idx), dv);
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) dv = cfma(cf[u], val[u], dv);
+            } else {
+                const C zs = S.Zs[j];
+                dv = mk(g * zs.y, -g * zs.x);
+                dv = cfma(mk(-(gam.x + kap), -gam.y), v, dv);
             }
             if (P.stage < 0) {
                 P.x_out[vg] = dv;
@@ -501,6 +488,64 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
             }
         }
         __syncwarp();
+    }
+}
+
+// SA_FP32_AUX: the physical representative (empty pattern) of every instance
+// in FP64, one thread per variable: FP64 side copies of its own variables,
+// the tier-1 targets gathered from the FP32 stage input, FP64 coefficients and
+// multiplicities, FP64 RK4 stage update; the FP32 mirror is written for the
+// tier-1 readers.
+template <typename T>
+__global__ void __launch_bounds__(128) rho0_kernel(StageParams<T> P, int ninst) {
+    using C = typename Cx<T>::t;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = tid / kSideSlots, loc = tid % kSideSlots;
+    if (i >= ninst) return;
+    const InstDev I = P.inst[i];
+    if (uint32_t(loc) >= I.n_rho0) return;
+    // the empty pattern is the instance's first pattern: G = 1, one category
+    const uint32_t p = I.pat_begin;
+    const PatHdr h = P.hdr[p];
+    const int G = h.G;
+    int kind, q = 1, r = 0;
+    if (loc == 0) kind = KZ;
+    else if (loc == 1) kind = KX;
+    else if (loc == 2) kind = KY;
+    else if (loc == 3) kind = KP;
+    else kind = KT;
+    if (kind == KZ) q = 0;
+    const double2* xsin = P.xs_in + I.side;
+    auto own = [&](int ii) { return xsin[ii]; };
+    auto gath = [&](uint32_t ii) { const C t = __ldg(P.x_in + ii); return make_double2(t.x, t.y); };
+    const double2 k = var_rhs<double>(P, kind, q, r, G, P.cat_word + h.cat_off, P.cat_M + h.cat_off,
+                                      reinterpret_cast<const uint2*>(P.rec) + h.rec_off, h, I,
+                                      make_double2(0.0, 0.0), own, gath);
+    const double dt = P.dt;
+    const int si = int(I.side) + loc;
+    const uint32_t vg = h.var_off + loc;
+    if (P.stage < 0) {
+        P.xs_out[si] = k;
+        P.x_out[vg] = mk(T(k.x), T(k.y));
+    } else if (P.stage == 3) {
+        const double2 y6 = P.ys[si], a6 = P.accs[si];
+        const double2 yn = make_double2(y6.x + dt / 6.0 * (a6.x + k.x), y6.y + dt / 6.0 * (a6.y + k.y));
+        P.ys_out[si] = yn;
+        P.y_out[vg] = mk(T(yn.x), T(yn.y));
+    } else {
+        const double2 y6 = P.ys[si];
+        double2 a6;
+        if (P.stage == 0) a6 = k;
+        else {
+            a6 = P.accs[si];
+            a6.x += 2.0 * k.x;
+            a6.y += 2.0 * k.y;
+        }
+        P.accs[si] = a6;
+        const double a = P.stage == 2 ? dt : 0.5 * dt;
+        const double2 xn = make_double2(y6.x + a * k.x, y6.y + a * k.y);
+        P.xs_out[si] = xn;
+        P.x_out[vg] = mk(T(xn.x), T(xn.y));
     }
 }
 
@@ -558,9 +603,13 @@ size_t stage_smem_bytes(int item, int block, bool fp64) {
 }
 
 template <typename T, bool SIDE>
-static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, cudaStream_t st) {
+static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int ninst, cudaStream_t st) {
     const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, sizeof(T) == 8);
     stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+    if (SIDE) {
+        const int threads = ninst * kSideSlots;
+        rho0_kernel<T><<<(threads + 127) / 128, 128, 0, st>>>(p, ninst);
+    }
     return cudaGetLastError();
 }
 
@@ -606,8 +655,8 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
 }
 
 cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, cudaStream_t st) {
-    if (fp64) return launch_t<double, false>(make_params<double>(s, cfg), cfg, st);
-    return launch_t<float, true>(make_params<float>(s, cfg), cfg, st);
+    if (fp64) return launch_t<double, false>(make_params<double>(s, cfg), cfg, s.ninst, st);
+    return launch_t<float, true>(make_params<float>(s, cfg), cfg, s.ninst, st);
 }
 
 // Sets the dynamic shared-memory limit once for the largest chunk (outside

@@ -69,6 +69,8 @@ struct InstDev {
     uint32_t side;       // first FP64 side slot
     uint32_t var_begin;  // first variable
     uint32_t n_rho0;     // variables of the physical representative (4 or 5)
+    uint32_t pat_begin;  // first pattern (the empty pattern)
+    uint32_t pad2[3];
 };
 
 // ---- host tables of one instance ------------------------------------------
@@ -131,6 +133,7 @@ struct StageLaunch {
     const void* x_in; void* x_out; const void* y; void* acc; void* y_out;
     const void* xs_in; void* xs_out; const void* ys; void* accs; void* ys_out;
     double dt; int stage; unsigned int* queue; unsigned int* err;
+    int ninst;
 };
 
 // builder.cpp
