@@ -82,7 +82,6 @@ struct sa_heom {
     std::vector<DRecA> drecA;
     std::vector<uint32_t> drecS;
     int max_u = 0;
-    int rec_cap = 8;
     // tuning
     int block = 256, chunk = 128, use_queue = 1;
     // device
@@ -101,7 +100,7 @@ struct sa_heom {
     double* d_rho0 = nullptr;
     cudaStream_t cap = nullptr;
     size_t state_bytes = 0, side_off = 0;
-    LaunchCfg cfg{256, 128, 1, 1, 8};
+    LaunchCfg cfg{256, 128, 1, 1};
     std::map<std::tuple<const void*, uint64_t, int64_t>, cudaGraphExec_t> graphs;
 };
 
@@ -150,7 +149,6 @@ void build_items(sa_heom* h) {
     }
     begin.push_back(uint32_t(h->npat));
     h->items.clear();
-    h->rec_cap = 8;
     h->vdesc.assign(size_t(h->nvar), 0u);
     for (size_t c = 0; c + 1 < begin.size(); ++c) {
         const PatHdr &a = h->hdr[begin[c]], &b = h->hdr[begin[c + 1]];
@@ -161,9 +159,6 @@ void build_items(sa_heom* h) {
         d.nv = b.var_off - a.var_off;
         d.c0 = a.cat_off;
         d.ncat = b.cat_off - a.cat_off;
-        d.r0 = a.rec_off;
-        d.nrec = b.rec_off - a.rec_off;
-        h->rec_cap = std::max<int>(h->rec_cap, int(d.nrec));
         h->items.push_back(d);
         uint32_t* out = &h->vdesc[d.v0];
         auto put = [&](uint32_t l, uint32_t j, uint32_t kind, uint32_t q, uint32_t r) {
@@ -220,7 +215,6 @@ int apply_tuning(sa_heom* h) {
     h->cfg.block = h->block;
     h->cfg.chunk = h->chunk;
     h->cfg.use_queue = h->use_queue;
-    h->cfg.rec_cap = (h->rec_cap + 7) / 8 * 8;
     const uint32_t nchunks = uint32_t(h->items.size());
     if (h->host_only) return SA_OK;
     if (h->d_chunk) cudaFree(h->d_chunk);

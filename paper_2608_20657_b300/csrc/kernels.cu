@@ -82,7 +82,6 @@ template <typename T> struct StageParams {
     const uint32_t* __restrict__ lut_off;   // per G
     uint32_t nchunks;
     int chunk;                              // variable capacity of one work item
-    int rec_cap;                            // record capacity of one work item
     const C* x_in;                          // stage input (gathered)
     C* x_out;                               // next stage input, or dR/dt (stage -1)
     const C* y;                             // state at the start of the step
@@ -242,11 +241,8 @@ template <typename T> struct PatConst {
 template <typename T> struct WarpSmem {
     using C = typename Cx<T>::t;
     C* x;        // stage input slice
-    uint32_t* vd;  // lane order and (kind, q, r) of the item's variables
-    int4* rA;    // decoded records: X'-index, S'-row base, S'-column base, T'-index
-    uint32_t* rS;  // decoded records: small fields
-    C* rcr;      // decoded records: row coefficient
-    C* rcc;      // decoded records: column coefficient
+    C* y;        // RK4 state slice
+    C* acc;      // RK4 accumulator slice
     C* R;        // grouped row sums R_q per category (Eq. grouped-row-sum)
     C* Cs;       // grouped column sums C_q per category (Eq. grouped-column-sum)
     C* Zs;       // sum_q M_q (X_q - Y_q) per pattern (Eq. HZ)
@@ -260,25 +256,21 @@ template <typename T> struct WarpSmem {
 __host__ __device__ __forceinline__ size_t al16(size_t b) { return (b + 15) / 16 * 16; }
 
 template <typename T>
-__host__ __device__ __forceinline__ size_t warp_smem_bytes(int item, int rec_cap) {
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int item) {
     const size_t cs = 2 * sizeof(T);
     const size_t nc = size_t(item) / 4 + 8;
-    return al16(cs * item) + al16(4 * item) + al16(16 * rec_cap) + al16(4 * rec_cap) + 2 * al16(cs * rec_cap) +
-           2 * al16(cs * nc) + 2 * al16(cs * kItemPats) + al16(sizeof(PatHdr) * (kItemPats + 1)) +
+    return 3 * al16(cs * item) + 2 * al16(cs * nc) + 2 * al16(cs * kItemPats) + al16(sizeof(PatHdr) * (kItemPats + 1)) +
            al16(sizeof(PatConst<T>) * kItemPats) + al16(4 * nc) + al16(sizeof(T) * nc);
 }
 
 template <typename T>
-__device__ __forceinline__ WarpSmem<T> carve_warp(unsigned char* p, int item, int rec_cap) {
+__device__ __forceinline__ WarpSmem<T> carve_warp(unsigned char* p, int item) {
     using C = typename Cx<T>::t;
     const int nc = item / 4 + 8;
     WarpSmem<T> W;
     W.x = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * item);
-    W.vd = reinterpret_cast<uint32_t*>(p); p += al16(4 * item);
-    W.rA = reinterpret_cast<int4*>(p);    p += al16(16 * rec_cap);
-    W.rS = reinterpret_cast<uint32_t*>(p); p += al16(4 * rec_cap);
-    W.rcr = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * rec_cap);
-    W.rcc = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * rec_cap);
+    W.y = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * item);
+    W.acc = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * item);
     W.R = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * nc);
     W.Cs = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * nc);
     W.Zs = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * kItemPats);
@@ -301,7 +293,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const WarpSmem<T> S = carve_warp<T>(smem + size_t(wib) * warp_smem_bytes<T>(P.chunk, P.rec_cap), P.chunk, P.rec_cap);
+    const WarpSmem<T> S = carve_warp<T>(smem + size_t(wib) * warp_smem_bytes<T>(P.chunk), P.chunk);
     const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
     unsigned int it = blockIdx.x * (blockDim.x >> 5) + wib;
     const T dtT = T(P.dt);
@@ -319,16 +311,14 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
         if (c >= P.nchunks) break;
         const ItemDesc d = P.items[c];
         const int np = int(d.np);
-        const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0, ncat = d.ncat, r0 = d.r0, nrec = d.nrec;
-        // ---- stage the item: stage-input slice, lane order, decoded records,
-        // pattern headers and constants, category words and multiplicities
+        const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0, ncat = d.ncat;
+        // ---- stage the item
         for (uint32_t i = lane; i < nv; i += 32) {
             S.x[i] = P.x_in[v0 + i];
-            S.vd[i] = __ldg(P.vdesc + v0 + i);
-        }
-        for (uint32_t k = lane; k < nrec; k += 32) {
-            S.rA[k] = __ldg(P.drecA + r0 + k);
-            S.rS[k] = __ldg(P.drecS + r0 + k);
+            if (P.stage > 0) {
+                S.y[i] = P.y[v0 + i];
+                S.acc[i] = P.acc[v0 + i];
+            }
         }
         for (int j = lane; j <= np; j += 32) S.ph[j] = P.hdr[d.p0 + j];
         for (int j = lane; j < np; j += 32) {
@@ -346,19 +336,6 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
             S.cM[cl] = __ldg(P.cat_M + c0 + cl);
         }
         __syncwarp();
-        // coefficients of the records (the owning pattern gives the instance)
-        for (uint32_t k = lane; k < nrec; k += 32) {
-            int lo = 0, hi = np - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (S.ph[mid].rec_off - r0 <= k) lo = mid;
-                else hi = mid - 1;
-            }
-            const uint32_t cid = S.rS[k] >> 23;
-            const uint32_t cb = S.pc[lo].coef_base;
-            S.rcr[k] = __ldg(P.coef_row + cb + cid);
-            S.rcc[k] = __ldg(P.coef_col + cb + cid);
-        }
         // ---- grouped sums per category and per pattern
         for (uint32_t cl = lane; cl < ncat; cl += 32) {
             int lo = 0, hi = np - 1;  // owning pattern: last j with cat_off <= c0 + cl
@@ -397,7 +374,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
         __syncwarp();
         // ---- one unique variable per lane
         for (uint32_t i = lane; i < nv; i += 32) {
-            const uint32_t e = S.vd[i];
+            const uint32_t e = __ldg(P.vdesc + v0 + i);
             const uint32_t l = e & 1023u;
             const int j = int((e >> 10) & 31u);
             const int kind = int((e >> 15) & 7u);
@@ -417,14 +394,11 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
             const C gam = S.gam[j];
             const C v = S.x[l];
             const C* xp = S.x + pl;
+            const C* __restrict__ crow = P.coef_row + pc.coef_base;
+            const C* __restrict__ ccol = P.coef_col + pc.coef_base;
+            const int4* __restrict__ dA = P.drecA;
+            const uint32_t* __restrict__ dS = P.drecS;
             const C* __restrict__ X = P.x_in;
-            const int rb = int(h.rec_off - r0);  // item-local record base of the pattern
-            // stream operands of the RK4 stage, issued before the derivative
-            C yv = v, av = mk(T(0), T(0));
-            if (P.stage > 0) {
-                yv = P.y[vg];
-                av = P.acc[vg];
-            }
             C dv;
             // Hamiltonian, damping and loss (Eqs. HZ, HX and their Y, P, S, T
             // counterparts) with the grouped sums, then the hierarchy terms of
@@ -436,30 +410,30 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 dv = mk(g * t.y, -g * t.x);
                 dv = cfma(mk(-gam.x, -gam.y), v, dv);
                 const uint32_t wr = S.cw[cb + q - 1];
-                const int ra = rb + int(wr & 1023);
+                const uint32_t ra = h.rec_off + (wr & 1023);
                 const int nr = int((wr >> 10) & 31);
 #pragma unroll 2
                 for (int t2 = 0; t2 < nr; ++t2) {
-                    const int4 A = S.rA[ra + t2];
-                    const uint32_t sm = S.rS[ra + t2];
+                    const int4 A = __ldg(dA + ra + t2);
+                    const uint32_t sm = __ldg(dS + ra + t2);
                     const int smerge = int(sm >> 12) & 63;
                     // S'[tau*, tau(cc)], or T'[tau*] when cc merges with the moved molecule
                     int idx = A.y + cc - ((sm & 1u) && cc > q ? 1 : 0) - (cc > smerge ? 1 : 0);
                     idx = cc == smerge ? A.w : idx;
-                    dv = cfma(S.rcr[ra + t2], __ldg(X + idx), dv);
+                    dv = cfma(__ldg(crow + (sm >> 23)), __ldg(X + idx), dv);
                 }
                 const uint32_t wc = S.cw[cb + cc - 1];
-                const int rc = rb + int(wc & 1023);
+                const uint32_t rc = h.rec_off + (wc & 1023);
                 const int nc = int((wc >> 10) & 31);
 #pragma unroll 2
                 for (int t2 = 0; t2 < nc; ++t2) {
-                    const int4 A = S.rA[rc + t2];
-                    const uint32_t sm = S.rS[rc + t2];
+                    const int4 A = __ldg(dA + rc + t2);
+                    const uint32_t sm = __ldg(dS + rc + t2);
                     const int ts = int(sm >> 7) & 31, ipos = int(sm >> 2) & 31, Gp = int(sm >> 18) & 31;
                     // S'[tau(q), tau*], or T'[tau*]
                     const int ta = q - ((sm & 1u) && q > cc ? 1 : 0) + (((sm >> 1) & 1u) && q >= ipos ? 1 : 0);
                     const int idx = ta == ts ? A.w : A.z + (ta - 1) * (Gp - 1) - (ts > ta ? 1 : 0);
-                    dv = cfma(S.rcc[rc + t2], __ldg(X + idx), dv);
+                    dv = cfma(__ldg(ccol + (sm >> 23)), __ldg(X + idx), dv);
                 }
             } else if (kind == KP) {
                 const C t = csub(xp[G + q], xp[q]);
@@ -469,13 +443,14 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 // the row and column coefficients combined
                 const uint32_t wr = S.cw[cb + q - 1];
                 const int nup = int((wr >> 20) & 15);
-                const int ra = rb + int(wr & 1023) + nup;
+                const uint32_t ra = h.rec_off + (wr & 1023) + nup;
                 const int nr = int((wr >> 10) & 31) - nup;
 #pragma unroll 2
                 for (int t2 = 0; t2 < nr; ++t2) {
-                    const int4 A = S.rA[ra + t2];
-                    const int Gp = int(S.rS[ra + t2] >> 18) & 31;
-                    const C cf = cadd(S.rcr[ra + t2], S.rcc[ra + t2]);
+                    const int4 A = __ldg(dA + ra + t2);
+                    const uint32_t sm = __ldg(dS + ra + t2);
+                    const int Gp = int(sm >> 18) & 31;
+                    const C cf = cadd(__ldg(crow + (sm >> 23)), __ldg(ccol + (sm >> 23)));
                     dv = cfma(cf, __ldg(X + A.x + 2 * Gp), dv);
                 }
             } else if (kind == KX || kind == KY) {
@@ -485,14 +460,15 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 dv = mk(sd * v.y + g * t.y, -sd * v.x - g * t.x);
                 dv = cfma(mk(-(gam.x + T(0.5) * kap), -gam.y), v, dv);
                 const uint32_t w = S.cw[cb + q - 1];
-                const int ra = rb + int(w & 1023);
+                const uint32_t ra = h.rec_off + (w & 1023);
                 const int n = int((w >> 10) & 31);
-                const C* cft = kind == KX ? S.rcr : S.rcc;
+                const C* __restrict__ cft = kind == KX ? crow : ccol;
 #pragma unroll 2
                 for (int t2 = 0; t2 < n; ++t2) {
-                    const int4 A = S.rA[ra + t2];
-                    const int idx = kind == KX ? A.x : A.x + (int(S.rS[ra + t2] >> 18) & 31);  // X'[tau*] or Y'[tau*]
-                    dv = cfma(cft[ra + t2], __ldg(X + idx), dv);
+                    const int4 A = __ldg(dA + ra + t2);
+                    const uint32_t sm = __ldg(dS + ra + t2);
+                    const int idx = kind == KX ? A.x : A.x + (int(sm >> 18) & 31);  // X'[tau*] or Y'[tau*]
+                    dv = cfma(__ldg(cft + (sm >> 23)), __ldg(X + idx), dv);
                 }
             } else {
                 const C zs = S.Zs[j];
@@ -503,12 +479,12 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 P.x_out[vg] = dv;
             } else if (P.stage == 0) {
                 P.acc[vg] = dv;
-                P.x_out[vg] = caxpy(aT, dv, yv);  // x_in is y in the first stage
+                P.x_out[vg] = caxpy(aT, dv, v);  // x_in is y in the first stage
             } else if (P.stage == 3) {
-                P.y_out[vg] = caxpy(dtT / T(6), cadd(av, dv), yv);
+                P.y_out[vg] = caxpy(dtT / T(6), cadd(S.acc[l], dv), S.y[l]);
             } else {
-                P.acc[vg] = caxpy(T(2), dv, av);
-                P.x_out[vg] = caxpy(aT, dv, yv);
+                P.acc[vg] = caxpy(T(2), dv, S.acc[l]);
+                P.x_out[vg] = caxpy(aT, dv, S.y[l]);
             }
         }
         __syncwarp();
@@ -621,14 +597,14 @@ __global__ void init_rho0_kernel(const InstDev* __restrict__ inst, int ninst, co
 
 // ---- host launch wrappers (called from api.cu) -----------------------------
 
-size_t stage_smem_bytes(int item, int rec_cap, int block, bool fp64) {
-    const size_t w = fp64 ? warp_smem_bytes<double>(item, rec_cap) : warp_smem_bytes<float>(item, rec_cap);
+size_t stage_smem_bytes(int item, int block, bool fp64) {
+    const size_t w = fp64 ? warp_smem_bytes<double>(item) : warp_smem_bytes<float>(item);
     return w * size_t(block / 32);
 }
 
 template <typename T, bool SIDE>
 static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int ninst, cudaStream_t st) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.rec_cap, cfg.block, sizeof(T) == 8);
+    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, sizeof(T) == 8);
     stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     if (SIDE) {
         const int threads = ninst * kSideSlots;
@@ -660,7 +636,6 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.lut_off = static_cast<const uint32_t*>(s.lut_off);
     p.nchunks = s.nchunks;
     p.chunk = cfg.chunk;
-    p.rec_cap = cfg.rec_cap;
     p.x_in = static_cast<const C*>(s.x_in);
     p.x_out = static_cast<C*>(s.x_out);
     p.y = static_cast<const C*>(s.y);
@@ -687,7 +662,7 @@ cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, 
 // Sets the dynamic shared-memory limit once for the largest chunk (outside
 // any stream capture) and returns the CTAs per SM for this configuration.
 cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.rec_cap, cfg.block, fp64);
+    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, fp64);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -111,7 +111,7 @@ struct DRecA {
 // one work item of the stage kernel (one warp): a run of consecutive
 // patterns and the ranges of their variables and categories
 struct ItemDesc {
-    uint32_t p0, np, v0, nv, c0, ncat, r0, nrec;
+    uint32_t p0, np, v0, nv, c0, ncat, pad0, pad1;
 };
 constexpr int kItemPats = 32;     // patterns per work item (5-bit local index)
 constexpr int kMaxItemVars = 1024; // variables per work item (10-bit local index)
@@ -122,7 +122,6 @@ struct LaunchCfg {
     int chunk;      // variable capacity of one work item
     int use_queue;  // 1: persistent grid + atomic work queue
     int grid;       // CTAs
-    int rec_cap;    // most connection records in one work item
 };
 struct StageLaunch {
     const void* hdr; const void* cat_word; const void* cat_M; const void* gamma; const void* rec;
