@@ -262,6 +262,35 @@ int sa_heom_launches_per_step(const sa_heom* h);
  */
 int sa_heom_device_error(sa_heom* h, void* stream);
 
+/*
+ * sa_heom_observables_noalloc -- the same observables as sa_heom_observables
+ * (same kernel, same out[8 * i ..] layout), for callers that may not call
+ * cudaMalloc.  The paper has no counterpart to this entry point.
+ *
+ * sa_heom_observables keeps its device output buffer in the handle and
+ * allocates or grows it with cudaMalloc on first use, and cudaMalloc /
+ * cudaFree can synchronise the whole device.  That is not acceptable for an
+ * application that reserves the device's memory up front for its own pool
+ * allocator and forbids any further driver allocation, nor inside a timing-
+ * critical loop that must not stall other streams.  This entry point calls
+ * no cudaMalloc, cudaFree or other allocating routine: its device output
+ * lives in a fixed array of SA_HEOM_NOALLOC_MAX_INSTANCES * 8 doubles
+ * (256 KiB) compiled into the library, which every GPU that loads the library
+ * holds until the process exits.
+ *   - Batches with more than SA_HEOM_NOALLOC_MAX_INSTANCES instances are
+ *     rejected with SA_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call and every handle shares the one array, which keeps the last
+ *     call's contents; calls whose work overlaps on the GPU (different streams
+ *     or host threads) race on it.  Each call overwrites every slot it reads
+ *     back, so no clearing is needed between calls.
+ * Synchronous on `stream`; returns SA_ERR_NUMERIC if a value is not finite.
+ */
+#define SA_HEOM_NOALLOC_MAX_INSTANCES 4096
+int sa_heom_observables_noalloc(sa_heom* h, const void* d_state, double* out, void* stream);
+
 const char* sa_heom_strerror(int code);
 const char* sa_heom_last_error(void);
 

@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "sa_heom_autotune": [vp, vp, vp, vp],
             "sa_heom_launches_per_step": [vp],
             "sa_heom_device_error": [vp, vp],
+            "sa_heom_observables_noalloc": [vp, vp, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -111,7 +112,7 @@ def exported_symbols() -> list[str]:
             "sa_heom_dump_terms", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_state_upload",
             "sa_heom_state_download", "sa_heom_rhs", "sa_heom_step", "sa_heom_propagate", "sa_heom_observables",
             "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_launches_per_step", "sa_heom_device_error",
-            "sa_heom_strerror", "sa_heom_last_error"]
+            "sa_heom_observables_noalloc", "sa_heom_strerror", "sa_heom_last_error"]
 
 
 def _check(rc: int, where: str):
@@ -283,6 +284,13 @@ class Heom:
     def observables(self, state, stream=None) -> np.ndarray:
         out = np.zeros((self.count, 8))
         _check(lib().sa_heom_observables(self._h, _dev(state), _ptr(out), _stream(stream)), "sa_heom_observables")
+        return out
+
+    def observables_noalloc(self, state, stream=None) -> np.ndarray:
+        """sa_heom_observables_noalloc: observables without any device allocation."""
+        out = np.zeros((self.count, 8))
+        _check(lib().sa_heom_observables_noalloc(self._h, _dev(state), _ptr(out), _stream(stream)),
+               "sa_heom_observables_noalloc")
         return out
 
     def set_tuning(self, block=0, chunk=0, queue=-1):

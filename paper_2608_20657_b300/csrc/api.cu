@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -928,3 +929,54 @@ int sa_heom_device_error(sa_heom* h, void* stream) {
 }
 
 }  // extern "C"
+
+// ---- observables that allocate nothing ---------------------------------------
+// The paper has no counterpart: this is a service for callers that may not
+// call cudaMalloc (see sa_heom_observables_noalloc in include/sa_heom.h).
+// Device-side output of the observables kernel, shared by every handle and
+// every call in the process; each loaded GPU holds it until the process exits.
+static __device__ __align__(256) double g_obs_scratch[SA_HEOM_NOALLOC_MAX_INSTANCES * 8];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_obs_mu;
+double* g_obs_addr[kMaxDevices] = {};  // device address of g_obs_scratch per device ordinal
+}  // namespace
+
+extern "C" int sa_heom_observables_noalloc(sa_heom* h, const void* d_state, double* out, void* stream) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!d_state || !out) return fail(SA_ERR_INVALID_ARG, "d_state and out required");
+    if (h->count > SA_HEOM_NOALLOC_MAX_INSTANCES)
+        return fail(SA_ERR_UNSUPPORTED, "sa_heom_observables_noalloc serves at most " +
+                                            std::to_string(SA_HEOM_NOALLOC_MAX_INSTANCES) + " instances; this batch has " +
+                                            std::to_string(h->count));
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(SA_ERR_UNSUPPORTED, "device ordinal out of range");
+    double* scratch = nullptr;
+    {
+        // set-up, once per device, with that device current: the host-side
+        // name of the array is only a stand-in, so ask the runtime for its
+        // device address
+        std::lock_guard<std::mutex> lock(g_obs_mu);
+        if (!g_obs_addr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_obs_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_obs_scratch)");
+            g_obs_addr[dev] = static_cast<double*>(p);
+        }
+        scratch = g_obs_addr[dev];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the kernel writes all 8 * count slots it is read back from, so nothing
+    // left from an earlier call needs clearing
+    CK(launch_observables(static_cast<const InstDev*>(h->d_inst), static_cast<const double*>(h->d_theta), h->count,
+                          h->precision == SA_FP64 ? d_state : nullptr, side(h, d_state), scratch, st));
+    const size_t need = size_t(h->count) * 8;
+    CK(cudaMemcpyAsync(out, scratch, need * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t j = 0; j < need; ++j)
+        if (!std::isfinite(out[j])) return fail(SA_ERR_NUMERIC, "non-finite observable");
+    return SA_OK;
+}
