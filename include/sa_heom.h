@@ -251,7 +251,9 @@ int sa_heom_observables(sa_heom* h, const void* d_state, double* out, void* stre
 int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue);
 int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best);
 
-/* Number of stage-kernel launches one RK4 step issues (for launch counting). */
+/* Kernel launches one RK4 step issues: 4 stage kernels (SA_FP64), or 4 stage
+ * kernels each followed by the FP64 physical-representative kernel
+ * (SA_FP32_AUX). */
 int sa_heom_launches_per_step(const sa_heom* h);
 
 /*

@@ -920,7 +920,9 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     return SA_OK;
 }
 
-int sa_heom_launches_per_step(const sa_heom* h) { return h ? 4 : 0; }
+// four stage kernels, plus the FP64 physical-representative kernel after each
+// stage in SA_FP32_AUX mode
+int sa_heom_launches_per_step(const sa_heom* h) { return h ? (h->precision == SA_FP64 ? 4 : 8) : 0; }
 
 int sa_heom_device_error(sa_heom* h, void* stream) {
     int rc = check_device(h);
