@@ -82,7 +82,6 @@ struct sa_heom {
     std::vector<uint32_t> vdesc;
     std::vector<DRecA> drecA;
     std::vector<uint32_t> drecS;
-    std::vector<uint16_t> drecQ;
     int max_u = 0;
     // tuning
     int block = 256, chunk = 128, use_queue = 1;
@@ -92,7 +91,7 @@ struct sa_heom {
     void *d_rec = nullptr, *d_inst = nullptr, *d_theta = nullptr, *d_coef_row = nullptr, *d_coef_col = nullptr;
     void *d_coef_row_d = nullptr, *d_coef_col_d = nullptr, *d_lut = nullptr, *d_lut_off = nullptr;
     void* d_chunk = nullptr;
-    void *d_vdesc = nullptr, *d_drecA = nullptr, *d_drecS = nullptr, *d_drecQ = nullptr;
+    void *d_vdesc = nullptr, *d_drecA = nullptr, *d_drecS = nullptr;
     unsigned int* d_err = nullptr;
     void* d_work[3] = {nullptr, nullptr, nullptr};  // acc, xa, xb
     unsigned int* d_queue = nullptr;
@@ -166,26 +165,6 @@ void build_items(sa_heom* h) {
         auto put = [&](uint32_t l, uint32_t j, uint32_t kind, uint32_t q, uint32_t r) {
             *out++ = l | (j << 10) | (kind << 15) | (q << 18) | (r << 23);
         };
-        if (h->precision == SA_FP32_AUX) {
-            // the record-centric kernel takes the variables in memory order
-            for (uint32_t j = 0; j < d.np; ++j) {
-                const PatHdr& H = h->hdr[d.p0 + j];
-                const int G = H.G;
-                const uint32_t l0 = H.var_off - d.v0;
-                put(l0, j, 0, 0, 0);
-                for (int q = 1; q <= G; ++q) put(l0 + uint32_t(loc_X(G, q)), j, 1, q, 0);
-                for (int q = 1; q <= G; ++q) put(l0 + uint32_t(loc_Y(G, q)), j, 2, q, 0);
-                for (int q = 1; q <= G; ++q) put(l0 + uint32_t(loc_P(G, q)), j, 3, q, 0);
-                for (int q = 1; q <= G; ++q)
-                    for (int r = 1; r <= G; ++r)
-                        if (r != q) put(l0 + uint32_t(loc_S(G, q, r)), j, 4, q, r);
-                for (int q = 1; q <= G; ++q) {
-                    const int tr = (h->cat_word[H.cat_off + q - 1] >> 15) & 31;
-                    if (tr != 31) put(l0 + uint32_t(loc_T(G, tr)), j, 5, q, 0);
-                }
-            }
-            continue;
-        }
         for (uint32_t j = 0; j < d.np; ++j) {  // S
             const PatHdr& H = h->hdr[d.p0 + j];
             const int G = H.G;
@@ -218,20 +197,6 @@ void build_items(sa_heom* h) {
 void decode_records(sa_heom* h) {
     h->drecA.resize(h->rec.size());
     h->drecS.resize(h->rec.size());
-    h->drecQ.assign(h->rec.size(), 0);
-    // source category, raise flag and T-rank of every record
-    for (int64_t p = 0; p < h->npat; ++p) {
-        const PatHdr& H = h->hdr[p];
-        for (int q = 1; q <= H.G; ++q) {
-            const uint32_t w = h->cat_word[H.cat_off + q - 1];
-            const int rs = w & 1023, nr = (w >> 10) & 31, tr = (w >> 15) & 31;
-            for (int t = 0; t < nr; ++t) {
-                const size_t i = size_t(H.rec_off) + rs + t;
-                const int raise = (h->rec[i].packed >> 23) & 1;
-                h->drecQ[i] = uint16_t(q | (raise << 5) | ((tr != 31 ? 1 : 0) << 6) | ((tr != 31 ? tr : 0) << 7));
-            }
-        }
-    }
     for (size_t i = 0; i < h->rec.size(); ++i) {
         const Record& R = h->rec[i];
         const uint32_t pk = R.packed;
@@ -277,7 +242,7 @@ void free_device(sa_heom* h) {
     void* ptrs[] = {h->d_hdr, h->d_cat_word, h->d_catM, h->d_catMd, h->d_gamma, h->d_rec, h->d_inst, h->d_theta,
                     h->d_coef_row, h->d_coef_col, h->d_coef_row_d, h->d_coef_col_d, h->d_lut, h->d_lut_off,
                     h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0,
-                    h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS, h->d_drecQ};
+                    h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -305,7 +270,6 @@ StageLaunch base_launch(const sa_heom* h) {
     s.vdesc = h->d_vdesc;
     s.drecA = h->d_drecA;
     s.drecS = h->d_drecS;
-    s.drecQ = h->d_drecQ;
     s.inst = h->d_inst;
     s.coef_row = h->d_coef_row;
     s.coef_col = h->d_coef_col;
@@ -560,7 +524,6 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     if (!rc) rc = upload(&h->d_lut, h->lut);
     if (!rc) rc = upload(&h->d_drecA, h->drecA);
     if (!rc) rc = upload(&h->d_drecS, h->drecS);
-    if (!rc) rc = upload(&h->d_drecQ, h->drecQ);
     if (!rc) rc = upload(&h->d_lut_off, h->lut_off);
     for (int w = 0; w < 3 && !rc; ++w) {
         e = cudaMalloc(&h->d_work[w], h->state_bytes);

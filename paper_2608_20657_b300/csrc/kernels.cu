@@ -54,10 +54,6 @@ template <class C> __device__ __forceinline__ C cfma(C a, C b, C acc) {
     acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
     return acc;
 }
-// a * b
-template <class C> __device__ __forceinline__ C cmulc(C a, C b) {
-    return mk(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
 // acc + s * a (s real)
 template <class C, class S> __device__ __forceinline__ C caxpy(S s, C a, C acc) {
     acc.x = fma(s, a.x, acc.x);
@@ -76,7 +72,6 @@ template <typename T> struct StageParams {
     const uint32_t* __restrict__ vdesc;    // per variable: item-local order and (kind, q, r)
     const int4* __restrict__ drecA;        // decoded records: X'-index, S'-row base, S'-column base, T'-index
     const uint32_t* __restrict__ drecS;    // decoded records: small fields and coefficient id
-    const uint16_t* __restrict__ drecQ;    // decoded records: source category, raise flag, T-rank
     const InstDev* __restrict__ inst;
     const C* __restrict__ coef_row;
     const C* __restrict__ coef_col;
@@ -496,250 +491,6 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
     }
 }
 
-// Shared memory of one warp work item for the record-centric kernel.
-template <typename T> struct RecSmem {
-    using C = typename Cx<T>::t;
-    C* x;        // stage input slice
-    C* dv;       // hierarchy part of the derivative, accumulated per variable
-    C* R;        // grouped row sums R_q per category (Eq. grouped-row-sum)
-    C* Cs;       // grouped column sums C_q per category (Eq. grouped-column-sum)
-    C* Zs;       // sum_q M_q (X_q - Y_q) per pattern (Eq. HZ)
-    C* gam;      // Gamma_Lambda per pattern
-    PatHdr* ph;  // pattern headers (kItemPats + 1)
-    PatConst<T>* pc;
-    uint32_t* cw;
-    T* cM;
-};
-
-template <typename T>
-__host__ __device__ __forceinline__ size_t rec_smem_bytes(int item) {
-    const size_t cs = 2 * sizeof(T);
-    const size_t nc = size_t(item) / 4 + 8;
-    return 2 * al16(cs * item) + 2 * al16(cs * nc) + 2 * al16(cs * kItemPats) + al16(sizeof(PatHdr) * (kItemPats + 1)) +
-           al16(sizeof(PatConst<T>) * kItemPats) + al16(4 * nc) + al16(sizeof(T) * nc);
-}
-
-template <typename T>
-__device__ __forceinline__ RecSmem<T> carve_rec(unsigned char* p, int item) {
-    using C = typename Cx<T>::t;
-    const int nc = item / 4 + 8;
-    RecSmem<T> W;
-    W.x = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * item);
-    W.dv = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * item);
-    W.R = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * nc);
-    W.Cs = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * nc);
-    W.Zs = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * kItemPats);
-    W.gam = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * kItemPats);
-    W.ph = reinterpret_cast<PatHdr*>(p);  p += al16(sizeof(PatHdr) * (kItemPats + 1));
-    W.pc = reinterpret_cast<PatConst<T>*>(p); p += al16(sizeof(PatConst<T>) * kItemPats);
-    W.cw = reinterpret_cast<uint32_t*>(p); p += al16(4 * nc);
-    W.cM = reinterpret_cast<T*>(p);
-    return W;
-}
-
-__device__ __forceinline__ void cadd_shared(float2* p, float2 v) {
-    atomicAdd(&p->x, v.x);
-    atomicAdd(&p->y, v.y);
-}
-
-// Record-centric FP32 stage kernel.  One warp per work item.  The hierarchy
-// terms are formed record by record: a lane takes one connection record
-// (pattern Lambda, category q, channel k, raise or lower) and adds its
-// contribution to every variable of row q (X_q, S_{q,b}, P_q, T_q: the row
-// delta of Eq. projector-commutator-element) and of column q (Y_q, S_{a,q},
-// T_q: the column delta).  The target entries of one record lie on one row
-// or one column of the target pattern, so their indices follow by increments
-// and the record's metadata is read once for 2G+2 terms.  The contributions
-// are summed in shared memory (float atomics), then every lane takes one
-// variable in memory order: Hamiltonian, damping and loss, plus the summed
-// hierarchy part, fused into the RK4 stage update.  The physical
-// representative is left to rho0_kernel (FP64).
-__global__ void __launch_bounds__(256) stage_kernel_rec(StageParams<float> P) {
-    using T = float;
-    using C = float2;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const RecSmem<T> S = carve_rec<T>(smem + size_t(wib) * rec_smem_bytes<T>(P.chunk), P.chunk);
-    const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
-    unsigned int it = blockIdx.x * (blockDim.x >> 5) + wib;
-    const T dtT = T(P.dt);
-    const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
-    const C* __restrict__ X = P.x_in;
-    for (;;) {
-        unsigned int c;
-        if (P.use_queue) {
-            unsigned int t = 0;
-            if (lane == 0) t = atomicAdd(P.queue, 1u);
-            c = __shfl_sync(0xffffffffu, t, 0);
-        } else {
-            c = it;
-            it += nwarps;
-        }
-        if (c >= P.nchunks) break;
-        const ItemDesc d = P.items[c];
-        const int np = int(d.np);
-        const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0, ncat = d.ncat;
-        const uint32_t r0 = P.hdr[d.p0].rec_off, nrec = P.hdr[d.p0 + np].rec_off - r0;
-        // ---- stage the item
-        for (uint32_t i = lane; i < nv; i += 32) {
-            S.x[i] = X[v0 + i];
-            S.dv[i] = make_float2(0.f, 0.f);
-        }
-        for (int j = lane; j <= np; j += 32) S.ph[j] = P.hdr[d.p0 + j];
-        for (int j = lane; j < np; j += 32) {
-            S.gam[j] = __ldg(P.gamma + d.p0 + j);
-            const InstDev& I = P.inst[P.hdr[d.p0 + j].inst];
-            PatConst<T> pc;
-            pc.g = I.gf;
-            pc.det = I.detf;
-            pc.kap = I.kappaf;
-            pc.coef_base = I.coef_base;
-            S.pc[j] = pc;
-        }
-        for (uint32_t cl = lane; cl < ncat; cl += 32) {
-            S.cw[cl] = __ldg(P.cat_word + c0 + cl);
-            S.cM[cl] = __ldg(P.cat_M + c0 + cl);
-        }
-        __syncwarp();
-        // ---- grouped sums per category and per pattern
-        for (uint32_t cl = lane; cl < ncat; cl += 32) {
-            int lo = 0, hi = np - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (S.ph[mid].cat_off - c0 <= cl) lo = mid;
-                else hi = mid - 1;
-            }
-            const PatHdr h = S.ph[lo];
-            const int G = h.G;
-            const int cb = int(h.cat_off - c0);
-            const int q = int(cl) - cb + 1;
-            const C* xp = S.x + (h.var_off - v0);
-            const T Mq = S.cM[cl];
-            C Rs = xp[2 * G + q];
-            if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((S.cw[cl] >> 15) & 31)], Rs);
-            C Cq = Rs;
-            for (int e2 = 1; e2 <= G; ++e2) {
-                if (e2 == q) continue;
-                const T Mb = S.cM[cb + e2 - 1];
-                Rs = caxpy(Mb, xp[loc_S_d(G, q, e2)], Rs);
-                Cq = caxpy(Mb, xp[loc_S_d(G, e2, q)], Cq);
-            }
-            S.R[cl] = Rs;
-            S.Cs[cl] = Cq;
-        }
-        for (int j = lane; j < np; j += 32) {
-            const PatHdr h = S.ph[j];
-            const int G = h.G;
-            const int cb = int(h.cat_off - c0);
-            const C* xp = S.x + (h.var_off - v0);
-            C zs = mk(T(0), T(0));
-            for (int q = 1; q <= G; ++q) zs = caxpy(S.cM[cb + q - 1], csub(xp[q], xp[G + q]), zs);
-            S.Zs[j] = zs;
-        }
-        // ---- hierarchy terms, one connection record per lane
-        for (uint32_t k = lane; k < nrec; k += 32) {
-            int lo = 0, hi = np - 1;  // owning pattern: last j with rec_off <= r0 + k
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (S.ph[mid].rec_off - r0 <= k) lo = mid;
-                else hi = mid - 1;
-            }
-            const PatHdr h = S.ph[lo];
-            if (h.tier == 0) continue;  // the physical representative: rho0_kernel
-            const int G = h.G;
-            C* dvp = S.dv + (h.var_off - v0);
-            const int4 A = __ldg(P.drecA + r0 + k);
-            const uint32_t sm = __ldg(P.drecS + r0 + k);
-            const uint32_t qw = __ldg(P.drecQ + r0 + k);
-            const int q = int(qw & 31u), raise = int((qw >> 5) & 1u), hasT = int((qw >> 6) & 1u);
-            const int trank = int((qw >> 7) & 31u);
-            const int del = int(sm & 1u), ins = int((sm >> 1) & 1u), ipos = int(sm >> 2) & 31;
-            const int ts = int(sm >> 7) & 31, smerge = int(sm >> 12) & 63, Gp = int(sm >> 18) & 31;
-            const uint32_t cb = S.pc[lo].coef_base + (sm >> 23);
-            const C crow = __ldg(P.coef_row + cb), ccol = __ldg(P.coef_col + cb);
-            // row side: X_q <- X'[tau*]; P_q <- P'[tau*] (lower only, row + column
-            // coefficients); S_{q,b} <- S'[tau*, tau(b)] or T'; T_q <- S'[tau*, tau(q)]
-            cadd_shared(dvp + q, cmulc(crow, X[A.x]));
-            if (!raise) cadd_shared(dvp + 2 * G + q, cmulc(cadd(crow, ccol), X[A.x + 2 * Gp]));
-            const int srow = 3 * G + (q - 1) * (G - 1);  // loc of S_{q,b} is srow + b - [b > q]
-#pragma unroll 4
-            for (int b = 1; b <= G; ++b) {
-                if (b == q) continue;
-                int idx = A.y + b - (del && b > q ? 1 : 0) - (b > smerge ? 1 : 0);
-                idx = b == smerge ? A.w : idx;
-                cadd_shared(dvp + srow + b - (b > q ? 1 : 0), cmulc(crow, X[idx]));
-            }
-            if (hasT) cadd_shared(dvp + (G + 1) * (G + 1) + trank, cmulc(crow, X[A.y + q - (q > smerge ? 1 : 0)]));
-            // column side: Y_q <- Y'[tau*]; S_{a,q} <- S'[tau(a), tau*] or T';
-            // T_q <- S'[tau(q), tau*]
-            cadd_shared(dvp + G + q, cmulc(ccol, X[A.x + Gp]));
-#pragma unroll 4
-            for (int a = 1; a <= G; ++a) {
-                if (a == q) continue;
-                const int ta = a - (del && a > q ? 1 : 0) + (ins && a >= ipos ? 1 : 0);
-                const int idx = ta == ts ? A.w : A.z + (ta - 1) * (Gp - 1) - (ts > ta ? 1 : 0);
-                cadd_shared(dvp + loc_S_d(G, a, q), cmulc(ccol, X[idx]));
-            }
-            if (hasT) {
-                const int ta = q + (ins && q >= ipos ? 1 : 0);
-                cadd_shared(dvp + (G + 1) * (G + 1) + trank, cmulc(ccol, X[A.z + (ta - 1) * (Gp - 1) - (ts > ta ? 1 : 0)]));
-            }
-        }
-        __syncwarp();
-        // ---- one variable per lane, memory order
-        for (uint32_t i = lane; i < nv; i += 32) {
-            const uint32_t e = __ldg(P.vdesc + v0 + i);
-            const int j = int((e >> 10) & 31u);
-            const int kind = int((e >> 15) & 7u);
-            const int q = int((e >> 18) & 31u);
-            const int r = int((e >> 23) & 31u);
-            const PatHdr h = S.ph[j];
-            if (h.tier == 0) continue;
-            const uint32_t vg = v0 + i;
-            C yv = S.x[i], av = mk(T(0), T(0));
-            if (P.stage > 0) {
-                yv = P.y[vg];
-                av = P.acc[vg];
-            }
-            const int G = h.G;
-            const C* xp = S.x + (h.var_off - v0);
-            const int cb = int(h.cat_off - c0);
-            const PatConst<T> pc = S.pc[j];
-            const C gam = S.gam[j];
-            const C v = S.x[i];
-            C dv = S.dv[i];
-            if (kind == KZ) {
-                const C zs = S.Zs[j];
-                dv = cadd(dv, mk(pc.g * zs.y, -pc.g * zs.x));
-                dv = cfma(mk(-(gam.x + pc.kap), -gam.y), v, dv);
-            } else if (kind == KX || kind == KY) {
-                const C Z = xp[0];
-                const C t = kind == KX ? csub(Z, S.R[cb + q - 1]) : csub(S.Cs[cb + q - 1], Z);
-                const T sd = kind == KX ? pc.det : -pc.det;
-                dv = cadd(dv, mk(sd * v.y + pc.g * t.y, -sd * v.x - pc.g * t.x));
-                dv = cfma(mk(-(gam.x + T(0.5) * pc.kap), -gam.y), v, dv);
-            } else {
-                const C t = csub(xp[G + (kind == KS ? r : q)], xp[q]);
-                dv = cadd(dv, mk(pc.g * t.y, -pc.g * t.x));
-                dv = cfma(mk(-gam.x, -gam.y), v, dv);
-            }
-            if (P.stage < 0) {
-                P.x_out[vg] = dv;
-            } else if (P.stage == 0) {
-                P.acc[vg] = dv;
-                P.x_out[vg] = caxpy(aT, dv, yv);
-            } else if (P.stage == 3) {
-                P.y_out[vg] = caxpy(dtT / T(6), cadd(av, dv), yv);
-            } else {
-                P.acc[vg] = caxpy(T(2), dv, av);
-                P.x_out[vg] = caxpy(aT, dv, yv);
-            }
-        }
-        __syncwarp();
-    }
-}
-
 // SA_FP32_AUX: the physical representative (empty pattern) of every instance
 // in FP64, one thread per variable: FP64 side copies of its own variables,
 // the tier-1 targets gathered from the FP32 stage input, FP64 coefficients and
@@ -847,15 +598,14 @@ __global__ void init_rho0_kernel(const InstDev* __restrict__ inst, int ninst, co
 // ---- host launch wrappers (called from api.cu) -----------------------------
 
 size_t stage_smem_bytes(int item, int block, bool fp64) {
-    const size_t w = fp64 ? warp_smem_bytes<double>(item) : rec_smem_bytes<float>(item);
+    const size_t w = fp64 ? warp_smem_bytes<double>(item) : warp_smem_bytes<float>(item);
     return w * size_t(block / 32);
 }
 
 template <typename T, bool SIDE>
 static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int ninst, cudaStream_t st) {
     const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, sizeof(T) == 8);
-    if constexpr (sizeof(T) == 4) stage_kernel_rec<<<cfg.grid, cfg.block, sm, st>>>(p);
-    else stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+    stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     if (SIDE) {
         const int threads = ninst * kSideSlots;
         rho0_kernel<T><<<(threads + 127) / 128, 128, 0, st>>>(p, ninst);
@@ -876,7 +626,6 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.vdesc = static_cast<const uint32_t*>(s.vdesc);
     p.drecA = static_cast<const int4*>(s.drecA);
     p.drecS = static_cast<const uint32_t*>(s.drecS);
-    p.drecQ = static_cast<const uint16_t*>(s.drecQ);
     p.inst = static_cast<const InstDev*>(s.inst);
     p.coef_row = static_cast<const C*>(s.coef_row);
     p.coef_col = static_cast<const C*>(s.coef_col);
@@ -929,9 +678,9 @@ cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm)
         if (e != cudaSuccess) return e;
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stage_kernel<double, false>, cfg.block, sm);
     }
-    e = cudaFuncSetAttribute(stage_kernel_rec, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    e = cudaFuncSetAttribute(stage_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stage_kernel_rec, cfg.block, sm);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stage_kernel<float, true>, cfg.block, sm);
 }
 
 cudaError_t launch_observables(const InstDev* inst, const double* theta, int ninst, const void* main64,

@@ -125,7 +125,7 @@ struct LaunchCfg {
 };
 struct StageLaunch {
     const void* hdr; const void* cat_word; const void* cat_M; const void* gamma; const void* rec;
-    const void* items; const void* vdesc; const void* drecA; const void* drecS; const void* drecQ;
+    const void* items; const void* vdesc; const void* drecA; const void* drecS;
     const void* inst; const void* coef_row; const void* coef_col;
     const void* cat_Md; const void* coef_row_d; const void* coef_col_d;
     const void* lut; const void* lut_off;
