@@ -237,152 +237,105 @@ template <typename T> struct PatConst {
     uint32_t coef_base;  // the instance's coefficient table
 };
 
-// Per-warp staging buffer of one work item (two per warp: the next item is
-// copied in with cp.async while the current one is processed).
-template <typename T> struct WarpBuf {
+// Per-warp shared-memory image of one work item.
+template <typename T> struct WarpSmem {
     using C = typename Cx<T>::t;
     C* x;        // stage input slice
-    PatHdr* ph;  // pattern headers (kItemPats + 1)
-    C* gam;      // Gamma_Lambda per pattern
-    uint32_t* cw;
-    T* cM;
-};
-// Per-warp work arrays.
-template <typename T> struct WarpWork {
-    using C = typename Cx<T>::t;
+    C* y;        // RK4 state slice
+    C* acc;      // RK4 accumulator slice
     C* R;        // grouped row sums R_q per category (Eq. grouped-row-sum)
     C* Cs;       // grouped column sums C_q per category (Eq. grouped-column-sum)
     C* Zs;       // sum_q M_q (X_q - Y_q) per pattern (Eq. HZ)
+    C* gam;      // Gamma_Lambda per pattern
+    PatHdr* ph;  // pattern headers (kItemPats + 1)
     PatConst<T>* pc;
+    uint32_t* cw;
+    T* cM;
 };
 
 __host__ __device__ __forceinline__ size_t al16(size_t b) { return (b + 15) / 16 * 16; }
 
 template <typename T>
-__host__ __device__ __forceinline__ size_t wbuf_bytes(int item) {
-    const size_t cs = 2 * sizeof(T);
-    const size_t nc = size_t(item) / 4 + 8;
-    return al16(cs * item) + al16(sizeof(PatHdr) * (kItemPats + 1)) + al16(cs * kItemPats) + al16(4 * nc) +
-           al16(sizeof(T) * nc);
-}
-template <typename T>
-__host__ __device__ __forceinline__ size_t wwork_bytes(int item) {
-    const size_t cs = 2 * sizeof(T);
-    const size_t nc = size_t(item) / 4 + 8;
-    return 2 * al16(cs * nc) + al16(cs * kItemPats) + al16(sizeof(PatConst<T>) * kItemPats);
-}
-template <typename T>
 __host__ __device__ __forceinline__ size_t warp_smem_bytes(int item) {
-    return 2 * wbuf_bytes<T>(item) + wwork_bytes<T>(item);
+    const size_t cs = 2 * sizeof(T);
+    const size_t nc = size_t(item) / 4 + 8;
+    return 3 * al16(cs * item) + 2 * al16(cs * nc) + 2 * al16(cs * kItemPats) + al16(sizeof(PatHdr) * (kItemPats + 1)) +
+           al16(sizeof(PatConst<T>) * kItemPats) + al16(4 * nc) + al16(sizeof(T) * nc);
 }
 
 template <typename T>
-__device__ __forceinline__ WarpBuf<T> carve_buf(unsigned char* p, int item) {
+__device__ __forceinline__ WarpSmem<T> carve_warp(unsigned char* p, int item) {
     using C = typename Cx<T>::t;
     const int nc = item / 4 + 8;
-    WarpBuf<T> B;
-    B.x = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * item);
-    B.ph = reinterpret_cast<PatHdr*>(p);  p += al16(sizeof(PatHdr) * (kItemPats + 1));
-    B.gam = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * kItemPats);
-    B.cw = reinterpret_cast<uint32_t*>(p); p += al16(4 * nc);
-    B.cM = reinterpret_cast<T*>(p);
-    return B;
-}
-template <typename T>
-__device__ __forceinline__ WarpWork<T> carve_work(unsigned char* p, int item) {
-    using C = typename Cx<T>::t;
-    const int nc = item / 4 + 8;
-    WarpWork<T> W;
+    WarpSmem<T> W;
+    W.x = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * item);
+    W.y = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * item);
+    W.acc = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * item);
     W.R = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * nc);
     W.Cs = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * nc);
     W.Zs = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * kItemPats);
-    W.pc = reinterpret_cast<PatConst<T>*>(p);
+    W.gam = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * kItemPats);
+    W.ph = reinterpret_cast<PatHdr*>(p);  p += al16(sizeof(PatHdr) * (kItemPats + 1));
+    W.pc = reinterpret_cast<PatConst<T>*>(p); p += al16(sizeof(PatConst<T>) * kItemPats);
+    W.cw = reinterpret_cast<uint32_t*>(p); p += al16(4 * nc);
+    W.cM = reinterpret_cast<T*>(p);
     return W;
 }
 
-// asynchronous global -> shared copies of 4, 8 or 16 bytes (cp.async)
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
-                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-                 "l"(src), "n"(BYTES)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// Issue the copies of work item d into buffer B (every lane takes a share).
-template <typename T>
-__device__ __forceinline__ void prefetch_item(const StageParams<T>& P, const ItemDesc& d, const WarpBuf<T>& B,
-                                              int lane) {
-    using C = typename Cx<T>::t;
-    for (uint32_t i = lane; i < d.nv; i += 32) cp_async<sizeof(C)>(B.x + i, P.x_in + d.v0 + i);
-    for (uint32_t j = lane; j <= d.np; j += 32) cp_async<16>(B.ph + j, P.hdr + d.p0 + j);
-    for (uint32_t j = lane; j < d.np; j += 32) cp_async<sizeof(C)>(B.gam + j, P.gamma + d.p0 + j);
-    for (uint32_t cl = lane; cl < d.ncat; cl += 32) {
-        cp_async<4>(B.cw + cl, P.cat_word + d.c0 + cl);
-        cp_async<sizeof(T)>(B.cM + cl, P.cat_M + d.c0 + cl);
-    }
-    cp_async_commit();
-}
-
 // One warp per work item (a run of consecutive patterns, at most `item`
-// variables and kItemPats patterns), with no block-wide barrier.  While an
-// item is processed, its successor's stage-input slice, headers and category
-// data are copied into the warp's other buffer with cp.async.  The warp forms
-// the grouped sums, then each lane takes one variable at a time in the
-// host-made order (S variables first, then T, P, X, Y, Z, so that the lanes of
-// a warp run the same code path).
+// variables and kItemPats patterns), with no block-wide barrier: the warp
+// stages its slices, forms the grouped sums, then each lane takes one
+// variable at a time in the host-made order (S variables first, then T, P,
+// X, Y, Z, so that the lanes of a warp run the same code path).
 template <typename T, bool FP64SIDE>
 __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    unsigned char* wbase = smem + size_t(wib) * warp_smem_bytes<T>(P.chunk);
-    const size_t bb = wbuf_bytes<T>(P.chunk);
-    const WarpWork<T> W = carve_work<T>(wbase + 2 * bb, P.chunk);
+    const WarpSmem<T> S = carve_warp<T>(smem + size_t(wib) * warp_smem_bytes<T>(P.chunk), P.chunk);
     const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
     unsigned int it = blockIdx.x * (blockDim.x >> 5) + wib;
-    auto next_item = [&]() -> unsigned int {
+    const T dtT = T(P.dt);
+    const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
+    for (;;) {
+        unsigned int c;
         if (P.use_queue) {
             unsigned int t = 0;
             if (lane == 0) t = atomicAdd(P.queue, 1u);
-            return __shfl_sync(0xffffffffu, t, 0);
+            c = __shfl_sync(0xffffffffu, t, 0);
+        } else {
+            c = it;
+            it += nwarps;
         }
-        const unsigned int c = it;
-        it += nwarps;
-        return c;
-    };
-    const T dtT = T(P.dt);
-    const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
-    unsigned int c = next_item();
-    ItemDesc d{};
-    if (c < P.nchunks) {
-        d = P.items[c];
-        prefetch_item(P, d, carve_buf<T>(wbase, P.chunk), lane);
-    }
-    unsigned int cn = next_item();
-    int b = 0;
-    while (c < P.nchunks) {
-        ItemDesc dn{};
-        if (cn < P.nchunks) dn = P.items[cn];
-        cp_async_wait_all();
-        __syncwarp();
-        const WarpBuf<T> S = carve_buf<T>(wbase + (b ? bb : 0), P.chunk);
-        if (cn < P.nchunks) prefetch_item(P, dn, carve_buf<T>(wbase + (b ? 0 : bb), P.chunk), lane);
-        const unsigned int cnn = next_item();
+        if (c >= P.nchunks) break;
+        const ItemDesc d = P.items[c];
         const int np = int(d.np);
         const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0, ncat = d.ncat;
+        // ---- stage the item
+        for (uint32_t i = lane; i < nv; i += 32) {
+            S.x[i] = P.x_in[v0 + i];
+            if (P.stage > 0) {
+                S.y[i] = P.y[v0 + i];
+                S.acc[i] = P.acc[v0 + i];
+            }
+        }
+        for (int j = lane; j <= np; j += 32) S.ph[j] = P.hdr[d.p0 + j];
         for (int j = lane; j < np; j += 32) {
-            const InstDev& I = P.inst[S.ph[j].inst];
+            S.gam[j] = __ldg(P.gamma + d.p0 + j);
+            const InstDev& I = P.inst[P.hdr[d.p0 + j].inst];
             PatConst<T> pc;
             pc.g = sizeof(T) == 8 ? T(I.g) : T(I.gf);
             pc.det = sizeof(T) == 8 ? T(I.detuning) : T(I.detf);
             pc.kap = sizeof(T) == 8 ? T(I.kappa) : T(I.kappaf);
             pc.coef_base = I.coef_base;
-            W.pc[j] = pc;
+            S.pc[j] = pc;
         }
+        for (uint32_t cl = lane; cl < ncat; cl += 32) {
+            S.cw[cl] = __ldg(P.cat_word + c0 + cl);
+            S.cM[cl] = __ldg(P.cat_M + c0 + cl);
+        }
+        __syncwarp();
         // ---- grouped sums per category and per pattern
         for (uint32_t cl = lane; cl < ncat; cl += 32) {
             int lo = 0, hi = np - 1;  // owning pattern: last j with cat_off <= c0 + cl
@@ -406,8 +359,8 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 Rs = caxpy(Mb, xp[loc_S_d(G, q, e2)], Rs);
                 Cq = caxpy(Mb, xp[loc_S_d(G, e2, q)], Cq);
             }
-            W.R[cl] = Rs;
-            W.Cs[cl] = Cq;
+            S.R[cl] = Rs;
+            S.Cs[cl] = Cq;
         }
         for (int j = lane; j < np; j += 32) {
             const PatHdr h = S.ph[j];
@@ -416,7 +369,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
             const C* xp = S.x + (h.var_off - v0);
             C zs = mk(T(0), T(0));
             for (int q = 1; q <= G; ++q) zs = caxpy(S.cM[cb + q - 1], csub(xp[q], xp[G + q]), zs);
-            W.Zs[j] = zs;
+            S.Zs[j] = zs;
         }
         __syncwarp();
         // ---- one unique variable per lane
@@ -432,20 +385,14 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
             const int G = h.G;
             const int pl = int(h.var_off - v0);
             const int cb = int(h.cat_off - c0);
+            const InstDev& I = P.inst[h.inst];
             // SA_FP32_AUX: the physical representative is integrated in FP64 by
             // rho0_kernel
             if (FP64SIDE && h.tier == 0) continue;
-            // stream operands of the RK4 stage, issued before the derivative
-            C yv = mk(T(0), T(0)), av = mk(T(0), T(0));
-            if (P.stage > 0) {
-                yv = P.y[vg];
-                av = P.acc[vg];
-            }
-            const PatConst<T> pc = W.pc[j];
+            const PatConst<T> pc = S.pc[j];
             const T g = pc.g, det = pc.det, kap = pc.kap;
             const C gam = S.gam[j];
             const C v = S.x[l];
-            if (P.stage == 0) yv = v;
             const C* xp = S.x + pl;
             const C* __restrict__ crow = P.coef_row + pc.coef_base;
             const C* __restrict__ ccol = P.coef_col + pc.coef_base;
@@ -508,7 +455,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 }
             } else if (kind == KX || kind == KY) {
                 const C Z = xp[0];
-                const C t = kind == KX ? csub(Z, W.R[cb + q - 1]) : csub(W.Cs[cb + q - 1], Z);
+                const C t = kind == KX ? csub(Z, S.R[cb + q - 1]) : csub(S.Cs[cb + q - 1], Z);
                 const T sd = kind == KX ? det : -det;
                 dv = mk(sd * v.y + g * t.y, -sd * v.x - g * t.x);
                 dv = cfma(mk(-(gam.x + T(0.5) * kap), -gam.y), v, dv);
@@ -524,7 +471,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                     dv = cfma(__ldg(cft + (sm >> 23)), __ldg(X + idx), dv);
                 }
             } else {
-                const C zs = W.Zs[j];
+                const C zs = S.Zs[j];
                 dv = mk(g * zs.y, -g * zs.x);
                 dv = cfma(mk(-(gam.x + kap), -gam.y), v, dv);
             }
@@ -532,21 +479,16 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 P.x_out[vg] = dv;
             } else if (P.stage == 0) {
                 P.acc[vg] = dv;
-                P.x_out[vg] = caxpy(aT, dv, yv);  // x_in is y in the first stage
+                P.x_out[vg] = caxpy(aT, dv, v);  // x_in is y in the first stage
             } else if (P.stage == 3) {
-                P.y_out[vg] = caxpy(dtT / T(6), cadd(av, dv), yv);
+                P.y_out[vg] = caxpy(dtT / T(6), cadd(S.acc[l], dv), S.y[l]);
             } else {
-                P.acc[vg] = caxpy(T(2), dv, av);
-                P.x_out[vg] = caxpy(aT, dv, yv);
+                P.acc[vg] = caxpy(T(2), dv, S.acc[l]);
+                P.x_out[vg] = caxpy(aT, dv, S.y[l]);
             }
         }
         __syncwarp();
-        c = cn;
-        d = dn;
-        cn = cnn;
-        b ^= 1;
     }
-    cp_async_wait_all();
 }
 
 // SA_FP32_AUX: the physical representative (empty pattern) of every instance
