@@ -293,6 +293,33 @@ int sa_heom_device_error(sa_heom* h, void* stream);
 #define SA_HEOM_NOALLOC_MAX_INSTANCES 4096
 int sa_heom_observables_noalloc(sa_heom* h, const void* d_state, double* out, void* stream);
 
+/*
+ * Conventional scaled HEOM on the GPU (cross-check of the symmetry-adapted
+ * path on small ensembles): every label n in N0^{N m} with |n| <= L
+ * (Eq. direct-ado-count, lexicographic order, the zero label first), every
+ * ADO a dense (N+1) x (N+1) complex matrix (Eq. basis), right-hand side
+ * Eq. scaled-HEOM with the same cavity loss, classical RK4.
+ *   sa_conv_build:   tables for one instance (N <= 64, at most 4 GB per state
+ *                    vector); allocates three RK4 work vectors.
+ *   sa_conv_info:    number of ADOs and bytes of one state vector
+ *                    (double2[n_ados * (N+1)^2], ADO-major, row-major).
+ *   sa_conv_labels:  n_ados * N * m occupations (molecule-major).
+ *   sa_conv_set_rho0: zero the state and copy rho0 ((N+1)^2 complex,
+ *                    row-major, host) into the zero-label ADO; synchronous.
+ *   sa_conv_rhs:     one right-hand side, d_x -> d_dx (distinct).
+ *   sa_conv_step:    nsteps RK4 steps of size dt in place; asynchronous.
+ * Errors as for sa_heom_*; sa_conv_last_error gives the detail.
+ */
+typedef struct sa_conv sa_conv;
+int sa_conv_build(const sa_params* p, sa_conv** out);
+void sa_conv_destroy(sa_conv* c);
+int sa_conv_info(const sa_conv* c, int64_t* n_ados, size_t* state_bytes);
+int sa_conv_labels(const sa_conv* c, uint8_t* out);
+int sa_conv_set_rho0(const sa_conv* c, const double* rho0, void* d_state, void* stream);
+int sa_conv_rhs(sa_conv* c, const void* d_x, void* d_dx, void* stream);
+int sa_conv_step(sa_conv* c, void* d_state, double dt, int64_t nsteps, void* stream);
+const char* sa_conv_last_error(void);
+
 const char* sa_heom_strerror(int code);
 const char* sa_heom_last_error(void);
 

@@ -91,6 +91,12 @@ def lib() -> ctypes.CDLL:
             "sa_heom_launches_per_step": [vp],
             "sa_heom_device_error": [vp, vp],
             "sa_heom_observables_noalloc": [vp, vp, vp, vp],
+            "sa_conv_build": [P(Params), P(vp)],
+            "sa_conv_info": [vp, P(i64), P(ctypes.c_size_t)],
+            "sa_conv_labels": [vp, vp],
+            "sa_conv_set_rho0": [vp, vp, vp, vp],
+            "sa_conv_rhs": [vp, vp, vp, vp],
+            "sa_conv_step": [vp, vp, dbl, i64, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -102,6 +108,10 @@ def lib() -> ctypes.CDLL:
         L.sa_heom_strerror.restype = ctypes.c_char_p
         L.sa_heom_last_error.argtypes = []
         L.sa_heom_last_error.restype = ctypes.c_char_p
+        L.sa_conv_destroy.argtypes = [vp]
+        L.sa_conv_destroy.restype = None
+        L.sa_conv_last_error.argtypes = []
+        L.sa_conv_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -112,7 +122,9 @@ def exported_symbols() -> list[str]:
             "sa_heom_dump_terms", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_state_upload",
             "sa_heom_state_download", "sa_heom_rhs", "sa_heom_step", "sa_heom_propagate", "sa_heom_observables",
             "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_launches_per_step", "sa_heom_device_error",
-            "sa_heom_observables_noalloc", "sa_heom_strerror", "sa_heom_last_error"]
+            "sa_heom_observables_noalloc", "sa_heom_strerror", "sa_heom_last_error", "sa_conv_build",
+            "sa_conv_destroy", "sa_conv_info", "sa_conv_labels", "sa_conv_set_rho0", "sa_conv_rhs", "sa_conv_step",
+            "sa_conv_last_error"]
 
 
 def _check(rc: int, where: str):
@@ -306,3 +318,58 @@ class Heom:
 
     def launches_per_step(self) -> int:
         return int(lib().sa_heom_launches_per_step(self._h))
+
+
+def _check_conv(rc: int, where: str):
+    if rc != 0:
+        raise SaHeomError(rc, where, lib().sa_conv_last_error().decode())
+
+
+class Conventional:
+    """Conventional scaled HEOM on the GPU (sa_conv_* handle): dense ADOs."""
+
+    def __init__(self, params: Params):
+        h = ctypes.c_void_p()
+        _check_conv(lib().sa_conv_build(ctypes.byref(params), ctypes.byref(h)), "sa_conv_build")
+        self._h = h
+        self.N, self.m = params.N, params.m
+        self.D = self.N + 1
+        n = ctypes.c_int64()
+        sb = ctypes.c_size_t()
+        _check_conv(lib().sa_conv_info(self._h, ctypes.byref(n), ctypes.byref(sb)), "sa_conv_info")
+        self.nado, self.state_bytes = n.value, sb.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sa_conv_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def labels(self) -> np.ndarray:
+        out = np.zeros((self.nado, self.N * self.m), np.uint8)
+        _check_conv(lib().sa_conv_labels(self._h, _ptr(out)), "sa_conv_labels")
+        return out
+
+    def new_state(self, device="cuda"):
+        import torch
+
+        return torch.zeros(self.state_bytes, dtype=torch.uint8, device=device)
+
+    def set_rho0(self, state, rho0, stream=None):
+        r = np.ascontiguousarray(np.asarray(rho0, np.complex128).reshape(self.D, self.D))
+        _check_conv(lib().sa_conv_set_rho0(self._h, _ptr(r), _dev(state), _stream(stream)), "sa_conv_set_rho0")
+
+    def rhs(self, x, dx, stream=None):
+        _check_conv(lib().sa_conv_rhs(self._h, _dev(x), _dev(dx), _stream(stream)), "sa_conv_rhs")
+
+    def step(self, state, dt: float, nsteps: int = 1, stream=None):
+        _check_conv(lib().sa_conv_step(self._h, _dev(state), float(dt), int(nsteps), _stream(stream)), "sa_conv_step")
+
+    def to_numpy(self, state) -> np.ndarray:
+        return state.view(__import__("torch").float64).cpu().numpy().view(np.complex128).reshape(
+            self.nado, self.D, self.D)
