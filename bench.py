@@ -103,10 +103,11 @@ def _stage_sha() -> str:
     return hashlib.sha256(src).hexdigest()[:16]
 
 
-def _traffic(workload: str):
-    """DRAM bytes per stage launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", f"stage_kernel_{workload}_traffic.json")
+def _traffic(workload: str, kernel: int):
+    """DRAM bytes per stage launch from the committed ncu summary of this
+    kernel variant, if it was taken on the current kernel source."""
+    name = "list_stage_kernel" if kernel == 1 else "stage_kernel"
+    p = os.path.join(ROOT, "profiles", f"{name}_{workload}_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
@@ -200,6 +201,11 @@ def run_reference(args):
 
 # ------------------------------------------------------------ GPU arm
 
+def _kernel_name(kernel, fp32):
+    base = "list_stage_kernel" if kernel == 1 else "stage_kernel"
+    return base + ("<float,true>" if fp32 else "<double,false>")
+
+
 def run_ours(args):
     import torch
 
@@ -220,9 +226,12 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     if args.tune:
         best = tuple(int(v) for v in args.tune.split(","))
-        h.set_tuning(*best)
+        h.set_tuning(*best[:3])
+        if len(best) > 3:
+            h.set_kernel(best[3])
     else:
-        best = h.autotune(st)
+        h.autotune(st)
+    tuning = h.tuning()
     h.init_state(st, _rho0(ws))
     torch.cuda.synchronize()
 
@@ -261,8 +270,8 @@ def run_ours(args):
     achieved = bytes_launch / (launch_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _traffic(args.workload), "peak_source": f"{peak_kind} hbm_gbs",
-            "kernel": "stage_kernel<float,true>", "bytes_per_launch": bytes_launch}
+            "traffic": _traffic(args.workload, tuning["kernel"]), "peak_source": f"{peak_kind} hbm_gbs",
+            "kernel": _kernel_name(tuning["kernel"], precision == S.SA_FP32_AUX), "bytes_per_launch": bytes_launch}
 
     # end to end through the public API with host buffers: upload the state
     # from pinned host memory, K steps with the observables of every step read
@@ -324,7 +333,7 @@ def run_ours(args):
                                                         if args.workload == "w4" else ""),
                            "n_instances": h.count, "n_vars": n_vars, "n_patterns": h.n_patterns,
                            "state_bytes": h.state_bytes, "l2": "inputs larger than L2 (4 vectors)",
-                           "tuning": {"block": best[0], "chunk": best[1], "queue": best[2]},
+                           "tuning": tuning,
                            "parallelism": f"replicas{world}"},
                 "roofline": roof, "gpu_launches": h.launches_per_step() * args.steps, "clocks": ck, "e2e": e2e}
         line.update(extra)
@@ -348,7 +357,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--tune", default="", help="block,chunk,queue (skips the autotuner)")
+    ap.add_argument("--tune", default="", help="block,chunk,queue[,kernel] (skips the autotuner; kernel 0 = "
+                                                "connection records, 1 = term lists)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -176,6 +176,32 @@ int sa_heom_dump_categories(const sa_heom* h, int inst, int32_t* vec_id, int64_t
 int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, int32_t* k, int32_t* n,
                        int32_t* dir, int32_t* side);
 
+/*
+ * sa_heom_dump_lists -- the host copy of the SA_KERNEL_LISTS tables for the
+ * current tuning (handles built with SA_BUILD_HOST_ONLY after
+ * sa_heom_set_kernel(h, SA_KERNEL_LISTS); device handles keep them on the
+ * device only and get STATE).  sizes[0..3] <- work items, rounds of 32 lanes,
+ * term rows, batch variables.  Each non-NULL array receives (batch-global
+ * indices):
+ *   items  uint32[8 * items]: first pattern, patterns, first variable v0,
+ *          variables, first category, categories, first round, lane
+ *          variables nl of every work item;
+ *   lvd    uint32[variables]: at v0 + i, lane position i < nl of the item,
+ *          l | a << 10 | b << 21 (item-local variable l; operand-area
+ *          indices a, b of the term -i g (op[a] - op[b]));
+ *   lvj    uint8[variables]: at v0 + i, j | class << 5 (pattern j of the
+ *          item; diagonal class 0: P S T, 1: X, 2: Y, 3: Z);
+ *   rbase  uint32[rounds + 1]: first term row of every round;
+ *   tidx   uint32[32 * rows], tcid uint16[32 * rows]: entry 32 * row + lane
+ *          = target variable and coefficient slot (side * 512 + cid for the
+ *          row / column coefficient of coefficient id cid; 1024 + cid for
+ *          row + column, the P_q lower terms; 1536 = zero, padding);
+ *   opz    int32[4]: operand-area offsets of R_q, C_q, the Z sums, the zero
+ *          (the item's stage-input slice occupies [0, chunk)).
+ */
+int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* lvd, uint8_t* lvj,
+                       uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz);
+
 /* sa_heom_state_bytes -- bytes of one state vector of the whole batch. */
 int sa_heom_state_bytes(const sa_heom* h, size_t* bytes);
 
@@ -246,10 +272,32 @@ int sa_heom_observables(sa_heom* h, const void* d_state, double* out, void* stre
  * one work item per warp.  Any argument
  * <= 0 keeps its current value.  sa_heom_autotune times a few candidates of
  * the RK4 stage kernel on d_state (which it leaves changed) and keeps the
- * fastest; best[3] receives block, chunk, queue.
+ * fastest; best[3] receives block, chunk, queue (sa_heom_get_tuning also
+ * reports the kernel variant it chose).
  */
 int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue);
 int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best);
+
+/*
+ * Stage-kernel variant.  Both evaluate the same right-hand side (Eqs.
+ * uvar-up, uvar-down and the commutator of Eq. HS) and fuse the RK4 stage.
+ *   SA_KERNEL_RECORDS  each lane walks the connection records of its
+ *                      variable's row and column categories and resolves
+ *                      the aligned accessor (Eq. aligned-accessor) on the
+ *                      fly; device tables ~ 24 B per record.
+ *   SA_KERNEL_LISTS    the host resolves every hierarchy term once; the
+ *                      device holds, per work item, the variables in lane
+ *                      order (sorted by term count) and per round of 32
+ *                      lanes a term-major list of (target index, coefficient
+ *                      slot) entries: 6 B per term plus padding to the
+ *                      round's longest list, 5 B per variable.
+ * sa_heom_set_kernel rebuilds the launch tables (synchronous; INVALID_ARG for
+ * an unknown variant, OOM if the lists do not fit).  sa_heom_get_tuning
+ * writes block, chunk, queue, kernel to out[0..3].
+ */
+enum { SA_KERNEL_RECORDS = 0, SA_KERNEL_LISTS = 1 };
+int sa_heom_set_kernel(sa_heom* h, int kernel);
+int sa_heom_get_tuning(const sa_heom* h, int* out);
 
 /* Kernel launches one RK4 step issues: 4 stage kernels (SA_FP64), or 4 stage
  * kernels each followed by the FP64 physical-representative kernel

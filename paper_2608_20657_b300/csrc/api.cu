@@ -17,6 +17,7 @@
 namespace sa {
 cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, cudaStream_t st);
 cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm);
+void list_operand_layout(int item, int* opR, int* opC, int* opZ, int* opZero);
 cudaError_t launch_observables(const InstDev* inst, const double* theta, int ninst, const void* main64,
                                const void* side64, double* out, cudaStream_t st);
 cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0, void* main64, void* main32,
@@ -83,8 +84,13 @@ struct sa_heom {
     std::vector<DRecA> drecA;
     std::vector<uint32_t> drecS;
     int max_u = 0;
+    // term lists of the list kernel (built per tuning, freed after upload)
+    std::vector<uint32_t> lvd, rbase, tidx;
+    std::vector<uint8_t> lvj;
+    std::vector<uint16_t> tcid;
+    uint64_t list_rows = 0;
     // tuning
-    int block = 256, chunk = 128, use_queue = 1;
+    int block = 256, chunk = 128, use_queue = 1, kernel = SA_KERNEL_RECORDS;
     // device
     int device = -1, num_sms = 0;
     void *d_hdr = nullptr, *d_cat_word = nullptr, *d_catM = nullptr, *d_catMd = nullptr, *d_gamma = nullptr;
@@ -92,6 +98,8 @@ struct sa_heom {
     void *d_coef_row_d = nullptr, *d_coef_col_d = nullptr, *d_lut = nullptr, *d_lut_off = nullptr;
     void* d_chunk = nullptr;
     void *d_vdesc = nullptr, *d_drecA = nullptr, *d_drecS = nullptr;
+    void *d_lvd = nullptr, *d_lvj = nullptr, *d_rbase = nullptr, *d_tidx = nullptr, *d_tcid = nullptr;
+    void* d_lcoef = nullptr;
     unsigned int* d_err = nullptr;
     void* d_work[3] = {nullptr, nullptr, nullptr};  // acc, xa, xb
     unsigned int* d_queue = nullptr;
@@ -101,7 +109,7 @@ struct sa_heom {
     double* d_rho0 = nullptr;
     cudaStream_t cap = nullptr;
     size_t state_bytes = 0, side_off = 0;
-    LaunchCfg cfg{256, 128, 1, 1};
+    LaunchCfg cfg{256, 128, 1, 1, SA_KERNEL_RECORDS};
     std::map<std::tuple<const void*, uint64_t, int64_t>, cudaGraphExec_t> graphs;
 };
 
@@ -192,6 +200,169 @@ void build_items(sa_heom* h) {
     }
 }
 
+// Term lists of the list kernel.  For every work item: its variables in lane
+// order (the physical representative left out in SA_FP32_AUX mode, where the
+// FP64 kernel integrates it), sorted by hierarchy-term count, longest first;
+// per variable the operand-area indices of its commutator term and its
+// diagonal class; per round of 32 lanes T rows of 32 (target, coefficient
+// slot) entries, T the round's longest list, short lists padded with the zero
+// slot.  Two passes over the items (sizes, then contents), each in parallel.
+struct ListItem {
+    std::vector<uint32_t> order;     // lane order: item-local variable indices
+    std::vector<uint32_t> desc;      // per item-local variable: l | a << 10 | b << 21
+    std::vector<uint8_t> cls;        // per item-local variable: j | class << 5
+    std::vector<uint32_t> off, cnt;  // per item-local variable: its terms
+    std::vector<uint32_t> tix;
+    std::vector<uint16_t> tsl;
+};
+
+void list_item(const sa_heom* h, const ItemDesc& d, ListItem& W) {
+    int opR, opC, opZ, opZero;
+    list_operand_layout(h->chunk, &opR, &opC, &opZ, &opZero);
+    const bool side64 = h->precision == SA_FP32_AUX;
+    W.desc.assign(d.nv, 0u);
+    W.cls.assign(d.nv, 0);
+    W.cnt.assign(d.nv, 0u);
+    W.order.clear();
+    std::vector<uint32_t> tv;  // per term: item-local variable
+    W.tix.clear();
+    W.tsl.clear();
+    for (uint32_t j = 0; j < d.np; ++j) {
+        const PatHdr& H = h->hdr[d.p0 + j];
+        const int G = H.G;
+        const uint32_t pl = H.var_off - d.v0, cb = H.cat_off - d.c0;
+        const bool skip = side64 && H.tier == 0;
+        auto put = [&](int64_t loc, uint32_t a, uint32_t b, uint32_t c) {
+            const uint32_t l = pl + uint32_t(loc);
+            W.desc[l] = l | (a << 10) | (b << 21);
+            W.cls[l] = uint8_t(j | (c << 5));
+            if (!skip) W.order.push_back(l);
+        };
+        put(loc_Z(), uint32_t(opZ) + j, uint32_t(opZero), 3);
+        for (int q = 1; q <= G; ++q) {
+            put(loc_X(G, q), pl, uint32_t(opR) + cb + q - 1, 1);
+            put(loc_Y(G, q), uint32_t(opC) + cb + q - 1, pl, 2);
+            put(loc_P(G, q), pl + G + q, pl + q, 0);
+            for (int r = 1; r <= G; ++r)
+                if (r != q) put(loc_S(G, q, r), pl + G + r, pl + q, 0);
+            const int tr = (h->cat_word[H.cat_off + q - 1] >> 15) & 31;
+            if (tr != 31) put(loc_T(G, tr), pl + G + q, pl + q, 0);
+        }
+        if (skip) continue;
+        const int inst = H.inst;
+        const uint32_t vb = uint32_t(h->var_begin[inst]);
+        const int64_t p = int64_t(d.p0 + j) - int64_t(h->instdev[inst].pat_begin);
+        for_each_term(h->inst[inst], p, [&](int64_t loc, int kind, int64_t src, uint32_t packed, int side) {
+            const int cid = int(packed >> 23);
+            if (kind == 3 && side == 1) return;  // folded into the row term's coefficient
+            const int slot = kind == 3 ? 2 * kCoefPerInst + cid : side * kCoefPerInst + cid;
+            const uint32_t l = pl + uint32_t(loc);
+            tv.push_back(l);
+            W.tix.push_back(vb + uint32_t(src));
+            W.tsl.push_back(uint16_t(slot));
+            ++W.cnt[l];
+        });
+    }
+    // terms grouped by variable (counting sort, stable)
+    W.off.assign(d.nv + 1, 0u);
+    for (uint32_t l = 0; l < d.nv; ++l) W.off[l + 1] = W.off[l] + W.cnt[l];
+    std::vector<uint32_t> pos(W.off.begin(), W.off.end() - 1);
+    std::vector<uint32_t> ix(W.tix.size());
+    std::vector<uint16_t> sl(W.tsl.size());
+    for (size_t t = 0; t < tv.size(); ++t) {
+        const uint32_t k = pos[tv[t]]++;
+        ix[k] = W.tix[t];
+        sl[k] = W.tsl[t];
+    }
+    W.tix.swap(ix);
+    W.tsl.swap(sl);
+    std::stable_sort(W.order.begin(), W.order.end(), [&](uint32_t x, uint32_t y) { return W.cnt[x] > W.cnt[y]; });
+}
+
+uint64_t list_item_rows(const ListItem& W) {
+    uint64_t rows = 0;
+    for (size_t i = 0; i < W.order.size(); i += 32) rows += W.cnt[W.order[i]];
+    return rows;
+}
+
+int build_lists(sa_heom* h) {
+    const size_t ni = h->items.size();
+    std::vector<uint32_t> nrounds(ni + 1, 0);
+    std::vector<uint64_t> nrows(ni + 1, 0);
+#pragma omp parallel
+    {
+        ListItem W;
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t c = 0; c < int64_t(ni); ++c) {
+            list_item(h, h->items[c], W);
+            nrounds[c] = uint32_t((W.order.size() + 31) / 32);
+            nrows[c] = list_item_rows(W);
+        }
+    }
+    // exclusive prefix sums
+    uint64_t rr = 0, rw = 0;
+    for (size_t c = 0; c < ni; ++c) {
+        const uint64_t a = nrounds[c], b = nrows[c];
+        h->items[c].r0 = uint32_t(rr);
+        nrounds[c] = uint32_t(rr);
+        nrows[c] = rw;
+        rr += a;
+        rw += b;
+    }
+    if (rr >= (uint64_t(1) << 32) || rw >= (uint64_t(1) << 32))
+        return fail(SA_ERR_UNSUPPORTED, "term lists exceed 32-bit row indices");
+    nrounds[ni] = uint32_t(rr);
+    nrows[ni] = rw;
+    h->list_rows = rw;
+    try {
+        h->lvd.assign(size_t(h->nvar), 0u);
+        h->lvj.assign(size_t(h->nvar), 0);
+        h->rbase.assign(rr + 1, 0u);
+        h->tidx.assign(rw * 32, 0u);
+        h->tcid.assign(rw * 32, 0);
+    } catch (const std::bad_alloc&) {
+        return fail(SA_ERR_OOM, "host memory for the term lists");
+    }
+    h->rbase[rr] = uint32_t(rw);
+#pragma omp parallel
+    {
+        ListItem W;
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t c = 0; c < int64_t(ni); ++c) {
+            ItemDesc& d = h->items[c];
+            list_item(h, d, W);
+            d.nl = uint32_t(W.order.size());
+            uint64_t row = nrows[c];
+            uint32_t rho = nrounds[c];
+            for (size_t i0 = 0; i0 < W.order.size(); i0 += 32, ++rho) {
+                h->rbase[rho] = uint32_t(row);
+                const uint32_t T = W.cnt[W.order[i0]];
+                for (uint32_t u = 0; u < 32; ++u) {
+                    const size_t i = i0 + u;
+                    const uint32_t l = i < W.order.size() ? W.order[i] : 0u;
+                    const uint32_t n = i < W.order.size() ? W.cnt[l] : 0u;
+                    if (i < W.order.size()) {
+                        h->lvd[d.v0 + i] = W.desc[l];
+                        h->lvj[d.v0 + i] = W.cls[l];
+                    }
+                    for (uint32_t t = 0; t < T; ++t) {
+                        const size_t e = size_t(row + t) * 32 + u;
+                        if (t < n) {
+                            h->tidx[e] = W.tix[W.off[l] + t];
+                            h->tcid[e] = W.tsl[W.off[l] + t];
+                        } else {
+                            h->tidx[e] = d.v0;
+                            h->tcid[e] = uint16_t(kListCoefZero);
+                        }
+                    }
+                }
+                row += T;
+            }
+        }
+    }
+    return SA_OK;
+}
+
 // Decoded connection records: the batch-global indices the aligned accessor
 // resolves to for each kind of variable, and the small remap fields.
 void decode_records(sa_heom* h) {
@@ -211,18 +382,66 @@ void decode_records(sa_heom* h) {
     }
 }
 
+// Per-instance coefficient table of the list kernel: row, column and
+// row + column coefficients, then zeros.
+template <typename V>
+std::vector<V> list_coefficients(const sa_heom* h) {
+    std::vector<V> t(size_t(2) * kListCoefStride * h->count, V(0));
+    for (int i = 0; i < h->count; ++i) {
+        V* o = &t[size_t(2) * kListCoefStride * i];
+        const double* r = &h->coef_row_d[size_t(2) * kCoefPerInst * i];
+        const double* c = &h->coef_col_d[size_t(2) * kCoefPerInst * i];
+        for (int k = 0; k < 2 * kCoefPerInst; ++k) {
+            o[k] = V(r[k]);
+            o[2 * kCoefPerInst + k] = V(c[k]);
+            o[4 * kCoefPerInst + k] = V(r[k] + c[k]);
+        }
+    }
+    return t;
+}
+
+void free_lists(sa_heom* h) {
+    void** ptrs[] = {&h->d_lvd, &h->d_lvj, &h->d_rbase, &h->d_tidx, &h->d_tcid};
+    for (void** p : ptrs) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+}
+
 int apply_tuning(sa_heom* h) {
     build_items(h);
     h->cfg.block = h->block;
     h->cfg.chunk = h->chunk;
     h->cfg.use_queue = h->use_queue;
+    h->cfg.kernel = h->kernel;
     const uint32_t nchunks = uint32_t(h->items.size());
+    if (h->kernel == SA_KERNEL_LISTS) {
+        const int rc = build_lists(h);
+        if (rc) return rc;
+    }
     if (h->host_only) return SA_OK;
     if (h->d_chunk) cudaFree(h->d_chunk);
     if (h->d_vdesc) cudaFree(h->d_vdesc);
     h->d_chunk = h->d_vdesc = nullptr;
+    free_lists(h);
     int rc = upload(&h->d_chunk, h->items);
     if (!rc) rc = upload(&h->d_vdesc, h->vdesc);
+    if (!rc && h->kernel == SA_KERNEL_LISTS) {
+        if (!h->d_lcoef)
+            rc = h->precision == SA_FP64 ? upload(&h->d_lcoef, list_coefficients<double>(h))
+                                         : upload(&h->d_lcoef, list_coefficients<float>(h));
+        if (!rc) rc = upload(&h->d_lvd, h->lvd);
+        if (!rc) rc = upload(&h->d_lvj, h->lvj);
+        if (!rc) rc = upload(&h->d_rbase, h->rbase);
+        if (!rc) rc = upload(&h->d_tidx, h->tidx);
+        if (!rc) rc = upload(&h->d_tcid, h->tcid);
+        // the host copies are not needed again
+        std::vector<uint32_t>().swap(h->lvd);
+        std::vector<uint8_t>().swap(h->lvj);
+        std::vector<uint32_t>().swap(h->tidx);
+        std::vector<uint16_t>().swap(h->tcid);
+        if (rc) free_lists(h);
+    }
     if (rc) return rc;
     int occ = 0;
     CK(stage_occupancy(h->cfg, h->precision == SA_FP64, &occ));
@@ -242,7 +461,8 @@ void free_device(sa_heom* h) {
     void* ptrs[] = {h->d_hdr, h->d_cat_word, h->d_catM, h->d_catMd, h->d_gamma, h->d_rec, h->d_inst, h->d_theta,
                     h->d_coef_row, h->d_coef_col, h->d_coef_row_d, h->d_coef_col_d, h->d_lut, h->d_lut_off,
                     h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0,
-                    h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS};
+                    h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS, h->d_lvd, h->d_lvj, h->d_rbase,
+                    h->d_tidx, h->d_tcid, h->d_lcoef};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -278,6 +498,12 @@ StageLaunch base_launch(const sa_heom* h) {
     s.coef_col_d = h->d_coef_col_d;
     s.lut = h->d_lut;
     s.lut_off = h->d_lut_off;
+    s.lvd = h->d_lvd;
+    s.lvj = h->d_lvj;
+    s.rbase = h->d_rbase;
+    s.tidx = h->d_tidx;
+    s.tcid = h->d_tcid;
+    s.lcoef = h->d_lcoef;
     s.nchunks = uint32_t(h->items.size());
     s.err = h->d_err;
     s.ninst = h->count;
@@ -648,6 +874,25 @@ int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, i
     return SA_OK;
 }
 
+int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* lvd, uint8_t* lvj,
+                       uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz) {
+    if (!h || !sizes) return fail(SA_ERR_INVALID_ARG, "handle and sizes required");
+    if (!h->host_only || h->kernel != SA_KERNEL_LISTS)
+        return fail(SA_ERR_STATE, "term lists are kept on the host only for host-only handles with SA_KERNEL_LISTS");
+    sizes[0] = int64_t(h->items.size());
+    sizes[1] = int64_t(h->rbase.size()) - 1;
+    sizes[2] = int64_t(h->list_rows);
+    sizes[3] = h->nvar;
+    if (items) std::memcpy(items, h->items.data(), h->items.size() * sizeof(ItemDesc));
+    if (lvd) std::copy(h->lvd.begin(), h->lvd.end(), lvd);
+    if (lvj) std::copy(h->lvj.begin(), h->lvj.end(), lvj);
+    if (rbase) std::copy(h->rbase.begin(), h->rbase.end(), rbase);
+    if (tidx) std::copy(h->tidx.begin(), h->tidx.end(), tidx);
+    if (tcid) std::copy(h->tcid.begin(), h->tcid.end(), tcid);
+    if (opz) list_operand_layout(h->chunk, &opz[0], &opz[1], &opz[2], &opz[3]);
+    return SA_OK;
+}
+
 int sa_heom_state_bytes(const sa_heom* h, size_t* bytes) {
     if (!h || !bytes) return fail(SA_ERR_INVALID_ARG, "handle, out");
     *bytes = h->state_bytes;
@@ -868,6 +1113,32 @@ int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue) {
     return apply_tuning(h);
 }
 
+int sa_heom_set_kernel(sa_heom* h, int kernel) {
+    if (!h) return fail(SA_ERR_INVALID_ARG, "null handle");
+    if (kernel != SA_KERNEL_RECORDS && kernel != SA_KERNEL_LISTS)
+        return fail(SA_ERR_INVALID_ARG, "kernel must be SA_KERNEL_RECORDS or SA_KERNEL_LISTS");
+    const int old = h->kernel;
+    h->kernel = kernel;
+    const int rc = apply_tuning(h);
+    if (rc && rc != SA_ERR_INVALID_ARG) {
+        // keep the handle usable with the variant it had
+        const std::string why = g_err;
+        h->kernel = old;
+        apply_tuning(h);
+        g_err = why;
+    }
+    return rc;
+}
+
+int sa_heom_get_tuning(const sa_heom* h, int* out) {
+    if (!h || !out) return fail(SA_ERR_INVALID_ARG, "handle and out required");
+    out[0] = h->block;
+    out[1] = h->chunk;
+    out[2] = h->use_queue;
+    out[3] = h->kernel;
+    return SA_OK;
+}
+
 int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     int rc = check_device(h);
     if (rc) return rc;
@@ -878,14 +1149,16 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     // (items smaller than the largest pattern or above the shared-memory
     // budget are skipped by set_tuning)
     float best_ms = 1e30f;
-    int bb = h->block, bc = h->chunk, bq = h->use_queue;
+    int bb = h->block, bc = h->chunk, bq = h->use_queue, bk = h->kernel;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    for (int k : {int(SA_KERNEL_RECORDS), int(SA_KERNEL_LISTS)})
     for (int q = 0; q < 2; ++q)
         for (int b : blocks)
             for (int c : chunks) {
                 if (c < h->max_u) continue;
+                h->kernel = k;
                 if (sa_heom_set_tuning(h, b, c, q)) continue;
                 // warm-up + timed: two RK4 steps
                 for (int rep = 0; rep < 2; ++rep) {
@@ -906,10 +1179,12 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
                     bb = b;
                     bc = c;
                     bq = q;
+                    bk = k;
                 }
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    h->kernel = bk;
     rc = sa_heom_set_tuning(h, bb, bc, bq);
     if (rc) return rc;
     if (best) {

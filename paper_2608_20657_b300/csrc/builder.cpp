@@ -400,85 +400,21 @@ int build_instance(const sa_params& p, HostInstance& hi, std::string& err) {
 int64_t expand_terms(const HostInstance& hi, int64_t* var, int64_t* src, int32_t* kk, int32_t* nn, int32_t* dd,
                      int32_t* side) {
     int64_t cnt = 0;
-    auto emit = [&](int64_t v, int64_t s, uint32_t packed, int sd) {
-        if (var) {
-            int cid = int(packed >> 23);
-            var[cnt] = v;
-            src[cnt] = s;
-            kk[cnt] = (cid >> 1) / kCoefN;
-            nn[cnt] = (cid >> 1) % kCoefN;
-            dd[cnt] = (cid & 1) ? +1 : -1;
-            side[cnt] = sd;
-        }
-        ++cnt;
-    };
     for (int64_t i = 0; i < hi.P; ++i) {
-        int G = hi.G[i];
-        int64_t base = int64_t(hi.var_off[i]);
-        const uint32_t* cw = &hi.cat_word[hi.cat_off[i]];
-        const Record* R = &hi.rec[hi.rec_off[i]];
-        const int8_t* tr = &hi.cat_trank[hi.cat_off[i]];
-        auto target_index = [&](const Record& rc, int rowc, int colc, bool same) -> int64_t {
-            // rowc / colc: target category (0 = cavity); same: P entry
-            uint32_t pk = rc.packed;
-            int tstar = pk & 31, Gp = (pk >> 5) & 31, trs = (pk >> 10) & 31;
-            (void)tstar;
-            int64_t loc;
-            if (rowc == 0 && colc == 0) loc = loc_Z();
-            else if (colc == 0) loc = loc_X(Gp, rowc);
-            else if (rowc == 0) loc = loc_Y(Gp, colc);
-            else if (same) loc = loc_P(Gp, rowc);
-            else if (rowc != colc) loc = loc_S(Gp, rowc, colc);
-            else loc = loc_T(Gp, trs);
-            return int64_t(rc.target) + loc;
-        };
-        auto tau_of = [](uint32_t pk, int moved, int rr) {
-            int ipos = (pk >> 16) & 31, ins = (pk >> 21) & 1, del = (pk >> 22) & 1;
-            return rr - ((del && rr > moved) ? 1 : 0) + ((ins && rr >= ipos) ? 1 : 0);
-        };
-        // every variable: (kind, q, r) in canonical order
-        auto each_var = [&](int kind, int q, int r, int64_t loc) {
-            int row = 0, col = 0;
-            bool same = false;
-            if (kind == 1) row = q;
-            if (kind == 2) col = q;
-            if (kind == 3) { row = q; col = q; same = true; }
-            if (kind == 4) { row = q; col = r; }
-            if (kind == 5) { row = q; col = q; }
-            if (row) {
-                uint32_t w = cw[row - 1];
-                int rs = w & 1023, nr = (w >> 10) & 31;
-                for (int j = 0; j < nr; ++j) {
-                    const Record& rc = R[rs + j];
-                    bool raise = ((rc.packed >> 23) & 1) != 0;
-                    if (same && raise) continue;  // cancels against the column raise
-                    int tstar = rc.packed & 31;
-                    int cc = col == 0 ? 0 : (same ? tstar : tau_of(rc.packed, row, col));
-                    emit(base + loc, target_index(rc, tstar, cc, same), rc.packed, 0);
-                }
+        const int64_t base = int64_t(hi.var_off[i]);
+        for_each_term(hi, i, [&](int64_t loc, int kind, int64_t s, uint32_t packed, int sd) {
+            (void)kind;
+            if (var) {
+                const int cid = int(packed >> 23);
+                var[cnt] = base + loc;
+                src[cnt] = s;
+                kk[cnt] = (cid >> 1) / kCoefN;
+                nn[cnt] = (cid >> 1) % kCoefN;
+                dd[cnt] = (cid & 1) ? +1 : -1;
+                side[cnt] = sd;
             }
-            if (col) {
-                uint32_t w = cw[col - 1];
-                int rs = w & 1023, nr = (w >> 10) & 31;
-                for (int j = 0; j < nr; ++j) {
-                    const Record& rc = R[rs + j];
-                    bool raise = ((rc.packed >> 23) & 1) != 0;
-                    if (same && raise) continue;
-                    int tstar = rc.packed & 31;
-                    int rr = row == 0 ? 0 : (same ? tstar : tau_of(rc.packed, col, row));
-                    emit(base + loc, target_index(rc, rr, tstar, same), rc.packed, 1);
-                }
-            }
-        };
-        each_var(0, 0, 0, loc_Z());
-        for (int q = 1; q <= G; ++q) {
-            each_var(1, q, 0, loc_X(G, q));
-            each_var(2, q, 0, loc_Y(G, q));
-            each_var(3, q, 0, loc_P(G, q));
-            for (int r = 1; r <= G; ++r)
-                if (r != q) each_var(4, q, r, loc_S(G, q, r));
-            if (tr[q - 1] >= 0) each_var(5, q, 0, loc_T(G, tr[q - 1]));
-        }
+            ++cnt;
+        });
     }
     return cnt;
 }

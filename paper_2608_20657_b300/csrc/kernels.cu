@@ -80,6 +80,13 @@ template <typename T> struct StageParams {
     const double2* __restrict__ coef_col_d;
     const uint16_t* __restrict__ lut;       // (kind | q << 3 | r << 8) per (G, local index)
     const uint32_t* __restrict__ lut_off;   // per G
+    // list kernel
+    const uint32_t* __restrict__ lvd;       // per lane variable: l | a << 10 | b << 21 (operand-area indices)
+    const uint8_t* __restrict__ lvj;        // per lane variable: pattern j | diagonal class << 5
+    const uint32_t* __restrict__ rbase;     // first term row of every round of 32 lanes (+ sentinel)
+    const uint32_t* __restrict__ tidx;      // term rows of 32: batch-global target index
+    const uint16_t* __restrict__ tcid;      // term rows of 32: coefficient slot in the instance's list table
+    const C* __restrict__ lcoef;            // per instance kListCoefStride slots
     uint32_t nchunks;
     int chunk;                              // variable capacity of one work item
     const C* x_in;                          // stage input (gathered)
@@ -491,6 +498,221 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
     }
 }
 
+// ---- list kernel -----------------------------------------------------------
+// Per-warp shared memory of the list kernel.  The operand area op[] holds the
+// item's stage-input slice (chunk entries), then the grouped row sums R_q and
+// column sums C_q of its categories, the Z sums of its patterns and one zero:
+// every commutator term of Eq. HS is diag * v - i g (op[a] - op[b]) with
+// host-chosen operand indices a, b.
+template <typename T> struct ListSmem {
+    using C = typename Cx<T>::t;
+    C* op;       // chunk + 2 nc + kItemPats + 1 entries
+    C* y;        // RK4 state slice
+    C* acc;      // RK4 accumulator slice
+    C* gam;      // Gamma_Lambda per pattern
+    PatHdr* ph;  // pattern headers (kItemPats + 1)
+    PatConst<T>* pc;
+    uint32_t* cw;
+    T* cM;
+};
+
+__host__ __device__ __forceinline__ int list_ncat(int item) { return item / 4 + 8; }
+// operand-area layout (host and device): x slice, R, C, Z sums, zero
+__host__ __device__ __forceinline__ int list_opR(int item) { return item; }
+__host__ __device__ __forceinline__ int list_opC(int item) { return item + list_ncat(item); }
+__host__ __device__ __forceinline__ int list_opZ(int item) { return item + 2 * list_ncat(item); }
+__host__ __device__ __forceinline__ int list_opZero(int item) { return item + 2 * list_ncat(item) + kItemPats; }
+
+template <typename T>
+__host__ __device__ __forceinline__ size_t list_smem_bytes(int item) {
+    const size_t cs = 2 * sizeof(T);
+    const size_t nc = size_t(list_ncat(item));
+    return al16(cs * (list_opZero(item) + 1)) + 2 * al16(cs * item) + al16(cs * kItemPats) +
+           al16(sizeof(PatHdr) * (kItemPats + 1)) + al16(sizeof(PatConst<T>) * kItemPats) + al16(4 * nc) +
+           al16(sizeof(T) * nc);
+}
+
+template <typename T>
+__device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
+    using C = typename Cx<T>::t;
+    const int nc = list_ncat(item);
+    ListSmem<T> W;
+    W.op = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * (list_opZero(item) + 1));
+    W.y = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * item);
+    W.acc = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * item);
+    W.gam = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * kItemPats);
+    W.ph = reinterpret_cast<PatHdr*>(p);  p += al16(sizeof(PatHdr) * (kItemPats + 1));
+    W.pc = reinterpret_cast<PatConst<T>*>(p); p += al16(sizeof(PatConst<T>) * kItemPats);
+    W.cw = reinterpret_cast<uint32_t*>(p); p += al16(4 * nc);
+    W.cM = reinterpret_cast<T*>(p);
+    return W;
+}
+
+// One warp per work item, like stage_kernel, but the hierarchy terms come
+// from host-resolved lists: the lanes take the item's variables in rounds of
+// 32 (sorted by term count, so a round's lanes run the same number of terms),
+// and term t of a round is one coalesced row of 32 (target index,
+// coefficient slot) entries; padded entries name a zero coefficient.  The
+// commutator, damping and loss use the same formula for every kind of
+// variable, with operands and the diagonal class chosen by the host.
+template <typename T, bool FP64SIDE>
+__global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int chunk = P.chunk;
+    const ListSmem<T> S = carve_list<T>(smem + size_t(wib) * list_smem_bytes<T>(chunk), chunk);
+    C* const opR = S.op + list_opR(chunk);
+    C* const opC = S.op + list_opC(chunk);
+    C* const opZ = S.op + list_opZ(chunk);
+    if (lane == 0) S.op[list_opZero(chunk)] = mk(T(0), T(0));
+    const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
+    unsigned int it = blockIdx.x * (blockDim.x >> 5) + wib;
+    const T dtT = T(P.dt);
+    const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
+    for (;;) {
+        unsigned int c;
+        if (P.use_queue) {
+            unsigned int t = 0;
+            if (lane == 0) t = atomicAdd(P.queue, 1u);
+            c = __shfl_sync(0xffffffffu, t, 0);
+        } else {
+            c = it;
+            it += nwarps;
+        }
+        if (c >= P.nchunks) break;
+        const ItemDesc d = P.items[c];
+        const int np = int(d.np);
+        const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0, ncat = d.ncat;
+        // ---- stage the item
+        for (uint32_t i = lane; i < nv; i += 32) {
+            S.op[i] = P.x_in[v0 + i];
+            if (P.stage > 0) {
+                S.y[i] = P.y[v0 + i];
+                S.acc[i] = P.acc[v0 + i];
+            }
+        }
+        for (int j = lane; j <= np; j += 32) S.ph[j] = P.hdr[d.p0 + j];
+        for (int j = lane; j < np; j += 32) {
+            S.gam[j] = __ldg(P.gamma + d.p0 + j);
+            const uint32_t inst = P.hdr[d.p0 + j].inst;
+            const InstDev& I = P.inst[inst];
+            PatConst<T> pc;
+            pc.g = sizeof(T) == 8 ? T(I.g) : T(I.gf);
+            pc.det = sizeof(T) == 8 ? T(I.detuning) : T(I.detf);
+            pc.kap = sizeof(T) == 8 ? T(I.kappa) : T(I.kappaf);
+            pc.coef_base = inst * uint32_t(kListCoefStride);
+            S.pc[j] = pc;
+        }
+        for (uint32_t cl = lane; cl < ncat; cl += 32) {
+            S.cw[cl] = __ldg(P.cat_word + c0 + cl);
+            S.cM[cl] = __ldg(P.cat_M + c0 + cl);
+        }
+        __syncwarp();
+        // ---- grouped sums per category (Eqs. grouped-row-sum,
+        // grouped-column-sum) and per pattern (Eq. HZ)
+        for (uint32_t cl = lane; cl < ncat; cl += 32) {
+            int lo = 0, hi = np - 1;  // owning pattern: last j with cat_off <= c0 + cl
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (S.ph[mid].cat_off - c0 <= cl) lo = mid;
+                else hi = mid - 1;
+            }
+            const PatHdr h = S.ph[lo];
+            const int G = h.G;
+            const int cb = int(h.cat_off - c0);
+            const int q = int(cl) - cb + 1;
+            const C* xp = S.op + (h.var_off - v0);
+            const T Mq = S.cM[cl];
+            C Rs = xp[2 * G + q];
+            if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((S.cw[cl] >> 15) & 31)], Rs);
+            C Cq = Rs;
+            for (int e2 = 1; e2 <= G; ++e2) {
+                if (e2 == q) continue;
+                const T Mb = S.cM[cb + e2 - 1];
+                Rs = caxpy(Mb, xp[loc_S_d(G, q, e2)], Rs);
+                Cq = caxpy(Mb, xp[loc_S_d(G, e2, q)], Cq);
+            }
+            opR[cl] = Rs;
+            opC[cl] = Cq;
+        }
+        for (int j = lane; j < np; j += 32) {
+            const PatHdr h = S.ph[j];
+            const int G = h.G;
+            const int cb = int(h.cat_off - c0);
+            const C* xp = S.op + (h.var_off - v0);
+            C zs = mk(T(0), T(0));
+            for (int q = 1; q <= G; ++q) zs = caxpy(S.cM[cb + q - 1], csub(xp[q], xp[G + q]), zs);
+            opZ[j] = zs;
+        }
+        __syncwarp();
+        // ---- the lanes' variables, one round of 32 at a time
+        const uint32_t nl = d.nl;
+        const uint32_t* __restrict__ rb = P.rbase + d.r0;
+        const C* __restrict__ X = P.x_in;
+        for (uint32_t i0 = 0, rho = 0; i0 < nl; i0 += 32, ++rho) {
+            const uint32_t i = i0 + lane;
+            const bool on = i < nl;
+            // lanes past the end take operand 0 and the zero-coefficient rows
+            const uint32_t w0 = on ? __ldg(P.lvd + v0 + i) : 0u;
+            const uint32_t w1 = on ? uint32_t(__ldg(P.lvj + v0 + i)) : 0u;
+            const uint32_t l = w0 & 1023u, a = (w0 >> 10) & 2047u, b = w0 >> 21;
+            const int j = int(w1 & 31u), cls = int(w1 >> 5);
+            const C v = S.op[l];
+            const C gam = S.gam[j];
+            const PatConst<T> pc = S.pc[j];
+            // diagonal: -Gamma, the cavity loss (1/2 per cavity index) and
+            // -/+ i detuning for X / Y (classes: 0 P S T, 1 X, 2 Y, 3 Z)
+            const T lossf = cls == 0 ? T(0) : (cls == 3 ? T(1) : T(0.5));
+            const T dim = cls == 1 ? -pc.det : (cls == 2 ? pc.det : T(0));
+            const C diag = mk(-(gam.x + lossf * pc.kap), dim - gam.y);
+            const C t = csub(S.op[a], S.op[b]);
+            C dv = mk(pc.g * t.y, -pc.g * t.x);
+            dv = cfma(diag, v, dv);
+            // hierarchy terms (Eqs. uvar-up, uvar-down)
+            const C* __restrict__ cf = P.lcoef + pc.coef_base;
+            const uint32_t r0 = __ldg(rb + rho), r1 = __ldg(rb + rho + 1);
+            const uint32_t* __restrict__ ti = P.tidx + size_t(r0) * 32 + lane;
+            const uint16_t* __restrict__ tc = P.tcid + size_t(r0) * 32 + lane;
+            const int nt = int(r1 - r0);
+            int t2 = 0;
+            for (; t2 + 4 <= nt; t2 += 4) {
+                uint32_t ix[4], cx[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    ix[u] = __ldg(ti + (t2 + u) * 32);
+                    cx[u] = __ldg(tc + (t2 + u) * 32);
+                }
+                C xv[4], cv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    xv[u] = __ldg(X + ix[u]);
+                    cv[u] = __ldg(cf + cx[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) dv = cfma(cv[u], xv[u], dv);
+            }
+            for (; t2 < nt; ++t2) dv = cfma(__ldg(cf + __ldg(tc + t2 * 32)), __ldg(X + __ldg(ti + t2 * 32)), dv);
+            if (on) {
+                const uint32_t vg = v0 + l;
+                if (P.stage < 0) {
+                    P.x_out[vg] = dv;
+                } else if (P.stage == 0) {
+                    P.acc[vg] = dv;
+                    P.x_out[vg] = caxpy(aT, dv, v);  // x_in is y in the first stage
+                } else if (P.stage == 3) {
+                    P.y_out[vg] = caxpy(dtT / T(6), cadd(S.acc[l], dv), S.y[l]);
+                } else {
+                    P.acc[vg] = caxpy(T(2), dv, S.acc[l]);
+                    P.x_out[vg] = caxpy(aT, dv, S.y[l]);
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // SA_FP32_AUX: the physical representative (empty pattern) of every instance
 // in FP64, one thread per variable: FP64 side copies of its own variables,
 // the tier-1 targets gathered from the FP32 stage input, FP64 coefficients and
@@ -597,15 +819,26 @@ __global__ void init_rho0_kernel(const InstDev* __restrict__ inst, int ninst, co
 
 // ---- host launch wrappers (called from api.cu) -----------------------------
 
-size_t stage_smem_bytes(int item, int block, bool fp64) {
-    const size_t w = fp64 ? warp_smem_bytes<double>(item) : warp_smem_bytes<float>(item);
+size_t stage_smem_bytes(int item, int block, bool fp64, int kernel) {
+    size_t w;
+    if (kernel == SA_KERNEL_LISTS) w = fp64 ? list_smem_bytes<double>(item) : list_smem_bytes<float>(item);
+    else w = fp64 ? warp_smem_bytes<double>(item) : warp_smem_bytes<float>(item);
     return w * size_t(block / 32);
+}
+
+// operand-area offsets of the list kernel for a given item capacity
+void list_operand_layout(int item, int* opR, int* opC, int* opZ, int* opZero) {
+    *opR = list_opR(item);
+    *opC = list_opC(item);
+    *opZ = list_opZ(item);
+    *opZero = list_opZero(item);
 }
 
 template <typename T, bool SIDE>
 static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int ninst, cudaStream_t st) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, sizeof(T) == 8);
-    stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, sizeof(T) == 8, cfg.kernel);
+    if (cfg.kernel == SA_KERNEL_LISTS) list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+    else stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     if (SIDE) {
         const int threads = ninst * kSideSlots;
         rho0_kernel<T><<<(threads + 127) / 128, 128, 0, st>>>(p, ninst);
@@ -634,6 +867,12 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.coef_col_d = static_cast<const double2*>(s.coef_col_d);
     p.lut = static_cast<const uint16_t*>(s.lut);
     p.lut_off = static_cast<const uint32_t*>(s.lut_off);
+    p.lvd = static_cast<const uint32_t*>(s.lvd);
+    p.lvj = static_cast<const uint8_t*>(s.lvj);
+    p.rbase = static_cast<const uint32_t*>(s.rbase);
+    p.tidx = static_cast<const uint32_t*>(s.tidx);
+    p.tcid = static_cast<const uint16_t*>(s.tcid);
+    p.lcoef = static_cast<const C*>(s.lcoef);
     p.nchunks = s.nchunks;
     p.chunk = cfg.chunk;
     p.x_in = static_cast<const C*>(s.x_in);
@@ -661,8 +900,15 @@ cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, 
 
 // Sets the dynamic shared-memory limit once for the largest chunk (outside
 // any stream capture) and returns the CTAs per SM for this configuration.
+template <class K>
+static cudaError_t occupancy_of(K kern, int block, size_t sm, int lim, int* blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, block, sm);
+}
+
 cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, fp64);
+    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, fp64, cfg.kernel);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -672,15 +918,12 @@ cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm)
         *blocks_per_sm = 0;
         return cudaSuccess;
     }
-    cudaError_t e;
-    if (fp64) {
-        e = cudaFuncSetAttribute(stage_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-        if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stage_kernel<double, false>, cfg.block, sm);
+    if (cfg.kernel == SA_KERNEL_LISTS) {
+        if (fp64) return occupancy_of(list_stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
+        return occupancy_of(list_stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
     }
-    e = cudaFuncSetAttribute(stage_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, stage_kernel<float, true>, cfg.block, sm);
+    if (fp64) return occupancy_of(stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
+    return occupancy_of(stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
 }
 
 cudaError_t launch_observables(const InstDev* inst, const double* theta, int ninst, const void* main64,

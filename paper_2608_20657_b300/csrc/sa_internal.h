@@ -111,10 +111,17 @@ struct DRecA {
 // one work item of the stage kernel (one warp): a run of consecutive
 // patterns and the ranges of their variables and categories
 struct ItemDesc {
-    uint32_t p0, np, v0, nv, c0, ncat, pad0, pad1;
+    uint32_t p0, np, v0, nv, c0, ncat;
+    uint32_t r0;  // list kernel: first round of 32 lanes in the round table
+    uint32_t nl;  // list kernel: variables the lanes take (the item's, less any integrated elsewhere)
 };
 constexpr int kItemPats = 32;     // patterns per work item (5-bit local index)
 constexpr int kMaxItemVars = 1024; // variables per work item (10-bit local index)
+// list kernel: coefficient slots per instance -- row coefficients, column
+// coefficients, row + column (the P_q lower terms), then one zero slot for
+// padded entries
+constexpr int kListCoefZero = 3 * kCoefPerInst;
+constexpr int kListCoefStride = 3 * kCoefPerInst + 8;
 
 // launch description shared by api.cu and kernels.cu (type-erased pointers)
 struct LaunchCfg {
@@ -122,6 +129,7 @@ struct LaunchCfg {
     int chunk;      // variable capacity of one work item
     int use_queue;  // 1: persistent grid + atomic work queue
     int grid;       // CTAs
+    int kernel;     // SA_KERNEL_RECORDS or SA_KERNEL_LISTS (include/sa_heom.h)
 };
 struct StageLaunch {
     const void* hdr; const void* cat_word; const void* cat_M; const void* gamma; const void* rec;
@@ -129,6 +137,7 @@ struct StageLaunch {
     const void* inst; const void* coef_row; const void* coef_col;
     const void* cat_Md; const void* coef_row_d; const void* coef_col_d;
     const void* lut; const void* lut_off;
+    const void* lvd; const void* lvj; const void* rbase; const void* tidx; const void* tcid; const void* lcoef;
     uint32_t nchunks;
     const void* x_in; void* x_out; const void* y; void* acc; void* y_out;
     const void* xs_in; void* xs_out; const void* ys; void* accs; void* ys_out;
@@ -151,5 +160,81 @@ inline int64_t loc_Y(int G, int q) { return G + q; }
 inline int64_t loc_P(int G, int q) { return 2 * G + q; }
 inline int64_t loc_S(int G, int q, int r) { return 3 * G + 1 + int64_t(q - 1) * (G - 1) + (r - 1) - (r > q ? 1 : 0); }
 inline int64_t loc_T(int G, int trank) { return int64_t(G + 1) * (G + 1) + trank; }
+
+// Hierarchy terms of the variables of pattern i (Eqs. uvar-up / uvar-down),
+// resolved through the connection records and the aligned accessor
+// (Eq. aligned-accessor).  emit(loc, kind, src, packed, side) is called once
+// per term: loc is the variable's local index in the pattern, kind 0..5 for
+// Z X Y P S T, src the instance-relative index of the target entry, packed
+// the record word (its coefficient id in bits 23..31) and side 0 for the row
+// delta, 1 for the column delta.  The terms of one variable are emitted
+// together.  The two raise terms of P_q cancel and are not emitted; its row
+// and column lower terms name the same target.
+template <class Emit>
+void for_each_term(const HostInstance& hi, int64_t i, Emit&& emit) {
+    const int G = hi.G[i];
+    const uint32_t* cw = &hi.cat_word[hi.cat_off[i]];
+    const Record* R = &hi.rec[hi.rec_off[i]];
+    const int8_t* tr = &hi.cat_trank[hi.cat_off[i]];
+    auto target_index = [&](const Record& rc, int rowc, int colc, bool same) -> int64_t {
+        // rowc / colc: target category (0 = cavity); same: P entry
+        const uint32_t pk = rc.packed;
+        const int Gp = (pk >> 5) & 31, trs = (pk >> 10) & 31;
+        int64_t loc;
+        if (rowc == 0 && colc == 0) loc = loc_Z();
+        else if (colc == 0) loc = loc_X(Gp, rowc);
+        else if (rowc == 0) loc = loc_Y(Gp, colc);
+        else if (same) loc = loc_P(Gp, rowc);
+        else if (rowc != colc) loc = loc_S(Gp, rowc, colc);
+        else loc = loc_T(Gp, trs);
+        return int64_t(rc.target) + loc;
+    };
+    auto tau_of = [](uint32_t pk, int moved, int rr) {
+        const int ipos = (pk >> 16) & 31, ins = (pk >> 21) & 1, del = (pk >> 22) & 1;
+        return rr - ((del && rr > moved) ? 1 : 0) + ((ins && rr >= ipos) ? 1 : 0);
+    };
+    auto each_var = [&](int kind, int q, int r, int64_t loc) {
+        int row = 0, col = 0;
+        bool same = false;
+        if (kind == 1) row = q;
+        if (kind == 2) col = q;
+        if (kind == 3) { row = q; col = q; same = true; }
+        if (kind == 4) { row = q; col = r; }
+        if (kind == 5) { row = q; col = q; }
+        if (row) {
+            const uint32_t w = cw[row - 1];
+            const int rs = w & 1023, nr = (w >> 10) & 31;
+            for (int j = 0; j < nr; ++j) {
+                const Record& rc = R[rs + j];
+                const bool raise = ((rc.packed >> 23) & 1) != 0;
+                if (same && raise) continue;  // cancels against the column raise
+                const int tstar = rc.packed & 31;
+                const int cc = col == 0 ? 0 : (same ? tstar : tau_of(rc.packed, row, col));
+                emit(loc, kind, target_index(rc, tstar, cc, same), rc.packed, 0);
+            }
+        }
+        if (col) {
+            const uint32_t w = cw[col - 1];
+            const int rs = w & 1023, nr = (w >> 10) & 31;
+            for (int j = 0; j < nr; ++j) {
+                const Record& rc = R[rs + j];
+                const bool raise = ((rc.packed >> 23) & 1) != 0;
+                if (same && raise) continue;
+                const int tstar = rc.packed & 31;
+                const int rr = row == 0 ? 0 : (same ? tstar : tau_of(rc.packed, col, row));
+                emit(loc, kind, target_index(rc, rr, tstar, same), rc.packed, 1);
+            }
+        }
+    };
+    each_var(0, 0, 0, loc_Z());
+    for (int q = 1; q <= G; ++q) {
+        each_var(1, q, 0, loc_X(G, q));
+        each_var(2, q, 0, loc_Y(G, q));
+        each_var(3, q, 0, loc_P(G, q));
+        for (int r = 1; r <= G; ++r)
+            if (r != q) each_var(4, q, r, loc_S(G, q, r));
+        if (tr[q - 1] >= 0) each_var(5, q, 0, loc_T(G, tr[q - 1]));
+    }
+}
 
 }  // namespace sa

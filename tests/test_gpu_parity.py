@@ -42,34 +42,43 @@ def _rhs_gpu(h, x):
     return h.download(dx)
 
 
+KERNELS = [S.SA_KERNEL_RECORDS, S.SA_KERNEL_LISTS]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("N,m,L", SMALL)
-def test_rhs_fp64(N, m, L):
+def test_rhs_fp64(N, m, L, kernel):
     """Eq. uvar-propagator: one right-hand side on a seeded random vector."""
     bath = _generic_bath(m, N + 7 * m + L)
     kw = dict(detuning=0.1, g=0.2, kappa=0.05)
     sa = oracle.SA(N, m, L, bath, **kw)
     h = S.Heom(S.make_params(N, m, L, bath, **kw))
+    h.set_kernel(kernel)
     x = W.random_state(sa.nvar, seed=N * 100 + L)
     assert rel_err(_rhs_gpu(h, x), sa.rhs(x)) <= 1e-13
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("N,m,L", SMALL[::2])
-def test_rhs_fp32(N, m, L):
+def test_rhs_fp32(N, m, L, kernel):
     bath = _generic_bath(m, N + 7 * m + L)
     kw = dict(detuning=0.1, g=0.2, kappa=0.05)
     sa = oracle.SA(N, m, L, bath, **kw)
     h = S.Heom(S.make_params(N, m, L, bath, **kw), precision=S.SA_FP32_AUX)
+    h.set_kernel(kernel)
     x = W.random_state(sa.nvar, seed=N * 100 + L).astype(np.complex64).astype(np.complex128)
     assert rel_err(_rhs_gpu(h, x), sa.rhs(x)) <= 2e-6
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("N,m,L", [(3, 2, 3), (10, 2, 6), (12, 3, 4), (40, 2, 7)])
-def test_rk4_steps_fp64(N, m, L):
+def test_rk4_steps_fp64(N, m, L, kernel):
     """Classical RK4 fused into the stage kernels: 40 steps vs the oracle."""
     bath = _generic_bath(m, N + 7 * m + L)
     kw = dict(detuning=0.1, g=0.2, kappa=0.05)
     sa = oracle.SA(N, m, L, bath, **kw)
     h = S.Heom(S.make_params(N, m, L, bath, **kw))
+    h.set_kernel(kernel)
     x = W.random_state(sa.nvar, seed=3, scale=0.1)
     st = h.new_state()
     h.upload(st, x)
@@ -112,11 +121,13 @@ def test_w3_fp32_population_error():
     assert err <= 1e-5
 
 
-def test_batch_matches_single_instances():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_batch_matches_single_instances(kernel):
     """A batch of uneven instances (w4 recipe) equals the oracle run of each
     instance: 30 RK4 steps from the upper-polariton start, FP64."""
     ws = W.batch_w4(24, seed=11)
     h = S.Heom([S.params_from(w) for w in ws])
+    h.set_kernel(kernel)
     st = h.new_state()
     h.init_state(st, np.stack([S.rho0_vars(w) for w in ws]))
     for _ in range(30):
@@ -130,11 +141,13 @@ def test_batch_matches_single_instances():
         assert rel_err(y[a:a + sa.nvar], ref) <= 1e-11, i
 
 
-def test_batch_fp32_population_error():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_batch_fp32_population_error(kernel):
     """Batched FP32-aux vs the FP64 oracle for a few w4 instances over 2000
     steps: populations within 1e-5."""
     ws = W.batch_w4(8, seed=5)
     h = S.Heom([S.params_from(w) for w in ws], precision=S.SA_FP32_AUX)
+    h.set_kernel(kernel)
     st = h.new_state()
     h.init_state(st, np.stack([S.rho0_vars(w) for w in ws]))
     obs = h.propagate(st, 0.02, 2000, 500)
@@ -144,12 +157,14 @@ def test_batch_fp32_population_error():
         assert np.max(np.abs(obs[:, i, 1:7] - ob[:, 1:7])) <= 1e-5, i
 
 
-def test_graph_equals_steps_and_tuning_invariance():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_graph_equals_steps_and_tuning_invariance(kernel):
     """propagate (CUDA graph) is bit-identical to single steps, and every
     launch tuning gives bit-identical results (each variable's arithmetic
     does not depend on the chunking)."""
     w = W.WORKLOADS["w3"]
     h = S.Heom(S.params_from(w))
+    h.set_kernel(kernel)
     a, b = h.new_state(), h.new_state()
     h.init_state(a, S.rho0_vars(w))
     h.init_state(b, S.rho0_vars(w))
@@ -227,14 +242,16 @@ def test_fp32_rho0_is_fp64():
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("precision,tol", [(S.SA_FP64, 1e-13), (S.SA_FP32_AUX, 2e-6)])
-def test_w5_full_size_sampled(precision, tol):
+def test_w5_full_size_sampled(precision, tol, kernel):
     """Full-size w5 (4,058,820 patterns, 170,187,185 variables) in the launch
     configuration the benchmark uses: the right-hand side of a seeded random
     state at 20,000 sampled variables against the oracle evaluated one by one."""
     w = W.WORKLOADS["w5"]
     sa = oracle_sa(w, cache=False)
     h = S.Heom(S.params_from(w), precision=precision)
+    h.set_kernel(kernel)
     assert h.n_vars == sa.nvar == 170187185
     x = W.random_state(sa.nvar, seed=2608)
     if precision == S.SA_FP32_AUX:
@@ -252,11 +269,13 @@ def test_w5_full_size_sampled(precision, tol):
 
 
 @pytest.mark.slow
-def test_w4_full_batch_sampled():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_w4_full_batch_sampled(kernel):
     """Full w4 batch (512 instances, FP32-aux) in the benchmark's launch
     configuration: RHS of a seeded random float state at sampled variables."""
     ws = W.batch_w4()
     h = S.Heom([S.params_from(w) for w in ws], precision=S.SA_FP32_AUX)
+    h.set_kernel(kernel)
     x = W.random_state(h.n_vars, seed=7).astype(np.complex64).astype(np.complex128)
     xs, dx = h.new_state(), h.new_state()
     h.upload(xs, x)

@@ -1,0 +1,198 @@
+"""The term lists of the SA_KERNEL_LISTS stage kernel, checked on the CPU.
+
+A host-only handle builds the same lists the device kernel reads.  Here they
+are evaluated in numpy the way the kernel does -- per work item an operand
+area (the item's stage-input slice, the grouped row and column sums R_q and
+C_q of Eqs. grouped-row-sum / grouped-column-sum, the Z sums of Eq. HZ, a
+zero), then for every lane variable
+    dv = diag * v - i g (op[a] - op[b]) + sum_t coef[slot_t] * x[idx_t]
+-- with the coefficients of Eqs. uvar-up / uvar-down written out from the
+bath, and compared with the oracle's right-hand side.  The structure of the
+lists is checked too: every variable once, rounds padded to their longest
+list and no further, padding only with the zero slot.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.bath as OB
+import paper_2608_20657_b300 as S
+import workloads as W
+
+ZERO_SLOT = 1536
+
+
+def _generic_bath(m, seed):
+    rng = np.random.default_rng(seed)
+    return {"c": rng.uniform(0.1, 0.5, m) + 1j * rng.uniform(-0.4, 0.4, m),
+            "cc": rng.uniform(0.1, 0.5, m) + 1j * rng.uniform(-0.4, 0.4, m),
+            "nu": rng.uniform(0.2, 1.2, m) + 1j * rng.uniform(-0.3, 0.3, m)}
+
+
+def _slot_coefficients(bath):
+    """Coefficient of every list slot: row, column, row + column, zero."""
+    c, cc = np.asarray(bath["c"]), np.asarray(bath["cc"])
+    out = np.zeros(ZERO_SLOT + 1, complex)
+    for cid in range(512):
+        k, n, up = (cid >> 1) // 32, (cid >> 1) % 32, cid & 1
+        if k >= c.size:
+            continue
+        ac = abs(c[k])
+        if up:
+            row, col = -1j * np.sqrt((n + 1) * ac), 1j * np.sqrt((n + 1) * ac)
+        else:
+            row, col = -1j * np.sqrt(n / ac) * c[k], 1j * np.sqrt(n / ac) * cc[k]
+        out[cid], out[512 + cid], out[1024 + cid] = row, col, row + col
+    return out
+
+
+def _layout(G, M):
+    """Local indices of the canonical layout of a pattern with multiplicities M."""
+    X = lambda q: q
+    Y = lambda q: G + q
+    P = lambda q: 2 * G + q
+    Sv = lambda q, r: 3 * G + 1 + (q - 1) * (G - 1) + (r - 1) - (1 if r > q else 0)
+    tr = np.cumsum([0] + [1 if m >= 2 else 0 for m in M])
+    T = lambda q: (G + 1) ** 2 + tr[q - 1]
+    return X, Y, P, Sv, T
+
+
+def _eval_lists(lib, sas, baths, x, insts):
+    """Right-hand side of the batch from the dumped lists; NaN where no lane
+    writes (the physical representative in SA_FP32_AUX mode)."""
+    L = lib.dump_lists()
+    R0, C0, Z0, ZZ = (int(v) for v in L["opz"])
+    out = np.full(x.size, np.nan, complex)
+    # batch pattern tables
+    pats = [lib.dump_patterns(i) for i in range(len(sas))]
+    voff = [lib.var_offset(i) for i in range(len(sas))]
+    gvar, gcat, ginst, gG, gM, ggam = [], [], [], [], [], []
+    cbase = 0
+    for i, (P, sa) in enumerate(zip(pats, sas)):
+        vec = sa.vectors().astype(float)
+        nu = np.asarray(baths[i]["nu"])
+        for p in range(P["G"].size):
+            gvar.append(voff[i] + P["var_off"][p])
+            gcat.append(cbase + P["cat_off"][p])
+            ginst.append(i)
+            gG.append(P["G"][p])
+            gM.append(P["cat_M"][P["cat_off"][p]:P["cat_off"][p + 1]])
+            ids = P["ids"][p]
+            ggam.append(sum(vec[v] @ nu for v in ids if v >= 0))
+        cbase += P["cat_off"][-1]
+    coefs = [_slot_coefficients(b) for b in baths]
+    for it in L["items"]:
+        p0, np_, v0, nv, c0, ncat, r0, nl = (int(v) for v in it)
+        op = np.zeros(ZZ + 1, complex)
+        op[:nv] = x[v0:v0 + nv]
+        for j in range(np_):
+            p = p0 + j
+            G, M = gG[p], gM[p]
+            X, Y, P, Sv, T = _layout(G, M)
+            xp = x[gvar[p]:]
+            cb = gcat[p] - c0
+            zs = 0
+            for q in range(1, G + 1):
+                base = xp[P(q)] + ((M[q - 1] - 1) * xp[T(q)] if M[q - 1] >= 2 else 0)
+                op[R0 + cb + q - 1] = base + sum(M[b - 1] * xp[Sv(q, b)] for b in range(1, G + 1) if b != q)
+                op[C0 + cb + q - 1] = base + sum(M[b - 1] * xp[Sv(b, q)] for b in range(1, G + 1) if b != q)
+                zs += M[q - 1] * (xp[X(q)] - xp[Y(q)])
+            op[Z0 + j] = zs
+        seen = []
+        for rho, i0 in enumerate(range(0, nl, 32)):
+            ra, rb = int(L["rbase"][r0 + rho]), int(L["rbase"][r0 + rho + 1])
+            rows = np.arange(ra, rb)
+            counts = []
+            for u in range(32):
+                e = rows * 32 + u
+                idx, slot = L["tidx"][e].astype(np.int64), L["tcid"][e].astype(np.int64)
+                real = slot != ZERO_SLOT
+                # padding only after the variable's own terms
+                n = int(real.sum())
+                assert np.all(real[:n]) and not np.any(real[n:])
+                if i0 + u >= nl:
+                    assert n == 0
+                    continue
+                counts.append(n)
+                w0, w1 = int(L["lvd"][v0 + i0 + u]), int(L["lvj"][v0 + i0 + u])
+                l, a, b = w0 & 1023, (w0 >> 10) & 2047, w0 >> 21
+                j, cls = w1 & 31, w1 >> 5
+                p = p0 + j
+                vg = v0 + l
+                assert gvar[p] <= vg < (gvar[p + 1] if p + 1 < len(gvar) else x.size)
+                inst = ginst[p]
+                sa_p = sas[inst].params
+                g, det, kap = sa_p.g, sa_p.detuning, sa_p.kappa
+                lossf = [0.0, 0.5, 0.5, 1.0][cls]
+                dim = [0.0, -det, det, 0.0][cls]
+                diag = -(ggam[p].real + lossf * kap) + 1j * (dim - ggam[p].imag)
+                dv = diag * op[l] - 1j * g * (op[a] - op[b])
+                dv += np.sum(coefs[inst][slot[:n]] * x[idx[:n]])
+                out[vg] = dv
+                seen.append(l)
+            # a round is as long as its longest list, and lists are sorted
+            assert counts and max(counts) == rb - ra and counts == sorted(counts, reverse=True)
+        assert len(seen) == len(set(seen)) == nl
+    return out
+
+
+def _case(params_list, baths, sas, precision, chunk=None):
+    lib = S.Heom(params_list, precision=precision, host_only=True)
+    if chunk:
+        lib.set_tuning(chunk=chunk)
+    lib.set_kernel(S.SA_KERNEL_LISTS)
+    assert lib.tuning()["kernel"] == S.SA_KERNEL_LISTS
+    rng = np.random.default_rng(11)
+    xs = [rng.standard_normal(sa.nvar) + 1j * rng.standard_normal(sa.nvar) for sa in sas]
+    x = np.concatenate(xs)
+    got = _eval_lists(lib, sas, baths, x, range(len(sas)))
+    off = 0
+    for i, sa in enumerate(sas):
+        ref = sa.rhs(xs[i])
+        g = got[off:off + sa.nvar]
+        n_rho0 = 5 if sa.N >= 2 else 4
+        if precision == S.SA_FP32_AUX:
+            # the physical representative is integrated by the FP64 kernel
+            assert np.all(np.isnan(g[:n_rho0]))
+            g, ref = g[n_rho0:], ref[n_rho0:]
+        assert not np.any(np.isnan(g))
+        np.testing.assert_allclose(g, ref, rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()))
+        off += sa.nvar
+    assert oracle.errors() == 0
+
+
+@pytest.mark.parametrize("precision", [S.SA_FP64, S.SA_FP32_AUX])
+@pytest.mark.parametrize("N,m,L", [(1, 1, 3), (2, 1, 3), (3, 2, 3), (10, 2, 6), (12, 3, 4), (7, 4, 3), (2, 2, 6)])
+def test_lists_reproduce_oracle_rhs(N, m, L, precision):
+    bath = _generic_bath(m, N + 7 * m + L)
+    kw = dict(detuning=0.1, g=0.2, kappa=0.05)
+    sa = oracle.SA(N, m, L, bath, **kw)
+    _case([S.make_params(N, m, L, bath, **kw)], [bath], [sa], precision)
+
+
+def test_lists_batch_and_chunk():
+    """A batch of unlike instances, with a larger work-item capacity."""
+    specs = [(3, 1, 4, 1), (9, 2, 3, 2), (5, 3, 3, 3)]
+    sas, baths, ps = [], [], []
+    for N, m, L, seed in specs:
+        b = _generic_bath(m, seed)
+        kw = dict(detuning=0.03 * seed, g=0.1 / seed, kappa=0.01 * seed)
+        sas.append(oracle.SA(N, m, L, b, **kw))
+        baths.append(b)
+        ps.append(S.make_params(N, m, L, b, **kw))
+    _case(ps, baths, sas, S.SA_FP32_AUX, chunk=256)
+    _case(ps, baths, sas, S.SA_FP64, chunk=64)
+
+
+def test_lists_state_errors():
+    """Dumps exist only for host-only handles with the list kernel; an unknown
+    variant is rejected."""
+    bath = _generic_bath(1, 3)
+    lib = S.Heom(S.make_params(2, 1, 3, bath), host_only=True)
+    with pytest.raises(S.SaHeomError) as e:
+        lib.dump_lists()
+    assert e.value.code == -7
+    with pytest.raises(S.SaHeomError) as e:
+        lib.set_kernel(7)
+    assert e.value.code == -1
+    assert lib.tuning()["kernel"] == S.SA_KERNEL_RECORDS
