@@ -33,6 +33,9 @@
  *        row major); T_q for the categories with M_q >= 2, in order.
  *    The physical density operator is the first pattern of each instance
  *    (Z, X_0, Y_0, P_0[, T_0], Sec. IV.C).
+ *  - State buffers (d_state, d_x, d_dx) must be 16-byte aligned (cudaMalloc
+ *    and torch allocations are); the entry points that run the stage
+ *    kernels return INVALID_ARG otherwise.
  *  - SA_FP64 state buffers hold double2[n_vars_total] padded to 256 bytes.
  *    SA_FP32_AUX state buffers hold float2[n_vars_total], padded to 256
  *    bytes, followed by double2[8 * n_instances]: slot 8*i + j holds
@@ -202,6 +205,22 @@ int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, i
 int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* lvd, uint8_t* lvj,
                        uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz);
 
+/*
+ * sa_heom_dump_ell -- the host copy of the SA_KERNEL_ELL tables (host-only
+ * handles after sa_heom_set_kernel(h, SA_KERNEL_ELL); STATE otherwise).
+ * sizes[0..2] <- warps W = ceil(variables / 32), term rows, variables.
+ *   wpat   uint32[W]: first pattern (batch index) of warp w's variables
+ *          32 w .. 32 w + 31;
+ *   vword  uint32[variables]: pattern offset from wpat (5 bits) | kind << 5
+ *          (0..5: Z X Y P S T) | q << 8 | r << 13 | T-rank of q << 18
+ *          (31: none);
+ *   rbase  uint32[W + 1]: first term row of every warp;
+ *   tidx   uint32[32 * rows], tcid uint16[32 * rows]: entry 32 * row + lane
+ *          as in sa_heom_dump_lists (1536 = zero slot, padding).
+ */
+int sa_heom_dump_ell(const sa_heom* h, int64_t* sizes, uint32_t* wpat, uint32_t* vword, uint32_t* rbase,
+                     uint32_t* tidx, uint16_t* tcid);
+
 /* sa_heom_state_bytes -- bytes of one state vector of the whole batch. */
 int sa_heom_state_bytes(const sa_heom* h, size_t* bytes);
 
@@ -291,11 +310,16 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best);
  *                      lanes a term-major list of (target index, coefficient
  *                      slot) entries: 6 B per term plus padding to the
  *                      round's longest list, 5 B per variable.
+ *   SA_KERNEL_ELL      the same host-resolved terms, one thread per variable
+ *                      in memory order (warp w takes variables 32 w ..
+ *                      32 w + 31): T_w rows of 32 entries per warp, T_w its
+ *                      longest list; 4 B per variable; no shared memory.
+ *                      The item capacity (chunk) does not apply to it.
  * sa_heom_set_kernel rebuilds the launch tables (synchronous; INVALID_ARG for
  * an unknown variant, OOM if the lists do not fit).  sa_heom_get_tuning
  * writes block, chunk, queue, kernel to out[0..3].
  */
-enum { SA_KERNEL_RECORDS = 0, SA_KERNEL_LISTS = 1 };
+enum { SA_KERNEL_RECORDS = 0, SA_KERNEL_LISTS = 1, SA_KERNEL_ELL = 2 };
 int sa_heom_set_kernel(sa_heom* h, int kernel);
 int sa_heom_get_tuning(const sa_heom* h, int* out);
 

@@ -20,7 +20,7 @@ MAXM = 8
 
 SA_FP64, SA_FP32_AUX = 0, 1
 SA_BUILD_DEVICE, SA_BUILD_HOST_ONLY = 0, 1
-SA_KERNEL_RECORDS, SA_KERNEL_LISTS = 0, 1
+SA_KERNEL_RECORDS, SA_KERNEL_LISTS, SA_KERNEL_ELL = 0, 1, 2
 BATH_HIGH_T, BATH_MATSUBARA, BATH_PADE = 0, 1, 2
 ERRORS = {0: "SA_OK", -1: "SA_ERR_INVALID_ARG", -2: "SA_ERR_UNSUPPORTED", -3: "SA_ERR_OOM",
           -4: "SA_ERR_CUDA", -5: "SA_ERR_TIMEOUT", -6: "SA_ERR_NUMERIC", -7: "SA_ERR_STATE"}
@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
             "sa_heom_autotune": [vp, vp, vp, vp],
             "sa_heom_set_kernel": [vp, i32],
             "sa_heom_dump_lists": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
+            "sa_heom_dump_ell": [vp, vp, vp, vp, vp, vp, vp],
             "sa_heom_get_tuning": [vp, vp],
             "sa_heom_launches_per_step": [vp],
             "sa_heom_device_error": [vp, vp],
@@ -125,7 +126,7 @@ def exported_symbols() -> list[str]:
             "sa_heom_var_offset", "sa_heom_dump_vectors", "sa_heom_dump_patterns", "sa_heom_dump_categories",
             "sa_heom_dump_terms", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_state_upload",
             "sa_heom_state_download", "sa_heom_rhs", "sa_heom_step", "sa_heom_propagate", "sa_heom_observables",
-            "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_set_kernel", "sa_heom_get_tuning", "sa_heom_dump_lists",
+            "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_set_kernel", "sa_heom_get_tuning", "sa_heom_dump_lists", "sa_heom_dump_ell",
             "sa_heom_launches_per_step", "sa_heom_device_error",
             "sa_heom_observables_noalloc", "sa_heom_strerror", "sa_heom_last_error", "sa_conv_build",
             "sa_conv_destroy", "sa_conv_info", "sa_conv_labels", "sa_conv_set_rho0", "sa_conv_rhs", "sa_conv_step",
@@ -334,6 +335,18 @@ class Heom:
         _check(lib().sa_heom_dump_lists(self._h, _ptr(sizes), *(_ptr(out[k]) for k in
                                                                 ("items", "lvd", "lvj", "rbase", "tidx", "tcid",
                                                                  "opz"))), "sa_heom_dump_lists")
+        return out
+
+    def dump_ell(self) -> dict:
+        """Host copy of the SA_KERNEL_ELL tables (host-only handles)."""
+        sizes = np.zeros(3, np.int64)
+        _check(lib().sa_heom_dump_ell(self._h, _ptr(sizes), None, None, None, None, None), "sa_heom_dump_ell")
+        nw, rows, nv = (int(v) for v in sizes)
+        out = dict(wpat=np.zeros(nw, np.uint32), vword=np.zeros(nv, np.uint32), rbase=np.zeros(nw + 1, np.uint32),
+                   tidx=np.zeros(32 * rows, np.uint32), tcid=np.zeros(32 * rows, np.uint16))
+        _check(lib().sa_heom_dump_ell(self._h, _ptr(sizes), *(_ptr(out[k]) for k in
+                                                              ("wpat", "vword", "rbase", "tidx", "tcid"))),
+               "sa_heom_dump_ell")
         return out
 
     def tuning(self) -> dict:

@@ -89,6 +89,11 @@ struct sa_heom {
     std::vector<uint8_t> lvj;
     std::vector<uint16_t> tcid;
     uint64_t list_rows = 0;
+    std::vector<uint32_t> wpat;   // ELL: first pattern of every warp row
+    std::vector<ItemDesc> list_items;  // SA_KERNEL_LISTS: the item table the current lists were built with
+    std::vector<uint8_t> blobs;        // SA_KERNEL_LISTS: per-item table blobs
+    int tables = -1;              // variant whose term tables are current (-1: none)
+    int tables_chunk = 0;         // item capacity they were built for (SA_KERNEL_LISTS)
     // tuning
     int block = 256, chunk = 128, use_queue = 1, kernel = SA_KERNEL_RECORDS;
     // device
@@ -100,6 +105,8 @@ struct sa_heom {
     void *d_vdesc = nullptr, *d_drecA = nullptr, *d_drecS = nullptr;
     void *d_lvd = nullptr, *d_lvj = nullptr, *d_rbase = nullptr, *d_tidx = nullptr, *d_tcid = nullptr;
     void* d_lcoef = nullptr;
+    void* d_wpat = nullptr;
+    void* d_blobs = nullptr;
     unsigned int* d_err = nullptr;
     void* d_work[3] = {nullptr, nullptr, nullptr};  // acc, xa, xb
     unsigned int* d_queue = nullptr;
@@ -279,6 +286,67 @@ void list_item(const sa_heom* h, const ItemDesc& d, ListItem& W) {
     std::stable_sort(W.order.begin(), W.order.end(), [&](uint32_t x, uint32_t y) { return W.cnt[x] > W.cnt[y]; });
 }
 
+// Per-item table blobs of the list kernel (BlobLayout): everything the warp
+// stages for an item besides the state slices, contiguous and 16-byte
+// aligned so that one bulk copy brings it.
+template <typename V>
+int build_blobs(sa_heom* h) {
+    const size_t ni = h->items.size();
+    uint64_t off16 = 0;
+    for (size_t c = 0; c < ni; ++c) {
+        ItemDesc& d = h->items[c];
+        const BlobLayout B = blob_layout<V>(d.np, d.ncat, d.nl);
+        d.blob16 = uint32_t(off16);
+        d.blob_bytes = B.bytes;
+        off16 += B.bytes / 16;
+        if (off16 >= (uint64_t(1) << 32)) return fail(SA_ERR_UNSUPPORTED, "list-kernel blobs exceed 64 GB");
+    }
+    try {
+        h->blobs.assign(size_t(off16) * 16, 0);
+    } catch (const std::bad_alloc&) {
+        return fail(SA_ERR_OOM, "host memory for the list-kernel blobs");
+    }
+    const std::vector<double>& gam = h->gamma_d;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t c = 0; c < int64_t(ni); ++c) {
+        const ItemDesc& d = h->items[c];
+        const BlobLayout B = blob_layout<V>(d.np, d.ncat, d.nl);
+        uint8_t* o = &h->blobs[size_t(d.blob16) * 16];
+        PatHdr* ph = reinterpret_cast<PatHdr*>(o + B.hdr);
+        PatConst<V>* pc = reinterpret_cast<PatConst<V>*>(o + B.pc);
+        V* gm = reinterpret_cast<V*>(o + B.gam);
+        uint32_t* cw = reinterpret_cast<uint32_t*>(o + B.cw);
+        V* cM = reinterpret_cast<V*>(o + B.cM);
+        uint8_t* cj = o + B.cj;
+        uint32_t* rb = reinterpret_cast<uint32_t*>(o + B.rb);
+        uint32_t* lvd = reinterpret_cast<uint32_t*>(o + B.lvd);
+        uint8_t* lvj = o + B.lvj;
+        for (uint32_t j = 0; j < d.np; ++j) {
+            const PatHdr& H = h->hdr[d.p0 + j];
+            const sa_params& q = h->inst[H.inst].p;
+            ph[j] = H;
+            pc[j].g = V(q.g);
+            pc[j].det = V(q.detuning);
+            pc[j].kap = V(q.kappa);
+            pc[j].coef_base = uint32_t(H.inst) * uint32_t(kListCoefStride);
+            gm[2 * j] = V(gam[2 * size_t(d.p0 + j)]);
+            gm[2 * j + 1] = V(gam[2 * size_t(d.p0 + j) + 1]);
+            for (uint32_t cl = H.cat_off - d.c0; cl < h->hdr[d.p0 + j + 1].cat_off - d.c0; ++cl) cj[cl] = uint8_t(j);
+        }
+        for (uint32_t cl = 0; cl < d.ncat; ++cl) {
+            cw[cl] = h->cat_word[d.c0 + cl];
+            cM[cl] = V(h->catMd[d.c0 + cl]);
+        }
+        const uint32_t nrounds = (d.nl + 31) / 32;
+        for (uint32_t r = 0; d.nl && r <= nrounds; ++r) rb[r] = h->rbase[d.r0 + r];
+        for (uint32_t i = 0; i < d.nl; ++i) {
+            lvd[i] = h->lvd[d.v0 + i];
+            lvj[i] = h->lvj[d.v0 + i];
+        }
+    }
+    return SA_OK;
+}
+
 uint64_t list_item_rows(const ListItem& W) {
     uint64_t rows = 0;
     for (size_t i = 0; i < W.order.size(); i += 32) rows += W.cnt[W.order[i]];
@@ -324,6 +392,7 @@ int build_lists(sa_heom* h) {
         return fail(SA_ERR_OOM, "host memory for the term lists");
     }
     h->rbase[rr] = uint32_t(rw);
+
 #pragma omp parallel
     {
         ListItem W;
@@ -333,6 +402,9 @@ int build_lists(sa_heom* h) {
             list_item(h, d, W);
             d.nl = uint32_t(W.order.size());
             uint64_t row = nrows[c];
+            d.row0 = uint32_t(row);
+            d.row1 = uint32_t(nrows[c + 1]);
+
             uint32_t rho = nrounds[c];
             for (size_t i0 = 0; i0 < W.order.size(); i0 += 32, ++rho) {
                 h->rbase[rho] = uint32_t(row);
@@ -358,6 +430,113 @@ int build_lists(sa_heom* h) {
                 }
                 row += T;
             }
+        }
+    }
+    const int rc = h->precision == SA_FP64 ? build_blobs<double>(h) : build_blobs<float>(h);
+    if (rc) return rc;
+    h->list_items = h->items;
+    return SA_OK;
+}
+
+// ELL tables: warp w takes the variables 32 w .. 32 w + 31 in memory order.
+// Per variable a word (pattern offset from the warp's first pattern | kind
+// << 5 | q << 8 | r << 13 | T-rank of q << 18); per warp T_w rows of 32
+// (target, coefficient slot) entries, T_w the longest list among its lanes,
+// short lists padded with the zero slot.  The physical representative has no
+// list in SA_FP32_AUX mode (the FP64 kernel integrates it).  Two parallel
+// passes over the patterns (term counts, then contents).
+int build_ell(sa_heom* h) {
+    const int64_t nv = h->nvar, nw = (nv + 31) / 32, np = h->npat;
+    const bool side64 = h->precision == SA_FP32_AUX;
+    std::vector<uint32_t> cnt;
+    try {
+        cnt.assign(size_t(nw) * 32, 0u);
+        h->wpat.assign(size_t(nw), 0u);
+        h->lvd.assign(size_t(nv), 0u);
+        h->rbase.assign(size_t(nw) + 1, 0u);
+    } catch (const std::bad_alloc&) {
+        return fail(SA_ERR_OOM, "host memory for the ELL tables");
+    }
+    auto each_term = [&](int64_t gp, auto&& fn) {
+        const PatHdr& H = h->hdr[gp];
+        if (side64 && H.tier == 0) return;
+        const int inst = H.inst;
+        const uint32_t vb = uint32_t(h->var_begin[inst]);
+        for_each_term(h->inst[inst], gp - int64_t(h->instdev[inst].pat_begin),
+                      [&](int64_t loc, int kind, int64_t src, uint32_t packed, int side) {
+                          if (kind == 3 && side == 1) return;  // folded into the row term's coefficient
+                          const int cid = int(packed >> 23);
+                          const int slot = kind == 3 ? 2 * kCoefPerInst + cid : side * kCoefPerInst + cid;
+                          fn(H.var_off + uint32_t(loc), vb + uint32_t(src), slot);
+                      });
+    };
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t gp = 0; gp < np; ++gp) each_term(gp, [&](uint32_t v, uint32_t, int) { ++cnt[v]; });
+    // warps: first pattern, rows
+#pragma omp parallel for schedule(static)
+    for (int64_t w = 0; w < nw; ++w) {
+        const uint32_t v = uint32_t(w * 32);
+        int64_t lo = 0, hi = np - 1;  // last pattern with var_off <= v
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) / 2;
+            if (h->hdr[mid].var_off <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        h->wpat[w] = uint32_t(lo);
+        uint32_t T = 0;
+        for (int u = 0; u < 32; ++u) T = std::max(T, cnt[size_t(w) * 32 + u]);
+        h->rbase[w + 1] = T;
+    }
+    uint64_t rows = 0;
+    for (int64_t w = 0; w < nw; ++w) {
+        const uint64_t T = h->rbase[w + 1];
+        h->rbase[w] = uint32_t(rows);
+        rows += T;
+        if (rows >= (uint64_t(1) << 32)) return fail(SA_ERR_UNSUPPORTED, "ELL tables exceed 32-bit row indices");
+    }
+    h->rbase[nw] = uint32_t(rows);
+    h->list_rows = rows;
+    try {
+        h->tidx.assign(size_t(rows) * 32, 0u);
+        h->tcid.assign(size_t(rows) * 32, uint16_t(kListCoefZero));
+    } catch (const std::bad_alloc&) {
+        return fail(SA_ERR_OOM, "host memory for the ELL tables");
+    }
+    // padding names the lane's own variable (any valid index would do)
+#pragma omp parallel for schedule(static)
+    for (int64_t w = 0; w < nw; ++w)
+        for (uint32_t t = h->rbase[w]; t < h->rbase[w + 1]; ++t)
+            for (int u = 0; u < 32; ++u) h->tidx[size_t(t) * 32 + u] = uint32_t(std::min<int64_t>(w * 32 + u, nv - 1));
+#pragma omp parallel
+    {
+        std::vector<uint32_t> k;  // terms written per variable of the pattern
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t gp = 0; gp < np; ++gp) {
+            const PatHdr& H = h->hdr[gp];
+            const uint32_t v0 = H.var_off, nvp = h->hdr[gp + 1].var_off - v0;
+            const int G = H.G;
+            auto word = [&](int64_t loc, uint32_t kind, int q, int r) {
+                const uint32_t v = v0 + uint32_t(loc);
+                const uint32_t trq = q ? (h->cat_word[H.cat_off + q - 1] >> 15) & 31u : 31u;
+                h->lvd[v] = uint32_t(gp - h->wpat[v >> 5]) | (kind << 5) | (uint32_t(q) << 8) | (uint32_t(r) << 13) |
+                            (trq << 18);
+            };
+            word(loc_Z(), 0, 0, 0);
+            for (int q = 1; q <= G; ++q) {
+                word(loc_X(G, q), 1, q, 0);
+                word(loc_Y(G, q), 2, q, 0);
+                word(loc_P(G, q), 3, q, 0);
+                for (int r = 1; r <= G; ++r)
+                    if (r != q) word(loc_S(G, q, r), 4, q, r);
+                const int tr = (h->cat_word[H.cat_off + q - 1] >> 15) & 31;
+                if (tr != 31) word(loc_T(G, tr), 5, q, 0);
+            }
+            k.assign(nvp, 0u);
+            each_term(gp, [&](uint32_t v, uint32_t src, int slot) {
+                const size_t e = (size_t(h->rbase[v >> 5]) + k[v - v0]++) * 32 + (v & 31u);
+                h->tidx[e] = src;
+                h->tcid[e] = uint16_t(slot);
+            });
         }
     }
     return SA_OK;
@@ -401,11 +580,54 @@ std::vector<V> list_coefficients(const sa_heom* h) {
 }
 
 void free_lists(sa_heom* h) {
-    void** ptrs[] = {&h->d_lvd, &h->d_lvj, &h->d_rbase, &h->d_tidx, &h->d_tcid};
+    void** ptrs[] = {&h->d_lvd, &h->d_lvj, &h->d_rbase, &h->d_tidx, &h->d_tcid, &h->d_wpat, &h->d_blobs};
     for (void** p : ptrs) {
         if (*p) cudaFree(*p);
         *p = nullptr;
     }
+    h->tables = -1;
+}
+
+// Term tables of the current variant: built (and, on a device handle,
+// uploaded) unless the current ones already serve it.
+int ensure_tables(sa_heom* h) {
+    const int k = h->kernel;
+    if (k == SA_KERNEL_RECORDS) return SA_OK;
+    if (h->tables == k && (k == SA_KERNEL_ELL || h->tables_chunk == h->chunk)) {
+        if (k == SA_KERNEL_LISTS)  // the item table was rebuilt: same items, restore their rounds
+            h->items = h->list_items;
+        return SA_OK;
+    }
+    if (!h->host_only) free_lists(h);
+    h->tables = -1;
+    int rc = k == SA_KERNEL_LISTS ? build_lists(h) : build_ell(h);
+    if (rc) return rc;
+    if (!h->host_only) {
+        if (!h->d_lcoef)
+            rc = h->precision == SA_FP64 ? upload(&h->d_lcoef, list_coefficients<double>(h))
+                                         : upload(&h->d_lcoef, list_coefficients<float>(h));
+
+        if (!rc && k == SA_KERNEL_LISTS) rc = upload(&h->d_blobs, h->blobs);
+        if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_lvd, h->lvd);
+        if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_wpat, h->wpat);
+        if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_rbase, h->rbase);
+        if (!rc) rc = upload(&h->d_tidx, h->tidx);
+        if (!rc) rc = upload(&h->d_tcid, h->tcid);
+        // the host copies are not needed again
+        std::vector<uint32_t>().swap(h->lvd);
+        std::vector<uint8_t>().swap(h->lvj);
+        std::vector<uint32_t>().swap(h->tidx);
+        std::vector<uint16_t>().swap(h->tcid);
+        std::vector<uint32_t>().swap(h->wpat);
+        std::vector<uint8_t>().swap(h->blobs);
+        if (rc) {
+            free_lists(h);
+            return rc;
+        }
+    }
+    h->tables = k;
+    h->tables_chunk = h->chunk;
+    return SA_OK;
 }
 
 int apply_tuning(sa_heom* h) {
@@ -415,33 +637,14 @@ int apply_tuning(sa_heom* h) {
     h->cfg.use_queue = h->use_queue;
     h->cfg.kernel = h->kernel;
     const uint32_t nchunks = uint32_t(h->items.size());
-    if (h->kernel == SA_KERNEL_LISTS) {
-        const int rc = build_lists(h);
-        if (rc) return rc;
-    }
+    int rc = ensure_tables(h);
+    if (rc) return rc;
     if (h->host_only) return SA_OK;
     if (h->d_chunk) cudaFree(h->d_chunk);
     if (h->d_vdesc) cudaFree(h->d_vdesc);
     h->d_chunk = h->d_vdesc = nullptr;
-    free_lists(h);
-    int rc = upload(&h->d_chunk, h->items);
+    rc = upload(&h->d_chunk, h->items);
     if (!rc) rc = upload(&h->d_vdesc, h->vdesc);
-    if (!rc && h->kernel == SA_KERNEL_LISTS) {
-        if (!h->d_lcoef)
-            rc = h->precision == SA_FP64 ? upload(&h->d_lcoef, list_coefficients<double>(h))
-                                         : upload(&h->d_lcoef, list_coefficients<float>(h));
-        if (!rc) rc = upload(&h->d_lvd, h->lvd);
-        if (!rc) rc = upload(&h->d_lvj, h->lvj);
-        if (!rc) rc = upload(&h->d_rbase, h->rbase);
-        if (!rc) rc = upload(&h->d_tidx, h->tidx);
-        if (!rc) rc = upload(&h->d_tcid, h->tcid);
-        // the host copies are not needed again
-        std::vector<uint32_t>().swap(h->lvd);
-        std::vector<uint8_t>().swap(h->lvj);
-        std::vector<uint32_t>().swap(h->tidx);
-        std::vector<uint16_t>().swap(h->tcid);
-        if (rc) free_lists(h);
-    }
     if (rc) return rc;
     int occ = 0;
     CK(stage_occupancy(h->cfg, h->precision == SA_FP64, &occ));
@@ -462,7 +665,7 @@ void free_device(sa_heom* h) {
                     h->d_coef_row, h->d_coef_col, h->d_coef_row_d, h->d_coef_col_d, h->d_lut, h->d_lut_off,
                     h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0,
                     h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS, h->d_lvd, h->d_lvj, h->d_rbase,
-                    h->d_tidx, h->d_tcid, h->d_lcoef};
+                    h->d_tidx, h->d_tcid, h->d_lcoef, h->d_wpat, h->d_blobs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -504,6 +707,9 @@ StageLaunch base_launch(const sa_heom* h) {
     s.tidx = h->d_tidx;
     s.tcid = h->d_tcid;
     s.lcoef = h->d_lcoef;
+    s.wpat = h->d_wpat;
+    s.blobs = h->d_blobs;
+    s.nvar = uint32_t(h->nvar);
     s.nchunks = uint32_t(h->items.size());
     s.err = h->d_err;
     s.ninst = h->count;
@@ -550,6 +756,9 @@ int read_device_error(sa_heom* h, cudaStream_t st) {
     if (w) return fail(SA_ERR_TIMEOUT, "a bounded device wait expired in the stage kernel");
     return SA_OK;
 }
+
+// the stage kernels copy state slices with 16-byte bulk copies
+bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
 
 int check_device(const sa_heom* h) {
     if (!h) return fail(SA_ERR_INVALID_ARG, "null handle");
@@ -883,13 +1092,34 @@ int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32
     sizes[1] = int64_t(h->rbase.size()) - 1;
     sizes[2] = int64_t(h->list_rows);
     sizes[3] = h->nvar;
-    if (items) std::memcpy(items, h->items.data(), h->items.size() * sizeof(ItemDesc));
+    if (items)
+        for (size_t c = 0; c < h->items.size(); ++c) {
+            const ItemDesc& d = h->items[c];
+            const uint32_t f[8] = {d.p0, d.np, d.v0, d.nv, d.c0, d.ncat, d.r0, d.nl};
+            std::memcpy(items + 8 * c, f, sizeof(f));
+        }
     if (lvd) std::copy(h->lvd.begin(), h->lvd.end(), lvd);
     if (lvj) std::copy(h->lvj.begin(), h->lvj.end(), lvj);
     if (rbase) std::copy(h->rbase.begin(), h->rbase.end(), rbase);
     if (tidx) std::copy(h->tidx.begin(), h->tidx.end(), tidx);
     if (tcid) std::copy(h->tcid.begin(), h->tcid.end(), tcid);
     if (opz) list_operand_layout(h->chunk, &opz[0], &opz[1], &opz[2], &opz[3]);
+    return SA_OK;
+}
+
+int sa_heom_dump_ell(const sa_heom* h, int64_t* sizes, uint32_t* wpat, uint32_t* vword, uint32_t* rbase,
+                     uint32_t* tidx, uint16_t* tcid) {
+    if (!h || !sizes) return fail(SA_ERR_INVALID_ARG, "handle and sizes required");
+    if (!h->host_only || h->kernel != SA_KERNEL_ELL)
+        return fail(SA_ERR_STATE, "ELL tables are kept on the host only for host-only handles with SA_KERNEL_ELL");
+    sizes[0] = int64_t(h->wpat.size());
+    sizes[1] = int64_t(h->list_rows);
+    sizes[2] = h->nvar;
+    if (wpat) std::copy(h->wpat.begin(), h->wpat.end(), wpat);
+    if (vword) std::copy(h->lvd.begin(), h->lvd.end(), vword);
+    if (rbase) std::copy(h->rbase.begin(), h->rbase.end(), rbase);
+    if (tidx) std::copy(h->tidx.begin(), h->tidx.end(), tidx);
+    if (tcid) std::copy(h->tcid.begin(), h->tcid.end(), tcid);
     return SA_OK;
 }
 
@@ -969,6 +1199,7 @@ int sa_heom_rhs(sa_heom* h, const void* d_x, void* d_dx, void* stream) {
     int rc = check_device(h);
     if (rc) return rc;
     if (!d_x || !d_dx || d_x == d_dx) return fail(SA_ERR_INVALID_ARG, "distinct d_x and d_dx required");
+    if (misaligned(d_x) || misaligned(d_dx)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CK(cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int), st));
     StageLaunch L = base_launch(h);
@@ -986,6 +1217,7 @@ int sa_heom_step(sa_heom* h, void* d_state, double dt, void* stream) {
     int rc = check_device(h);
     if (rc) return rc;
     if (!d_state || !std::isfinite(dt)) return fail(SA_ERR_INVALID_ARG, "d_state and finite dt required");
+    if (misaligned(d_state)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CK(cudaMemsetAsync(h->d_queue, 0, 4 * sizeof(unsigned int), st));
     return enqueue_step(h, d_state, dt, 0, st);
@@ -1044,6 +1276,7 @@ int sa_heom_propagate(sa_heom* h, void* d_state, double dt, int64_t nsteps, int6
     int rc = check_device(h);
     if (rc) return rc;
     if (!d_state || !std::isfinite(dt) || nsteps < 0) return fail(SA_ERR_INVALID_ARG, "d_state, dt, nsteps");
+    if (misaligned(d_state)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (!h_obs) return run_steps(h, d_state, dt, nsteps, st);
     if (obs_every <= 0) obs_every = std::max<int64_t>(nsteps, 1);
@@ -1115,8 +1348,8 @@ int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue) {
 
 int sa_heom_set_kernel(sa_heom* h, int kernel) {
     if (!h) return fail(SA_ERR_INVALID_ARG, "null handle");
-    if (kernel != SA_KERNEL_RECORDS && kernel != SA_KERNEL_LISTS)
-        return fail(SA_ERR_INVALID_ARG, "kernel must be SA_KERNEL_RECORDS or SA_KERNEL_LISTS");
+    if (kernel != SA_KERNEL_RECORDS && kernel != SA_KERNEL_LISTS && kernel != SA_KERNEL_ELL)
+        return fail(SA_ERR_INVALID_ARG, "kernel must be SA_KERNEL_RECORDS, SA_KERNEL_LISTS or SA_KERNEL_ELL");
     const int old = h->kernel;
     h->kernel = kernel;
     const int rc = apply_tuning(h);
@@ -1143,6 +1376,7 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     int rc = check_device(h);
     if (rc) return rc;
     if (!d_state) return fail(SA_ERR_INVALID_ARG, "d_state required");
+    if (misaligned(d_state)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int blocks[] = {128, 256};
     const int chunks[] = {64, 96, 128, 192, 256};
@@ -1153,11 +1387,13 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int k : {int(SA_KERNEL_RECORDS), int(SA_KERNEL_LISTS)})
+    for (int k : {int(SA_KERNEL_RECORDS), int(SA_KERNEL_LISTS), int(SA_KERNEL_ELL)})
     for (int q = 0; q < 2; ++q)
         for (int b : blocks)
             for (int c : chunks) {
                 if (c < h->max_u) continue;
+                // the ELL kernel has neither work items nor a queue
+                if (k == SA_KERNEL_ELL && (q != 0 || c != std::max(128, (h->max_u + 31) / 32 * 32))) continue;
                 h->kernel = k;
                 if (sa_heom_set_tuning(h, b, c, q)) continue;
                 // warm-up + timed: two RK4 steps

@@ -87,6 +87,10 @@ template <typename T> struct StageParams {
     const uint32_t* __restrict__ tidx;      // term rows of 32: batch-global target index
     const uint16_t* __restrict__ tcid;      // term rows of 32: coefficient slot in the instance's list table
     const C* __restrict__ lcoef;            // per instance kListCoefStride slots
+    // ELL kernel (lvd: per-variable word, rbase: per warp row, tidx / tcid as above)
+    const unsigned char* __restrict__ blobs; // list kernel: per-item table blobs (16-byte aligned)
+    const uint32_t* __restrict__ wpat;      // first pattern of every warp row of 32 variables
+    uint32_t nvar;
     uint32_t nchunks;
     int chunk;                              // variable capacity of one work item
     const C* x_in;                          // stage input (gathered)
@@ -238,11 +242,6 @@ __device__ __forceinline__ typename Cx<A>::t var_rhs(const StageParams<T>& P, in
     return d;
 }
 
-// Per-pattern constants staged with the work item.
-template <typename T> struct PatConst {
-    T g, det, kap;       // coupling, detuning, loss rate of the pattern's instance
-    uint32_t coef_base;  // the instance's coefficient table
-};
 
 // Per-warp shared-memory image of one work item.
 template <typename T> struct WarpSmem {
@@ -499,21 +498,76 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
 }
 
 // ---- list kernel -----------------------------------------------------------
+// TMA bulk copies and mbarriers (inline PTX).
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy: 16-byte aligned addresses, size a positive multiple of 16
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// bulk prefetch of a global range into L2 (same alignment rules)
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: about a second of SM clocks, then report failure
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (2LL << 30)) return false;
+    return true;
+}
+
+// The 16-byte aligned byte range enclosing `count` elements of `esz` bytes
+// at `first`, and how many elements precede the first wanted one.  Tables and
+// state buffers are padded so that the rounded range stays inside them.
+struct Span {
+    const char* src;
+    uint32_t bytes;
+    uint32_t skip;
+};
+__device__ __forceinline__ Span span(const void* base, size_t first, uint32_t count, uint32_t esz) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(base) + first * esz;
+    const uintptr_t lo = a & ~uintptr_t(15), hi = (a + uintptr_t(count) * esz + 15) & ~uintptr_t(15);
+    Span sp;
+    sp.src = reinterpret_cast<const char*>(lo);
+    sp.bytes = count ? uint32_t(hi - lo) : 0u;
+    sp.skip = uint32_t(a - lo) / esz;
+    return sp;
+}
+
 // Per-warp shared memory of the list kernel.  The operand area op[] holds the
-// item's stage-input slice (chunk entries), then the grouped row sums R_q and
+// item's stage-input slice (chunk entries, after a skip of 0 or 1 entries
+// that the bulk copy's alignment leaves), then the grouped row sums R_q and
 // column sums C_q of its categories, the Z sums of its patterns and one zero:
 // every commutator term of Eq. HS is diag * v - i g (op[a] - op[b]) with
-// host-chosen operand indices a, b.
+// host-chosen operand indices a, b.  The item's host-made tables arrive as
+// one blob (see BlobLayout).
 template <typename T> struct ListSmem {
     using C = typename Cx<T>::t;
-    C* op;       // chunk + 2 nc + kItemPats + 1 entries
-    C* y;        // RK4 state slice
-    C* acc;      // RK4 accumulator slice
-    C* gam;      // Gamma_Lambda per pattern
-    PatHdr* ph;  // pattern headers (kItemPats + 1)
-    PatConst<T>* pc;
-    uint32_t* cw;
-    T* cM;
+    uint64_t* bar;        // the warp's mbarrier
+    C* op;                // skip + chunk + 2 nc + kItemPats + 1 entries (+ 2 spare)
+    C* y;                 // RK4 state slice (skip + chunk + 1)
+    C* acc;               // RK4 accumulator slice
+    unsigned char* blob;  // the item's table blob
 };
 
 __host__ __device__ __forceinline__ int list_ncat(int item) { return item / 4 + 8; }
@@ -526,35 +580,37 @@ __host__ __device__ __forceinline__ int list_opZero(int item) { return item + 2 
 template <typename T>
 __host__ __device__ __forceinline__ size_t list_smem_bytes(int item) {
     const size_t cs = 2 * sizeof(T);
-    const size_t nc = size_t(list_ncat(item));
-    return al16(cs * (list_opZero(item) + 1)) + 2 * al16(cs * item) + al16(cs * kItemPats) +
-           al16(sizeof(PatHdr) * (kItemPats + 1)) + al16(sizeof(PatConst<T>) * kItemPats) + al16(4 * nc) +
-           al16(sizeof(T) * nc);
+    return 16 + al16(cs * (list_opZero(item) + 3)) + 2 * al16(cs * (item + 2)) +
+           blob_layout<T>(kItemPats, uint32_t(list_ncat(item)), uint32_t(item)).bytes;
 }
 
 template <typename T>
 __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
     using C = typename Cx<T>::t;
-    const int nc = list_ncat(item);
     ListSmem<T> W;
-    W.op = reinterpret_cast<C*>(p);       p += al16(sizeof(C) * (list_opZero(item) + 1));
-    W.y = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * item);
-    W.acc = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * item);
-    W.gam = reinterpret_cast<C*>(p);      p += al16(sizeof(C) * kItemPats);
-    W.ph = reinterpret_cast<PatHdr*>(p);  p += al16(sizeof(PatHdr) * (kItemPats + 1));
-    W.pc = reinterpret_cast<PatConst<T>*>(p); p += al16(sizeof(PatConst<T>) * kItemPats);
-    W.cw = reinterpret_cast<uint32_t*>(p); p += al16(4 * nc);
-    W.cM = reinterpret_cast<T*>(p);
+    W.bar = reinterpret_cast<uint64_t*>(p);  p += 16;
+    W.op = reinterpret_cast<C*>(p);          p += al16(sizeof(C) * (list_opZero(item) + 3));
+    W.y = reinterpret_cast<C*>(p);           p += al16(sizeof(C) * (item + 2));
+    W.acc = reinterpret_cast<C*>(p);         p += al16(sizeof(C) * (item + 2));
+    W.blob = p;
     return W;
 }
 
-// One warp per work item, like stage_kernel, but the hierarchy terms come
-// from host-resolved lists: the lanes take the item's variables in rounds of
-// 32 (sorted by term count, so a round's lanes run the same number of terms),
-// and term t of a round is one coalesced row of 32 (target index,
-// coefficient slot) entries; padded entries name a zero coefficient.  The
-// commutator, damping and loss use the same formula for every kind of
-// variable, with operands and the diagonal class chosen by the host.
+// One warp per work item, like stage_kernel, but
+//  * the item's stage-input, state and accumulator slices and its table blob
+//    (pattern headers and constants, damping rates, category words,
+//    multiplicities and owners, round table, lane words) arrive by four TMA
+//    bulk copies on the warp's mbarrier, and its term rows are prefetched
+//    into L2 by bulk prefetches;
+//  * the hierarchy terms come from host-resolved lists: the lanes take the
+//    item's variables in rounds of 32 (sorted by term count, so a round's
+//    lanes run the same number of terms), and term t of a round is one
+//    coalesced row of 32 (target index, coefficient slot) entries; padded
+//    entries name a zero coefficient;
+//  * the commutator, damping and loss use one formula for every kind of
+//    variable, with operands and the diagonal class chosen by the host.
+// A bounded wait that expires sets bit 0 of the error word; the warp then
+// waits (bounded again) for its copies and stops.
 template <typename T, bool FP64SIDE>
 __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
     using C = typename Cx<T>::t;
@@ -563,14 +619,16 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
     const int wib = threadIdx.x >> 5;
     const int chunk = P.chunk;
     const ListSmem<T> S = carve_list<T>(smem + size_t(wib) * list_smem_bytes<T>(chunk), chunk);
-    C* const opR = S.op + list_opR(chunk);
-    C* const opC = S.op + list_opC(chunk);
-    C* const opZ = S.op + list_opZ(chunk);
-    if (lane == 0) S.op[list_opZero(chunk)] = mk(T(0), T(0));
+    if (lane == 0) {
+        mbar_init(S.bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
     const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
     unsigned int it = blockIdx.x * (blockDim.x >> 5) + wib;
     const T dtT = T(P.dt);
     const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
+    uint32_t parity = 0;
     for (;;) {
         unsigned int c;
         if (P.use_queue) {
@@ -583,54 +641,62 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
         }
         if (c >= P.nchunks) break;
         const ItemDesc d = P.items[c];
-        const int np = int(d.np);
-        const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0, ncat = d.ncat;
-        // ---- stage the item
-        for (uint32_t i = lane; i < nv; i += 32) {
-            S.op[i] = P.x_in[v0 + i];
-            if (P.stage > 0) {
-                S.y[i] = P.y[v0 + i];
-                S.acc[i] = P.acc[v0 + i];
-            }
+        const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0;
+        // ---- bulk copies of the item: lanes 0-3 take one array each
+        const Span sx = span(P.x_in, v0, nv, sizeof(C));
+        Span sp;
+        void* dst = nullptr;
+        if (lane == 0) { sp = sx; dst = S.op; }
+        else if (lane == 1) { sp = span(P.y, v0, P.stage > 0 ? nv : 0u, sizeof(C)); dst = S.y; }
+        else if (lane == 2) { sp = span(P.acc, v0, P.stage > 0 ? nv : 0u, sizeof(C)); dst = S.acc; }
+        else if (lane == 3) {
+            sp.src = reinterpret_cast<const char*>(P.blobs) + size_t(d.blob16) * 16;
+            sp.bytes = d.blob_bytes;
+            dst = S.blob;
         }
-        for (int j = lane; j <= np; j += 32) S.ph[j] = P.hdr[d.p0 + j];
-        for (int j = lane; j < np; j += 32) {
-            S.gam[j] = __ldg(P.gamma + d.p0 + j);
-            const uint32_t inst = P.hdr[d.p0 + j].inst;
-            const InstDev& I = P.inst[inst];
-            PatConst<T> pc;
-            pc.g = sizeof(T) == 8 ? T(I.g) : T(I.gf);
-            pc.det = sizeof(T) == 8 ? T(I.detuning) : T(I.detf);
-            pc.kap = sizeof(T) == 8 ? T(I.kappa) : T(I.kappaf);
-            pc.coef_base = inst * uint32_t(kListCoefStride);
-            S.pc[j] = pc;
-        }
-        for (uint32_t cl = lane; cl < ncat; cl += 32) {
-            S.cw[cl] = __ldg(P.cat_word + c0 + cl);
-            S.cM[cl] = __ldg(P.cat_M + c0 + cl);
-        }
+        else sp.bytes = 0;
+        const uint32_t total = __reduce_add_sync(0xffffffffu, sp.bytes);
+        // earlier generic-proxy accesses of these buffers come before the copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
+        if (lane == 0) mbar_expect_tx(S.bar, total);
+        __syncwarp();
+        if (sp.bytes) bulk_g2s(dst, sp.src, sp.bytes, S.bar);
+        if (lane == 4 && d.row1 > d.row0) bulk_prefetch_l2(P.tidx + size_t(d.row0) * 32, (d.row1 - d.row0) * 128u);
+        if (lane == 5 && d.row1 > d.row0) bulk_prefetch_l2(P.tcid + size_t(d.row0) * 32, (d.row1 - d.row0) * 64u);
+        if (!__all_sync(0xffffffffu, mbar_wait(S.bar, parity))) {
+            if (lane == 0) atomicOr(P.err, 1u);
+            mbar_wait(S.bar, parity);
+            return;
+        }
+        parity ^= 1u;
+        const int np = int(d.np);
+        const uint32_t ncat = d.ncat, nl = d.nl;
+        const BlobLayout B = blob_layout<T>(uint32_t(np), ncat, nl);
+        const PatHdr* const ph = reinterpret_cast<const PatHdr*>(S.blob + B.hdr);
+        const uint32_t* const cw = reinterpret_cast<const uint32_t*>(S.blob + B.cw);
+        const T* const cM = reinterpret_cast<const T*>(S.blob + B.cM);
+        const uint8_t* const cj = S.blob + B.cj;
+        C* const op = S.op + sx.skip;
+        C* const opR = op + list_opR(chunk);
+        C* const opC = op + list_opC(chunk);
+        C* const opZ = op + list_opZ(chunk);
+        if (lane == 0) op[list_opZero(chunk)] = mk(T(0), T(0));
         // ---- grouped sums per category (Eqs. grouped-row-sum,
         // grouped-column-sum) and per pattern (Eq. HZ)
         for (uint32_t cl = lane; cl < ncat; cl += 32) {
-            int lo = 0, hi = np - 1;  // owning pattern: last j with cat_off <= c0 + cl
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (S.ph[mid].cat_off - c0 <= cl) lo = mid;
-                else hi = mid - 1;
-            }
-            const PatHdr h = S.ph[lo];
+            const PatHdr h = ph[cj[cl]];
             const int G = h.G;
             const int cb = int(h.cat_off - c0);
             const int q = int(cl) - cb + 1;
-            const C* xp = S.op + (h.var_off - v0);
-            const T Mq = S.cM[cl];
+            const C* xp = op + (h.var_off - v0);
+            const T Mq = cM[cl];
             C Rs = xp[2 * G + q];
-            if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((S.cw[cl] >> 15) & 31)], Rs);
+            if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((cw[cl] >> 15) & 31)], Rs);
             C Cq = Rs;
             for (int e2 = 1; e2 <= G; ++e2) {
                 if (e2 == q) continue;
-                const T Mb = S.cM[cb + e2 - 1];
+                const T Mb = cM[cb + e2 - 1];
                 Rs = caxpy(Mb, xp[loc_S_d(G, q, e2)], Rs);
                 Cq = caxpy(Mb, xp[loc_S_d(G, e2, q)], Cq);
             }
@@ -638,41 +704,42 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
             opC[cl] = Cq;
         }
         for (int j = lane; j < np; j += 32) {
-            const PatHdr h = S.ph[j];
+            const PatHdr h = ph[j];
             const int G = h.G;
             const int cb = int(h.cat_off - c0);
-            const C* xp = S.op + (h.var_off - v0);
+            const C* xp = op + (h.var_off - v0);
             C zs = mk(T(0), T(0));
-            for (int q = 1; q <= G; ++q) zs = caxpy(S.cM[cb + q - 1], csub(xp[q], xp[G + q]), zs);
+            for (int q = 1; q <= G; ++q) zs = caxpy(cM[cb + q - 1], csub(xp[q], xp[G + q]), zs);
             opZ[j] = zs;
         }
         __syncwarp();
         // ---- the lanes' variables, one round of 32 at a time
-        const uint32_t nl = d.nl;
-        const uint32_t* __restrict__ rb = P.rbase + d.r0;
         const C* __restrict__ X = P.x_in;
+        const uint32_t* const lvd = reinterpret_cast<const uint32_t*>(S.blob + B.lvd);
+        const uint8_t* const lvj = S.blob + B.lvj;
+        const uint32_t* const rb = reinterpret_cast<const uint32_t*>(S.blob + B.rb);
         for (uint32_t i0 = 0, rho = 0; i0 < nl; i0 += 32, ++rho) {
             const uint32_t i = i0 + lane;
             const bool on = i < nl;
             // lanes past the end take operand 0 and the zero-coefficient rows
-            const uint32_t w0 = on ? __ldg(P.lvd + v0 + i) : 0u;
-            const uint32_t w1 = on ? uint32_t(__ldg(P.lvj + v0 + i)) : 0u;
+            const uint32_t w0 = on ? lvd[i] : 0u;
+            const uint32_t w1 = on ? uint32_t(lvj[i]) : 0u;
             const uint32_t l = w0 & 1023u, a = (w0 >> 10) & 2047u, b = w0 >> 21;
             const int j = int(w1 & 31u), cls = int(w1 >> 5);
-            const C v = S.op[l];
-            const C gam = S.gam[j];
-            const PatConst<T> pc = S.pc[j];
+            const C v = op[l];
+            const C gm = reinterpret_cast<const C*>(S.blob + B.gam)[j];
+            const PatConst<T> pc = reinterpret_cast<const PatConst<T>*>(S.blob + B.pc)[j];
             // diagonal: -Gamma, the cavity loss (1/2 per cavity index) and
             // -/+ i detuning for X / Y (classes: 0 P S T, 1 X, 2 Y, 3 Z)
             const T lossf = cls == 0 ? T(0) : (cls == 3 ? T(1) : T(0.5));
             const T dim = cls == 1 ? -pc.det : (cls == 2 ? pc.det : T(0));
-            const C diag = mk(-(gam.x + lossf * pc.kap), dim - gam.y);
-            const C t = csub(S.op[a], S.op[b]);
+            const C diag = mk(-(gm.x + lossf * pc.kap), dim - gm.y);
+            const C t = csub(op[a], op[b]);
             C dv = mk(pc.g * t.y, -pc.g * t.x);
             dv = cfma(diag, v, dv);
             // hierarchy terms (Eqs. uvar-up, uvar-down)
             const C* __restrict__ cf = P.lcoef + pc.coef_base;
-            const uint32_t r0 = __ldg(rb + rho), r1 = __ldg(rb + rho + 1);
+            const uint32_t r0 = rb[rho], r1 = rb[rho + 1];
             const uint32_t* __restrict__ ti = P.tidx + size_t(r0) * 32 + lane;
             const uint16_t* __restrict__ tc = P.tcid + size_t(r0) * 32 + lane;
             const int nt = int(r1 - r0);
@@ -702,14 +769,122 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
                     P.acc[vg] = dv;
                     P.x_out[vg] = caxpy(aT, dv, v);  // x_in is y in the first stage
                 } else if (P.stage == 3) {
-                    P.y_out[vg] = caxpy(dtT / T(6), cadd(S.acc[l], dv), S.y[l]);
+                    P.y_out[vg] = caxpy(dtT / T(6), cadd(S.acc[sx.skip + l], dv), S.y[sx.skip + l]);
                 } else {
-                    P.acc[vg] = caxpy(T(2), dv, S.acc[l]);
-                    P.x_out[vg] = caxpy(aT, dv, S.y[l]);
+                    P.acc[vg] = caxpy(T(2), dv, S.acc[sx.skip + l]);
+                    P.x_out[vg] = caxpy(aT, dv, S.y[sx.skip + l]);
                 }
             }
         }
         __syncwarp();
+    }
+}
+
+// ---- ELL kernel ------------------------------------------------------------
+// One thread per unique variable, lanes in memory order: warp w takes the 32
+// consecutive variables [32 w, 32 w + 32) of the batch vector, so the state,
+// the accumulator and the outputs move in full coalesced rows, and needs no
+// shared memory.  The hierarchy terms of the warp are T_w rows of 32
+// (target index, coefficient slot) entries, T_w the longest list among its
+// lanes (shorter lists padded with the zero slot).  The commutator reads the
+// variable's own-pattern operands from x directly (L1-resident: the warp reads
+// the same pattern); X_q, Y_q and Z form their grouped sums (Eqs.
+// grouped-row-sum, grouped-column-sum, HZ) in a loop over the categories.
+// Per-variable word: pattern offset from the warp's first pattern (5 bits) |
+// kind << 5 | q << 8 | r << 13 | T-rank of q << 18 (31: none).
+template <typename T, bool FP64SIDE>
+__global__ void __launch_bounds__(256) ell_stage_kernel(StageParams<T> P) {
+    using C = typename Cx<T>::t;
+    const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t w = v >> 5;
+    const uint32_t nw = (P.nvar + 31) >> 5;
+    if (w >= nw) return;  // whole warps only
+    const int lane = int(v & 31u);
+    const bool on = v < P.nvar;
+    const uint32_t e = on ? __ldg(P.lvd + v) : 0u;
+    const uint32_t p = __ldg(P.wpat + w) + (e & 31u);
+    const PatHdr h = P.hdr[p];
+    const int kind = int((e >> 5) & 7u), q = int((e >> 8) & 31u), r = int((e >> 13) & 31u);
+    const int trq = int((e >> 18) & 31u);
+    const C* __restrict__ X = P.x_in;
+    const bool live = on && !(FP64SIDE && h.tier == 0);  // SA_FP32_AUX: tier 0 is integrated in FP64
+    const uint32_t base = h.var_off;
+    const int G = h.G;
+    const InstDev& I = P.inst[h.inst];
+    const T g = sizeof(T) == 8 ? T(I.g) : T(I.gf);
+    const T det = sizeof(T) == 8 ? T(I.detuning) : T(I.detf);
+    const T kap = sizeof(T) == 8 ? T(I.kappa) : T(I.kappaf);
+    const C gam = __ldg(P.gamma + p);
+    const C xv = __ldg(X + (on ? v : 0u));
+    // operands of -i g (a - b)
+    C a, b;
+    if (kind == KS || kind == KP || kind == KT) {
+        a = __ldg(X + base + G + (kind == KS ? r : q));
+        b = __ldg(X + base + q);
+    } else {
+        const C Z = __ldg(X + base);
+        C s = mk(T(0), T(0));
+        if (kind != KZ) {
+            // R_q (X) or C_q (Y): P_q + (M_q - 1) T_q + sum_{b != q} M_b S
+            s = __ldg(X + base + 2 * G + q);
+            if (trq != 31) s = caxpy(__ldg(P.cat_M + h.cat_off + q - 1) - T(1), __ldg(X + base + (G + 1) * (G + 1) + trq), s);
+        }
+        for (int b2 = 1; b2 <= G; ++b2) {
+            const T Mb = __ldg(P.cat_M + h.cat_off + b2 - 1);
+            if (kind == KZ) {
+                s = caxpy(Mb, csub(__ldg(X + base + b2), __ldg(X + base + G + b2)), s);
+            } else if (b2 != q) {
+                const int l = kind == KX ? loc_S_d(G, q, b2) : loc_S_d(G, b2, q);
+                s = caxpy(Mb, __ldg(X + base + l), s);
+            }
+        }
+        if (kind == KX) { a = Z; b = s; }
+        else if (kind == KY) { a = s; b = Z; }
+        else { a = s; b = mk(T(0), T(0)); }
+    }
+    const T lossf = kind == KZ ? T(1) : ((kind == KX || kind == KY) ? T(0.5) : T(0));
+    const T dim = kind == KX ? -det : (kind == KY ? det : T(0));
+    const C diag = mk(-(gam.x + lossf * kap), dim - gam.y);
+    const C t = csub(a, b);
+    C dv = mk(g * t.y, -g * t.x);
+    dv = cfma(diag, xv, dv);
+    // hierarchy terms (Eqs. uvar-up, uvar-down)
+    const C* __restrict__ cf = P.lcoef + h.inst * uint32_t(kListCoefStride);
+    const uint32_t r0 = __ldg(P.rbase + w), r1 = __ldg(P.rbase + w + 1);
+    const uint32_t* __restrict__ ti = P.tidx + size_t(r0) * 32 + lane;
+    const uint16_t* __restrict__ tc = P.tcid + size_t(r0) * 32 + lane;
+    const int nt = int(r1 - r0);
+    int t2 = 0;
+    for (; t2 + 4 <= nt; t2 += 4) {
+        uint32_t ix[4], cx[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            ix[u] = __ldg(ti + (t2 + u) * 32);
+            cx[u] = __ldg(tc + (t2 + u) * 32);
+        }
+        C xs[4], cs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            xs[u] = __ldg(X + ix[u]);
+            cs[u] = __ldg(cf + cx[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dv = cfma(cs[u], xs[u], dv);
+    }
+    for (; t2 < nt; ++t2) dv = cfma(__ldg(cf + __ldg(tc + t2 * 32)), __ldg(X + __ldg(ti + t2 * 32)), dv);
+    if (!live) return;
+    const T dtT = T(P.dt);
+    if (P.stage < 0) {
+        P.x_out[v] = dv;
+    } else if (P.stage == 0) {
+        P.acc[v] = dv;
+        P.x_out[v] = caxpy(T(0.5) * dtT, dv, xv);  // x_in is y in the first stage
+    } else if (P.stage == 3) {
+        P.y_out[v] = caxpy(dtT / T(6), cadd(P.acc[v], dv), P.y[v]);
+    } else {
+        const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
+        P.acc[v] = caxpy(T(2), dv, P.acc[v]);
+        P.x_out[v] = caxpy(aT, dv, P.y[v]);
     }
 }
 
@@ -820,6 +995,7 @@ __global__ void init_rho0_kernel(const InstDev* __restrict__ inst, int ninst, co
 // ---- host launch wrappers (called from api.cu) -----------------------------
 
 size_t stage_smem_bytes(int item, int block, bool fp64, int kernel) {
+    if (kernel == SA_KERNEL_ELL) return 0;
     size_t w;
     if (kernel == SA_KERNEL_LISTS) w = fp64 ? list_smem_bytes<double>(item) : list_smem_bytes<float>(item);
     else w = fp64 ? warp_smem_bytes<double>(item) : warp_smem_bytes<float>(item);
@@ -837,8 +1013,14 @@ void list_operand_layout(int item, int* opR, int* opC, int* opZ, int* opZero) {
 template <typename T, bool SIDE>
 static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int ninst, cudaStream_t st) {
     const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, sizeof(T) == 8, cfg.kernel);
-    if (cfg.kernel == SA_KERNEL_LISTS) list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
-    else stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+    if (cfg.kernel == SA_KERNEL_ELL) {
+        const unsigned grid = unsigned((size_t(p.nvar) + 31) / 32 * 32 + cfg.block - 1) / unsigned(cfg.block);
+        if (grid > 0) ell_stage_kernel<T, SIDE><<<grid, cfg.block, 0, st>>>(p);
+    } else if (cfg.kernel == SA_KERNEL_LISTS) {
+        list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+    } else {
+        stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+    }
     if (SIDE) {
         const int threads = ninst * kSideSlots;
         rho0_kernel<T><<<(threads + 127) / 128, 128, 0, st>>>(p, ninst);
@@ -873,6 +1055,9 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.tidx = static_cast<const uint32_t*>(s.tidx);
     p.tcid = static_cast<const uint16_t*>(s.tcid);
     p.lcoef = static_cast<const C*>(s.lcoef);
+    p.wpat = static_cast<const uint32_t*>(s.wpat);
+    p.blobs = static_cast<const unsigned char*>(s.blobs);
+    p.nvar = s.nvar;
     p.nchunks = s.nchunks;
     p.chunk = cfg.chunk;
     p.x_in = static_cast<const C*>(s.x_in);
@@ -917,6 +1102,11 @@ cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm)
     if (sm > size_t(lim)) {
         *blocks_per_sm = 0;
         return cudaSuccess;
+    }
+    if (cfg.kernel == SA_KERNEL_ELL) {
+        if (fp64) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ell_stage_kernel<double, false>,
+                                                                       cfg.block, 0);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ell_stage_kernel<float, true>, cfg.block, 0);
     }
     if (cfg.kernel == SA_KERNEL_LISTS) {
         if (fp64) return occupancy_of(list_stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);

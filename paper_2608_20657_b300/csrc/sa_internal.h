@@ -112,9 +112,49 @@ struct DRecA {
 // patterns and the ranges of their variables and categories
 struct ItemDesc {
     uint32_t p0, np, v0, nv, c0, ncat;
-    uint32_t r0;  // list kernel: first round of 32 lanes in the round table
-    uint32_t nl;  // list kernel: variables the lanes take (the item's, less any integrated elsewhere)
+    uint32_t r0;          // list kernel: first round of 32 lanes in the round table
+    uint32_t nl;          // list kernel: variables the lanes take (the item's, less any integrated elsewhere)
+    uint32_t row0, row1;  // list kernel: the item's term rows
+    uint32_t blob16;      // list kernel: the item's table blob, in 16-byte units
+    uint32_t blob_bytes;
 };
+
+// per-pattern constants of the list kernel (T = float or double)
+template <typename T> struct PatConst {
+    T g, det, kap;       // coupling, detuning, loss rate of the pattern's instance
+    uint32_t coef_base;  // the instance's coefficient table
+};
+
+// Byte offsets of the sections of a list-kernel item blob (every section
+// 16-byte aligned): pattern headers, pattern constants, damping rates
+// Gamma_Lambda (complex T), category words, multiplicities (T), owning
+// pattern of every category (u8), round table (first term row of every
+// round and the end), lane words, lane bytes.
+struct BlobLayout {
+    uint32_t hdr, pc, gam, cw, cM, cj, rb, lvd, lvj, bytes;
+};
+#if defined(__CUDACC__)
+#define SA_HOST_DEVICE __host__ __device__
+#else
+#define SA_HOST_DEVICE
+#endif
+template <typename T>
+SA_HOST_DEVICE inline BlobLayout blob_layout(uint32_t np, uint32_t ncat, uint32_t nl) {
+    auto a16 = [](uint32_t b) { return (b + 15u) & ~15u; };
+    const uint32_t nrounds = (nl + 31u) / 32u;
+    BlobLayout L;
+    L.hdr = 0;
+    L.pc = L.hdr + a16(np * uint32_t(sizeof(PatHdr)));
+    L.gam = L.pc + a16(np * uint32_t(sizeof(PatConst<T>)));
+    L.cw = L.gam + a16(np * 2u * uint32_t(sizeof(T)));
+    L.cM = L.cw + a16(ncat * 4u);
+    L.cj = L.cM + a16(ncat * uint32_t(sizeof(T)));
+    L.rb = L.cj + a16(ncat);
+    L.lvd = L.rb + a16((nrounds + 1u) * 4u);
+    L.lvj = L.lvd + a16(nl * 4u);
+    L.bytes = L.lvj + a16(nl);
+    return L;
+}
 constexpr int kItemPats = 32;     // patterns per work item (5-bit local index)
 constexpr int kMaxItemVars = 1024; // variables per work item (10-bit local index)
 // list kernel: coefficient slots per instance -- row coefficients, column
@@ -129,7 +169,7 @@ struct LaunchCfg {
     int chunk;      // variable capacity of one work item
     int use_queue;  // 1: persistent grid + atomic work queue
     int grid;       // CTAs
-    int kernel;     // SA_KERNEL_RECORDS or SA_KERNEL_LISTS (include/sa_heom.h)
+    int kernel;     // SA_KERNEL_RECORDS, SA_KERNEL_LISTS or SA_KERNEL_ELL (include/sa_heom.h)
 };
 struct StageLaunch {
     const void* hdr; const void* cat_word; const void* cat_M; const void* gamma; const void* rec;
@@ -138,6 +178,7 @@ struct StageLaunch {
     const void* cat_Md; const void* coef_row_d; const void* coef_col_d;
     const void* lut; const void* lut_off;
     const void* lvd; const void* lvj; const void* rbase; const void* tidx; const void* tcid; const void* lcoef;
+    const void* wpat; uint32_t nvar; const void* blobs;
     uint32_t nchunks;
     const void* x_in; void* x_out; const void* y; void* acc; void* y_out;
     const void* xs_in; void* xs_out; const void* ys; void* accs; void* ys_out;

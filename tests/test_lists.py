@@ -1,4 +1,5 @@
-"""The term lists of the SA_KERNEL_LISTS stage kernel, checked on the CPU.
+"""The term tables of the SA_KERNEL_LISTS and SA_KERNEL_ELL stage kernels,
+checked on the CPU.
 
 A host-only handle builds the same lists the device kernel reads.  Here they
 are evaluated in numpy the way the kernel does -- per work item an operand
@@ -182,6 +183,107 @@ def test_lists_batch_and_chunk():
         ps.append(S.make_params(N, m, L, b, **kw))
     _case(ps, baths, sas, S.SA_FP32_AUX, chunk=256)
     _case(ps, baths, sas, S.SA_FP64, chunk=64)
+
+
+def _eval_ell(lib, sas, baths, x):
+    """Right-hand side of the batch from the dumped ELL tables."""
+    E = lib.dump_ell()
+    pats = [lib.dump_patterns(i) for i in range(len(sas))]
+    voff = [lib.var_offset(i) for i in range(len(sas))]
+    labs = [sa.var_labels() for sa in sas]
+    gvar, ginst, gG, gM, ggam = [], [], [], [], []
+    for i, (P, sa) in enumerate(zip(pats, sas)):
+        vec = sa.vectors().astype(float)
+        nu = np.asarray(baths[i]["nu"])
+        for p in range(P["G"].size):
+            gvar.append(voff[i] + P["var_off"][p])
+            ginst.append(i)
+            gG.append(P["G"][p])
+            gM.append(P["cat_M"][P["cat_off"][p]:P["cat_off"][p + 1]])
+            ggam.append(sum(vec[v] @ nu for v in P["ids"][p] if v >= 0))
+    gvar.append(x.size)
+    coefs = [_slot_coefficients(b) for b in baths]
+    out = np.zeros(x.size, complex)
+    nw = E["wpat"].size
+    assert nw == (x.size + 31) // 32
+    for v in range(x.size):
+        w, lane = v >> 5, v & 31
+        e = int(E["vword"][v])
+        p = int(E["wpat"][w]) + (e & 31)
+        kind, q, r, trq = (e >> 5) & 7, (e >> 8) & 31, (e >> 13) & 31, (e >> 18) & 31
+        assert gvar[p] <= v < gvar[p + 1]
+        inst = ginst[p]
+        lab = labs[inst]
+        lv = v - voff[inst]
+        assert (kind, q, r) == (lab["kind"][lv], lab["q"][lv], lab["r"][lv] if kind == 4 else 0)
+        G, M = gG[p], gM[p]
+        X, Y, P, Sv, T = _layout(G, M)
+        assert trq == (T(q) - (G + 1) ** 2 if q and M[q - 1] >= 2 else 31)
+        xp = x[gvar[p]:]
+        if kind in (3, 4, 5):
+            a, b = xp[Y(r if kind == 4 else q)], xp[X(q)]
+        elif kind == 0:
+            a, b = sum(M[c - 1] * (xp[X(c)] - xp[Y(c)]) for c in range(1, G + 1)), 0
+        else:
+            s = xp[P(q)] + ((M[q - 1] - 1) * xp[T(q)] if M[q - 1] >= 2 else 0)
+            if kind == 1:
+                a, b = xp[0], s + sum(M[c - 1] * xp[Sv(q, c)] for c in range(1, G + 1) if c != q)
+            else:
+                a, b = s + sum(M[c - 1] * xp[Sv(c, q)] for c in range(1, G + 1) if c != q), xp[0]
+        sp = sas[inst].params
+        lossf = {0: 1.0, 1: 0.5, 2: 0.5}.get(kind, 0.0)
+        dim = {1: -sp.detuning, 2: sp.detuning}.get(kind, 0.0)
+        diag = -(ggam[p].real + lossf * sp.kappa) + 1j * (dim - ggam[p].imag)
+        rows = np.arange(int(E["rbase"][w]), int(E["rbase"][w + 1]))
+        idx, slot = E["tidx"][rows * 32 + lane].astype(np.int64), E["tcid"][rows * 32 + lane].astype(np.int64)
+        real = slot != ZERO_SLOT
+        n = int(real.sum())
+        assert np.all(real[:n]) and not np.any(real[n:])
+        out[v] = diag * x[v] - 1j * sp.g * (a - b) + np.sum(coefs[inst][slot[:n]] * x[idx[:n]])
+    # every warp's rows are as many as its longest list
+    for w in range(nw):
+        rows = np.arange(int(E["rbase"][w]), int(E["rbase"][w + 1]))
+        if rows.size:
+            assert np.any(E["tcid"][rows[-1] * 32:(rows[-1] + 1) * 32] != ZERO_SLOT)
+    return out
+
+
+@pytest.mark.parametrize("precision", [S.SA_FP64, S.SA_FP32_AUX])
+@pytest.mark.parametrize("N,m,L", [(1, 1, 3), (3, 2, 3), (10, 2, 6), (7, 4, 3)])
+def test_ell_reproduces_oracle_rhs(N, m, L, precision):
+    bath = _generic_bath(m, N + 7 * m + L)
+    kw = dict(detuning=0.1, g=0.2, kappa=0.05)
+    sa = oracle.SA(N, m, L, bath, **kw)
+    lib = S.Heom(S.make_params(N, m, L, bath, **kw), precision=precision, host_only=True)
+    lib.set_kernel(S.SA_KERNEL_ELL)
+    x = W.random_state(sa.nvar, seed=5)
+    got = _eval_ell(lib, [sa], [bath], x)
+    ref = sa.rhs(x)
+    n0 = (5 if N >= 2 else 4) if precision == S.SA_FP32_AUX else 0  # no lists for the FP64-integrated rho_0
+    if n0:
+        # without its hierarchy terms, the physical representative differs
+        assert np.max(np.abs(got[:n0] - ref[:n0])) > 1e-6
+    np.testing.assert_allclose(got[n0:], ref[n0:], rtol=0, atol=1e-12 * max(1.0, np.abs(ref).max()))
+
+
+def test_ell_batch():
+    specs = [(3, 1, 4, 1), (9, 2, 3, 2), (5, 3, 3, 3)]
+    sas, baths, ps = [], [], []
+    for N, m, L, seed in specs:
+        b = _generic_bath(m, seed)
+        kw = dict(detuning=0.03 * seed, g=0.1 / seed, kappa=0.01 * seed)
+        sas.append(oracle.SA(N, m, L, b, **kw))
+        baths.append(b)
+        ps.append(S.make_params(N, m, L, b, **kw))
+    lib = S.Heom(ps, precision=S.SA_FP64, host_only=True)
+    lib.set_kernel(S.SA_KERNEL_ELL)
+    xs = [W.random_state(sa.nvar, seed=i) for i, sa in enumerate(sas)]
+    got = _eval_ell(lib, sas, baths, np.concatenate(xs))
+    off = 0
+    for sa, x in zip(sas, xs):
+        ref = sa.rhs(x)
+        np.testing.assert_allclose(got[off:off + sa.nvar], ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+        off += sa.nvar
 
 
 def test_lists_state_errors():
