@@ -651,7 +651,9 @@ int apply_tuning(sa_heom* h) {
     if (occ < 1) return fail(SA_ERR_UNSUPPORTED, "stage kernel does not fit on an SM with this tuning (shared memory)");
     const int wpb = h->block / 32;
     const int64_t blocks_needed = (int64_t(nchunks) + wpb - 1) / wpb;
-    h->cfg.grid = h->use_queue ? int(std::min<int64_t>(int64_t(h->num_sms) * occ, blocks_needed)) : int(blocks_needed);
+    // the list kernel is persistent in both modes (its warps pipeline their items)
+    const bool persistent = h->use_queue || h->kernel == SA_KERNEL_LISTS;
+    h->cfg.grid = persistent ? int(std::min<int64_t>(int64_t(h->num_sms) * occ, blocks_needed)) : int(blocks_needed);
     if (h->cfg.grid < 1) h->cfg.grid = 1;
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();

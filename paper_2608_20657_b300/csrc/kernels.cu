@@ -571,11 +571,13 @@ template <typename T> struct ListSmem {
 };
 
 __host__ __device__ __forceinline__ int list_ncat(int item) { return item / 4 + 8; }
-// operand-area layout (host and device): x slice, R, C, Z sums, zero
-__host__ __device__ __forceinline__ int list_opR(int item) { return item; }
-__host__ __device__ __forceinline__ int list_opC(int item) { return item + list_ncat(item); }
-__host__ __device__ __forceinline__ int list_opZ(int item) { return item + 2 * list_ncat(item); }
-__host__ __device__ __forceinline__ int list_opZero(int item) { return item + 2 * list_ncat(item) + kItemPats; }
+// operand-area layout (host and device): x slice, two entries the slice's
+// bulk copy may round into, R, C, Z sums, zero.  The bulk copies never write
+// where the warp writes, so no proxy fence is needed between items.
+__host__ __device__ __forceinline__ int list_opR(int item) { return item + 2; }
+__host__ __device__ __forceinline__ int list_opC(int item) { return item + 2 + list_ncat(item); }
+__host__ __device__ __forceinline__ int list_opZ(int item) { return item + 2 + 2 * list_ncat(item); }
+__host__ __device__ __forceinline__ int list_opZero(int item) { return item + 2 + 2 * list_ncat(item) + kItemPats; }
 
 template <typename T>
 __host__ __device__ __forceinline__ size_t list_smem_bytes(int item) {
@@ -656,9 +658,8 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
         }
         else sp.bytes = 0;
         const uint32_t total = __reduce_add_sync(0xffffffffu, sp.bytes);
-        // earlier generic-proxy accesses of these buffers come before the copies
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
+        // the copies overwrite only what the warp has read (the previous
+        // item's slices and blob), after the __syncwarp that ended it
         if (lane == 0) mbar_expect_tx(S.bar, total);
         __syncwarp();
         if (sp.bytes) bulk_g2s(dst, sp.src, sp.bytes, S.bar);
