@@ -314,6 +314,8 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best);
  *                      in memory order (warp w takes variables 32 w ..
  *                      32 w + 31): T_w rows of 32 entries per warp, T_w its
  *                      longest list; 4 B per variable; no shared memory.
+ *                      A grouped-sum kernel forms R_q, C_q and the Z sums
+ *                      first (scratch: 2 per category + 1 per pattern).
  *                      The item capacity (chunk) does not apply to it.
  * sa_heom_set_kernel rebuilds the launch tables (synchronous; INVALID_ARG for
  * an unknown variant, OOM if the lists do not fit).  sa_heom_get_tuning
@@ -325,7 +327,8 @@ int sa_heom_get_tuning(const sa_heom* h, int* out);
 
 /* Kernel launches one RK4 step issues: 4 stage kernels (SA_FP64), or 4 stage
  * kernels each followed by the FP64 physical-representative kernel
- * (SA_FP32_AUX). */
+ * (SA_FP32_AUX); SA_KERNEL_ELL adds a grouped-sum kernel before each stage
+ * kernel. */
 int sa_heom_launches_per_step(const sa_heom* h);
 
 /*

@@ -107,6 +107,8 @@ struct sa_heom {
     void* d_lcoef = nullptr;
     void* d_wpat = nullptr;
     void* d_blobs = nullptr;
+    void* d_catpat = nullptr;  // ELL: owning pattern of every category
+    void* d_sums = nullptr;    // ELL: grouped sums scratch (R, C per category; Z per pattern)
     unsigned int* d_err = nullptr;
     void* d_work[3] = {nullptr, nullptr, nullptr};  // acc, xa, xb
     unsigned int* d_queue = nullptr;
@@ -611,6 +613,16 @@ int ensure_tables(sa_heom* h) {
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_lvd, h->lvd);
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_wpat, h->wpat);
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_rbase, h->rbase);
+        if (!rc && k == SA_KERNEL_ELL && !h->d_catpat) {
+            std::vector<uint32_t> cp(size_t(h->ncat));
+            for (int64_t p = 0; p < h->npat; ++p)
+                for (uint32_t c = h->hdr[p].cat_off; c < h->hdr[p + 1].cat_off; ++c) cp[c] = uint32_t(p);
+            rc = upload(&h->d_catpat, cp);
+        }
+        if (!rc && k == SA_KERNEL_ELL && !h->d_sums) {
+            const size_t bytes = size_t(2 * h->ncat + h->npat) * (h->precision == SA_FP64 ? 16 : 8);
+            if (cudaMalloc(&h->d_sums, bytes) != cudaSuccess) rc = fail(SA_ERR_OOM, "grouped-sum scratch");
+        }
         if (!rc) rc = upload(&h->d_tidx, h->tidx);
         if (!rc) rc = upload(&h->d_tcid, h->tcid);
         // the host copies are not needed again
@@ -667,7 +679,7 @@ void free_device(sa_heom* h) {
                     h->d_coef_row, h->d_coef_col, h->d_coef_row_d, h->d_coef_col_d, h->d_lut, h->d_lut_off,
                     h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0,
                     h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS, h->d_lvd, h->d_lvj, h->d_rbase,
-                    h->d_tidx, h->d_tcid, h->d_lcoef, h->d_wpat, h->d_blobs};
+                    h->d_tidx, h->d_tcid, h->d_lcoef, h->d_wpat, h->d_blobs, h->d_catpat, h->d_sums};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -711,6 +723,10 @@ StageLaunch base_launch(const sa_heom* h) {
     s.lcoef = h->d_lcoef;
     s.wpat = h->d_wpat;
     s.blobs = h->d_blobs;
+    s.catpat = h->d_catpat;
+    s.ncat = uint32_t(h->ncat);
+    s.npat = uint32_t(h->npat);
+    s.sums = h->d_sums;
     s.nvar = uint32_t(h->nvar);
     s.nchunks = uint32_t(h->items.size());
     s.err = h->d_err;
@@ -1435,7 +1451,11 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
 
 // four stage kernels, plus the FP64 physical-representative kernel after each
 // stage in SA_FP32_AUX mode
-int sa_heom_launches_per_step(const sa_heom* h) { return h ? (h->precision == SA_FP64 ? 4 : 8) : 0; }
+int sa_heom_launches_per_step(const sa_heom* h) {
+    if (!h) return 0;
+    const int per_stage = 1 + (h->precision == SA_FP64 ? 0 : 1) + (h->kernel == SA_KERNEL_ELL ? 1 : 0);
+    return 4 * per_stage;
+}
 
 int sa_heom_device_error(sa_heom* h, void* stream) {
     int rc = check_device(h);

@@ -91,6 +91,11 @@ template <typename T> struct StageParams {
     const unsigned char* __restrict__ blobs; // list kernel: per-item table blobs (16-byte aligned)
     const uint32_t* __restrict__ wpat;      // first pattern of every warp row of 32 variables
     uint32_t nvar;
+    const uint32_t* __restrict__ catpat;    // owning pattern of every category
+    uint32_t ncat, npat;
+    C* sumR;                                // grouped row sums R_q per category
+    C* sumC;                                // grouped column sums C_q per category
+    C* sumZ;                                // sum_q M_q (X_q - Y_q) per pattern
     uint32_t nchunks;
     int chunk;                              // variable capacity of one work item
     const C* x_in;                          // stage input (gathered)
@@ -782,6 +787,47 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
 }
 
 // ---- ELL kernel ------------------------------------------------------------
+// Grouped sums of the stage input, one thread each: R_q and C_q of every
+// category (Eqs. grouped-row-sum, grouped-column-sum: P_q + (M_q - 1) T_q +
+// sum_{b != q} M_b S_{q,b}, resp. S_{b,q}), then sum_q M_q (X_q - Y_q) of
+// every pattern (Eq. HZ), into the scratch arrays the ELL kernel reads.
+template <typename T, bool FP64SIDE>
+__global__ void __launch_bounds__(256) grouped_sums_kernel(StageParams<T> P) {
+    using C = typename Cx<T>::t;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const C* __restrict__ X = P.x_in;
+    if (t < P.ncat) {
+        const uint32_t p = __ldg(P.catpat + t);
+        const PatHdr h = P.hdr[p];
+        if (FP64SIDE && h.tier == 0) return;  // integrated in FP64
+        const int G = h.G;
+        const int q = int(t - h.cat_off) + 1;
+        const C* xp = X + h.var_off;
+        const T* M = P.cat_M + h.cat_off;
+        const uint32_t tr = (__ldg(P.cat_word + t) >> 15) & 31u;
+        C Rs = __ldg(xp + 2 * G + q);
+        if (tr != 31u) Rs = caxpy(__ldg(M + q - 1) - T(1), __ldg(xp + (G + 1) * (G + 1) + int(tr)), Rs);
+        C Cq = Rs;
+        for (int b = 1; b <= G; ++b) {
+            if (b == q) continue;
+            const T Mb = __ldg(M + b - 1);
+            Rs = caxpy(Mb, __ldg(xp + loc_S_d(G, q, b)), Rs);
+            Cq = caxpy(Mb, __ldg(xp + loc_S_d(G, b, q)), Cq);
+        }
+        P.sumR[t] = Rs;
+        P.sumC[t] = Cq;
+    } else if (t < P.ncat + P.npat) {
+        const uint32_t p = t - P.ncat;
+        const PatHdr h = P.hdr[p];
+        if (FP64SIDE && h.tier == 0) return;
+        const C* xp = X + h.var_off;
+        const T* M = P.cat_M + h.cat_off;
+        C zs = mk(T(0), T(0));
+        for (int q = 1; q <= int(h.G); ++q) zs = caxpy(__ldg(M + q - 1), csub(__ldg(xp + q), __ldg(xp + h.G + q)), zs);
+        P.sumZ[p] = zs;
+    }
+}
+
 // One thread per unique variable, lanes in memory order: warp w takes the 32
 // consecutive variables [32 w, 32 w + 32) of the batch vector, so the state,
 // the accumulator and the outputs move in full coalesced rows, and needs no
@@ -789,8 +835,8 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
 // (target index, coefficient slot) entries, T_w the longest list among its
 // lanes (shorter lists padded with the zero slot).  The commutator reads the
 // variable's own-pattern operands from x directly (L1-resident: the warp reads
-// the same pattern); X_q, Y_q and Z form their grouped sums (Eqs.
-// grouped-row-sum, grouped-column-sum, HZ) in a loop over the categories.
+// the same pattern) and the grouped sums of X_q, Y_q and Z from the arrays
+// grouped_sums_kernel wrote.
 // Per-variable word: pattern offset from the warp's first pattern (5 bits) |
 // kind << 5 | q << 8 | r << 13 | T-rank of q << 18 (31: none).
 template <typename T, bool FP64SIDE>
@@ -806,7 +852,6 @@ __global__ void __launch_bounds__(256) ell_stage_kernel(StageParams<T> P) {
     const uint32_t p = __ldg(P.wpat + w) + (e & 31u);
     const PatHdr h = P.hdr[p];
     const int kind = int((e >> 5) & 7u), q = int((e >> 8) & 31u), r = int((e >> 13) & 31u);
-    const int trq = int((e >> 18) & 31u);
     const C* __restrict__ X = P.x_in;
     const bool live = on && !(FP64SIDE && h.tier == 0);  // SA_FP32_AUX: tier 0 is integrated in FP64
     const uint32_t base = h.var_off;
@@ -822,26 +867,15 @@ __global__ void __launch_bounds__(256) ell_stage_kernel(StageParams<T> P) {
     if (kind == KS || kind == KP || kind == KT) {
         a = __ldg(X + base + G + (kind == KS ? r : q));
         b = __ldg(X + base + q);
+    } else if (kind == KX) {
+        a = __ldg(X + base);
+        b = P.sumR[h.cat_off + q - 1];
+    } else if (kind == KY) {
+        a = P.sumC[h.cat_off + q - 1];
+        b = __ldg(X + base);
     } else {
-        const C Z = __ldg(X + base);
-        C s = mk(T(0), T(0));
-        if (kind != KZ) {
-            // R_q (X) or C_q (Y): P_q + (M_q - 1) T_q + sum_{b != q} M_b S
-            s = __ldg(X + base + 2 * G + q);
-            if (trq != 31) s = caxpy(__ldg(P.cat_M + h.cat_off + q - 1) - T(1), __ldg(X + base + (G + 1) * (G + 1) + trq), s);
-        }
-        for (int b2 = 1; b2 <= G; ++b2) {
-            const T Mb = __ldg(P.cat_M + h.cat_off + b2 - 1);
-            if (kind == KZ) {
-                s = caxpy(Mb, csub(__ldg(X + base + b2), __ldg(X + base + G + b2)), s);
-            } else if (b2 != q) {
-                const int l = kind == KX ? loc_S_d(G, q, b2) : loc_S_d(G, b2, q);
-                s = caxpy(Mb, __ldg(X + base + l), s);
-            }
-        }
-        if (kind == KX) { a = Z; b = s; }
-        else if (kind == KY) { a = s; b = Z; }
-        else { a = s; b = mk(T(0), T(0)); }
+        a = P.sumZ[p];
+        b = mk(T(0), T(0));
     }
     const T lossf = kind == KZ ? T(1) : ((kind == KX || kind == KY) ? T(0.5) : T(0));
     const T dim = kind == KX ? -det : (kind == KY ? det : T(0));
@@ -1015,6 +1049,8 @@ template <typename T, bool SIDE>
 static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int ninst, cudaStream_t st) {
     const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, sizeof(T) == 8, cfg.kernel);
     if (cfg.kernel == SA_KERNEL_ELL) {
+        const unsigned gs = unsigned((size_t(p.ncat) + p.npat + 255) / 256);
+        grouped_sums_kernel<T, SIDE><<<gs, 256, 0, st>>>(p);
         const unsigned grid = unsigned((size_t(p.nvar) + 31) / 32 * 32 + cfg.block - 1) / unsigned(cfg.block);
         if (grid > 0) ell_stage_kernel<T, SIDE><<<grid, cfg.block, 0, st>>>(p);
     } else if (cfg.kernel == SA_KERNEL_LISTS) {
@@ -1057,6 +1093,12 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.tcid = static_cast<const uint16_t*>(s.tcid);
     p.lcoef = static_cast<const C*>(s.lcoef);
     p.wpat = static_cast<const uint32_t*>(s.wpat);
+    p.catpat = static_cast<const uint32_t*>(s.catpat);
+    p.ncat = s.ncat;
+    p.npat = s.npat;
+    p.sumR = static_cast<C*>(s.sums);
+    p.sumC = p.sumR ? p.sumR + s.ncat : nullptr;
+    p.sumZ = p.sumC ? p.sumC + s.ncat : nullptr;
     p.blobs = static_cast<const unsigned char*>(s.blobs);
     p.nvar = s.nvar;
     p.nchunks = s.nchunks;

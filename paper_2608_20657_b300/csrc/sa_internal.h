@@ -179,6 +179,7 @@ struct StageLaunch {
     const void* lut; const void* lut_off;
     const void* lvd; const void* lvj; const void* rbase; const void* tidx; const void* tcid; const void* lcoef;
     const void* wpat; uint32_t nvar; const void* blobs;
+    const void* catpat; uint32_t ncat, npat; void* sums;
     uint32_t nchunks;
     const void* x_in; void* x_out; const void* y; void* acc; void* y_out;
     const void* xs_in; void* xs_out; const void* ys; void* accs; void* ys_out;
