@@ -274,6 +274,16 @@ int sa_heom_propagate(sa_heom* h, void* d_state, double dt, int64_t nsteps, int6
                       void* stream);
 
 /*
+ * sa_heom_prepare -- capture and instantiate now every CUDA graph that
+ * sa_heom_propagate(h, d_state, dt, nsteps, obs_every, ...) will replay
+ * (runs of at most 64 steps, keyed by state pointer, dt and run length), so
+ * that the propagation itself builds none.  Runs no kernel; synchronous.
+ * obs_every <= 0: no observables (one run of nsteps).  The handle keeps up to
+ * 16 graphs; a call needing more than that prepares only the last ones.
+ */
+int sa_heom_prepare(sa_heom* h, void* d_state, double dt, int64_t nsteps, int64_t obs_every);
+
+/*
  * sa_heom_observables -- Eqs. trace-uvar, Pcav-uvar, Pexc-uvar, PB-uvar,
  * PD-uvar, Pplus-uvar, Pminus-uvar from the FP64 physical representative of
  * every instance: out[8 * i ..] = Tr, P_cav, P_exc, P_B, P_D, P_+, P_-,
@@ -317,6 +327,7 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best);
  *                      A grouped-sum kernel forms R_q, C_q and the Z sums
  *                      first (scratch: 2 per category + 1 per pattern).
  *                      The item capacity (chunk) does not apply to it.
+ * A new handle uses SA_KERNEL_LISTS.
  * sa_heom_set_kernel rebuilds the launch tables (synchronous; INVALID_ARG for
  * an unknown variant, OOM if the lists do not fit).  sa_heom_get_tuning
  * writes block, chunk, queue, kernel to out[0..3].

@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
             "sa_heom_rhs": [vp, vp, vp, vp],
             "sa_heom_step": [vp, vp, dbl, vp],
             "sa_heom_propagate": [vp, vp, dbl, i64, i64, vp, vp],
+            "sa_heom_prepare": [vp, vp, dbl, i64, i64],
             "sa_heom_observables": [vp, vp, vp, vp],
             "sa_heom_set_tuning": [vp, i32, i32, i32],
             "sa_heom_autotune": [vp, vp, vp, vp],
@@ -126,7 +127,7 @@ def exported_symbols() -> list[str]:
             "sa_heom_var_offset", "sa_heom_dump_vectors", "sa_heom_dump_patterns", "sa_heom_dump_categories",
             "sa_heom_dump_terms", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_state_upload",
             "sa_heom_state_download", "sa_heom_rhs", "sa_heom_step", "sa_heom_propagate", "sa_heom_observables",
-            "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_set_kernel", "sa_heom_get_tuning", "sa_heom_dump_lists", "sa_heom_dump_ell",
+            "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_set_kernel", "sa_heom_get_tuning", "sa_heom_prepare", "sa_heom_dump_lists", "sa_heom_dump_ell",
             "sa_heom_launches_per_step", "sa_heom_device_error",
             "sa_heom_observables_noalloc", "sa_heom_strerror", "sa_heom_last_error", "sa_conv_build",
             "sa_conv_destroy", "sa_conv_info", "sa_conv_labels", "sa_conv_set_rho0", "sa_conv_rhs", "sa_conv_step",
@@ -298,6 +299,11 @@ class Heom:
         _check(lib().sa_heom_propagate(self._h, _dev(state), float(dt), int(nsteps), int(oe), _ptr(out),
                                        _stream(stream)), "sa_heom_propagate")
         return out
+
+    def prepare(self, state, dt: float, nsteps: int, obs_every: int = 0):
+        """Build now the CUDA graphs a propagate of nsteps (observables every
+        obs_every steps; 0 = none) will replay."""
+        _check(lib().sa_heom_prepare(self._h, _dev(state), float(dt), int(nsteps), int(obs_every)), "sa_heom_prepare")
 
     def observables(self, state, stream=None) -> np.ndarray:
         out = np.zeros((self.count, 8))

@@ -95,7 +95,7 @@ struct sa_heom {
     int tables = -1;              // variant whose term tables are current (-1: none)
     int tables_chunk = 0;         // item capacity they were built for (SA_KERNEL_LISTS)
     // tuning
-    int block = 256, chunk = 128, use_queue = 1, kernel = SA_KERNEL_RECORDS;
+    int block = 256, chunk = 128, use_queue = 1, kernel = SA_KERNEL_LISTS;
     // device
     int device = -1, num_sms = 0;
     void *d_hdr = nullptr, *d_cat_word = nullptr, *d_catM = nullptr, *d_catMd = nullptr, *d_gamma = nullptr;
@@ -118,7 +118,7 @@ struct sa_heom {
     double* d_rho0 = nullptr;
     cudaStream_t cap = nullptr;
     size_t state_bytes = 0, side_off = 0;
-    LaunchCfg cfg{256, 128, 1, 1, SA_KERNEL_RECORDS};
+    LaunchCfg cfg{256, 128, 1, 1, SA_KERNEL_LISTS};
     std::map<std::tuple<const void*, uint64_t, int64_t>, cudaGraphExec_t> graphs;
 };
 
@@ -1104,8 +1104,9 @@ int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, i
 int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* lvd, uint8_t* lvj,
                        uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz) {
     if (!h || !sizes) return fail(SA_ERR_INVALID_ARG, "handle and sizes required");
-    if (!h->host_only || h->kernel != SA_KERNEL_LISTS)
-        return fail(SA_ERR_STATE, "term lists are kept on the host only for host-only handles with SA_KERNEL_LISTS");
+    if (!h->host_only || h->tables != SA_KERNEL_LISTS)
+        return fail(SA_ERR_STATE, "term lists are kept on the host only for host-only handles, after "
+                                  "sa_heom_set_kernel(h, SA_KERNEL_LISTS)");
     sizes[0] = int64_t(h->items.size());
     sizes[1] = int64_t(h->rbase.size()) - 1;
     sizes[2] = int64_t(h->list_rows);
@@ -1128,8 +1129,9 @@ int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32
 int sa_heom_dump_ell(const sa_heom* h, int64_t* sizes, uint32_t* wpat, uint32_t* vword, uint32_t* rbase,
                      uint32_t* tidx, uint16_t* tcid) {
     if (!h || !sizes) return fail(SA_ERR_INVALID_ARG, "handle and sizes required");
-    if (!h->host_only || h->kernel != SA_KERNEL_ELL)
-        return fail(SA_ERR_STATE, "ELL tables are kept on the host only for host-only handles with SA_KERNEL_ELL");
+    if (!h->host_only || h->tables != SA_KERNEL_ELL)
+        return fail(SA_ERR_STATE, "ELL tables are kept on the host only for host-only handles, after "
+                                  "sa_heom_set_kernel(h, SA_KERNEL_ELL)");
     sizes[0] = int64_t(h->wpat.size());
     sizes[1] = int64_t(h->list_rows);
     sizes[2] = h->nvar;
@@ -1285,6 +1287,33 @@ static int run_steps(sa_heom* h, void* d_state, double dt, int64_t n, cudaStream
         if (rc) return rc;
         CK(cudaGraphLaunch(ex, st));
         n -= s;
+    }
+    return SA_OK;
+}
+
+int sa_heom_prepare(sa_heom* h, void* d_state, double dt, int64_t nsteps, int64_t obs_every) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!d_state || !std::isfinite(dt) || nsteps < 0) return fail(SA_ERR_INVALID_ARG, "d_state, dt, nsteps");
+    if (misaligned(d_state)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
+    // the run lengths run_steps asks for: 64-step graphs and the remainder of
+    // every observation interval
+    const int64_t seg = obs_every > 0 ? std::min(obs_every, std::max<int64_t>(nsteps, 1)) : nsteps;
+    std::vector<int64_t> lens;
+    auto add = [&](int64_t n) {
+        if (n >= 64) lens.push_back(64);
+        if (n % 64) lens.push_back(n % 64);
+    };
+    if (nsteps > 0) {
+        add(seg);
+        if (obs_every > 0 && nsteps % seg) add(nsteps % seg);
+    }
+    std::sort(lens.begin(), lens.end());
+    lens.erase(std::unique(lens.begin(), lens.end()), lens.end());
+    for (int64_t n : lens) {
+        cudaGraphExec_t ex;
+        rc = graph_for(h, d_state, dt, n, &ex);
+        if (rc) return rc;
     }
     return SA_OK;
 }

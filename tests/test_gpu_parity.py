@@ -157,6 +157,26 @@ def test_batch_fp32_population_error(kernel):
         assert np.max(np.abs(obs[:, i, 1:7] - ob[:, 1:7])) <= 1e-5, i
 
 
+def test_prepare_builds_the_graphs_propagate_uses():
+    """sa_heom_prepare runs nothing; a propagation after it equals one
+    without it, bit for bit, with and without observables."""
+    w = W.WORKLOADS["w2"]
+    h = S.Heom(S.params_from(w))
+    a, b = h.new_state(), h.new_state()
+    h.init_state(a, S.rho0_vars(w))
+    h.init_state(b, S.rho0_vars(w))
+    h.prepare(a, 0.02, 150)
+    h.prepare(a, 0.02, 150, 7)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    h.propagate(a, 0.02, 150, observe=False)
+    oa = h.propagate(a, 0.02, 150, 7)
+    h.propagate(b, 0.02, 150, observe=False)
+    ob = h.propagate(b, 0.02, 150, 7)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and np.array_equal(oa, ob)
+
+
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_graph_equals_steps_and_tuning_invariance(kernel):
     """propagate (CUDA graph) is bit-identical to single steps, and every

@@ -287,14 +287,21 @@ def test_ell_batch():
 
 
 def test_lists_state_errors():
-    """Dumps exist only for host-only handles with the list kernel; an unknown
-    variant is rejected."""
+    """Dumps exist only for host-only handles whose tables were built by
+    sa_heom_set_kernel; an unknown variant is rejected and changes nothing."""
     bath = _generic_bath(1, 3)
     lib = S.Heom(S.make_params(2, 1, 3, bath), host_only=True)
-    with pytest.raises(S.SaHeomError) as e:
-        lib.dump_lists()
-    assert e.value.code == -7
+    assert lib.tuning()["kernel"] == S.SA_KERNEL_LISTS
+    for dump in (lib.dump_lists, lib.dump_ell):
+        with pytest.raises(S.SaHeomError) as e:
+            dump()
+        assert e.value.code == -7
     with pytest.raises(S.SaHeomError) as e:
         lib.set_kernel(7)
     assert e.value.code == -1
-    assert lib.tuning()["kernel"] == S.SA_KERNEL_RECORDS
+    assert lib.tuning()["kernel"] == S.SA_KERNEL_LISTS
+    lib.set_kernel(S.SA_KERNEL_ELL)
+    with pytest.raises(S.SaHeomError) as e:
+        lib.dump_lists()
+    assert e.value.code == -7
+    assert lib.dump_ell()["wpat"].size == (lib.n_vars + 31) // 32
