@@ -932,7 +932,7 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     h->coef_row_f.assign(h->coef_row_d.begin(), h->coef_row_d.end());
     h->coef_col_f.assign(h->coef_col_d.begin(), h->coef_col_d.end());
     build_lut(h);
-    h->chunk = std::max(128, (h->max_u + 31) / 32 * 32);
+    h->chunk = std::max(192, (h->max_u + 31) / 32 * 32);
     if (h->chunk > kMaxItemVars) {
         delete h;
         return fail(SA_ERR_UNSUPPORTED, "a pattern has more than 1024 unique variables");
@@ -1426,7 +1426,7 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     if (misaligned(d_state)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int blocks[] = {128, 256};
-    const int chunks[] = {64, 96, 128, 192, 256};
+    const int chunks[] = {64, 96, 128, 160, 192, 224, 256};
     // (items smaller than the largest pattern or above the shared-memory
     // budget are skipped by set_tuning)
     float best_ms = 1e30f;
@@ -1434,10 +1434,11 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    // item size outermost: the list kernel's tables are rebuilt per item size only
     for (int k : {int(SA_KERNEL_RECORDS), int(SA_KERNEL_LISTS), int(SA_KERNEL_ELL)})
-    for (int q = 0; q < 2; ++q)
+    for (int c : chunks)
         for (int b : blocks)
-            for (int c : chunks) {
+            for (int q = 0; q < 2; ++q) {
                 if (c < h->max_u) continue;
                 // the ELL kernel has neither work items nor a queue
                 if (k == SA_KERNEL_ELL && (q != 0 || c != std::max(128, (h->max_u + 31) / 32 * 32))) continue;

@@ -570,8 +570,6 @@ template <typename T> struct ListSmem {
     using C = typename Cx<T>::t;
     uint64_t* bar;        // the warp's mbarrier
     C* op;                // skip + chunk + 2 nc + kItemPats + 1 entries (+ 2 spare)
-    C* y;                 // RK4 state slice (skip + chunk + 1)
-    C* acc;               // RK4 accumulator slice
     unsigned char* blob;  // the item's table blob
 };
 
@@ -587,7 +585,7 @@ __host__ __device__ __forceinline__ int list_opZero(int item) { return item + 2 
 template <typename T>
 __host__ __device__ __forceinline__ size_t list_smem_bytes(int item) {
     const size_t cs = 2 * sizeof(T);
-    return 16 + al16(cs * (list_opZero(item) + 3)) + 2 * al16(cs * (item + 2)) +
+    return 16 + al16(cs * (list_opZero(item) + 3)) +
            blob_layout<T>(kItemPats, uint32_t(list_ncat(item)), uint32_t(item)).bytes;
 }
 
@@ -597,18 +595,18 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
     ListSmem<T> W;
     W.bar = reinterpret_cast<uint64_t*>(p);  p += 16;
     W.op = reinterpret_cast<C*>(p);          p += al16(sizeof(C) * (list_opZero(item) + 3));
-    W.y = reinterpret_cast<C*>(p);           p += al16(sizeof(C) * (item + 2));
-    W.acc = reinterpret_cast<C*>(p);         p += al16(sizeof(C) * (item + 2));
     W.blob = p;
     return W;
 }
 
 // One warp per work item, like stage_kernel, but
-//  * the item's stage-input, state and accumulator slices and its table blob
-//    (pattern headers and constants, damping rates, category words,
-//    multiplicities and owners, round table, lane words) arrive by four TMA
-//    bulk copies on the warp's mbarrier, and its term rows are prefetched
-//    into L2 by bulk prefetches;
+//  * the item's stage-input slice and its table blob (pattern headers and
+//    constants, damping rates, category words, multiplicities and owners,
+//    round table, lane words) arrive by two TMA bulk copies on the warp's
+//    mbarrier; its RK4 state and accumulator slices and its term rows are
+//    prefetched into L2 by bulk prefetches, and each lane reads its own
+//    variable's state and accumulator from there (keeping them out of shared
+//    memory leaves room for larger items at the same occupancy);
 //  * the hierarchy terms come from host-resolved lists: the lanes take the
 //    item's variables in rounds of 32 (sorted by term count, so a round's
 //    lanes run the same number of terms), and term t of a round is one
@@ -649,13 +647,16 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
         if (c >= P.nchunks) break;
         const ItemDesc d = P.items[c];
         const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0;
-        // ---- bulk copies of the item: lanes 0-3 take one array each
+        // ---- bulk copies (lanes 0, 3) and L2 prefetches (lanes 1, 2, 4, 5) of the item
         const Span sx = span(P.x_in, v0, nv, sizeof(C));
         Span sp;
         void* dst = nullptr;
         if (lane == 0) { sp = sx; dst = S.op; }
-        else if (lane == 1) { sp = span(P.y, v0, P.stage > 0 ? nv : 0u, sizeof(C)); dst = S.y; }
-        else if (lane == 2) { sp = span(P.acc, v0, P.stage > 0 ? nv : 0u, sizeof(C)); dst = S.acc; }
+        else if (lane == 1 || lane == 2) {
+            const Span t = span(lane == 1 ? P.y : static_cast<const C*>(P.acc), v0, P.stage > 0 ? nv : 0u, sizeof(C));
+            if (t.bytes) bulk_prefetch_l2(t.src, t.bytes);
+            sp.bytes = 0;
+        }
         else if (lane == 3) {
             sp.src = reinterpret_cast<const char*>(P.blobs) + size_t(d.blob16) * 16;
             sp.bytes = d.blob_bytes;
@@ -733,6 +734,11 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
             const uint32_t l = w0 & 1023u, a = (w0 >> 10) & 2047u, b = w0 >> 21;
             const int j = int(w1 & 31u), cls = int(w1 >> 5);
             const C v = op[l];
+            C yv = mk(T(0), T(0)), av = mk(T(0), T(0));
+            if (on && P.stage > 0) {
+                yv = __ldg(P.y + v0 + l);
+                av = P.acc[v0 + l];
+            }
             const C gm = reinterpret_cast<const C*>(S.blob + B.gam)[j];
             const PatConst<T> pc = reinterpret_cast<const PatConst<T>*>(S.blob + B.pc)[j];
             // diagonal: -Gamma, the cavity loss (1/2 per cavity index) and
@@ -775,10 +781,10 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
                     P.acc[vg] = dv;
                     P.x_out[vg] = caxpy(aT, dv, v);  // x_in is y in the first stage
                 } else if (P.stage == 3) {
-                    P.y_out[vg] = caxpy(dtT / T(6), cadd(S.acc[sx.skip + l], dv), S.y[sx.skip + l]);
+                    P.y_out[vg] = caxpy(dtT / T(6), cadd(av, dv), yv);
                 } else {
-                    P.acc[vg] = caxpy(T(2), dv, S.acc[sx.skip + l]);
-                    P.x_out[vg] = caxpy(aT, dv, S.y[sx.skip + l]);
+                    P.acc[vg] = caxpy(T(2), dv, av);
+                    P.x_out[vg] = caxpy(aT, dv, yv);
                 }
             }
         }
