@@ -154,14 +154,17 @@ void build_lut(sa_heom* h) {
 // Y, Z, every kind in memory order -- with their local index and (kind, q, r).
 void build_items(sa_heom* h) {
     std::vector<uint32_t> begin{0};
-    int64_t vars = 0, pats = 0;
+    int64_t vars = 0, pats = 0, insts = 0;
     for (int64_t p = 0; p < h->npat; ++p) {
         int64_t u = int64_t(h->hdr[p + 1].var_off) - int64_t(h->hdr[p].var_off);
-        if (pats > 0 && (vars + u > h->chunk || pats >= kItemPats)) {
+        const bool new_inst = pats > 0 && h->hdr[p].inst != h->hdr[p - 1].inst;
+        if (pats > 0 && (vars + u > h->chunk || pats >= kItemPats || (new_inst && insts >= kItemInsts))) {
             begin.push_back(uint32_t(p));
             vars = 0;
             pats = 0;
+            insts = 0;
         }
+        if (pats == 0 || new_inst) ++insts;
         vars += u;
         ++pats;
     }
@@ -314,8 +317,9 @@ int build_blobs(sa_heom* h) {
         const ItemDesc& d = h->items[c];
         const BlobLayout B = blob_layout<V>(d.np, d.ncat, d.nl);
         uint8_t* o = &h->blobs[size_t(d.blob16) * 16];
-        PatHdr* ph = reinterpret_cast<PatHdr*>(o + B.hdr);
-        PatConst<V>* pc = reinterpret_cast<PatConst<V>*>(o + B.pc);
+        ItemPat* ph = reinterpret_cast<ItemPat*>(o + B.pat);
+        PatConst<V>* ic = reinterpret_cast<PatConst<V>*>(o + B.ic);
+        int nic = 0;
         V* gm = reinterpret_cast<V*>(o + B.gam);
         uint32_t* cw = reinterpret_cast<uint32_t*>(o + B.cw);
         V* cM = reinterpret_cast<V*>(o + B.cM);
@@ -325,12 +329,20 @@ int build_blobs(sa_heom* h) {
         uint8_t* lvj = o + B.lvj;
         for (uint32_t j = 0; j < d.np; ++j) {
             const PatHdr& H = h->hdr[d.p0 + j];
-            const sa_params& q = h->inst[H.inst].p;
-            ph[j] = H;
-            pc[j].g = V(q.g);
-            pc[j].det = V(q.detuning);
-            pc[j].kap = V(q.kappa);
-            pc[j].coef_base = uint32_t(H.inst) * uint32_t(kListCoefStride);
+            ph[j].var_rel = uint16_t(H.var_off - d.v0);
+            ph[j].cat_rel = uint16_t(H.cat_off - d.c0);
+            ph[j].G = H.G;
+            ph[j].tier = H.tier;
+            if (j == 0 || H.inst != h->hdr[d.p0 + j - 1].inst) {
+                // the item's instances, in order (at most kItemInsts)
+                const sa_params& q = h->inst[H.inst].p;
+                ic[nic].g = V(q.g);
+                ic[nic].det = V(q.detuning);
+                ic[nic].kap = V(q.kappa);
+                ic[nic].coef_base = uint32_t(H.inst) * uint32_t(kListCoefStride);
+                ++nic;
+            }
+            ph[j].islot = uint16_t(nic - 1);
             gm[2 * j] = V(gam[2 * size_t(d.p0 + j)]);
             gm[2 * j + 1] = V(gam[2 * size_t(d.p0 + j) + 1]);
             for (uint32_t cl = H.cat_off - d.c0; cl < h->hdr[d.p0 + j + 1].cat_off - d.c0; ++cl) cj[cl] = uint8_t(j);
@@ -610,6 +622,7 @@ int ensure_tables(sa_heom* h) {
                                          : upload(&h->d_lcoef, list_coefficients<float>(h));
 
         if (!rc && k == SA_KERNEL_LISTS) rc = upload(&h->d_blobs, h->blobs);
+
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_lvd, h->lvd);
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_wpat, h->wpat);
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_rbase, h->rbase);

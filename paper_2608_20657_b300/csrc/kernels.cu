@@ -600,8 +600,8 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
 }
 
 // One warp per work item, like stage_kernel, but
-//  * the item's stage-input slice and its table blob (pattern headers and
-//    constants, damping rates, category words, multiplicities and owners,
+//  * the item's stage-input slice and its table blob (instance constants,
+//    patterns, damping rates, category words, multiplicities and owners,
 //    round table, lane words) arrive by two TMA bulk copies on the warp's
 //    mbarrier; its RK4 state and accumulator slices and its term rows are
 //    prefetched into L2 by bulk prefetches, and each lane reads its own
@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
         }
         if (c >= P.nchunks) break;
         const ItemDesc d = P.items[c];
-        const uint32_t v0 = d.v0, nv = d.nv, c0 = d.c0;
+        const uint32_t v0 = d.v0, nv = d.nv;
         // ---- bulk copies (lanes 0, 3) and L2 prefetches (lanes 1, 2, 4, 5) of the item
         const Span sx = span(P.x_in, v0, nv, sizeof(C));
         Span sp;
@@ -680,7 +680,7 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
         const int np = int(d.np);
         const uint32_t ncat = d.ncat, nl = d.nl;
         const BlobLayout B = blob_layout<T>(uint32_t(np), ncat, nl);
-        const PatHdr* const ph = reinterpret_cast<const PatHdr*>(S.blob + B.hdr);
+        const ItemPat* const ph = reinterpret_cast<const ItemPat*>(S.blob + B.pat);
         const uint32_t* const cw = reinterpret_cast<const uint32_t*>(S.blob + B.cw);
         const T* const cM = reinterpret_cast<const T*>(S.blob + B.cM);
         const uint8_t* const cj = S.blob + B.cj;
@@ -692,11 +692,11 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
         // ---- grouped sums per category (Eqs. grouped-row-sum,
         // grouped-column-sum) and per pattern (Eq. HZ)
         for (uint32_t cl = lane; cl < ncat; cl += 32) {
-            const PatHdr h = ph[cj[cl]];
+            const ItemPat h = ph[cj[cl]];
             const int G = h.G;
-            const int cb = int(h.cat_off - c0);
+            const int cb = int(h.cat_rel);
             const int q = int(cl) - cb + 1;
-            const C* xp = op + (h.var_off - v0);
+            const C* xp = op + h.var_rel;
             const T Mq = cM[cl];
             C Rs = xp[2 * G + q];
             if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((cw[cl] >> 15) & 31)], Rs);
@@ -711,10 +711,10 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
             opC[cl] = Cq;
         }
         for (int j = lane; j < np; j += 32) {
-            const PatHdr h = ph[j];
+            const ItemPat h = ph[j];
             const int G = h.G;
-            const int cb = int(h.cat_off - c0);
-            const C* xp = op + (h.var_off - v0);
+            const int cb = int(h.cat_rel);
+            const C* xp = op + h.var_rel;
             C zs = mk(T(0), T(0));
             for (int q = 1; q <= G; ++q) zs = caxpy(cM[cb + q - 1], csub(xp[q], xp[G + q]), zs);
             opZ[j] = zs;
@@ -740,7 +740,7 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
                 av = P.acc[v0 + l];
             }
             const C gm = reinterpret_cast<const C*>(S.blob + B.gam)[j];
-            const PatConst<T> pc = reinterpret_cast<const PatConst<T>*>(S.blob + B.pc)[j];
+            const PatConst<T> pc = reinterpret_cast<const PatConst<T>*>(S.blob + B.ic)[ph[j].islot];
             // diagonal: -Gamma, the cavity loss (1/2 per cavity index) and
             // -/+ i detuning for X / Y (classes: 0 P S T, 1 X, 2 Y, 3 Z)
             const T lossf = cls == 0 ? T(0) : (cls == 3 ? T(1) : T(0.5));

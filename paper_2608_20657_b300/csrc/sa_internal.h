@@ -125,13 +125,24 @@ template <typename T> struct PatConst {
     uint32_t coef_base;  // the instance's coefficient table
 };
 
+// A pattern as the list kernel's blob gives it (8 bytes): its first variable
+// and first category relative to the work item's, G, tier and the slot of its
+// instance among the item's instances.
+struct ItemPat {
+    uint16_t var_rel, cat_rel;
+    uint8_t G, tier;
+    uint16_t islot;
+};
+constexpr int kItemInsts = 4;  // instances per work item
+
 // Byte offsets of the sections of a list-kernel item blob (every section
-// 16-byte aligned): pattern headers, pattern constants, damping rates
-// Gamma_Lambda (complex T), category words, multiplicities (T), owning
-// pattern of every category (u8), round table (first term row of every
-// round and the end), lane words, lane bytes.
+// 16-byte aligned): the constants of the item's instances (kItemInsts
+// PatConst slots), patterns (ItemPat), damping rates Gamma_Lambda (complex
+// T), category words, multiplicities (T), owning pattern of every category
+// (u8), round table (first term row of every round and the end), lane words,
+// lane bytes.
 struct BlobLayout {
-    uint32_t hdr, pc, gam, cw, cM, cj, rb, lvd, lvj, bytes;
+    uint32_t ic, pat, gam, cw, cM, cj, rb, lvd, lvj, bytes;
 };
 #if defined(__CUDACC__)
 #define SA_HOST_DEVICE __host__ __device__
@@ -143,9 +154,9 @@ SA_HOST_DEVICE inline BlobLayout blob_layout(uint32_t np, uint32_t ncat, uint32_
     auto a16 = [](uint32_t b) { return (b + 15u) & ~15u; };
     const uint32_t nrounds = (nl + 31u) / 32u;
     BlobLayout L;
-    L.hdr = 0;
-    L.pc = L.hdr + a16(np * uint32_t(sizeof(PatHdr)));
-    L.gam = L.pc + a16(np * uint32_t(sizeof(PatConst<T>)));
+    L.ic = 0;
+    L.pat = L.ic + a16(uint32_t(kItemInsts * sizeof(PatConst<T>)));
+    L.gam = L.pat + a16(np * uint32_t(sizeof(ItemPat)));
     L.cw = L.gam + a16(np * 2u * uint32_t(sizeof(T)));
     L.cM = L.cw + a16(ncat * 4u);
     L.cj = L.cM + a16(ncat * uint32_t(sizeof(T)));
