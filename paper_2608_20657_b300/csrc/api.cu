@@ -117,6 +117,8 @@ struct sa_heom {
     size_t obs_cap = 0;
     double* d_rho0 = nullptr;
     cudaStream_t cap = nullptr;
+    cudaStream_t side = nullptr;                          // SA_FP32_AUX: stream of the FP64 rho_0 kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;     // its fork and join
     size_t state_bytes = 0, side_off = 0;
     LaunchCfg cfg{256, 128, 1, 1, SA_KERNEL_LISTS};
     std::map<std::tuple<const void*, uint64_t, int64_t>, cudaGraphExec_t> graphs;
@@ -696,6 +698,9 @@ void free_device(sa_heom* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
 }
 
 int ensure_queue(sa_heom* h, size_t slots) {
@@ -744,6 +749,9 @@ StageLaunch base_launch(const sa_heom* h) {
     s.nchunks = uint32_t(h->items.size());
     s.err = h->d_err;
     s.ninst = h->count;
+    s.side_stream = h->side;
+    s.ev_fork = h->ev_fork;
+    s.ev_join = h->ev_join;
     return s;
 }
 
@@ -1012,6 +1020,11 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     }
     if (!rc) {
         e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess && precision == SA_FP32_AUX) {
+            e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+        }
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamCreate");
     }
     h->host_only = false;

@@ -1052,8 +1052,28 @@ void list_operand_layout(int item, int* opR, int* opC, int* opZ, int* opZero) {
 }
 
 template <typename T, bool SIDE>
-static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int ninst, cudaStream_t st) {
+static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int ninst, cudaStream_t st,
+                            const StageLaunch& s) {
     const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, sizeof(T) == 8, cfg.kernel);
+    // the FP64 physical-representative kernel reads the same stage input and
+    // writes other variables: it overlaps the stage kernel on a side stream
+    cudaStream_t side = static_cast<cudaStream_t>(s.side_stream);
+    const bool fork = SIDE && side && s.ev_fork && s.ev_join;
+    if (SIDE) {
+        cudaStream_t rs = st;
+        if (fork) {
+            cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(s.ev_fork), st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, static_cast<cudaEvent_t>(s.ev_fork), 0);
+            if (e != cudaSuccess) return e;
+            rs = side;
+        }
+        const int threads = ninst * kSideSlots;
+        rho0_kernel<T><<<(threads + 127) / 128, 128, 0, rs>>>(p, ninst);
+        if (fork) {
+            const cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(s.ev_join), side);
+            if (e != cudaSuccess) return e;
+        }
+    }
     if (cfg.kernel == SA_KERNEL_ELL) {
         const unsigned gs = unsigned((size_t(p.ncat) + p.npat + 255) / 256);
         grouped_sums_kernel<T, SIDE><<<gs, 256, 0, st>>>(p);
@@ -1064,9 +1084,9 @@ static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int n
     } else {
         stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     }
-    if (SIDE) {
-        const int threads = ninst * kSideSlots;
-        rho0_kernel<T><<<(threads + 127) / 128, 128, 0, st>>>(p, ninst);
+    if (fork) {
+        const cudaError_t e = cudaStreamWaitEvent(st, static_cast<cudaEvent_t>(s.ev_join), 0);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -1128,8 +1148,8 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
 }
 
 cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, cudaStream_t st) {
-    if (fp64) return launch_t<double, false>(make_params<double>(s, cfg), cfg, s.ninst, st);
-    return launch_t<float, true>(make_params<float>(s, cfg), cfg, s.ninst, st);
+    if (fp64) return launch_t<double, false>(make_params<double>(s, cfg), cfg, s.ninst, st, s);
+    return launch_t<float, true>(make_params<float>(s, cfg), cfg, s.ninst, st, s);
 }
 
 // Sets the dynamic shared-memory limit once for the largest chunk (outside

@@ -196,6 +196,9 @@ struct StageLaunch {
     const void* xs_in; void* xs_out; const void* ys; void* accs; void* ys_out;
     double dt; int stage; unsigned int* queue; unsigned int* err;
     int ninst;
+    // SA_FP32_AUX: the FP64 physical-representative kernel runs on a side
+    // stream, forked before and joined after the stage kernel
+    void* side_stream; void* ev_fork; void* ev_join;
 };
 
 // builder.cpp
