@@ -200,15 +200,10 @@ int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, i
  *          row / column coefficient of coefficient id cid; 1024 + cid for
  *          row + column, the P_q lower terms; 1536 = zero, padding);
  *   opz    int32[4]: operand-area offsets of R_q, C_q, the Z sums, the zero
- *          (the item's stage-input slice occupies [0, chunk));
- *   tpk    uint32[32 * rows], written only when sizes[4] (also written) is 1:
- *          the same entries packed as (target - v0 + 2^20) << 11 | slot, the
- *          form the device uses when every target lies within 2^20
- *          variables of its work item's first variable v0.
- * sizes must hold 5 values.
+ *          (the item's stage-input slice occupies [0, chunk)).
  */
 int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* lvd, uint8_t* lvj,
-                       uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz, uint32_t* tpk);
+                       uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz);
 
 /*
  * sa_heom_dump_ell -- the host copy of the SA_KERNEL_ELL tables (host-only

@@ -91,8 +91,6 @@ struct sa_heom {
     uint64_t list_rows = 0;
     std::vector<uint32_t> wpat;   // ELL: first pattern of every warp row
     std::vector<ItemDesc> list_items;  // SA_KERNEL_LISTS: the item table the current lists were built with
-    std::vector<uint32_t> tpk;         // SA_KERNEL_LISTS: packed term entries (when list_packed)
-    bool list_packed = false;
     std::vector<uint8_t> blobs;        // SA_KERNEL_LISTS: per-item table blobs
     int tables = -1;              // variant whose term tables are current (-1: none)
     int tables_chunk = 0;         // item capacity they were built for (SA_KERNEL_LISTS)
@@ -109,7 +107,6 @@ struct sa_heom {
     void* d_lcoef = nullptr;
     void* d_wpat = nullptr;
     void* d_blobs = nullptr;
-    void* d_tpk = nullptr;
     void* d_catpat = nullptr;  // ELL: owning pattern of every category
     void* d_sums = nullptr;    // ELL: grouped sums scratch (R, C per category; Z per pattern)
     unsigned int* d_err = nullptr;
@@ -123,7 +120,7 @@ struct sa_heom {
     cudaStream_t side = nullptr;                          // SA_FP32_AUX: stream of the FP64 rho_0 kernel
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;     // its fork and join
     size_t state_bytes = 0, side_off = 0;
-    LaunchCfg cfg{256, 128, 1, 1, SA_KERNEL_LISTS, 0};
+    LaunchCfg cfg{256, 128, 1, 1, SA_KERNEL_LISTS};
     std::map<std::tuple<const void*, uint64_t, int64_t>, cudaGraphExec_t> graphs;
 };
 
@@ -454,33 +451,6 @@ int build_lists(sa_heom* h) {
     const int rc = h->precision == SA_FP64 ? build_blobs<double>(h) : build_blobs<float>(h);
     if (rc) return rc;
     h->list_items = h->items;
-    // packed 32-bit entries when every target lies within 2^20 variables of
-    // its item's first variable (offsets are relative to v0)
-    bool fits = true;
-#pragma omp parallel for schedule(dynamic, 256) reduction(&& : fits)
-    for (int64_t c = 0; c < int64_t(ni); ++c) {
-        const ItemDesc& d = h->items[c];
-        for (size_t e = size_t(d.row0) * 32; e < size_t(d.row1) * 32; ++e) {
-            const int64_t off = int64_t(h->tidx[e]) - int64_t(d.v0);
-            fits = fits && off >= -int64_t(kPackBias) && off < int64_t(kPackBias);
-        }
-    }
-    h->list_packed = fits;
-    std::vector<uint32_t>().swap(h->tpk);
-    if (fits) {
-        try {
-            h->tpk.assign(h->tidx.size(), 0u);
-        } catch (const std::bad_alloc&) {
-            return fail(SA_ERR_OOM, "host memory for the packed term lists");
-        }
-#pragma omp parallel for schedule(dynamic, 256)
-        for (int64_t c = 0; c < int64_t(ni); ++c) {
-            const ItemDesc& d = h->items[c];
-            for (size_t e = size_t(d.row0) * 32; e < size_t(d.row1) * 32; ++e)
-                h->tpk[e] = (uint32_t(int64_t(h->tidx[e]) - int64_t(d.v0) + kPackBias) << kPackSlotBits) |
-                            uint32_t(h->tcid[e]);
-        }
-    }
     return SA_OK;
 }
 
@@ -626,7 +596,7 @@ std::vector<V> list_coefficients(const sa_heom* h) {
 }
 
 void free_lists(sa_heom* h) {
-    void** ptrs[] = {&h->d_lvd, &h->d_lvj, &h->d_rbase, &h->d_tidx, &h->d_tcid, &h->d_wpat, &h->d_blobs, &h->d_tpk};
+    void** ptrs[] = {&h->d_lvd, &h->d_lvj, &h->d_rbase, &h->d_tidx, &h->d_tcid, &h->d_wpat, &h->d_blobs};
     for (void** p : ptrs) {
         if (*p) cudaFree(*p);
         *p = nullptr;
@@ -668,10 +638,8 @@ int ensure_tables(sa_heom* h) {
             const size_t bytes = size_t(2 * h->ncat + h->npat) * (h->precision == SA_FP64 ? 16 : 8);
             if (cudaMalloc(&h->d_sums, bytes) != cudaSuccess) rc = fail(SA_ERR_OOM, "grouped-sum scratch");
         }
-        const bool packed = k == SA_KERNEL_LISTS && h->list_packed;
-        if (!rc && packed) rc = upload(&h->d_tpk, h->tpk);
-        if (!rc && !packed) rc = upload(&h->d_tidx, h->tidx);
-        if (!rc && !packed) rc = upload(&h->d_tcid, h->tcid);
+        if (!rc) rc = upload(&h->d_tidx, h->tidx);
+        if (!rc) rc = upload(&h->d_tcid, h->tcid);
         // the host copies are not needed again
         std::vector<uint32_t>().swap(h->lvd);
         std::vector<uint8_t>().swap(h->lvj);
@@ -679,7 +647,6 @@ int ensure_tables(sa_heom* h) {
         std::vector<uint16_t>().swap(h->tcid);
         std::vector<uint32_t>().swap(h->wpat);
         std::vector<uint8_t>().swap(h->blobs);
-        std::vector<uint32_t>().swap(h->tpk);
         if (rc) {
             free_lists(h);
             return rc;
@@ -699,7 +666,6 @@ int apply_tuning(sa_heom* h) {
     const uint32_t nchunks = uint32_t(h->items.size());
     int rc = ensure_tables(h);
     if (rc) return rc;
-    h->cfg.packed = (h->kernel == SA_KERNEL_LISTS && h->list_packed) ? 1 : 0;
     if (h->host_only) return SA_OK;
     if (h->d_chunk) cudaFree(h->d_chunk);
     if (h->d_vdesc) cudaFree(h->d_vdesc);
@@ -728,7 +694,7 @@ void free_device(sa_heom* h) {
                     h->d_coef_row, h->d_coef_col, h->d_coef_row_d, h->d_coef_col_d, h->d_lut, h->d_lut_off,
                     h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0,
                     h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS, h->d_lvd, h->d_lvj, h->d_rbase,
-                    h->d_tidx, h->d_tcid, h->d_lcoef, h->d_wpat, h->d_blobs, h->d_catpat, h->d_sums, h->d_tpk};
+                    h->d_tidx, h->d_tcid, h->d_lcoef, h->d_wpat, h->d_blobs, h->d_catpat, h->d_sums};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -775,7 +741,6 @@ StageLaunch base_launch(const sa_heom* h) {
     s.lcoef = h->d_lcoef;
     s.wpat = h->d_wpat;
     s.blobs = h->d_blobs;
-    s.tpk = h->d_tpk;
     s.catpat = h->d_catpat;
     s.ncat = uint32_t(h->ncat);
     s.npat = uint32_t(h->npat);
@@ -1163,7 +1128,7 @@ int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, i
 }
 
 int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* lvd, uint8_t* lvj,
-                       uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz, uint32_t* tpk) {
+                       uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz) {
     if (!h || !sizes) return fail(SA_ERR_INVALID_ARG, "handle and sizes required");
     if (!h->host_only || h->tables != SA_KERNEL_LISTS)
         return fail(SA_ERR_STATE, "term lists are kept on the host only for host-only handles, after "
@@ -1172,8 +1137,6 @@ int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32
     sizes[1] = int64_t(h->rbase.size()) - 1;
     sizes[2] = int64_t(h->list_rows);
     sizes[3] = h->nvar;
-    sizes[4] = h->list_packed ? 1 : 0;
-    if (tpk && h->list_packed) std::copy(h->tpk.begin(), h->tpk.end(), tpk);
     if (items)
         for (size_t c = 0; c < h->items.size(); ++c) {
             const ItemDesc& d = h->items[c];

@@ -86,7 +86,6 @@ template <typename T> struct StageParams {
     const uint32_t* __restrict__ rbase;     // first term row of every round of 32 lanes (+ sentinel)
     const uint32_t* __restrict__ tidx;      // term rows of 32: batch-global target index
     const uint16_t* __restrict__ tcid;      // term rows of 32: coefficient slot in the instance's list table
-    const uint32_t* __restrict__ tpk;       // list kernel, packed rows: (target - v0 + kPackBias) << 11 | slot
     const C* __restrict__ lcoef;            // per instance kListCoefStride slots
     // ELL kernel (lvd: per-variable word, rbase: per warp row, tidx / tcid as above)
     const unsigned char* __restrict__ blobs; // list kernel: per-item table blobs (16-byte aligned)
@@ -617,7 +616,7 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
 //    variable, with operands and the diagonal class chosen by the host.
 // A bounded wait that expires sets bit 0 of the error word; the warp then
 // waits (bounded again) for its copies and stops.
-template <typename T, bool FP64SIDE, bool PK>
+template <typename T, bool FP64SIDE>
 __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -670,9 +669,8 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
         if (lane == 0) mbar_expect_tx(S.bar, total);
         __syncwarp();
         if (sp.bytes) bulk_g2s(dst, sp.src, sp.bytes, S.bar);
-        if (lane == 4 && d.row1 > d.row0)
-            bulk_prefetch_l2((PK ? P.tpk : P.tidx) + size_t(d.row0) * 32, (d.row1 - d.row0) * 128u);
-        if (!PK && lane == 5 && d.row1 > d.row0) bulk_prefetch_l2(P.tcid + size_t(d.row0) * 32, (d.row1 - d.row0) * 64u);
+        if (lane == 4 && d.row1 > d.row0) bulk_prefetch_l2(P.tidx + size_t(d.row0) * 32, (d.row1 - d.row0) * 128u);
+        if (lane == 5 && d.row1 > d.row0) bulk_prefetch_l2(P.tcid + size_t(d.row0) * 32, (d.row1 - d.row0) * 64u);
         if (!__all_sync(0xffffffffu, mbar_wait(S.bar, parity))) {
             if (lane == 0) atomicOr(P.err, 1u);
             mbar_wait(S.bar, parity);
@@ -754,27 +752,17 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
             // hierarchy terms (Eqs. uvar-up, uvar-down)
             const C* __restrict__ cf = P.lcoef + pc.coef_base;
             const uint32_t r0 = rb[rho], r1 = rb[rho + 1];
-            const int nt = int(r1 - r0);
-            // entry t of this lane: target index and coefficient slot, from
-            // the packed word (offset from v0 << 11 | slot) or the two arrays
-            const uint32_t* __restrict__ ti = (PK ? P.tpk : P.tidx) + size_t(r0) * 32 + lane;
+            const uint32_t* __restrict__ ti = P.tidx + size_t(r0) * 32 + lane;
             const uint16_t* __restrict__ tc = P.tcid + size_t(r0) * 32 + lane;
-            const uint32_t pbase = v0 - uint32_t(kPackBias);
-            auto entry = [&](int t, uint32_t& ix, uint32_t& cx) {
-                if constexpr (PK) {
-                    const uint32_t e = __ldg(ti + t * 32);
-                    ix = pbase + (e >> kPackSlotBits);
-                    cx = e & ((1u << kPackSlotBits) - 1u);
-                } else {
-                    ix = __ldg(ti + t * 32);
-                    cx = __ldg(tc + t * 32);
-                }
-            };
+            const int nt = int(r1 - r0);
             int t2 = 0;
             for (; t2 + 4 <= nt; t2 += 4) {
                 uint32_t ix[4], cx[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) entry(t2 + u, ix[u], cx[u]);
+                for (int u = 0; u < 4; ++u) {
+                    ix[u] = __ldg(ti + (t2 + u) * 32);
+                    cx[u] = __ldg(tc + (t2 + u) * 32);
+                }
                 C xv[4], cv[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -784,11 +772,7 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) dv = cfma(cv[u], xv[u], dv);
             }
-            for (; t2 < nt; ++t2) {
-                uint32_t ix, cx;
-                entry(t2, ix, cx);
-                dv = cfma(__ldg(cf + cx), __ldg(X + ix), dv);
-            }
+            for (; t2 < nt; ++t2) dv = cfma(__ldg(cf + __ldg(tc + t2 * 32)), __ldg(X + __ldg(ti + t2 * 32)), dv);
             if (on) {
                 const uint32_t vg = v0 + l;
                 if (P.stage < 0) {
@@ -1096,8 +1080,7 @@ static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int n
         const unsigned grid = unsigned((size_t(p.nvar) + 31) / 32 * 32 + cfg.block - 1) / unsigned(cfg.block);
         if (grid > 0) ell_stage_kernel<T, SIDE><<<grid, cfg.block, 0, st>>>(p);
     } else if (cfg.kernel == SA_KERNEL_LISTS) {
-        if (cfg.packed) list_stage_kernel<T, SIDE, true><<<cfg.grid, cfg.block, sm, st>>>(p);
-        else list_stage_kernel<T, SIDE, false><<<cfg.grid, cfg.block, sm, st>>>(p);
+        list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     } else {
         stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     }
@@ -1134,7 +1117,6 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.rbase = static_cast<const uint32_t*>(s.rbase);
     p.tidx = static_cast<const uint32_t*>(s.tidx);
     p.tcid = static_cast<const uint16_t*>(s.tcid);
-    p.tpk = static_cast<const uint32_t*>(s.tpk);
     p.lcoef = static_cast<const C*>(s.lcoef);
     p.wpat = static_cast<const uint32_t*>(s.wpat);
     p.catpat = static_cast<const uint32_t*>(s.catpat);
@@ -1196,11 +1178,8 @@ cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ell_stage_kernel<float, true>, cfg.block, 0);
     }
     if (cfg.kernel == SA_KERNEL_LISTS) {
-        if (fp64)
-            return cfg.packed ? occupancy_of(list_stage_kernel<double, false, true>, cfg.block, sm, lim, blocks_per_sm)
-                              : occupancy_of(list_stage_kernel<double, false, false>, cfg.block, sm, lim, blocks_per_sm);
-        return cfg.packed ? occupancy_of(list_stage_kernel<float, true, true>, cfg.block, sm, lim, blocks_per_sm)
-                          : occupancy_of(list_stage_kernel<float, true, false>, cfg.block, sm, lim, blocks_per_sm);
+        if (fp64) return occupancy_of(list_stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
+        return occupancy_of(list_stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
     }
     if (fp64) return occupancy_of(stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
     return occupancy_of(stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);

@@ -173,11 +173,6 @@ constexpr int kMaxItemVars = 1024; // variables per work item (10-bit local inde
 // padded entries
 constexpr int kListCoefZero = 3 * kCoefPerInst;
 constexpr int kListCoefStride = 3 * kCoefPerInst + 8;
-// packed list entries (used when every target lies within 2^20 variables of
-// its work item's first variable): (target - v0 + kPackBias) << kPackSlotBits | slot
-constexpr int kPackSlotBits = 11;
-constexpr int kPackBias = 1 << 20;
-static_assert(kListCoefZero < (1 << kPackSlotBits), "list slots must fit the packed entry");
 
 // launch description shared by api.cu and kernels.cu (type-erased pointers)
 struct LaunchCfg {
@@ -186,7 +181,6 @@ struct LaunchCfg {
     int use_queue;  // 1: persistent grid + atomic work queue
     int grid;       // CTAs
     int kernel;     // SA_KERNEL_RECORDS, SA_KERNEL_LISTS or SA_KERNEL_ELL (include/sa_heom.h)
-    int packed;     // SA_KERNEL_LISTS: term rows as packed 32-bit entries
 };
 struct StageLaunch {
     const void* hdr; const void* cat_word; const void* cat_M; const void* gamma; const void* rec;
@@ -195,7 +189,6 @@ struct StageLaunch {
     const void* cat_Md; const void* coef_row_d; const void* coef_col_d;
     const void* lut; const void* lut_off;
     const void* lvd; const void* lvj; const void* rbase; const void* tidx; const void* tcid; const void* lcoef;
-    const void* tpk;
     const void* wpat; uint32_t nvar; const void* blobs;
     const void* catpat; uint32_t ncat, npat; void* sums;
     uint32_t nchunks;

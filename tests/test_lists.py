@@ -134,12 +134,6 @@ def _eval_lists(lib, sas, baths, x, insts):
             # a round is as long as its longest list, and lists are sorted
             assert counts and max(counts) == rb - ra and counts == sorted(counts, reverse=True)
         assert len(seen) == len(set(seen)) == nl
-        if L["packed"] and nl:
-            # the packed words the device reads decode to the same entries
-            e = np.arange(int(L["rbase"][r0]) * 32, int(L["rbase"][r0 + (nl + 31) // 32]) * 32)
-            w = L["tpk"][e].astype(np.int64)
-            assert np.array_equal(v0 + (w >> 11) - (1 << 20), L["tidx"][e])
-            assert np.array_equal(w & 2047, L["tcid"][e])
     return out
 
 
