@@ -171,6 +171,10 @@ def cpu_baseline(workload: str, seconds: float = 15.0, dt: float = 0.02) -> dict
                       f"{el:.1f} s, FP64 C oracle with OpenMP over patterns"}
 
 
+def _workload_name(workload: str) -> str:
+    return workload + (" (512 seeded instances, FP32-aux + FP64 rho_0)" if workload == "w4" else "")
+
+
 def run_reference(args):
     rank, world = _dist()
     if rank != 0:
@@ -193,7 +197,9 @@ def run_reference(args):
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                      "data": "synthetic", "config": {"workload": args.workload, "sample": cb["sample"]},
+                      "data": "synthetic",
+                      "config": {"workload": _workload_name(args.workload), "n_instances": n_all,
+                                 "sample": cb["sample"], "parallelism": "replicas1"},
                       "cpu_baseline": cb, "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                                                    "d2h_bytes_per_step": 0}}))
     return 0
@@ -331,8 +337,7 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if precision == S.SA_FP32_AUX else "f64",
                 "data": "synthetic",
-                "config": {"workload": args.workload + (" (512 seeded instances, FP32-aux + FP64 rho_0)"
-                                                        if args.workload == "w4" else ""),
+                "config": {"workload": _workload_name(args.workload),
                            "n_instances": h.count, "n_vars": n_vars, "n_patterns": h.n_patterns,
                            "state_bytes": h.state_bytes, "l2": "inputs larger than L2 (4 vectors)",
                            "tuning": tuning,
