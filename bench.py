@@ -167,8 +167,19 @@ def cpu_baseline(workload: str, seconds: float = 15.0, dt: float = 0.02) -> dict
         if el >= seconds or (workload == "w5" and steps >= 1):
             break
     return {"value": total * steps / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "cpu": _cpu_model(), "nproc": os.cpu_count(),
             "sample": f"{len(sample)} of {n_all} instances ({total} unique variables), {steps} RK4 steps, "
                       f"{el:.1f} s, FP64 C oracle with OpenMP over patterns"}
+
+
+def _cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def _workload_name(workload: str) -> str:
@@ -226,6 +237,8 @@ def run_ours(args):
 
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     ws, ps, precision, dt = _params(args.workload)
+    if args.precision == "fp64":
+        precision = S.SA_FP64
     h = S.Heom(ps, precision=precision)
     st = h.new_state()
     h.init_state(st, _rho0(ws))
@@ -268,16 +281,20 @@ def run_ours(args):
     n_vars = h.n_vars
     value = n_vars * world * args.steps / (ms / 1e3)
 
-    # roofline of the stage kernel (4 launches per step; in FP32-aux mode each
-    # is followed by the small FP64 kernel of the physical density matrix,
-    # whose time is charged to the stage kernel here)
+    # roofline of the stage kernel (4 launches per step; in FP32-aux mode the
+    # small FP64 kernel of the physical density matrix overlaps each of them
+    # on a side stream)
     launch_ms = ms_step / 4.0
     bytes_launch = FP32_BYTES_PER_VAR_STEP * n_vars / 4.0 if precision == S.SA_FP32_AUX else \
         FP64_BYTES_PER_VAR_STEP * n_vars / 4.0
     achieved = bytes_launch / (launch_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
+    traffic = _traffic(args.workload, tuning["kernel"])
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _traffic(args.workload, tuning["kernel"]), "peak_source": f"{peak_kind} hbm_gbs",
+            "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
+            # DRAM bytes the kernel really moves (ncu, per launch) over the same live launch time
+            "dram_achieved": traffic / (launch_ms / 1e3) / 1e9 if traffic else None,
+            "dram_frac": traffic / (launch_ms / 1e3) / 1e9 / peak if traffic else None,
             "kernel": _kernel_name(tuning["kernel"], precision == S.SA_FP32_AUX), "bytes_per_launch": bytes_launch}
 
     # end to end through the public API with host buffers: upload the state
@@ -306,7 +323,7 @@ def run_ours(args):
     # FP64 comparison on the same batch: time per step and the population
     # error of the FP32-aux path against it
     extra = {}
-    if rank == 0 and args.workload == "w4" and not args.no_fp64:
+    if rank == 0 and args.workload == "w4" and not args.no_fp64 and precision == S.SA_FP32_AUX:
         h64 = S.Heom(ps, precision=S.SA_FP64)
         s64 = h64.new_state()
         h64.autotune(s64)
@@ -326,11 +343,34 @@ def run_ours(args):
         o64 = h64.propagate(a, dt, nerr, max(1, nerr // 10))
         o32 = h.propagate(b, dt, nerr, max(1, nerr // 10))
         err = float(np.max(np.abs(o64[:, :, 1:7] - o32[:, :, 1:7])))
-        extra = {"fp64_ms_per_step": ms64, "fp32_over_fp64_speedup": ms64 / ms_step,
-                 "time_to_t_final_s": {"fp32_aux": ms_step * 10000 / 1e3, "fp64": ms64 * 10000 / 1e3,
-                                       "steps": 10000},
-                 "fp32_max_population_error_vs_fp64": err, "population_error_window_steps": nerr}
         del h64, s64, a, b
+        # the plain single-instance FP64 path: the instances one after another, each
+        # with its own handle (a seeded sample of them, scaled to the whole batch)
+        rng = np.random.default_rng(2608)
+        pick = np.sort(rng.choice(len(ps), size=min(32, len(ps)), replace=False))
+        k1, ms_single = 20, 0.0
+        for i in pick:
+            h1 = S.Heom([ps[i]], precision=S.SA_FP64)
+            s1 = h1.new_state()
+            h1.init_state(s1, _rho0([ws[i]]))
+            h1.propagate(s1, dt, 3, observe=False)
+            h1.prepare(s1, dt, k1)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            h1.propagate(s1, dt, k1, observe=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_single += e0.elapsed_time(e1) / k1
+            del h1, s1
+        ms_single *= len(ps) / len(pick)
+        extra = {"fp64_ms_per_step": ms64, "fp32_over_fp64_speedup": ms64 / ms_step,
+                 "fp64_single_instance_ms_per_step": ms_single,
+                 "fp32_batched_over_fp64_single_speedup": ms_single / ms_step,
+                 "fp64_single_instance_note": f"{len(pick)} seeded instances run one at a time ({k1} steps each, "
+                                              "own handle and CUDA graph), summed and scaled to the batch",
+                 "time_to_t_final_s": {"fp32_aux": ms_step * 10000 / 1e3, "fp64": ms64 * 10000 / 1e3,
+                                       "fp64_single_instance": ms_single * 10000 / 1e3, "steps": 10000},
+                 "fp32_max_population_error_vs_fp64": err, "population_error_window_steps": nerr}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -361,6 +401,8 @@ def main():
     ap.add_argument("--workload", default="w4", choices=["w3", "w4", "w5"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--err-steps", type=int, default=2000)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="fp32: FP32 auxiliary variables with FP64 rho_0 (default); fp64: everything in FP64")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
