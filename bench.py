@@ -103,15 +103,15 @@ def _stage_sha() -> str:
     return hashlib.sha256(src).hexdigest()[:16]
 
 
-def _traffic(workload: str, kernel: int):
+def _traffic(workload: str, kernel_name: str):
     """DRAM bytes per stage launch from the committed ncu summary of this
-    kernel variant, if it was taken on the current kernel source."""
-    name = "list_stage_kernel" if kernel == 1 else "stage_kernel"
-    p = os.path.join(ROOT, "profiles", f"{name}_{workload}_traffic.json")
+    kernel (variant and precision), if it was taken on the current kernel
+    source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel_name.split('<')[0]}_{workload}_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_sha") != _stage_sha():
+    if d.get("kernel_sha") != _stage_sha() or d.get("kernel") != kernel_name:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -219,7 +219,7 @@ def run_reference(args):
 # ------------------------------------------------------------ GPU arm
 
 def _kernel_name(kernel, fp32):
-    base = "list_stage_kernel" if kernel == 1 else "stage_kernel"
+    base = {1: "list_stage_kernel", 2: "ell_stage_kernel"}.get(kernel, "stage_kernel")
     return base + ("<float,true>" if fp32 else "<double,false>")
 
 
@@ -289,13 +289,14 @@ def run_ours(args):
         FP64_BYTES_PER_VAR_STEP * n_vars / 4.0
     achieved = bytes_launch / (launch_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    traffic = _traffic(args.workload, tuning["kernel"])
+    kname = _kernel_name(tuning["kernel"], precision == S.SA_FP32_AUX)
+    traffic = _traffic(args.workload, kname)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
             # DRAM bytes the kernel really moves (ncu, per launch) over the same live launch time
             "dram_achieved": traffic / (launch_ms / 1e3) / 1e9 if traffic else None,
             "dram_frac": traffic / (launch_ms / 1e3) / 1e9 / peak if traffic else None,
-            "kernel": _kernel_name(tuning["kernel"], precision == S.SA_FP32_AUX), "bytes_per_launch": bytes_launch}
+            "kernel": kname, "bytes_per_launch": bytes_launch}
 
     # end to end through the public API with host buffers: upload the state
     # from pinned host memory, K steps with the observables of every step read
