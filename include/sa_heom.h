@@ -102,6 +102,8 @@ typedef struct sa_counts {
     int64_t n_records;              /* hierarchy connection records (pattern, category, k, +/-) */
     int64_t n_terms;                /* per-variable hierarchy terms the records expand to */
     int64_t state_bytes;            /* one state vector at the handle's precision */
+    uint64_t conventional_ados;     /* C(Nm+L, L) exactly when it is below 2^64, else 0
+                                       (batch: the largest instance's, 0 if any overflows) */
 } sa_counts;
 
 typedef struct sa_heom sa_heom;

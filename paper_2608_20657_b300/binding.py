@@ -52,7 +52,8 @@ class Params(ctypes.Structure):
 class Counts(ctypes.Structure):
     _fields_ = [("log10_conventional_ados", ctypes.c_double), ("n_vectors", ctypes.c_int64),
                 ("n_patterns", ctypes.c_int64), ("n_vars", ctypes.c_int64), ("n_categories", ctypes.c_int64),
-                ("n_records", ctypes.c_int64), ("n_terms", ctypes.c_int64), ("state_bytes", ctypes.c_int64)]
+                ("n_records", ctypes.c_int64), ("n_terms", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
+                ("conventional_ados", ctypes.c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

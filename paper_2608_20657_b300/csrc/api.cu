@@ -834,9 +834,12 @@ int sa_bath_drude_lorentz(double lambda, double gamma, double kT, int scheme, in
 }
 
 static void fill_counts(const HostInstance& hi, int precision, sa_counts* out) {
-    const double nm = double(hi.N) * hi.m;
-    out->log10_conventional_ados = (std::lgamma(nm + hi.L + 1.0) - std::lgamma(hi.L + 1.0) - std::lgamma(nm + 1.0)) /
-                                   std::log(10.0);
+    // log10 C(Nm+L, L) = sum_{j=1..L} log10((Nm + j) / j): no cancellation for
+    // Nm up to 2^65 (a difference of lgamma values would lose it all)
+    const long double nm = (long double)hi.N * hi.m;
+    long double lg = 0.0L;
+    for (int j = 1; j <= hi.L; ++j) lg += std::log10((nm + j) / (long double)j);
+    out->log10_conventional_ados = double(lg);
     out->n_vectors = hi.V;
     out->n_patterns = hi.P;
     out->n_vars = int64_t(hi.var_off[hi.P]);
@@ -844,6 +847,22 @@ static void fill_counts(const HostInstance& hi, int precision, sa_counts* out) {
     out->n_records = int64_t(hi.rec.size());
     out->n_terms = hi.n_terms;
     out->state_bytes = out->n_vars * (precision == SA_FP64 ? 16 : 8);
+    // C(Nm+L, L) = prod_{j=1..L} (Nm + j) / j, exact while every partial
+    // product fits (each prefix is itself a binomial coefficient)
+    using u128 = unsigned __int128;
+    const u128 n = u128(uint64_t(hi.N)) * uint64_t(hi.m);
+    u128 c = 1;
+    bool ok = true;
+    for (int j = 1; j <= hi.L && ok; ++j) {
+        const u128 f = n + uint64_t(j);
+        if (c > ~u128(0) / f) {
+            ok = false;
+            break;
+        }
+        c = c * f / uint64_t(j);
+        ok = c <= u128(~uint64_t(0));
+    }
+    out->conventional_ados = ok ? uint64_t(c) : 0;
 }
 
 int sa_heom_counts(const sa_params* p, sa_counts* out) {
@@ -1072,6 +1091,15 @@ int sa_heom_info(const sa_heom* h, int inst, sa_counts* out) {
     }
     t.log10_conventional_ados = lmax;
     t.state_bytes = int64_t(h->state_bytes);
+    t.conventional_ados = 0;
+    bool exact = true;
+    for (int i = 0; i < h->count; ++i) {
+        sa_counts c{};
+        fill_counts(h->inst[i], h->precision, &c);
+        exact = exact && c.conventional_ados != 0;
+        t.conventional_ados = std::max(t.conventional_ados, c.conventional_ados);
+    }
+    if (!exact) t.conventional_ados = 0;
     *out = t;
     return SA_OK;
 }

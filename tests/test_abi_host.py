@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import math
+
 import numpy as np
 import pytest
 
@@ -62,3 +64,17 @@ def test_bath_rejects_bad_input():
         S.bath_drude_lorentz(-1.0, 0.05, 0.025, S.BATH_MATSUBARA, 1)
     with pytest.raises(S.SaHeomError):
         S.bath_drude_lorentz(0.01, 0.05, 0.025, S.BATH_MATSUBARA, 8)
+
+
+@pytest.mark.parametrize("N,m,L", [(2, 1, 3), (10, 2, 6), (100, 2, 8), (1000, 4, 12), (2 ** 61 - 1, 8, 1),
+                                   (2 ** 61, 8, 1), (40, 3, 17), (10 ** 12, 1, 2)])
+def test_exact_conventional_ado_count(N, m, L):
+    """sa_counts.conventional_ados is C(Nm+L, L) (Eq. direct-ado-count) whenever
+    that fits in 64 bits and 0 otherwise; its log10 agrees either way."""
+    rng = np.random.default_rng(m)
+    bath = {"c": rng.uniform(0.1, 0.5, m) + 0j, "cc": rng.uniform(0.1, 0.5, m) + 0j,
+            "nu": rng.uniform(0.2, 1.2, m) + 0j}
+    c = S.counts(S.make_params(N, m, L, bath))
+    exact = math.comb(N * m + L, L)
+    assert c["conventional_ados"] == (exact if exact < 2 ** 64 else 0)
+    assert abs(c["log10_conventional_ados"] - math.log10(exact)) < 1e-9 * max(1.0, math.log10(exact))
