@@ -52,6 +52,7 @@ class Params(ctypes.Structure):
         ("cc_im", ctypes.c_double * MAXM),
         ("nu_re", ctypes.c_double * MAXM),
         ("nu_im", ctypes.c_double * MAXM),
+        ("term", ctypes.c_double),
     ]
 
 
@@ -104,11 +105,12 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def make_params(N, m, L, bath, detuning=0.0, g=0.0, kappa=0.0) -> Params:
-    """bath: dict with complex arrays c, cc, nu of length m (Eq. BCF-exp)."""
+def make_params(N, m, L, bath, detuning=0.0, g=0.0, kappa=0.0, term=0.0) -> Params:
+    """bath: dict with complex arrays c, cc, nu of length m (Eq. BCF-exp);
+    term: terminator strength Delta of the omitted Matsubara terms (0: off)."""
     p = Params()
     p.N, p.m, p.L = int(N), int(m), int(L)
-    p.detuning, p.g, p.kappa = float(detuning), float(g), float(kappa)
+    p.detuning, p.g, p.kappa, p.term = float(detuning), float(g), float(kappa), float(term)
     c = np.asarray(bath["c"], dtype=complex)
     cc = np.asarray(bath["cc"], dtype=complex)
     nu = np.asarray(bath["nu"], dtype=complex)
@@ -134,9 +136,9 @@ KIND = {"Z": 0, "X": 1, "Y": 2, "P": 3, "S": 4, "T": 5}
 class SA:
     """Symmetry-adapted HEOM oracle (O-2).  State: complex128 array of nvar."""
 
-    def __init__(self, N, m, L, bath, detuning=0.0, g=0.0, kappa=0.0, cache=True):
+    def __init__(self, N, m, L, bath, detuning=0.0, g=0.0, kappa=0.0, cache=True, term=0.0):
         self.N, self.m, self.L = int(N), int(m), int(L)
-        self.params = make_params(N, m, L, bath, detuning, g, kappa)
+        self.params = make_params(N, m, L, bath, detuning, g, kappa, term)
         self._h = lib().orc_sa_create(ctypes.byref(self.params), 1 if cache else 0)
         if not self._h:
             raise ValueError("oracle rejected the parameters")
@@ -249,9 +251,9 @@ class SA:
 class Conventional:
     """Conventional scaled HEOM oracle (O-1).  State: (nado, N+1, N+1)."""
 
-    def __init__(self, N, m, L, bath, detuning=0.0, g=0.0, kappa=0.0):
+    def __init__(self, N, m, L, bath, detuning=0.0, g=0.0, kappa=0.0, term=0.0):
         self.N, self.m, self.L = int(N), int(m), int(L)
-        self.params = make_params(N, m, L, bath, detuning, g, kappa)
+        self.params = make_params(N, m, L, bath, detuning, g, kappa, term)
         self._h = lib().orc_conv_create(ctypes.byref(self.params))
         if not self._h:
             raise ValueError("oracle rejected the parameters")

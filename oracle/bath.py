@@ -151,6 +151,21 @@ def pade(lam, gam, kT, K, sigma=0.0):
     return _pack(c, nu, sigma)
 
 
+def terminator(lam, gam, kT, K):
+    """Terminator strength Delta for a Drude-Lorentz bath kept to K Matsubara
+    terms: the omitted terms j > K of the Matsubara expansion (Eq. BCF-exp with
+    nu_j = 2 pi j kT, c_j = 4 lam gam kT nu_j / (nu_j^2 - gam^2)) taken as white
+    noise, Delta = sum_{j > K} c_j / nu_j, summed directly in 50-digit
+    arithmetic (the sum converges like 1/j^2)."""
+    lam, gam, kT = mp.mpf(lam), mp.mpf(gam), mp.mpf(kT)
+
+    def term(j):
+        nuj = 2 * mp.pi * j * kT
+        return 4 * lam * gam * kT / (nuj ** 2 - gam ** 2)
+
+    return float(mp.nsum(term, [K + 1, mp.inf]))
+
+
 def coth_approx(x, scheme: str, K: int):
     """coth x as represented by a scheme: 1/x + sum 2 eta x / (x^2 + xi^2)."""
     if scheme == "matsubara":

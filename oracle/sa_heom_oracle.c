@@ -36,6 +36,10 @@
  *  - Cavity loss: Lindblad kappa (a rho a^+ - 1/2 {a^+ a, rho}); the jump part
  *    leaves the single-excitation manifold, so -kappa/2 {|c><c|, .} acts on
  *    every ADO.
+ *  - Terminator (Sec. V names the Ishizaki-Tanimura treatment of the omitted
+ *    Matsubara terms without a formula): the residual correlation is taken as
+ *    white noise of weight Delta = sum over omitted terms of c_k / nu_k, which
+ *    adds -Delta sum_i [Q_i, [Q_i, rho_n]] to every ADO (off when Delta = 0).
  *  - Pattern order (the global vector of Eq. global-R): tier ascending, then
  *    the vector lists compared lexicographically with larger vectors first.
  *    Variable order inside a pattern: Z; X_1..X_G; Y_1..Y_G; P_1..P_G;
@@ -73,6 +77,7 @@ typedef struct {
     double c_re[ORC_MAXM], c_im[ORC_MAXM];   /* c_k  (Eq. BCF-exp) */
     double cc_re[ORC_MAXM], cc_im[ORC_MAXM]; /* c-check_k */
     double nu_re[ORC_MAXM], nu_im[ORC_MAXM]; /* nu_k */
+    double term;    /* terminator strength Delta (0: off) */
 } orc_params;
 
 static cplx ck(const orc_params* p, int k) { return p->c_re[k] + I * p->c_im[k]; }
@@ -675,6 +680,13 @@ static cplx var_rhs(const orc_sa* s, const double* x, long long i, int kind, int
         break;
     }
     (void)M;
+    /* terminator: -Delta sum_i [Q_i, [Q_i, rho]] multiplies entry (a, b) by the
+     * number of molecules i for which exactly one of a, b is e_i: 0 for Z and
+     * P, 1 for X and Y, 2 for S and T */
+    {
+        int w = (kind == K_X || kind == K_Y) ? 1 : ((kind == K_S || kind == K_T) ? 2 : 0);
+        d += -p->term * (double)w * v;
+    }
     hterm ht[4 * ORC_MAXM];
     int nt = var_hterms(s, i, kind, q, r, ht);
     for (int t = 0; t < nt; ++t) d += ht[t].coef * ld(x, ht[t].src);
@@ -943,6 +955,20 @@ void orc_conv_rhs(const orc_conv* c, const double* xin, double* dxout) {
         matmul(D, Pc, rho, t1);
         matmul(D, rho, Pc, t2);
         for (int e = 0; e < D * D; ++e) d[e] += -0.5 * p->kappa * (t1[e] + t2[e]);
+        /* terminator: -Delta sum_i [Q_i, [Q_i, rho]], with the matrices */
+        if (p->term != 0.0) {
+            cplx* t3 = (cplx*)malloc(sizeof(cplx) * D * D);
+            for (int i = 0; i < N; ++i) {
+                const cplx* Qi = Q + (size_t)i * D * D;
+                matmul(D, Qi, rho, t1);
+                matmul(D, rho, Qi, t2);
+                for (int e = 0; e < D * D; ++e) t3[e] = t1[e] - t2[e];
+                matmul(D, Qi, t3, t1);
+                matmul(D, t3, Qi, t2);
+                for (int e = 0; e < D * D; ++e) d[e] += -p->term * (t1[e] - t2[e]);
+            }
+            free(t3);
+        }
         for (int i = 0; i < N; ++i) {
             const cplx* Qi = Q + (size_t)i * D * D;
             for (int k = 0; k < m; ++k) {

@@ -512,3 +512,65 @@ def test_initial_state_observables(orc):
 
 def test_no_internal_errors(orc):
     assert orc.errors() == 0
+
+
+# ---- terminator (the Ishizaki-Tanimura treatment of omitted Matsubara terms,
+# named in Sec. V; reading: -Delta sum_i [Q_i, [Q_i, rho_n]] on every ADO)
+
+@pytest.mark.parametrize("case", [(2, 1, 3, "hight", 0.02, 0.05, 0.01), (3, 2, 3, "mats", 0.02, 0.05, 0.0),
+                                  (3, 2, 3, "generic", 0.1, 0.2, 0.05), (4, 1, 4, "hight", 0.0, 0.03, 0.0)])
+def test_terminator_sa_equals_conventional(orc, case):
+    """With the terminator on, the symmetry-adapted RHS (a per-variable weight)
+    still equals the conventional RHS (the double commutator with explicit Q_i
+    matrices), for any vector."""
+    N, m, L, kind, det, g, kap = case
+    bath = _bath(kind, m)
+    Delta = 0.0123
+    sa = orc.SA(N, m, L, bath, det, g, kap, term=Delta)
+    cv = orc.Conventional(N, m, L, bath, det, g, kap, term=Delta)
+    mp = cv.map_to(sa)
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(sa.nvar) + 1j * rng.standard_normal(sa.nvar)
+    dsa, dcv = sa.rhs(x), cv.rhs(x[mp])
+    assert np.abs(dcv - dsa[mp]).max() <= 1e-13 * np.abs(dcv).max()
+    # and the term is really there: it changes the RHS by -Delta w x
+    d0 = orc.SA(N, m, L, bath, det, g, kap).rhs(x)
+    lab = sa.var_labels()
+    w = np.select([np.isin(lab["kind"], [1, 2]), np.isin(lab["kind"], [4, 5])], [1.0, 2.0], 0.0)
+    assert np.abs((dsa - d0) + Delta * w * x).max() <= 1e-14 * np.abs(x).max()
+    assert orc.errors() == 0
+
+
+def test_terminator_closed_form(orc):
+    """L = 0, g = 0: every variable evolves on its own, dX_0 = (-i Delta' - Delta) X_0,
+    dT_0 = -2 Delta T_0, Z and P_0 constant.  RK4 on a scalar linear equation
+    multiplies by 1 + z + z^2/2 + z^3/6 + z^4/24 (z = rate dt) per step, exactly."""
+    bath = _bath("hight", 1)
+    N, det, Delta = 5, 0.03, 0.02
+    sa = orc.SA(N, 1, 0, bath, det, 0.0, 0.0, term=Delta)
+    X0, T0 = 0.2 - 0.1j, 0.05
+    x = sa.initial_state(0.5, X0, np.conj(X0), 0.1, T0)
+    dt, steps = 0.05, 400
+    y = sa.rk4(x, dt, steps)
+    amp = lambda z: (1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24) ** steps
+    ix = sa.rho0_index()
+    assert abs(y[ix["X0"]] - X0 * amp((-1j * det - Delta) * dt)) < 1e-13
+    assert abs(y[ix["Y0"]] - np.conj(X0) * amp((1j * det - Delta) * dt)) < 1e-13
+    assert abs(y[ix["T0"]] - T0 * amp(-2 * Delta * dt)) < 1e-14
+    assert y[ix["Z"]] == 0.5 and y[ix["P0"]] == 0.1
+
+
+@pytest.mark.parametrize("K", [0, 1, 2, 5])
+def test_terminator_strength(orc, K):
+    """oracle.bath.terminator sums the omitted Matsubara c_j / nu_j term by term;
+    it must equal the closed form of the full sum, lambda (2 kT / gamma -
+    cot(gamma / 2 kT)), less the first K terms, and vanish as K grows."""
+    import math
+
+    import oracle.bath as B
+
+    lam, gam, kT = 0.02, 0.05, 0.025
+    full = lam * (2 * kT / gam - 1 / math.tan(gam / (2 * kT)))
+    kept = sum(4 * lam * gam * kT / ((2 * math.pi * j * kT) ** 2 - gam ** 2) for j in range(1, K + 1))
+    assert abs(B.terminator(lam, gam, kT, K) - (full - kept)) < 1e-15
+    assert B.terminator(lam, gam, kT, K + 1) < B.terminator(lam, gam, kT, K)
