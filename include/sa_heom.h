@@ -79,6 +79,12 @@ enum { SA_BATH_HIGH_T = 0, SA_BATH_MATSUBARA = 1, SA_BATH_PADE = 2 };
  *   kappa      photon population decay rate: -kappa/2 {|c><c|, .} on every
  *              ADO (Lindblad on the cavity mode restricted to the manifold).
  *   c, cc, nu  c_k, c-check_k, nu_k of Eq. BCF-exp, k < m.
+ *   term       terminator strength Delta (0: off): the bath terms left out of
+ *              the expansion taken as white noise (the Ishizaki-Tanimura
+ *              treatment Sec. V names), -Delta sum_i [Q_i, [Q_i, .]] on every
+ *              ADO, i.e. -Delta w V per unique variable with w = 0 for Z and
+ *              P, 1 for X and Y, 2 for S and T.  sa_bath_terminator gives
+ *              Delta for the Matsubara scheme.
  */
 typedef struct sa_params {
     int64_t N;
@@ -90,6 +96,7 @@ typedef struct sa_params {
     double c_re[SA_HEOM_MAXM], c_im[SA_HEOM_MAXM];
     double cc_re[SA_HEOM_MAXM], cc_im[SA_HEOM_MAXM];
     double nu_re[SA_HEOM_MAXM], nu_im[SA_HEOM_MAXM];
+    double term;
 } sa_params;
 
 /* Sizes of one instance or of a whole batch. */
@@ -123,6 +130,16 @@ typedef struct sa_heom sa_heom;
  * Other fields of *p are left untouched.  Errors: INVALID_ARG (non-positive
  * lambda, gamma or kT, negative sigma, too many terms, n_poles > 12 for Pade).
  */
+/*
+ * sa_bath_terminator -- *out = Delta for a Drude-Lorentz bath kept to
+ * n_matsubara Matsubara poles (SA_BATH_MATSUBARA): the sum over the omitted
+ * poles j > n_matsubara of c_j / nu_j, from the closed form of the full sum,
+ * lambda (2 kT / gamma - cot(gamma / (2 kT))), less the kept ones.  Errors:
+ * INVALID_ARG (non-positive lambda, gamma or kT, n_matsubara < 0, a pole on
+ * gamma).
+ */
+int sa_bath_terminator(double lambda, double gamma, double kT, int n_matsubara, double* out);
+
 int sa_bath_drude_lorentz(double lambda, double gamma, double kT, int scheme, int n_poles,
                           double sigma, sa_params* p);
 

@@ -40,6 +40,7 @@ class Params(ctypes.Structure):
         ("c_re", ctypes.c_double * MAXM), ("c_im", ctypes.c_double * MAXM),
         ("cc_re", ctypes.c_double * MAXM), ("cc_im", ctypes.c_double * MAXM),
         ("nu_re", ctypes.c_double * MAXM), ("nu_im", ctypes.c_double * MAXM),
+        ("term", ctypes.c_double),
     ]
 
     def bath(self) -> dict:
@@ -72,6 +73,7 @@ def lib() -> ctypes.CDLL:
         P = ctypes.POINTER
         sig = {
             "sa_bath_drude_lorentz": [dbl, dbl, dbl, i32, i32, dbl, P(Params)],
+            "sa_bath_terminator": [dbl, dbl, dbl, i32, P(dbl)],
             "sa_heom_counts": [P(Params), P(Counts)],
             "sa_heom_build": [P(Params), i32, i32, i32, P(vp)],
             "sa_heom_info": [vp, i32, P(Counts)],
@@ -124,7 +126,7 @@ def lib() -> ctypes.CDLL:
 
 
 def exported_symbols() -> list[str]:
-    return ["sa_bath_drude_lorentz", "sa_heom_counts", "sa_heom_build", "sa_heom_destroy", "sa_heom_info",
+    return ["sa_bath_drude_lorentz", "sa_bath_terminator", "sa_heom_counts", "sa_heom_build", "sa_heom_destroy", "sa_heom_info",
             "sa_heom_var_offset", "sa_heom_dump_vectors", "sa_heom_dump_patterns", "sa_heom_dump_categories",
             "sa_heom_dump_terms", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_state_upload",
             "sa_heom_state_download", "sa_heom_rhs", "sa_heom_step", "sa_heom_propagate", "sa_heom_observables",
@@ -157,15 +159,16 @@ def _stream(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
 
 
-def make_params(N, m=None, L=0, bath=None, detuning=0.0, g=0.0, kappa=0.0) -> Params:
-    """sa_params from a bath dict {c, cc, nu} (complex arrays of length m)."""
+def make_params(N, m=None, L=0, bath=None, detuning=0.0, g=0.0, kappa=0.0, term=0.0) -> Params:
+    """sa_params from a bath dict {c, cc, nu} (complex arrays of length m);
+    term: terminator strength Delta (0: off, see bath_terminator)."""
     p = Params()
     c = np.asarray(bath["c"], complex)
     cc = np.asarray(bath["cc"], complex)
     nu = np.asarray(bath["nu"], complex)
     m = len(c) if m is None else m
     p.N, p.m, p.L = int(N), int(m), int(L)
-    p.detuning, p.g, p.kappa = float(detuning), float(g), float(kappa)
+    p.detuning, p.g, p.kappa, p.term = float(detuning), float(g), float(kappa), float(term)
     for k in range(m):
         p.c_re[k], p.c_im[k] = c[k].real, c[k].imag
         p.cc_re[k], p.cc_im[k] = cc[k].real, cc[k].imag
@@ -178,6 +181,13 @@ def bath_drude_lorentz(lam, gam, kT, scheme=BATH_MATSUBARA, n_poles=1, sigma=0.0
     p = Params()
     _check(lib().sa_bath_drude_lorentz(lam, gam, kT, scheme, n_poles, sigma, ctypes.byref(p)), "sa_bath_drude_lorentz")
     return p.bath()
+
+
+def bath_terminator(lam, gam, kT, n_matsubara) -> float:
+    """sa_bath_terminator: Delta of the Matsubara poles beyond n_matsubara."""
+    out = ctypes.c_double()
+    _check(lib().sa_bath_terminator(lam, gam, kT, int(n_matsubara), ctypes.byref(out)), "sa_bath_terminator")
+    return out.value
 
 
 def counts(p: Params) -> dict:

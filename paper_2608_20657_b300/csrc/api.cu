@@ -256,7 +256,7 @@ void list_item(const sa_heom* h, const ItemDesc& d, ListItem& W) {
         for (int q = 1; q <= G; ++q) {
             put(loc_X(G, q), pl, uint32_t(opR) + cb + q - 1, 1);
             put(loc_Y(G, q), uint32_t(opC) + cb + q - 1, pl, 2);
-            put(loc_P(G, q), pl + G + q, pl + q, 0);
+            put(loc_P(G, q), pl + G + q, pl + q, 4);
             for (int r = 1; r <= G; ++r)
                 if (r != q) put(loc_S(G, q, r), pl + G + r, pl + q, 0);
             const int tr = (h->cat_word[H.cat_off + q - 1] >> 15) & 31;
@@ -341,6 +341,7 @@ int build_blobs(sa_heom* h) {
                 ic[nic].g = V(q.g);
                 ic[nic].det = V(q.detuning);
                 ic[nic].kap = V(q.kappa);
+                ic[nic].term = V(q.term);
                 ic[nic].coef_base = uint32_t(H.inst) * uint32_t(kListCoefStride);
                 ++nic;
             }
@@ -833,6 +834,13 @@ int sa_bath_drude_lorentz(double lambda, double gamma, double kT, int scheme, in
     return rc;
 }
 
+int sa_bath_terminator(double lambda, double gamma, double kT, int n_matsubara, double* out) {
+    std::string err;
+    const int rc = terminator(lambda, gamma, kT, n_matsubara, out, err);
+    if (rc) g_err = err;
+    return rc;
+}
+
 static void fill_counts(const HostInstance& hi, int precision, sa_counts* out) {
     // log10 C(Nm+L, L) = sum_{j=1..L} log10((Nm + j) / j): no cancellation for
     // Nm up to 2^65 (a difference of lgamma values would lose it all)
@@ -951,7 +959,8 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
         D.gf = float(hi.p.g);
         D.detf = float(hi.p.detuning);
         D.kappaf = float(hi.p.kappa);
-        D.pad = 0;
+        D.termf = float(hi.p.term);
+        D.term = hi.p.term;
         D.coef_base = uint32_t(i) * kCoefPerInst;
         D.side = uint32_t(i) * kSideSlots;
         D.var_begin = vb;

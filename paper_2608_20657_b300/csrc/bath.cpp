@@ -101,6 +101,36 @@ bool pade_poles(int K, std::vector<ld>& eta, std::vector<ld>& xi) {
 
 }  // namespace
 
+// Terminator strength of the Matsubara scheme: the omitted poles' c_j / nu_j.
+// With nu_j = 2 pi j kT and c_j = 4 lambda gamma kT nu_j / (nu_j^2 - gamma^2),
+// c_j / nu_j = 4 lambda gamma kT / (nu_j^2 - gamma^2), whose sum over all j
+// is lambda (2 kT / gamma - cot(gamma / 2 kT)) (partial fractions of cot).
+int terminator(double lambda, double gamma, double kT, int n_matsubara, double* out, std::string& err) {
+    if (!out || !(lambda > 0) || !(gamma > 0) || !(kT > 0) || !std::isfinite(lambda) || !std::isfinite(gamma) ||
+        !std::isfinite(kT) || n_matsubara < 0) {
+        err = "lambda, gamma, kT > 0 and n_matsubara >= 0 required";
+        return SA_ERR_INVALID_ARG;
+    }
+    const long double x = (long double)gamma / (2.0L * kT);
+    const long double pi = 3.141592653589793238462643383279502884L;
+    if (std::fabs(std::sin(x)) < 1e-300L) {
+        err = "gamma / (2 kT) is a multiple of pi";
+        return SA_ERR_INVALID_ARG;
+    }
+    long double d = (long double)lambda * (1.0L / x - std::cos(x) / std::sin(x));
+    for (int j = 1; j <= n_matsubara; ++j) {
+        const long double nuj = 2.0L * pi * j * kT;
+        const long double den = nuj * nuj - (long double)gamma * gamma;
+        if (den == 0.0L) {
+            err = "a Matsubara pole coincides with gamma";
+            return SA_ERR_INVALID_ARG;
+        }
+        d -= 4.0L * lambda * gamma * kT / den;
+    }
+    *out = double(d);
+    return SA_OK;
+}
+
 int drude_lorentz(double lambda, double gamma, double kT, int scheme, int n_poles, double sigma, sa_params* p,
                   std::string& err) {
     if (!p || !(lambda > 0) || !(gamma > 0) || !(kT > 0) || !(sigma >= 0) || !std::isfinite(lambda) ||

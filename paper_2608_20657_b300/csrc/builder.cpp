@@ -167,7 +167,7 @@ int build_instance(const sa_params& p, HostInstance& hi, std::string& err) {
         err = "N >= 1, 1 <= m <= 8, 0 <= L <= 30 required";
         return SA_ERR_INVALID_ARG;
     }
-    const double scal[3] = {p.detuning, p.g, p.kappa};
+    const double scal[4] = {p.detuning, p.g, p.kappa, p.term};
     for (double v : scal)
         if (!std::isfinite(v)) {
             err = "non-finite system parameter";

@@ -19,7 +19,7 @@ struct ConvDev {
     const double2* gamma;
     const double2* coef;
     int N, D, m, L;
-    double g, det, kappa;
+    double g, det, kappa, term;
     long long nado;
 };
 cudaError_t conv_launch(const ConvDev& P, const void* x, void* xout, const void* y, void* acc, void* yout,
@@ -98,6 +98,7 @@ ConvDev devview(const sa_conv* c) {
     P.g = c->p.g;
     P.det = c->p.detuning;
     P.kappa = c->p.kappa;
+    P.term = c->p.term;
     P.nado = c->nado;
     return P;
 }

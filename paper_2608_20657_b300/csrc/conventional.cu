@@ -29,7 +29,7 @@ struct ConvDev {
     const double2* gamma;   // per ADO: Gamma_n
     const double2* coef;    // per k: [0] sqrt|c_k|, [1] c_k / sqrt|c_k|, [2] cc_k / sqrt|c_k| (complex)
     int N, D, m, L;
-    double g, det, kappa;
+    double g, det, kappa, term;
     long long nado;
 };
 
@@ -68,7 +68,10 @@ __global__ void __launch_bounds__(256) conv_stage_kernel(ConvDev P, const double
         Hr.y = (hr - hb) * v.y + P.g * (sy - ty);
     }
     const double2 gam = P.gamma[t];
-    const double lk = 0.5 * P.kappa * ((a == 0 ? 1.0 : 0.0) + (b == 0 ? 1.0 : 0.0));
+    // cavity loss and the terminator: sum_i [Q_i, [Q_i, rho]]_{ab} counts the
+    // molecules i for which exactly one of a, b is e_i
+    const double lk = 0.5 * P.kappa * ((a == 0 ? 1.0 : 0.0) + (b == 0 ? 1.0 : 0.0)) +
+                      P.term * (a != b ? double((a > 0) + (b > 0)) : 0.0);
     // -i Hr - Gamma v - loss v
     double dx = Hr.y - (gam.x + lk) * v.x + gam.y * v.y;
     double dy = -Hr.x - (gam.x + lk) * v.y - gam.y * v.x;

@@ -140,6 +140,9 @@ __device__ __forceinline__ typename Cx<A>::t var_rhs(const StageParams<T>& P, in
     const A g = A(sizeof(A) == 8 ? I.g : I.gf);
     const A det = A(sizeof(A) == 8 ? I.detuning : I.detf);
     const A kap = A(sizeof(A) == 8 ? I.kappa : I.kappaf);
+    // terminator -Delta w: w = 0 for Z and P, 1 for X and Y, 2 for S and T
+    const A trm = A(sizeof(A) == 8 ? I.term : I.termf) *
+                  A(kind == KX || kind == KY ? 1 : ((kind == KS || kind == KT) ? 2 : 0));
     int self;
     switch (kind) {
         case KZ: self = 0; break;
@@ -171,13 +174,13 @@ __device__ __forceinline__ typename Cx<A>::t var_rhs(const StageParams<T>& P, in
         const CA t = kind == KX ? csub(Z, s) : csub(s, Z);
         const A sd = kind == KX ? det : -det;
         d = mk(sd * v.y + g * t.y, -sd * v.x - g * t.x);
-        const CA dm = cadd(gam, mk(A(0.5) * kap, A(0)));
+        const CA dm = cadd(gam, mk(A(0.5) * kap + trm, A(0)));
         d = cfma(mk(-dm.x, -dm.y), v, d);
     } else {
         // P, T: -i g (Y_q - X_q);  S_{q,r}: -i g (Y_r - X_q)
         const CA t = csub(own(G + (kind == KS ? r : q)), own(q));
         d = mk(g * t.y, -g * t.x);
-        d = cfma(mk(-gam.x, -gam.y), v, d);
+        d = cfma(mk(-(gam.x + trm), -gam.y), v, d);
     }
     // hierarchy terms: the records of the row category (row delta of
     // Eq. projector-commutator-element) and of the column category (column
@@ -340,6 +343,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
             pc.det = sizeof(T) == 8 ? T(I.detuning) : T(I.detf);
             pc.kap = sizeof(T) == 8 ? T(I.kappa) : T(I.kappaf);
             pc.coef_base = I.coef_base;
+            pc.term = sizeof(T) == 8 ? T(I.term) : T(I.termf);
             S.pc[j] = pc;
         }
         for (uint32_t cl = lane; cl < ncat; cl += 32) {
@@ -401,7 +405,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
             // rho0_kernel
             if (FP64SIDE && h.tier == 0) continue;
             const PatConst<T> pc = S.pc[j];
-            const T g = pc.g, det = pc.det, kap = pc.kap;
+            const T g = pc.g, det = pc.det, kap = pc.kap, trm = pc.term;
             const C gam = S.gam[j];
             const C v = S.x[l];
             const C* xp = S.x + pl;
@@ -419,7 +423,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 const int cc = kind == KS ? r : q;  // column category
                 const C t = csub(xp[G + cc], xp[q]);
                 dv = mk(g * t.y, -g * t.x);
-                dv = cfma(mk(-gam.x, -gam.y), v, dv);
+                dv = cfma(mk(-(gam.x + T(2) * trm), -gam.y), v, dv);  // terminator weight 2
                 const uint32_t wr = S.cw[cb + q - 1];
                 const uint32_t ra = h.rec_off + (wr & 1023);
                 const int nr = int((wr >> 10) & 31);
@@ -469,7 +473,7 @@ __global__ void __launch_bounds__(256) stage_kernel(StageParams<T> P) {
                 const C t = kind == KX ? csub(Z, S.R[cb + q - 1]) : csub(S.Cs[cb + q - 1], Z);
                 const T sd = kind == KX ? det : -det;
                 dv = mk(sd * v.y + g * t.y, -sd * v.x - g * t.x);
-                dv = cfma(mk(-(gam.x + T(0.5) * kap), -gam.y), v, dv);
+                dv = cfma(mk(-(gam.x + T(0.5) * kap + trm), -gam.y), v, dv);  // terminator weight 1
                 const uint32_t w = S.cw[cb + q - 1];
                 const uint32_t ra = h.rec_off + (w & 1023);
                 const int n = int((w >> 10) & 31);
@@ -742,10 +746,13 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
             const C gm = reinterpret_cast<const C*>(S.blob + B.gam)[j];
             const PatConst<T> pc = reinterpret_cast<const PatConst<T>*>(S.blob + B.ic)[ph[j].islot];
             // diagonal: -Gamma, the cavity loss (1/2 per cavity index) and
-            // -/+ i detuning for X / Y (classes: 0 P S T, 1 X, 2 Y, 3 Z)
-            const T lossf = cls == 0 ? T(0) : (cls == 3 ? T(1) : T(0.5));
+            // -/+ i detuning for X / Y, the terminator -Delta w (classes: 0 S T,
+            // 1 X, 2 Y, 3 Z, 4 P)
+            const bool xy = cls == 1 || cls == 2;
+            const T lossf = cls == 3 ? T(1) : (xy ? T(0.5) : T(0));
+            const T wt = cls == 0 ? T(2) : (xy ? T(1) : T(0));
             const T dim = cls == 1 ? -pc.det : (cls == 2 ? pc.det : T(0));
-            const C diag = mk(-(gm.x + lossf * pc.kap), dim - gm.y);
+            const C diag = mk(-(gm.x + lossf * pc.kap + wt * pc.term), dim - gm.y);
             const C t = csub(op[a], op[b]);
             C dv = mk(pc.g * t.y, -pc.g * t.x);
             dv = cfma(diag, v, dv);
@@ -884,8 +891,10 @@ __global__ void __launch_bounds__(256) ell_stage_kernel(StageParams<T> P) {
         b = mk(T(0), T(0));
     }
     const T lossf = kind == KZ ? T(1) : ((kind == KX || kind == KY) ? T(0.5) : T(0));
+    const T wt = (kind == KX || kind == KY) ? T(1) : ((kind == KS || kind == KT) ? T(2) : T(0));
+    const T trm = sizeof(T) == 8 ? T(I.term) : T(I.termf);
     const T dim = kind == KX ? -det : (kind == KY ? det : T(0));
-    const C diag = mk(-(gam.x + lossf * kap), dim - gam.y);
+    const C diag = mk(-(gam.x + lossf * kap + wt * trm), dim - gam.y);
     const C t = csub(a, b);
     C dv = mk(g * t.y, -g * t.x);
     dv = cfma(diag, xv, dv);

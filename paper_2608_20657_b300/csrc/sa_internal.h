@@ -64,13 +64,15 @@ inline uint32_t pack_cat(int rec_start, int nrec, int trank, int nup) {
 // per-instance constants on the device
 struct InstDev {
     double g, detuning, kappa, N;
-    float gf, detf, kappaf, pad;
+    float gf, detf, kappaf, termf;
     uint32_t coef_base;  // into the coefficient tables
     uint32_t side;       // first FP64 side slot
     uint32_t var_begin;  // first variable
     uint32_t n_rho0;     // variables of the physical representative (4 or 5)
     uint32_t pat_begin;  // first pattern (the empty pattern)
     uint32_t pad2[3];
+    double term;         // terminator strength Delta (0: off)
+    double pad3;
 };
 
 // ---- host tables of one instance ------------------------------------------
@@ -123,6 +125,7 @@ struct ItemDesc {
 template <typename T> struct PatConst {
     T g, det, kap;       // coupling, detuning, loss rate of the pattern's instance
     uint32_t coef_base;  // the instance's coefficient table
+    T term;              // terminator strength Delta
 };
 
 // A pattern as the list kernel's blob gives it (8 bytes): its first variable
@@ -208,6 +211,7 @@ int64_t expand_terms(const HostInstance& hi, int64_t* var, int64_t* src, int32_t
 // bath.cpp
 int drude_lorentz(double lambda, double gamma, double kT, int scheme, int n_poles, double sigma, sa_params* p,
                   std::string& err);
+int terminator(double lambda, double gamma, double kT, int n_matsubara, double* out, std::string& err);
 
 // local index of a variable inside a pattern (canonical layout)
 inline int64_t loc_Z() { return 0; }

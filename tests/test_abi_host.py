@@ -78,3 +78,15 @@ def test_exact_conventional_ado_count(N, m, L):
     exact = math.comb(N * m + L, L)
     assert c["conventional_ados"] == (exact if exact < 2 ** 64 else 0)
     assert abs(c["log10_conventional_ados"] - math.log10(exact)) < 1e-9 * max(1.0, math.log10(exact))
+
+
+@pytest.mark.parametrize("K", [0, 1, 3, 6])
+def test_terminator_strength_matches_oracle(K):
+    """sa_bath_terminator (closed form less the kept poles) against the oracle's
+    term-by-term sum of the omitted Matsubara c_j / nu_j."""
+    for lam, gam, kT in [(0.01, 0.05, 0.025), (0.03, 0.02, 0.01), (0.02, 0.05, 0.025)]:
+        got = S.bath_terminator(lam, gam, kT, K)
+        ref = OB.terminator(lam, gam, kT, K)
+        assert abs(got - ref) <= 1e-15 + 1e-12 * abs(ref)
+    with pytest.raises(S.SaHeomError):
+        S.bath_terminator(-0.01, 0.05, 0.025, K)

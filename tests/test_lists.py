@@ -124,9 +124,11 @@ def _eval_lists(lib, sas, baths, x, insts):
                 inst = ginst[p]
                 sa_p = sas[inst].params
                 g, det, kap = sa_p.g, sa_p.detuning, sa_p.kappa
-                lossf = [0.0, 0.5, 0.5, 1.0][cls]
-                dim = [0.0, -det, det, 0.0][cls]
-                diag = -(ggam[p].real + lossf * kap) + 1j * (dim - ggam[p].imag)
+                # classes: 0 S T, 1 X, 2 Y, 3 Z, 4 P
+                lossf = [0.0, 0.5, 0.5, 1.0, 0.0][cls]
+                dim = [0.0, -det, det, 0.0, 0.0][cls]
+                wt = [2.0, 1.0, 1.0, 0.0, 0.0][cls]  # terminator weight
+                diag = -(ggam[p].real + lossf * kap + wt * sa_p.term) + 1j * (dim - ggam[p].imag)
                 dv = diag * op[l] - 1j * g * (op[a] - op[b])
                 dv += np.sum(coefs[inst][slot[:n]] * x[idx[:n]])
                 out[vg] = dv
@@ -166,7 +168,7 @@ def _case(params_list, baths, sas, precision, chunk=None):
 @pytest.mark.parametrize("N,m,L", [(1, 1, 3), (2, 1, 3), (3, 2, 3), (10, 2, 6), (12, 3, 4), (7, 4, 3), (2, 2, 6)])
 def test_lists_reproduce_oracle_rhs(N, m, L, precision):
     bath = _generic_bath(m, N + 7 * m + L)
-    kw = dict(detuning=0.1, g=0.2, kappa=0.05)
+    kw = dict(detuning=0.1, g=0.2, kappa=0.05, term=0.013)
     sa = oracle.SA(N, m, L, bath, **kw)
     _case([S.make_params(N, m, L, bath, **kw)], [bath], [sa], precision)
 
@@ -232,8 +234,9 @@ def _eval_ell(lib, sas, baths, x):
                 a, b = s + sum(M[c - 1] * xp[Sv(c, q)] for c in range(1, G + 1) if c != q), xp[0]
         sp = sas[inst].params
         lossf = {0: 1.0, 1: 0.5, 2: 0.5}.get(kind, 0.0)
+        wt = {1: 1.0, 2: 1.0, 4: 2.0, 5: 2.0}.get(kind, 0.0)  # terminator weight
         dim = {1: -sp.detuning, 2: sp.detuning}.get(kind, 0.0)
-        diag = -(ggam[p].real + lossf * sp.kappa) + 1j * (dim - ggam[p].imag)
+        diag = -(ggam[p].real + lossf * sp.kappa + wt * sp.term) + 1j * (dim - ggam[p].imag)
         rows = np.arange(int(E["rbase"][w]), int(E["rbase"][w + 1]))
         idx, slot = E["tidx"][rows * 32 + lane].astype(np.int64), E["tcid"][rows * 32 + lane].astype(np.int64)
         real = slot != ZERO_SLOT
@@ -252,7 +255,7 @@ def _eval_ell(lib, sas, baths, x):
 @pytest.mark.parametrize("N,m,L", [(1, 1, 3), (3, 2, 3), (10, 2, 6), (7, 4, 3)])
 def test_ell_reproduces_oracle_rhs(N, m, L, precision):
     bath = _generic_bath(m, N + 7 * m + L)
-    kw = dict(detuning=0.1, g=0.2, kappa=0.05)
+    kw = dict(detuning=0.1, g=0.2, kappa=0.05, term=0.013)
     sa = oracle.SA(N, m, L, bath, **kw)
     lib = S.Heom(S.make_params(N, m, L, bath, **kw), precision=precision, host_only=True)
     lib.set_kernel(S.SA_KERNEL_ELL)
