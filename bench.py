@@ -50,6 +50,17 @@ def _peaks():
     return 6400.0, "fallback"
 
 
+def max_over_ranks(value: float, dist) -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's);
+    the tensor lives where the process group's backend can reduce it."""
+    import torch
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -274,9 +285,7 @@ def run_ours(args):
         dist.barrier()
     ck = clocks.stop() if clocks else None
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist)
     ms_step = ms / args.steps
     n_vars = h.n_vars
     value = n_vars * world * args.steps / (ms / 1e3)
