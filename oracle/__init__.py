@@ -53,6 +53,7 @@ class Params(ctypes.Structure):
         ("nu_re", ctypes.c_double * MAXM),
         ("nu_im", ctypes.c_double * MAXM),
         ("term", ctypes.c_double),
+        ("d", ctypes.c_int),
     ]
 
 
@@ -105,11 +106,12 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def make_params(N, m, L, bath, detuning=0.0, g=0.0, kappa=0.0, term=0.0) -> Params:
+def make_params(N, m, L, bath, detuning=0.0, g=0.0, kappa=0.0, term=0.0, d=0) -> Params:
     """bath: dict with complex arrays c, cc, nu of length m (Eq. BCF-exp);
-    term: terminator strength Delta of the omitted Matsubara terms (0: off)."""
+    term: terminator strength Delta of the omitted Matsubara terms (0: off);
+    d: distinguished molecules (0, or 1: molecule 1 keeps its label)."""
     p = Params()
-    p.N, p.m, p.L = int(N), int(m), int(L)
+    p.N, p.m, p.L, p.d = int(N), int(m), int(L), int(d)
     p.detuning, p.g, p.kappa, p.term = float(detuning), float(g), float(kappa), float(term)
     c = np.asarray(bath["c"], dtype=complex)
     cc = np.asarray(bath["cc"], dtype=complex)
@@ -136,9 +138,9 @@ KIND = {"Z": 0, "X": 1, "Y": 2, "P": 3, "S": 4, "T": 5}
 class SA:
     """Symmetry-adapted HEOM oracle (O-2).  State: complex128 array of nvar."""
 
-    def __init__(self, N, m, L, bath, detuning=0.0, g=0.0, kappa=0.0, cache=True, term=0.0):
-        self.N, self.m, self.L = int(N), int(m), int(L)
-        self.params = make_params(N, m, L, bath, detuning, g, kappa, term)
+    def __init__(self, N, m, L, bath, detuning=0.0, g=0.0, kappa=0.0, cache=True, term=0.0, d=0):
+        self.N, self.m, self.L, self.d = int(N), int(m), int(L), int(d)
+        self.params = make_params(N, m, L, bath, detuning, g, kappa, term, d)
         self._h = lib().orc_sa_create(ctypes.byref(self.params), 1 if cache else 0)
         if not self._h:
             raise ValueError("oracle rejected the parameters")
@@ -231,12 +233,33 @@ class SA:
         return y, obs
 
     def rho0_index(self) -> dict:
-        """Indices of the physical representative's variables (empty pattern)."""
-        G = 1
-        idx = {"Z": 0, "X0": 1, "Y0": 2, "P0": 3}
-        if self.N >= 2:
-            idx["T0"] = (G + 1) ** 2
+        """Indices of the physical representative's variables (empty pattern).
+        With d = 1 its categories are the distinguished molecule (suffix d)
+        and the zero category of the others (suffix 0)."""
+        if self.d == 0:
+            idx = {"Z": 0, "X0": 1, "Y0": 2, "P0": 3}
+            if self.N >= 2:
+                idx["T0"] = 4
+            return idx
+        if self.N == 1:
+            return {"Z": 0, "Xd": 1, "Yd": 2, "Pd": 3}
+        idx = {"Z": 0, "Xd": 1, "X0": 2, "Yd": 3, "Y0": 4, "Pd": 5, "P0": 6, "Sd0": 7, "S0d": 8}
+        if self.N >= 3:
+            idx["T0"] = 9
         return idx
+
+    def initial_state_dense(self, rho) -> np.ndarray:
+        """Factorised initial hierarchy from a dense (N+1)x(N+1) rho_S in the
+        basis {c, e_1 .. e_N}, invariant under permutations of the molecules
+        it does not distinguish (all of them for d = 0, 2..N for d = 1)."""
+        rho = np.asarray(rho, complex)
+        x = self.zeros()
+        ix = self.rho0_index()
+        e = {"Z": (0, 0), "X0": (self.d + 1, 0), "Y0": (0, self.d + 1), "P0": (self.d + 1, self.d + 1),
+             "T0": (self.d + 1, self.d + 2), "Xd": (1, 0), "Yd": (0, 1), "Pd": (1, 1), "Sd0": (1, 2), "S0d": (2, 1)}
+        for k, j in ix.items():
+            x[j] = rho[e[k]]
+        return x
 
     def initial_state(self, Z, X0, Y0, P0, T0=0.0) -> np.ndarray:
         """Factorised initial hierarchy (Eqs. factorized-initial-zero/higher)."""

@@ -78,6 +78,7 @@ typedef struct {
     double cc_re[ORC_MAXM], cc_im[ORC_MAXM]; /* c-check_k */
     double nu_re[ORC_MAXM], nu_im[ORC_MAXM]; /* nu_k */
     double term;    /* terminator strength Delta (0: off) */
+    int d;          /* distinguished molecules: 0, or 1 (molecule 1 keeps its label) */
 } orc_params;
 
 static cplx ck(const orc_params* p, int k) { return p->c_re[k] + I * p->c_im[k]; }
@@ -103,7 +104,9 @@ int orc_num_threads(void) {
 typedef struct {
     int m, L;
     int V;                 /* vectors including the zero vector (id 0) */
-    unsigned char* comp;   /* V * m components */
+    int Vtot;              /* V, or 2 V with a distinguished molecule: ids V .. 2V-1
+                              are the distinguished molecule's vectors (id - V) */
+    unsigned char* comp;   /* Vtot * m components */
     int* norm;             /* |alpha| */
     int* lut;              /* mixed-radix (L+1)^m code -> id, -1 if |alpha| > L */
     long long lut_size;
@@ -131,7 +134,7 @@ static long long vec_code(const unsigned char* a, int m, int L) {
     return c;
 }
 
-static void vecset_build(vecset* vs, int m, int L) {
+static void vecset_build(vecset* vs, int m, int L, int d) {
     vs->m = m; vs->L = L;
     long long total = 1;
     for (int k = 0; k < m; ++k) total *= (L + 1);
@@ -149,11 +152,12 @@ static void vecset_build(vecset* vs, int m, int L) {
     qsort(all, cnt, m, vec_qsort_cmp);
     /* after sorting, the zero vector is last; move it to id 0 */
     vs->V = cnt;   /* >= 1: the zero vector is always in the set */
-    vs->comp = (unsigned char*)calloc((size_t)cnt + 1, m);
+    vs->Vtot = d ? 2 * cnt : cnt;
+    vs->comp = (unsigned char*)calloc((size_t)vs->Vtot + 1, m);
     for (int v = 1; v < cnt; ++v)
         for (int k = 0; k < m; ++k) vs->comp[(size_t)v * m + k] = all[(size_t)(v - 1) * m + k];
     free(all);
-    vs->norm = (int*)malloc(sizeof(int) * cnt);
+    vs->norm = (int*)malloc(sizeof(int) * vs->Vtot);
     vs->lut = (int*)malloc(sizeof(int) * total);
     for (long long c = 0; c < total; ++c) vs->lut[c] = -1;
     for (int v = 0; v < cnt; ++v) {
@@ -162,18 +166,25 @@ static void vecset_build(vecset* vs, int m, int L) {
         vs->norm[v] = s;
         vs->lut[vec_code(vs->comp + (size_t)v * m, m, L)] = v;
     }
+    for (int v = cnt; v < vs->Vtot; ++v) { /* the distinguished molecule's copies */
+        memcpy(vs->comp + (size_t)v * m, vs->comp + (size_t)(v - cnt) * m, m);
+        vs->norm[v] = vs->norm[v - cnt];
+    }
 }
 
 static void vecset_free(vecset* vs) { free(vs->comp); free(vs->norm); free(vs->lut); }
 
-/* id of alpha +/- e_k; -1 if it leaves the set (negative or |alpha| > L) */
+/* id of alpha +/- e_k; -1 if it leaves the set (negative or |alpha| > L).
+ * A distinguished molecule's vector stays among the distinguished ids. */
 static int vec_shift(const vecset* vs, int id, int k, int dir) {
     unsigned char t[ORC_MAXM];
     memcpy(t, vs->comp + (size_t)id * vs->m, vs->m);
     int v = (int)t[k] + dir;
     if (v < 0 || v > vs->L) return -1;
     t[k] = (unsigned char)v;
-    return vs->lut[vec_code(t, vs->m, vs->L)];
+    int w = vs->lut[vec_code(t, vs->m, vs->L)];
+    if (w < 0) return -1;
+    return id >= vs->V ? vs->V + w : w;
 }
 
 /* ====================================================================== */
@@ -246,13 +257,21 @@ static void patgen_push(patgen* pg, const int* cur, int r, int tier) {
     pg->n += 1;
 }
 
-static void patgen_rec(patgen* pg, const vecset* vs, int* cur, int r, int tier, int start, int maxr) {
-    patgen_push(pg, cur, r, tier);
+/* extra >= 0: the distinguished molecule's id, appended to every multiset
+ * (it is the largest id, so the list stays ascending); its norm is already
+ * in tier */
+static void patgen_rec(patgen* pg, const vecset* vs, int* cur, int r, int tier, int start, int maxr, int extra) {
+    if (extra >= 0) {
+        cur[r] = extra;
+        patgen_push(pg, cur, r + 1, tier);
+    } else {
+        patgen_push(pg, cur, r, tier);
+    }
     if (r >= maxr) return;
     for (int v = start; v < vs->V; ++v) {
         if (tier + vs->norm[v] > vs->L) continue;
         cur[r] = v;
-        patgen_rec(pg, vs, cur, r + 1, tier + vs->norm[v], v, maxr);
+        patgen_rec(pg, vs, cur, r + 1, tier + vs->norm[v], v, maxr, extra);
     }
 }
 
@@ -284,18 +303,25 @@ static long long var_local(int G, int kind, int q, int r, int trank_q) {
 }
 
 orc_sa* orc_sa_create(const orc_params* p, int use_cache) {
-    if (p->N < 1 || p->m < 1 || p->m > ORC_MAXM || p->L < 0) return NULL;
+    if (p->N < 1 || p->m < 1 || p->m > ORC_MAXM || p->L < 0 || p->d < 0 || p->d > 1) return NULL;
     for (int k = 0; k < p->m; ++k)
         if (!(absck(p, k) > 0.0)) return NULL;
     orc_sa* s = (orc_sa*)calloc(1, sizeof(orc_sa));
     s->p = *p;
-    vecset_build(&s->vs, p->m, p->L);
-    /* patterns: at most N nonzero vectors, never more than L */
+    vecset_build(&s->vs, p->m, p->L, p->d);
+    /* patterns: at most N - d nonzero vectors of the undistinguished
+     * molecules, never more than L; with d = 1 the distinguished molecule's
+     * vector (zero included) is one more entry of every pattern */
     int maxr = p->L;
-    if ((long long)maxr > p->N) maxr = (int)p->N;
+    if ((long long)maxr > p->N - p->d) maxr = (int)(p->N - p->d);
     patgen pg; memset(&pg, 0, sizeof(pg));
     int cur[256];
-    patgen_rec(&pg, &s->vs, cur, 0, 0, 1, maxr);
+    if (p->d) {
+        for (int dv = 0; dv < s->vs.V; ++dv)
+            patgen_rec(&pg, &s->vs, cur, 0, s->vs.norm[dv], 1, maxr, s->vs.V + dv);
+    } else {
+        patgen_rec(&pg, &s->vs, cur, 0, 0, 1, maxr, -1);
+    }
     g_sort_ids = pg.buf;
     qsort(pg.refs, pg.n, sizeof(patref), patref_cmp);
     s->P = pg.n;
@@ -819,29 +845,54 @@ void orc_sa_rk4(const orc_sa* s, double* x, double dt, long long nsteps) {
  * out: Tr, P_cav, P_exc, P_B, P_D, P_+, P_-, Hermiticity defect of rho_S.
  */
 void orc_sa_observables(const orc_sa* s, const double* x, double* out) {
+    /* the physical density operator is the empty pattern (pattern 0): its
+     * categories are the zero category, and with d = 1 also the
+     * distinguished molecule's; rho_S entries follow from the variables and
+     * the multiplicities (Eqs. trace-uvar .. Pminus-uvar, written over the
+     * categories) */
     const orc_params* p = &s->p;
-    int G = s->G[0];   /* empty pattern: only the zero category */
+    int G = s->G[0];
+    const long long* M = s->cat_M + s->cat_off[0];
+    const int* tr = s->trank + s->cat_off[0];
     double N = (double)p->N;
     cplx Z = ld(x, var_local(G, K_Z, 0, 0, 0));
-    cplx X0 = ld(x, var_local(G, K_X, 1, 0, 0));
-    cplx Y0 = ld(x, var_local(G, K_Y, 1, 0, 0));
-    cplx P0 = ld(x, var_local(G, K_P, 1, 0, 0));
-    cplx T0 = s->h[0] > 0 ? ld(x, var_local(G, K_T, 1, 0, 0)) : 0;
+    cplx Pexc = 0, PBn = 0, XB = 0, YB = 0;
+    double hd = fabs(cimag(Z));
+    for (int q = 1; q <= G; ++q) {
+        double Mq = (double)M[q - 1];
+        cplx Xq = ld(x, var_local(G, K_X, q, 0, 0)), Yq = ld(x, var_local(G, K_Y, q, 0, 0));
+        cplx Pq = ld(x, var_local(G, K_P, q, 0, 0));
+        Pexc += Mq * Pq;
+        PBn += Mq * Pq;
+        XB += Mq * Xq;
+        YB += Mq * Yq;
+        if (fabs(cimag(Pq)) > hd) hd = fabs(cimag(Pq));
+        if (cabs(Xq - conj(Yq)) > hd) hd = cabs(Xq - conj(Yq));
+        if (M[q - 1] >= 2) {
+            cplx Tq = ld(x, var_local(G, K_T, q, 0, tr[q - 1]));
+            PBn += Mq * (Mq - 1.0) * Tq;
+            if (fabs(cimag(Tq)) > hd) hd = fabs(cimag(Tq));
+        }
+        for (int r = 1; r <= G; ++r) {
+            if (r == q) continue;
+            cplx Sqr = ld(x, var_local(G, K_S, q, r, 0)), Srq = ld(x, var_local(G, K_S, r, q, 0));
+            PBn += Mq * (double)M[r - 1] * Sqr;
+            if (cabs(Sqr - conj(Srq)) > hd) hd = cabs(Sqr - conj(Srq));
+        }
+    }
+    cplx PB = PBn / N;
+    XB /= sqrt(N);
+    YB /= sqrt(N);
     double omr = 2.0 * p->g * sqrt(N);
     double theta = 0.5 * atan2(omr, -p->detuning);
     double cs = cos(theta), sn = sin(theta);
-    cplx PB = P0 + (N - 1.0) * T0;
-    out[0] = creal(Z + N * P0);
+    out[0] = creal(Z + Pexc);
     out[1] = creal(Z);
-    out[2] = creal(N * P0);
+    out[2] = creal(Pexc);
     out[3] = creal(PB);
-    out[4] = creal((N - 1.0) * (P0 - T0));
-    out[5] = creal(Z * cs * cs + PB * sn * sn + sqrt(N) * sn * cs * (X0 + Y0));
-    out[6] = creal(Z * sn * sn + PB * cs * cs - sqrt(N) * sn * cs * (X0 + Y0));
-    double hd = fabs(cimag(Z));
-    if (fabs(cimag(P0)) > hd) hd = fabs(cimag(P0));
-    if (fabs(cimag(T0)) > hd) hd = fabs(cimag(T0));
-    if (cabs(X0 - conj(Y0)) > hd) hd = cabs(X0 - conj(Y0));
+    out[4] = creal(Pexc - PB);
+    out[5] = creal(Z * cs * cs + PB * sn * sn + sn * cs * (XB + YB));
+    out[6] = creal(Z * sn * sn + PB * cs * cs - sn * cs * (XB + YB));
     out[7] = hd;
 }
 
@@ -1022,8 +1073,9 @@ void orc_conv_rk4(const orc_conv* c, double* x, double dt, long long nsteps) {
 /*
  * For every entry (a, b) of every conventional ADO, the symmetry-adapted
  * variable that holds it: canonicalise the label (sort the molecules' local
- * vectors, Eq. pattern-one), then name the entry by the categories of the
- * molecules in its row and column (Eqs. Z-variable .. T-variable).
+ * vectors, Eq. pattern-one; with d = 1 molecule 1 keeps its own category),
+ * then name the entry by the categories of the molecules in its row and
+ * column (Eqs. Z-variable .. T-variable).
  * map has nado * (N+1)^2 entries; -1 if the canonical pattern is missing.
  */
 void orc_conv_to_sa(const orc_conv* c, const orc_sa* s, long long* map) {
@@ -1034,6 +1086,8 @@ void orc_conv_to_sa(const orc_conv* c, const orc_sa* s, long long* map) {
         int nk = 0, tier = 0;
         for (int i = 0; i < N; ++i) {
             vid[i] = s->vs.lut[vec_code(n + i * m, m, s->p.L)];
+            /* with d = 1, molecule 1 is the distinguished one: its own ids */
+            if (i == 0 && s->p.d) vid[i] += s->vs.V;
             if (vid[i] > 0) { key[nk++] = vid[i]; tier += s->vs.norm[vid[i]]; }
         }
         /* insertion sort: ascending id = vectors in canonical order */

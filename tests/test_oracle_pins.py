@@ -574,3 +574,110 @@ def test_terminator_strength(orc, K):
     kept = sum(4 * lam * gam * kT / ((2 * math.pi * j * kT) ** 2 - gam ** 2) for j in range(1, K + 1))
     assert abs(B.terminator(lam, gam, kT, K) - (full - kept)) < 1e-15
     assert B.terminator(lam, gam, kT, K + 1) < B.terminator(lam, gam, kT, K)
+
+
+# ---- one distinguished molecule (Sec. V.F: localised and cavity-site states;
+# the distinguished molecule keeps its own singleton category)
+
+def test_distinguished_counts_text(orc):
+    """Sec. V.F text, one distinguished molecule: 41391 patterns for N >= 26,
+    1715600 variables for N >= 28, 27.45 MB, 5.59 times the symmetric count."""
+    bath = {"c": np.array([0.1 + 0.0j]), "cc": np.array([0.1 + 0.0j]), "nu": np.array([1.0])}
+    base = orc.SA(27, 1, 25, bath, cache=False).nvar
+    seen = 0
+    for line in open(os.path.join(GOLD, "exact_counts.txt")):
+        if not line.strip() or line[0] == "#":
+            continue
+        kind, m, L, d, N, val = line.split()
+        if int(d) != 1:
+            continue
+        sa = orc.SA(int(N), int(m), int(L), bath, cache=False, d=1)
+        seen += 1
+        if kind == "patterns":
+            assert sa.npat == int(val)
+            assert orc.SA(int(N) - 1, int(m), int(L), bath, cache=False, d=1).npat < int(val)
+        elif kind == "variables":
+            assert sa.nvar == int(val)
+            assert orc.SA(int(N) - 1, int(m), int(L), bath, cache=False, d=1).nvar < int(val)
+        elif kind == "megabytes":
+            assert f"{16 * sa.nvar / 1e6:.2f}" == val
+        elif kind == "ratio":
+            assert f"{sa.nvar / base:.2f}" == val
+    assert seen == 4
+
+
+D_CASES = [(1, 1, 3), (2, 1, 3), (3, 1, 3), (3, 2, 3), (4, 1, 4), (4, 2, 2), (5, 1, 3), (2, 3, 2)]
+
+
+@pytest.mark.parametrize("N,m,L", D_CASES)
+def test_distinguished_sa_equals_conventional_rhs(orc, N, m, L):
+    """With molecule 1 distinguished, the reduced generator is still an exact
+    reduction of Eq. scaled-HEOM: every conventional entry maps to a variable,
+    every variable is some entry, and the right-hand sides agree for any
+    vector (loss and terminator on)."""
+    bath = _bath_generic(m, seed=N + m + L)
+    kw = dict(detuning=0.1, g=0.2, kappa=0.05, term=0.01)
+    sa = orc.SA(N, m, L, bath, d=1, **kw)
+    cv = orc.Conventional(N, m, L, bath, **kw)
+    mp = cv.map_to(sa)
+    assert (mp >= 0).all() and set(np.unique(mp)) == set(range(sa.nvar))
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(sa.nvar) + 1j * rng.standard_normal(sa.nvar)
+    dcv, dsa = cv.rhs(x[mp]), sa.rhs(x)
+    assert np.abs(dcv - dsa[mp]).max() <= 1e-13 * np.abs(dcv).max()
+    assert orc.errors() == 0
+
+
+@pytest.mark.parametrize("N", [2, 3, 5])
+def test_distinguished_localised_propagation(orc, N):
+    """rho_S(0) = |e_1><e_1| (Eq. localized_initial_condition) is not
+    permutation-invariant, so it needs the distinguished molecule: RK4 on both
+    hierarchies agrees to rounding, and the observables follow the dense
+    reduced density matrix."""
+    import oracle.bath as B
+
+    bath = B.high_t(0.01, 0.05, 0.025)
+    kw = dict(detuning=0.0, g=0.05 / np.sqrt(N), kappa=0.0)
+    sa = orc.SA(N, 1, 4, bath, d=1, **kw)
+    cv = orc.Conventional(N, 1, 4, bath, **kw)
+    mp = cv.map_to(sa)
+    rho = np.zeros((N + 1, N + 1), complex)
+    rho[1, 1] = 1.0
+    x = sa.initial_state_dense(rho)
+    xc = cv.zeros()
+    xc[0] = rho
+    assert np.array_equal(x[mp[0]], rho)
+    ys = sa.rk4(x, 0.05, 200)
+    yc = cv.rk4(xc, 0.05, 200)
+    assert np.abs(yc - ys[mp]).max() <= 1e-12
+    # populations from the dense rho_S of the conventional run
+    r = yc[0]
+    obs = sa.observables(ys)
+    Bv = np.concatenate([[0], np.ones(N) / np.sqrt(N)])
+    assert abs(obs[0] - np.trace(r).real) < 1e-12
+    assert abs(obs[1] - r[0, 0].real) < 1e-12
+    assert abs(obs[3] - (Bv @ r @ Bv).real) < 1e-12
+
+
+@pytest.mark.parametrize("N", [2, 5, 10, 100, 10 ** 12])
+def test_distinguished_initial_tc_populations(orc, N):
+    """Resonant initial TC populations of Sec. V.F: the localised state has
+    P_+ = P_- = 1/(2N), P_D = 1 - 1/N; the cavity-site superposition
+    sqrt(0.3)|e_1> + sqrt(0.7)|c> has P_D = 0.3 (1 - 1/N) and
+    P_+- = (sqrt(0.7) +- sqrt(0.3/N))^2 / 2."""
+    import oracle.bath as B
+
+    sa = orc.SA(N, 1, 2, B.high_t(0.01, 0.05, 0.025), 0.0, 0.05 / np.sqrt(N), 0.0, d=1)
+    ix = sa.rho0_index()
+    x = sa.zeros()
+    x[ix["Pd"]] = 1.0
+    o = sa.observables(x)
+    assert abs(o[5] - 1 / (2 * N)) < 1e-13 and abs(o[6] - 1 / (2 * N)) < 1e-13
+    assert abs(o[4] - (1 - 1 / N)) < 1e-13 and abs(o[0] - 1) < 1e-15
+    x = sa.zeros()
+    x[ix["Pd"]], x[ix["Z"]] = 0.3, 0.7
+    x[ix["Xd"]] = x[ix["Yd"]] = np.sqrt(0.21)
+    o = sa.observables(x)
+    assert abs(o[4] - 0.3 * (1 - 1 / N)) < 1e-13
+    assert abs(o[5] - 0.5 * (np.sqrt(0.7) + np.sqrt(0.3 / N)) ** 2) < 1e-13
+    assert abs(o[6] - 0.5 * (np.sqrt(0.7) - np.sqrt(0.3 / N)) ** 2) < 1e-13
