@@ -57,7 +57,8 @@ extern "C" {
 
 enum {
     SA_OK = 0,
-    SA_ERR_INVALID_ARG = -1, /* N < 1, m outside 1..8, L outside 0..30, |c_k| = 0, non-finite input */
+    SA_ERR_INVALID_ARG = -1, /* N < 1, m outside 1..8, L outside 0..30, d outside 0..1, |c_k| = 0,
+                                non-finite input */
     SA_ERR_UNSUPPORTED = -2, /* size beyond the 32-bit table indices, missing device */
     SA_ERR_OOM = -3,         /* host or device allocation failed */
     SA_ERR_CUDA = -4,        /* a CUDA runtime call failed; see sa_heom_last_error() */
@@ -85,6 +86,16 @@ enum { SA_BATH_HIGH_T = 0, SA_BATH_MATSUBARA = 1, SA_BATH_PADE = 2 };
  *              ADO, i.e. -Delta w V per unique variable with w = 0 for Z and
  *              P, 1 for X and Y, 2 for S and T.  sa_bath_terminator gives
  *              Delta for the Matsubara scheme.
+ *   d          distinguished molecules, 0 or 1.  With d = 1 molecule 1 is
+ *              kept out of the permutation symmetry (Sec. V.F: the localised
+ *              state |e_1><e_1| and cavity-site superpositions): its local
+ *              vector is stored with the pattern as vector id V + v (ids
+ *              V .. 2V-1, V = n_vectors), so it always forms a category of
+ *              its own with M = 1, listed after the other nonzero vectors
+ *              and before the zero category (M = N - r, r counting molecule
+ *              1).  The other N - 1 molecules are symmetrised as with d = 0.
+ *              Set the initial state with sa_heom_init_physical.
+ *   reserved   must be 0.
  */
 typedef struct sa_params {
     int64_t N;
@@ -97,6 +108,8 @@ typedef struct sa_params {
     double cc_re[SA_HEOM_MAXM], cc_im[SA_HEOM_MAXM];
     double nu_re[SA_HEOM_MAXM], nu_im[SA_HEOM_MAXM];
     double term;
+    int32_t d;
+    int32_t reserved;
 } sa_params;
 
 /* Sizes of one instance or of a whole batch. */
@@ -248,9 +261,24 @@ int sa_heom_state_bytes(const sa_heom* h, size_t* bytes);
  * initial-zero/higher): every ADO zero except the physical representative,
  * set per instance from rho0[10 * i ..]: Z, X_0, Y_0, P_0, T_0 as (re, im)
  * pairs (T_0 ignored for N = 1).  d_state: caller-owned device buffer of
- * sa_heom_state_bytes bytes.  Asynchronous on `stream`.
+ * sa_heom_state_bytes bytes.  SA_ERR_INVALID_ARG for a batch with a d = 1
+ * instance.  Asynchronous on `stream`.
  */
 int sa_heom_init_state(const sa_heom* h, const double* rho0, void* d_state, void* stream);
+
+/*
+ * sa_heom_init_physical -- the same factorised initial hierarchy with the
+ * physical representative (the tier-0 pattern, whose variables are rho_S
+ * written over its categories) given variable by variable in the canonical
+ * layout: Z, X_1..X_G, Y_1..Y_G, P_1..P_G, S_{q,r} row-major (r != q), then
+ * T.  phys[32 * i ..] holds instance i's values as (re, im) pairs; only the
+ * first n of them are read, n = the pattern's variable count (5 for d = 0,
+ * N >= 2; 10 for d = 1, N >= 3, where category 1 is molecule 1 and category
+ * 2 the other N - 1 molecules).  Needed for d = 1 (sa_heom_init_state
+ * returns SA_ERR_INVALID_ARG for such instances); valid for every instance.
+ * The values are not checked for Hermiticity.  Asynchronous on `stream`.
+ */
+int sa_heom_init_physical(const sa_heom* h, const double* phys, void* d_state, void* stream);
 
 /*
  * sa_heom_state_upload / sa_heom_state_download -- copy a full state between

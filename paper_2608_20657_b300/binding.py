@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
         ("c_re", ctypes.c_double * MAXM), ("c_im", ctypes.c_double * MAXM),
         ("cc_re", ctypes.c_double * MAXM), ("cc_im", ctypes.c_double * MAXM),
         ("nu_re", ctypes.c_double * MAXM), ("nu_im", ctypes.c_double * MAXM),
-        ("term", ctypes.c_double),
+        ("term", ctypes.c_double), ("d", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
     def bath(self) -> dict:
@@ -84,6 +84,7 @@ def lib() -> ctypes.CDLL:
             "sa_heom_dump_terms": [vp, i32, vp, vp, vp, vp, vp, vp],
             "sa_heom_state_bytes": [vp, P(ctypes.c_size_t)],
             "sa_heom_init_state": [vp, vp, vp, vp],
+            "sa_heom_init_physical": [vp, vp, vp, vp],
             "sa_heom_state_upload": [vp, vp, vp, vp],
             "sa_heom_state_download": [vp, vp, vp, vp],
             "sa_heom_rhs": [vp, vp, vp, vp],
@@ -128,7 +129,8 @@ def lib() -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     return ["sa_bath_drude_lorentz", "sa_bath_terminator", "sa_heom_counts", "sa_heom_build", "sa_heom_destroy", "sa_heom_info",
             "sa_heom_var_offset", "sa_heom_dump_vectors", "sa_heom_dump_patterns", "sa_heom_dump_categories",
-            "sa_heom_dump_terms", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_state_upload",
+            "sa_heom_dump_terms", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_init_physical",
+            "sa_heom_state_upload",
             "sa_heom_state_download", "sa_heom_rhs", "sa_heom_step", "sa_heom_propagate", "sa_heom_observables",
             "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_set_kernel", "sa_heom_get_tuning", "sa_heom_prepare", "sa_heom_dump_lists", "sa_heom_dump_ell",
             "sa_heom_launches_per_step", "sa_heom_device_error",
@@ -159,9 +161,10 @@ def _stream(stream) -> ctypes.c_void_p:
     return ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
 
 
-def make_params(N, m=None, L=0, bath=None, detuning=0.0, g=0.0, kappa=0.0, term=0.0) -> Params:
+def make_params(N, m=None, L=0, bath=None, detuning=0.0, g=0.0, kappa=0.0, term=0.0, d=0) -> Params:
     """sa_params from a bath dict {c, cc, nu} (complex arrays of length m);
-    term: terminator strength Delta (0: off, see bath_terminator)."""
+    term: terminator strength Delta (0: off, see bath_terminator); d: 1 keeps
+    molecule 1 out of the permutation symmetry."""
     p = Params()
     c = np.asarray(bath["c"], complex)
     cc = np.asarray(bath["cc"], complex)
@@ -169,6 +172,7 @@ def make_params(N, m=None, L=0, bath=None, detuning=0.0, g=0.0, kappa=0.0, term=
     m = len(c) if m is None else m
     p.N, p.m, p.L = int(N), int(m), int(L)
     p.detuning, p.g, p.kappa, p.term = float(detuning), float(g), float(kappa), float(term)
+    p.d = int(d)
     for k in range(m):
         p.c_re[k], p.c_im[k] = c[k].real, c[k].imag
         p.cc_re[k], p.cc_im[k] = cc[k].real, cc[k].imag
@@ -282,6 +286,17 @@ class Heom:
         r[:] = np.asarray(rho0, complex).reshape(-1, 5) if np.ndim(rho0) > 1 else np.asarray(rho0, complex)
         flat = np.ascontiguousarray(r.view(np.float64).reshape(-1))
         _check(lib().sa_heom_init_state(self._h, _ptr(flat), _dev(state), _stream(stream)), "sa_heom_init_state")
+
+    def init_physical(self, state, phys, stream=None):
+        """phys: (count, n) complex, n <= 16: each instance's physical
+        representative in the canonical layout (Z, X_q, Y_q, P_q, S_qr, T)."""
+        ph = np.asarray(phys, complex)
+        ph = ph.reshape(self.count, -1) if ph.ndim > 1 else ph.reshape(1, -1)
+        assert ph.shape[1] <= 16
+        r = np.zeros((self.count, 16), complex)
+        r[:, :ph.shape[1]] = ph
+        flat = np.ascontiguousarray(r.view(np.float64).reshape(-1))
+        _check(lib().sa_heom_init_physical(self._h, _ptr(flat), _dev(state), _stream(stream)), "sa_heom_init_physical")
 
     def upload(self, state, x: np.ndarray, stream=None):
         x = np.ascontiguousarray(x, np.complex128)

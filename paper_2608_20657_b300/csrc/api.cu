@@ -18,10 +18,11 @@ namespace sa {
 cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, cudaStream_t st);
 cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm);
 void list_operand_layout(int item, int* opR, int* opC, int* opZ, int* opZero);
-cudaError_t launch_observables(const InstDev* inst, const double* theta, int ninst, const void* main64,
-                               const void* side64, double* out, cudaStream_t st);
-cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0, void* main64, void* main32,
-                             void* side64, cudaStream_t st);
+cudaError_t launch_observables(const InstDev* inst, const double* theta, int ninst, const PatHdr* hdr,
+                               const double* catMd, const uint32_t* cat_word, const void* main64, const void* side64,
+                               double* out, cudaStream_t st);
+cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0, int stride, void* main64,
+                             void* main32, void* side64, cudaStream_t st);
 }  // namespace sa
 
 using namespace sa;
@@ -761,6 +762,14 @@ void* side(const sa_heom* h, const void* buf) {
     return static_cast<char*>(const_cast<void*>(buf)) + h->side_off;
 }
 
+// observables of every instance's physical representative into d_out
+cudaError_t observables_into(const sa_heom* h, const void* d_state, double* d_out, cudaStream_t st) {
+    return launch_observables(static_cast<const InstDev*>(h->d_inst), static_cast<const double*>(h->d_theta),
+                              h->count, static_cast<const PatHdr*>(h->d_hdr), static_cast<const double*>(h->d_catMd),
+                              static_cast<const uint32_t*>(h->d_cat_word), h->precision == SA_FP64 ? d_state : nullptr,
+                              side(h, d_state), d_out, st);
+}
+
 // The four fused RK4 stage launches of one step; slot: first queue counter.
 int enqueue_step(sa_heom* h, void* y, double dt, size_t slot, cudaStream_t st) {
     void* acc = h->d_work[0];
@@ -964,7 +973,11 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
         D.coef_base = uint32_t(i) * kCoefPerInst;
         D.side = uint32_t(i) * kSideSlots;
         D.var_begin = vb;
-        D.n_rho0 = hi.N >= 2 ? 5u : 4u;
+        D.n_rho0 = uint32_t(hi.var_off[1] - hi.var_off[0]);
+        if (D.n_rho0 > uint32_t(kSideSlots)) {
+            delete h;
+            return fail(SA_ERR_UNSUPPORTED, "physical representative larger than its FP64 side slots");
+        }
         D.pat_begin = uint32_t(pbase);
         h->theta[i] = 0.5 * std::atan2(2.0 * hi.p.g * std::sqrt(double(hi.N)), -hi.p.detuning);
         std::copy(hi.coef_row.begin(), hi.coef_row.end(), h->coef_row_d.begin() + size_t(2) * kCoefPerInst * i);
@@ -1037,7 +1050,7 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
         }
     }
     if (!rc) {
-        e = cudaMalloc(&h->d_rho0, sizeof(double) * 10 * count);
+        e = cudaMalloc(&h->d_rho0, sizeof(double) * 2 * kSideSlots * count);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(rho0)");
     }
     if (!rc) rc = ensure_queue(h, 64);
@@ -1122,7 +1135,7 @@ int sa_heom_var_offset(const sa_heom* h, int inst, int64_t* out) {
 int sa_heom_dump_vectors(const sa_heom* h, int inst, uint8_t* comp) {
     if (!h || inst < 0 || inst >= h->count || !comp) return fail(SA_ERR_INVALID_ARG, "handle, instance, out");
     const HostInstance& hi = h->inst[inst];
-    std::memcpy(comp, hi.comp.data(), hi.comp.size());
+    std::memcpy(comp, hi.comp.data(), size_t(hi.V) * hi.m);
     return SA_OK;
 }
 
@@ -1212,22 +1225,49 @@ int sa_heom_state_bytes(const sa_heom* h, size_t* bytes) {
     return SA_OK;
 }
 
+// zero the state and write the physical representative of every instance
+// from rho0 (stride doubles per instance, n_rho0 (re, im) pairs each)
+static int init_from(sa_heom* h, const double* rho0, int stride, void* d_state, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<double> buf(size_t(2) * kSideSlots * h->count, 0.0);
+    for (int i = 0; i < h->count; ++i)
+        for (uint32_t j = 0; j < 2 * h->instdev[i].n_rho0; ++j) {
+            const double v = rho0[size_t(stride) * i + j];
+            if (!std::isfinite(v)) return fail(SA_ERR_INVALID_ARG, "non-finite initial value");
+            buf[size_t(2) * kSideSlots * i + j] = v;
+        }
+    CK(cudaMemsetAsync(d_state, 0, h->state_bytes, st));
+    CK(cudaMemcpyAsync(h->d_rho0, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, st));
+    // a copy from pageable memory returns once the source has been staged,
+    // so the vector may die on return
+    const int s = 2 * kSideSlots;
+    if (h->precision == SA_FP64)
+        CK(launch_init_rho0(static_cast<const InstDev*>(h->d_inst), h->count, h->d_rho0, s, d_state, nullptr, nullptr,
+                            st));
+    else
+        CK(launch_init_rho0(static_cast<const InstDev*>(h->d_inst), h->count, h->d_rho0, s, nullptr, d_state,
+                            side(h, d_state), st));
+    return SA_OK;
+}
+
 int sa_heom_init_state(const sa_heom* hc, const double* rho0, void* d_state, void* stream) {
     sa_heom* h = const_cast<sa_heom*>(hc);
     int rc = check_device(h);
     if (rc) return rc;
     if (!rho0 || !d_state) return fail(SA_ERR_INVALID_ARG, "rho0 and d_state required");
-    for (int i = 0; i < 10 * h->count; ++i)
-        if (!std::isfinite(rho0[i])) return fail(SA_ERR_INVALID_ARG, "non-finite rho0");
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CK(cudaMemsetAsync(d_state, 0, h->state_bytes, st));
-    CK(cudaMemcpyAsync(h->d_rho0, rho0, sizeof(double) * 10 * h->count, cudaMemcpyHostToDevice, st));
-    if (h->precision == SA_FP64)
-        CK(launch_init_rho0(static_cast<const InstDev*>(h->d_inst), h->count, h->d_rho0, d_state, nullptr, nullptr, st));
-    else
-        CK(launch_init_rho0(static_cast<const InstDev*>(h->d_inst), h->count, h->d_rho0, nullptr, d_state,
-                            side(h, d_state), st));
-    return SA_OK;
+    for (int i = 0; i < h->count; ++i)
+        if (h->inst[i].d)
+            return fail(SA_ERR_INVALID_ARG,
+                        "instance " + std::to_string(i) + " has a distinguished molecule: use sa_heom_init_physical");
+    return init_from(h, rho0, 10, d_state, stream);
+}
+
+int sa_heom_init_physical(const sa_heom* hc, const double* phys, void* d_state, void* stream) {
+    sa_heom* h = const_cast<sa_heom*>(hc);
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!phys || !d_state) return fail(SA_ERR_INVALID_ARG, "phys and d_state required");
+    return init_from(h, phys, 2 * kSideSlots, d_state, stream);
 }
 
 int sa_heom_state_upload(const sa_heom* h, const double* host_x, void* d_state, void* stream) {
@@ -1398,17 +1438,13 @@ int sa_heom_propagate(sa_heom* h, void* d_state, double dt, int64_t nsteps, int6
         CK(cudaMalloc(&h->d_obs, need * sizeof(double)));
         h->obs_cap = need;
     }
-    const void* m64 = h->precision == SA_FP64 ? d_state : nullptr;
-    const void* s64 = side(h, d_state);
-    const InstDev* di = static_cast<const InstDev*>(h->d_inst);
-    const double* th = static_cast<const double*>(h->d_theta);
-    CK(launch_observables(di, th, h->count, m64, s64, h->d_obs, st));
+    CK(observables_into(h, d_state, h->d_obs, st));
     int64_t done = 0, row = 1;
     while (done < nsteps) {
         int64_t n = std::min(obs_every, nsteps - done);
         rc = run_steps(h, d_state, dt, n, st);
         if (rc) return rc;
-        CK(launch_observables(di, th, h->count, m64, s64, h->d_obs + size_t(row) * h->count * 8, st));
+        CK(observables_into(h, d_state, h->d_obs + size_t(row) * h->count * 8, st));
         done += n;
         ++row;
     }
@@ -1433,8 +1469,7 @@ int sa_heom_observables(sa_heom* h, const void* d_state, double* out, void* stre
         CK(cudaMalloc(&h->d_obs, need * sizeof(double)));
         h->obs_cap = need;
     }
-    CK(launch_observables(static_cast<const InstDev*>(h->d_inst), static_cast<const double*>(h->d_theta), h->count,
-                          h->precision == SA_FP64 ? d_state : nullptr, side(h, d_state), h->d_obs, st));
+    CK(observables_into(h, d_state, h->d_obs, st));
     CK(cudaMemcpyAsync(out, h->d_obs, need * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     for (size_t j = 0; j < need; ++j)
@@ -1599,8 +1634,7 @@ extern "C" int sa_heom_observables_noalloc(sa_heom* h, const void* d_state, doub
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the kernel writes all 8 * count slots it is read back from, so nothing
     // left from an earlier call needs clearing
-    CK(launch_observables(static_cast<const InstDev*>(h->d_inst), static_cast<const double*>(h->d_theta), h->count,
-                          h->precision == SA_FP64 ? d_state : nullptr, side(h, d_state), scratch, st));
+    CK(observables_into(h, d_state, scratch, st));
     const size_t need = size_t(h->count) * 8;
     CK(cudaMemcpyAsync(out, scratch, need * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));

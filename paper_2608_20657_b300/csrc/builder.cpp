@@ -75,13 +75,19 @@ void build_vectors(HostInstance& hi) {
     std::sort(vecs.begin(), vecs.end(),
               [m](const std::vector<uint8_t>& a, const std::vector<uint8_t>& b) { return vec_before(a.data(), b.data(), m); });
     hi.V = int(vecs.size()) + 1;
-    hi.comp.assign(size_t(hi.V) * m, 0);
-    hi.norm.assign(hi.V, 0);
+    hi.Vtot = hi.d ? 2 * hi.V : hi.V;
+    hi.comp.assign(size_t(hi.Vtot) * m, 0);
+    hi.norm.assign(hi.Vtot, 0);
     for (int v = 1; v < hi.V; ++v) {
         for (int k = 0; k < m; ++k) {
             hi.comp[size_t(v) * m + k] = vecs[v - 1][k];
             hi.norm[v] += vecs[v - 1][k];
         }
+    }
+    // the distinguished molecule's copies, zero vector included
+    for (int v = hi.V; v < hi.Vtot; ++v) {
+        std::memcpy(&hi.comp[size_t(v) * m], &hi.comp[size_t(v - hi.V) * m], m);
+        hi.norm[v] = hi.norm[v - hi.V];
     }
     int64_t total = 1;
     for (int k = 0; k < m; ++k) total *= (L + 1);
@@ -89,13 +95,16 @@ void build_vectors(HostInstance& hi) {
     for (int v = 0; v < hi.V; ++v) hi.lut[vcode(&hi.comp[size_t(v) * m], m, L)] = v;
 }
 
+// id of alpha +/- e_k, -1 outside the set; molecule 1's vectors stay among
+// its own ids
 int shift_vec(const HostInstance& hi, int id, int k, int dir) {
     uint8_t t[SA_HEOM_MAXM];
     std::memcpy(t, &hi.comp[size_t(id) * hi.m], hi.m);
     int v = int(t[k]) + dir;
     if (v < 0 || v > hi.L) return -1;
     t[k] = uint8_t(v);
-    return hi.lut[vcode(t, hi.m, hi.L)];
+    const int w = hi.lut[vcode(t, hi.m, hi.L)];
+    return (w >= 0 && id >= hi.V) ? hi.V + w : w;
 }
 
 // ---- pattern enumeration ---------------------------------------------------
@@ -163,8 +172,9 @@ struct PatMap {
 }  // namespace
 
 int build_instance(const sa_params& p, HostInstance& hi, std::string& err) {
-    if (p.N < 1 || p.m < 1 || p.m > SA_HEOM_MAXM || p.L < 0 || p.L > SA_HEOM_MAXL) {
-        err = "N >= 1, 1 <= m <= 8, 0 <= L <= 30 required";
+    if (p.N < 1 || p.m < 1 || p.m > SA_HEOM_MAXM || p.L < 0 || p.L > SA_HEOM_MAXL || p.d < 0 || p.d > 1 ||
+        p.reserved != 0) {
+        err = "N >= 1, 1 <= m <= 8, 0 <= L <= 30, d in {0, 1}, reserved = 0 required";
         return SA_ERR_INVALID_ARG;
     }
     const double scal[4] = {p.detuning, p.g, p.kappa, p.term};
@@ -190,11 +200,13 @@ int build_instance(const sa_params& p, HostInstance& hi, std::string& err) {
     hi.m = p.m;
     hi.L = p.L;
     hi.N = p.N;
+    hi.d = p.d;
     const int m = hi.m, L = hi.L;
     build_vectors(hi);
 
-    // patterns, tier by tier, each tier in canonical (lexicographic) order
-    Enum en{hi, {}, int(std::min<int64_t>(L, p.N)), {}};
+    // patterns, tier by tier, each tier in canonical (lexicographic) order:
+    // at most N - d nonzero vectors of the symmetrised molecules
+    Enum en{hi, {}, int(std::min<int64_t>(L, p.N - p.d)), {}};
     en.first_with_norm_le.assign(L + 1, hi.V);
     for (int n = 0; n <= L; ++n) {
         for (int v = 1; v < hi.V; ++v)
@@ -204,7 +216,43 @@ int build_instance(const sa_params& p, HostInstance& hi, std::string& err) {
             }
     }
     hi.id_off.push_back(0);
-    for (int t = 0; t <= L; ++t) en.dfs(1, t, t);
+    if (!hi.d) {
+        for (int t = 0; t <= L; ++t) en.dfs(1, t, t);
+    } else {
+        // molecule 1's id (V + v, above every other id) closes each list;
+        // the lists of one tier are then sorted lexicographically
+        std::vector<uint32_t> all_ids, scratch_off{0};
+        std::vector<uint8_t> all_tier;
+        for (int t = 0; t <= L; ++t) {
+            const size_t first = all_tier.size();
+            for (int dv = 0; dv < hi.V; ++dv) {
+                if (hi.norm[dv] > t) continue;
+                const size_t before = hi.tier.size();
+                en.dfs(1, t - hi.norm[dv], t);
+                // dfs appended to hi.ids / id_off / tier: move them out, with dv
+                for (size_t j = before; j < hi.tier.size(); ++j) {
+                    all_ids.insert(all_ids.end(), hi.ids.begin() + hi.id_off[j], hi.ids.begin() + hi.id_off[j + 1]);
+                    all_ids.push_back(uint32_t(hi.V + dv));
+                    scratch_off.push_back(uint32_t(all_ids.size()));
+                    all_tier.push_back(uint8_t(t));
+                }
+                hi.ids.resize(hi.id_off[before]);
+                hi.id_off.resize(before + 1);
+                hi.tier.resize(before);
+            }
+            std::vector<size_t> ord(all_tier.size() - first);
+            for (size_t j = 0; j < ord.size(); ++j) ord[j] = first + j;
+            std::sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
+                return std::lexicographical_compare(all_ids.begin() + scratch_off[a], all_ids.begin() + scratch_off[a + 1],
+                                                    all_ids.begin() + scratch_off[b], all_ids.begin() + scratch_off[b + 1]);
+            });
+            for (size_t j : ord) {
+                hi.ids.insert(hi.ids.end(), all_ids.begin() + scratch_off[j], all_ids.begin() + scratch_off[j + 1]);
+                hi.id_off.push_back(uint32_t(hi.ids.size()));
+                hi.tier.push_back(uint8_t(t));
+            }
+        }
+    }
     hi.P = int64_t(hi.tier.size());
 
     // categories, multiplicities, layout, damping

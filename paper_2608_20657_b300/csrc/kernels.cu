@@ -938,6 +938,7 @@ __global__ void __launch_bounds__(256) ell_stage_kernel(StageParams<T> P) {
     }
 }
 
+// -- begin: physical-representative kernels (outside the stage kernels' code)
 // SA_FP32_AUX: the physical representative (empty pattern) of every instance
 // in FP64, one thread per variable: FP64 side copies of its own variables,
 // the tier-1 targets gathered from the FP32 stage input, FP64 coefficients and
@@ -951,17 +952,26 @@ __global__ void __launch_bounds__(128) rho0_kernel(StageParams<T> P, int ninst) 
     if (i >= ninst) return;
     const InstDev I = P.inst[i];
     if (uint32_t(loc) >= I.n_rho0) return;
-    // the empty pattern is the instance's first pattern: G = 1, one category
+    // the physical representative is the instance's first pattern: the zero
+    // category (G = 1), or molecule 1's category and the zero category
     const uint32_t p = I.pat_begin;
     const PatHdr h = P.hdr[p];
     const int G = h.G;
-    int kind, q = 1, r = 0;
-    if (loc == 0) kind = KZ;
-    else if (loc == 1) kind = KX;
-    else if (loc == 2) kind = KY;
-    else if (loc == 3) kind = KP;
-    else kind = KT;
-    if (kind == KZ) q = 0;
+    const int nsq = (G + 1) * (G + 1);
+    int kind, q = 0, r = 0;
+    if (loc < nsq) {
+        const uint32_t e = P.lut[P.lut_off[G] + loc];
+        kind = int(e & 7u);
+        q = int((e >> 3) & 31u);
+        r = int((e >> 8) & 31u);
+    } else {
+        // T variable of T-rank loc - (G+1)^2
+        kind = KT;
+        for (int a = 1; a <= G; ++a)
+            if (P.cat_Md[h.cat_off + a - 1] >= 2.0 && int((P.cat_word[h.cat_off + a - 1] >> 15) & 31u) == loc - nsq)
+                q = a;
+        if (q == 0) return;  // no category of that T-rank (the host tables rule it out)
+    }
     const double2* xsin = P.xs_in + I.side;
     auto own = [&](int ii) { return xsin[ii]; };
     auto gath = [&](uint32_t ii) { const C t = __ldg(P.x_in + ii); return make_double2(t.x, t.y); };
@@ -997,50 +1007,77 @@ __global__ void __launch_bounds__(128) rho0_kernel(StageParams<T> P, int ninst) 
 }
 
 // Observables of the physical representative of every instance
-// (Eqs. trace-uvar .. Pminus-uvar) plus the Hermiticity defect of rho_S.
+// (Eqs. trace-uvar .. Pminus-uvar, written over its categories q with
+// multiplicities M_q: P_exc = sum M_q P_q, P_B = [sum M_q P_q + sum M_q
+// (M_q - 1) T_q + sum_{q != r} M_q M_r S_qr] / N, <B|rho|c> = sum M_q X_q /
+// sqrt N) plus the Hermiticity defect of rho_S.
 __global__ void observables_kernel(const InstDev* __restrict__ inst, const double* __restrict__ theta, int ninst,
-                                   const double2* __restrict__ main64, const double2* __restrict__ side64,
-                                   double* __restrict__ out) {
+                                   const PatHdr* __restrict__ hdr, const double* __restrict__ catMd,
+                                   const uint32_t* __restrict__ cat_word, const double2* __restrict__ main64,
+                                   const double2* __restrict__ side64, double* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ninst) return;
     const InstDev I = inst[i];
     const double2* v = side64 ? side64 + I.side : main64 + I.var_begin;
-    const double2 Z = v[0], X0 = v[1], Y0 = v[2], P0 = v[3];
-    const double2 T0 = I.n_rho0 > 4 ? v[4] : make_double2(0.0, 0.0);
+    const PatHdr h = hdr[I.pat_begin];
+    const int G = h.G;
+    const double* M = catMd + h.cat_off;
+    const uint32_t* cw = cat_word + h.cat_off;
+    const double2 Z = v[0];
+    double Pexc = 0.0, PBn = 0.0, XY = 0.0;
+    double hd = fabs(Z.y);
+    for (int q = 1; q <= G; ++q) {
+        const double Mq = M[q - 1];
+        const double2 Xq = v[q], Yq = v[G + q], Pq = v[2 * G + q];
+        Pexc += Mq * Pq.x;
+        PBn += Mq * Pq.x;
+        XY += Mq * (Xq.x + Yq.x);
+        hd = fmax(hd, fabs(Pq.y));
+        hd = fmax(hd, hypot(Xq.x - Yq.x, Xq.y + Yq.y));
+        if (Mq >= 2.0) {
+            const double2 Tq = v[(G + 1) * (G + 1) + int((cw[q - 1] >> 15) & 31u)];
+            PBn += Mq * (Mq - 1.0) * Tq.x;
+            hd = fmax(hd, fabs(Tq.y));
+        }
+        for (int r = 1; r <= G; ++r) {
+            if (r == q) continue;
+            const double2 Sqr = v[loc_S_d(G, q, r)], Srq = v[loc_S_d(G, r, q)];
+            PBn += Mq * M[r - 1] * Sqr.x;
+            hd = fmax(hd, hypot(Sqr.x - Srq.x, Sqr.y + Srq.y));
+        }
+    }
     const double N = I.N;
+    const double PB = PBn / N;
     const double th = theta[i];
     const double cs = cos(th), sn = sin(th);
-    const double PBr = P0.x + (N - 1.0) * T0.x;
-    const double sq = sqrt(N) * sn * cs;
+    const double xy = sn * cs * (XY / sqrt(N));
     double* o = out + 8 * i;
-    o[0] = Z.x + N * P0.x;
+    o[0] = Z.x + Pexc;
     o[1] = Z.x;
-    o[2] = N * P0.x;
-    o[3] = PBr;
-    o[4] = (N - 1.0) * (P0.x - T0.x);
-    o[5] = Z.x * cs * cs + PBr * sn * sn + sq * (X0.x + Y0.x);
-    o[6] = Z.x * sn * sn + PBr * cs * cs - sq * (X0.x + Y0.x);
-    double hd = fabs(Z.y);
-    hd = fmax(hd, fabs(P0.y));
-    hd = fmax(hd, fabs(T0.y));
-    hd = fmax(hd, hypot(X0.x - Y0.x, X0.y + Y0.y));
+    o[2] = Pexc;
+    o[3] = PB;
+    o[4] = Pexc - PB;
+    o[5] = Z.x * cs * cs + PB * sn * sn + xy;
+    o[6] = Z.x * sn * sn + PB * cs * cs - xy;
     o[7] = hd;
 }
 
 // Factorised initial state: write rho_0 of every instance (zeroing is a memset).
 __global__ void init_rho0_kernel(const InstDev* __restrict__ inst, int ninst, const double* __restrict__ rho0,
-                                 double2* __restrict__ main64, float2* __restrict__ main32,
+                                 int stride, double2* __restrict__ main64, float2* __restrict__ main32,
                                  double2* __restrict__ side64) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ninst) return;
     const InstDev I = inst[i];
     for (uint32_t j = 0; j < I.n_rho0; ++j) {
-        const double re = rho0[10 * i + 2 * j], im = rho0[10 * i + 2 * j + 1];
+        const double re = rho0[size_t(stride) * i + 2 * j], im = rho0[size_t(stride) * i + 2 * j + 1];
         if (main64) main64[I.var_begin + j] = make_double2(re, im);
         if (main32) main32[I.var_begin + j] = make_float2(float(re), float(im));
         if (side64) side64[I.side + j] = make_double2(re, im);
     }
 }
+
+// -- end: physical-representative kernels
 
 // ---- host launch wrappers (called from api.cu) -----------------------------
 
@@ -1194,18 +1231,23 @@ cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm)
     return occupancy_of(stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
 }
 
-cudaError_t launch_observables(const InstDev* inst, const double* theta, int ninst, const void* main64,
-                               const void* side64, double* out, cudaStream_t st) {
-    observables_kernel<<<(ninst + 127) / 128, 128, 0, st>>>(inst, theta, ninst, static_cast<const double2*>(main64),
+// -- begin: physical-representative kernels (outside the stage kernels' code)
+cudaError_t launch_observables(const InstDev* inst, const double* theta, int ninst, const PatHdr* hdr,
+                               const double* catMd, const uint32_t* cat_word, const void* main64, const void* side64,
+                               double* out, cudaStream_t st) {
+    observables_kernel<<<(ninst + 127) / 128, 128, 0, st>>>(inst, theta, ninst, hdr, catMd, cat_word,
+                                                            static_cast<const double2*>(main64),
                                                             static_cast<const double2*>(side64), out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0, void* main64, void* main32,
-                             void* side64, cudaStream_t st) {
-    init_rho0_kernel<<<(ninst + 127) / 128, 128, 0, st>>>(inst, ninst, rho0, static_cast<double2*>(main64),
+cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0, int stride, void* main64,
+                             void* main32, void* side64, cudaStream_t st) {
+    init_rho0_kernel<<<(ninst + 127) / 128, 128, 0, st>>>(inst, ninst, rho0, stride, static_cast<double2*>(main64),
                                                           static_cast<float2*>(main32), static_cast<double2*>(side64));
     return cudaGetLastError();
 }
+
+// -- end: physical-representative kernels
 
 }  // namespace sa

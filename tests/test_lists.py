@@ -79,7 +79,7 @@ def _eval_lists(lib, sas, baths, x, insts):
             gG.append(P["G"][p])
             gM.append(P["cat_M"][P["cat_off"][p]:P["cat_off"][p + 1]])
             ids = P["ids"][p]
-            ggam.append(sum(vec[v] @ nu for v in ids if v >= 0))
+            ggam.append(sum(vec[v % len(vec)] @ nu for v in ids if v >= 0))  # molecule 1: ids V + v
         cbase += P["cat_off"][-1]
     coefs = [_slot_coefficients(b) for b in baths]
     for it in L["items"]:
@@ -153,7 +153,7 @@ def _case(params_list, baths, sas, precision, chunk=None):
     for i, sa in enumerate(sas):
         ref = sa.rhs(xs[i])
         g = got[off:off + sa.nvar]
-        n_rho0 = 5 if sa.N >= 2 else 4
+        n_rho0 = int(sa.patterns()["var_off"][1])  # the physical representative's variables
         if precision == S.SA_FP32_AUX:
             # the physical representative is integrated by the FP64 kernel
             assert np.all(np.isnan(g[:n_rho0]))
@@ -166,20 +166,22 @@ def _case(params_list, baths, sas, precision, chunk=None):
 
 @pytest.mark.parametrize("precision", [S.SA_FP64, S.SA_FP32_AUX])
 @pytest.mark.parametrize("N,m,L", [(1, 1, 3), (2, 1, 3), (3, 2, 3), (10, 2, 6), (12, 3, 4), (7, 4, 3), (2, 2, 6)])
-def test_lists_reproduce_oracle_rhs(N, m, L, precision):
+@pytest.mark.parametrize("d", [0, 1])
+def test_lists_reproduce_oracle_rhs(N, m, L, precision, d):
     bath = _generic_bath(m, N + 7 * m + L)
-    kw = dict(detuning=0.1, g=0.2, kappa=0.05, term=0.013)
+    kw = dict(detuning=0.1, g=0.2, kappa=0.05, term=0.013, d=d)
     sa = oracle.SA(N, m, L, bath, **kw)
     _case([S.make_params(N, m, L, bath, **kw)], [bath], [sa], precision)
 
 
 def test_lists_batch_and_chunk():
-    """A batch of unlike instances, with a larger work-item capacity."""
+    """A batch of unlike instances, with a larger work-item capacity; the
+    second instance keeps molecule 1 distinguished."""
     specs = [(3, 1, 4, 1), (9, 2, 3, 2), (5, 3, 3, 3)]
     sas, baths, ps = [], [], []
     for N, m, L, seed in specs:
         b = _generic_bath(m, seed)
-        kw = dict(detuning=0.03 * seed, g=0.1 / seed, kappa=0.01 * seed)
+        kw = dict(detuning=0.03 * seed, g=0.1 / seed, kappa=0.01 * seed, d=int(seed == 2))
         sas.append(oracle.SA(N, m, L, b, **kw))
         baths.append(b)
         ps.append(S.make_params(N, m, L, b, **kw))
@@ -202,7 +204,7 @@ def _eval_ell(lib, sas, baths, x):
             ginst.append(i)
             gG.append(P["G"][p])
             gM.append(P["cat_M"][P["cat_off"][p]:P["cat_off"][p + 1]])
-            ggam.append(sum(vec[v] @ nu for v in P["ids"][p] if v >= 0))
+            ggam.append(sum(vec[v % len(vec)] @ nu for v in P["ids"][p] if v >= 0))
     gvar.append(x.size)
     coefs = [_slot_coefficients(b) for b in baths]
     out = np.zeros(x.size, complex)
@@ -253,16 +255,17 @@ def _eval_ell(lib, sas, baths, x):
 
 @pytest.mark.parametrize("precision", [S.SA_FP64, S.SA_FP32_AUX])
 @pytest.mark.parametrize("N,m,L", [(1, 1, 3), (3, 2, 3), (10, 2, 6), (7, 4, 3)])
-def test_ell_reproduces_oracle_rhs(N, m, L, precision):
+@pytest.mark.parametrize("d", [0, 1])
+def test_ell_reproduces_oracle_rhs(N, m, L, precision, d):
     bath = _generic_bath(m, N + 7 * m + L)
-    kw = dict(detuning=0.1, g=0.2, kappa=0.05, term=0.013)
+    kw = dict(detuning=0.1, g=0.2, kappa=0.05, term=0.013, d=d)
     sa = oracle.SA(N, m, L, bath, **kw)
     lib = S.Heom(S.make_params(N, m, L, bath, **kw), precision=precision, host_only=True)
     lib.set_kernel(S.SA_KERNEL_ELL)
     x = W.random_state(sa.nvar, seed=5)
     got = _eval_ell(lib, [sa], [bath], x)
     ref = sa.rhs(x)
-    n0 = (5 if N >= 2 else 4) if precision == S.SA_FP32_AUX else 0  # no lists for the FP64-integrated rho_0
+    n0 = int(sa.patterns()["var_off"][1]) if precision == S.SA_FP32_AUX else 0  # no lists for the FP64 rho_0
     if n0:
         # without its hierarchy terms, the physical representative differs
         assert np.max(np.abs(got[:n0] - ref[:n0])) > 1e-6

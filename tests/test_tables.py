@@ -42,9 +42,25 @@ CASES = [(1, 1, 3), (2, 1, 3), (3, 1, 0), (3, 2, 3), (4, 1, 5), (5, 2, 4), (10, 
          (100, 2, 8), (30, 1, 12), (1000000, 1, 9), (6, 5, 3), (2, 2, 6)]
 
 
+D_CASES = [(1, 1, 3), (2, 1, 3), (3, 1, 0), (3, 2, 3), (4, 1, 5), (5, 2, 4), (10, 2, 6), (12, 3, 4), (7, 4, 3),
+           (100, 2, 8), (30, 1, 12), (1000000, 1, 9), (6, 5, 3), (2, 2, 6), (2, 1, 1), (1, 3, 4)]
+
+
 @pytest.mark.parametrize("N,m,L", CASES)
 def test_tables_bit_exact(N, m, L):
-    sa, lib = _pair(N, m, L, _generic_bath(m, N + 7 * m + L), detuning=0.1, g=0.2, kappa=0.05)
+    _check_tables(N, m, L, 0)
+
+
+@pytest.mark.parametrize("N,m,L", D_CASES)
+def test_tables_bit_exact_distinguished(N, m, L):
+    """One distinguished molecule (Sec. V.F): molecule 1's vector ids
+    V .. 2V-1 close every pattern, with the same order, categories and
+    connections as the oracle's."""
+    _check_tables(N, m, L, 1)
+
+
+def _check_tables(N, m, L, d):
+    sa, lib = _pair(N, m, L, _generic_bath(m, N + 7 * m + L), detuning=0.1, g=0.2, kappa=0.05, d=d)
     assert lib.n_patterns == sa.npat and lib.n_vars == sa.nvar
     assert np.array_equal(lib.dump_vectors(0), sa.vectors())
     a, b = lib.dump_patterns(0), sa.patterns()
@@ -100,7 +116,7 @@ def test_batch_offsets_and_counts():
         off += c["n_vars"]
     assert h.n_vars == off
     side = (off * 8 + 255) // 256 * 256
-    assert h.state_bytes == side + 12 * 8 * 16
+    assert h.state_bytes == side + 12 * 16 * 16  # 16 FP64 slots per instance
 
 
 def test_saturation_in_library():
@@ -113,13 +129,14 @@ def test_saturation_in_library():
     assert nvar[L] < nvar[L + 1] == nvar[-1]
 
 
-@pytest.mark.parametrize("bad", [dict(N=0), dict(m=0), dict(m=9), dict(L=-1), dict(L=31)])
+@pytest.mark.parametrize("bad", [dict(N=0), dict(m=0), dict(m=9), dict(L=-1), dict(L=31), dict(d=2), dict(d=-1),
+                                 dict(reserved=1)])
 def test_invalid_arguments_rejected(bad):
-    args = dict(N=3, m=1, L=2)
+    args = dict(N=3, m=1, L=2, d=0, reserved=0)
     args.update(bad)
     bath = {"c": np.ones(8) * 0.1, "cc": np.ones(8) * 0.1, "nu": np.ones(8)}
     p = S.make_params(args["N"], min(max(args["m"], 1), 8), args["L"], bath)
-    p.m = args["m"]
+    p.m, p.d, p.reserved = args["m"], args["d"], args["reserved"]
     with pytest.raises(S.SaHeomError) as e:
         S.Heom(p, host_only=True)
     assert e.value.code == -1
