@@ -53,11 +53,13 @@ extern "C" {
 #endif
 
 #define SA_HEOM_MAXM 8  /* exponentials per local bath (static channel included) */
+#define SA_HEOM_MAXD 3  /* distinguished molecules */
+#define SA_HEOM_PHYS_SLOTS 32 /* complex values per instance in sa_heom_init_physical */
 #define SA_HEOM_MAXL 30 /* hierarchy depth */
 
 enum {
     SA_OK = 0,
-    SA_ERR_INVALID_ARG = -1, /* N < 1, m outside 1..8, L outside 0..30, d outside 0..1, |c_k| = 0,
+    SA_ERR_INVALID_ARG = -1, /* N < 1, m outside 1..8, L outside 0..30, d outside 0..min(3, N), |c_k| = 0,
                                 non-finite input */
     SA_ERR_UNSUPPORTED = -2, /* size beyond the 32-bit table indices, missing device */
     SA_ERR_OOM = -3,         /* host or device allocation failed */
@@ -86,15 +88,17 @@ enum { SA_BATH_HIGH_T = 0, SA_BATH_MATSUBARA = 1, SA_BATH_PADE = 2 };
  *              ADO, i.e. -Delta w V per unique variable with w = 0 for Z and
  *              P, 1 for X and Y, 2 for S and T.  sa_bath_terminator gives
  *              Delta for the Matsubara scheme.
- *   d          distinguished molecules, 0 or 1.  With d = 1 molecule 1 is
- *              kept out of the permutation symmetry (Sec. V.F: the localised
- *              state |e_1><e_1| and cavity-site superpositions): its local
- *              vector is stored with the pattern as vector id V + v (ids
- *              V .. 2V-1, V = n_vectors), so it always forms a category of
- *              its own with M = 1, listed after the other nonzero vectors
- *              and before the zero category (M = N - r, r counting molecule
- *              1).  The other N - 1 molecules are symmetrised as with d = 0.
- *              Set the initial state with sa_heom_init_physical.
+ *   d          distinguished molecules, 0 .. min(SA_HEOM_MAXD, N)
+ *              (Eq. N-symmetric-pool).  Molecules 1..d are kept out of the
+ *              permutation symmetry (Sec. V.F: the localised state
+ *              |e_1><e_1| and cavity-site superpositions need d = 1): the
+ *              local vector v of molecule j is stored with the pattern as
+ *              vector id j V + v (V = n_vectors), so each forms a category of
+ *              its own with M = 1, listed after the other nonzero vectors in
+ *              molecule order and before the zero category (M = N - r, r
+ *              counting the distinguished entries).  The other N - d
+ *              molecules are symmetrised as with d = 0.  Set the initial
+ *              state with sa_heom_init_physical.
  *   reserved   must be 0.
  */
 typedef struct sa_params {
@@ -190,9 +194,11 @@ int sa_heom_var_offset(const sa_heom* h, int inst, int64_t* out);
  * Table dumps of instance inst (host copies, canonical order), for checking
  * the builder against an independent implementation:
  *   sa_heom_dump_vectors:   comp[n_vectors * m] local vectors (id 0 = zero).
- *   sa_heom_dump_patterns:  per pattern tier, r (nonzero molecules), G, h,
+ *   sa_heom_dump_patterns:  per pattern tier, r (entries of its id list:
+ *                           nonzero vectors of the symmetric molecules plus
+ *                           one per distinguished molecule), G, h,
  *                           var_off (n_patterns + 1, instance-relative),
- *                           cat_off (n_patterns + 1), ids[n_patterns * L]
+ *                           cat_off (n_patterns + 1), ids[n_patterns * (L + d)]
  *                           (vector ids padded with -1).
  *   sa_heom_dump_categories: vector id and multiplicity M_q of each category.
  *   sa_heom_dump_terms:     the per-variable hierarchy terms the records
@@ -261,7 +267,7 @@ int sa_heom_state_bytes(const sa_heom* h, size_t* bytes);
  * initial-zero/higher): every ADO zero except the physical representative,
  * set per instance from rho0[10 * i ..]: Z, X_0, Y_0, P_0, T_0 as (re, im)
  * pairs (T_0 ignored for N = 1).  d_state: caller-owned device buffer of
- * sa_heom_state_bytes bytes.  SA_ERR_INVALID_ARG for a batch with a d = 1
+ * sa_heom_state_bytes bytes.  SA_ERR_INVALID_ARG for a batch with a d >= 1
  * instance.  Asynchronous on `stream`.
  */
 int sa_heom_init_state(const sa_heom* h, const double* rho0, void* d_state, void* stream);
@@ -271,11 +277,13 @@ int sa_heom_init_state(const sa_heom* h, const double* rho0, void* d_state, void
  * physical representative (the tier-0 pattern, whose variables are rho_S
  * written over its categories) given variable by variable in the canonical
  * layout: Z, X_1..X_G, Y_1..Y_G, P_1..P_G, S_{q,r} row-major (r != q), then
- * T.  phys[32 * i ..] holds instance i's values as (re, im) pairs; only the
- * first n of them are read, n = the pattern's variable count (5 for d = 0,
- * N >= 2; 10 for d = 1, N >= 3, where category 1 is molecule 1 and category
- * 2 the other N - 1 molecules).  Needed for d = 1 (sa_heom_init_state
- * returns SA_ERR_INVALID_ARG for such instances); valid for every instance.
+ * T.  phys[2 * SA_HEOM_PHYS_SLOTS * i ..] holds instance i's values as
+ * (re, im) pairs; only the first n of them are read, n = the pattern's
+ * variable count: (G + 1)^2 + h with G = d + 1 categories for N > d
+ * (molecules 1..d, then the other N - d), h = 1 for N - d >= 2 -- 5 for
+ * d = 0, 10 for d = 1, 17 for d = 2, 26 for d = 3.  Needed for d >= 1
+ * (sa_heom_init_state returns SA_ERR_INVALID_ARG for such instances); valid
+ * for every instance.
  * The values are not checked for Hermiticity.  Asynchronous on `stream`.
  */
 int sa_heom_init_physical(const sa_heom* h, const double* phys, void* d_state, void* stream);

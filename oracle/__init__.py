@@ -161,7 +161,7 @@ class SA:
         return out
 
     def patterns(self) -> dict:
-        P, L = self.npat, self.L
+        P, L = self.npat, self.L + self.d  # id lists: <= L symmetric entries + d distinguished
         tier = np.zeros(P, np.int32)
         r = np.zeros(P, np.int32)
         G = np.zeros(P, np.int32)
@@ -232,33 +232,55 @@ class SA:
         lib().orc_sa_propagate(self._h, _ptr(y), float(dt), int(nsteps), int(obs_every), _ptr(obs))
         return y, obs
 
+    def _phys_categories(self):
+        """Categories of the physical representative (the empty pattern) with
+        the basis index of a molecule in each: distinguished molecules 1..d
+        (named "d" when d = 1, else "1".."d"), then the zero category "0" of
+        the other N - d when N > d."""
+        names = ["d"] if self.d == 1 else [str(j) for j in range(1, self.d + 1)]
+        cats = [(n, j + 1) for j, n in enumerate(names)]
+        if self.N > self.d:
+            cats.append(("0", self.d + 1))
+        return cats
+
     def rho0_index(self) -> dict:
-        """Indices of the physical representative's variables (empty pattern).
-        With d = 1 its categories are the distinguished molecule (suffix d)
-        and the zero category of the others (suffix 0)."""
-        if self.d == 0:
-            idx = {"Z": 0, "X0": 1, "Y0": 2, "P0": 3}
-            if self.N >= 2:
-                idx["T0"] = 4
-            return idx
-        if self.N == 1:
-            return {"Z": 0, "Xd": 1, "Yd": 2, "Pd": 3}
-        idx = {"Z": 0, "Xd": 1, "X0": 2, "Yd": 3, "Y0": 4, "Pd": 5, "P0": 6, "Sd0": 7, "S0d": 8}
-        if self.N >= 3:
-            idx["T0"] = 9
+        """Indices of the physical representative's variables in the canonical
+        layout (Z; X_q; Y_q; P_q; S_qr row-major; T), keyed by kind and
+        category name, e.g. Z, X0, Y0, P0, T0 for d = 0."""
+        cats = self._phys_categories()
+        G = len(cats)
+        idx = {"Z": 0}
+        for q, (n, _) in enumerate(cats, 1):
+            idx["X" + n], idx["Y" + n], idx["P" + n] = q, G + q, 2 * G + q
+        for q, (n, _) in enumerate(cats, 1):
+            for r, (n2, _) in enumerate(cats, 1):
+                if r != q:
+                    idx["S" + n + n2] = 3 * G + 1 + (q - 1) * (G - 1) + (r - 1) - (1 if r > q else 0)
+        if self.N - self.d >= 2:
+            idx["T0"] = (G + 1) ** 2  # only the zero category has M >= 2
         return idx
 
     def initial_state_dense(self, rho) -> np.ndarray:
         """Factorised initial hierarchy from a dense (N+1)x(N+1) rho_S in the
         basis {c, e_1 .. e_N}, invariant under permutations of the molecules
-        it does not distinguish (all of them for d = 0, 2..N for d = 1)."""
+        it does not distinguish (molecules d+1..N)."""
         rho = np.asarray(rho, complex)
         x = self.zeros()
-        ix = self.rho0_index()
-        e = {"Z": (0, 0), "X0": (self.d + 1, 0), "Y0": (0, self.d + 1), "P0": (self.d + 1, self.d + 1),
-             "T0": (self.d + 1, self.d + 2), "Xd": (1, 0), "Yd": (0, 1), "Pd": (1, 1), "Sd0": (1, 2), "S0d": (2, 1)}
-        for k, j in ix.items():
-            x[j] = rho[e[k]]
+        rep = dict(self._phys_categories())
+        for k, j in self.rho0_index().items():
+            if k == "Z":
+                e = (0, 0)
+            elif k == "T0":
+                e = (self.d + 1, self.d + 2)
+            elif k[0] == "X":
+                e = (rep[k[1:]], 0)
+            elif k[0] == "Y":
+                e = (0, rep[k[1:]])
+            elif k[0] == "P":
+                e = (rep[k[1:]], rep[k[1:]])
+            else:
+                e = (rep[k[1]], rep[k[2]])
+            x[j] = rho[e]
         return x
 
     def initial_state(self, Z, X0, Y0, P0, T0=0.0) -> np.ndarray:

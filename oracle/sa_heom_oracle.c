@@ -40,6 +40,12 @@
  *    Matsubara terms without a formula): the residual correlation is taken as
  *    white noise of weight Delta = sum over omitted terms of c_k / nu_k, which
  *    adds -Delta sum_i [Q_i, [Q_i, rho_n]] to every ADO (off when Delta = 0).
+ *  - Distinguished molecules (Sec. IV, Eq. N-symmetric-pool; Sec. V.F): with
+ *    d of them, molecule j <= d carries its vector v as id j V + v, so its
+ *    vector is a category of its own (M = 1) in every pattern, and the lists
+ *    end with molecules 1..d in order; the other N - d molecules fill at most
+ *    min(L, N - d) nonzero slots and the zero category holds N - r of them
+ *    (r counting the distinguished entries).
  *  - Pattern order (the global vector of Eq. global-R): tier ascending, then
  *    the vector lists compared lexicographically with larger vectors first.
  *    Variable order inside a pattern: Z; X_1..X_G; Y_1..Y_G; P_1..P_G;
@@ -61,6 +67,7 @@
 typedef double complex cplx;
 
 #define ORC_MAXM 8
+#define ORC_MAXD 3   /* distinguished molecules */
 
 /* count of internal inconsistencies (a missing target or category); a
  * correct oracle leaves it at zero and the tests assert that */
@@ -78,7 +85,7 @@ typedef struct {
     double cc_re[ORC_MAXM], cc_im[ORC_MAXM]; /* c-check_k */
     double nu_re[ORC_MAXM], nu_im[ORC_MAXM]; /* nu_k */
     double term;    /* terminator strength Delta (0: off) */
-    int d;          /* distinguished molecules: 0, or 1 (molecule 1 keeps its label) */
+    int d;          /* distinguished molecules 0..ORC_MAXD: molecules 1..d keep their labels */
 } orc_params;
 
 static cplx ck(const orc_params* p, int k) { return p->c_re[k] + I * p->c_im[k]; }
@@ -104,8 +111,8 @@ int orc_num_threads(void) {
 typedef struct {
     int m, L;
     int V;                 /* vectors including the zero vector (id 0) */
-    int Vtot;              /* V, or 2 V with a distinguished molecule: ids V .. 2V-1
-                              are the distinguished molecule's vectors (id - V) */
+    int Vtot;              /* (d + 1) V: ids j V .. j V + V - 1 are distinguished
+                              molecule j's vectors (id - j V), j = 1..d */
     unsigned char* comp;   /* Vtot * m components */
     int* norm;             /* |alpha| */
     int* lut;              /* mixed-radix (L+1)^m code -> id, -1 if |alpha| > L */
@@ -152,7 +159,7 @@ static void vecset_build(vecset* vs, int m, int L, int d) {
     qsort(all, cnt, m, vec_qsort_cmp);
     /* after sorting, the zero vector is last; move it to id 0 */
     vs->V = cnt;   /* >= 1: the zero vector is always in the set */
-    vs->Vtot = d ? 2 * cnt : cnt;
+    vs->Vtot = (d + 1) * cnt;
     vs->comp = (unsigned char*)calloc((size_t)vs->Vtot + 1, m);
     for (int v = 1; v < cnt; ++v)
         for (int k = 0; k < m; ++k) vs->comp[(size_t)v * m + k] = all[(size_t)(v - 1) * m + k];
@@ -166,16 +173,16 @@ static void vecset_build(vecset* vs, int m, int L, int d) {
         vs->norm[v] = s;
         vs->lut[vec_code(vs->comp + (size_t)v * m, m, L)] = v;
     }
-    for (int v = cnt; v < vs->Vtot; ++v) { /* the distinguished molecule's copies */
-        memcpy(vs->comp + (size_t)v * m, vs->comp + (size_t)(v - cnt) * m, m);
-        vs->norm[v] = vs->norm[v - cnt];
+    for (int v = cnt; v < vs->Vtot; ++v) { /* the distinguished molecules' copies */
+        memcpy(vs->comp + (size_t)v * m, vs->comp + (size_t)(v % cnt) * m, m);
+        vs->norm[v] = vs->norm[v % cnt];
     }
 }
 
 static void vecset_free(vecset* vs) { free(vs->comp); free(vs->norm); free(vs->lut); }
 
 /* id of alpha +/- e_k; -1 if it leaves the set (negative or |alpha| > L).
- * A distinguished molecule's vector stays among the distinguished ids. */
+ * A distinguished molecule's vector stays among its own ids. */
 static int vec_shift(const vecset* vs, int id, int k, int dir) {
     unsigned char t[ORC_MAXM];
     memcpy(t, vs->comp + (size_t)id * vs->m, vs->m);
@@ -184,7 +191,7 @@ static int vec_shift(const vecset* vs, int id, int k, int dir) {
     t[k] = (unsigned char)v;
     int w = vs->lut[vec_code(t, vs->m, vs->L)];
     if (w < 0) return -1;
-    return id >= vs->V ? vs->V + w : w;
+    return (id / vs->V) * vs->V + w;
 }
 
 /* ====================================================================== */
@@ -257,21 +264,32 @@ static void patgen_push(patgen* pg, const int* cur, int r, int tier) {
     pg->n += 1;
 }
 
-/* extra >= 0: the distinguished molecule's id, appended to every multiset
- * (it is the largest id, so the list stays ascending); its norm is already
- * in tier */
-static void patgen_rec(patgen* pg, const vecset* vs, int* cur, int r, int tier, int start, int maxr, int extra) {
-    if (extra >= 0) {
-        cur[r] = extra;
-        patgen_push(pg, cur, r + 1, tier);
-    } else {
-        patgen_push(pg, cur, r, tier);
-    }
+/* extra[0..nextra-1]: the distinguished molecules' ids, appended to every
+ * multiset (they are the largest ids, in molecule order, so the list stays
+ * ascending); their norms are already in tier */
+static void patgen_rec(patgen* pg, const vecset* vs, int* cur, int r, int tier, int start, int maxr,
+                       const int* extra, int nextra) {
+    for (int j = 0; j < nextra; ++j) cur[r + j] = extra[j];
+    patgen_push(pg, cur, r + nextra, tier);
     if (r >= maxr) return;
     for (int v = start; v < vs->V; ++v) {
         if (tier + vs->norm[v] > vs->L) continue;
         cur[r] = v;
-        patgen_rec(pg, vs, cur, r + 1, tier + vs->norm[v], v, maxr, extra);
+        patgen_rec(pg, vs, cur, r + 1, tier + vs->norm[v], v, maxr, extra, nextra);
+    }
+}
+
+/* every choice of the d distinguished molecules' vectors (zero vector
+ * included) with total norm <= L, then the multisets of the others */
+static void patgen_dist(patgen* pg, const vecset* vs, int* cur, int* extra, int j, int d, int tier, int maxr) {
+    if (j == d) {
+        patgen_rec(pg, vs, cur, 0, tier, 1, maxr, extra, d);
+        return;
+    }
+    for (int dv = 0; dv < vs->V; ++dv) {
+        if (tier + vs->norm[dv] > vs->L) continue;
+        extra[j] = (j + 1) * vs->V + dv;
+        patgen_dist(pg, vs, cur, extra, j + 1, d, tier + vs->norm[dv], maxr);
     }
 }
 
@@ -303,25 +321,21 @@ static long long var_local(int G, int kind, int q, int r, int trank_q) {
 }
 
 orc_sa* orc_sa_create(const orc_params* p, int use_cache) {
-    if (p->N < 1 || p->m < 1 || p->m > ORC_MAXM || p->L < 0 || p->d < 0 || p->d > 1) return NULL;
+    if (p->N < 1 || p->m < 1 || p->m > ORC_MAXM || p->L < 0 || p->d < 0 || p->d > ORC_MAXD || p->d > p->N)
+        return NULL;
     for (int k = 0; k < p->m; ++k)
         if (!(absck(p, k) > 0.0)) return NULL;
     orc_sa* s = (orc_sa*)calloc(1, sizeof(orc_sa));
     s->p = *p;
     vecset_build(&s->vs, p->m, p->L, p->d);
     /* patterns: at most N - d nonzero vectors of the undistinguished
-     * molecules, never more than L; with d = 1 the distinguished molecule's
-     * vector (zero included) is one more entry of every pattern */
+     * molecules, never more than L; each distinguished molecule's vector
+     * (zero included) is one more entry of every pattern */
     int maxr = p->L;
     if ((long long)maxr > p->N - p->d) maxr = (int)(p->N - p->d);
     patgen pg; memset(&pg, 0, sizeof(pg));
-    int cur[256];
-    if (p->d) {
-        for (int dv = 0; dv < s->vs.V; ++dv)
-            patgen_rec(&pg, &s->vs, cur, 0, s->vs.norm[dv], 1, maxr, s->vs.V + dv);
-    } else {
-        patgen_rec(&pg, &s->vs, cur, 0, 0, 1, maxr, -1);
-    }
+    int cur[256], extra[ORC_MAXD + 1];
+    patgen_dist(&pg, &s->vs, cur, extra, 0, p->d, 0, maxr);
     g_sort_ids = pg.buf;
     qsort(pg.refs, pg.n, sizeof(patref), patref_cmp);
     s->P = pg.n;
@@ -416,10 +430,12 @@ long long orc_sa_num_categories(const orc_sa* s) { return s->cat_off[s->P]; }
 
 void orc_sa_vectors(const orc_sa* s, unsigned char* out) { memcpy(out, s->vs.comp, (size_t)s->vs.V * s->vs.m); }
 
-/* per pattern: tier, r, G, h, var_off, cat_off; ids padded with -1 to width L */
+/* per pattern: tier, r, G, h, var_off, cat_off; ids padded with -1 to width
+ * L + d (a pattern lists at most L nonzero vectors of the symmetric molecules
+ * and one entry per distinguished molecule) */
 void orc_sa_patterns(const orc_sa* s, int* tier, int* r, int* G, int* h, long long* var_off,
                      long long* cat_off, int* ids_padded) {
-    int L = s->p.L;
+    int L = s->p.L + s->p.d;
     for (long long i = 0; i < s->P; ++i) {
         int ri = (int)(s->id_off[i + 1] - s->id_off[i]);
         if (tier) tier[i] = s->tier[i];
@@ -1086,8 +1102,8 @@ void orc_conv_to_sa(const orc_conv* c, const orc_sa* s, long long* map) {
         int nk = 0, tier = 0;
         for (int i = 0; i < N; ++i) {
             vid[i] = s->vs.lut[vec_code(n + i * m, m, s->p.L)];
-            /* with d = 1, molecule 1 is the distinguished one: its own ids */
-            if (i == 0 && s->p.d) vid[i] += s->vs.V;
+            /* molecules 1..d are the distinguished ones: their own ids */
+            if (i < s->p.d) vid[i] += (i + 1) * s->vs.V;
             if (vid[i] > 0) { key[nk++] = vid[i]; tier += s->vs.norm[vid[i]]; }
         }
         /* insertion sort: ascending id = vectors in canonical order */

@@ -17,6 +17,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsaheom.so")
 MAXM = 8
+MAXD = 3         # SA_HEOM_MAXD
+PHYS_SLOTS = 32  # SA_HEOM_PHYS_SLOTS
 
 SA_FP64, SA_FP32_AUX = 0, 1
 SA_BUILD_DEVICE, SA_BUILD_HOST_ONLY = 0, 1
@@ -164,7 +166,7 @@ def _stream(stream) -> ctypes.c_void_p:
 def make_params(N, m=None, L=0, bath=None, detuning=0.0, g=0.0, kappa=0.0, term=0.0, d=0) -> Params:
     """sa_params from a bath dict {c, cc, nu} (complex arrays of length m);
     term: terminator strength Delta (0: off, see bath_terminator); d: 1 keeps
-    molecule 1 out of the permutation symmetry."""
+    molecules 1..d (d <= 3) out of the permutation symmetry."""
     p = Params()
     c = np.asarray(bath["c"], complex)
     cc = np.asarray(bath["cc"], complex)
@@ -252,7 +254,7 @@ class Heom:
 
     def dump_patterns(self, inst: int = 0) -> dict:
         i = self.info(inst)
-        P, L = i["n_patterns"], self.params[inst].L
+        P, L = i["n_patterns"], self.params[inst].L + self.params[inst].d  # id list width L + d
         tier, r, G, h = (np.zeros(P, np.int32) for _ in range(4))
         var_off = np.zeros(P + 1, np.int64)
         cat_off = np.zeros(P + 1, np.int64)
@@ -288,12 +290,12 @@ class Heom:
         _check(lib().sa_heom_init_state(self._h, _ptr(flat), _dev(state), _stream(stream)), "sa_heom_init_state")
 
     def init_physical(self, state, phys, stream=None):
-        """phys: (count, n) complex, n <= 16: each instance's physical
+        """phys: (count, n) complex, n <= 32: each instance's physical
         representative in the canonical layout (Z, X_q, Y_q, P_q, S_qr, T)."""
         ph = np.asarray(phys, complex)
         ph = ph.reshape(self.count, -1) if ph.ndim > 1 else ph.reshape(1, -1)
-        assert ph.shape[1] <= 16
-        r = np.zeros((self.count, 16), complex)
+        assert ph.shape[1] <= PHYS_SLOTS
+        r = np.zeros((self.count, PHYS_SLOTS), complex)
         r[:, :ph.shape[1]] = ph
         flat = np.ascontiguousarray(r.view(np.float64).reshape(-1))
         _check(lib().sa_heom_init_physical(self._h, _ptr(flat), _dev(state), _stream(stream)), "sa_heom_init_physical")

@@ -1152,7 +1152,8 @@ int sa_heom_dump_patterns(const sa_heom* h, int inst, int32_t* tier, int32_t* r,
         if (var_off) var_off[p] = int64_t(hi.var_off[p]);
         if (cat_off) cat_off[p] = int64_t(hi.cat_off[p]);
         if (ids)
-            for (int a = 0; a < hi.L; ++a) ids[p * hi.L + a] = a < rp ? int32_t(hi.ids[hi.id_off[p] + a]) : -1;
+            for (int a = 0, w = hi.L + hi.d; a < w; ++a)
+                ids[p * w + a] = a < rp ? int32_t(hi.ids[hi.id_off[p] + a]) : -1;
     }
     if (var_off) var_off[hi.P] = int64_t(hi.var_off[hi.P]);
     if (cat_off) cat_off[hi.P] = int64_t(hi.cat_off[hi.P]);

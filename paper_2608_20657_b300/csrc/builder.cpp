@@ -75,7 +75,7 @@ void build_vectors(HostInstance& hi) {
     std::sort(vecs.begin(), vecs.end(),
               [m](const std::vector<uint8_t>& a, const std::vector<uint8_t>& b) { return vec_before(a.data(), b.data(), m); });
     hi.V = int(vecs.size()) + 1;
-    hi.Vtot = hi.d ? 2 * hi.V : hi.V;
+    hi.Vtot = (hi.d + 1) * hi.V;
     hi.comp.assign(size_t(hi.Vtot) * m, 0);
     hi.norm.assign(hi.Vtot, 0);
     for (int v = 1; v < hi.V; ++v) {
@@ -84,10 +84,10 @@ void build_vectors(HostInstance& hi) {
             hi.norm[v] += vecs[v - 1][k];
         }
     }
-    // the distinguished molecule's copies, zero vector included
+    // the distinguished molecules' copies, zero vector included
     for (int v = hi.V; v < hi.Vtot; ++v) {
-        std::memcpy(&hi.comp[size_t(v) * m], &hi.comp[size_t(v - hi.V) * m], m);
-        hi.norm[v] = hi.norm[v - hi.V];
+        std::memcpy(&hi.comp[size_t(v) * m], &hi.comp[size_t(v % hi.V) * m], m);
+        hi.norm[v] = hi.norm[v % hi.V];
     }
     int64_t total = 1;
     for (int k = 0; k < m; ++k) total *= (L + 1);
@@ -95,8 +95,8 @@ void build_vectors(HostInstance& hi) {
     for (int v = 0; v < hi.V; ++v) hi.lut[vcode(&hi.comp[size_t(v) * m], m, L)] = v;
 }
 
-// id of alpha +/- e_k, -1 outside the set; molecule 1's vectors stay among
-// its own ids
+// id of alpha +/- e_k, -1 outside the set; a distinguished molecule's
+// vectors stay among its own ids
 int shift_vec(const HostInstance& hi, int id, int k, int dir) {
     uint8_t t[SA_HEOM_MAXM];
     std::memcpy(t, &hi.comp[size_t(id) * hi.m], hi.m);
@@ -104,7 +104,7 @@ int shift_vec(const HostInstance& hi, int id, int k, int dir) {
     if (v < 0 || v > hi.L) return -1;
     t[k] = uint8_t(v);
     const int w = hi.lut[vcode(t, hi.m, hi.L)];
-    return (w >= 0 && id >= hi.V) ? hi.V + w : w;
+    return w >= 0 ? (id / hi.V) * hi.V + w : w;
 }
 
 // ---- pattern enumeration ---------------------------------------------------
@@ -172,9 +172,9 @@ struct PatMap {
 }  // namespace
 
 int build_instance(const sa_params& p, HostInstance& hi, std::string& err) {
-    if (p.N < 1 || p.m < 1 || p.m > SA_HEOM_MAXM || p.L < 0 || p.L > SA_HEOM_MAXL || p.d < 0 || p.d > 1 ||
-        p.reserved != 0) {
-        err = "N >= 1, 1 <= m <= 8, 0 <= L <= 30, d in {0, 1}, reserved = 0 required";
+    if (p.N < 1 || p.m < 1 || p.m > SA_HEOM_MAXM || p.L < 0 || p.L > SA_HEOM_MAXL || p.d < 0 ||
+        p.d > SA_HEOM_MAXD || p.d > p.N || p.reserved != 0) {
+        err = "N >= 1, 1 <= m <= 8, 0 <= L <= 30, 0 <= d <= min(3, N), reserved = 0 required";
         return SA_ERR_INVALID_ARG;
     }
     const double scal[4] = {p.detuning, p.g, p.kappa, p.term};
@@ -219,26 +219,38 @@ int build_instance(const sa_params& p, HostInstance& hi, std::string& err) {
     if (!hi.d) {
         for (int t = 0; t <= L; ++t) en.dfs(1, t, t);
     } else {
-        // molecule 1's id (V + v, above every other id) closes each list;
-        // the lists of one tier are then sorted lexicographically
+        // distinguished molecule j's id (j V + v, above every id of molecule
+        // j - 1) closes each list in molecule order; the lists of one tier
+        // are then sorted lexicographically
         std::vector<uint32_t> all_ids, scratch_off{0};
         std::vector<uint8_t> all_tier;
+        int dv[SA_HEOM_MAXD] = {0};
         for (int t = 0; t <= L; ++t) {
             const size_t first = all_tier.size();
-            for (int dv = 0; dv < hi.V; ++dv) {
-                if (hi.norm[dv] > t) continue;
-                const size_t before = hi.tier.size();
-                en.dfs(1, t - hi.norm[dv], t);
-                // dfs appended to hi.ids / id_off / tier: move them out, with dv
-                for (size_t j = before; j < hi.tier.size(); ++j) {
-                    all_ids.insert(all_ids.end(), hi.ids.begin() + hi.id_off[j], hi.ids.begin() + hi.id_off[j + 1]);
-                    all_ids.push_back(uint32_t(hi.V + dv));
-                    scratch_off.push_back(uint32_t(all_ids.size()));
-                    all_tier.push_back(uint8_t(t));
+            // odometer over the distinguished molecules' vectors
+            std::fill(dv, dv + hi.d, 0);
+            while (true) {
+                int dn = 0;
+                for (int j = 0; j < hi.d; ++j) dn += hi.norm[dv[j]];
+                if (dn <= t) {
+                    const size_t before = hi.tier.size();
+                    en.dfs(1, t - dn, t);
+                    // dfs appended to hi.ids / id_off / tier: move them out,
+                    // with the distinguished ids
+                    for (size_t j = before; j < hi.tier.size(); ++j) {
+                        all_ids.insert(all_ids.end(), hi.ids.begin() + hi.id_off[j],
+                                       hi.ids.begin() + hi.id_off[j + 1]);
+                        for (int q = 0; q < hi.d; ++q) all_ids.push_back(uint32_t((q + 1) * hi.V + dv[q]));
+                        scratch_off.push_back(uint32_t(all_ids.size()));
+                        all_tier.push_back(uint8_t(t));
+                    }
+                    hi.ids.resize(hi.id_off[before]);
+                    hi.id_off.resize(before + 1);
+                    hi.tier.resize(before);
                 }
-                hi.ids.resize(hi.id_off[before]);
-                hi.id_off.resize(before + 1);
-                hi.tier.resize(before);
+                int j = hi.d - 1;
+                while (j >= 0 && ++dv[j] == hi.V) dv[j--] = 0;
+                if (j < 0) break;
             }
             std::vector<size_t> ord(all_tier.size() - first);
             for (size_t j = 0; j < ord.size(); ++j) ord[j] = first + j;

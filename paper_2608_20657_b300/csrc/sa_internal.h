@@ -15,7 +15,7 @@ namespace sa {
 constexpr int kMaxG = 31;            // categories per pattern (5-bit fields)
 constexpr int kCoefN = 32;           // occupation slots per channel in the coefficient table
 constexpr int kCoefPerInst = SA_HEOM_MAXM * kCoefN * 2;
-constexpr int kSideSlots = 16;       // FP64 slots of the physical representative per instance
+constexpr int kSideSlots = 32;       // FP64 slots of the physical representative per instance
 
 // ---- one hierarchy connection record ---------------------------------------
 // A record belongs to (pattern Lambda, category q, channel k, direction): the
@@ -68,7 +68,7 @@ struct InstDev {
     uint32_t coef_base;  // into the coefficient tables
     uint32_t side;       // first FP64 side slot
     uint32_t var_begin;  // first variable
-    uint32_t n_rho0;     // variables of the physical representative (4 or 5; up to 10 with d = 1)
+    uint32_t n_rho0;     // variables of the physical representative (5 for d = 0, up to 26 for d = 3)
     uint32_t pat_begin;  // first pattern (the empty pattern)
     uint32_t pad2[3];
     double term;         // terminator strength Delta (0: off)
@@ -83,8 +83,8 @@ struct HostInstance {
     // local vectors: id 0 = zero vector, then |alpha| descending, components
     // lexicographically descending
     int V = 0;
-    int d = 0;                       // distinguished molecules (0 or 1)
-    int Vtot = 0;                    // V, or 2 V: ids V .. 2V-1 are molecule 1's copies
+    int d = 0;                       // distinguished molecules (0 .. SA_HEOM_MAXD)
+    int Vtot = 0;                    // (d + 1) V: ids j V .. j V + V - 1 are molecule j's copies
     std::vector<uint8_t> comp;       // Vtot * m
     std::vector<int> norm;           // Vtot
     std::vector<int32_t> lut;        // mixed-radix code -> id

@@ -166,8 +166,10 @@ def _case(params_list, baths, sas, precision, chunk=None):
 
 @pytest.mark.parametrize("precision", [S.SA_FP64, S.SA_FP32_AUX])
 @pytest.mark.parametrize("N,m,L", [(1, 1, 3), (2, 1, 3), (3, 2, 3), (10, 2, 6), (12, 3, 4), (7, 4, 3), (2, 2, 6)])
-@pytest.mark.parametrize("d", [0, 1])
+@pytest.mark.parametrize("d", [0, 1, 2])
 def test_lists_reproduce_oracle_rhs(N, m, L, precision, d):
+    if d > N:
+        pytest.skip("d <= N")
     bath = _generic_bath(m, N + 7 * m + L)
     kw = dict(detuning=0.1, g=0.2, kappa=0.05, term=0.013, d=d)
     sa = oracle.SA(N, m, L, bath, **kw)
@@ -176,12 +178,12 @@ def test_lists_reproduce_oracle_rhs(N, m, L, precision, d):
 
 def test_lists_batch_and_chunk():
     """A batch of unlike instances, with a larger work-item capacity; the
-    second instance keeps molecule 1 distinguished."""
+    second and third keep one and two molecules distinguished."""
     specs = [(3, 1, 4, 1), (9, 2, 3, 2), (5, 3, 3, 3)]
     sas, baths, ps = [], [], []
     for N, m, L, seed in specs:
         b = _generic_bath(m, seed)
-        kw = dict(detuning=0.03 * seed, g=0.1 / seed, kappa=0.01 * seed, d=int(seed == 2))
+        kw = dict(detuning=0.03 * seed, g=0.1 / seed, kappa=0.01 * seed, d=seed - 1)
         sas.append(oracle.SA(N, m, L, b, **kw))
         baths.append(b)
         ps.append(S.make_params(N, m, L, b, **kw))
@@ -255,8 +257,10 @@ def _eval_ell(lib, sas, baths, x):
 
 @pytest.mark.parametrize("precision", [S.SA_FP64, S.SA_FP32_AUX])
 @pytest.mark.parametrize("N,m,L", [(1, 1, 3), (3, 2, 3), (10, 2, 6), (7, 4, 3)])
-@pytest.mark.parametrize("d", [0, 1])
+@pytest.mark.parametrize("d", [0, 1, 3])
 def test_ell_reproduces_oracle_rhs(N, m, L, precision, d):
+    if d > N:
+        pytest.skip("d <= N")
     bath = _generic_bath(m, N + 7 * m + L)
     kw = dict(detuning=0.1, g=0.2, kappa=0.05, term=0.013, d=d)
     sa = oracle.SA(N, m, L, bath, **kw)

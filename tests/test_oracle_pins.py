@@ -681,3 +681,104 @@ def test_distinguished_initial_tc_populations(orc, N):
     assert abs(o[4] - 0.3 * (1 - 1 / N)) < 1e-13
     assert abs(o[5] - 0.5 * (np.sqrt(0.7) + np.sqrt(0.3 / N)) ** 2) < 1e-13
     assert abs(o[6] - 0.5 * (np.sqrt(0.7) - np.sqrt(0.3 / N)) ** 2) < 1e-13
+
+
+def _orbits(N, m, L, d):
+    """Brute force: canonical patterns and unique variables are the orbits of
+    ADO labels n in N0^(N m), |n| <= L, and of (label, row, column) triples
+    under the permutations of molecules d+1..N (Sec. IV, Eq. N-symmetric-pool);
+    basis index 0 is the cavity, i the molecule i."""
+    import itertools
+
+    labels = [t for t in itertools.product(range(L + 1), repeat=N * m) if sum(t) <= L]
+    perms = [tuple(range(d)) + p for p in itertools.permutations(range(d, N))]
+    ado_orb, var_orb = set(), set()
+    for t in labels:
+        mol = [t[i * m:(i + 1) * m] for i in range(N)]
+        imgs = []
+        for p in perms:
+            # molecule i's vector moves to molecule p[i]
+            new = [None] * N
+            for i in range(N):
+                new[p[i]] = mol[i]
+            imgs.append((tuple(new), p))
+        ado_orb.add(min(im for im, _ in imgs))
+        for a in range(N + 1):
+            for b in range(N + 1):
+                var_orb.add(min((im, 0 if a == 0 else p[a - 1] + 1, 0 if b == 0 else p[b - 1] + 1)
+                                for im, p in imgs))
+    return len(ado_orb), len(var_orb)
+
+
+@pytest.mark.parametrize("N,m,L,d", [(1, 1, 3, 1), (2, 1, 3, 1), (3, 1, 3, 1), (4, 1, 3, 1), (3, 2, 2, 1),
+                                     (4, 2, 2, 2), (3, 1, 4, 2), (5, 1, 3, 2), (4, 1, 3, 3), (5, 1, 2, 3),
+                                     (4, 2, 2, 0), (5, 1, 3, 0)])
+def test_distinguished_counts_are_orbits(orc, N, m, L, d):
+    """The pattern and variable counts equal the orbit counts of the
+    conventional hierarchy under the residual permutation group, found by
+    brute force."""
+    bath = {"c": np.full(m, 0.1 + 0j), "cc": np.full(m, 0.1 + 0j), "nu": np.ones(m)}
+    sa = orc.SA(N, m, L, bath, cache=False, d=d)
+    assert (sa.npat, sa.nvar) == _orbits(N, m, L, d)
+
+
+@pytest.mark.parametrize("m,L,d", [(1, 4, 2), (2, 3, 2), (1, 3, 3), (1, 6, 1), (2, 4, 3)])
+def test_distinguished_saturation_thresholds(orc, m, L, d):
+    """Eqs. distinguished-pattern-threshold and distinguished-thresholds: the
+    pattern count stops growing exactly at N = L + d, the variable count
+    exactly at N = L + d + 2."""
+    bath = {"c": np.full(m, 0.1 + 0j), "cc": np.full(m, 0.1 + 0j), "nu": np.ones(m)}
+    sa = {N: orc.SA(N, m, L, bath, cache=False, d=d) for N in range(max(d, 1), L + d + 6)}
+    assert sa[L + d - 1].npat < sa[L + d].npat == sa[L + d + 5].npat
+    assert sa[L + d + 1].nvar < sa[L + d + 2].nvar == sa[L + d + 5].nvar
+
+
+@pytest.mark.parametrize("N,m,L,d", [(2, 1, 3, 2), (3, 1, 3, 2), (4, 2, 2, 2), (5, 1, 3, 2), (3, 1, 3, 3),
+                                     (4, 1, 3, 3), (5, 2, 2, 3)])
+def test_two_three_distinguished_sa_equals_conventional(orc, N, m, L, d):
+    """d = 2, 3: the reduced generator is still an exact reduction of Eq.
+    scaled-HEOM (the map is onto, and the right-hand sides agree, loss and
+    terminator on)."""
+    bath = _bath_generic(m, seed=N + m + L + d)
+    kw = dict(detuning=0.1, g=0.2, kappa=0.05, term=0.01)
+    sa = orc.SA(N, m, L, bath, d=d, **kw)
+    cv = orc.Conventional(N, m, L, bath, **kw)
+    mp = cv.map_to(sa)
+    assert (mp >= 0).all() and set(np.unique(mp)) == set(range(sa.nvar))
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal(sa.nvar) + 1j * rng.standard_normal(sa.nvar)
+    dcv, dsa = cv.rhs(x[mp]), sa.rhs(x)
+    assert np.abs(dcv - dsa[mp]).max() <= 1e-13 * np.abs(dcv).max()
+    # the dense initial state lands where the map puts the physical ADO
+    rho = rng.standard_normal((N + 1, N + 1)) + 1j * rng.standard_normal((N + 1, N + 1))
+    sym = np.zeros_like(rho)
+    import itertools
+
+    perms = list(itertools.permutations(range(d + 1, N + 1)))
+    for p in perms:  # average over the residual group so the state is invariant
+        idx = list(range(d + 1)) + list(p)
+        sym += rho[np.ix_(idx, idx)]
+    sym /= len(perms)
+    x0 = sa.initial_state_dense(sym)
+    assert np.allclose(x0[mp[0]], sym, atol=1e-15)
+    assert orc.errors() == 0
+
+
+@pytest.mark.parametrize("N", [3, 7, 100, 10 ** 12])
+def test_two_distinguished_initial_populations(orc, N):
+    """(|e_1> +- |e_2>)/sqrt 2 at resonance: the symmetric state has bright
+    weight 2/N, so P_+ = P_- = 1/N and P_D = 1 - 2/N; the antisymmetric one
+    is dark, P_D = 1 (only the S_12 terms of P_B tell them apart)."""
+    import oracle.bath as B
+
+    sa = orc.SA(N, 1, 2, B.high_t(0.01, 0.05, 0.025), 0.0, 0.05 / np.sqrt(N), 0.0, d=2)
+    ix = sa.rho0_index()
+    for sgn in (1.0, -1.0):
+        x = sa.zeros()
+        x[ix["P1"]] = x[ix["P2"]] = 0.5
+        x[ix["S12"]] = x[ix["S21"]] = 0.5 * sgn
+        o = sa.observables(x)
+        pb = 2.0 / N if sgn > 0 else 0.0
+        assert abs(o[0] - 1) < 1e-15 and abs(o[3] - pb) < 1e-15
+        assert abs(o[4] - (1 - pb)) < 1e-13
+        assert abs(o[5] - pb / 2) < 1e-15 and abs(o[6] - pb / 2) < 1e-15

@@ -59,6 +59,14 @@ def test_tables_bit_exact_distinguished(N, m, L):
     _check_tables(N, m, L, 1)
 
 
+@pytest.mark.parametrize("N,m,L,d", [(2, 1, 3, 2), (3, 2, 3, 2), (5, 2, 4, 2), (30, 1, 8, 2), (4, 3, 3, 2),
+                                     (3, 1, 3, 3), (6, 2, 3, 3), (40, 1, 6, 3), (3, 4, 2, 3)])
+def test_tables_bit_exact_several_distinguished(N, m, L, d):
+    """d = 2, 3 (Eq. N-symmetric-pool): molecule j's ids j V .. j V + V - 1
+    close every pattern in molecule order."""
+    _check_tables(N, m, L, d)
+
+
 def _check_tables(N, m, L, d):
     sa, lib = _pair(N, m, L, _generic_bath(m, N + 7 * m + L), detuning=0.1, g=0.2, kappa=0.05, d=d)
     assert lib.n_patterns == sa.npat and lib.n_vars == sa.nvar
@@ -116,7 +124,7 @@ def test_batch_offsets_and_counts():
         off += c["n_vars"]
     assert h.n_vars == off
     side = (off * 8 + 255) // 256 * 256
-    assert h.state_bytes == side + 12 * 16 * 16  # 16 FP64 slots per instance
+    assert h.state_bytes == side + 12 * 32 * 16  # 32 FP64 slots per instance
 
 
 def test_saturation_in_library():
@@ -129,8 +137,8 @@ def test_saturation_in_library():
     assert nvar[L] < nvar[L + 1] == nvar[-1]
 
 
-@pytest.mark.parametrize("bad", [dict(N=0), dict(m=0), dict(m=9), dict(L=-1), dict(L=31), dict(d=2), dict(d=-1),
-                                 dict(reserved=1)])
+@pytest.mark.parametrize("bad", [dict(N=0), dict(m=0), dict(m=9), dict(L=-1), dict(L=31), dict(d=4), dict(d=-1),
+                                 dict(N=2, d=3), dict(reserved=1)])
 def test_invalid_arguments_rejected(bad):
     args = dict(N=3, m=1, L=2, d=0, reserved=0)
     args.update(bad)
