@@ -5,7 +5,7 @@ The hot path -- the matrix-free unique-variable right-hand side fused into
 RK4 -- runs in the sm_103a kernels of ``libsaheom.so`` behind the C ABI of
 ``include/sa_heom.h``; :mod:`.binding` marshals arguments to it.
 """
-from .binding import (BATH_HIGH_T, BATH_MATSUBARA, BATH_PADE, SA_FP32_AUX, SA_FP64, SA_KERNEL_ELL, SA_KERNEL_LISTS, SA_KERNEL_RECORDS,
+from .binding import (MAXD, PHYS_SLOTS, BATH_HIGH_T, BATH_MATSUBARA, BATH_PADE, SA_FP32_AUX, SA_FP64, SA_KERNEL_ELL, SA_KERNEL_LISTS, SA_KERNEL_RECORDS,
                       Conventional, Heom, Params, SaHeomError, bath_drude_lorentz, bath_terminator, counts, lib,
                       make_params)
 from .problems import params_from, rho0_vars, theta

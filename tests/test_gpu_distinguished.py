@@ -1,10 +1,10 @@
-"""GPU parity with one distinguished molecule (d = 1, Sec. V.F): molecule 1
-keeps a category of its own in every pattern, so states that are not
-permutation-invariant -- the localised |e_1><e_1| (Eq. localized_initial_
-condition) and the cavity-site superposition -- propagate in the reduced
-hierarchy.  The kernels are the d = 0 kernels on the larger tables; the FP64
-physical-representative kernel, the observables and the initial state run
-over the physical pattern's two categories.
+"""GPU parity with distinguished molecules (Sec. V.F, Eq. N-symmetric-pool):
+molecules 1..d keep categories of their own in every pattern, so states that
+are not permutation-invariant -- the localised |e_1><e_1| (Eq. localized_
+initial_condition), the cavity-site superposition, (|e_1> + |e_2>)/sqrt 2 --
+propagate in the reduced hierarchy.  The kernels are the d = 0 kernels on the
+larger tables; the FP64 physical-representative kernel, the observables and
+the initial state run over the physical pattern's d + 1 categories.
 
 Tolerances as for d = 0: FP64 within 1e-11 relative of the FP64 oracle (1e-13
 for one right-hand side), FP32-aux right-hand side within 2e-6, FP32-aux
@@ -48,13 +48,17 @@ def _initial(sa, kind):
     """Physical representative of the localised state or of
     sqrt(0.3)|e_1> + sqrt(0.7)|c> (all hierarchy ADOs zero)."""
     ix = sa.rho0_index()
+    e1 = "d" if sa.d == 1 else "1"  # molecule 1's category
     x = sa.zeros()
     if kind == "localised":
-        x[ix["Pd"]] = 1.0
+        x[ix["P" + e1]] = 1.0
     else:
-        x[ix["Pd"]], x[ix["Z"]] = 0.3, 0.7
-        x[ix["Xd"]] = x[ix["Yd"]] = np.sqrt(0.21)
+        x[ix["P" + e1]], x[ix["Z"]] = 0.3, 0.7
+        x[ix["X" + e1]] = x[ix["Y" + e1]] = np.sqrt(0.21)
     return x
+
+
+D_MULTI = [(2, 1, 3, 2), (4, 2, 3, 2), (9, 1, 6, 2), (3, 1, 3, 3), (6, 2, 3, 3), (12, 1, 5, 3)]
 
 
 def _nphys(sa):
@@ -83,6 +87,50 @@ def test_rhs_fp32_distinguished(N, m, L, kernel):
     h.set_kernel(kernel)
     x = W.random_state(sa.nvar, seed=N * 100 + L).astype(np.complex64).astype(np.complex128)
     assert rel_err(_rhs_gpu(h, x), sa.rhs(x)) <= 2e-6
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("N,m,L,d", D_MULTI)
+def test_rhs_several_distinguished(N, m, L, d, kernel):
+    """d = 2, 3: one right-hand side, FP64 (1e-13) and FP32-aux (2e-6)."""
+    bath = _generic_bath(m, N + 7 * m + L + d)
+    kw = dict(detuning=0.1, g=0.2, kappa=0.05, term=0.011, d=d)
+    sa = oracle.SA(N, m, L, bath, **kw)
+    x = W.random_state(sa.nvar, seed=N * 100 + L + d)
+    h = S.Heom(S.make_params(N, m, L, bath, **kw))
+    h.set_kernel(kernel)
+    assert rel_err(_rhs_gpu(h, x), sa.rhs(x)) <= 1e-13
+    h = S.Heom(S.make_params(N, m, L, bath, **kw), precision=S.SA_FP32_AUX)
+    h.set_kernel(kernel)
+    xf = x.astype(np.complex64).astype(np.complex128)
+    assert rel_err(_rhs_gpu(h, xf), sa.rhs(xf)) <= 2e-6
+
+
+@pytest.mark.parametrize("precision", [S.SA_FP64, S.SA_FP32_AUX])
+def test_two_distinguished_propagation(precision):
+    """(|e_1> + |e_2>)/sqrt 2 with d = 2 (N = 8, two exponentials, L = 5):
+    at t = 0 on resonance P_+ = P_- = 1/N, P_D = 1 - 2/N; 1000 RK4 steps
+    against the oracle."""
+    N, L = 8, 5
+    bath = OB.matsubara(0.01, 0.05, 0.025, 1, 0.0)
+    kw = dict(detuning=0.0, g=0.05 / np.sqrt(N), kappa=0.004, term=0.001, d=2)
+    sa = oracle.SA(N, len(bath["c"]), L, bath, **kw)
+    ix = sa.rho0_index()
+    x0 = sa.zeros()
+    x0[ix["P1"]] = x0[ix["P2"]] = x0[ix["S12"]] = x0[ix["S21"]] = 0.5
+    y_or, obs_or = sa.propagate(x0, 0.02, 1000, 100)
+    h = S.Heom(S.make_params(N, len(bath["c"]), L, bath, **kw), precision=precision)
+    st = h.new_state()
+    h.init_physical(st, x0[:_nphys(sa)])
+    obs = h.propagate(st, 0.02, 1000, 100)
+    torch.cuda.synchronize()
+    assert abs(obs[0, 0, 5] - 1 / N) < 1e-14 and abs(obs[0, 0, 6] - 1 / N) < 1e-14
+    assert abs(obs[0, 0, 4] - (1 - 2 / N)) < 1e-14
+    if precision == S.SA_FP64:
+        assert rel_err(h.download(st), y_or) <= 1e-11
+        assert np.max(np.abs(obs[:, 0, :7] - obs_or[:, :7])) <= 1e-11
+    else:
+        assert np.max(np.abs(obs[:, 0, 1:7] - obs_or[:, 1:7])) <= 1e-5
 
 
 @pytest.mark.parametrize("kind", ["localised", "superposed"])
@@ -142,10 +190,10 @@ def test_localised_paper_size(precision, tol):
 
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_mixed_batch_matches_oracle(kernel):
-    """A batch with d = 0 and d = 1 instances (the d = 0 one started from its
-    own localised-free state through the same entry point): 40 RK4 steps of
-    every instance against its oracle, FP64."""
-    specs = [(5, 2, 4, 0), (9, 1, 5, 1), (3, 3, 3, 1), (1, 2, 4, 1)]
+    """A batch with d = 0 .. 3 instances, all started through
+    sa_heom_init_physical: 40 RK4 steps of every instance against its oracle,
+    FP64."""
+    specs = [(5, 2, 4, 0), (9, 1, 5, 1), (3, 3, 3, 1), (1, 2, 4, 1), (6, 1, 4, 2), (7, 2, 3, 3)]
     sas, ps, xs = [], [], []
     for i, (N, m, L, d) in enumerate(specs):
         b = _generic_bath(m, 40 + i)
@@ -157,7 +205,7 @@ def test_mixed_batch_matches_oracle(kernel):
     h = S.Heom(ps)
     h.set_kernel(kernel)
     st = h.new_state()
-    phys = np.zeros((len(sas), 16), complex)
+    phys = np.zeros((len(sas), S.PHYS_SLOTS), complex)
     for i, (sa, x) in enumerate(zip(sas, xs)):
         phys[i, :_nphys(sa)] = x[:_nphys(sa)]
     h.init_physical(st, phys)
