@@ -11,7 +11,7 @@ in HBM; the four state-sized vectors (~0.6 GB) exceed the 126 MB L2, so no
 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload w4|w5|w3]
+                  [--workload w4|w5|w3|sec5]
 
 Prints one JSON line (rank 0).  Under torchrun every rank runs its own copy
 of the batch (weak scaling, no data-path collective); the time is the max
@@ -142,8 +142,14 @@ def _params(workload):
     if workload == "w4":
         ws = W.batch_w4()
         return ws, [S.params_from(w) for w in ws], S.SA_FP32_AUX, 0.02
-    w = W.WORKLOADS[workload]
-    return [w], [S.params_from(w)], S.SA_FP32_AUX, w["dt"]
+    w = _single(workload)
+    return [w], [S.params_from(w)], S.SA_FP32_AUX, w["dt_fs"] if workload == "sec5" else w["dt"]
+
+
+def _single(workload):
+    """A one-instance workload: w3, w5, or the paper's production set (Sec. V:
+    N = 10^12, L = 25, one exponential plus the terminator, upper polariton)."""
+    return W.sec5(10 ** 12, "up") if workload == "sec5" else W.WORKLOADS[workload]
 
 
 def _rho0(ws):
@@ -162,7 +168,7 @@ def _oracle_sample(workload: str, budget_vars: int):
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     from tests._helpers import oracle_rho0, oracle_sa
 
-    ws = W.batch_w4() if workload == "w4" else [W.WORKLOADS[workload]]
+    ws = W.batch_w4() if workload == "w4" else [_single(workload)]
     sample, total = [], 0
     for w in ws:
         sa = oracle_sa(w, cache=True)
@@ -203,6 +209,8 @@ def _cpu_model() -> str:
 
 
 def _workload_name(workload: str) -> str:
+    if workload == "sec5":
+        return "sec5 (Sec. V production set: N = 10^12, L = 25, m = 1 + terminator, UP start, dt 0.5 fs)"
     return workload + (" (512 seeded instances, FP32-aux + FP64 rho_0)" if workload == "w4" else "")
 
 
@@ -417,7 +425,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="w4", choices=["w3", "w4", "w5"])
+    ap.add_argument("--workload", default="w4", choices=["w3", "w4", "w5", "sec5"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--err-steps", type=int, default=2000)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],

@@ -8,7 +8,7 @@ RK4 -- runs in the sm_103a kernels of ``libsaheom.so`` behind the C ABI of
 from .binding import (MAXD, PHYS_SLOTS, BATH_HIGH_T, BATH_MATSUBARA, BATH_PADE, SA_FP32_AUX, SA_FP64, SA_KERNEL_ELL, SA_KERNEL_LISTS, SA_KERNEL_RECORDS,
                       Conventional, Heom, Params, SaHeomError, bath_drude_lorentz, bath_terminator, counts, lib,
                       make_params)
-from .problems import params_from, rho0_vars, theta
+from .problems import in_library_units, params_from, phys_vars, rho0_vars, theta
 
 __all__ = ["Conventional", "Heom", "Params", "SaHeomError", "bath_drude_lorentz", "bath_terminator", "counts", "lib", "make_params", "params_from",
            "rho0_vars", "theta", "SA_FP64", "SA_FP32_AUX", "SA_KERNEL_RECORDS", "SA_KERNEL_LISTS", "SA_KERNEL_ELL", "BATH_HIGH_T", "BATH_MATSUBARA", "BATH_PADE"]

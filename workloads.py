@@ -23,6 +23,8 @@ Workloads
   w5  N=1000, m=4 (Drude-Lorentz + 3 Pade poles; lambda 0.03, gamma 0.02,
       kT 0.01), L=12, kappa 0.005, gsn 0.1, detuning 0.02; random
       permutation-invariant density matrix (seed 2608); dt 0.01 x 50000.
+  sec5(N, init, d)  the paper's own production set (Sec. V), in physical
+      units: energies in cm^-1, temperature in K, time in fs (see sec5).
 """
 from __future__ import annotations
 
@@ -45,6 +47,27 @@ WORKLOADS = {
     "w5": _w("w5_N1000_m4_L12", 1000, 12, "pade", 0.03, 0.02, 0.01, 3, 0.0, 0.1, 0.02, 0.005, "random", 0.01,
              50000, seed=SEED),
 }
+
+
+# Sec. V: the molecule numbers of Figs. 3-6 and the initial states of
+# Secs. V.A-V.F (up: upper polariton; localised: |e_1><e_1|; superposed:
+# sqrt(0.3)|e_1> + sqrt(0.7)|c>, the last two with molecule 1 distinguished)
+SEC5_N = (5, 10, 25, 100, 1000, 10 ** 12)
+
+
+def sec5(N: int, init: str = "up", d: int | None = None, steps: int = 4000) -> dict:
+    """The paper's production parameters (Sec. V): resonant cavity and
+    molecules (omega_cav = eps_x = 10000 cm^-1, so detuning 0), Rabi splitting
+    Omega_R = 500 cm^-1 at every N (g = Omega_R / (2 sqrt N)), Drude-Lorentz
+    bath lambda = 50 cm^-1, gamma = 18 cm^-1 at T = 300 K, one exponential per
+    local bath (the gamma pole) with every Matsubara term left to the
+    Ishizaki-Tanimura terminator, no cavity loss, depth L = 25, dt = 0.5 fs;
+    4000 steps reach the 2 ps of Figs. 5-6."""
+    if d is None:
+        d = 1 if init in ("localised", "superposed") else 0
+    return dict(name=f"sec5_N{N}_{init}", N=N, L=25, scheme="matsubara", poles=0, sigma=0.0, units="cm-1/fs",
+                lam_cm=50.0, gam_cm=18.0, T_K=300.0, omega_R_cm=500.0, detuning_cm=0.0, kappa_cm=0.0,
+                terminator=True, d=d, init=init, dt_fs=0.5, steps=steps)
 
 
 def batch_w4(count: int = 512, seed: int = SEED) -> list[dict]:
