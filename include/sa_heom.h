@@ -289,6 +289,34 @@ int sa_heom_init_state(const sa_heom* h, const double* rho0, void* d_state, void
 int sa_heom_init_physical(const sa_heom* h, const double* phys, void* d_state, void* stream);
 
 /*
+ * Arbitrary initial operators (Sec. IV, Eqs. Gt-linearity, Gt-covariance,
+ * reconstruct-ec, reconstruct-ee; Table tab:representative-initial-
+ * operators).  rho_S(t) of any initial operator A in the single-excitation
+ * manifold is a weighted sum of relabelled responses to five representative
+ * operators, each propagated in its own reduced hierarchy.
+ *
+ *   sa_heom_build_representatives: a batch handle of the representatives of
+ *     one d = 0 parameter set *p (d must be 0): instance 0 |c><c| (d = 0),
+ *     1 |e_1><c|, 2 |c><e_1|, 3 |e_1><e_1| (d = 1), 4 |e_1><e_2| (d = 2,
+ *     only for N >= 2).  Same precision and flags as sa_heom_build; the
+ *     handle takes every sa_heom_* call.
+ *   sa_heom_init_representatives: the factorised initial state of each
+ *     instance with its unit operator.  Asynchronous on `stream`.
+ *   sa_heom_reconstruct_dense: after any propagation of that state, writes
+ *     rho_S(t) = sum_ab A_ab G_t[|a><b|] for the dense initial operator
+ *     A = d_rho0 to d_rho_t.  Both are caller-owned device arrays of
+ *     (N+1)^2 complex128 (row-major, basis {c, e_1..e_N}, 16-byte aligned,
+ *     distinct); N + 1 <= 2^20.  A need not be Hermitian.  The handle keeps a
+ *     device workspace of about (3/256)(N+1)^2 complex values (allocated on
+ *     first use).  Reads A once in a partial-sum pass and once more with the
+ *     write of rho_S(t); repeatable bit for bit.  Asynchronous on `stream`.
+ *     SA_ERR_STATE if the handle is not a representatives handle.
+ */
+int sa_heom_build_representatives(const sa_params* p, int precision, int flags, sa_heom** out);
+int sa_heom_init_representatives(const sa_heom* h, void* d_state, void* stream);
+int sa_heom_reconstruct_dense(sa_heom* h, const void* d_state, const void* d_rho0, void* d_rho_t, void* stream);
+
+/*
  * sa_heom_state_upload / sa_heom_state_download -- copy a full state between
  * a host complex128 array in the canonical layout (n_vars_total complex
  * values) and a device state buffer, converting to / from the handle's

@@ -78,6 +78,9 @@ def lib() -> ctypes.CDLL:
             "sa_bath_terminator": [dbl, dbl, dbl, i32, P(dbl)],
             "sa_heom_counts": [P(Params), P(Counts)],
             "sa_heom_build": [P(Params), i32, i32, i32, P(vp)],
+            "sa_heom_build_representatives": [P(Params), i32, i32, P(vp)],
+            "sa_heom_init_representatives": [vp, vp, vp],
+            "sa_heom_reconstruct_dense": [vp, vp, vp, vp, vp],
             "sa_heom_info": [vp, i32, P(Counts)],
             "sa_heom_var_offset": [vp, i32, P(i64)],
             "sa_heom_dump_vectors": [vp, i32, vp],
@@ -129,7 +132,9 @@ def lib() -> ctypes.CDLL:
 
 
 def exported_symbols() -> list[str]:
-    return ["sa_bath_drude_lorentz", "sa_bath_terminator", "sa_heom_counts", "sa_heom_build", "sa_heom_destroy", "sa_heom_info",
+    return ["sa_bath_drude_lorentz", "sa_bath_terminator", "sa_heom_counts", "sa_heom_build",
+            "sa_heom_build_representatives", "sa_heom_init_representatives", "sa_heom_reconstruct_dense",
+            "sa_heom_destroy", "sa_heom_info",
             "sa_heom_var_offset", "sa_heom_dump_vectors", "sa_heom_dump_patterns", "sa_heom_dump_categories",
             "sa_heom_dump_terms", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_init_physical",
             "sa_heom_state_upload",
@@ -205,15 +210,26 @@ def counts(p: Params) -> dict:
 class Heom:
     """A built batch of instances (sa_heom handle)."""
 
-    def __init__(self, params, precision: int = SA_FP64, host_only: bool = False):
-        if isinstance(params, Params):
-            params = [params]
-        self.params = list(params)
-        arr = (Params * len(self.params))(*self.params)
+    def __init__(self, params, precision: int = SA_FP64, host_only: bool = False, representatives: bool = False):
+        """representatives: params is one d = 0 set; the handle is the batch of
+        its representative propagations (sa_heom_build_representatives)."""
+        flags = SA_BUILD_HOST_ONLY if host_only else SA_BUILD_DEVICE
         h = ctypes.c_void_p()
-        _check(lib().sa_heom_build(arr, len(self.params), precision,
-                                   SA_BUILD_HOST_ONLY if host_only else SA_BUILD_DEVICE, ctypes.byref(h)),
-               "sa_heom_build")
+        if representatives:
+            p = params[0] if isinstance(params, (list, tuple)) else params
+            _check(lib().sa_heom_build_representatives(ctypes.byref(p), precision, flags, ctypes.byref(h)),
+                   "sa_heom_build_representatives")
+            params = []
+            for d in ([0, 1, 1, 1, 2] if p.N >= 2 else [0, 1, 1, 1]):
+                q = Params.from_buffer_copy(p)
+                q.d = d
+                params.append(q)
+        else:
+            if isinstance(params, Params):
+                params = [params]
+            arr = (Params * len(params))(*params)
+            _check(lib().sa_heom_build(arr, len(params), precision, flags, ctypes.byref(h)), "sa_heom_build")
+        self.params = list(params)
         self._h = h
         self.count = len(self.params)
         self.precision = precision
@@ -299,6 +315,24 @@ class Heom:
         r[:, :ph.shape[1]] = ph
         flat = np.ascontiguousarray(r.view(np.float64).reshape(-1))
         _check(lib().sa_heom_init_physical(self._h, _ptr(flat), _dev(state), _stream(stream)), "sa_heom_init_physical")
+
+    def init_representatives(self, state, stream=None):
+        """sa_heom_init_representatives: each instance starts from its unit operator."""
+        _check(lib().sa_heom_init_representatives(self._h, _dev(state), _stream(stream)), "sa_heom_init_representatives")
+
+    def reconstruct_dense(self, state, rho0, out=None, stream=None):
+        """sa_heom_reconstruct_dense: rho_S(t) for the dense initial operator
+        rho0 ((N+1, N+1) complex128 torch tensor on the device) from the
+        representatives' current state; returns out (allocated if None)."""
+        import torch
+
+        assert rho0.dtype == torch.complex128 and rho0.is_contiguous()
+        if out is None:
+            out = torch.empty_like(rho0)
+        _check(lib().sa_heom_reconstruct_dense(self._h, _dev(state), ctypes.c_void_p(rho0.data_ptr()),
+                                               ctypes.c_void_p(out.data_ptr()), _stream(stream)),
+               "sa_heom_reconstruct_dense")
+        return out
 
     def upload(self, state, x: np.ndarray, stream=None):
         x = np.ascontiguousarray(x, np.complex128)

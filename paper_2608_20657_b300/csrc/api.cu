@@ -23,6 +23,10 @@ cudaError_t launch_observables(const InstDev* inst, const double* theta, int nin
                                double* out, cudaStream_t st);
 cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0, int stride, void* main64,
                              void* main32, void* side64, cudaStream_t st);
+size_t recon_workspace_bytes(int64_t n);
+cudaError_t launch_reconstruct(const InstDev* inst, const int16_t* loc, int nrep, const void* main64,
+                               const void* side64, const void* rho0, int64_t n, void* rho_t, void* ws,
+                               cudaStream_t st);
 }  // namespace sa
 
 using namespace sa;
@@ -123,6 +127,12 @@ struct sa_heom {
     size_t state_bytes = 0, side_off = 0;
     LaunchCfg cfg{256, 128, 1, 1, SA_KERNEL_LISTS};
     std::map<std::tuple<const void*, uint64_t, int64_t>, cudaGraphExec_t> graphs;
+    // representative propagations (sa_heom_build_representatives)
+    bool reps = false;
+    std::vector<int16_t> rep_loc;  // kReps x kRepSlots local indices in the physical pattern, -1: absent
+    void* d_rep_loc = nullptr;
+    void* d_recon_ws = nullptr;
+    size_t recon_ws = 0;
 };
 
 namespace {
@@ -696,7 +706,8 @@ void free_device(sa_heom* h) {
                     h->d_coef_row, h->d_coef_col, h->d_coef_row_d, h->d_coef_col_d, h->d_lut, h->d_lut_off,
                     h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0,
                     h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS, h->d_lvd, h->d_lvj, h->d_rbase,
-                    h->d_tidx, h->d_tcid, h->d_lcoef, h->d_wpat, h->d_blobs, h->d_catpat, h->d_sums};
+                    h->d_tidx, h->d_tcid, h->d_lcoef, h->d_wpat, h->d_blobs, h->d_catpat, h->d_sums,
+                    h->d_rep_loc, h->d_recon_ws};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -1269,6 +1280,93 @@ int sa_heom_init_physical(const sa_heom* hc, const double* phys, void* d_state, 
     if (rc) return rc;
     if (!phys || !d_state) return fail(SA_ERR_INVALID_ARG, "phys and d_state required");
     return init_from(h, phys, 2 * kSideSlots, d_state, stream);
+}
+
+// ---- arbitrary initial operators (Sec. IV, Table tab:representative-initial-operators)
+
+int sa_heom_build_representatives(const sa_params* p, int precision, int flags, sa_heom** out) {
+    if (!p || !out) return fail(SA_ERR_INVALID_ARG, "params and out required");
+    if (p->d != 0) return fail(SA_ERR_INVALID_ARG, "representatives are built from a d = 0 parameter set");
+    // |c><c| (d = 0), |e_1><c|, |c><e_1|, |e_1><e_1| (d = 1), |e_1><e_2| (d = 2, N >= 2)
+    const int count = p->N >= 2 ? kReps : kReps - 1;
+    sa_params ps[kReps];
+    const int dd[kReps] = {0, 1, 1, 1, 2};
+    for (int r = 0; r < count; ++r) {
+        ps[r] = *p;
+        ps[r].d = dd[r];
+    }
+    int rc = sa_heom_build(ps, count, precision, flags, out);
+    if (rc) return rc;
+    sa_heom* h = *out;
+    h->reps = true;
+    h->rep_loc.assign(size_t(kReps) * kRepSlots, int16_t(-1));
+    for (int r = 0; r < count; ++r) {
+        const HostInstance& hi = h->inst[r];
+        const int G = hi.G[0];
+        int16_t* L = &h->rep_loc[size_t(r) * kRepSlots];
+        auto put = [&](int slot, int64_t loc) { L[slot] = int16_t(loc); };
+        put(RZ, loc_Z());
+        for (int q = 1; q <= std::min(G, 3); ++q) {
+            put(RX1 + q - 1, loc_X(G, q));
+            put(RY1 + q - 1, loc_Y(G, q));
+            put(RP1 + q - 1, loc_P(G, q));
+        }
+        const int sq[6][2] = {{1, 2}, {1, 3}, {2, 1}, {2, 3}, {3, 1}, {3, 2}};
+        for (int k = 0; k < 6; ++k)
+            if (sq[k][0] <= G && sq[k][1] <= G) put(RS12 + k, loc_S(G, sq[k][0], sq[k][1]));
+        if (hi.h[0] >= 1) put(RT, loc_T(G, 0));  // only the others' category can hold two molecules
+    }
+    if (!h->host_only) {
+        cudaError_t e = cudaMalloc(&h->d_rep_loc, h->rep_loc.size() * sizeof(int16_t));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->d_rep_loc, h->rep_loc.data(), h->rep_loc.size() * sizeof(int16_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            sa_heom_destroy(h);
+            *out = nullptr;
+            return cuda_fail(e, "representative table");
+        }
+    }
+    return SA_OK;
+}
+
+int sa_heom_init_representatives(const sa_heom* hc, void* d_state, void* stream) {
+    sa_heom* h = const_cast<sa_heom*>(hc);
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!h->reps) return fail(SA_ERR_STATE, "not a representatives handle");
+    if (!d_state) return fail(SA_ERR_INVALID_ARG, "d_state required");
+    // the unit operator of each representative: Z, X_1, Y_1, P_1, S_12
+    std::vector<double> phys(size_t(2) * kSideSlots * h->count, 0.0);
+    const int slot[kReps] = {RZ, RX1, RY1, RP1, RS12};
+    for (int r = 0; r < h->count; ++r) phys[size_t(2) * kSideSlots * r + 2 * h->rep_loc[size_t(r) * kRepSlots + slot[r]]] = 1.0;
+    return init_from(h, phys.data(), 2 * kSideSlots, d_state, stream);
+}
+
+int sa_heom_reconstruct_dense(sa_heom* h, const void* d_state, const void* d_rho0, void* d_rho_t, void* stream) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!h->reps) return fail(SA_ERR_STATE, "not a representatives handle");
+    if (!d_state || !d_rho0 || !d_rho_t || d_rho0 == d_rho_t)
+        return fail(SA_ERR_INVALID_ARG, "d_state, d_rho0 and d_rho_t required, rho0 and rho_t distinct");
+    if ((reinterpret_cast<uintptr_t>(d_rho0) | reinterpret_cast<uintptr_t>(d_rho_t)) & 15)
+        return fail(SA_ERR_INVALID_ARG, "rho0 and rho_t must be 16-byte aligned");
+    const int64_t n = h->inst[0].N + 1;
+    // the output grid has (n / 32)^2 CTAs, at most 32768 per dimension
+    if (n > (int64_t(1) << 20)) return fail(SA_ERR_UNSUPPORTED, "dense output beyond N + 1 = 2^20");
+    const size_t need = recon_workspace_bytes(n);
+    if (need > h->recon_ws) {
+        if (h->d_recon_ws) cudaFree(h->d_recon_ws);
+        h->d_recon_ws = nullptr;
+        h->recon_ws = 0;
+        cudaError_t e = cudaMalloc(&h->d_recon_ws, need);
+        if (e != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(SA_ERR_OOM, "reconstruction workspace") : cuda_fail(e, "cudaMalloc");
+        h->recon_ws = need;
+    }
+    CK(launch_reconstruct(static_cast<const InstDev*>(h->d_inst), static_cast<const int16_t*>(h->d_rep_loc), h->count,
+                          h->precision == SA_FP64 ? d_state : nullptr, side(h, d_state), d_rho0, n, d_rho_t,
+                          h->d_recon_ws, static_cast<cudaStream_t>(stream)));
+    return SA_OK;
 }
 
 int sa_heom_state_upload(const sa_heom* h, const double* host_x, void* d_state, void* stream) {

@@ -16,6 +16,11 @@ constexpr int kMaxG = 31;            // categories per pattern (5-bit fields)
 constexpr int kCoefN = 32;           // occupation slots per channel in the coefficient table
 constexpr int kCoefPerInst = SA_HEOM_MAXM * kCoefN * 2;
 constexpr int kSideSlots = 32;       // FP64 slots of the physical representative per instance
+// representative propagations of arbitrary initial operators: |c><c|, |e_1><c|,
+// |c><e_1|, |e_1><e_1|, |e_1><e_2|, and the named variables of their physical
+// representatives (categories 1, 2, 3: molecule 1, molecule 2 or the others, the others)
+constexpr int kReps = 5, kRepSlots = 17;
+enum RepSlot { RZ, RX1, RX2, RX3, RY1, RY2, RY3, RP1, RP2, RP3, RS12, RS13, RS21, RS23, RS31, RS32, RT };
 
 // ---- one hierarchy connection record ---------------------------------------
 // A record belongs to (pattern Lambda, category q, channel k, direction): the
