@@ -18,11 +18,21 @@
 //     + (r_b - A_ba) S31 + (s_b - A_ab) S32 + (O - r_a - s_a - r_b - s_b + A_ab + A_ba) T
 // with S_qr, T the d = 2 response's variables (category 3 = the others).
 //
-// Kernels (FP64, HBM-bound): a tile pass of row / column partial sums, two
-// small passes finishing the per-index vectors and the four totals (fixed
-// summation order: the result is bitwise repeatable), and the output pass,
-// one CTA per symmetric pair of 32 x 32 tiles so that A is read once and
-// rho_S(t) written once.
+// For molecules a != b the entry separates as
+//     rho_ab(t) = alpha_a + beta_b + c1 A_ab + c2 A_ba
+// (alpha_a from a's aggregates and the constant terms, beta_b from b's), so
+// the bulk of the output costs two complex FMAs per entry: on B300, whose
+// FP64 rate is about 2 operations per clock per SM, a general form of ~100
+// FP64 operations per entry would bound the kernel by the FP64 pipe, not by
+// HBM.
+//
+// Kernels (FP64): a tile pass of row / column partial sums (a butterfly
+// reduce-scatter gives each lane one row's sum, about one add per element and
+// component), two small passes finishing the per-index vectors and the four
+// totals (fixed summation order: the result is bitwise repeatable), a
+// per-index pass for alpha, beta and the cavity row, cavity column and
+// diagonal (general form), and the bulk pass, one CTA per symmetric pair of
+// 32 x 32 tiles so that A is read once there and rho_S(t) written once.
 #include "sa_internal.h"
 
 namespace sa {
@@ -63,7 +73,9 @@ __global__ void gather_responses_kernel(const InstDev* __restrict__ inst, const 
 
 // per tile (kRB rows x kCB columns): row partial sums rowpart[tile col][row]
 // and column partial sums colpart[tile row][col] of the molecular block
-// without its diagonal
+// without its diagonal.  Each warp owns 32 columns and takes 32 rows at a
+// time: every lane sums its column, then a butterfly reduce-scatter leaves
+// in lane l the sum of row l over the warp's columns.
 __global__ void __launch_bounds__(kCB) recon_partials_kernel(const double2* __restrict__ A, int64_t n,
                                                              double2* __restrict__ rowpart,
                                                              double2* __restrict__ colpart) {
@@ -72,18 +84,30 @@ __global__ void __launch_bounds__(kCB) recon_partials_kernel(const double2* __re
     const int64_t i0 = int64_t(blockIdx.y) * kRB;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double2 cs = d2(0.0, 0.0);
-    for (int k = 0; k < kRB; ++k) {
-        const int64_t i = i0 + k;
-        double2 a = d2(0.0, 0.0);
-        if (i < n && j < n && i >= 1 && j >= 1 && i != j) a = __ldg(A + i * n + j);
-        cs = add(cs, a);
-        double rx = a.x, ry = a.y;
+    for (int c = 0; c < kRB / 32; ++c) {
+        double2 v[32];
 #pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            rx += __shfl_xor_sync(0xffffffffu, rx, o);
-            ry += __shfl_xor_sync(0xffffffffu, ry, o);
+        for (int k = 0; k < 32; ++k) {
+            const int64_t i = i0 + c * 32 + k;
+            v[k] = (i < n && j < n && i >= 1 && j >= 1 && i != j) ? __ldg(A + i * n + j) : d2(0.0, 0.0);
         }
-        if (lane == 0) red[k][warp] = d2(rx, ry);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) cs = add(cs, v[k]);
+        // reduce-scatter: at width w a lane keeps the upper half of its rows
+        // when bit w of its lane index is set, and adds its partner's copy
+#pragma unroll
+        for (int w = 16; w >= 1; w >>= 1) {
+            const bool up = (lane & w) != 0;
+#pragma unroll
+            for (int k = 0; k < w; ++k) {
+                const double2 send = up ? v[k] : v[k + w];
+                const double2 keep = up ? v[k + w] : v[k];
+                const double rx = __shfl_xor_sync(0xffffffffu, send.x, w);
+                const double ry = __shfl_xor_sync(0xffffffffu, send.y, w);
+                v[k] = d2(keep.x + rx, keep.y + ry);
+            }
+        }
+        red[c * 32 + lane][warp] = v[0];
     }
     __syncthreads();
     if (threadIdx.x < kRB) {
@@ -217,36 +241,86 @@ __device__ __forceinline__ double2 recon_entry(int64_t a, int64_t b, double2 Aab
     return out;
 }
 
-// one CTA per tile pair {(I, J), (J, I)}, I <= J: both tiles of A staged in
-// shared memory, both output tiles written with coalesced rows
-__global__ void __launch_bounds__(kT * 8, 2) recon_output_kernel(const double2* __restrict__ A, int64_t n,
+// c1, c2 of the separated form: the |e_1><e_2| response's weights of A_ab, A_ba
+__device__ __forceinline__ void sep_consts(const double2* Rw, double2& c1, double2& c2) {
+    c1 = add(sub(sub(Rw[RS12], Rw[RS13]), Rw[RS32]), Rw[RT]);
+    c2 = add(sub(sub(Rw[RS21], Rw[RS23]), Rw[RS31]), Rw[RT]);
+}
+
+// per index k: alpha_k and beta_k of the separated form, and the entries
+// (0, k), (k, 0), (k, k) in the general form
+__global__ void __launch_bounds__(256) recon_edges_kernel(const double2* __restrict__ A, int64_t n,
+                                                          const double2* __restrict__ resp,
+                                                          const double2* __restrict__ tot,
+                                                          const double2* __restrict__ rv,
+                                                          const double2* __restrict__ sv,
+                                                          double2* __restrict__ alpha, double2* __restrict__ beta,
+                                                          double2* __restrict__ B) {
+    __shared__ double2 R[kReps * kRepSlots];
+    __shared__ double2 T4[4];
+    for (int t = threadIdx.x; t < kReps * kRepSlots; t += blockDim.x) R[t] = resp[t];
+    if (threadIdx.x < 4) T4[threadIdx.x] = tot[threadIdx.x];
+    __syncthreads();
+    const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double2 Acc = __ldg(A);
+    const Agg z{d2(0.0, 0.0), d2(0.0, 0.0), d2(0.0, 0.0), d2(0.0, 0.0), d2(0.0, 0.0)};
+    if (k == 0) {
+        B[0] = recon_entry(0, 0, Acc, Acc, z, z, R, T4, Acc);
+        alpha[0] = beta[0] = d2(0.0, 0.0);
+        return;
+    }
+    Agg g;
+    g.u = __ldg(A + k * n);
+    g.v = __ldg(A + k);
+    g.p = __ldg(A + k * n + k);
+    g.r = rv[k];
+    g.s = sv[k];
+    B[k] = recon_entry(0, k, g.v, g.u, z, g, R, T4, Acc);          // (c, e_k)
+    B[k * n] = recon_entry(k, 0, g.u, g.v, g, z, R, T4, Acc);      // (e_k, c)
+    B[k * n + k] = recon_entry(k, k, g.p, g.p, g, g, R, T4, Acc);  // (e_k, e_k)
+    const double2* Rc = R;
+    const double2* Rw = R + 4 * kRepSlots;
+    const double2 U = T4[0], V = T4[1], P = T4[2], O = T4[3];
+    const double2 w[3] = {g.u, g.v, g.p}, W[3] = {U, V, P};
+    // the constant terms go into alpha
+    double2 a = fma2(Acc, Rc[RT], d2(0.0, 0.0));
+    a = fma2(O, Rw[RT], a);
+    double2 b = d2(0.0, 0.0);
+    for (int q = 0; q < 3; ++q) {
+        const double2* R1 = R + (1 + q) * kRepSlots;
+        a = fma2(W[q], R1[RT], a);
+        a = fma2(w[q], sub(R1[RS12], R1[RT]), a);
+        b = fma2(w[q], sub(R1[RS21], R1[RT]), b);
+    }
+    a = fma2(g.r, sub(Rw[RS13], Rw[RT]), a);
+    a = fma2(g.s, sub(Rw[RS23], Rw[RT]), a);
+    b = fma2(g.r, sub(Rw[RS31], Rw[RT]), b);
+    b = fma2(g.s, sub(Rw[RS32], Rw[RT]), b);
+    alpha[k] = a;
+    beta[k] = b;
+}
+
+// entries (a, b), a != b molecules: one CTA per tile pair {(I, J), (J, I)},
+// I <= J, both tiles of A staged in shared memory, both output tiles written
+// with coalesced rows
+__global__ void __launch_bounds__(kT * 8) recon_output_kernel(const double2* __restrict__ A, int64_t n,
                                                              const double2* __restrict__ resp,
-                                                             const double2* __restrict__ tot,
-                                                             const double2* __restrict__ rv,
-                                                             const double2* __restrict__ sv,
+                                                             const double2* __restrict__ alpha,
+                                                             const double2* __restrict__ beta,
                                                              double2* __restrict__ B) {
     const int64_t I = blockIdx.y, J = blockIdx.x;
     if (I > J) return;
     __shared__ double2 sA[kT][kT + 1];  // A(I-tile rows, J-tile cols)
     __shared__ double2 sB[kT][kT + 1];  // A(J-tile rows, I-tile cols)
-    __shared__ double2 R[kReps * kRepSlots];
-    __shared__ double2 T4[4];
-    __shared__ Agg gI[kT], gJ[kT];
+    __shared__ double2 aI[kT], bI[kT], aJ[kT], bJ[kT];
     const int tx = threadIdx.x % kT, ty = threadIdx.x / kT;  // 32 x 8
     const int64_t i0 = I * kT, j0 = J * kT;
-    for (int t = threadIdx.x; t < kReps * kRepSlots; t += blockDim.x) R[t] = resp[t];
-    if (threadIdx.x < 4) T4[threadIdx.x] = tot[threadIdx.x];
-    for (int k = threadIdx.x; k < 2 * kT; k += blockDim.x) {
-        const int64_t m = (k < kT ? i0 : j0) + (k % kT);
-        Agg g{d2(0.0, 0.0), d2(0.0, 0.0), d2(0.0, 0.0), d2(0.0, 0.0), d2(0.0, 0.0)};
-        if (m >= 1 && m < n) {
-            g.u = __ldg(A + m * n);
-            g.v = __ldg(A + m);
-            g.p = __ldg(A + m * n + m);
-            g.r = rv[m];
-            g.s = sv[m];
-        }
-        (k < kT ? gI : gJ)[k % kT] = g;
+    if (threadIdx.x < 4 * kT) {
+        const int q = threadIdx.x / kT, t = threadIdx.x % kT;
+        const int64_t m = (q < 2 ? i0 : j0) + t;
+        const double2 val = m < n ? ((q & 1) ? beta[m] : alpha[m]) : d2(0.0, 0.0);
+        (q == 0 ? aI : q == 1 ? bI : q == 2 ? aJ : bJ)[t] = val;
     }
     for (int yy = ty; yy < kT; yy += 8) {
         const int64_t ra = i0 + yy, ca = j0 + tx;
@@ -256,25 +330,29 @@ __global__ void __launch_bounds__(kT * 8, 2) recon_output_kernel(const double2* 
             sB[yy][tx] = (rb < n && cb < n) ? __ldg(A + rb * n + cb) : d2(0.0, 0.0);
         }
     }
+    double2 c1, c2;
+    sep_consts(resp + 4 * kRepSlots, c1, c2);
     __syncthreads();
-    const double2 Acc = __ldg(A);
     // tile (I, J): entry (a, b) = (i0 + yy, j0 + tx); A_ba lies in sB (or sA when I == J)
     for (int yy = ty; yy < kT; yy += 8) {
         const int64_t a = i0 + yy, b = j0 + tx;
-        if (a < n && b < n) {
-            const double2 Aab = sA[yy][tx];
+        if (a >= 1 && b >= 1 && a != b && a < n && b < n) {
             const double2 Aba = (I == J) ? sA[tx][yy] : sB[tx][yy];
-            B[a * n + b] = recon_entry(a, b, Aab, Aba, gI[yy], gJ[tx], R, T4, Acc);
+            double2 o = add(aI[yy], bJ[tx]);
+            o = fma2(c1, sA[yy][tx], o);
+            o = fma2(c2, Aba, o);
+            B[a * n + b] = o;
         }
     }
     if (I == J) return;
     // tile (J, I): entry (a, b) = (j0 + yy, i0 + tx)
     for (int yy = ty; yy < kT; yy += 8) {
         const int64_t a = j0 + yy, b = i0 + tx;
-        if (a < n && b < n) {
-            const double2 Aab = sB[yy][tx];
-            const double2 Aba = sA[tx][yy];
-            B[a * n + b] = recon_entry(a, b, Aab, Aba, gJ[yy], gI[tx], R, T4, Acc);
+        if (a >= 1 && b >= 1 && a != b && a < n && b < n) {
+            double2 o = add(aJ[yy], bI[tx]);
+            o = fma2(c1, sB[yy][tx], o);
+            o = fma2(c2, sA[tx][yy], o);
+            B[a * n + b] = o;
         }
     }
 }
@@ -283,8 +361,8 @@ __global__ void __launch_bounds__(kT * 8, 2) recon_output_kernel(const double2* 
 
 size_t recon_workspace_bytes(int64_t n) {
     const int64_t ncb = (n + kCB - 1) / kCB, nrb = (n + kRB - 1) / kRB, nblk = (n + 255) / 256;
-    // rowpart, colpart, r, s, block totals, totals, responses
-    return size_t(16) * size_t(ncb * n + nrb * n + 2 * n + 4 * nblk + 4 + kReps * kRepSlots);
+    // rowpart, colpart, r, s, alpha, beta, block totals, totals, responses
+    return size_t(16) * size_t(ncb * n + nrb * n + 4 * n + 4 * nblk + 4 + kReps * kRepSlots);
 }
 
 cudaError_t launch_reconstruct(const InstDev* inst, const int16_t* loc, int nrep, const void* main64,
@@ -296,7 +374,9 @@ cudaError_t launch_reconstruct(const InstDev* inst, const int16_t* loc, int nrep
     double2* colpart = rowpart + ncb * n;
     double2* r = colpart + nrb * n;
     double2* s = r + n;
-    double2* blocktot = s + n;
+    double2* alpha = s + n;
+    double2* beta = alpha + n;
+    double2* blocktot = beta + n;
     double2* tot = blocktot + 4 * nblk;
     double2* resp = tot + 4;
     const double2* A = static_cast<const double2*>(rho0);
@@ -305,8 +385,10 @@ cudaError_t launch_reconstruct(const InstDev* inst, const int16_t* loc, int nrep
     recon_partials_kernel<<<dim3(unsigned(ncb), unsigned(nrb)), kCB, 0, st>>>(A, n, rowpart, colpart);
     recon_vectors_kernel<<<unsigned(nblk), 256, 0, st>>>(A, n, rowpart, int(ncb), colpart, int(nrb), r, s, blocktot);
     recon_totals_kernel<<<1, 256, 0, st>>>(blocktot, int(nblk), tot);
+    double2* Bt = static_cast<double2*>(rho_t);
+    recon_edges_kernel<<<unsigned(nblk), 256, 0, st>>>(A, n, resp, tot, r, s, alpha, beta, Bt);
     const unsigned nt = unsigned((n + kT - 1) / kT);
-    recon_output_kernel<<<dim3(nt, nt), kT * 8, 0, st>>>(A, n, resp, tot, r, s, static_cast<double2*>(rho_t));
+    recon_output_kernel<<<dim3(nt, nt), kT * 8, 0, st>>>(A, n, resp, alpha, beta, Bt);
     return cudaGetLastError();
 }
 
