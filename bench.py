@@ -399,6 +399,9 @@ def run_ours(args):
                                        "fp64_single_instance": ms_single * 10000 / 1e3, "steps": 10000},
                  "fp32_max_population_error_vs_fp64": err, "population_error_window_steps": nerr}
 
+    if rank == 0 and not args.no_reconstruct:
+        extra["reconstruct"] = _time_reconstruct(S, torch, stream)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -419,6 +422,48 @@ def run_ours(args):
     return 0
 
 
+def _time_reconstruct(S, torch, stream, n: int = 8192, reps: int = 10) -> dict:
+    """Arbitrary initial operators (sa_heom_reconstruct_dense): the five
+    representative propagations of an N = n - 1 instance (one exponential,
+    L = 2, 20 steps), then the dense reconstruction of a seeded random
+    operator, timed with CUDA events over `reps` calls.  Algorithmic bytes:
+    A read twice and rho_S(t) written once, 48 per entry; FP64 work about 14
+    operations per entry (2 complex FMAs in the bulk pass, ~4 adds per
+    element in the partial sums)."""
+    bath = {"c": np.array([0.3 + 0.05j]), "cc": np.array([0.3 - 0.05j]), "nu": np.array([0.6 + 0j])}
+    h = S.Heom(S.make_params(n - 1, 1, 2, bath, g=0.01), representatives=True)
+    st = h.new_state()
+    h.init_representatives(st, stream)
+    h.propagate(st, 0.05, 20, observe=False, stream=stream)
+    gen = torch.Generator(device="cuda").manual_seed(2608)
+    a = torch.randn(n, n, dtype=torch.complex128, device="cuda", generator=gen)
+    out = torch.empty_like(a)
+    for _ in range(3):
+        h.reconstruct_dense(st, a, out, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        h.reconstruct_dense(st, a, out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    gbs = 48.0 * n * n / (ms * 1e-3) / 1e9
+    peak, peak_src = _peaks()
+    # FP64 issue rate: 2 operations per clock per SM at the maximum SM clock
+    mhz = 2032.0
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        mhz = float(json.load(open(pp)).get("sm_max_mhz", mhz))
+    props = torch.cuda.get_device_properties(0)
+    fp64_ops = 2.0 * props.multi_processor_count * mhz * 1e6
+    out_ok = bool(torch.isfinite(out).all())
+    del a, out, h, st
+    return {"n": n, "ms_per_call": ms, "algorithmic_gbs": gbs, "hbm_frac": gbs / peak, "hbm_peak_source": peak_src,
+            "bound": "alu (fp64)", "fp64_ops_per_entry": 14, "fp64_frac": 14.0 * n * n / (ms * 1e-3) / fp64_ops,
+            "finite": out_ok}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,6 +478,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-reconstruct", action="store_true")
     ap.add_argument("--tune", default="", help="block,chunk,queue[,kernel] (skips the autotuner; kernel 0 = "
                                                 "connection records, 1 = term lists)")
     args = ap.parse_args()
