@@ -782,3 +782,21 @@ def test_two_distinguished_initial_populations(orc, N):
         assert abs(o[0] - 1) < 1e-15 and abs(o[3] - pb) < 1e-15
         assert abs(o[4] - (1 - pb)) < 1e-13
         assert abs(o[5] - pb / 2) < 1e-15 and abs(o[6] - pb / 2) < 1e-15
+
+
+@pytest.mark.parametrize("N,m,L", [(1, 1, 4), (2, 1, 3), (2, 2, 3), (3, 1, 3), (3, 2, 2)])
+def test_all_molecules_distinguished_is_conventional(orc, N, m, L):
+    """d = N leaves no permutation symmetry (Eq. N-symmetric-pool with an
+    empty pool): every pattern is one ADO label, every molecule its own
+    category, so the reduced hierarchy is the conventional one entry for
+    entry -- C(Nm+L, L) patterns of (N+1)^2 variables, the map a bijection."""
+    bath = _bath_generic(m, seed=3 * N + m + L)
+    kw = dict(detuning=0.05, g=0.2, kappa=0.02, term=0.01)
+    sa = orc.SA(N, m, L, bath, d=N, **kw)
+    cv = orc.Conventional(N, m, L, bath, **kw)
+    assert sa.npat == cv.nado and sa.nvar == cv.nado * (N + 1) ** 2
+    mp = cv.map_to(sa)
+    assert np.array_equal(np.sort(mp.ravel()), np.arange(sa.nvar))
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(sa.nvar) + 1j * rng.standard_normal(sa.nvar)
+    assert np.abs(cv.rhs(x[mp]) - sa.rhs(x)[mp]).max() <= 1e-13 * np.abs(sa.rhs(x)).max()
