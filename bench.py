@@ -464,6 +464,65 @@ def _time_reconstruct(S, torch, stream, n: int = 8192, reps: int = 10) -> dict:
             "finite": out_ok}
 
 
+def run_conv_scaling(args):
+    """The conventional GPU hierarchy against the symmetry-adapted one as N
+    grows (the config-2 family: DL + 1 Matsubara pole, L = 6, g sqrt(N) =
+    0.05, bright start), FP64 both: ms per RK4 step, the two state sizes, and
+    the population agreement after the same steps.  Prints one JSON line."""
+    import torch
+
+    import paper_2608_20657_b300 as S
+
+    rank, _ = _dist()
+    if rank != 0:
+        return 0
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for N in [int(v) for v in args.conv_n.split(",")]:
+        w = dict(W.WORKLOADS["w2"], N=N)
+        p = S.params_from(w)
+        dt, k = w["dt"], 5
+        t0 = time.perf_counter()
+        cv = S.Conventional(p)
+        t_build = time.perf_counter() - t0
+        st = cv.new_state()
+        rho = np.zeros((N + 1, N + 1), complex)
+        rho[1:, 1:] = 1.0 / N  # |B><B|
+        cv.set_rho0(st, rho)
+        cv.step(st, dt, 2, stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        cv.step(st, dt, k, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_conv = e0.elapsed_time(e1) / k
+        rho_t = st[: (N + 1) ** 2 * 16].view(torch.float64).cpu().numpy().view(np.complex128).reshape(N + 1, N + 1)
+        conv_bytes, nado = cv.state_bytes, cv.nado
+        del cv, st
+        h = S.Heom(p)
+        s2 = h.new_state()
+        h.init_state(s2, S.rho0_vars(w))
+        h.propagate(s2, dt, 2, observe=False)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h.propagate(s2, dt, k, observe=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_sa = e0.elapsed_time(e1) / k
+        o = h.observables(s2)[0]
+        rows.append({"N": N, "conventional_ados": nado, "conventional_bytes": conv_bytes,
+                     "conventional_ms_per_step": ms_conv, "conventional_build_s": t_build,
+                     "sa_vars": h.n_vars, "sa_bytes": h.n_vars * 16, "sa_ms_per_step": ms_sa,
+                     "speedup": ms_conv / ms_sa,
+                     "pop_diff": float(max(abs(o[1] - rho_t[0, 0].real),
+                                           abs(o[2] - (np.trace(rho_t).real - rho_t[0, 0].real))))})
+        del h, s2
+    print(json.dumps({"conv_scaling": rows, "workload": "w2 family (DL + 1 Matsubara, L = 6), FP64, bright start",
+                      "steps_timed": 5}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -479,11 +538,16 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-reconstruct", action="store_true")
+    ap.add_argument("--conv-scaling", action="store_true",
+                    help="time the conventional against the symmetry-adapted hierarchy over --conv-n, then exit")
+    ap.add_argument("--conv-n", default="2,4,6,8,10,12")
     ap.add_argument("--tune", default="", help="block,chunk,queue[,kernel] (skips the autotuner; kernel 0 = "
                                                 "connection records, 1 = term lists)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.conv_scaling:
+        return run_conv_scaling(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -468,8 +468,10 @@ int sa_heom_observables_noalloc(sa_heom* h, const void* d_state, double* out, vo
  * (Eq. direct-ado-count, lexicographic order, the zero label first), every
  * ADO a dense (N+1) x (N+1) complex matrix (Eq. basis), right-hand side
  * Eq. scaled-HEOM with the same cavity loss, classical RK4.
- *   sa_conv_build:   tables for one instance (N <= 64, at most 4 GB per state
- *                    vector); allocates three RK4 work vectors.
+ *   sa_conv_build:   tables for one instance (N <= 64, at most 16 GB per
+ *                    state vector); allocates three RK4 work vectors.  The
+ *                    host build hashes every label once per channel and
+ *                    direction: seconds at a million ADOs.
  *   sa_conv_info:    number of ADOs and bytes of one state vector
  *                    (double2[n_ados * (N+1)^2], ADO-major, row-major).
  *   sa_conv_labels:  n_ados * N * m occupations (molecule-major).

@@ -115,12 +115,13 @@ int sa_conv_build(const sa_params* p, sa_conv** out) {
     for (int k = 0; k < p->m; ++k)
         if (!(std::sqrt(p->c_re[k] * p->c_re[k] + p->c_im[k] * p->c_im[k]) > 0.0))
             return cfail(SA_ERR_INVALID_ARG, "|c_k| = 0");
-    // the label count C(Nm + L, L) must stay modest
+    // the label count C(Nm + L, L) must stay modest: four state vectors (the
+    // caller's and three RK4 work vectors) of at most 16 GB each
     const double lg = std::lgamma(double(p->N * p->m + p->L) + 1) - std::lgamma(double(p->L) + 1) -
                       std::lgamma(double(p->N * p->m) + 1);
     const double D = double(p->N + 1);
-    if (lg > std::log(5.0e8) || std::exp(lg) * D * D * 16.0 > 4.0e9)
-        return cfail(SA_ERR_UNSUPPORTED, "conventional hierarchy too large (more than 4 GB per state vector)");
+    if (lg > std::log(5.0e8) || std::exp(lg) * D * D * 16.0 > 16.0e9)
+        return cfail(SA_ERR_UNSUPPORTED, "conventional hierarchy too large (more than 16 GB per state vector)");
     sa_conv* c = new sa_conv();
     c->p = *p;
     c->N = int(p->N);
