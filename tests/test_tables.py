@@ -165,3 +165,42 @@ def test_host_only_handle_refuses_device_calls():
     with pytest.raises(S.SaHeomError) as e:
         h.step(0, 0.1, stream=0)
     assert e.value.code == -7
+
+
+def test_representatives_handle_structure():
+    """sa_heom_build_representatives: the five representative hierarchies of
+    one parameter set (Table tab:representative-initial-operators) as a batch
+    with d = 0, 1, 1, 1, 2 -- four for N = 1 -- each instance the same tables
+    as a stand-alone build with that d; d != 0 in the input is refused."""
+    bath = _generic_bath(2, 5)
+    for N in (1, 2, 7):
+        p = S.make_params(N, 2, 3, bath, detuning=0.1, g=0.2, kappa=0.01, term=0.002)
+        h = S.Heom(p, host_only=True, representatives=True)
+        ds = [0, 1, 1, 1, 2] if N >= 2 else [0, 1, 1, 1]
+        assert h.count == len(ds) and [q.d for q in h.params] == ds
+        for i, d in enumerate(ds):
+            c = S.counts(S.make_params(N, 2, 3, bath, detuning=0.1, g=0.2, kappa=0.01, term=0.002, d=d))
+            assert h.info(i)["n_vars"] == c["n_vars"] and h.info(i)["n_patterns"] == c["n_patterns"]
+            a = h.dump_patterns(i)
+            sa = oracle.SA(N, 2, 3, bath, 0.1, 0.2, 0.01, term=0.002, d=d)
+            b = sa.patterns()
+            assert np.array_equal(a["ids"], b["ids"]) and np.array_equal(a["var_off"], b["var_off"])
+    with pytest.raises(S.SaHeomError) as e:
+        S.Heom(S.make_params(3, 2, 3, bath, d=1), host_only=True, representatives=True)
+    assert e.value.code == -1
+
+
+def test_new_entry_points_refuse_host_only_handles():
+    """sa_heom_init_physical, sa_heom_init_representatives and
+    sa_heom_reconstruct_dense need a device handle (SA_ERR_STATE, -7);
+    reconstruction also needs a representatives handle."""
+    import ctypes
+
+    bath = _generic_bath(1, 2)
+    h = S.Heom(S.make_params(3, 1, 2, bath), host_only=True, representatives=True)
+    L = S.lib()
+    buf = np.zeros(2 * S.PHYS_SLOTS * h.count)
+    assert L.sa_heom_init_physical(h._h, buf.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(16), None) == -7
+    assert L.sa_heom_init_representatives(h._h, ctypes.c_void_p(16), None) == -7
+    assert L.sa_heom_reconstruct_dense(h._h, ctypes.c_void_p(16), ctypes.c_void_p(32), ctypes.c_void_p(48),
+                                       None) == -7
