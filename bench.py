@@ -466,7 +466,7 @@ def _time_reconstruct(S, torch, stream, n: int = 8192, reps: int = 10) -> dict:
 
 def run_conv_scaling(args):
     """The conventional GPU hierarchy against the symmetry-adapted one as N
-    grows (the config-2 family: DL + 1 Matsubara pole, L = 6, g sqrt(N) =
+    grows (the w2 family: DL + 1 Matsubara pole, L = 6, g sqrt(N) =
     0.05, bright start), FP64 both: ms per RK4 step, the two state sizes, and
     the population agreement after the same steps.  Prints one JSON line."""
     import torch
