@@ -23,7 +23,7 @@ def test_unit_constants():
     assert abs(u["kT"] / f - kT_cm) < 1e-9
 
 
-@pytest.mark.parametrize("N", W.SEC5_N)
+@pytest.mark.parametrize("N", (1, 2, 3) + W.SEC5_N)
 @pytest.mark.parametrize("init", ["up", "localised", "superposed"])
 def test_params_agree_with_oracle(N, init):
     """The product's sa_params (bath through sa_bath_drude_lorentz, Delta
