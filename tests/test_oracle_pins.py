@@ -800,3 +800,33 @@ def test_all_molecules_distinguished_is_conventional(orc, N, m, L):
     rng = np.random.default_rng(9)
     x = rng.standard_normal(sa.nvar) + 1j * rng.standard_normal(sa.nvar)
     assert np.abs(cv.rhs(x[mp]) - sa.rhs(x)[mp]).max() <= 1e-13 * np.abs(sa.rhs(x)).max()
+
+
+@pytest.mark.parametrize("N", [2, 5, 40])
+def test_distinguished_localised_L0_closed_form(orc, N):
+    """L = 0 (no bath), resonance, d = 1: RK4 is exact on each eigen-
+    component of the Liouvillian, so rho(t_n) = sum_ab a_a a_b* |a><b|
+    R(-i (E_a - E_b) dt)^n with R(z) = 1 + z + z^2/2 + z^3/6 + z^4/24.  For
+    |e_1> the components are the polaritons (E = +- g sqrt N, weight 1/(2N)
+    each) and the dark part (E = 0, weight 1 - 1/N); the molecule-1
+    population P_11 and the cavity population follow in closed form."""
+    import oracle.bath as B
+
+    g, dt, n = 0.05 / np.sqrt(N), 0.05, 300
+    sa = orc.SA(N, 1, 0, B.high_t(0.01, 0.05, 0.025), 0.0, g, 0.0, d=1)
+    x = sa.zeros()
+    x[sa.rho0_index()["Pd"]] = 1.0
+    y = sa.rk4(x, dt, n)
+    R = lambda z: 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+    w = g * np.sqrt(N)
+    # <e_1|UP> = <e_1|LP> = 1/sqrt(2N); <e_1|dark part> = 1 - 1/N; <c|UP> = -<c|LP> = 1/sqrt 2
+    E = {"U": w, "L": -w, "D": 0.0}
+    a = {"U": 1 / np.sqrt(2 * N), "L": 1 / np.sqrt(2 * N), "D": None}
+    e1 = {"U": 1 / np.sqrt(2 * N), "L": 1 / np.sqrt(2 * N), "D": 1.0}  # <e_1|alpha> (dark: unnormalised part)
+    cav = {"U": 1 / np.sqrt(2), "L": -1 / np.sqrt(2), "D": 0.0}
+    amp = {"U": a["U"], "L": a["L"], "D": 1 - 1 / N}  # amplitude times norm of the dark part
+    P11 = sum(e1[p] * amp[p] * amp[q] * e1[q] * R(-1j * (E[p] - E[q]) * dt) ** n for p in E for q in E)
+    Pc = sum(cav[p] * amp[p] * amp[q] * cav[q] * R(-1j * (E[p] - E[q]) * dt) ** n for p in E for q in E)
+    ix = sa.rho0_index()
+    assert abs(y[ix["Pd"]] - P11) < 1e-13
+    assert abs(y[ix["Z"]] - Pc) < 1e-13
