@@ -15,6 +15,9 @@
  *    names a code; sa_heom_last_error() gives a one-line detail of the most
  *    recent failure on the calling thread.
  *  - Handles are not thread-safe: one thread uses a handle at a time.
+ *  - A device-built handle belongs to the device that was current when it
+ *    was built; every entry point that touches the device returns
+ *    SA_ERR_STATE, before any launch, when another device is current.
  *  - "stream" arguments are cudaStream_t values passed as void*; NULL is the
  *    legacy default stream.  Device pointers are plain CUDA device addresses
  *    (for instance a torch tensor's data_ptr()); the library never frees
@@ -64,9 +67,10 @@ enum {
     SA_ERR_UNSUPPORTED = -2, /* size beyond the 32-bit table indices, missing device */
     SA_ERR_OOM = -3,         /* host or device allocation failed */
     SA_ERR_CUDA = -4,        /* a CUDA runtime call failed; see sa_heom_last_error() */
-    SA_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait expired */
+    SA_ERR_TIMEOUT = -5,     /* a bounded device wait expired (sa_heom_device_error says what is
+                                then undefined) */
     SA_ERR_NUMERIC = -6,     /* NaN or Inf in the observables */
-    SA_ERR_STATE = -7        /* handle built host-only, or wrong call order */
+    SA_ERR_STATE = -7        /* handle built host-only, another device current, or wrong call order */
 };
 
 enum { SA_FP64 = 0, SA_FP32_AUX = 1 };                  /* precision */
@@ -218,6 +222,21 @@ int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, i
                        int32_t* dir, int32_t* side);
 
 /*
+ * sa_heom_dump_coefficients -- the FP64 coefficients of the hierarchy terms
+ * of instance `inst` (Eqs. uvar-up, uvar-down with c_k, c-check_k of Eq.
+ * scaled-HEOM), as the host tables hold them.  row and col receive
+ * 2 * SA_HEOM_MAXM * 32 * 2 doubles each: the (re, im) pair of coefficient
+ * id ((k * 32) + n) * 2 + raise, n the moved molecule's occupation in
+ * channel k before the move (0 .. L; 32 slots per channel), raise 1 for
+ * n -> n + 1 and 0 for n -> n - 1:
+ *   raise:  row -i sqrt((n + 1) |c_k|),  column +i sqrt((n + 1) |c_k|);
+ *   lower:  row -i sqrt(n / |c_k|) c_k,  column +i sqrt(n / |c_k|) c-check_k;
+ * with |c_k| = sqrt(Re c_k^2 + Im c_k^2); unused ids are zero.  Pure host.
+ */
+int sa_heom_dump_coefficients(const sa_heom* h, int inst, double* row, double* col);
+
+/*
+ * sa_heom_dump_lists/*
  * sa_heom_dump_lists -- the host copy of the SA_KERNEL_LISTS tables for the
  * current tuning (handles built with SA_BUILD_HOST_ONLY after
  * sa_heom_set_kernel(h, SA_KERNEL_LISTS); device handles keep them on the
@@ -234,9 +253,13 @@ int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, i
  *          item; diagonal class 0: P S T, 1: X, 2: Y, 3: Z);
  *   rbase  uint32[rounds + 1]: first term row of every round;
  *   tidx   uint32[32 * rows], tcid uint16[32 * rows]: entry 32 * row + lane
- *          = target variable and coefficient slot (side * 512 + cid for the
- *          row / column coefficient of coefficient id cid; 1024 + cid for
- *          row + column, the P_q lower terms; 1536 = zero, padding);
+ *          = target variable and coefficient slot, counted from the
+ *          coefficient table of the item's first instance.  Every instance
+ *          holds 2 + 6 m (L + 1) slots (the last unused), the instances'
+ *          tables one after another: slot 0 is zero (padding), then for
+ *          channel k, occupation n = 0..L before the move and direction
+ *          (lower, raise) the row, column and row + column (the P_q lower
+ *          terms) coefficients at 1 + 3 ((k (L + 1) + n) 2 + raise) + side;
  *   opz    int32[4]: operand-area offsets of R_q, C_q, the Z sums, the zero
  *          (the item's stage-input slice occupies [0, chunk)).
  */
@@ -254,7 +277,8 @@ int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32
  *          (31: none);
  *   rbase  uint32[W + 1]: first term row of every warp;
  *   tidx   uint32[32 * rows], tcid uint16[32 * rows]: entry 32 * row + lane
- *          as in sa_heom_dump_lists (1536 = zero slot, padding).
+ *          as in sa_heom_dump_lists, but the slots count from the variable's
+ *          own instance's table (0 = zero slot, padding).
  */
 int sa_heom_dump_ell(const sa_heom* h, int64_t* sizes, uint32_t* wpat, uint32_t* vword, uint32_t* rbase,
                      uint32_t* tidx, uint16_t* tcid);
@@ -263,6 +287,41 @@ int sa_heom_dump_ell(const sa_heom* h, int64_t* sizes, uint32_t* wpat, uint32_t*
 int sa_heom_state_bytes(const sa_heom* h, size_t* bytes);
 
 /*
+ * sa_heom_initial_vars -- the physical representative's variables of a
+ * factorised initial state, in the canonical layout sa_heom_init_physical
+ * takes (for d = 0 the first 10 doubles are also the rho0 of
+ * sa_heom_init_state).  Uses p->N, p->g, p->detuning and p->d (0 or 1).
+ *   SA_INIT_CAVITY      |c><c|                      (Eq. cavity-initial-uvar)
+ *   SA_INIT_BRIGHT      |B><B|, B = sum_i e_i / sqrt N (Eq. bright-initial-uvar)
+ *   SA_INIT_UP, _LP     upper / lower polariton cos(theta)|c> +/- ... with
+ *                       tan 2 theta = Omega_R / Delta, Omega_R = 2 g sqrt N,
+ *                       Delta = omega_cav - eps_x, theta in [0, pi/2]
+ *                       (Eqs. upper-/lower-polariton-initial)
+ *   SA_INIT_RANDOM      a random permutation-invariant density matrix from
+ *                       draws[0..8]: a 2 x 2 complex matrix A (row-major
+ *                       (re, im) pairs) and a dark weight w in [0, 1): the
+ *                       cavity-bright block is (1 - w) A A^+ / tr(A A^+), the
+ *                       dark block the eigenvalue w / (N - 1) (w ignored at
+ *                       N = 1)
+ *   SA_INIT_LOCALISED   |e_1><e_1| (d = 1 only; Sec. V.F)
+ *   SA_INIT_SUPERPOSED  sqrt(0.3)|e_1> + sqrt(0.7)|c> (d = 1 only; Sec. V.F)
+ * out receives *count (re, im) pairs: d = 0: Z, X_0, Y_0, P_0, T_0 (4 for
+ * N = 1); d = 1 (categories 1 = molecule 1, 2 = the others): Z, X_1, X_2,
+ * Y_1, Y_2, P_1, P_2, S_12, S_21, T_2 (9 for N = 2; Z, X_1, Y_1, P_1 for
+ * N = 1).  out needs room for 20 doubles.  Pure host.
+ *
+ * sa_unit_cm_to_rad_fs, sa_unit_kT_rad_fs -- the unit set of Sec. V with
+ * hbar = 1: an energy E in cm^-1 is the angular frequency 2 pi c E in
+ * rad/fs, and k_B T (T in K) likewise, from the exact SI c, h and k_B.
+ */
+enum { SA_INIT_CAVITY = 0, SA_INIT_BRIGHT = 1, SA_INIT_UP = 2, SA_INIT_LP = 3, SA_INIT_RANDOM = 4,
+       SA_INIT_LOCALISED = 5, SA_INIT_SUPERPOSED = 6 };
+int sa_heom_initial_vars(const sa_params* p, int kind, const double* draws, double* out, int* count);
+int sa_unit_cm_to_rad_fs(double e_cm, double* out);
+int sa_unit_kT_rad_fs(double T_K, double* out);
+
+/*
+ * sa_heom_init_state -- factorised initial hierarchy/*
  * sa_heom_init_state -- factorised initial hierarchy (Eqs. factorized-
  * initial-zero/higher): every ADO zero except the physical representative,
  * set per instance from rho0[10 * i ..]: Z, X_0, Y_0, P_0, T_0 as (re, im)
@@ -321,7 +380,11 @@ int sa_heom_reconstruct_dense(sa_heom* h, const void* d_state, const void* d_rho
  * a host complex128 array in the canonical layout (n_vars_total complex
  * values) and a device state buffer, converting to / from the handle's
  * precision (the FP64 copies of the physical representative are exact).
- * Synchronous with respect to the host.
+ * The complex128 values cross the bus as they are (16 bytes per variable;
+ * from page-locked host memory at full DMA speed) and an SA_FP32_AUX handle
+ * narrows or widens them on the device, staging them in its own RK4 work
+ * vectors (scratch between steps, so a call must not overlap a propagation
+ * of the same handle).  Synchronous with respect to the host.
  */
 int sa_heom_state_upload(const sa_heom* h, const double* host_x, void* d_state, void* stream);
 int sa_heom_state_download(const sa_heom* h, const void* d_state, double* host_x, void* stream);
@@ -415,7 +478,7 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best);
  * an unknown variant, OOM if the lists do not fit).  sa_heom_get_tuning
  * writes block, chunk, queue, kernel to out[0..3].
  */
-enum { SA_KERNEL_RECORDS = 0, SA_KERNEL_LISTS = 1, SA_KERNEL_ELL = 2 };
+enum { SA_KERNEL_RECORDS = 0, SA_KERNEL_LISTS = 1, SA_KERNEL_ELL = 2, SA_KERNEL_SPLIT = 3 };
 int sa_heom_set_kernel(sa_heom* h, int kernel);
 int sa_heom_get_tuning(const sa_heom* h, int* out);
 
@@ -428,12 +491,72 @@ int sa_heom_launches_per_step(const sa_heom* h);
 /*
  * sa_heom_device_error -- read the kernels' device error word (synchronises
  * `stream`).  Returns SA_ERR_TIMEOUT if a stage kernel gave up a bounded
- * wait on its bulk copies (the affected launch left its outputs incomplete);
- * SA_OK otherwise.  sa_heom_propagate with observables checks it too.
+ * wait on its bulk copies, SA_OK otherwise.  sa_heom_propagate with
+ * observables checks it too.  Reading the word clears it.  After
+ * SA_ERR_TIMEOUT the outputs of the affected launches, and so the caller's
+ * state buffer, are undefined, and unless the expiry was injected
+ * (SA_DEBUG_EXPIRE_WAIT) a copy the kernel gave up on may still land in
+ * shared memory of the exited block: discard the state and the handle
+ * (sa_heom_destroy) and build anew.
  */
 int sa_heom_device_error(sa_heom* h, void* stream);
 
 /*
+ * Checkpoint / resume (no counterpart in the paper).  A checkpoint is a
+ * host buffer of sa_heom_checkpoint_bytes bytes: a 64-byte header (format,
+ * precision, instance count, variables, state bytes, the caller's step index
+ * and sa_heom_config_hash) followed by the device state exactly as stored
+ * (float2 auxiliaries plus the FP64 copies of rho_S, or double2), so a resume
+ * continues bit for bit: the kernels compute every variable in a fixed
+ * order whatever the scheduling.
+ *   sa_heom_config_hash      64-bit FNV-1a hash of the precision, every
+ *                            instance's sa_params and the table layout
+ *                            version.  Pure host.
+ *   sa_heom_checkpoint_save  d_state -> host_buf (caller-owned, at least
+ *                            sa_heom_checkpoint_bytes); synchronous.
+ *   sa_heom_checkpoint_load  host_buf -> d_state, *step (nullable) <- the
+ *                            saved step index; SA_ERR_STATE, and d_state
+ *                            untouched, if the format, precision, sizes or
+ *                            parameter hash differ or the buffer is short.
+ *                            Synchronous.
+ */
+int sa_heom_config_hash(const sa_heom* h, uint64_t* out);
+int sa_heom_checkpoint_bytes(const sa_heom* h, size_t* bytes);
+int sa_heom_checkpoint_save(const sa_heom* h, const void* d_state, int64_t step, void* host_buf, size_t bytes,
+                            void* stream);
+int sa_heom_checkpoint_load(const sa_heom* h, const void* host_buf, size_t bytes, void* d_state, int64_t* step,
+                            void* stream);
+
+/*
+ * Failure detection (no counterpart in the paper).
+ *   sa_heom_validate   checks the host tables of every instance: pattern,
+ *                      category and variable counts (Eq. uvar-count),
+ *                      multiplicities summing to N, T-ranks, and every
+ *                      connection record -- its target must be the first
+ *                      variable of a pattern one tier up (raise) or down
+ *                      (lower) with the G' the record names, its moved
+ *                      category inside that pattern, its channel below m and
+ *                      occupation at most L.  SA_ERR_STATE names the first
+ *                      inconsistency (sa_heom_last_error).  Pure host; about
+ *                      a second at 10^8 records.
+ *   sa_heom_set_debug  SA_DEBUG_EXPIRE_WAIT: the list and split stage
+ *                      kernels take the expiry path of their bounded wait on
+ *                      an item's bulk copies without testing it (each warp
+ *                      still waits, bounded, for its copies before it
+ *                      leaves), so sa_heom_device_error reports
+ *                      SA_ERR_TIMEOUT; the launch's outputs are incomplete.
+ *                      0 turns it off again.  SA_DEBUG_CORRUPT_RECORD
+ *                      (host-only handles; STATE otherwise) moves the target
+ *                      of instance 0's first connection record off its
+ *                      pattern, for which sa_heom_validate must fail; it
+ *                      cannot be undone.  Other bits: INVALID_ARG.
+ */
+enum { SA_DEBUG_EXPIRE_WAIT = 1, SA_DEBUG_CORRUPT_RECORD = 2 };
+int sa_heom_validate(const sa_heom* h);
+int sa_heom_set_debug(sa_heom* h, int flags);
+
+/*
+ * sa_heom_observables_noalloc/*
  * sa_heom_observables_noalloc -- the same observables as sa_heom_observables
  * (same kernel, same out[8 * i ..] layout), for callers that may not call
  * cudaMalloc.  The paper has no counterpart to this entry point.
@@ -450,9 +573,11 @@ int sa_heom_device_error(sa_heom* h, void* stream);
  * holds until the process exits.
  *   - Batches with more than SA_HEOM_NOALLOC_MAX_INSTANCES instances are
  *     rejected with SA_ERR_UNSUPPORTED.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress,
+ *     which allocates nothing) with the handle's device current; the first
+ *     call on a device also loads the array there, so make that first call
+ *     before any stream capture.  No address is cached across calls, so a
+ *     cudaDeviceReset between calls leaves nothing stale.
  *   - Every call and every handle shares the one array, which keeps the last
  *     call's contents; calls whose work overlaps on the GPU (different streams
  *     or host threads) race on it.  Each call overwrites every slot it reads

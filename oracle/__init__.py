@@ -84,6 +84,7 @@ def lib():
             "orc_sa_rhs_at": (None, [vp, vp, vp, ll, vp]),
             "orc_sa_num_terms": (ll, [vp]),
             "orc_sa_terms": (None, [vp, vp, vp, vp, vp, vp, vp]),
+            "orc_sa_term_coefs": (None, [vp, vp, vp]),
             "orc_sa_rk4": (None, [vp, vp, ctypes.c_double, ll]),
             "orc_sa_observables": (None, [vp, vp, vp]),
             "orc_sa_propagate": (None, [vp, vp, ctypes.c_double, ll, ll, vp]),
@@ -195,7 +196,10 @@ class SA:
         d = np.zeros(n, np.int32)
         side = np.zeros(n, np.int32)
         lib().orc_sa_terms(self._h, _ptr(var), _ptr(src), _ptr(k), _ptr(nn), _ptr(d), _ptr(side))
-        return dict(var=var, src=src, k=k, n=nn, dir=d, side=side)
+        re = np.zeros(n)
+        im = np.zeros(n)
+        lib().orc_sa_term_coefs(self._h, _ptr(re), _ptr(im))
+        return dict(var=var, src=src, k=k, n=nn, dir=d, side=side, coef=re + 1j * im)
 
     # ---- dynamics -------------------------------------------------------
     def zeros(self) -> np.ndarray:

@@ -831,6 +831,24 @@ void orc_sa_terms(const orc_sa* s, long long* var, long long* src, int* k, int* 
     }
 }
 
+/* the coefficient of every hierarchy term, in the order of orc_sa_terms */
+void orc_sa_term_coefs(const orc_sa* s, double* re, double* im) {
+    long long t = 0;
+    for (long long i = 0; i < s->P; ++i) {
+        long long u = s->var_off[i + 1] - s->var_off[i];
+        for (long long loc = 0; loc < u; ++loc) {
+            int kind, q, r;
+            decode_local(s, i, loc, &kind, &q, &r);
+            hterm ht[4 * ORC_MAXM];
+            int nt = var_hterms(s, i, kind, q, r, ht);
+            for (int a = 0; a < nt; ++a, ++t) {
+                re[t] = creal(ht[a].coef);
+                im[t] = cimag(ht[a].coef);
+            }
+        }
+    }
+}
+
 /* classical RK4 (the integrator named in Sec. V), in place */
 void orc_sa_rk4(const orc_sa* s, double* x, double dt, long long nsteps) {
     long long n2 = 2 * s->nvar;

@@ -19,10 +19,13 @@ LIB_PATH = os.path.join(_HERE, "libsaheom.so")
 MAXM = 8
 MAXD = 3         # SA_HEOM_MAXD
 PHYS_SLOTS = 32  # SA_HEOM_PHYS_SLOTS
+NOALLOC_MAX_INSTANCES = 4096  # SA_HEOM_NOALLOC_MAX_INSTANCES
 
 SA_FP64, SA_FP32_AUX = 0, 1
 SA_BUILD_DEVICE, SA_BUILD_HOST_ONLY = 0, 1
-SA_KERNEL_RECORDS, SA_KERNEL_LISTS, SA_KERNEL_ELL = 0, 1, 2
+SA_KERNEL_RECORDS, SA_KERNEL_LISTS, SA_KERNEL_ELL, SA_KERNEL_SPLIT = 0, 1, 2, 3
+SA_DEBUG_EXPIRE_WAIT, SA_DEBUG_CORRUPT_RECORD = 1, 2
+INIT_KINDS = {"cavity": 0, "bright": 1, "up": 2, "lp": 3, "random": 4, "localised": 5, "superposed": 6}
 BATH_HIGH_T, BATH_MATSUBARA, BATH_PADE = 0, 1, 2
 ERRORS = {0: "SA_OK", -1: "SA_ERR_INVALID_ARG", -2: "SA_ERR_UNSUPPORTED", -3: "SA_ERR_OOM",
           -4: "SA_ERR_CUDA", -5: "SA_ERR_TIMEOUT", -6: "SA_ERR_NUMERIC", -7: "SA_ERR_STATE"}
@@ -106,6 +109,16 @@ def lib() -> ctypes.CDLL:
             "sa_heom_launches_per_step": [vp],
             "sa_heom_device_error": [vp, vp],
             "sa_heom_observables_noalloc": [vp, vp, vp, vp],
+            "sa_heom_validate": [vp],
+            "sa_heom_initial_vars": [P(Params), i32, vp, vp, P(i32)],
+            "sa_unit_cm_to_rad_fs": [dbl, P(dbl)],
+            "sa_unit_kT_rad_fs": [dbl, P(dbl)],
+            "sa_heom_dump_coefficients": [vp, i32, vp, vp],
+            "sa_heom_config_hash": [vp, P(ctypes.c_uint64)],
+            "sa_heom_checkpoint_bytes": [vp, P(ctypes.c_size_t)],
+            "sa_heom_checkpoint_save": [vp, vp, i64, vp, ctypes.c_size_t, vp],
+            "sa_heom_checkpoint_load": [vp, vp, ctypes.c_size_t, vp, P(i64), vp],
+            "sa_heom_set_debug": [vp, i32],
             "sa_conv_build": [P(Params), P(vp)],
             "sa_conv_info": [vp, P(i64), P(ctypes.c_size_t)],
             "sa_conv_labels": [vp, vp],
@@ -136,12 +149,14 @@ def exported_symbols() -> list[str]:
             "sa_heom_build_representatives", "sa_heom_init_representatives", "sa_heom_reconstruct_dense",
             "sa_heom_destroy", "sa_heom_info",
             "sa_heom_var_offset", "sa_heom_dump_vectors", "sa_heom_dump_patterns", "sa_heom_dump_categories",
-            "sa_heom_dump_terms", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_init_physical",
+            "sa_heom_dump_terms", "sa_heom_dump_coefficients", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_init_physical",
             "sa_heom_state_upload",
             "sa_heom_state_download", "sa_heom_rhs", "sa_heom_step", "sa_heom_propagate", "sa_heom_observables",
             "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_set_kernel", "sa_heom_get_tuning", "sa_heom_prepare", "sa_heom_dump_lists", "sa_heom_dump_ell",
             "sa_heom_launches_per_step", "sa_heom_device_error",
-            "sa_heom_observables_noalloc", "sa_heom_strerror", "sa_heom_last_error", "sa_conv_build",
+            "sa_heom_observables_noalloc", "sa_heom_initial_vars", "sa_unit_cm_to_rad_fs", "sa_unit_kT_rad_fs",
+            "sa_heom_validate", "sa_heom_set_debug", "sa_heom_config_hash",
+            "sa_heom_checkpoint_bytes", "sa_heom_checkpoint_save", "sa_heom_checkpoint_load", "sa_heom_strerror", "sa_heom_last_error", "sa_conv_build",
             "sa_conv_destroy", "sa_conv_info", "sa_conv_labels", "sa_conv_set_rho0", "sa_conv_rhs", "sa_conv_step",
             "sa_conv_last_error"]
 
@@ -198,6 +213,32 @@ def bath_terminator(lam, gam, kT, n_matsubara) -> float:
     """sa_bath_terminator: Delta of the Matsubara poles beyond n_matsubara."""
     out = ctypes.c_double()
     _check(lib().sa_bath_terminator(lam, gam, kT, int(n_matsubara), ctypes.byref(out)), "sa_bath_terminator")
+    return out.value
+
+
+def initial_vars(p: Params, kind: str, draws: dict | None = None) -> np.ndarray:
+    """sa_heom_initial_vars: the physical representative's variables of a
+    factorised initial state (canonical layout, complex)."""
+    d = np.zeros(9)
+    if draws is not None:
+        d[:8] = np.asarray(draws["A"], complex).reshape(4).view(np.float64)
+        d[8] = float(draws["w_dark"])
+    out = np.zeros(20)
+    n = ctypes.c_int()
+    _check(lib().sa_heom_initial_vars(ctypes.byref(p), INIT_KINDS[kind], _ptr(d) if draws is not None else None,
+                                      _ptr(out), ctypes.byref(n)), "sa_heom_initial_vars")
+    return out[:2 * n.value].view(complex).copy()
+
+
+def unit_cm_to_rad_fs(e_cm: float) -> float:
+    out = ctypes.c_double()
+    _check(lib().sa_unit_cm_to_rad_fs(float(e_cm), ctypes.byref(out)), "sa_unit_cm_to_rad_fs")
+    return out.value
+
+
+def unit_kT_rad_fs(T_K: float) -> float:
+    out = ctypes.c_double()
+    _check(lib().sa_unit_kT_rad_fs(float(T_K), ctypes.byref(out)), "sa_unit_kT_rad_fs")
     return out.value
 
 
@@ -292,6 +333,13 @@ class Heom:
                "sa_heom_dump_terms")
         return dict(var=var, src=src, k=k, n=nn, dir=d, side=s)
 
+    def dump_coefficients(self, inst: int = 0) -> tuple[np.ndarray, np.ndarray]:
+        """Row and column coefficients (complex) by coefficient id ((k * 32) + n) * 2 + raise."""
+        n = 2 * MAXM * 32 * 2
+        row, col = np.zeros(n), np.zeros(n)
+        _check(lib().sa_heom_dump_coefficients(self._h, inst, _ptr(row), _ptr(col)), "sa_heom_dump_coefficients")
+        return row[0::2] + 1j * row[1::2], col[0::2] + 1j * col[1::2]
+
     # ---- device state -------------------------------------------------
     def new_state(self, device="cuda"):
         import torch
@@ -339,8 +387,14 @@ class Heom:
         assert x.shape == (self.n_vars,)
         _check(lib().sa_heom_state_upload(self._h, _ptr(x), _dev(state), _stream(stream)), "sa_heom_state_upload")
 
-    def download(self, state, stream=None) -> np.ndarray:
-        x = np.zeros(self.n_vars, np.complex128)
+    def download(self, state, stream=None, out: np.ndarray | None = None) -> np.ndarray:
+        """The state as complex128; `out` (contiguous complex128 of n_vars, for
+        instance a view of page-locked memory) receives it if given."""
+        if out is None:
+            x = np.zeros(self.n_vars, np.complex128)
+        else:
+            x = out
+            assert x.dtype == np.complex128 and x.shape == (self.n_vars,) and x.flags.c_contiguous
         _check(lib().sa_heom_state_download(self._h, _dev(state), _ptr(x), _stream(stream)), "sa_heom_state_download")
         return x
 
@@ -424,6 +478,39 @@ class Heom:
 
     def device_error(self, stream=None):
         _check(lib().sa_heom_device_error(self._h, _stream(stream)), "sa_heom_device_error")
+
+    def config_hash(self) -> int:
+        """sa_heom_config_hash: hash of the precision, parameters and table layout version."""
+        out = ctypes.c_uint64()
+        _check(lib().sa_heom_config_hash(self._h, ctypes.byref(out)), "sa_heom_config_hash")
+        return int(out.value)
+
+    def checkpoint(self, state, step: int, stream=None) -> bytearray:
+        """sa_heom_checkpoint_save into a new host buffer."""
+        n = ctypes.c_size_t()
+        _check(lib().sa_heom_checkpoint_bytes(self._h, ctypes.byref(n)), "sa_heom_checkpoint_bytes")
+        buf = bytearray(n.value)
+        cbuf = (ctypes.c_char * n.value).from_buffer(buf)
+        _check(lib().sa_heom_checkpoint_save(self._h, _dev(state), int(step), ctypes.cast(cbuf, ctypes.c_void_p),
+                                             n.value, _stream(stream)), "sa_heom_checkpoint_save")
+        return buf
+
+    def resume(self, state, buf, stream=None) -> int:
+        """sa_heom_checkpoint_load: the saved state into `state`; returns the saved step index."""
+        buf = bytearray(buf) if not isinstance(buf, bytearray) else buf
+        cbuf = (ctypes.c_char * len(buf)).from_buffer(buf)
+        step = ctypes.c_int64()
+        _check(lib().sa_heom_checkpoint_load(self._h, ctypes.cast(cbuf, ctypes.c_void_p), len(buf), _dev(state),
+                                             ctypes.byref(step), _stream(stream)), "sa_heom_checkpoint_load")
+        return int(step.value)
+
+    def validate(self):
+        """sa_heom_validate: raises SaHeomError naming the first inconsistent table entry."""
+        _check(lib().sa_heom_validate(self._h), "sa_heom_validate")
+
+    def set_debug(self, flags: int):
+        """sa_heom_set_debug (SA_DEBUG_EXPIRE_WAIT, SA_DEBUG_CORRUPT_RECORD)."""
+        _check(lib().sa_heom_set_debug(self._h, int(flags)), "sa_heom_set_debug")
 
     def launches_per_step(self) -> int:
         return int(lib().sa_heom_launches_per_step(self._h))

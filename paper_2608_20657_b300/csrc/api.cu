@@ -24,6 +24,8 @@ cudaError_t launch_observables(const InstDev* inst, const double* theta, int nin
 cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0, int stride, void* main64,
                              void* main32, void* side64, cudaStream_t st);
 size_t recon_workspace_bytes(int64_t n);
+cudaError_t launch_marshal(const InstDev* inst, int ninst, uint64_t n0, uint64_t cnt, void* stage, void* main32,
+                           void* side64, int to_device, cudaStream_t st);
 cudaError_t launch_reconstruct(const InstDev* inst, const int16_t* loc, int nrep, const void* main64,
                                const void* side64, const void* rho0, int64_t n, void* rho_t, void* ws,
                                cudaStream_t st);
@@ -63,6 +65,11 @@ int upload(void** dptr, const std::vector<V>& h) {
 }
 }  // namespace
 
+namespace sa {
+// detail of a failure in a file other than this one (sa_heom_last_error)
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace sa
+
 struct sa_heom {
     int count = 0;
     int precision = SA_FP64;
@@ -89,9 +96,11 @@ struct sa_heom {
     std::vector<DRecA> drecA;
     std::vector<uint32_t> drecS;
     int max_u = 0;
+    uint64_t lcoef_total = 0;  // slots of the list/ELL coefficient tables of all instances
     // term lists of the list kernel (built per tuning, freed after upload)
     std::vector<uint32_t> lvd, rbase, tidx;
     std::vector<uint8_t> lvj;
+    std::vector<uint16_t> lw16;  // SA_KERNEL_SPLIT: hierarchy-pass lane words
     std::vector<uint16_t> tcid;
     uint64_t list_rows = 0;
     std::vector<uint32_t> wpat;   // ELL: first pattern of every warp row
@@ -101,6 +110,7 @@ struct sa_heom {
     int tables_chunk = 0;         // item capacity they were built for (SA_KERNEL_LISTS)
     // tuning
     int block = 256, chunk = 128, use_queue = 1, kernel = SA_KERNEL_LISTS;
+    int debug = 0;  // SA_DEBUG_* flags
     // device
     int device = -1, num_sms = 0;
     void *d_hdr = nullptr, *d_cat_word = nullptr, *d_catM = nullptr, *d_catMd = nullptr, *d_gamma = nullptr;
@@ -277,10 +287,12 @@ void list_item(const sa_heom* h, const ItemDesc& d, ListItem& W) {
         const int inst = H.inst;
         const uint32_t vb = uint32_t(h->var_begin[inst]);
         const int64_t p = int64_t(d.p0 + j) - int64_t(h->instdev[inst].pat_begin);
+        // term slots are relative to the coefficient table of the item's first instance
+        const int soff = int(h->instdev[inst].lcoef_base) - int(h->instdev[h->hdr[d.p0].inst].lcoef_base);
         for_each_term(h->inst[inst], p, [&](int64_t loc, int kind, int64_t src, uint32_t packed, int side) {
             const int cid = int(packed >> 23);
             if (kind == 3 && side == 1) return;  // folded into the row term's coefficient
-            const int slot = kind == 3 ? 2 * kCoefPerInst + cid : side * kCoefPerInst + cid;
+            const int slot = soff + list_slot(h->inst[inst].L, cid, kind == 3 ? 2 : side);
             const uint32_t l = pl + uint32_t(loc);
             tv.push_back(l);
             W.tix.push_back(vb + uint32_t(src));
@@ -353,7 +365,7 @@ int build_blobs(sa_heom* h) {
                 ic[nic].det = V(q.detuning);
                 ic[nic].kap = V(q.kappa);
                 ic[nic].term = V(q.term);
-                ic[nic].coef_base = uint32_t(H.inst) * uint32_t(kListCoefStride);
+                ic[nic].coef_base = h->instdev[h->hdr[d.p0].inst].lcoef_base;  // the item's term slots are relative to it
                 ++nic;
             }
             ph[j].islot = uint16_t(nic - 1);
@@ -381,8 +393,88 @@ uint64_t list_item_rows(const ListItem& W) {
     return rows;
 }
 
+// lanes of the item's term rounds: every lane variable (SA_KERNEL_LISTS), or
+// only those with hierarchy terms (SA_KERNEL_SPLIT: the others are handled
+// by its memory-order pass alone; lane order is by term count, so they come
+// last)
+uint32_t list_item_lanes(const ListItem& W, bool split) {
+    if (!split) return uint32_t(W.order.size());
+    uint32_t n = 0;
+    while (n < W.order.size() && W.cnt[W.order[n]] > 0) ++n;
+    return n;
+}
+
+// Per-item table blobs of the split kernel (SplitLayout).
+template <typename V>
+int build_split_blobs(sa_heom* h) {
+    const size_t ni = h->items.size();
+    uint64_t off16 = 0;
+    for (size_t c = 0; c < ni; ++c) {
+        ItemDesc& d = h->items[c];
+        const SplitLayout B = split_layout<V>(d.np, d.ncat, d.nv, d.nl);
+        d.blob16 = uint32_t(off16);
+        d.blob_bytes = B.bytes;
+        off16 += B.bytes / 16;
+        if (off16 >= (uint64_t(1) << 32)) return fail(SA_ERR_UNSUPPORTED, "split-kernel blobs exceed 64 GB");
+    }
+    try {
+        h->blobs.assign(size_t(off16) * 16, 0);
+    } catch (const std::bad_alloc&) {
+        return fail(SA_ERR_OOM, "host memory for the split-kernel blobs");
+    }
+    const std::vector<double>& gam = h->gamma_d;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t c = 0; c < int64_t(ni); ++c) {
+        const ItemDesc& d = h->items[c];
+        const SplitLayout B = split_layout<V>(d.np, d.ncat, d.nv, d.nl);
+        uint8_t* o = &h->blobs[size_t(d.blob16) * 16];
+        *reinterpret_cast<uint32_t*>(o) = h->instdev[h->hdr[d.p0].inst].lcoef_base;
+        ItemPat* ph = reinterpret_cast<ItemPat*>(o + B.pat);
+        V* pd = reinterpret_cast<V*>(o + B.pd);
+        uint32_t* cw = reinterpret_cast<uint32_t*>(o + B.cw);
+        V* cM = reinterpret_cast<V*>(o + B.cM);
+        uint8_t* cj = o + B.cj;
+        uint32_t* rb = reinterpret_cast<uint32_t*>(o + B.rb);
+        uint32_t* mw = reinterpret_cast<uint32_t*>(o + B.mw);
+        uint16_t* lw = reinterpret_cast<uint16_t*>(o + B.lw);
+        for (uint32_t j = 0; j < d.np; ++j) {
+            const PatHdr& H = h->hdr[d.p0 + j];
+            ph[j].var_rel = uint16_t(H.var_off - d.v0);
+            ph[j].cat_rel = uint16_t(H.cat_off - d.c0);
+            ph[j].G = H.G;
+            ph[j].tier = H.tier;
+            ph[j].islot = 0;
+            // diagonal coefficients by class (0 S T, 1 X, 2 Y, 3 Z, 4 P):
+            // -Gamma_Lambda, the cavity loss (1/2 per cavity label), -/+ i
+            // detuning for X / Y and the terminator -Delta w
+            const sa_params& q = h->inst[H.inst].p;
+            const double gre = gam[2 * size_t(d.p0 + j)], gim = gam[2 * size_t(d.p0 + j) + 1];
+            const double lossf[5] = {0.0, 0.5, 0.5, 1.0, 0.0}, wt[5] = {2.0, 1.0, 1.0, 0.0, 0.0};
+            const double dim[5] = {0.0, -q.detuning, q.detuning, 0.0, 0.0};
+            V* e = pd + size_t(2 * kSplitPd) * j;
+            for (int cl = 0; cl < 5; ++cl) {
+                e[2 * cl] = V(-(gre + lossf[cl] * q.kappa + wt[cl] * q.term));
+                e[2 * cl + 1] = V(dim[cl] - gim);
+            }
+            e[10] = V(q.g);
+            e[11] = V(0);
+            for (uint32_t cl = H.cat_off - d.c0; cl < h->hdr[d.p0 + j + 1].cat_off - d.c0; ++cl) cj[cl] = uint8_t(j);
+        }
+        for (uint32_t cl = 0; cl < d.ncat; ++cl) {
+            cw[cl] = h->cat_word[d.c0 + cl];
+            cM[cl] = V(h->catMd[d.c0 + cl]);
+        }
+        const uint32_t nrounds = (d.nl + 31) / 32;
+        for (uint32_t r = 0; d.nl && r <= nrounds; ++r) rb[r] = h->rbase[d.r0 + r];
+        for (uint32_t i = 0; i < d.nv; ++i) mw[i] = h->lvd[d.v0 + i];
+        for (uint32_t i = 0; i < d.nl; ++i) lw[i] = h->lw16[d.v0 + i];
+    }
+    return SA_OK;
+}
+
 int build_lists(sa_heom* h) {
     const size_t ni = h->items.size();
+    const bool split = h->kernel == SA_KERNEL_SPLIT;
     std::vector<uint32_t> nrounds(ni + 1, 0);
     std::vector<uint64_t> nrows(ni + 1, 0);
 #pragma omp parallel
@@ -391,7 +483,7 @@ int build_lists(sa_heom* h) {
 #pragma omp for schedule(dynamic, 64)
         for (int64_t c = 0; c < int64_t(ni); ++c) {
             list_item(h, h->items[c], W);
-            nrounds[c] = uint32_t((W.order.size() + 31) / 32);
+            nrounds[c] = (list_item_lanes(W, split) + 31) / 32;
             nrows[c] = list_item_rows(W);
         }
     }
@@ -412,7 +504,8 @@ int build_lists(sa_heom* h) {
     h->list_rows = rw;
     try {
         h->lvd.assign(size_t(h->nvar), 0u);
-        h->lvj.assign(size_t(h->nvar), 0);
+        if (split) h->lw16.assign(size_t(h->nvar), 0);
+        else h->lvj.assign(size_t(h->nvar), 0);
         h->rbase.assign(rr + 1, 0u);
         h->tidx.assign(rw * 32, 0u);
         h->tcid.assign(rw * 32, 0);
@@ -428,22 +521,27 @@ int build_lists(sa_heom* h) {
         for (int64_t c = 0; c < int64_t(ni); ++c) {
             ItemDesc& d = h->items[c];
             list_item(h, d, W);
-            d.nl = uint32_t(W.order.size());
+            const uint32_t nlane = list_item_lanes(W, split);
+            d.nl = nlane;
             uint64_t row = nrows[c];
             d.row0 = uint32_t(row);
             d.row1 = uint32_t(nrows[c + 1]);
 
             uint32_t rho = nrounds[c];
-            for (size_t i0 = 0; i0 < W.order.size(); i0 += 32, ++rho) {
+            for (size_t i0 = 0; i0 < nlane; i0 += 32, ++rho) {
                 h->rbase[rho] = uint32_t(row);
                 const uint32_t T = W.cnt[W.order[i0]];
                 for (uint32_t u = 0; u < 32; ++u) {
                     const size_t i = i0 + u;
-                    const uint32_t l = i < W.order.size() ? W.order[i] : 0u;
-                    const uint32_t n = i < W.order.size() ? W.cnt[l] : 0u;
-                    if (i < W.order.size()) {
-                        h->lvd[d.v0 + i] = W.desc[l];
-                        h->lvj[d.v0 + i] = W.cls[l];
+                    const uint32_t l = i < nlane ? W.order[i] : 0u;
+                    const uint32_t n = i < nlane ? W.cnt[l] : 0u;
+                    if (i < nlane) {
+                        if (split) {
+                            h->lw16[d.v0 + i] = uint16_t(l);
+                        } else {
+                            h->lvd[d.v0 + i] = W.desc[l];
+                            h->lvj[d.v0 + i] = W.cls[l];
+                        }
                     }
                     for (uint32_t t = 0; t < T; ++t) {
                         const size_t e = size_t(row + t) * 32 + u;
@@ -458,9 +556,19 @@ int build_lists(sa_heom* h) {
                 }
                 row += T;
             }
+            if (split) {
+                // memory-order words; variables outside the lane order belong to
+                // the physical representative the FP64 kernel integrates
+                std::vector<uint8_t> lane(d.nv, 0);
+                for (uint32_t l : W.order) lane[l] = 1;
+                for (uint32_t l = 0; l < d.nv; ++l)
+                    h->lvd[d.v0 + l] = split_word((W.desc[l] >> 10) & 2047u, W.desc[l] >> 21, W.cls[l] & 31u,
+                                                  uint32_t(W.cls[l]) >> 5, W.cnt[l] > 0 ? 1u : 0u, lane[l] ? 0u : 1u);
+            }
         }
     }
-    const int rc = h->precision == SA_FP64 ? build_blobs<double>(h) : build_blobs<float>(h);
+    const int rc = split ? (h->precision == SA_FP64 ? build_split_blobs<double>(h) : build_split_blobs<float>(h))
+                         : (h->precision == SA_FP64 ? build_blobs<double>(h) : build_blobs<float>(h));
     if (rc) return rc;
     h->list_items = h->items;
     return SA_OK;
@@ -494,7 +602,7 @@ int build_ell(sa_heom* h) {
                       [&](int64_t loc, int kind, int64_t src, uint32_t packed, int side) {
                           if (kind == 3 && side == 1) return;  // folded into the row term's coefficient
                           const int cid = int(packed >> 23);
-                          const int slot = kind == 3 ? 2 * kCoefPerInst + cid : side * kCoefPerInst + cid;
+                          const int slot = list_slot(h->inst[inst].L, cid, kind == 3 ? 2 : side);
                           fn(H.var_off + uint32_t(loc), vb + uint32_t(src), slot);
                       });
     };
@@ -589,20 +697,26 @@ void decode_records(sa_heom* h) {
     }
 }
 
-// Per-instance coefficient table of the list kernel: row, column and
-// row + column coefficients, then zeros.
+// Coefficient tables of the list and ELL kernels, instance after instance
+// (list_slot layout: zero, then row, column, row + column per (k, n, dir)).
 template <typename V>
 std::vector<V> list_coefficients(const sa_heom* h) {
-    std::vector<V> t(size_t(2) * kListCoefStride * h->count, V(0));
+    std::vector<V> t(size_t(2) * h->lcoef_total, V(0));
     for (int i = 0; i < h->count; ++i) {
-        V* o = &t[size_t(2) * kListCoefStride * i];
+        const HostInstance& hi = h->inst[i];
+        V* o = &t[size_t(2) * h->instdev[i].lcoef_base];
         const double* r = &h->coef_row_d[size_t(2) * kCoefPerInst * i];
         const double* c = &h->coef_col_d[size_t(2) * kCoefPerInst * i];
-        for (int k = 0; k < 2 * kCoefPerInst; ++k) {
-            o[k] = V(r[k]);
-            o[2 * kCoefPerInst + k] = V(c[k]);
-            o[4 * kCoefPerInst + k] = V(r[k] + c[k]);
-        }
+        for (int k = 0; k < hi.m; ++k)
+            for (int n = 0; n <= hi.L; ++n)
+                for (int raise = 0; raise < 2; ++raise) {
+                    const int cid = coef_id(k, n, raise);
+                    for (int z = 0; z < 2; ++z) {
+                        o[2 * list_slot(hi.L, cid, 0) + z] = V(r[2 * cid + z]);
+                        o[2 * list_slot(hi.L, cid, 1) + z] = V(c[2 * cid + z]);
+                        o[2 * list_slot(hi.L, cid, 2) + z] = V(r[2 * cid + z] + c[2 * cid + z]);
+                    }
+                }
     }
     return t;
 }
@@ -618,24 +732,27 @@ void free_lists(sa_heom* h) {
 
 // Term tables of the current variant: built (and, on a device handle,
 // uploaded) unless the current ones already serve it.
+int check_device(const sa_heom* h);
+
 int ensure_tables(sa_heom* h) {
     const int k = h->kernel;
     if (k == SA_KERNEL_RECORDS) return SA_OK;
     if (h->tables == k && (k == SA_KERNEL_ELL || h->tables_chunk == h->chunk)) {
-        if (k == SA_KERNEL_LISTS)  // the item table was rebuilt: same items, restore their rounds
+        if (k == SA_KERNEL_LISTS || k == SA_KERNEL_SPLIT)  // the item table was rebuilt: same items, restore their rounds
             h->items = h->list_items;
         return SA_OK;
     }
     if (!h->host_only) free_lists(h);
     h->tables = -1;
-    int rc = k == SA_KERNEL_LISTS ? build_lists(h) : build_ell(h);
+    const bool lists = k == SA_KERNEL_LISTS || k == SA_KERNEL_SPLIT;
+    int rc = lists ? build_lists(h) : build_ell(h);
     if (rc) return rc;
     if (!h->host_only) {
         if (!h->d_lcoef)
             rc = h->precision == SA_FP64 ? upload(&h->d_lcoef, list_coefficients<double>(h))
                                          : upload(&h->d_lcoef, list_coefficients<float>(h));
 
-        if (!rc && k == SA_KERNEL_LISTS) rc = upload(&h->d_blobs, h->blobs);
+        if (!rc && lists) rc = upload(&h->d_blobs, h->blobs);
 
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_lvd, h->lvd);
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_wpat, h->wpat);
@@ -655,6 +772,7 @@ int ensure_tables(sa_heom* h) {
         // the host copies are not needed again
         std::vector<uint32_t>().swap(h->lvd);
         std::vector<uint8_t>().swap(h->lvj);
+        std::vector<uint16_t>().swap(h->lw16);
         std::vector<uint32_t>().swap(h->tidx);
         std::vector<uint16_t>().swap(h->tcid);
         std::vector<uint32_t>().swap(h->wpat);
@@ -670,6 +788,10 @@ int ensure_tables(sa_heom* h) {
 }
 
 int apply_tuning(sa_heom* h) {
+    if (!h->host_only) {
+        const int rc0 = check_device(h);
+        if (rc0) return rc0;
+    }
     build_items(h);
     h->cfg.block = h->block;
     h->cfg.chunk = h->chunk;
@@ -691,9 +813,11 @@ int apply_tuning(sa_heom* h) {
     const int wpb = h->block / 32;
     const int64_t blocks_needed = (int64_t(nchunks) + wpb - 1) / wpb;
     // the list kernel is persistent in both modes (its warps pipeline their items)
-    const bool persistent = h->use_queue || h->kernel == SA_KERNEL_LISTS;
+    const bool persistent = h->use_queue || h->kernel == SA_KERNEL_LISTS || h->kernel == SA_KERNEL_SPLIT;
     h->cfg.grid = persistent ? int(std::min<int64_t>(int64_t(h->num_sms) * occ, blocks_needed)) : int(blocks_needed);
     if (h->cfg.grid < 1) h->cfg.grid = 1;
+    if (h->use_queue == 2 && h->cfg.grid >= kQueueStride)
+        return fail(SA_ERR_UNSUPPORTED, "queue mode 2 needs fewer than 2048 CTAs");
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     return SA_OK;
@@ -726,6 +850,9 @@ int ensure_queue(sa_heom* h, size_t slots) {
     h->queue_slots = n;
     return SA_OK;
 }
+
+// queue counters each stage launch owns (queue mode 2: per-SM ranges)
+size_t qstride(const sa_heom* h) { return h->use_queue == 2 ? size_t(kQueueStride) : 1u; }
 
 StageLaunch base_launch(const sa_heom* h) {
     StageLaunch s{};
@@ -761,6 +888,7 @@ StageLaunch base_launch(const sa_heom* h) {
     s.nvar = uint32_t(h->nvar);
     s.nchunks = uint32_t(h->items.size());
     s.err = h->d_err;
+    s.debug = h->debug;
     s.ninst = h->count;
     s.side_stream = h->side;
     s.ev_fork = h->ev_fork;
@@ -802,27 +930,41 @@ int enqueue_step(sa_heom* h, void* y, double dt, size_t slot, cudaStream_t st) {
         L.ys_out = side(h, y);
         L.dt = dt;
         L.stage = s;
-        L.queue = h->d_queue + slot + s;
+        L.queue = h->d_queue + (slot + s) * qstride(h);
         CK(launch_stage(L, h->cfg, h->precision == SA_FP64, st));
     }
     return SA_OK;
 }
 
-// the kernels' error word: bit 0 = a bounded wait on a bulk copy expired
+// the kernels' error word: bit 0 = a bounded wait on a bulk copy expired;
+// reading it clears it
 int read_device_error(sa_heom* h, cudaStream_t st) {
     unsigned int w = 0;
     CK(cudaMemcpyAsync(&w, h->d_err, sizeof(w), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (w) return fail(SA_ERR_TIMEOUT, "a bounded device wait expired in the stage kernel");
+    if (w) {
+        CK(cudaMemsetAsync(h->d_err, 0, sizeof(w), st));
+        CK(cudaStreamSynchronize(st));
+        return fail(SA_ERR_TIMEOUT, "a bounded device wait expired in the stage kernel");
+    }
     return SA_OK;
 }
 
 // the stage kernels copy state slices with 16-byte bulk copies
 bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
 
+// A device call needs a device-built handle and, current on the calling
+// thread, the device the handle's tables live on: a launch with another
+// device current would read them across devices.
 int check_device(const sa_heom* h) {
     if (!h) return fail(SA_ERR_INVALID_ARG, "null handle");
     if (h->host_only) return fail(SA_ERR_STATE, "handle was built with SA_BUILD_HOST_ONLY");
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != h->device)
+        return fail(SA_ERR_STATE, "device " + std::to_string(dev) + " is current, the handle was built on device " +
+                                      std::to_string(h->device));
     return SA_OK;
 }
 
@@ -990,6 +1132,8 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
             return fail(SA_ERR_UNSUPPORTED, "physical representative larger than its FP64 side slots");
         }
         D.pat_begin = uint32_t(pbase);
+        D.lcoef_base = uint32_t(h->lcoef_total);
+        h->lcoef_total += uint64_t(list_slots(hi.m, hi.L));
         h->theta[i] = 0.5 * std::atan2(2.0 * hi.p.g * std::sqrt(double(hi.N)), -hi.p.detuning);
         std::copy(hi.coef_row.begin(), hi.coef_row.end(), h->coef_row_d.begin() + size_t(2) * kCoefPerInst * i);
         std::copy(hi.coef_col.begin(), hi.coef_col.end(), h->coef_col_d.begin() + size_t(2) * kCoefPerInst * i);
@@ -1064,7 +1208,7 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
         e = cudaMalloc(&h->d_rho0, sizeof(double) * 2 * kSideSlots * count);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(rho0)");
     }
-    if (!rc) rc = ensure_queue(h, 64);
+    if (!rc) rc = ensure_queue(h, 4 * kQueueStride);
     if (!rc) {
         e = cudaMalloc(&h->d_err, 64);
         if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, 64);
@@ -1189,6 +1333,14 @@ int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, i
     return SA_OK;
 }
 
+int sa_heom_dump_coefficients(const sa_heom* h, int inst, double* row, double* col) {
+    if (!h || inst < 0 || inst >= h->count || !row || !col) return fail(SA_ERR_INVALID_ARG, "handle, instance, outputs");
+    const HostInstance& hi = h->inst[inst];
+    std::copy(hi.coef_row.begin(), hi.coef_row.end(), row);
+    std::copy(hi.coef_col.begin(), hi.coef_col.end(), col);
+    return SA_OK;
+}
+
 int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* lvd, uint8_t* lvj,
                        uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz) {
     if (!h || !sizes) return fail(SA_ERR_INVALID_ARG, "handle and sizes required");
@@ -1234,6 +1386,114 @@ int sa_heom_dump_ell(const sa_heom* h, int64_t* sizes, uint32_t* wpat, uint32_t*
 int sa_heom_state_bytes(const sa_heom* h, size_t* bytes) {
     if (!h || !bytes) return fail(SA_ERR_INVALID_ARG, "handle, out");
     *bytes = h->state_bytes;
+    return SA_OK;
+}
+
+// ---- checkpoints ------------------------------------------------------------
+// A checkpoint is a 64-byte header followed by the device state buffer as it
+// is (float2 + FP64 side slots, or double2): magic, format version,
+// precision, instance count, variables, state bytes, step index and a 64-bit
+// FNV-1a hash of every instance's parameters and the table layout version,
+// so a resume lands bit for bit on the same handle configuration.
+namespace {
+constexpr uint64_t kCkMagic = 0x4B434D4F45484153ull;  // "SAHEOMCK" in memory order
+constexpr uint32_t kCkVersion = 1;
+constexpr uint32_t kTableVersion = 2;  // bump when the canonical layout changes
+struct CkHeader {
+    uint64_t magic;
+    uint32_t version, precision;
+    int64_t count, nvar;
+    uint64_t state_bytes;
+    int64_t step;
+    uint64_t hash;
+    uint64_t pad;
+};
+static_assert(sizeof(CkHeader) == 64, "checkpoint header is 64 bytes");
+
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+uint64_t config_hash(const sa_heom* h) {
+    uint64_t x = fnv1a(0xcbf29ce484222325ull, &kTableVersion, sizeof(kTableVersion));
+    x = fnv1a(x, &h->precision, sizeof(h->precision));
+    for (int i = 0; i < h->count; ++i) {
+        const sa_params& p = h->inst[i].p;
+        x = fnv1a(x, &p.N, sizeof(p.N));
+        x = fnv1a(x, &p.m, sizeof(p.m));
+        x = fnv1a(x, &p.L, sizeof(p.L));
+        x = fnv1a(x, &p.d, sizeof(p.d));
+        const double v[4] = {p.detuning, p.g, p.kappa, p.term};
+        x = fnv1a(x, v, sizeof(v));
+        x = fnv1a(x, p.c_re, sizeof(double) * size_t(p.m));
+        x = fnv1a(x, p.c_im, sizeof(double) * size_t(p.m));
+        x = fnv1a(x, p.cc_re, sizeof(double) * size_t(p.m));
+        x = fnv1a(x, p.cc_im, sizeof(double) * size_t(p.m));
+        x = fnv1a(x, p.nu_re, sizeof(double) * size_t(p.m));
+        x = fnv1a(x, p.nu_im, sizeof(double) * size_t(p.m));
+    }
+    return x;
+}
+}  // namespace
+
+int sa_heom_config_hash(const sa_heom* h, uint64_t* out) {
+    if (!h || !out) return fail(SA_ERR_INVALID_ARG, "handle, out");
+    *out = config_hash(h);
+    return SA_OK;
+}
+
+int sa_heom_checkpoint_bytes(const sa_heom* h, size_t* bytes) {
+    if (!h || !bytes) return fail(SA_ERR_INVALID_ARG, "handle, out");
+    *bytes = sizeof(CkHeader) + h->state_bytes;
+    return SA_OK;
+}
+
+int sa_heom_checkpoint_save(const sa_heom* h, const void* d_state, int64_t step, void* host_buf, size_t bytes,
+                            void* stream) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!d_state || !host_buf || step < 0) return fail(SA_ERR_INVALID_ARG, "d_state, host_buf, step >= 0");
+    if (bytes < sizeof(CkHeader) + h->state_bytes) return fail(SA_ERR_INVALID_ARG, "host_buf too small");
+    CkHeader H{};
+    H.magic = kCkMagic;
+    H.version = kCkVersion;
+    H.precision = uint32_t(h->precision);
+    H.count = h->count;
+    H.nvar = h->nvar;
+    H.state_bytes = h->state_bytes;
+    H.step = step;
+    H.hash = config_hash(h);
+    std::memcpy(host_buf, &H, sizeof(H));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaMemcpyAsync(static_cast<char*>(host_buf) + sizeof(H), d_state, h->state_bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SA_OK;
+}
+
+int sa_heom_checkpoint_load(const sa_heom* h, const void* host_buf, size_t bytes, void* d_state, int64_t* step,
+                            void* stream) {
+    int rc = check_device(h);
+    if (rc) return rc;
+    if (!d_state || !host_buf) return fail(SA_ERR_INVALID_ARG, "host_buf, d_state");
+    if (bytes < sizeof(CkHeader)) return fail(SA_ERR_STATE, "checkpoint shorter than its header");
+    CkHeader H;
+    std::memcpy(&H, host_buf, sizeof(H));
+    if (H.magic != kCkMagic || H.version != kCkVersion) return fail(SA_ERR_STATE, "not a checkpoint of this format");
+    if (H.precision != uint32_t(h->precision) || H.count != h->count || H.nvar != h->nvar ||
+        H.state_bytes != h->state_bytes)
+        return fail(SA_ERR_STATE, "checkpoint precision or sizes differ from the handle's");
+    if (H.hash != config_hash(h)) return fail(SA_ERR_STATE, "checkpoint parameters differ from the handle's");
+    if (bytes < sizeof(CkHeader) + H.state_bytes) return fail(SA_ERR_STATE, "checkpoint truncated");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaMemcpyAsync(d_state, static_cast<const char*>(host_buf) + sizeof(H), h->state_bytes, cudaMemcpyHostToDevice,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    if (step) *step = H.step;
     return SA_OK;
 }
 
@@ -1379,16 +1639,17 @@ int sa_heom_state_upload(const sa_heom* h, const double* host_x, void* d_state, 
         CK(cudaStreamSynchronize(st));
         return SA_OK;
     }
-    std::vector<float> f(size_t(2) * h->nvar);
-    for (int64_t j = 0; j < 2 * h->nvar; ++j) f[j] = float(host_x[j]);
-    std::vector<double> s(size_t(2) * kSideSlots * h->count, 0.0);
-    for (int i = 0; i < h->count; ++i)
-        for (uint32_t j = 0; j < h->instdev[i].n_rho0; ++j) {
-            s[2 * (kSideSlots * i + j)] = host_x[2 * (h->var_begin[i] + j)];
-            s[2 * (kSideSlots * i + j) + 1] = host_x[2 * (h->var_begin[i] + j) + 1];
-        }
-    CK(cudaMemcpyAsync(d_state, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(side(h, d_state), s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    // SA_FP32_AUX: the complex128 values go to the device as they are, in
+    // chunks through the two RK4 stage-input work vectors (scratch between
+    // steps), and a kernel narrows them there
+    const uint64_t per = h->state_bytes / 16;
+    for (uint64_t n0 = 0, c = 0; n0 < uint64_t(h->nvar); n0 += per, ++c) {
+        const uint64_t cnt = std::min<uint64_t>(per, uint64_t(h->nvar) - n0);
+        void* stage = h->d_work[1 + (c & 1)];
+        CK(cudaMemcpyAsync(stage, host_x + 2 * n0, cnt * 16, cudaMemcpyHostToDevice, st));
+        CK(launch_marshal(static_cast<const InstDev*>(h->d_inst), h->count, n0, cnt, stage, d_state,
+                          side(h, d_state), 1, st));
+    }
     CK(cudaStreamSynchronize(st));
     return SA_OK;
 }
@@ -1403,17 +1664,17 @@ int sa_heom_state_download(const sa_heom* h, const void* d_state, double* host_x
         CK(cudaStreamSynchronize(st));
         return SA_OK;
     }
-    std::vector<float> f(size_t(2) * h->nvar);
-    std::vector<double> s(size_t(2) * kSideSlots * h->count);
-    CK(cudaMemcpyAsync(f.data(), d_state, f.size() * sizeof(float), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(s.data(), side(h, d_state), s.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // SA_FP32_AUX: widened to complex128 on the device, chunk by chunk in the
+    // two RK4 stage-input work vectors, then copied to the caller's buffer
+    const uint64_t per = h->state_bytes / 16;
+    for (uint64_t n0 = 0, c = 0; n0 < uint64_t(h->nvar); n0 += per, ++c) {
+        const uint64_t cnt = std::min<uint64_t>(per, uint64_t(h->nvar) - n0);
+        void* stage = h->d_work[1 + (c & 1)];
+        CK(launch_marshal(static_cast<const InstDev*>(h->d_inst), h->count, n0, cnt, stage,
+                          const_cast<void*>(d_state), side(h, d_state), 0, st));
+        CK(cudaMemcpyAsync(host_x + 2 * n0, stage, cnt * 16, cudaMemcpyDeviceToHost, st));
+    }
     CK(cudaStreamSynchronize(st));
-    for (int64_t j = 0; j < 2 * h->nvar; ++j) host_x[j] = double(f[j]);
-    for (int i = 0; i < h->count; ++i)
-        for (uint32_t j = 0; j < h->instdev[i].n_rho0; ++j) {
-            host_x[2 * (h->var_begin[i] + j)] = s[2 * (kSideSlots * i + j)];
-            host_x[2 * (h->var_begin[i] + j) + 1] = s[2 * (kSideSlots * i + j) + 1];
-        }
     return SA_OK;
 }
 
@@ -1423,7 +1684,7 @@ int sa_heom_rhs(sa_heom* h, const void* d_x, void* d_dx, void* stream) {
     if (!d_x || !d_dx || d_x == d_dx) return fail(SA_ERR_INVALID_ARG, "distinct d_x and d_dx required");
     if (misaligned(d_x) || misaligned(d_dx)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CK(cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int), st));
+    CK(cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int) * qstride(h), st));
     StageLaunch L = base_launch(h);
     L.x_in = d_x;
     L.x_out = d_dx;
@@ -1441,7 +1702,7 @@ int sa_heom_step(sa_heom* h, void* d_state, double dt, void* stream) {
     if (!d_state || !std::isfinite(dt)) return fail(SA_ERR_INVALID_ARG, "d_state and finite dt required");
     if (misaligned(d_state)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CK(cudaMemsetAsync(h->d_queue, 0, 4 * sizeof(unsigned int), st));
+    CK(cudaMemsetAsync(h->d_queue, 0, 4 * sizeof(unsigned int) * qstride(h), st));
     return enqueue_step(h, d_state, dt, 0, st);
 }
 
@@ -1454,10 +1715,10 @@ static int graph_for(sa_heom* h, void* d_state, double dt, int64_t steps, cudaGr
         *out = it->second;
         return SA_OK;
     }
-    int rc = ensure_queue(h, size_t(4 * steps));
+    int rc = ensure_queue(h, size_t(4 * steps) * qstride(h));
     if (rc) return rc;
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int) * 4 * steps, h->cap);
+    cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int) * 4 * steps * qstride(h), h->cap);
     for (int64_t s = 0; s < steps && e == cudaSuccess && rc == SA_OK; ++s) rc = enqueue_step(h, d_state, dt, 4 * s, h->cap);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
@@ -1581,19 +1842,22 @@ int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue) {
     int nb = block > 0 ? block : h->block;
     int nc = chunk > 0 ? chunk : h->chunk;
     int nq = queue >= 0 ? queue : h->use_queue;
-    if (nb < 64 || nb > 256 || nb % 32) return fail(SA_ERR_INVALID_ARG, "block must be 64..256, multiple of 32");
+    const int maxb = (h->kernel == SA_KERNEL_LISTS || h->kernel == SA_KERNEL_SPLIT) ? 1024 : 256;
+    if (nb < 64 || nb > maxb || nb % 32)
+        return fail(SA_ERR_INVALID_ARG, "block must be a multiple of 32 in 64..256 (1024 for the list and split kernels)");
     if (nc % 32 || nc < h->max_u || nc > kMaxItemVars)
         return fail(SA_ERR_INVALID_ARG, "chunk must be a multiple of 32 between the largest pattern and 1024");
     h->block = nb;
     h->chunk = nc;
-    h->use_queue = nq ? 1 : 0;
+    if (nq < 0 || nq > 2) return fail(SA_ERR_INVALID_ARG, "queue must be 0 (static), 1 (grid-wide) or 2 (per SM)");
+    h->use_queue = nq;
     return apply_tuning(h);
 }
 
 int sa_heom_set_kernel(sa_heom* h, int kernel) {
     if (!h) return fail(SA_ERR_INVALID_ARG, "null handle");
-    if (kernel != SA_KERNEL_RECORDS && kernel != SA_KERNEL_LISTS && kernel != SA_KERNEL_ELL)
-        return fail(SA_ERR_INVALID_ARG, "kernel must be SA_KERNEL_RECORDS, SA_KERNEL_LISTS or SA_KERNEL_ELL");
+    if (kernel != SA_KERNEL_RECORDS && kernel != SA_KERNEL_LISTS && kernel != SA_KERNEL_ELL && kernel != SA_KERNEL_SPLIT)
+        return fail(SA_ERR_INVALID_ARG, "kernel must be SA_KERNEL_RECORDS, SA_KERNEL_LISTS, SA_KERNEL_ELL or SA_KERNEL_SPLIT");
     const int old = h->kernel;
     h->kernel = kernel;
     const int rc = apply_tuning(h);
@@ -1632,11 +1896,13 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     // item size outermost: the list kernel's tables are rebuilt per item size only
-    for (int k : {int(SA_KERNEL_RECORDS), int(SA_KERNEL_LISTS), int(SA_KERNEL_ELL)})
+    for (int k : {int(SA_KERNEL_RECORDS), int(SA_KERNEL_LISTS), int(SA_KERNEL_ELL), int(SA_KERNEL_SPLIT)})
     for (int c : chunks)
         for (int b : blocks)
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < 3; ++q) {
                 if (c < h->max_u) continue;
+                // per-SM ranges only for the list and split kernels
+                if (q == 2 && k != SA_KERNEL_LISTS && k != SA_KERNEL_SPLIT) continue;
                 // the ELL kernel has neither work items nor a queue
                 if (k == SA_KERNEL_ELL && (q != 0 || c != std::max(128, (h->max_u + 31) / 32 * 32))) continue;
                 h->kernel = k;
@@ -1684,6 +1950,79 @@ int sa_heom_launches_per_step(const sa_heom* h) {
     return 4 * per_stage;
 }
 
+int sa_heom_set_debug(sa_heom* h, int flags) {
+    if (!h) return fail(SA_ERR_INVALID_ARG, "null handle");
+    if (flags & ~(SA_DEBUG_EXPIRE_WAIT | SA_DEBUG_CORRUPT_RECORD)) return fail(SA_ERR_INVALID_ARG, "unknown flag");
+    if (flags & SA_DEBUG_CORRUPT_RECORD) {
+        if (!h->host_only) return fail(SA_ERR_STATE, "SA_DEBUG_CORRUPT_RECORD needs a host-only handle");
+        HostInstance& hi = h->inst[0];
+        if (hi.rec.empty()) return fail(SA_ERR_STATE, "instance 0 has no connection record");
+        hi.rec[0].target += 1;  // no longer the first variable of a pattern
+    }
+    const int expire = flags & SA_DEBUG_EXPIRE_WAIT;
+    if (expire != (h->debug & SA_DEBUG_EXPIRE_WAIT)) {
+        // the step graphs hold the kernels' parameters: rebuild them
+        for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+        h->graphs.clear();
+    }
+    h->debug = expire;
+    return SA_OK;
+}
+
+// Consistency of the host tables of one instance: pattern, category and
+// variable counts (Eq. uvar-count), multiplicities summing to N, T-ranks,
+// and every connection record (its target is the first variable of a
+// pattern one tier up or down, with the G' the record names, its moved
+// category inside that pattern, its channel and occupation inside m and L).
+static int validate_instance(const HostInstance& hi, int inst) {
+    auto bad = [&](int64_t p, const std::string& what) {
+        return fail(SA_ERR_STATE, "instance " + std::to_string(inst) + ", pattern " + std::to_string(p) + ": " + what);
+    };
+    const int64_t P = hi.P;
+    if (int64_t(hi.cat_off.size()) != P + 1 || int64_t(hi.var_off.size()) != P + 1 ||
+        int64_t(hi.rec_off.size()) != P + 1 || int64_t(hi.G.size()) != P || int64_t(hi.tier.size()) != P)
+        return bad(-1, "table sizes");
+    for (int64_t p = 0; p < P; ++p) {
+        const int G = int(hi.cat_off[p + 1]) - int(hi.cat_off[p]);
+        if (G < 1 || G > kMaxG || G != hi.G[p]) return bad(p, "category count");
+        int64_t msum = 0;
+        int nt = 0;
+        for (uint32_t c = hi.cat_off[p]; c < hi.cat_off[p + 1]; ++c) {
+            if (hi.cat_M[c] < 1) return bad(p, "multiplicity below 1");
+            msum += hi.cat_M[c];
+            if ((hi.cat_M[c] >= 2) != (hi.cat_trank[c] >= 0) || (hi.cat_trank[c] >= 0 && hi.cat_trank[c] != nt))
+                return bad(p, "T-rank");
+            if (hi.cat_trank[c] >= 0) ++nt;
+        }
+        if (msum != hi.N) return bad(p, "multiplicities do not sum to N");
+        if (int64_t(hi.var_off[p + 1] - hi.var_off[p]) != int64_t(G + 1) * (G + 1) + nt) return bad(p, "variable count");
+        if (hi.rec_off[p + 1] < hi.rec_off[p] || hi.rec_off[p + 1] > hi.rec.size()) return bad(p, "record range");
+        for (uint32_t r = hi.rec_off[p]; r < hi.rec_off[p + 1]; ++r) {
+            const Record& R = hi.rec[r];
+            const int ts = R.packed & 31, Gp = (R.packed >> 5) & 31, cid = int(R.packed >> 23);
+            const int k = cid / (2 * kCoefN), n = (cid >> 1) % kCoefN, raise = cid & 1;
+            if (k >= hi.m || n > hi.L) return bad(p, "record " + std::to_string(r) + ": coefficient id");
+            const auto it = std::lower_bound(hi.var_off.begin(), hi.var_off.end() - 1, uint64_t(R.target));
+            if (it == hi.var_off.end() - 1 || *it != R.target)
+                return bad(p, "record " + std::to_string(r) + ": target is not the first variable of a pattern");
+            const int64_t pt = it - hi.var_off.begin();
+            if (int(hi.tier[pt]) != int(hi.tier[p]) + (raise ? 1 : -1))
+                return bad(p, "record " + std::to_string(r) + ": target not one tier away");
+            if (Gp != hi.G[pt] || ts < 1 || ts > Gp) return bad(p, "record " + std::to_string(r) + ": target categories");
+        }
+    }
+    return SA_OK;
+}
+
+int sa_heom_validate(const sa_heom* h) {
+    if (!h) return fail(SA_ERR_INVALID_ARG, "null handle");
+    for (int i = 0; i < h->count; ++i) {
+        const int rc = validate_instance(h->inst[i], i);
+        if (rc) return rc;
+    }
+    return SA_OK;
+}
+
 int sa_heom_device_error(sa_heom* h, void* stream) {
     int rc = check_device(h);
     if (rc) return rc;
@@ -1699,12 +2038,6 @@ int sa_heom_device_error(sa_heom* h, void* stream) {
 // every call in the process; each loaded GPU holds it until the process exits.
 static __device__ __align__(256) double g_obs_scratch[SA_HEOM_NOALLOC_MAX_INSTANCES * 8];
 
-namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_obs_mu;
-double* g_obs_addr[kMaxDevices] = {};  // device address of g_obs_scratch per device ordinal
-}  // namespace
-
 extern "C" int sa_heom_observables_noalloc(sa_heom* h, const void* d_state, double* out, void* stream) {
     int rc = check_device(h);
     if (rc) return rc;
@@ -1713,23 +2046,17 @@ extern "C" int sa_heom_observables_noalloc(sa_heom* h, const void* d_state, doub
         return fail(SA_ERR_UNSUPPORTED, "sa_heom_observables_noalloc serves at most " +
                                             std::to_string(SA_HEOM_NOALLOC_MAX_INSTANCES) + " instances; this batch has " +
                                             std::to_string(h->count));
-    int dev = -1;
-    CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(SA_ERR_UNSUPPORTED, "device ordinal out of range");
-    double* scratch = nullptr;
+    // The host-side name of the array is only a stand-in for it: ask the
+    // runtime for its device address on the current device (check_device made
+    // sure that is the handle's).  The first call on a device loads the array
+    // there; every later call asks again, which allocates nothing and never
+    // leaves a stale address behind (after a cudaDeviceReset, say).
+    void* p = nullptr;
     {
-        // set-up, once per device, with that device current: the host-side
-        // name of the array is only a stand-in, so ask the runtime for its
-        // device address
-        std::lock_guard<std::mutex> lock(g_obs_mu);
-        if (!g_obs_addr[dev]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_obs_scratch);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_obs_scratch)");
-            g_obs_addr[dev] = static_cast<double*>(p);
-        }
-        scratch = g_obs_addr[dev];
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_obs_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_obs_scratch)");
     }
+    double* const scratch = static_cast<double*>(p);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the kernel writes all 8 * count slots it is read back from, so nothing
     // left from an earlier call needs clearing

@@ -86,7 +86,7 @@ template <typename T> struct StageParams {
     const uint32_t* __restrict__ rbase;     // first term row of every round of 32 lanes (+ sentinel)
     const uint32_t* __restrict__ tidx;      // term rows of 32: batch-global target index
     const uint16_t* __restrict__ tcid;      // term rows of 32: coefficient slot in the instance's list table
-    const C* __restrict__ lcoef;            // per instance kListCoefStride slots
+    const C* __restrict__ lcoef;            // per instance list_slots(m, L) slots from InstDev::lcoef_base
     // ELL kernel (lvd: per-variable word, rbase: per warp row, tidx / tcid as above)
     const unsigned char* __restrict__ blobs; // list kernel: per-item table blobs (16-byte aligned)
     const uint32_t* __restrict__ wpat;      // first pattern of every warp row of 32 variables
@@ -113,6 +113,7 @@ template <typename T> struct StageParams {
     int use_queue;
     unsigned int* queue;
     unsigned int* err;                      // device error word (bit 0: a bounded wait expired)
+    int expire_wait;                        // SA_DEBUG_EXPIRE_WAIT: report the first bulk-copy wait as expired
 };
 
 enum { KZ = 0, KX = 1, KY = 2, KP = 3, KS = 4, KT = 5 };
@@ -528,12 +529,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
+// One test of the phase; a thread whose phase is not complete is suspended
+// until it completes or about a millisecond has passed (the suspend-time
+// hint, in ns), so a waiting warp does not spin on the barrier.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000000u)
         : "memory");
     return ok != 0;
 }
@@ -562,6 +567,56 @@ __device__ __forceinline__ Span span(const void* base, size_t first, uint32_t co
     sp.skip = uint32_t(a - lo) / esz;
     return sp;
 }
+
+// The work items of a warp, one at a time (lane 0 draws, the warp shares
+// the result; the caller breaks out when it reaches nchunks).
+//  * mode 0: static striding over the items;
+//  * mode 1: one grid-wide atomic counter;
+//  * mode 2: the items are cut into gridDim.x contiguous ranges, one per CTA,
+//    each with its own counter (queue[blockIdx.x]); a warp drains its CTA's
+//    range, then takes whole ranges to help with from a helper counter
+//    (queue[gridDim.x]) until every range has had one.  The warps of a CTA
+//    then work on neighbouring items, whose tier +/-1 gathers share L1 lines
+//    (with one CTA per SM, the whole SM does).
+struct ItemQueue {
+    unsigned int it, nwarps, range, nr;
+    int mode;
+    __device__ __forceinline__ void init(int use_queue, int wib) {
+        nwarps = gridDim.x * (blockDim.x >> 5);
+        it = blockIdx.x * (blockDim.x >> 5) + unsigned(wib);
+        mode = use_queue;
+        range = blockIdx.x;
+        nr = gridDim.x;
+    }
+    __device__ __forceinline__ unsigned int next(unsigned int* queue, unsigned int nchunks, int lane) {
+        if (mode == 0) {
+            const unsigned int c = it;
+            it += nwarps;
+            return c;
+        }
+        unsigned int t = 0;
+        if (mode == 1) {
+            if (lane == 0) t = atomicAdd(queue, 1u);
+            return __shfl_sync(0xffffffffu, t, 0);
+        }
+        if (lane == 0) {
+            t = nchunks;
+            while (range < nr) {
+                const unsigned int lo = unsigned((uint64_t(range) * nchunks) / nr);
+                const unsigned int hi = unsigned((uint64_t(range + 1) * nchunks) / nr);
+                if (*reinterpret_cast<volatile unsigned int*>(queue + range) < hi - lo) {
+                    const unsigned int k = atomicAdd(queue + range, 1u);
+                    if (k < hi - lo) {
+                        t = lo + k;
+                        break;
+                    }
+                }
+                range = atomicAdd(queue + nr, 1u);  // next range to help with (nr or more: done)
+            }
+        }
+        return __shfl_sync(0xffffffffu, t, 0);
+    }
+};
 
 // Per-warp shared memory of the list kernel.  The operand area op[] holds the
 // item's stage-input slice (chunk entries, after a skip of 0 or 1 entries
@@ -621,7 +676,7 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
 // A bounded wait that expires sets bit 0 of the error word; the warp then
 // waits (bounded again) for its copies and stops.
 template <typename T, bool FP64SIDE>
-__global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
+__global__ void __launch_bounds__(1024) list_stage_kernel(StageParams<T> P) {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -633,21 +688,13 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
-    const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
-    unsigned int it = blockIdx.x * (blockDim.x >> 5) + wib;
+    ItemQueue Q;
+    Q.init(P.use_queue, wib);
     const T dtT = T(P.dt);
     const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
     uint32_t parity = 0;
     for (;;) {
-        unsigned int c;
-        if (P.use_queue) {
-            unsigned int t = 0;
-            if (lane == 0) t = atomicAdd(P.queue, 1u);
-            c = __shfl_sync(0xffffffffu, t, 0);
-        } else {
-            c = it;
-            it += nwarps;
-        }
+        const unsigned int c = Q.next(P.queue, P.nchunks, lane);
         if (c >= P.nchunks) break;
         const ItemDesc d = P.items[c];
         const uint32_t v0 = d.v0, nv = d.nv;
@@ -675,7 +722,9 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
         if (sp.bytes) bulk_g2s(dst, sp.src, sp.bytes, S.bar);
         if (lane == 4 && d.row1 > d.row0) bulk_prefetch_l2(P.tidx + size_t(d.row0) * 32, (d.row1 - d.row0) * 128u);
         if (lane == 5 && d.row1 > d.row0) bulk_prefetch_l2(P.tcid + size_t(d.row0) * 32, (d.row1 - d.row0) * 64u);
-        if (!__all_sync(0xffffffffu, mbar_wait(S.bar, parity))) {
+        // SA_DEBUG_EXPIRE_WAIT takes the expiry path without testing the
+        // barrier; the drain below still waits (bounded) for the copies
+        if (!__all_sync(0xffffffffu, !P.expire_wait && mbar_wait(S.bar, parity))) {
             if (lane == 0) atomicOr(P.err, 1u);
             mbar_wait(S.bar, parity);
             return;
@@ -799,6 +848,216 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
     }
 }
 
+// ---- split kernel ----------------------------------------------------------
+// Per-warp shared memory of the split kernel: the list kernel's operand area
+// (stage-input slice, R, C, Z sums, zero), the hierarchy sums of the item's
+// variables (hs, item-local index) and the item's table blob (SplitLayout).
+template <typename T> struct SplitSmem {
+    using C = typename Cx<T>::t;
+    uint64_t* bar;
+    C* op;
+    C* hs;
+    unsigned char* blob;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ size_t split_smem_bytes(int item) {
+    const size_t cs = 2 * sizeof(T);
+    return 16 + al16(cs * (list_opZero(item) + 3)) + al16(cs * item) +
+           split_layout<T>(kItemPats, uint32_t(list_ncat(item)), uint32_t(item), uint32_t(item)).bytes;
+}
+
+template <typename T>
+__device__ __forceinline__ SplitSmem<T> carve_split(unsigned char* p, int item) {
+    using C = typename Cx<T>::t;
+    SplitSmem<T> W;
+    W.bar = reinterpret_cast<uint64_t*>(p);  p += 16;
+    W.op = reinterpret_cast<C*>(p);          p += al16(sizeof(C) * (list_opZero(item) + 3));
+    W.hs = reinterpret_cast<C*>(p);          p += al16(sizeof(C) * item);
+    W.blob = p;
+    return W;
+}
+
+// One warp per work item, staged like the list kernel (the item's stage-input
+// slice and table blob by TMA bulk copies on the warp's mbarrier; its RK4
+// state, accumulator and term rows bulk-prefetched into L2), then three
+// passes:
+//  * grouped sums R_q, C_q per category and the Z sums per pattern (Eqs.
+//    grouped-row-sum, grouped-column-sum, HZ) into the operand area;
+//  * the hierarchy pass: lanes take the item's variables that have
+//    hierarchy terms in rounds of 32, sorted by term count, and sum their
+//    terms (Eqs. uvar-up, uvar-down) from coalesced rows of (target index,
+//    coefficient slot) entries into hs;
+//  * the update pass: lanes take the item's variables in memory order, so
+//    that the RK4 state, the accumulator and both outputs move in coalesced
+//    rows: diag * v - i g (op[a] - op[b]) + hs, then the RK4 stage update.
+// A bounded wait that expires sets bit 0 of the error word; the warp then
+// waits (bounded again) for its copies and stops.
+template <typename T, bool FP64SIDE>
+__global__ void __launch_bounds__(1024) split_stage_kernel(StageParams<T> P) {
+    using C = typename Cx<T>::t;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int chunk = P.chunk;
+    const SplitSmem<T> S = carve_split<T>(smem + size_t(wib) * split_smem_bytes<T>(chunk), chunk);
+    if (lane == 0) {
+        mbar_init(S.bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    ItemQueue Q;
+    Q.init(P.use_queue, wib);
+    const T dtT = T(P.dt);
+    const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
+    uint32_t parity = 0;
+    for (;;) {
+        const unsigned int c = Q.next(P.queue, P.nchunks, lane);
+        if (c >= P.nchunks) break;
+        const ItemDesc d = P.items[c];
+        const uint32_t v0 = d.v0, nv = d.nv;
+        // ---- bulk copies (lanes 0, 3) and L2 prefetches (lanes 1, 2, 4, 5) of the item
+        const Span sx = span(P.x_in, v0, nv, sizeof(C));
+        Span sp;
+        void* dst = nullptr;
+        if (lane == 0) { sp = sx; dst = S.op; }
+        else if (lane == 1 || lane == 2) {
+            const Span t = span(lane == 1 ? P.y : static_cast<const C*>(P.acc), v0, P.stage > 0 ? nv : 0u, sizeof(C));
+            if (t.bytes) bulk_prefetch_l2(t.src, t.bytes);
+            sp.bytes = 0;
+        }
+        else if (lane == 3) {
+            sp.src = reinterpret_cast<const char*>(P.blobs) + size_t(d.blob16) * 16;
+            sp.bytes = d.blob_bytes;
+            dst = S.blob;
+        }
+        else sp.bytes = 0;
+        const uint32_t total = __reduce_add_sync(0xffffffffu, sp.bytes);
+        // the copies overwrite only what the warp has read (the previous
+        // item's slice and blob), after the __syncwarp that ended it
+        if (lane == 0) mbar_expect_tx(S.bar, total);
+        __syncwarp();
+        if (sp.bytes) bulk_g2s(dst, sp.src, sp.bytes, S.bar);
+        if (lane == 4 && d.row1 > d.row0) bulk_prefetch_l2(P.tidx + size_t(d.row0) * 32, (d.row1 - d.row0) * 128u);
+        if (lane == 5 && d.row1 > d.row0) bulk_prefetch_l2(P.tcid + size_t(d.row0) * 32, (d.row1 - d.row0) * 64u);
+        // SA_DEBUG_EXPIRE_WAIT takes the expiry path without testing the
+        // barrier; the drain below still waits (bounded) for the copies
+        if (!__all_sync(0xffffffffu, !P.expire_wait && mbar_wait(S.bar, parity))) {
+            if (lane == 0) atomicOr(P.err, 1u);
+            mbar_wait(S.bar, parity);
+            return;
+        }
+        parity ^= 1u;
+        const int np = int(d.np);
+        const uint32_t ncat = d.ncat, nl = d.nl;
+        const SplitLayout B = split_layout<T>(uint32_t(np), ncat, nv, nl);
+        const ItemPat* const ph = reinterpret_cast<const ItemPat*>(S.blob + B.pat);
+        const uint32_t* const cw = reinterpret_cast<const uint32_t*>(S.blob + B.cw);
+        const T* const cM = reinterpret_cast<const T*>(S.blob + B.cM);
+        const uint8_t* const cj = S.blob + B.cj;
+        C* const op = S.op + sx.skip;
+        C* const opR = op + list_opR(chunk);
+        C* const opC = op + list_opC(chunk);
+        C* const opZ = op + list_opZ(chunk);
+        if (lane == 0) op[list_opZero(chunk)] = mk(T(0), T(0));
+        // ---- grouped sums per category (Eqs. grouped-row-sum,
+        // grouped-column-sum) and per pattern (Eq. HZ)
+        for (uint32_t cl = lane; cl < ncat; cl += 32) {
+            const ItemPat h = ph[cj[cl]];
+            const int G = h.G;
+            const int cb = int(h.cat_rel);
+            const int q = int(cl) - cb + 1;
+            const C* xp = op + h.var_rel;
+            const T Mq = cM[cl];
+            C Rs = xp[2 * G + q];
+            if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((cw[cl] >> 15) & 31)], Rs);
+            C Cq = Rs;
+            for (int e2 = 1; e2 <= G; ++e2) {
+                if (e2 == q) continue;
+                const T Mb = cM[cb + e2 - 1];
+                Rs = caxpy(Mb, xp[loc_S_d(G, q, e2)], Rs);
+                Cq = caxpy(Mb, xp[loc_S_d(G, e2, q)], Cq);
+            }
+            opR[cl] = Rs;
+            opC[cl] = Cq;
+        }
+        for (int j = lane; j < np; j += 32) {
+            const ItemPat h = ph[j];
+            const int G = h.G;
+            const int cb = int(h.cat_rel);
+            const C* xp = op + h.var_rel;
+            C zs = mk(T(0), T(0));
+            for (int q = 1; q <= G; ++q) zs = caxpy(cM[cb + q - 1], csub(xp[q], xp[G + q]), zs);
+            opZ[j] = zs;
+        }
+        // ---- hierarchy pass: rounds of 32 lanes over the variables with terms
+        const C* __restrict__ X = P.x_in;
+        const C* __restrict__ cf = P.lcoef + *reinterpret_cast<const uint32_t*>(S.blob);
+        const uint16_t* const lw = reinterpret_cast<const uint16_t*>(S.blob + B.lw);
+        const uint32_t* const rb = reinterpret_cast<const uint32_t*>(S.blob + B.rb);
+        C* const hs = S.hs;
+        for (uint32_t i0 = 0, rho = 0; i0 < nl; i0 += 32, ++rho) {
+            const uint32_t i = i0 + lane;
+            const bool on = i < nl;
+            const uint32_t r0 = rb[rho], r1 = rb[rho + 1];
+            const uint32_t* __restrict__ ti = P.tidx + size_t(r0) * 32 + lane;
+            const uint16_t* __restrict__ tc = P.tcid + size_t(r0) * 32 + lane;
+            const int nt = int(r1 - r0);
+            C hv = mk(T(0), T(0));
+            int t2 = 0;
+            for (; t2 + 4 <= nt; t2 += 4) {
+                uint32_t ix[4], cx[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {  // term rows stream through L2 only
+                    ix[u] = __ldcg(ti + (t2 + u) * 32);
+                    cx[u] = __ldcg(tc + (t2 + u) * 32);
+                }
+                C xv[4], cv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    xv[u] = __ldg(X + ix[u]);
+                    cv[u] = __ldg(cf + cx[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) hv = cfma(cv[u], xv[u], hv);
+            }
+            for (; t2 < nt; ++t2) hv = cfma(__ldg(cf + __ldcg(tc + t2 * 32)), __ldg(X + __ldcg(ti + t2 * 32)), hv);
+            if (on) hs[lw[i]] = hv;
+        }
+        __syncwarp();
+        // ---- update pass: the item's variables in memory order
+        const uint32_t* const mw = reinterpret_cast<const uint32_t*>(S.blob + B.mw);
+        const C* const pd = reinterpret_cast<const C*>(S.blob + B.pd);
+        for (uint32_t i = lane; i < nv; i += 32) {
+            const uint32_t w = mw[i];
+            if (w >> 31) continue;  // the physical representative: the FP64 kernel's
+            const uint32_t a = w & 2047u, b = (w >> 11) & 2047u, j = (w >> 22) & 31u, cls = (w >> 27) & 7u;
+            const C v = op[i];
+            const C* const pj = pd + kSplitPd * j;
+            const T g = pj[5].x;
+            const C t = csub(op[a], op[b]);
+            C dv = mk(g * t.y, -g * t.x);
+            dv = cfma(pj[cls], v, dv);
+            if ((w >> 30) & 1u) dv = cadd(dv, hs[i]);
+            const uint32_t vg = v0 + i;
+            if (P.stage < 0) {
+                P.x_out[vg] = dv;
+            } else if (P.stage == 0) {
+                P.acc[vg] = dv;
+                P.x_out[vg] = caxpy(aT, dv, v);  // x_in is y in the first stage
+            } else if (P.stage == 3) {
+                const C yv = __ldcg(P.y + vg), av = __ldcg(P.acc + vg);
+                P.y_out[vg] = caxpy(dtT / T(6), cadd(av, dv), yv);
+            } else {
+                const C yv = __ldcg(P.y + vg), av = __ldcg(P.acc + vg);
+                P.acc[vg] = caxpy(T(2), dv, av);
+                P.x_out[vg] = caxpy(aT, dv, yv);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // ---- ELL kernel ------------------------------------------------------------
 // Grouped sums of the stage input, one thread each: R_q and C_q of every
 // category (Eqs. grouped-row-sum, grouped-column-sum: P_q + (M_q - 1) T_q +
@@ -899,7 +1158,7 @@ __global__ void __launch_bounds__(256) ell_stage_kernel(StageParams<T> P) {
     C dv = mk(g * t.y, -g * t.x);
     dv = cfma(diag, xv, dv);
     // hierarchy terms (Eqs. uvar-up, uvar-down)
-    const C* __restrict__ cf = P.lcoef + h.inst * uint32_t(kListCoefStride);
+    const C* __restrict__ cf = P.lcoef + I.lcoef_base;
     const uint32_t r0 = __ldg(P.rbase + w), r1 = __ldg(P.rbase + w + 1);
     const uint32_t* __restrict__ ti = P.tidx + size_t(r0) * 32 + lane;
     const uint16_t* __restrict__ tc = P.tcid + size_t(r0) * 32 + lane;
@@ -1077,6 +1336,40 @@ __global__ void init_rho0_kernel(const InstDev* __restrict__ inst, int ninst, co
     }
 }
 
+// State marshalling of SA_FP32_AUX handles, one chunk of variables
+// [n0, n0 + cnt) at a time, through a device staging buffer that holds the
+// caller's complex128 values: narrow them to the float2 state and copy the
+// physical representatives' variables exactly into their FP64 side slots
+// (narrow), or widen the float2 state into the staging buffer with the
+// physical representatives taken from their side slots (widen).
+__global__ void narrow_state_kernel(const double2* __restrict__ stage, uint64_t n0, uint64_t cnt,
+                                    float2* __restrict__ main32) {
+    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const double2 v = stage[i];
+    main32[n0 + i] = make_float2(float(v.x), float(v.y));
+}
+__global__ void widen_state_kernel(const float2* __restrict__ main32, uint64_t n0, uint64_t cnt,
+                                   double2* __restrict__ stage) {
+    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const float2 v = main32[n0 + i];
+    stage[i] = make_double2(double(v.x), double(v.y));
+}
+// one thread per side slot: the physical representative's variables that
+// fall in the chunk
+__global__ void side_state_kernel(const InstDev* __restrict__ inst, int ninst, uint64_t n0, uint64_t cnt,
+                                  double2* __restrict__ stage, double2* __restrict__ side64, int to_side) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / kSideSlots, j = t % kSideSlots;
+    if (i >= ninst) return;
+    const InstDev& I = inst[i];
+    const uint64_t v = uint64_t(I.var_begin) + uint64_t(j);
+    if (uint32_t(j) >= I.n_rho0 || v < n0 || v >= n0 + cnt) return;
+    if (to_side) side64[I.side + j] = stage[v - n0];
+    else stage[v - n0] = side64[I.side + j];
+}
+
 // -- end: physical-representative kernels
 
 // ---- host launch wrappers (called from api.cu) -----------------------------
@@ -1085,6 +1378,7 @@ size_t stage_smem_bytes(int item, int block, bool fp64, int kernel) {
     if (kernel == SA_KERNEL_ELL) return 0;
     size_t w;
     if (kernel == SA_KERNEL_LISTS) w = fp64 ? list_smem_bytes<double>(item) : list_smem_bytes<float>(item);
+    else if (kernel == SA_KERNEL_SPLIT) w = fp64 ? split_smem_bytes<double>(item) : split_smem_bytes<float>(item);
     else w = fp64 ? warp_smem_bytes<double>(item) : warp_smem_bytes<float>(item);
     return w * size_t(block / 32);
 }
@@ -1127,6 +1421,8 @@ static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int n
         if (grid > 0) ell_stage_kernel<T, SIDE><<<grid, cfg.block, 0, st>>>(p);
     } else if (cfg.kernel == SA_KERNEL_LISTS) {
         list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+    } else if (cfg.kernel == SA_KERNEL_SPLIT) {
+        split_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     } else {
         stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     }
@@ -1190,6 +1486,7 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.use_queue = cfg.use_queue;
     p.queue = s.queue;
     p.err = s.err;
+    p.expire_wait = (s.debug & SA_DEBUG_EXPIRE_WAIT) ? 1 : 0;
     return p;
 }
 
@@ -1227,6 +1524,10 @@ cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm)
         if (fp64) return occupancy_of(list_stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
         return occupancy_of(list_stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
     }
+    if (cfg.kernel == SA_KERNEL_SPLIT) {
+        if (fp64) return occupancy_of(split_stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
+        return occupancy_of(split_stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
+    }
     if (fp64) return occupancy_of(stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
     return occupancy_of(stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
 }
@@ -1245,6 +1546,25 @@ cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0,
                              void* main32, void* side64, cudaStream_t st) {
     init_rho0_kernel<<<(ninst + 127) / 128, 128, 0, st>>>(inst, ninst, rho0, stride, static_cast<double2*>(main64),
                                                           static_cast<float2*>(main32), static_cast<double2*>(side64));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_marshal(const InstDev* inst, int ninst, uint64_t n0, uint64_t cnt, void* stage, void* main32,
+                           void* side64, int to_device, cudaStream_t st) {
+    if (cnt == 0) return cudaSuccess;
+    const unsigned grid = unsigned((cnt + 255) / 256);
+    const unsigned sgrid = unsigned((size_t(ninst) * kSideSlots + 255) / 256);
+    if (to_device) {
+        narrow_state_kernel<<<grid, 256, 0, st>>>(static_cast<const double2*>(stage), n0, cnt,
+                                                  static_cast<float2*>(main32));
+        side_state_kernel<<<sgrid, 256, 0, st>>>(inst, ninst, n0, cnt, static_cast<double2*>(stage),
+                                                 static_cast<double2*>(side64), 1);
+    } else {
+        widen_state_kernel<<<grid, 256, 0, st>>>(static_cast<const float2*>(main32), n0, cnt,
+                                                 static_cast<double2*>(stage));
+        side_state_kernel<<<sgrid, 256, 0, st>>>(inst, ninst, n0, cnt, static_cast<double2*>(stage),
+                                                 static_cast<double2*>(side64), 0);
+    }
     return cudaGetLastError();
 }
 

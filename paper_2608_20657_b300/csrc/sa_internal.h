@@ -75,7 +75,8 @@ struct InstDev {
     uint32_t var_begin;  // first variable
     uint32_t n_rho0;     // variables of the physical representative (5 for d = 0, up to 26 for d = 3)
     uint32_t pat_begin;  // first pattern (the empty pattern)
-    uint32_t pad2[3];
+    uint32_t lcoef_base; // first slot of the instance's list/ELL coefficient table
+    uint32_t pad2[2];
     double term;         // terminator strength Delta (0: off)
     double pad3;
 };
@@ -176,14 +177,65 @@ SA_HOST_DEVICE inline BlobLayout blob_layout(uint32_t np, uint32_t ncat, uint32_
     L.bytes = L.lvj + a16(nl);
     return L;
 }
+// Byte offsets of the sections of a split-kernel item blob (SA_KERNEL_SPLIT;
+// every section 16-byte aligned): a 16-byte header whose first word is the
+// coefficient base of the item (its first instance's table; the item's term
+// slots are relative to it), patterns (ItemPat), per pattern six complex T --
+// the diagonal coefficient of each variable class (0 S and T, 1 X, 2 Y, 3 Z,
+// 4 P: -Gamma_Lambda, the cavity loss, -/+ i detuning, the terminator) and
+// the coupling g as (g, 0) --, category words, multiplicities (T), owning
+// pattern of every category (u8), the round table of the hierarchy pass, one
+// word per variable in memory order (u32, split_word) and the hierarchy-pass
+// lane words (u16: item-local variable index).
+struct SplitLayout {
+    uint32_t pat, pd, cw, cM, cj, rb, mw, lw, bytes;
+};
+constexpr int kSplitPd = 6;  // complex entries per pattern in the pd section
+template <typename T>
+SA_HOST_DEVICE inline SplitLayout split_layout(uint32_t np, uint32_t ncat, uint32_t nv, uint32_t nl) {
+    auto a16 = [](uint32_t b) { return (b + 15u) & ~15u; };
+    const uint32_t nrounds = (nl + 31u) / 32u;
+    SplitLayout L;
+    L.pat = 16;
+    L.pd = L.pat + a16(np * uint32_t(sizeof(ItemPat)));
+    L.cw = L.pd + a16(np * uint32_t(kSplitPd * 2 * sizeof(T)));
+    L.cM = L.cw + a16(ncat * 4u);
+    L.cj = L.cM + a16(ncat * uint32_t(sizeof(T)));
+    L.rb = L.cj + a16(ncat);
+    L.mw = L.rb + a16((nrounds + 1u) * 4u);
+    L.lw = L.mw + a16(nv * 4u);
+    L.bytes = L.lw + a16(nl * 2u);
+    return L;
+}
+// memory-order word of a variable in the split kernel: operand-area indices
+// a, b of its commutator term -i g (op[a] - op[b]), its pattern j in the
+// item, its diagonal class, whether it has hierarchy terms, and whether the
+// FP64 physical-representative kernel integrates it instead (skip)
+SA_HOST_DEVICE inline uint32_t split_word(uint32_t a, uint32_t b, uint32_t j, uint32_t cls, uint32_t has,
+                                          uint32_t skip) {
+    return a | (b << 11) | (j << 22) | (cls << 27) | (has << 30) | (skip << 31);
+}
 constexpr int kItemPats = 32;     // patterns per work item (5-bit local index)
 constexpr int kMaxItemVars = 1024; // variables per work item (10-bit local index)
-// list kernel: coefficient slots per instance -- row coefficients, column
-// coefficients, row + column (the P_q lower terms), then one zero slot for
-// padded entries
-constexpr int kListCoefZero = 3 * kCoefPerInst;
-constexpr int kListCoefStride = 3 * kCoefPerInst + 8;
+// List and ELL kernels: the coefficient table of one instance, compact so
+// that a warp's coefficient loads stay in a few cache lines.  Slot 0 is zero
+// (padded entries); then, for each channel k, occupation n = 0..L before the
+// move and direction (lower, raise), the row, column and row + column (the
+// two lower terms of P_q) coefficients side by side.  An instance holds
+// list_slots(m, L) = 2 + 6 m (L + 1) slots (the last one unused; an even
+// count, so every table starts 16-byte aligned in both precisions).
+constexpr int kListCoefZero = 0;
+inline int list_slot(int L, int cid, int side3) {
+    const int k = cid / (2 * kCoefN), n = (cid >> 1) % kCoefN, raise = cid & 1;
+    return 1 + ((k * (L + 1) + n) * 2 + raise) * 3 + side3;
+}
+inline int list_slots(int m, int L) { return 2 + 6 * m * (L + 1); }
 
+// Work-queue counters one stage launch owns: one grid-wide counter (queue
+// mode 1), or one counter per CTA and a helper counter (queue mode 2, see
+// ItemQueue in kernels.cu), so grids of mode 2 have fewer than kQueueStride
+// CTAs.  Zeroed before every launch.
+constexpr int kQueueStride = 2048;
 // launch description shared by api.cu and kernels.cu (type-erased pointers)
 struct LaunchCfg {
     int block;      // threads per CTA
@@ -205,12 +257,15 @@ struct StageLaunch {
     const void* x_in; void* x_out; const void* y; void* acc; void* y_out;
     const void* xs_in; void* xs_out; const void* ys; void* accs; void* ys_out;
     double dt; int stage; unsigned int* queue; unsigned int* err;
+    int debug;  // SA_DEBUG_* flags (include/sa_heom.h)
     int ninst;
     // SA_FP32_AUX: the FP64 physical-representative kernel runs on a side
     // stream, forked before and joined after the stage kernel
     void* side_stream; void* ev_fork; void* ev_join;
 };
 
+// api.cu: the detail sa_heom_last_error reports
+void set_error(const std::string& msg);
 // builder.cpp
 int build_instance(const sa_params& p, HostInstance& out, std::string& err);
 int64_t expand_terms(const HostInstance& hi, int64_t* var, int64_t* src, int32_t* k, int32_t* n, int32_t* dir,

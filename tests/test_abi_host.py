@@ -90,3 +90,22 @@ def test_terminator_strength_matches_oracle(K):
         assert abs(got - ref) <= 1e-15 + 1e-12 * abs(ref)
     with pytest.raises(S.SaHeomError):
         S.bath_terminator(-0.01, 0.05, 0.025, K)
+
+
+@pytest.mark.parametrize("kind", ["cavity", "bright", "up", "lp", "random"])
+@pytest.mark.parametrize("N", [1, 2, 7, 1000])
+def test_initial_vars_match_oracle(kind, N):
+    """sa_heom_initial_vars against the oracle's initial unique variables
+    (Eqs. cavity-/bright-initial-uvar, upper-/lower-polariton-initial, the
+    random invariant state of its draws)."""
+    import workloads as W
+    from tests._helpers import oracle_rho0
+
+    if kind == "random" and N == 1:
+        pytest.skip("the oracle's random state needs a dark block (N >= 2)")
+    w = dict(W.WORKLOADS["w3"], N=N, init=kind)
+    draws = W.random_rho_draws()
+    got = S.rho0_vars(w, draws)
+    ref = np.array(oracle_rho0(w, draws), complex)
+    n = 5 if N >= 2 else 4
+    assert np.max(np.abs(got[:n] - ref[:n])) <= 1e-15

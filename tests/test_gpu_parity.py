@@ -42,7 +42,7 @@ def _rhs_gpu(h, x):
     return h.download(dx)
 
 
-KERNELS = [S.SA_KERNEL_RECORDS, S.SA_KERNEL_LISTS, S.SA_KERNEL_ELL]
+KERNELS = [S.SA_KERNEL_RECORDS, S.SA_KERNEL_LISTS, S.SA_KERNEL_ELL, S.SA_KERNEL_SPLIT]
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -223,7 +223,8 @@ def test_invariants_on_gpu():
 
 def test_edge_cases():
     """N = 1 (4 physical variables), L = 0 (the empty pattern only: Rabi
-    closed form), a pattern count above one chunk's 256-pattern limit."""
+    closed form), and many more patterns than one work item's 32-pattern
+    limit."""
     bath = {"c": np.array([0.1 + 0.05j]), "cc": np.array([0.1 - 0.05j]), "nu": np.array([0.3 + 0j])}
     for N, L in [(1, 4), (1, 0)]:
         sa = oracle.SA(N, 1, L, bath, 0.05, 0.1, 0.02)
@@ -239,7 +240,7 @@ def test_edge_cases():
     Om = math.hypot(2 * gsn, det)
     assert np.max(np.abs(obs[:, 1] - (1 - (2 * gsn / Om) ** 2 * np.sin(Om * t / 2) ** 2))) < 1e-9
     # many tiny patterns: N = 1, m = 6, L = 5 gives 462 four-variable patterns,
-    # so chunks hit the 256-pattern limit before the variable limit
+    # so work items hit the 32-pattern limit before the variable limit
     bath6 = _generic_bath(6, 2)
     sa = oracle.SA(1, 6, 5, bath6, 0.1, 0.2, 0.0)
     h = S.Heom(S.make_params(1, 6, 5, bath6, detuning=0.1, g=0.2))

@@ -20,7 +20,7 @@ import oracle.bath as OB
 import paper_2608_20657_b300 as S
 import workloads as W
 
-ZERO_SLOT = 1536
+ZERO_SLOT = 0
 
 
 def _generic_bath(m, seed):
@@ -30,21 +30,32 @@ def _generic_bath(m, seed):
             "nu": rng.uniform(0.2, 1.2, m) + 1j * rng.uniform(-0.3, 0.3, m)}
 
 
-def _slot_coefficients(bath):
-    """Coefficient of every list slot: row, column, row + column, zero."""
+def _slot_coefficients(bath, L):
+    """Coefficient of every list slot of one instance: slot 0 zero, then for
+    each channel k, occupation n = 0..L before the move and direction (lower,
+    raise) the row, column and row + column coefficients side by side."""
     c, cc = np.asarray(bath["c"]), np.asarray(bath["cc"])
-    out = np.zeros(ZERO_SLOT + 1, complex)
-    for cid in range(512):
-        k, n, up = (cid >> 1) // 32, (cid >> 1) % 32, cid & 1
-        if k >= c.size:
-            continue
+    out = np.zeros(1 + 6 * c.size * (L + 1), complex)
+    for k in range(c.size):
         ac = abs(c[k])
-        if up:
-            row, col = -1j * np.sqrt((n + 1) * ac), 1j * np.sqrt((n + 1) * ac)
-        else:
-            row, col = -1j * np.sqrt(n / ac) * c[k], 1j * np.sqrt(n / ac) * cc[k]
-        out[cid], out[512 + cid], out[1024 + cid] = row, col, row + col
+        for n in range(L + 1):
+            for up in (0, 1):
+                if up:
+                    row, col = -1j * np.sqrt((n + 1) * ac), 1j * np.sqrt((n + 1) * ac)
+                else:
+                    row, col = -1j * np.sqrt(n / ac) * c[k], 1j * np.sqrt(n / ac) * cc[k]
+                s0 = 1 + ((k * (L + 1) + n) * 2 + up) * 3
+                out[s0], out[s0 + 1], out[s0 + 2] = row, col, row + col
     return out
+
+
+def _global_coefficients(baths, sas):
+    """The instances' slot tables one after another (each padded to an even
+    length) and the first slot of each."""
+    tabs = [_slot_coefficients(b, sa.L) for b, sa in zip(baths, sas)]
+    tabs = [np.concatenate([t, np.zeros(t.size % 2, complex)]) for t in tabs]
+    base = np.concatenate([[0], np.cumsum([t.size for t in tabs])])
+    return np.concatenate(tabs), base
 
 
 def _layout(G, M):
@@ -81,9 +92,10 @@ def _eval_lists(lib, sas, baths, x, insts):
             ids = P["ids"][p]
             ggam.append(sum(vec[v % len(vec)] @ nu for v in ids if v >= 0))  # molecule 1: ids V + v
         cbase += P["cat_off"][-1]
-    coefs = [_slot_coefficients(b) for b in baths]
+    coefs, cbase = _global_coefficients(baths, sas)
     for it in L["items"]:
         p0, np_, v0, nv, c0, ncat, r0, nl = (int(v) for v in it)
+        cf = coefs[cbase[ginst[p0]]:]  # term slots are relative to the item's first instance
         op = np.zeros(ZZ + 1, complex)
         op[:nv] = x[v0:v0 + nv]
         for j in range(np_):
@@ -130,7 +142,7 @@ def _eval_lists(lib, sas, baths, x, insts):
                 wt = [2.0, 1.0, 1.0, 0.0, 0.0][cls]  # terminator weight
                 diag = -(ggam[p].real + lossf * kap + wt * sa_p.term) + 1j * (dim - ggam[p].imag)
                 dv = diag * op[l] - 1j * g * (op[a] - op[b])
-                dv += np.sum(coefs[inst][slot[:n]] * x[idx[:n]])
+                dv += np.sum(cf[slot[:n]] * x[idx[:n]])
                 out[vg] = dv
                 seen.append(l)
             # a round is as long as its longest list, and lists are sorted
@@ -208,7 +220,7 @@ def _eval_ell(lib, sas, baths, x):
             gM.append(P["cat_M"][P["cat_off"][p]:P["cat_off"][p + 1]])
             ggam.append(sum(vec[v % len(vec)] @ nu for v in P["ids"][p] if v >= 0))
     gvar.append(x.size)
-    coefs = [_slot_coefficients(b) for b in baths]
+    coefs = [_slot_coefficients(b, sa.L) for b, sa in zip(baths, sas)]
     out = np.zeros(x.size, complex)
     nw = E["wpat"].size
     assert nw == (x.size + 31) // 32

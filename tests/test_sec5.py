@@ -15,12 +15,13 @@ from tests._helpers import oracle_initial, oracle_sa, physical
 def test_unit_constants():
     """With hbar = 1, 1 cm^-1 is 2 pi c rad/fs: hbar = 5308.8 cm^-1 fs
     (textbook value); k_B T at 300 K is about 208 cm^-1 (Sec. V)."""
-    f = S.problems.RAD_PER_FS_PER_CM
+    f = S.binding.unit_cm_to_rad_fs(1.0)
     assert abs(1.0 / f - 5308.837) < 1e-3
-    kT_cm = S.problems.KB_CM_PER_K * 300.0
+    kT_cm = S.binding.unit_kT_rad_fs(300.0) / f
     assert abs(kT_cm - 208.0) < 1.0
     u = physical(W.sec5(10))
     assert abs(u["kT"] / f - kT_cm) < 1e-9
+    assert abs(S.in_library_units(W.sec5(10))["kT"] - u["kT"]) <= 1e-15 * u["kT"]
 
 
 @pytest.mark.parametrize("N", (1, 2, 3) + W.SEC5_N)
@@ -42,7 +43,7 @@ def test_params_agree_with_oracle(N, init):
         a, b = getattr(p, f)[0], getattr(q, f)[0]
         assert abs(a - b) <= 1e-14 * abs(b), f
     # Omega_R = 2 g sqrt(N) = 500 cm^-1 at every N
-    assert abs(2 * p.g * math.sqrt(N) / S.problems.RAD_PER_FS_PER_CM - 500.0) < 1e-9
+    assert abs(2 * p.g * math.sqrt(N) / S.binding.unit_cm_to_rad_fs(1.0) - 500.0) < 1e-9
     assert p.term > 0
     ph = S.phys_vars(w)
     x = oracle_initial(sa, w)

@@ -89,10 +89,17 @@ def _check_tables(N, m, L, d):
         assert np.all(np.bincount(sub["side"]) == pairs.size // 2)
     o = np.stack([ot[k][keep] for k in ("var", "src", "k", "n", "dir", "side")], 1)
     l = np.stack([lt[k] for k in ("var", "src", "k", "n", "dir", "side")], 1)
-    o = o[np.lexsort(o.T[::-1])]
-    l = l[np.lexsort(l.T[::-1])]
+    oi, li = np.lexsort(o.T[::-1]), np.lexsort(l.T[::-1])
+    o, l = o[oi], l[li]
     assert o.shape == l.shape
     assert np.array_equal(o, l)
+    # the FP64 coefficient of every term, exactly (IEEE equality) as the
+    # oracle forms it per term
+    row, col = lib.dump_coefficients(0)
+    cid = (l[:, 2] * 32 + l[:, 3]) * 2 + (l[:, 4] > 0)
+    lc = np.where(l[:, 5] == 0, row[cid], col[cid])
+    oc = ot["coef"][keep][oi]
+    assert np.all(lc.real == oc.real) and np.all(lc.imag == oc.imag)
     assert oracle.errors() == 0
 
 

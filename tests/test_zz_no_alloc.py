@@ -30,6 +30,31 @@ def test_noalloc_observables_match(precision):
         assert np.all(np.isfinite(got))
 
 
+def test_noalloc_full_array_and_side_stream():
+    """A batch of exactly SA_HEOM_NOALLOC_MAX_INSTANCES small instances fills
+    the whole fixed array; calls on a stream of the caller's own, twice in a
+    row with the state advanced in between, match sa_heom_observables."""
+    bath = S.bath_drude_lorentz(0.01, 0.05, 0.025, S.BATH_HIGH_T, 0)
+    n = S.NOALLOC_MAX_INSTANCES
+    assert n == 4096
+    rng = np.random.default_rng(11)
+    ps = [S.make_params(2, len(bath["c"]), 0, bath, detuning=float(rng.uniform(-0.05, 0.05)),
+                        g=float(rng.uniform(0.01, 0.1))) for _ in range(n)]
+    h = S.Heom(ps, precision=S.SA_FP64)
+    st = h.new_state()
+    h.init_state(st, np.tile(np.array([1, 0, 0, 0, 0], complex), (n, 1)))
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for call in range(2):
+        with torch.cuda.stream(side):
+            h.propagate(st, 0.05, 40, observe=False, stream=side)
+            got = h.observables_noalloc(st, stream=side)
+        ref = h.observables(st, stream=side)
+        assert got.shape == ref.shape == (n, 8)
+        assert np.max(np.abs(got - ref)) <= 1e-14, call
+        assert np.all(np.abs(got[:, 1] - 1.0) > 1e-6), call  # the cavity population moved
+
+
 def test_noalloc_rejects_oversized_batch():
     bath = S.bath_drude_lorentz(0.01, 0.05, 0.025, S.BATH_HIGH_T, 0)
     p = S.make_params(2, len(bath["c"]), 0, bath, g=0.03)
