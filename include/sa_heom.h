@@ -75,6 +75,7 @@ enum {
 
 enum { SA_FP64 = 0, SA_FP32_AUX = 1 };                  /* precision */
 enum { SA_BUILD_DEVICE = 0, SA_BUILD_HOST_ONLY = 1 };   /* build flags */
+enum { SA_BUILD_ADJOINT_REPS = 2 };  /* sa_heom_build_representatives: the adjoint shortcut */
 enum { SA_BATH_HIGH_T = 0, SA_BATH_MATSUBARA = 1, SA_BATH_PADE = 2 };
 
 /*
@@ -358,7 +359,13 @@ int sa_heom_init_physical(const sa_heom* h, const double* phys, void* d_state, v
  *     one d = 0 parameter set *p (d must be 0): instance 0 |c><c| (d = 0),
  *     1 |e_1><c|, 2 |c><e_1|, 3 |e_1><e_1| (d = 1), 4 |e_1><e_2| (d = 2,
  *     only for N >= 2).  Same precision and flags as sa_heom_build; the
- *     handle takes every sa_heom_* call.
+ *     handle takes every sa_heom_* call.  With flags | SA_BUILD_ADJOINT_REPS
+ *     the |c><e_1| propagation is left out (instances 0 |c><c|, 1 |e_1><c|,
+ *     2 |e_1><e_1|, 3 |e_1><e_2|: a fifth fewer variables) and its response
+ *     is taken as the adjoint of the |e_1><c| response (Eq. adjoint-
+ *     preservation).  That holds when the propagator maps adjoints to
+ *     adjoints, which needs every nu_k real and c-check_k = conj(c_k)
+ *     exactly; other baths get SA_ERR_INVALID_ARG.
  *   sa_heom_init_representatives: the factorised initial state of each
  *     instance with its unit operator.  Asynchronous on `stream`.
  *   sa_heom_reconstruct_dense: after any propagation of that state, writes

@@ -22,7 +22,7 @@ PHYS_SLOTS = 32  # SA_HEOM_PHYS_SLOTS
 NOALLOC_MAX_INSTANCES = 4096  # SA_HEOM_NOALLOC_MAX_INSTANCES
 
 SA_FP64, SA_FP32_AUX = 0, 1
-SA_BUILD_DEVICE, SA_BUILD_HOST_ONLY = 0, 1
+SA_BUILD_DEVICE, SA_BUILD_HOST_ONLY, SA_BUILD_ADJOINT_REPS = 0, 1, 2
 SA_KERNEL_RECORDS, SA_KERNEL_LISTS, SA_KERNEL_ELL, SA_KERNEL_SPLIT = 0, 1, 2, 3
 SA_DEBUG_EXPIRE_WAIT, SA_DEBUG_CORRUPT_RECORD = 1, 2
 INIT_KINDS = {"cavity": 0, "bright": 1, "up": 2, "lp": 3, "random": 4, "localised": 5, "superposed": 6}
@@ -251,17 +251,23 @@ def counts(p: Params) -> dict:
 class Heom:
     """A built batch of instances (sa_heom handle)."""
 
-    def __init__(self, params, precision: int = SA_FP64, host_only: bool = False, representatives: bool = False):
+    def __init__(self, params, precision: int = SA_FP64, host_only: bool = False, representatives: bool = False,
+                 adjoint: bool = False):
         """representatives: params is one d = 0 set; the handle is the batch of
-        its representative propagations (sa_heom_build_representatives)."""
+        its representative propagations (sa_heom_build_representatives);
+        adjoint: leave out the |c><e_1| propagation (SA_BUILD_ADJOINT_REPS)."""
         flags = SA_BUILD_HOST_ONLY if host_only else SA_BUILD_DEVICE
         h = ctypes.c_void_p()
         if representatives:
             p = params[0] if isinstance(params, (list, tuple)) else params
+            flags |= SA_BUILD_ADJOINT_REPS if adjoint else 0
             _check(lib().sa_heom_build_representatives(ctypes.byref(p), precision, flags, ctypes.byref(h)),
                    "sa_heom_build_representatives")
             params = []
-            for d in ([0, 1, 1, 1, 2] if p.N >= 2 else [0, 1, 1, 1]):
+            ds = [0, 1, 1, 1, 2] if p.N >= 2 else [0, 1, 1, 1]
+            if adjoint:
+                del ds[2]
+            for d in ds:
                 q = Params.from_buffer_copy(p)
                 q.d = d
                 params.append(q)

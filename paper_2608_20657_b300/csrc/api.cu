@@ -26,7 +26,7 @@ cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0,
 size_t recon_workspace_bytes(int64_t n);
 cudaError_t launch_marshal(const InstDev* inst, int ninst, uint64_t n0, uint64_t cnt, void* stage, void* main32,
                            void* side64, int to_device, cudaStream_t st);
-cudaError_t launch_reconstruct(const InstDev* inst, const int16_t* loc, int nrep, const void* main64,
+cudaError_t launch_reconstruct(const InstDev* inst, const RepSrc* src, const void* main64,
                                const void* side64, const void* rho0, int64_t n, void* rho_t, void* ws,
                                cudaStream_t st);
 }  // namespace sa
@@ -139,8 +139,9 @@ struct sa_heom {
     std::map<std::tuple<const void*, uint64_t, int64_t>, cudaGraphExec_t> graphs;
     // representative propagations (sa_heom_build_representatives)
     bool reps = false;
-    std::vector<int16_t> rep_loc;  // kReps x kRepSlots local indices in the physical pattern, -1: absent
-    void* d_rep_loc = nullptr;
+    std::vector<RepSrc> rep_src;   // kReps x kRepSlots: where each response value lives
+    std::vector<int> rep_unit;     // per instance: the slot of its unit initial operator
+    void* d_rep_loc = nullptr;     // device copy of rep_src
     void* d_recon_ws = nullptr;
     size_t recon_ws = 0;
 };
@@ -319,6 +320,27 @@ void list_item(const sa_heom* h, const ItemDesc& d, ListItem& W) {
 // Per-item table blobs of the list kernel (BlobLayout): everything the warp
 // stages for an item besides the state slices, contiguous and 16-byte
 // aligned so that one bulk copy brings it.
+// the diagonal coefficients of a pattern's variable classes (0 S T, 1 X,
+// 2 Y, 3 Z, 4 P: -Gamma_Lambda, the cavity loss (1/2 per cavity label),
+// -/+ i detuning for X / Y, the terminator -Delta w) and (g, 0), as the list
+// and split blobs hold them
+template <typename V>
+void pattern_diag(const sa_heom* h, uint32_t p, V* e) {
+    const sa_params& q = h->inst[h->hdr[p].inst].p;
+    const double gre = h->gamma_d[2 * size_t(p)], gim = h->gamma_d[2 * size_t(p) + 1];
+    const double lossf[5] = {0.0, 0.5, 0.5, 1.0, 0.0}, wt[5] = {2.0, 1.0, 1.0, 0.0, 0.0};
+    const double dim[5] = {0.0, -q.detuning, q.detuning, 0.0, 0.0};
+    for (int cl = 0; cl < 5; ++cl) {
+        e[2 * cl] = V(-(gre + lossf[cl] * q.kappa + wt[cl] * q.term));
+        e[2 * cl + 1] = V(dim[cl] - gim);
+    }
+    e[10] = V(q.g);
+    e[11] = V(0);
+}
+
+// Per-item table blobs of the list kernel (BlobLayout): everything the warp
+// stages for an item besides the state slices, contiguous and 16-byte
+// aligned so that one bulk copy brings it.
 template <typename V>
 int build_blobs(sa_heom* h) {
     const size_t ni = h->items.size();
@@ -336,16 +358,14 @@ int build_blobs(sa_heom* h) {
     } catch (const std::bad_alloc&) {
         return fail(SA_ERR_OOM, "host memory for the list-kernel blobs");
     }
-    const std::vector<double>& gam = h->gamma_d;
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t c = 0; c < int64_t(ni); ++c) {
         const ItemDesc& d = h->items[c];
         const BlobLayout B = blob_layout<V>(d.np, d.ncat, d.nl);
         uint8_t* o = &h->blobs[size_t(d.blob16) * 16];
+        *reinterpret_cast<uint32_t*>(o) = h->instdev[h->hdr[d.p0].inst].lcoef_base;  // term slots are relative to it
         ItemPat* ph = reinterpret_cast<ItemPat*>(o + B.pat);
-        PatConst<V>* ic = reinterpret_cast<PatConst<V>*>(o + B.ic);
-        int nic = 0;
-        V* gm = reinterpret_cast<V*>(o + B.gam);
+        V* pd = reinterpret_cast<V*>(o + B.pd);
         uint32_t* cw = reinterpret_cast<uint32_t*>(o + B.cw);
         V* cM = reinterpret_cast<V*>(o + B.cM);
         uint8_t* cj = o + B.cj;
@@ -358,19 +378,8 @@ int build_blobs(sa_heom* h) {
             ph[j].cat_rel = uint16_t(H.cat_off - d.c0);
             ph[j].G = H.G;
             ph[j].tier = H.tier;
-            if (j == 0 || H.inst != h->hdr[d.p0 + j - 1].inst) {
-                // the item's instances, in order (at most kItemInsts)
-                const sa_params& q = h->inst[H.inst].p;
-                ic[nic].g = V(q.g);
-                ic[nic].det = V(q.detuning);
-                ic[nic].kap = V(q.kappa);
-                ic[nic].term = V(q.term);
-                ic[nic].coef_base = h->instdev[h->hdr[d.p0].inst].lcoef_base;  // the item's term slots are relative to it
-                ++nic;
-            }
-            ph[j].islot = uint16_t(nic - 1);
-            gm[2 * j] = V(gam[2 * size_t(d.p0 + j)]);
-            gm[2 * j + 1] = V(gam[2 * size_t(d.p0 + j) + 1]);
+            ph[j].islot = 0;
+            pattern_diag<V>(h, d.p0 + j, pd + size_t(2 * kSplitPd) * j);
             for (uint32_t cl = H.cat_off - d.c0; cl < h->hdr[d.p0 + j + 1].cat_off - d.c0; ++cl) cj[cl] = uint8_t(j);
         }
         for (uint32_t cl = 0; cl < d.ncat; ++cl) {
@@ -422,7 +431,6 @@ int build_split_blobs(sa_heom* h) {
     } catch (const std::bad_alloc&) {
         return fail(SA_ERR_OOM, "host memory for the split-kernel blobs");
     }
-    const std::vector<double>& gam = h->gamma_d;
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t c = 0; c < int64_t(ni); ++c) {
         const ItemDesc& d = h->items[c];
@@ -444,20 +452,7 @@ int build_split_blobs(sa_heom* h) {
             ph[j].G = H.G;
             ph[j].tier = H.tier;
             ph[j].islot = 0;
-            // diagonal coefficients by class (0 S T, 1 X, 2 Y, 3 Z, 4 P):
-            // -Gamma_Lambda, the cavity loss (1/2 per cavity label), -/+ i
-            // detuning for X / Y and the terminator -Delta w
-            const sa_params& q = h->inst[H.inst].p;
-            const double gre = gam[2 * size_t(d.p0 + j)], gim = gam[2 * size_t(d.p0 + j) + 1];
-            const double lossf[5] = {0.0, 0.5, 0.5, 1.0, 0.0}, wt[5] = {2.0, 1.0, 1.0, 0.0, 0.0};
-            const double dim[5] = {0.0, -q.detuning, q.detuning, 0.0, 0.0};
-            V* e = pd + size_t(2 * kSplitPd) * j;
-            for (int cl = 0; cl < 5; ++cl) {
-                e[2 * cl] = V(-(gre + lossf[cl] * q.kappa + wt[cl] * q.term));
-                e[2 * cl + 1] = V(dim[cl] - gim);
-            }
-            e[10] = V(q.g);
-            e[11] = V(0);
+            pattern_diag<V>(h, d.p0 + j, pd + size_t(2 * kSplitPd) * j);
             for (uint32_t cl = H.cat_off - d.c0; cl < h->hdr[d.p0 + j + 1].cat_off - d.c0; ++cl) cj[cl] = uint8_t(j);
         }
         for (uint32_t cl = 0; cl < d.ncat; ++cl) {
@@ -816,8 +811,6 @@ int apply_tuning(sa_heom* h) {
     const bool persistent = h->use_queue || h->kernel == SA_KERNEL_LISTS || h->kernel == SA_KERNEL_SPLIT;
     h->cfg.grid = persistent ? int(std::min<int64_t>(int64_t(h->num_sms) * occ, blocks_needed)) : int(blocks_needed);
     if (h->cfg.grid < 1) h->cfg.grid = 1;
-    if (h->use_queue == 2 && h->cfg.grid >= kQueueStride)
-        return fail(SA_ERR_UNSUPPORTED, "queue mode 2 needs fewer than 2048 CTAs");
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     return SA_OK;
@@ -850,9 +843,6 @@ int ensure_queue(sa_heom* h, size_t slots) {
     h->queue_slots = n;
     return SA_OK;
 }
-
-// queue counters each stage launch owns (queue mode 2: per-SM ranges)
-size_t qstride(const sa_heom* h) { return h->use_queue == 2 ? size_t(kQueueStride) : 1u; }
 
 StageLaunch base_launch(const sa_heom* h) {
     StageLaunch s{};
@@ -930,7 +920,7 @@ int enqueue_step(sa_heom* h, void* y, double dt, size_t slot, cudaStream_t st) {
         L.ys_out = side(h, y);
         L.dt = dt;
         L.stage = s;
-        L.queue = h->d_queue + (slot + s) * qstride(h);
+        L.queue = h->d_queue + slot + s;
         CK(launch_stage(L, h->cfg, h->precision == SA_FP64, st));
     }
     return SA_OK;
@@ -1208,7 +1198,7 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
         e = cudaMalloc(&h->d_rho0, sizeof(double) * 2 * kSideSlots * count);
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(rho0)");
     }
-    if (!rc) rc = ensure_queue(h, 4 * kQueueStride);
+    if (!rc) rc = ensure_queue(h, 64);
     if (!rc) {
         e = cudaMalloc(&h->d_err, 64);
         if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, 64);
@@ -1547,39 +1537,69 @@ int sa_heom_init_physical(const sa_heom* hc, const double* phys, void* d_state, 
 int sa_heom_build_representatives(const sa_params* p, int precision, int flags, sa_heom** out) {
     if (!p || !out) return fail(SA_ERR_INVALID_ARG, "params and out required");
     if (p->d != 0) return fail(SA_ERR_INVALID_ARG, "representatives are built from a d = 0 parameter set");
-    // |c><c| (d = 0), |e_1><c|, |c><e_1|, |e_1><e_1| (d = 1), |e_1><e_2| (d = 2, N >= 2)
-    const int count = p->N >= 2 ? kReps : kReps - 1;
+    if (flags & ~(SA_BUILD_HOST_ONLY | SA_BUILD_ADJOINT_REPS)) return fail(SA_ERR_INVALID_ARG, "unknown build flag");
+    const bool adj = (flags & SA_BUILD_ADJOINT_REPS) != 0;
+    if (adj)
+        for (int k = 0; k < p->m && k < SA_HEOM_MAXM; ++k)
+            if (p->nu_im[k] != 0.0 || p->cc_re[k] != p->c_re[k] || p->cc_im[k] != -p->c_im[k])
+                return fail(SA_ERR_INVALID_ARG, "the adjoint shortcut needs real nu_k and c-check_k = conj(c_k) "
+                                                "(channel " + std::to_string(k) + ")");
+    // the representatives |c><c| (d = 0), |e_1><c|, |c><e_1|, |e_1><e_1|
+    // (d = 1), |e_1><e_2| (d = 2, N >= 2); with the adjoint shortcut the
+    // |c><e_1| propagation is left out and its response is the adjoint of
+    // the |e_1><c| one
+    const int nrep = p->N >= 2 ? kReps : kReps - 1;
+    int rinst[kReps];  // batch instance of each representative (-1: none)
     sa_params ps[kReps];
+    int count = 0;
     const int dd[kReps] = {0, 1, 1, 1, 2};
-    for (int r = 0; r < count; ++r) {
-        ps[r] = *p;
-        ps[r].d = dd[r];
+    const int unit[kReps] = {RZ, RX1, RY1, RP1, RS12};
+    std::vector<int> units;
+    for (int r = 0; r < kReps; ++r) {
+        rinst[r] = -1;
+        if (r >= nrep || (adj && r == 2)) continue;
+        ps[count] = *p;
+        ps[count].d = dd[r];
+        units.push_back(unit[r]);
+        rinst[r] = count++;
     }
-    int rc = sa_heom_build(ps, count, precision, flags, out);
+    int rc = sa_heom_build(ps, count, precision, flags & SA_BUILD_HOST_ONLY, out);
     if (rc) return rc;
     sa_heom* h = *out;
     h->reps = true;
-    h->rep_loc.assign(size_t(kReps) * kRepSlots, int16_t(-1));
-    for (int r = 0; r < count; ++r) {
-        const HostInstance& hi = h->inst[r];
+    h->rep_unit = units;
+    h->rep_src.assign(size_t(kReps) * kRepSlots, RepSrc{-1, 0, 0});
+    // an adjoint response swaps the row and column labels: X <-> Y, S_qr <-> S_rq
+    const int adjslot[kRepSlots] = {RZ, RY1, RY2, RY3, RX1, RX2, RX3, RP1, RP2, RP3,
+                                    RS21, RS31, RS12, RS32, RS13, RS23, RT};
+    for (int r = 0; r < nrep; ++r) {
+        const bool via_adj = adj && r == 2;
+        const int i = via_adj ? rinst[1] : rinst[r];
+        const HostInstance& hi = h->inst[i];
         const int G = hi.G[0];
-        int16_t* L = &h->rep_loc[size_t(r) * kRepSlots];
-        auto put = [&](int slot, int64_t loc) { L[slot] = int16_t(loc); };
-        put(RZ, loc_Z());
+        int16_t loc[kRepSlots];
+        for (int k = 0; k < kRepSlots; ++k) loc[k] = -1;
+        loc[RZ] = int16_t(loc_Z());
         for (int q = 1; q <= std::min(G, 3); ++q) {
-            put(RX1 + q - 1, loc_X(G, q));
-            put(RY1 + q - 1, loc_Y(G, q));
-            put(RP1 + q - 1, loc_P(G, q));
+            loc[RX1 + q - 1] = int16_t(loc_X(G, q));
+            loc[RY1 + q - 1] = int16_t(loc_Y(G, q));
+            loc[RP1 + q - 1] = int16_t(loc_P(G, q));
         }
         const int sq[6][2] = {{1, 2}, {1, 3}, {2, 1}, {2, 3}, {3, 1}, {3, 2}};
         for (int k = 0; k < 6; ++k)
-            if (sq[k][0] <= G && sq[k][1] <= G) put(RS12 + k, loc_S(G, sq[k][0], sq[k][1]));
-        if (hi.h[0] >= 1) put(RT, loc_T(G, 0));  // only the others' category can hold two molecules
+            if (sq[k][0] <= G && sq[k][1] <= G) loc[RS12 + k] = int16_t(loc_S(G, sq[k][0], sq[k][1]));
+        if (hi.h[0] >= 1) loc[RT] = int16_t(loc_T(G, 0));  // only the others' category can hold two molecules
+        for (int k = 0; k < kRepSlots; ++k) {
+            RepSrc& S = h->rep_src[size_t(r) * kRepSlots + k];
+            S.loc = loc[via_adj ? adjslot[k] : k];
+            S.inst = int8_t(i);
+            S.conj = via_adj ? 1 : 0;
+        }
     }
     if (!h->host_only) {
-        cudaError_t e = cudaMalloc(&h->d_rep_loc, h->rep_loc.size() * sizeof(int16_t));
+        cudaError_t e = cudaMalloc(&h->d_rep_loc, h->rep_src.size() * sizeof(RepSrc));
         if (e == cudaSuccess)
-            e = cudaMemcpy(h->d_rep_loc, h->rep_loc.data(), h->rep_loc.size() * sizeof(int16_t), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(h->d_rep_loc, h->rep_src.data(), h->rep_src.size() * sizeof(RepSrc), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             sa_heom_destroy(h);
             *out = nullptr;
@@ -1595,10 +1615,21 @@ int sa_heom_init_representatives(const sa_heom* hc, void* d_state, void* stream)
     if (rc) return rc;
     if (!h->reps) return fail(SA_ERR_STATE, "not a representatives handle");
     if (!d_state) return fail(SA_ERR_INVALID_ARG, "d_state required");
-    // the unit operator of each representative: Z, X_1, Y_1, P_1, S_12
+    // the unit operator of each propagated representative: Z, X_1, Y_1, P_1 or S_12
     std::vector<double> phys(size_t(2) * kSideSlots * h->count, 0.0);
-    const int slot[kReps] = {RZ, RX1, RY1, RP1, RS12};
-    for (int r = 0; r < h->count; ++r) phys[size_t(2) * kSideSlots * r + 2 * h->rep_loc[size_t(r) * kRepSlots + slot[r]]] = 1.0;
+    for (int i = 0; i < h->count; ++i) {
+        const HostInstance& hi = h->inst[i];
+        const int G = hi.G[0];
+        int64_t l = 0;
+        switch (h->rep_unit[i]) {
+            case RZ: l = loc_Z(); break;
+            case RX1: l = loc_X(G, 1); break;
+            case RY1: l = loc_Y(G, 1); break;
+            case RP1: l = loc_P(G, 1); break;
+            default: l = loc_S(G, 1, 2); break;
+        }
+        phys[size_t(2) * kSideSlots * i + 2 * l] = 1.0;
+    }
     return init_from(h, phys.data(), 2 * kSideSlots, d_state, stream);
 }
 
@@ -1623,7 +1654,7 @@ int sa_heom_reconstruct_dense(sa_heom* h, const void* d_state, const void* d_rho
             return e == cudaErrorMemoryAllocation ? fail(SA_ERR_OOM, "reconstruction workspace") : cuda_fail(e, "cudaMalloc");
         h->recon_ws = need;
     }
-    CK(launch_reconstruct(static_cast<const InstDev*>(h->d_inst), static_cast<const int16_t*>(h->d_rep_loc), h->count,
+    CK(launch_reconstruct(static_cast<const InstDev*>(h->d_inst), static_cast<const RepSrc*>(h->d_rep_loc),
                           h->precision == SA_FP64 ? d_state : nullptr, side(h, d_state), d_rho0, n, d_rho_t,
                           h->d_recon_ws, static_cast<cudaStream_t>(stream)));
     return SA_OK;
@@ -1684,7 +1715,7 @@ int sa_heom_rhs(sa_heom* h, const void* d_x, void* d_dx, void* stream) {
     if (!d_x || !d_dx || d_x == d_dx) return fail(SA_ERR_INVALID_ARG, "distinct d_x and d_dx required");
     if (misaligned(d_x) || misaligned(d_dx)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CK(cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int) * qstride(h), st));
+    CK(cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int), st));
     StageLaunch L = base_launch(h);
     L.x_in = d_x;
     L.x_out = d_dx;
@@ -1702,7 +1733,7 @@ int sa_heom_step(sa_heom* h, void* d_state, double dt, void* stream) {
     if (!d_state || !std::isfinite(dt)) return fail(SA_ERR_INVALID_ARG, "d_state and finite dt required");
     if (misaligned(d_state)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CK(cudaMemsetAsync(h->d_queue, 0, 4 * sizeof(unsigned int) * qstride(h), st));
+    CK(cudaMemsetAsync(h->d_queue, 0, 4 * sizeof(unsigned int), st));
     return enqueue_step(h, d_state, dt, 0, st);
 }
 
@@ -1715,10 +1746,10 @@ static int graph_for(sa_heom* h, void* d_state, double dt, int64_t steps, cudaGr
         *out = it->second;
         return SA_OK;
     }
-    int rc = ensure_queue(h, size_t(4 * steps) * qstride(h));
+    int rc = ensure_queue(h, size_t(4 * steps));
     if (rc) return rc;
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int) * 4 * steps * qstride(h), h->cap);
+    cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int) * 4 * steps, h->cap);
     for (int64_t s = 0; s < steps && e == cudaSuccess && rc == SA_OK; ++s) rc = enqueue_step(h, d_state, dt, 4 * s, h->cap);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
@@ -1842,15 +1873,12 @@ int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue) {
     int nb = block > 0 ? block : h->block;
     int nc = chunk > 0 ? chunk : h->chunk;
     int nq = queue >= 0 ? queue : h->use_queue;
-    const int maxb = (h->kernel == SA_KERNEL_LISTS || h->kernel == SA_KERNEL_SPLIT) ? 1024 : 256;
-    if (nb < 64 || nb > maxb || nb % 32)
-        return fail(SA_ERR_INVALID_ARG, "block must be a multiple of 32 in 64..256 (1024 for the list and split kernels)");
+    if (nb < 64 || nb > 256 || nb % 32) return fail(SA_ERR_INVALID_ARG, "block must be 64..256, multiple of 32");
     if (nc % 32 || nc < h->max_u || nc > kMaxItemVars)
         return fail(SA_ERR_INVALID_ARG, "chunk must be a multiple of 32 between the largest pattern and 1024");
     h->block = nb;
     h->chunk = nc;
-    if (nq < 0 || nq > 2) return fail(SA_ERR_INVALID_ARG, "queue must be 0 (static), 1 (grid-wide) or 2 (per SM)");
-    h->use_queue = nq;
+    h->use_queue = nq ? 1 : 0;
     return apply_tuning(h);
 }
 
@@ -1899,10 +1927,8 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     for (int k : {int(SA_KERNEL_RECORDS), int(SA_KERNEL_LISTS), int(SA_KERNEL_ELL), int(SA_KERNEL_SPLIT)})
     for (int c : chunks)
         for (int b : blocks)
-            for (int q = 0; q < 3; ++q) {
+            for (int q = 0; q < 2; ++q) {
                 if (c < h->max_u) continue;
-                // per-SM ranges only for the list and split kernels
-                if (q == 2 && k != SA_KERNEL_LISTS && k != SA_KERNEL_SPLIT) continue;
                 // the ELL kernel has neither work items nor a queue
                 if (k == SA_KERNEL_ELL && (q != 0 || c != std::max(128, (h->max_u + 31) / 32 * 32))) continue;
                 h->kernel = k;

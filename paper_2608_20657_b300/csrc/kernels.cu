@@ -569,24 +569,15 @@ __device__ __forceinline__ Span span(const void* base, size_t first, uint32_t co
 }
 
 // The work items of a warp, one at a time (lane 0 draws, the warp shares
-// the result; the caller breaks out when it reaches nchunks).
-//  * mode 0: static striding over the items;
-//  * mode 1: one grid-wide atomic counter;
-//  * mode 2: the items are cut into gridDim.x contiguous ranges, one per CTA,
-//    each with its own counter (queue[blockIdx.x]); a warp drains its CTA's
-//    range, then takes whole ranges to help with from a helper counter
-//    (queue[gridDim.x]) until every range has had one.  The warps of a CTA
-//    then work on neighbouring items, whose tier +/-1 gathers share L1 lines
-//    (with one CTA per SM, the whole SM does).
+// the result; the caller breaks out when it reaches nchunks): static
+// striding over the items (use_queue 0) or one grid-wide atomic counter (1).
 struct ItemQueue {
-    unsigned int it, nwarps, range, nr;
+    unsigned int it, nwarps;
     int mode;
     __device__ __forceinline__ void init(int use_queue, int wib) {
         nwarps = gridDim.x * (blockDim.x >> 5);
         it = blockIdx.x * (blockDim.x >> 5) + unsigned(wib);
         mode = use_queue;
-        range = blockIdx.x;
-        nr = gridDim.x;
     }
     __device__ __forceinline__ unsigned int next(unsigned int* queue, unsigned int nchunks, int lane) {
         if (mode == 0) {
@@ -595,25 +586,7 @@ struct ItemQueue {
             return c;
         }
         unsigned int t = 0;
-        if (mode == 1) {
-            if (lane == 0) t = atomicAdd(queue, 1u);
-            return __shfl_sync(0xffffffffu, t, 0);
-        }
-        if (lane == 0) {
-            t = nchunks;
-            while (range < nr) {
-                const unsigned int lo = unsigned((uint64_t(range) * nchunks) / nr);
-                const unsigned int hi = unsigned((uint64_t(range + 1) * nchunks) / nr);
-                if (*reinterpret_cast<volatile unsigned int*>(queue + range) < hi - lo) {
-                    const unsigned int k = atomicAdd(queue + range, 1u);
-                    if (k < hi - lo) {
-                        t = lo + k;
-                        break;
-                    }
-                }
-                range = atomicAdd(queue + nr, 1u);  // next range to help with (nr or more: done)
-            }
-        }
+        if (lane == 0) t = atomicAdd(queue, 1u);
         return __shfl_sync(0xffffffffu, t, 0);
     }
 };
@@ -676,7 +649,7 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
 // A bounded wait that expires sets bit 0 of the error word; the warp then
 // waits (bounded again) for its copies and stops.
 template <typename T, bool FP64SIDE>
-__global__ void __launch_bounds__(1024) list_stage_kernel(StageParams<T> P) {
+__global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -773,14 +746,48 @@ __global__ void __launch_bounds__(1024) list_stage_kernel(StageParams<T> P) {
             opZ[j] = zs;
         }
         __syncwarp();
-        // ---- the lanes' variables, one round of 32 at a time
+        // ---- the lanes' variables, one round of 32 at a time.  The first four
+        // term rows of every round are loaded one round ahead, so that a
+        // round's gathers wait on one memory latency instead of two.
         const C* __restrict__ X = P.x_in;
+        const C* __restrict__ cf = P.lcoef + *reinterpret_cast<const uint32_t*>(S.blob);
+        const C* const pd = reinterpret_cast<const C*>(S.blob + B.pd);
         const uint32_t* const lvd = reinterpret_cast<const uint32_t*>(S.blob + B.lvd);
         const uint8_t* const lvj = S.blob + B.lvj;
         const uint32_t* const rb = reinterpret_cast<const uint32_t*>(S.blob + B.rb);
-        for (uint32_t i0 = 0, rho = 0; i0 < nl; i0 += 32, ++rho) {
-            const uint32_t i = i0 + lane;
+        const uint32_t nrounds = (nl + 31) / 32;
+        uint32_t nix[4], ncx[4];
+        auto first_rows = [&](uint32_t rho) {
+            const uint32_t r0 = rb[rho];
+            const uint32_t nt = rb[rho + 1] - r0;
+            const uint32_t* __restrict__ ti = P.tidx + size_t(r0) * 32 + lane;
+            const uint16_t* __restrict__ tc = P.tcid + size_t(r0) * 32 + lane;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                nix[u] = uint32_t(u) < nt ? __ldcg(ti + u * 32) : v0;
+                ncx[u] = uint32_t(u) < nt ? uint32_t(__ldcg(tc + u * 32)) : 0u;
+            }
+        };
+        if (nrounds) first_rows(0);
+        for (uint32_t rho = 0; rho < nrounds; ++rho) {
+            const uint32_t i = rho * 32 + lane;
             const bool on = i < nl;
+            const uint32_t r0 = rb[rho];
+            const int nt = int(rb[rho + 1] - r0);
+            uint32_t ix[4], cx[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                ix[u] = nix[u];
+                cx[u] = ncx[u];
+            }
+            if (rho + 1 < nrounds) first_rows(rho + 1);
+            // gathers of the first (up to) four terms
+            C xv[4], cv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xv[u] = __ldg(X + ix[u]);
+                cv[u] = __ldg(cf + cx[u]);
+            }
             // lanes past the end take operand 0 and the zero-coefficient rows
             const uint32_t w0 = on ? lvd[i] : 0u;
             const uint32_t w1 = on ? uint32_t(lvj[i]) : 0u;
@@ -789,46 +796,38 @@ __global__ void __launch_bounds__(1024) list_stage_kernel(StageParams<T> P) {
             const C v = op[l];
             C yv = mk(T(0), T(0)), av = mk(T(0), T(0));
             if (on && P.stage > 0) {
-                yv = __ldg(P.y + v0 + l);
-                av = P.acc[v0 + l];
+                yv = __ldcg(P.y + v0 + l);
+                av = __ldcg(P.acc + v0 + l);
             }
-            const C gm = reinterpret_cast<const C*>(S.blob + B.gam)[j];
-            const PatConst<T> pc = reinterpret_cast<const PatConst<T>*>(S.blob + B.ic)[ph[j].islot];
-            // diagonal: -Gamma, the cavity loss (1/2 per cavity index) and
-            // -/+ i detuning for X / Y, the terminator -Delta w (classes: 0 S T,
-            // 1 X, 2 Y, 3 Z, 4 P)
-            const bool xy = cls == 1 || cls == 2;
-            const T lossf = cls == 3 ? T(1) : (xy ? T(0.5) : T(0));
-            const T wt = cls == 0 ? T(2) : (xy ? T(1) : T(0));
-            const T dim = cls == 1 ? -pc.det : (cls == 2 ? pc.det : T(0));
-            const C diag = mk(-(gm.x + lossf * pc.kap + wt * pc.term), dim - gm.y);
+            // commutator and diagonal (classes: 0 S T, 1 X, 2 Y, 3 Z, 4 P)
+            const C* const pj = pd + kSplitPd * j;
+            const T g = pj[5].x;
             const C t = csub(op[a], op[b]);
-            C dv = mk(pc.g * t.y, -pc.g * t.x);
-            dv = cfma(diag, v, dv);
-            // hierarchy terms (Eqs. uvar-up, uvar-down)
-            const C* __restrict__ cf = P.lcoef + pc.coef_base;
-            const uint32_t r0 = rb[rho], r1 = rb[rho + 1];
+            C dv = mk(g * t.y, -g * t.x);
+            dv = cfma(pj[cls], v, dv);
+            // hierarchy terms (Eqs. uvar-up, uvar-down); rows past the
+            // round's end were loaded as the zero slot
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dv = cfma(cv[u], xv[u], dv);
             const uint32_t* __restrict__ ti = P.tidx + size_t(r0) * 32 + lane;
             const uint16_t* __restrict__ tc = P.tcid + size_t(r0) * 32 + lane;
-            const int nt = int(r1 - r0);
-            int t2 = 0;
+            int t2 = 4;
             for (; t2 + 4 <= nt; t2 += 4) {
-                uint32_t ix[4], cx[4];
+                uint32_t jx[4], jc[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    ix[u] = __ldg(ti + (t2 + u) * 32);
-                    cx[u] = __ldg(tc + (t2 + u) * 32);
+                    jx[u] = __ldcg(ti + (t2 + u) * 32);
+                    jc[u] = __ldcg(tc + (t2 + u) * 32);
                 }
-                C xv[4], cv[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    xv[u] = __ldg(X + ix[u]);
-                    cv[u] = __ldg(cf + cx[u]);
+                    xv[u] = __ldg(X + jx[u]);
+                    cv[u] = __ldg(cf + jc[u]);
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) dv = cfma(cv[u], xv[u], dv);
             }
-            for (; t2 < nt; ++t2) dv = cfma(__ldg(cf + __ldg(tc + t2 * 32)), __ldg(X + __ldg(ti + t2 * 32)), dv);
+            for (; t2 < nt; ++t2) dv = cfma(__ldg(cf + __ldcg(tc + t2 * 32)), __ldg(X + __ldcg(ti + t2 * 32)), dv);
             if (on) {
                 const uint32_t vg = v0 + l;
                 if (P.stage < 0) {
@@ -894,7 +893,7 @@ __device__ __forceinline__ SplitSmem<T> carve_split(unsigned char* p, int item) 
 // A bounded wait that expires sets bit 0 of the error word; the warp then
 // waits (bounded again) for its copies and stops.
 template <typename T, bool FP64SIDE>
-__global__ void __launch_bounds__(1024) split_stage_kernel(StageParams<T> P) {
+__global__ void __launch_bounds__(256) split_stage_kernel(StageParams<T> P) {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;

@@ -53,20 +53,19 @@ constexpr int kRB = 128;  // partial-sum tile: rows
 constexpr int kCB = 256;  // partial-sum tile: columns (one per thread)
 constexpr int kT = 32;    // output tile
 
-// response value of representative r, slot k
-__global__ void gather_responses_kernel(const InstDev* __restrict__ inst, const int16_t* __restrict__ loc, int nrep,
+// response value of representative r, slot k (zero where the
+// representative or the variable does not exist)
+__global__ void gather_responses_kernel(const InstDev* __restrict__ inst, const RepSrc* __restrict__ src,
                                         const double2* __restrict__ main64, const double2* __restrict__ side64,
                                         double2* __restrict__ resp) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= kReps * kRepSlots) return;
-    const int r = t / kRepSlots;
+    const RepSrc S = src[t];
     double2 v = d2(0.0, 0.0);
-    if (r < nrep) {
-        const int l = loc[t];
-        if (l >= 0) {
-            const InstDev I = inst[r];
-            v = side64 ? side64[I.side + l] : main64[I.var_begin + l];
-        }
+    if (S.loc >= 0) {
+        const InstDev I = inst[S.inst];
+        v = side64 ? side64[I.side + S.loc] : main64[I.var_begin + S.loc];
+        if (S.conj) v.y = -v.y;
     }
     resp[t] = v;
 }
@@ -365,7 +364,7 @@ size_t recon_workspace_bytes(int64_t n) {
     return size_t(16) * size_t(ncb * n + nrb * n + 4 * n + 4 * nblk + 4 + kReps * kRepSlots);
 }
 
-cudaError_t launch_reconstruct(const InstDev* inst, const int16_t* loc, int nrep, const void* main64,
+cudaError_t launch_reconstruct(const InstDev* inst, const RepSrc* src, const void* main64,
                                const void* side64, const void* rho0, int64_t n, void* rho_t, void* ws,
                                cudaStream_t st) {
     const int64_t ncb = (n + kCB - 1) / kCB, nrb = (n + kRB - 1) / kRB, nblk = (n + 255) / 256;
@@ -380,7 +379,7 @@ cudaError_t launch_reconstruct(const InstDev* inst, const int16_t* loc, int nrep
     double2* tot = blocktot + 4 * nblk;
     double2* resp = tot + 4;
     const double2* A = static_cast<const double2*>(rho0);
-    gather_responses_kernel<<<1, 128, 0, st>>>(inst, loc, nrep, static_cast<const double2*>(main64),
+    gather_responses_kernel<<<1, 128, 0, st>>>(inst, src, static_cast<const double2*>(main64),
                                               static_cast<const double2*>(side64), resp);
     recon_partials_kernel<<<dim3(unsigned(ncb), unsigned(nrb)), kCB, 0, st>>>(A, n, rowpart, colpart);
     recon_vectors_kernel<<<unsigned(nblk), 256, 0, st>>>(A, n, rowpart, int(ncb), colpart, int(nrb), r, s, blocktot);

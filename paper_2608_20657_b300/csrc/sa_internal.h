@@ -21,6 +21,16 @@ constexpr int kSideSlots = 32;       // FP64 slots of the physical representativ
 // representatives (categories 1, 2, 3: molecule 1, molecule 2 or the others, the others)
 constexpr int kReps = 5, kRepSlots = 17;
 enum RepSlot { RZ, RX1, RX2, RX3, RY1, RY2, RY3, RP1, RP2, RP3, RS12, RS13, RS21, RS23, RS31, RS32, RT };
+// Where a representative's response value lives: the batch instance that
+// propagates it, the variable's local index in that instance's physical
+// pattern (-1: absent), and whether the value is the complex conjugate of
+// that variable (the |c><e_1| response taken as the adjoint of the |e_1><c|
+// one, Eq. adjoint-preservation).
+struct RepSrc {
+    int16_t loc;
+    int8_t inst;
+    int8_t conj;
+};
 
 // ---- one hierarchy connection record ---------------------------------------
 // A record belongs to (pattern Lambda, category q, channel k, direction): the
@@ -147,14 +157,18 @@ struct ItemPat {
 constexpr int kItemInsts = 4;  // instances per work item
 
 // Byte offsets of the sections of a list-kernel item blob (every section
-// 16-byte aligned): the constants of the item's instances (kItemInsts
-// PatConst slots), patterns (ItemPat), damping rates Gamma_Lambda (complex
-// T), category words, multiplicities (T), owning pattern of every category
-// (u8), round table (first term row of every round and the end), lane words,
-// lane bytes.
+// 16-byte aligned): a 16-byte header whose first word is the item's
+// coefficient base (its first instance's table; the item's term slots are
+// relative to it), patterns (ItemPat), per pattern kSplitPd complex T (the
+// diagonal coefficient of each variable class -- 0 S and T, 1 X, 2 Y, 3 Z,
+// 4 P: -Gamma_Lambda, the cavity loss, -/+ i detuning, the terminator -- and
+// the coupling g as (g, 0)), category words, multiplicities (T), owning
+// pattern of every category (u8), round table (first term row of every
+// round and the end), lane words, lane bytes.
 struct BlobLayout {
-    uint32_t ic, pat, gam, cw, cM, cj, rb, lvd, lvj, bytes;
+    uint32_t pat, pd, cw, cM, cj, rb, lvd, lvj, bytes;
 };
+constexpr int kSplitPd = 6;  // complex entries per pattern in the pd sections
 #if defined(__CUDACC__)
 #define SA_HOST_DEVICE __host__ __device__
 #else
@@ -165,10 +179,9 @@ SA_HOST_DEVICE inline BlobLayout blob_layout(uint32_t np, uint32_t ncat, uint32_
     auto a16 = [](uint32_t b) { return (b + 15u) & ~15u; };
     const uint32_t nrounds = (nl + 31u) / 32u;
     BlobLayout L;
-    L.ic = 0;
-    L.pat = L.ic + a16(uint32_t(kItemInsts * sizeof(PatConst<T>)));
-    L.gam = L.pat + a16(np * uint32_t(sizeof(ItemPat)));
-    L.cw = L.gam + a16(np * 2u * uint32_t(sizeof(T)));
+    L.pat = 16;
+    L.pd = L.pat + a16(np * uint32_t(sizeof(ItemPat)));
+    L.cw = L.pd + a16(np * uint32_t(kSplitPd * 2 * sizeof(T)));
     L.cM = L.cw + a16(ncat * 4u);
     L.cj = L.cM + a16(ncat * uint32_t(sizeof(T)));
     L.rb = L.cj + a16(ncat);
@@ -190,7 +203,6 @@ SA_HOST_DEVICE inline BlobLayout blob_layout(uint32_t np, uint32_t ncat, uint32_
 struct SplitLayout {
     uint32_t pat, pd, cw, cM, cj, rb, mw, lw, bytes;
 };
-constexpr int kSplitPd = 6;  // complex entries per pattern in the pd section
 template <typename T>
 SA_HOST_DEVICE inline SplitLayout split_layout(uint32_t np, uint32_t ncat, uint32_t nv, uint32_t nl) {
     auto a16 = [](uint32_t b) { return (b + 15u) & ~15u; };
@@ -231,11 +243,6 @@ inline int list_slot(int L, int cid, int side3) {
 }
 inline int list_slots(int m, int L) { return 2 + 6 * m * (L + 1); }
 
-// Work-queue counters one stage launch owns: one grid-wide counter (queue
-// mode 1), or one counter per CTA and a helper counter (queue mode 2, see
-// ItemQueue in kernels.cu), so grids of mode 2 have fewer than kQueueStride
-// CTAs.  Zeroed before every launch.
-constexpr int kQueueStride = 2048;
 // launch description shared by api.cu and kernels.cu (type-erased pointers)
 struct LaunchCfg {
     int block;      // threads per CTA

@@ -55,6 +55,42 @@ def test_reconstruct_matches_oracle(N, L, precision, tol):
     assert oracle.errors() == 0
 
 
+def _conjugate_bath(seed):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(0.1, 0.5, 2) + 1j * rng.uniform(-0.4, 0.4, 2)
+    return {"c": c, "cc": c.conj(), "nu": rng.uniform(0.2, 1.2, 2) + 0j}
+
+
+@pytest.mark.parametrize("precision,tol", [(S.SA_FP64, 1e-11), (S.SA_FP32_AUX, 1e-5)])
+@pytest.mark.parametrize("N,L", [(1, 3), (2, 3), (5, 3), (40, 2)])
+def test_reconstruct_adjoint_shortcut(N, L, precision, tol):
+    """Eq. adjoint-preservation: with real nu_k and c-check_k = conj(c_k) the
+    |c><e_1| response is the adjoint of the |e_1><c| one, so four
+    propagations (SA_BUILD_ADJOINT_REPS) give the same rho_S(t) as five, and
+    the oracle's."""
+    bath = _conjugate_bath(N + 3 * L)
+    kw = dict(detuning=0.08, g=0.15, kappa=0.02, term=0.005)
+    p = S.make_params(N, 2, L, bath, **kw)
+    rng = np.random.default_rng(11 + N)
+    A = rng.standard_normal((N + 1, N + 1)) + 1j * rng.standard_normal((N + 1, N + 1))
+    ref = R.reconstruct(R.responses(R.representative_hierarchies(N, 2, L, bath, **kw), 0.05, 30), A)
+    h5 = S.Heom(p, precision=precision, representatives=True)
+    h4 = S.Heom(p, precision=precision, representatives=True, adjoint=True)
+    assert h4.count == h5.count - 1 == (4 if N >= 2 else 3)
+    assert h4.n_vars < h5.n_vars
+    out = []
+    for h in (h5, h4):
+        st = h.new_state()
+        h.init_representatives(st)
+        h.propagate(st, 0.05, 30, observe=False)
+        a = torch.from_numpy(np.ascontiguousarray(A)).to("cuda")
+        out.append(h.reconstruct_dense(st, a).cpu().numpy())
+    five, four = out
+    scale = np.abs(ref).max()
+    assert np.abs(four - ref).max() <= tol * scale
+    assert np.abs(four - five).max() <= (1e-13 if precision == S.SA_FP64 else 1e-6) * scale
+
+
 def test_reconstruct_large_symmetric_state():
     """N = 2000: for the permutation-invariant upper-polariton operator the
     reconstruction from the five representatives equals the symmetric

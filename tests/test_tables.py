@@ -211,3 +211,19 @@ def test_new_entry_points_refuse_host_only_handles():
     assert L.sa_heom_init_representatives(h._h, ctypes.c_void_p(16), None) == -7
     assert L.sa_heom_reconstruct_dense(h._h, ctypes.c_void_p(16), ctypes.c_void_p(32), ctypes.c_void_p(48),
                                        None) == -7
+
+
+def test_adjoint_shortcut_needs_a_conjugate_bath():
+    """SA_BUILD_ADJOINT_REPS is refused unless every nu_k is real and
+    c-check_k = conj(c_k) (Eq. adjoint-preservation); accepted, it leaves the
+    |c><e_1| propagation out of the batch."""
+    c = np.array([0.3 + 0.1j, 0.2 - 0.05j])
+    good = {"c": c, "cc": c.conj(), "nu": np.array([0.5 + 0j, 0.9 + 0j])}
+    h5 = S.Heom(S.make_params(4, 2, 3, good, g=0.1), host_only=True, representatives=True)
+    h4 = S.Heom(S.make_params(4, 2, 3, good, g=0.1), host_only=True, representatives=True, adjoint=True)
+    assert (h5.count, h4.count) == (5, 4)
+    assert h4.n_vars == h5.n_vars - h5.info(2)["n_vars"]
+    for bad in [dict(good, nu=np.array([0.5 + 0.1j, 0.9 + 0j])), dict(good, cc=c.conj() * 1.01)]:
+        with pytest.raises(S.SaHeomError) as e:
+            S.Heom(S.make_params(4, 2, 3, bad, g=0.1), host_only=True, representatives=True, adjoint=True)
+        assert e.value.code == -1
