@@ -351,57 +351,11 @@ def run_ours(args):
                "steps": k_e2e, "note": "state upload + propagate with observables every step + state download"}
         del back
 
-    # FP64 comparison on the same batch: time per step and the population
+    # FP64 comparison on the same workload: time per step and the population
     # error of the FP32-aux path against it
     extra = {}
-    if rank == 0 and args.workload == "w4" and not args.no_fp64 and precision == S.SA_FP32_AUX:
-        h64 = S.Heom(ps, precision=S.SA_FP64)
-        s64 = h64.new_state()
-        h64.autotune(s64)
-        h64.init_state(s64, _rho0(ws))
-        h64.propagate(s64, dt, 3, observe=False)
-        torch.cuda.synchronize()
-        k64 = max(3, min(args.steps, 20))
-        e0.record(stream)
-        h64.propagate(s64, dt, k64, observe=False)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1) / k64
-        nerr = args.err_steps
-        a, b = h64.new_state(), h.new_state()
-        h64.init_state(a, _rho0(ws))
-        h.init_state(b, _rho0(ws))
-        o64 = h64.propagate(a, dt, nerr, max(1, nerr // 10))
-        o32 = h.propagate(b, dt, nerr, max(1, nerr // 10))
-        err = float(np.max(np.abs(o64[:, :, 1:7] - o32[:, :, 1:7])))
-        del h64, s64, a, b
-        # the plain single-instance FP64 path: the instances one after another, each
-        # with its own handle (a seeded sample of them, scaled to the whole batch)
-        rng = np.random.default_rng(2608)
-        pick = np.sort(rng.choice(len(ps), size=min(32, len(ps)), replace=False))
-        k1, ms_single = 20, 0.0
-        for i in pick:
-            h1 = S.Heom([ps[i]], precision=S.SA_FP64)
-            s1 = h1.new_state()
-            h1.init_state(s1, _rho0([ws[i]]))
-            h1.propagate(s1, dt, 3, observe=False)
-            h1.prepare(s1, dt, k1)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            h1.propagate(s1, dt, k1, observe=False)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms_single += e0.elapsed_time(e1) / k1
-            del h1, s1
-        ms_single *= len(ps) / len(pick)
-        extra = {"fp64_ms_per_step": ms64, "fp32_over_fp64_speedup": ms64 / ms_step,
-                 "fp64_single_instance_ms_per_step": ms_single,
-                 "fp32_batched_over_fp64_single_speedup": ms_single / ms_step,
-                 "fp64_single_instance_note": f"{len(pick)} seeded instances run one at a time ({k1} steps each, "
-                                              "own handle and CUDA graph), summed and scaled to the batch",
-                 "time_to_t_final_s": {"fp32_aux": ms_step * 10000 / 1e3, "fp64": ms64 * 10000 / 1e3,
-                                       "fp64_single_instance": ms_single * 10000 / 1e3, "steps": 10000},
-                 "fp32_max_population_error_vs_fp64": err, "population_error_window_steps": nerr}
+    if rank == 0 and args.workload in ("w4", "w5") and not args.no_fp64 and precision == S.SA_FP32_AUX:
+        extra = _fp64_comparison(S, torch, stream, args, h, ws, ps, dt, ms_step)
 
     if rank == 0 and not args.no_reconstruct:
         extra["reconstruct"] = _time_reconstruct(S, torch, stream)
@@ -424,6 +378,71 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def _fp64_comparison(S, torch, stream, args, h32, ws, ps, dt, ms_step) -> dict:
+    """The FP64 path on the same workload: ms per RK4 step, and the largest
+    population error of the FP32-aux path against it over --err-steps steps
+    (observed every tenth of them).  For the batch (w4) also the plain
+    single-instance FP64 path: 32 seeded instances, each with its own handle
+    and CUDA graph, run one after another and scaled to the batch; w5 is one
+    instance, so its FP64 path is that path already."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h64 = S.Heom(ps, precision=S.SA_FP64)
+    s64 = h64.new_state()
+    if args.workload == "w4":
+        h64.autotune(s64)
+    else:  # one instance of 170 M variables: the list kernel's usual shape (no search)
+        h64.set_tuning(128, 192, 1)
+    h64.init_state(s64, _rho0(ws))
+    h64.propagate(s64, dt, 3, observe=False)
+    k64 = max(3, min(args.steps, 20))
+    h64.prepare(s64, dt, k64)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    h64.propagate(s64, dt, k64, observe=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1) / k64
+    nerr = args.err_steps
+    a, b = h64.new_state(), h32.new_state()
+    h64.init_state(a, _rho0(ws))
+    h32.init_state(b, _rho0(ws))
+    o64 = h64.propagate(a, dt, nerr, max(1, nerr // 10))
+    o32 = h32.propagate(b, dt, nerr, max(1, nerr // 10))
+    err = float(np.max(np.abs(o64[:, :, 1:7] - o32[:, :, 1:7])))
+    del h64, s64, a, b
+    torch.cuda.empty_cache()
+    t_final = W.WORKLOADS["w5"]["steps"] if args.workload == "w5" else 10000
+    out = {"fp64_ms_per_step": ms64, "fp32_over_fp64_speedup": ms64 / ms_step,
+           "fp32_max_population_error_vs_fp64": err, "population_error_window_steps": nerr,
+           "time_to_t_final_s": {"fp32_aux": ms_step * t_final / 1e3, "fp64": ms64 * t_final / 1e3,
+                                 "steps": t_final}}
+    if args.workload != "w4":
+        return out
+    rng = np.random.default_rng(2608)
+    pick = np.sort(rng.choice(len(ps), size=min(32, len(ps)), replace=False))
+    k1, ms_single = 20, 0.0
+    for i in pick:
+        h1 = S.Heom([ps[i]], precision=S.SA_FP64)
+        s1 = h1.new_state()
+        h1.init_state(s1, _rho0([ws[i]]))
+        h1.propagate(s1, dt, 3, observe=False)
+        h1.prepare(s1, dt, k1)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        h1.propagate(s1, dt, k1, observe=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_single += e0.elapsed_time(e1) / k1
+        del h1, s1
+    ms_single *= len(ps) / len(pick)
+    out.update({"fp64_single_instance_ms_per_step": ms_single,
+                "fp32_batched_over_fp64_single_speedup": ms_single / ms_step,
+                "fp64_single_instance_note": f"{len(pick)} seeded instances run one at a time ({k1} steps each, "
+                                             "own handle and CUDA graph), summed and scaled to the batch"})
+    out["time_to_t_final_s"]["fp64_single_instance"] = ms_single * t_final / 1e3
+    return out
 
 
 def _time_reconstruct(S, torch, stream, n: int = 8192, reps: int = 10) -> dict:

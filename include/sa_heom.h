@@ -485,7 +485,7 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best);
  * an unknown variant, OOM if the lists do not fit).  sa_heom_get_tuning
  * writes block, chunk, queue, kernel to out[0..3].
  */
-enum { SA_KERNEL_RECORDS = 0, SA_KERNEL_LISTS = 1, SA_KERNEL_ELL = 2, SA_KERNEL_SPLIT = 3 };
+enum { SA_KERNEL_RECORDS = 0, SA_KERNEL_LISTS = 1, SA_KERNEL_ELL = 2 };
 int sa_heom_set_kernel(sa_heom* h, int kernel);
 int sa_heom_get_tuning(const sa_heom* h, int* out);
 
@@ -546,8 +546,8 @@ int sa_heom_checkpoint_load(const sa_heom* h, const void* host_buf, size_t bytes
  *                      occupation at most L.  SA_ERR_STATE names the first
  *                      inconsistency (sa_heom_last_error).  Pure host; about
  *                      a second at 10^8 records.
- *   sa_heom_set_debug  SA_DEBUG_EXPIRE_WAIT: the list and split stage
- *                      kernels take the expiry path of their bounded wait on
+ *   sa_heom_set_debug  SA_DEBUG_EXPIRE_WAIT: the list stage kernel
+ *                      takes the expiry path of their bounded wait on
  *                      an item's bulk copies without testing it (each warp
  *                      still waits, bounded, for its copies before it
  *                      leaves), so sa_heom_device_error reports

@@ -100,7 +100,6 @@ struct sa_heom {
     // term lists of the list kernel (built per tuning, freed after upload)
     std::vector<uint32_t> lvd, rbase, tidx;
     std::vector<uint8_t> lvj;
-    std::vector<uint16_t> lw16;  // SA_KERNEL_SPLIT: hierarchy-pass lane words
     std::vector<uint16_t> tcid;
     uint64_t list_rows = 0;
     std::vector<uint32_t> wpat;   // ELL: first pattern of every warp row
@@ -314,7 +313,12 @@ void list_item(const sa_heom* h, const ItemDesc& d, ListItem& W) {
     }
     W.tix.swap(ix);
     W.tsl.swap(sl);
-    std::stable_sort(W.order.begin(), W.order.end(), [&](uint32_t x, uint32_t y) { return W.cnt[x] > W.cnt[y]; });
+    // lanes by term count, longest first, and in memory order within a count:
+    // a round's lanes then read and write nearly contiguous state, and the
+    // row terms of consecutive S_{q,r} of one row q (the same connection
+    // record) gather from consecutive entries of the target's row
+    std::sort(W.order.begin(), W.order.end(),
+              [&](uint32_t x, uint32_t y) { return W.cnt[x] != W.cnt[y] ? W.cnt[x] > W.cnt[y] : x < y; });
 }
 
 // Per-item table blobs of the list kernel (BlobLayout): everything the warp
@@ -323,7 +327,7 @@ void list_item(const sa_heom* h, const ItemDesc& d, ListItem& W) {
 // the diagonal coefficients of a pattern's variable classes (0 S T, 1 X,
 // 2 Y, 3 Z, 4 P: -Gamma_Lambda, the cavity loss (1/2 per cavity label),
 // -/+ i detuning for X / Y, the terminator -Delta w) and (g, 0), as the list
-// and split blobs hold them
+// blobs hold them
 template <typename V>
 void pattern_diag(const sa_heom* h, uint32_t p, V* e) {
     const sa_params& q = h->inst[h->hdr[p].inst].p;
@@ -379,7 +383,7 @@ int build_blobs(sa_heom* h) {
             ph[j].G = H.G;
             ph[j].tier = H.tier;
             ph[j].islot = 0;
-            pattern_diag<V>(h, d.p0 + j, pd + size_t(2 * kSplitPd) * j);
+            pattern_diag<V>(h, d.p0 + j, pd + size_t(2 * kPatDiag) * j);
             for (uint32_t cl = H.cat_off - d.c0; cl < h->hdr[d.p0 + j + 1].cat_off - d.c0; ++cl) cj[cl] = uint8_t(j);
         }
         for (uint32_t cl = 0; cl < d.ncat; ++cl) {
@@ -402,74 +406,8 @@ uint64_t list_item_rows(const ListItem& W) {
     return rows;
 }
 
-// lanes of the item's term rounds: every lane variable (SA_KERNEL_LISTS), or
-// only those with hierarchy terms (SA_KERNEL_SPLIT: the others are handled
-// by its memory-order pass alone; lane order is by term count, so they come
-// last)
-uint32_t list_item_lanes(const ListItem& W, bool split) {
-    if (!split) return uint32_t(W.order.size());
-    uint32_t n = 0;
-    while (n < W.order.size() && W.cnt[W.order[n]] > 0) ++n;
-    return n;
-}
-
-// Per-item table blobs of the split kernel (SplitLayout).
-template <typename V>
-int build_split_blobs(sa_heom* h) {
-    const size_t ni = h->items.size();
-    uint64_t off16 = 0;
-    for (size_t c = 0; c < ni; ++c) {
-        ItemDesc& d = h->items[c];
-        const SplitLayout B = split_layout<V>(d.np, d.ncat, d.nv, d.nl);
-        d.blob16 = uint32_t(off16);
-        d.blob_bytes = B.bytes;
-        off16 += B.bytes / 16;
-        if (off16 >= (uint64_t(1) << 32)) return fail(SA_ERR_UNSUPPORTED, "split-kernel blobs exceed 64 GB");
-    }
-    try {
-        h->blobs.assign(size_t(off16) * 16, 0);
-    } catch (const std::bad_alloc&) {
-        return fail(SA_ERR_OOM, "host memory for the split-kernel blobs");
-    }
-#pragma omp parallel for schedule(dynamic, 256)
-    for (int64_t c = 0; c < int64_t(ni); ++c) {
-        const ItemDesc& d = h->items[c];
-        const SplitLayout B = split_layout<V>(d.np, d.ncat, d.nv, d.nl);
-        uint8_t* o = &h->blobs[size_t(d.blob16) * 16];
-        *reinterpret_cast<uint32_t*>(o) = h->instdev[h->hdr[d.p0].inst].lcoef_base;
-        ItemPat* ph = reinterpret_cast<ItemPat*>(o + B.pat);
-        V* pd = reinterpret_cast<V*>(o + B.pd);
-        uint32_t* cw = reinterpret_cast<uint32_t*>(o + B.cw);
-        V* cM = reinterpret_cast<V*>(o + B.cM);
-        uint8_t* cj = o + B.cj;
-        uint32_t* rb = reinterpret_cast<uint32_t*>(o + B.rb);
-        uint32_t* mw = reinterpret_cast<uint32_t*>(o + B.mw);
-        uint16_t* lw = reinterpret_cast<uint16_t*>(o + B.lw);
-        for (uint32_t j = 0; j < d.np; ++j) {
-            const PatHdr& H = h->hdr[d.p0 + j];
-            ph[j].var_rel = uint16_t(H.var_off - d.v0);
-            ph[j].cat_rel = uint16_t(H.cat_off - d.c0);
-            ph[j].G = H.G;
-            ph[j].tier = H.tier;
-            ph[j].islot = 0;
-            pattern_diag<V>(h, d.p0 + j, pd + size_t(2 * kSplitPd) * j);
-            for (uint32_t cl = H.cat_off - d.c0; cl < h->hdr[d.p0 + j + 1].cat_off - d.c0; ++cl) cj[cl] = uint8_t(j);
-        }
-        for (uint32_t cl = 0; cl < d.ncat; ++cl) {
-            cw[cl] = h->cat_word[d.c0 + cl];
-            cM[cl] = V(h->catMd[d.c0 + cl]);
-        }
-        const uint32_t nrounds = (d.nl + 31) / 32;
-        for (uint32_t r = 0; d.nl && r <= nrounds; ++r) rb[r] = h->rbase[d.r0 + r];
-        for (uint32_t i = 0; i < d.nv; ++i) mw[i] = h->lvd[d.v0 + i];
-        for (uint32_t i = 0; i < d.nl; ++i) lw[i] = h->lw16[d.v0 + i];
-    }
-    return SA_OK;
-}
-
 int build_lists(sa_heom* h) {
     const size_t ni = h->items.size();
-    const bool split = h->kernel == SA_KERNEL_SPLIT;
     std::vector<uint32_t> nrounds(ni + 1, 0);
     std::vector<uint64_t> nrows(ni + 1, 0);
 #pragma omp parallel
@@ -478,7 +416,7 @@ int build_lists(sa_heom* h) {
 #pragma omp for schedule(dynamic, 64)
         for (int64_t c = 0; c < int64_t(ni); ++c) {
             list_item(h, h->items[c], W);
-            nrounds[c] = (list_item_lanes(W, split) + 31) / 32;
+            nrounds[c] = uint32_t((W.order.size() + 31) / 32);
             nrows[c] = list_item_rows(W);
         }
     }
@@ -499,8 +437,7 @@ int build_lists(sa_heom* h) {
     h->list_rows = rw;
     try {
         h->lvd.assign(size_t(h->nvar), 0u);
-        if (split) h->lw16.assign(size_t(h->nvar), 0);
-        else h->lvj.assign(size_t(h->nvar), 0);
+        h->lvj.assign(size_t(h->nvar), 0);
         h->rbase.assign(rr + 1, 0u);
         h->tidx.assign(rw * 32, 0u);
         h->tcid.assign(rw * 32, 0);
@@ -516,7 +453,7 @@ int build_lists(sa_heom* h) {
         for (int64_t c = 0; c < int64_t(ni); ++c) {
             ItemDesc& d = h->items[c];
             list_item(h, d, W);
-            const uint32_t nlane = list_item_lanes(W, split);
+            const uint32_t nlane = uint32_t(W.order.size());
             d.nl = nlane;
             uint64_t row = nrows[c];
             d.row0 = uint32_t(row);
@@ -531,12 +468,8 @@ int build_lists(sa_heom* h) {
                     const uint32_t l = i < nlane ? W.order[i] : 0u;
                     const uint32_t n = i < nlane ? W.cnt[l] : 0u;
                     if (i < nlane) {
-                        if (split) {
-                            h->lw16[d.v0 + i] = uint16_t(l);
-                        } else {
-                            h->lvd[d.v0 + i] = W.desc[l];
-                            h->lvj[d.v0 + i] = W.cls[l];
-                        }
+                        h->lvd[d.v0 + i] = W.desc[l];
+                        h->lvj[d.v0 + i] = W.cls[l];
                     }
                     for (uint32_t t = 0; t < T; ++t) {
                         const size_t e = size_t(row + t) * 32 + u;
@@ -551,19 +484,9 @@ int build_lists(sa_heom* h) {
                 }
                 row += T;
             }
-            if (split) {
-                // memory-order words; variables outside the lane order belong to
-                // the physical representative the FP64 kernel integrates
-                std::vector<uint8_t> lane(d.nv, 0);
-                for (uint32_t l : W.order) lane[l] = 1;
-                for (uint32_t l = 0; l < d.nv; ++l)
-                    h->lvd[d.v0 + l] = split_word((W.desc[l] >> 10) & 2047u, W.desc[l] >> 21, W.cls[l] & 31u,
-                                                  uint32_t(W.cls[l]) >> 5, W.cnt[l] > 0 ? 1u : 0u, lane[l] ? 0u : 1u);
-            }
         }
     }
-    const int rc = split ? (h->precision == SA_FP64 ? build_split_blobs<double>(h) : build_split_blobs<float>(h))
-                         : (h->precision == SA_FP64 ? build_blobs<double>(h) : build_blobs<float>(h));
+    const int rc = h->precision == SA_FP64 ? build_blobs<double>(h) : build_blobs<float>(h);
     if (rc) return rc;
     h->list_items = h->items;
     return SA_OK;
@@ -733,13 +656,13 @@ int ensure_tables(sa_heom* h) {
     const int k = h->kernel;
     if (k == SA_KERNEL_RECORDS) return SA_OK;
     if (h->tables == k && (k == SA_KERNEL_ELL || h->tables_chunk == h->chunk)) {
-        if (k == SA_KERNEL_LISTS || k == SA_KERNEL_SPLIT)  // the item table was rebuilt: same items, restore their rounds
+        if (k == SA_KERNEL_LISTS)  // the item table was rebuilt: same items, restore their rounds
             h->items = h->list_items;
         return SA_OK;
     }
     if (!h->host_only) free_lists(h);
     h->tables = -1;
-    const bool lists = k == SA_KERNEL_LISTS || k == SA_KERNEL_SPLIT;
+    const bool lists = k == SA_KERNEL_LISTS;
     int rc = lists ? build_lists(h) : build_ell(h);
     if (rc) return rc;
     if (!h->host_only) {
@@ -767,7 +690,6 @@ int ensure_tables(sa_heom* h) {
         // the host copies are not needed again
         std::vector<uint32_t>().swap(h->lvd);
         std::vector<uint8_t>().swap(h->lvj);
-        std::vector<uint16_t>().swap(h->lw16);
         std::vector<uint32_t>().swap(h->tidx);
         std::vector<uint16_t>().swap(h->tcid);
         std::vector<uint32_t>().swap(h->wpat);
@@ -808,7 +730,7 @@ int apply_tuning(sa_heom* h) {
     const int wpb = h->block / 32;
     const int64_t blocks_needed = (int64_t(nchunks) + wpb - 1) / wpb;
     // the list kernel is persistent in both modes (its warps pipeline their items)
-    const bool persistent = h->use_queue || h->kernel == SA_KERNEL_LISTS || h->kernel == SA_KERNEL_SPLIT;
+    const bool persistent = h->use_queue || h->kernel == SA_KERNEL_LISTS;
     h->cfg.grid = persistent ? int(std::min<int64_t>(int64_t(h->num_sms) * occ, blocks_needed)) : int(blocks_needed);
     if (h->cfg.grid < 1) h->cfg.grid = 1;
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
@@ -1884,8 +1806,8 @@ int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue) {
 
 int sa_heom_set_kernel(sa_heom* h, int kernel) {
     if (!h) return fail(SA_ERR_INVALID_ARG, "null handle");
-    if (kernel != SA_KERNEL_RECORDS && kernel != SA_KERNEL_LISTS && kernel != SA_KERNEL_ELL && kernel != SA_KERNEL_SPLIT)
-        return fail(SA_ERR_INVALID_ARG, "kernel must be SA_KERNEL_RECORDS, SA_KERNEL_LISTS, SA_KERNEL_ELL or SA_KERNEL_SPLIT");
+    if (kernel != SA_KERNEL_RECORDS && kernel != SA_KERNEL_LISTS && kernel != SA_KERNEL_ELL)
+        return fail(SA_ERR_INVALID_ARG, "kernel must be SA_KERNEL_RECORDS, SA_KERNEL_LISTS or SA_KERNEL_ELL");
     const int old = h->kernel;
     h->kernel = kernel;
     const int rc = apply_tuning(h);
@@ -1924,7 +1846,7 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     // item size outermost: the list kernel's tables are rebuilt per item size only
-    for (int k : {int(SA_KERNEL_RECORDS), int(SA_KERNEL_LISTS), int(SA_KERNEL_ELL), int(SA_KERNEL_SPLIT)})
+    for (int k : {int(SA_KERNEL_RECORDS), int(SA_KERNEL_LISTS), int(SA_KERNEL_ELL)})
     for (int c : chunks)
         for (int b : blocks)
             for (int q = 0; q < 2; ++q) {

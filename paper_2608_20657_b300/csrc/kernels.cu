@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
                 av = __ldcg(P.acc + v0 + l);
             }
             // commutator and diagonal (classes: 0 S T, 1 X, 2 Y, 3 Z, 4 P)
-            const C* const pj = pd + kSplitPd * j;
+            const C* const pj = pd + kPatDiag * j;
             const T g = pj[5].x;
             const C t = csub(op[a], op[b]);
             C dv = mk(g * t.y, -g * t.x);
@@ -841,216 +841,6 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
                     P.acc[vg] = caxpy(T(2), dv, av);
                     P.x_out[vg] = caxpy(aT, dv, yv);
                 }
-            }
-        }
-        __syncwarp();
-    }
-}
-
-// ---- split kernel ----------------------------------------------------------
-// Per-warp shared memory of the split kernel: the list kernel's operand area
-// (stage-input slice, R, C, Z sums, zero), the hierarchy sums of the item's
-// variables (hs, item-local index) and the item's table blob (SplitLayout).
-template <typename T> struct SplitSmem {
-    using C = typename Cx<T>::t;
-    uint64_t* bar;
-    C* op;
-    C* hs;
-    unsigned char* blob;
-};
-
-template <typename T>
-__host__ __device__ __forceinline__ size_t split_smem_bytes(int item) {
-    const size_t cs = 2 * sizeof(T);
-    return 16 + al16(cs * (list_opZero(item) + 3)) + al16(cs * item) +
-           split_layout<T>(kItemPats, uint32_t(list_ncat(item)), uint32_t(item), uint32_t(item)).bytes;
-}
-
-template <typename T>
-__device__ __forceinline__ SplitSmem<T> carve_split(unsigned char* p, int item) {
-    using C = typename Cx<T>::t;
-    SplitSmem<T> W;
-    W.bar = reinterpret_cast<uint64_t*>(p);  p += 16;
-    W.op = reinterpret_cast<C*>(p);          p += al16(sizeof(C) * (list_opZero(item) + 3));
-    W.hs = reinterpret_cast<C*>(p);          p += al16(sizeof(C) * item);
-    W.blob = p;
-    return W;
-}
-
-// One warp per work item, staged like the list kernel (the item's stage-input
-// slice and table blob by TMA bulk copies on the warp's mbarrier; its RK4
-// state, accumulator and term rows bulk-prefetched into L2), then three
-// passes:
-//  * grouped sums R_q, C_q per category and the Z sums per pattern (Eqs.
-//    grouped-row-sum, grouped-column-sum, HZ) into the operand area;
-//  * the hierarchy pass: lanes take the item's variables that have
-//    hierarchy terms in rounds of 32, sorted by term count, and sum their
-//    terms (Eqs. uvar-up, uvar-down) from coalesced rows of (target index,
-//    coefficient slot) entries into hs;
-//  * the update pass: lanes take the item's variables in memory order, so
-//    that the RK4 state, the accumulator and both outputs move in coalesced
-//    rows: diag * v - i g (op[a] - op[b]) + hs, then the RK4 stage update.
-// A bounded wait that expires sets bit 0 of the error word; the warp then
-// waits (bounded again) for its copies and stops.
-template <typename T, bool FP64SIDE>
-__global__ void __launch_bounds__(256) split_stage_kernel(StageParams<T> P) {
-    using C = typename Cx<T>::t;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int chunk = P.chunk;
-    const SplitSmem<T> S = carve_split<T>(smem + size_t(wib) * split_smem_bytes<T>(chunk), chunk);
-    if (lane == 0) {
-        mbar_init(S.bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    ItemQueue Q;
-    Q.init(P.use_queue, wib);
-    const T dtT = T(P.dt);
-    const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
-    uint32_t parity = 0;
-    for (;;) {
-        const unsigned int c = Q.next(P.queue, P.nchunks, lane);
-        if (c >= P.nchunks) break;
-        const ItemDesc d = P.items[c];
-        const uint32_t v0 = d.v0, nv = d.nv;
-        // ---- bulk copies (lanes 0, 3) and L2 prefetches (lanes 1, 2, 4, 5) of the item
-        const Span sx = span(P.x_in, v0, nv, sizeof(C));
-        Span sp;
-        void* dst = nullptr;
-        if (lane == 0) { sp = sx; dst = S.op; }
-        else if (lane == 1 || lane == 2) {
-            const Span t = span(lane == 1 ? P.y : static_cast<const C*>(P.acc), v0, P.stage > 0 ? nv : 0u, sizeof(C));
-            if (t.bytes) bulk_prefetch_l2(t.src, t.bytes);
-            sp.bytes = 0;
-        }
-        else if (lane == 3) {
-            sp.src = reinterpret_cast<const char*>(P.blobs) + size_t(d.blob16) * 16;
-            sp.bytes = d.blob_bytes;
-            dst = S.blob;
-        }
-        else sp.bytes = 0;
-        const uint32_t total = __reduce_add_sync(0xffffffffu, sp.bytes);
-        // the copies overwrite only what the warp has read (the previous
-        // item's slice and blob), after the __syncwarp that ended it
-        if (lane == 0) mbar_expect_tx(S.bar, total);
-        __syncwarp();
-        if (sp.bytes) bulk_g2s(dst, sp.src, sp.bytes, S.bar);
-        if (lane == 4 && d.row1 > d.row0) bulk_prefetch_l2(P.tidx + size_t(d.row0) * 32, (d.row1 - d.row0) * 128u);
-        if (lane == 5 && d.row1 > d.row0) bulk_prefetch_l2(P.tcid + size_t(d.row0) * 32, (d.row1 - d.row0) * 64u);
-        // SA_DEBUG_EXPIRE_WAIT takes the expiry path without testing the
-        // barrier; the drain below still waits (bounded) for the copies
-        if (!__all_sync(0xffffffffu, !P.expire_wait && mbar_wait(S.bar, parity))) {
-            if (lane == 0) atomicOr(P.err, 1u);
-            mbar_wait(S.bar, parity);
-            return;
-        }
-        parity ^= 1u;
-        const int np = int(d.np);
-        const uint32_t ncat = d.ncat, nl = d.nl;
-        const SplitLayout B = split_layout<T>(uint32_t(np), ncat, nv, nl);
-        const ItemPat* const ph = reinterpret_cast<const ItemPat*>(S.blob + B.pat);
-        const uint32_t* const cw = reinterpret_cast<const uint32_t*>(S.blob + B.cw);
-        const T* const cM = reinterpret_cast<const T*>(S.blob + B.cM);
-        const uint8_t* const cj = S.blob + B.cj;
-        C* const op = S.op + sx.skip;
-        C* const opR = op + list_opR(chunk);
-        C* const opC = op + list_opC(chunk);
-        C* const opZ = op + list_opZ(chunk);
-        if (lane == 0) op[list_opZero(chunk)] = mk(T(0), T(0));
-        // ---- grouped sums per category (Eqs. grouped-row-sum,
-        // grouped-column-sum) and per pattern (Eq. HZ)
-        for (uint32_t cl = lane; cl < ncat; cl += 32) {
-            const ItemPat h = ph[cj[cl]];
-            const int G = h.G;
-            const int cb = int(h.cat_rel);
-            const int q = int(cl) - cb + 1;
-            const C* xp = op + h.var_rel;
-            const T Mq = cM[cl];
-            C Rs = xp[2 * G + q];
-            if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((cw[cl] >> 15) & 31)], Rs);
-            C Cq = Rs;
-            for (int e2 = 1; e2 <= G; ++e2) {
-                if (e2 == q) continue;
-                const T Mb = cM[cb + e2 - 1];
-                Rs = caxpy(Mb, xp[loc_S_d(G, q, e2)], Rs);
-                Cq = caxpy(Mb, xp[loc_S_d(G, e2, q)], Cq);
-            }
-            opR[cl] = Rs;
-            opC[cl] = Cq;
-        }
-        for (int j = lane; j < np; j += 32) {
-            const ItemPat h = ph[j];
-            const int G = h.G;
-            const int cb = int(h.cat_rel);
-            const C* xp = op + h.var_rel;
-            C zs = mk(T(0), T(0));
-            for (int q = 1; q <= G; ++q) zs = caxpy(cM[cb + q - 1], csub(xp[q], xp[G + q]), zs);
-            opZ[j] = zs;
-        }
-        // ---- hierarchy pass: rounds of 32 lanes over the variables with terms
-        const C* __restrict__ X = P.x_in;
-        const C* __restrict__ cf = P.lcoef + *reinterpret_cast<const uint32_t*>(S.blob);
-        const uint16_t* const lw = reinterpret_cast<const uint16_t*>(S.blob + B.lw);
-        const uint32_t* const rb = reinterpret_cast<const uint32_t*>(S.blob + B.rb);
-        C* const hs = S.hs;
-        for (uint32_t i0 = 0, rho = 0; i0 < nl; i0 += 32, ++rho) {
-            const uint32_t i = i0 + lane;
-            const bool on = i < nl;
-            const uint32_t r0 = rb[rho], r1 = rb[rho + 1];
-            const uint32_t* __restrict__ ti = P.tidx + size_t(r0) * 32 + lane;
-            const uint16_t* __restrict__ tc = P.tcid + size_t(r0) * 32 + lane;
-            const int nt = int(r1 - r0);
-            C hv = mk(T(0), T(0));
-            int t2 = 0;
-            for (; t2 + 4 <= nt; t2 += 4) {
-                uint32_t ix[4], cx[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {  // term rows stream through L2 only
-                    ix[u] = __ldcg(ti + (t2 + u) * 32);
-                    cx[u] = __ldcg(tc + (t2 + u) * 32);
-                }
-                C xv[4], cv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    xv[u] = __ldg(X + ix[u]);
-                    cv[u] = __ldg(cf + cx[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) hv = cfma(cv[u], xv[u], hv);
-            }
-            for (; t2 < nt; ++t2) hv = cfma(__ldg(cf + __ldcg(tc + t2 * 32)), __ldg(X + __ldcg(ti + t2 * 32)), hv);
-            if (on) hs[lw[i]] = hv;
-        }
-        __syncwarp();
-        // ---- update pass: the item's variables in memory order
-        const uint32_t* const mw = reinterpret_cast<const uint32_t*>(S.blob + B.mw);
-        const C* const pd = reinterpret_cast<const C*>(S.blob + B.pd);
-        for (uint32_t i = lane; i < nv; i += 32) {
-            const uint32_t w = mw[i];
-            if (w >> 31) continue;  // the physical representative: the FP64 kernel's
-            const uint32_t a = w & 2047u, b = (w >> 11) & 2047u, j = (w >> 22) & 31u, cls = (w >> 27) & 7u;
-            const C v = op[i];
-            const C* const pj = pd + kSplitPd * j;
-            const T g = pj[5].x;
-            const C t = csub(op[a], op[b]);
-            C dv = mk(g * t.y, -g * t.x);
-            dv = cfma(pj[cls], v, dv);
-            if ((w >> 30) & 1u) dv = cadd(dv, hs[i]);
-            const uint32_t vg = v0 + i;
-            if (P.stage < 0) {
-                P.x_out[vg] = dv;
-            } else if (P.stage == 0) {
-                P.acc[vg] = dv;
-                P.x_out[vg] = caxpy(aT, dv, v);  // x_in is y in the first stage
-            } else if (P.stage == 3) {
-                const C yv = __ldcg(P.y + vg), av = __ldcg(P.acc + vg);
-                P.y_out[vg] = caxpy(dtT / T(6), cadd(av, dv), yv);
-            } else {
-                const C yv = __ldcg(P.y + vg), av = __ldcg(P.acc + vg);
-                P.acc[vg] = caxpy(T(2), dv, av);
-                P.x_out[vg] = caxpy(aT, dv, yv);
             }
         }
         __syncwarp();
@@ -1377,7 +1167,6 @@ size_t stage_smem_bytes(int item, int block, bool fp64, int kernel) {
     if (kernel == SA_KERNEL_ELL) return 0;
     size_t w;
     if (kernel == SA_KERNEL_LISTS) w = fp64 ? list_smem_bytes<double>(item) : list_smem_bytes<float>(item);
-    else if (kernel == SA_KERNEL_SPLIT) w = fp64 ? split_smem_bytes<double>(item) : split_smem_bytes<float>(item);
     else w = fp64 ? warp_smem_bytes<double>(item) : warp_smem_bytes<float>(item);
     return w * size_t(block / 32);
 }
@@ -1420,8 +1209,7 @@ static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int n
         if (grid > 0) ell_stage_kernel<T, SIDE><<<grid, cfg.block, 0, st>>>(p);
     } else if (cfg.kernel == SA_KERNEL_LISTS) {
         list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
-    } else if (cfg.kernel == SA_KERNEL_SPLIT) {
-        split_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+
     } else {
         stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
     }
@@ -1522,10 +1310,6 @@ cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm)
     if (cfg.kernel == SA_KERNEL_LISTS) {
         if (fp64) return occupancy_of(list_stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
         return occupancy_of(list_stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
-    }
-    if (cfg.kernel == SA_KERNEL_SPLIT) {
-        if (fp64) return occupancy_of(split_stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
-        return occupancy_of(split_stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
     }
     if (fp64) return occupancy_of(stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
     return occupancy_of(stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);

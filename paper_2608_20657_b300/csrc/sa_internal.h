@@ -159,7 +159,7 @@ constexpr int kItemInsts = 4;  // instances per work item
 // Byte offsets of the sections of a list-kernel item blob (every section
 // 16-byte aligned): a 16-byte header whose first word is the item's
 // coefficient base (its first instance's table; the item's term slots are
-// relative to it), patterns (ItemPat), per pattern kSplitPd complex T (the
+// relative to it), patterns (ItemPat), per pattern kPatDiag complex T (the
 // diagonal coefficient of each variable class -- 0 S and T, 1 X, 2 Y, 3 Z,
 // 4 P: -Gamma_Lambda, the cavity loss, -/+ i detuning, the terminator -- and
 // the coupling g as (g, 0)), category words, multiplicities (T), owning
@@ -168,7 +168,7 @@ constexpr int kItemInsts = 4;  // instances per work item
 struct BlobLayout {
     uint32_t pat, pd, cw, cM, cj, rb, lvd, lvj, bytes;
 };
-constexpr int kSplitPd = 6;  // complex entries per pattern in the pd sections
+constexpr int kPatDiag = 6;  // complex entries per pattern in the pd section
 #if defined(__CUDACC__)
 #define SA_HOST_DEVICE __host__ __device__
 #else
@@ -181,7 +181,7 @@ SA_HOST_DEVICE inline BlobLayout blob_layout(uint32_t np, uint32_t ncat, uint32_
     BlobLayout L;
     L.pat = 16;
     L.pd = L.pat + a16(np * uint32_t(sizeof(ItemPat)));
-    L.cw = L.pd + a16(np * uint32_t(kSplitPd * 2 * sizeof(T)));
+    L.cw = L.pd + a16(np * uint32_t(kPatDiag * 2 * sizeof(T)));
     L.cM = L.cw + a16(ncat * 4u);
     L.cj = L.cM + a16(ncat * uint32_t(sizeof(T)));
     L.rb = L.cj + a16(ncat);
@@ -189,43 +189,6 @@ SA_HOST_DEVICE inline BlobLayout blob_layout(uint32_t np, uint32_t ncat, uint32_
     L.lvj = L.lvd + a16(nl * 4u);
     L.bytes = L.lvj + a16(nl);
     return L;
-}
-// Byte offsets of the sections of a split-kernel item blob (SA_KERNEL_SPLIT;
-// every section 16-byte aligned): a 16-byte header whose first word is the
-// coefficient base of the item (its first instance's table; the item's term
-// slots are relative to it), patterns (ItemPat), per pattern six complex T --
-// the diagonal coefficient of each variable class (0 S and T, 1 X, 2 Y, 3 Z,
-// 4 P: -Gamma_Lambda, the cavity loss, -/+ i detuning, the terminator) and
-// the coupling g as (g, 0) --, category words, multiplicities (T), owning
-// pattern of every category (u8), the round table of the hierarchy pass, one
-// word per variable in memory order (u32, split_word) and the hierarchy-pass
-// lane words (u16: item-local variable index).
-struct SplitLayout {
-    uint32_t pat, pd, cw, cM, cj, rb, mw, lw, bytes;
-};
-template <typename T>
-SA_HOST_DEVICE inline SplitLayout split_layout(uint32_t np, uint32_t ncat, uint32_t nv, uint32_t nl) {
-    auto a16 = [](uint32_t b) { return (b + 15u) & ~15u; };
-    const uint32_t nrounds = (nl + 31u) / 32u;
-    SplitLayout L;
-    L.pat = 16;
-    L.pd = L.pat + a16(np * uint32_t(sizeof(ItemPat)));
-    L.cw = L.pd + a16(np * uint32_t(kSplitPd * 2 * sizeof(T)));
-    L.cM = L.cw + a16(ncat * 4u);
-    L.cj = L.cM + a16(ncat * uint32_t(sizeof(T)));
-    L.rb = L.cj + a16(ncat);
-    L.mw = L.rb + a16((nrounds + 1u) * 4u);
-    L.lw = L.mw + a16(nv * 4u);
-    L.bytes = L.lw + a16(nl * 2u);
-    return L;
-}
-// memory-order word of a variable in the split kernel: operand-area indices
-// a, b of its commutator term -i g (op[a] - op[b]), its pattern j in the
-// item, its diagonal class, whether it has hierarchy terms, and whether the
-// FP64 physical-representative kernel integrates it instead (skip)
-SA_HOST_DEVICE inline uint32_t split_word(uint32_t a, uint32_t b, uint32_t j, uint32_t cls, uint32_t has,
-                                          uint32_t skip) {
-    return a | (b << 11) | (j << 22) | (cls << 27) | (has << 30) | (skip << 31);
 }
 constexpr int kItemPats = 32;     // patterns per work item (5-bit local index)
 constexpr int kMaxItemVars = 1024; // variables per work item (10-bit local index)

@@ -25,7 +25,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-KERNELS = [S.SA_KERNEL_RECORDS, S.SA_KERNEL_LISTS, S.SA_KERNEL_ELL, S.SA_KERNEL_SPLIT]
+KERNELS = [S.SA_KERNEL_RECORDS, S.SA_KERNEL_LISTS, S.SA_KERNEL_ELL]
 D_SMALL = [(1, 1, 3), (2, 1, 3), (3, 2, 3), (5, 2, 4), (10, 2, 6), (12, 3, 4), (7, 4, 3), (30, 1, 12), (2, 2, 6)]
 
 

@@ -23,7 +23,7 @@ BATH = {"c": np.array([0.2 + 0.05j]), "cc": np.array([0.2 - 0.05j]), "nu": np.ar
 KW = dict(detuning=0.05, g=0.1, kappa=0.01)
 
 
-@pytest.mark.parametrize("kernel", [S.SA_KERNEL_LISTS, S.SA_KERNEL_SPLIT])
+@pytest.mark.parametrize("kernel", [S.SA_KERNEL_LISTS])
 def test_expired_wait_reported_then_recovers(kernel):
     N, m, L = 3, 1, 3
     sa = oracle.SA(N, m, L, BATH, **KW)

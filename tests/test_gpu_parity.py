@@ -42,7 +42,7 @@ def _rhs_gpu(h, x):
     return h.download(dx)
 
 
-KERNELS = [S.SA_KERNEL_RECORDS, S.SA_KERNEL_LISTS, S.SA_KERNEL_ELL, S.SA_KERNEL_SPLIT]
+KERNELS = [S.SA_KERNEL_RECORDS, S.SA_KERNEL_LISTS, S.SA_KERNEL_ELL]
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
