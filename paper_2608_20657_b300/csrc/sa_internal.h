@@ -190,7 +190,7 @@ SA_HOST_DEVICE inline BlobLayout blob_layout(uint32_t np, uint32_t ncat, uint32_
     L.bytes = L.lvj + a16(nl);
     return L;
 }
-constexpr int kItemPats = 32;     // patterns per work item (5-bit local index)
+constexpr int kItemPats = 16;     // patterns per work item (at most 31: 5-bit local index)
 constexpr int kMaxItemVars = 1024; // variables per work item (10-bit local index)
 // List and ELL kernels: the coefficient table of one instance, compact so
 // that a warp's coefficient loads stay in a few cache lines.  Slot 0 is zero

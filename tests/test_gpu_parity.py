@@ -223,7 +223,7 @@ def test_invariants_on_gpu():
 
 def test_edge_cases():
     """N = 1 (4 physical variables), L = 0 (the empty pattern only: Rabi
-    closed form), and many more patterns than one work item's 32-pattern
+    closed form), and many more patterns than one work item's 16-pattern
     limit."""
     bath = {"c": np.array([0.1 + 0.05j]), "cc": np.array([0.1 - 0.05j]), "nu": np.array([0.3 + 0j])}
     for N, L in [(1, 4), (1, 0)]:
@@ -240,7 +240,7 @@ def test_edge_cases():
     Om = math.hypot(2 * gsn, det)
     assert np.max(np.abs(obs[:, 1] - (1 - (2 * gsn / Om) ** 2 * np.sin(Om * t / 2) ** 2))) < 1e-9
     # many tiny patterns: N = 1, m = 6, L = 5 gives 462 four-variable patterns,
-    # so work items hit the 32-pattern limit before the variable limit
+    # so work items hit the 16-pattern limit before the variable limit
     bath6 = _generic_bath(6, 2)
     sa = oracle.SA(1, 6, 5, bath6, 0.1, 0.2, 0.0)
     h = S.Heom(S.make_params(1, 6, 5, bath6, detuning=0.1, g=0.2))
