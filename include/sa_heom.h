@@ -241,31 +241,39 @@ int sa_heom_dump_coefficients(const sa_heom* h, int inst, double* row, double* c
  * sa_heom_dump_lists -- the host copy of the SA_KERNEL_LISTS tables for the
  * current tuning (handles built with SA_BUILD_HOST_ONLY after
  * sa_heom_set_kernel(h, SA_KERNEL_LISTS); device handles keep them on the
- * device only and get STATE).  sizes[0..3] <- work items, rounds of 32 lanes,
- * term rows, batch variables.  Each non-NULL array receives (batch-global
- * indices):
+ * device only and get STATE).  Instances whose tables are identical (same
+ * m, L, d, decay rates and hierarchy structure -- e.g. every instance with
+ * N >= L + d + 2 of one (m, L)) share one template: its work items and lists
+ * are built once, for the first such instance, with targets and coefficient
+ * slots relative to the instance, and a work unit pairs a template item with
+ * an instance.  sizes[0..4] <- template items, rounds of 32 lanes, term rows,
+ * lane slots (32 per round), work units.  Each non-NULL array receives:
  *   items  uint32[8 * items]: first pattern, patterns, first variable v0,
- *          variables, first category, categories, first round, lane
- *          variables nl of every work item;
- *   lvd    uint32[variables]: at v0 + i, lane position i < nl of the item,
- *          l | a << 10 | b << 21 (item-local variable l; operand-area
+ *          variables, first category (relative to the template's
+ *          representative instance), categories, first round r0, lane
+ *          variables nl of every template item;
+ *   units  uint32[2 * units]: template item, instance; the instances of a
+ *          template one after another, each instance's items in order;
+ *   lvd    uint32[lane slots]: at 32 r0 + i, lane position i < nl of the
+ *          item, l | a << 10 | b << 21 (item-local variable l; operand-area
  *          indices a, b of the term -i g (op[a] - op[b]));
- *   lvj    uint8[variables]: at v0 + i, j | class << 5 (pattern j of the
- *          item; diagonal class 0: P S T, 1: X, 2: Y, 3: Z);
+ *   lvj    uint8[lane slots]: at 32 r0 + i, j | class << 5 (pattern j of the
+ *          item; diagonal class 0: S T, 1: X, 2: Y, 3: Z, 4: P);
  *   rbase  uint32[rounds + 1]: first term row of every round;
  *   tidx   uint32[32 * rows], tcid uint16[32 * rows]: entry 32 * row + lane
- *          = target variable and coefficient slot, counted from the
- *          coefficient table of the item's first instance.  Every instance
- *          holds 2 + 6 m (L + 1) slots (the last unused), the instances'
- *          tables one after another: slot 0 is zero (padding), then for
- *          channel k, occupation n = 0..L before the move and direction
- *          (lower, raise) the row, column and row + column (the P_q lower
- *          terms) coefficients at 1 + 3 ((k (L + 1) + n) 2 + raise) + side;
+ *          = target variable relative to the instance's first variable and
+ *          coefficient slot in the instance's coefficient table.  Every
+ *          instance holds 2 + 6 m (L + 1) slots (the last unused), the
+ *          instances' tables one after another: slot 0 is zero (padding),
+ *          then for channel k, occupation n = 0..L before the move and
+ *          direction (lower, raise) the row, column and row + column (the
+ *          P_q lower terms) coefficients at 1 + 3 ((k (L + 1) + n) 2 + raise)
+ *          + side;
  *   opz    int32[4]: operand-area offsets of R_q, C_q, the Z sums, the zero
  *          (the item's stage-input slice occupies [0, chunk)).
  */
-int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* lvd, uint8_t* lvj,
-                       uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz);
+int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* units, uint32_t* lvd,
+                       uint8_t* lvj, uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz);
 
 /*
  * sa_heom_dump_ell -- the host copy of the SA_KERNEL_ELL tables (host-only
@@ -278,8 +286,9 @@ int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32
  *          (31: none);
  *   rbase  uint32[W + 1]: first term row of every warp;
  *   tidx   uint32[32 * rows], tcid uint16[32 * rows]: entry 32 * row + lane
- *          as in sa_heom_dump_lists, but the slots count from the variable's
- *          own instance's table (0 = zero slot, padding).
+ *          = batch-global target variable and coefficient slot in the
+ *          variable's own instance's table (layout as in sa_heom_dump_lists;
+ *          0 = zero slot, padding).
  */
 int sa_heom_dump_ell(const sa_heom* h, int64_t* sizes, uint32_t* wpat, uint32_t* vword, uint32_t* rbase,
                      uint32_t* tidx, uint16_t* tcid);

@@ -103,7 +103,7 @@ def lib() -> ctypes.CDLL:
             "sa_heom_set_tuning": [vp, i32, i32, i32],
             "sa_heom_autotune": [vp, vp, vp, vp],
             "sa_heom_set_kernel": [vp, i32],
-            "sa_heom_dump_lists": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
+            "sa_heom_dump_lists": [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
             "sa_heom_dump_ell": [vp, vp, vp, vp, vp, vp, vp],
             "sa_heom_get_tuning": [vp, vp],
             "sa_heom_launches_per_step": [vp],
@@ -453,16 +453,17 @@ class Heom:
 
     def dump_lists(self) -> dict:
         """Host copy of the SA_KERNEL_LISTS tables (host-only handles)."""
-        sizes = np.zeros(4, np.int64)
-        _check(lib().sa_heom_dump_lists(self._h, _ptr(sizes), None, None, None, None, None, None, None),
+        sizes = np.zeros(5, np.int64)
+        _check(lib().sa_heom_dump_lists(self._h, _ptr(sizes), None, None, None, None, None, None, None, None),
                "sa_heom_dump_lists")
-        ni, nr, rows, nv = (int(v) for v in sizes)
-        out = dict(items=np.zeros((ni, 8), np.uint32), lvd=np.zeros(nv, np.uint32), lvj=np.zeros(nv, np.uint8),
+        ni, nr, rows, nlane, nu = (int(v) for v in sizes)
+        out = dict(items=np.zeros((ni, 8), np.uint32), units=np.zeros((nu, 2), np.uint32),
+                   lvd=np.zeros(nlane, np.uint32), lvj=np.zeros(nlane, np.uint8),
                    rbase=np.zeros(nr + 1, np.uint32), tidx=np.zeros(32 * rows, np.uint32),
                    tcid=np.zeros(32 * rows, np.uint16), opz=np.zeros(4, np.int32))
         _check(lib().sa_heom_dump_lists(self._h, _ptr(sizes), *(_ptr(out[k]) for k in
-                                                                ("items", "lvd", "lvj", "rbase", "tidx", "tcid",
-                                                                 "opz"))), "sa_heom_dump_lists")
+                                                                ("items", "units", "lvd", "lvj", "rbase", "tidx",
+                                                                 "tcid", "opz"))), "sa_heom_dump_lists")
         return out
 
     def dump_ell(self) -> dict:

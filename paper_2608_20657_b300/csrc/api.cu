@@ -104,6 +104,15 @@ struct sa_heom {
     uint64_t list_rows = 0;
     std::vector<uint32_t> wpat;   // ELL: first pattern of every warp row
     std::vector<ItemDesc> list_items;  // SA_KERNEL_LISTS: the item table the current lists were built with
+    // SA_KERNEL_LISTS: instances whose tables are identical (same m, L, d, bath
+    // rates and structure, e.g. every saturated instance of one (m, L)) share
+    // one template: its items, lists and blobs are built once, for its
+    // representative instance, and a work unit pairs a template item with an
+    // instance
+    std::vector<int> tmpl;             // per instance: the representative instance of its template
+    std::vector<uint32_t> units;       // per work unit: template item, instance
+    void* d_units = nullptr;
+    void* d_instk = nullptr;           // InstK<T> per instance
     std::vector<uint8_t> blobs;        // SA_KERNEL_LISTS: per-item table blobs
     int tables = -1;              // variant whose term tables are current (-1: none)
     int tables_chunk = 0;         // item capacity they were built for (SA_KERNEL_LISTS)
@@ -235,6 +244,94 @@ void build_items(sa_heom* h) {
     }
 }
 
+// Templates of the list kernel: an instance shares the template of an
+// earlier instance when everything its lists and blobs are made of is equal
+// -- channels, depth, distinguished molecules, pattern and variable layout,
+// category words and vectors, connection records, damping rates and the
+// structure of the multiplicities (equal for the nonzero vectors, and the
+// same r = N - M_0 for the zero category).  Hashing picks the candidates.
+namespace {
+uint64_t mix(uint64_t h, uint64_t v) {
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    return h;
+}
+template <class V> uint64_t hash_vec(uint64_t h, const std::vector<V>& v) {
+    h = mix(h, v.size());
+    for (size_t i = 0; i < v.size(); i += 1 + v.size() / 4096) {  // a sample suffices to pick candidates
+        uint64_t w = 0;
+        std::memcpy(&w, &v[i], sizeof(V) < 8 ? sizeof(V) : 8);
+        h = mix(h, w);
+    }
+    return h;
+}
+// the multiplicity as a template holds it: M for a nonzero vector, M_0 - N (= -r) for the zero vector
+int64_t tmpl_mult(const HostInstance& hi, size_t c) { return hi.cat_vec[c] == 0 ? hi.cat_M[c] - hi.N : hi.cat_M[c]; }
+bool same_tables(const HostInstance& a, const HostInstance& b) {
+    if (a.m != b.m || a.L != b.L || a.d != b.d || a.P != b.P || a.var_off != b.var_off || a.cat_off != b.cat_off ||
+        a.cat_word != b.cat_word || a.cat_vec != b.cat_vec || a.rec_off != b.rec_off || a.rec.size() != b.rec.size() ||
+        a.gamma_re != b.gamma_re || a.gamma_im != b.gamma_im || a.tier != b.tier)
+        return false;
+    for (size_t i = 0; i < a.rec.size(); ++i)
+        if (a.rec[i].target != b.rec[i].target || a.rec[i].packed != b.rec[i].packed) return false;
+    for (size_t c = 0; c < a.cat_M.size(); ++c)
+        if (tmpl_mult(a, c) != tmpl_mult(b, c)) return false;
+    return true;
+}
+}  // namespace
+
+void assign_templates(sa_heom* h) {
+    h->tmpl.assign(size_t(h->count), -1);
+    std::map<uint64_t, std::vector<int>> reps;
+    for (int i = 0; i < h->count; ++i) {
+        const HostInstance& hi = h->inst[i];
+        uint64_t k = mix(mix(mix(uint64_t(hi.m), uint64_t(hi.L)), uint64_t(hi.d)), uint64_t(hi.P));
+        k = hash_vec(k, hi.var_off);
+        k = hash_vec(k, hi.cat_word);
+        k = hash_vec(k, hi.gamma_re);
+        std::vector<int>& cand = reps[k];
+        for (int r : cand)
+            if (same_tables(h->inst[r], hi)) {
+                h->tmpl[i] = r;
+                break;
+            }
+        if (h->tmpl[i] < 0) {
+            h->tmpl[i] = i;
+            cand.push_back(i);
+        }
+    }
+}
+
+// The list kernel's work items: per template, runs of its representative's
+// consecutive patterns with at most `chunk` variables and kItemPats patterns
+// (batch-global p0, v0, c0 while the lists are built).
+std::vector<ItemDesc> template_items(const sa_heom* h) {
+    std::vector<ItemDesc> out;
+    for (int r = 0; r < h->count; ++r) {
+        if (h->tmpl[r] != r) continue;
+        const int64_t pb = h->instdev[r].pat_begin, pe = pb + h->inst[r].P;
+        int64_t p = pb;
+        while (p < pe) {
+            int64_t q = p, vars = 0;
+            while (q < pe && q - p < kItemPats) {
+                const int64_t u = int64_t(h->hdr[q + 1].var_off) - int64_t(h->hdr[q].var_off);
+                if (q > p && vars + u > h->chunk) break;
+                vars += u;
+                ++q;
+            }
+            ItemDesc d{};
+            d.p0 = uint32_t(p);
+            d.np = uint32_t(q - p);
+            d.v0 = h->hdr[p].var_off;
+            d.nv = h->hdr[q].var_off - h->hdr[p].var_off;
+            d.c0 = h->hdr[p].cat_off;
+            d.ncat = h->hdr[q].cat_off - h->hdr[p].cat_off;
+            out.push_back(d);
+            p = q;
+        }
+    }
+    return out;
+}
+
 // Term lists of the list kernel.  For every work item: its variables in lane
 // order (the physical representative left out in SA_FP32_AUX mode, where the
 // FP64 kernel integrates it), sorted by hierarchy-term count, longest first;
@@ -284,18 +381,17 @@ void list_item(const sa_heom* h, const ItemDesc& d, ListItem& W) {
             if (tr != 31) put(loc_T(G, tr), pl + G + q, pl + q, 0);
         }
         if (skip) continue;
+        // targets relative to the instance's first variable, slots to its
+        // coefficient table: every instance of the template reads the same lists
         const int inst = H.inst;
-        const uint32_t vb = uint32_t(h->var_begin[inst]);
         const int64_t p = int64_t(d.p0 + j) - int64_t(h->instdev[inst].pat_begin);
-        // term slots are relative to the coefficient table of the item's first instance
-        const int soff = int(h->instdev[inst].lcoef_base) - int(h->instdev[h->hdr[d.p0].inst].lcoef_base);
         for_each_term(h->inst[inst], p, [&](int64_t loc, int kind, int64_t src, uint32_t packed, int side) {
             const int cid = int(packed >> 23);
             if (kind == 3 && side == 1) return;  // folded into the row term's coefficient
-            const int slot = soff + list_slot(h->inst[inst].L, cid, kind == 3 ? 2 : side);
+            const int slot = list_slot(h->inst[inst].L, cid, kind == 3 ? 2 : side);
             const uint32_t l = pl + uint32_t(loc);
             tv.push_back(l);
-            W.tix.push_back(vb + uint32_t(src));
+            W.tix.push_back(uint32_t(src));
             W.tsl.push_back(uint16_t(slot));
             ++W.cnt[l];
         });
@@ -321,6 +417,9 @@ void list_item(const sa_heom* h, const ItemDesc& d, ListItem& W) {
               [&](uint32_t x, uint32_t y) { return W.cnt[x] != W.cnt[y] ? W.cnt[x] > W.cnt[y] : x < y; });
 }
 
+// Per-item table blobs of the list kernel (BlobLayout): everything the warp
+// stages for an item besides the state slices, contiguous and 16-byte
+// aligned so that one bulk copy brings it.
 // Per-item table blobs of the list kernel (BlobLayout): everything the warp
 // stages for an item besides the state slices, contiguous and 16-byte
 // aligned so that one bulk copy brings it.
@@ -367,7 +466,6 @@ int build_blobs(sa_heom* h) {
         const ItemDesc& d = h->items[c];
         const BlobLayout B = blob_layout<V>(d.np, d.ncat, d.nl);
         uint8_t* o = &h->blobs[size_t(d.blob16) * 16];
-        *reinterpret_cast<uint32_t*>(o) = h->instdev[h->hdr[d.p0].inst].lcoef_base;  // term slots are relative to it
         ItemPat* ph = reinterpret_cast<ItemPat*>(o + B.pat);
         V* pd = reinterpret_cast<V*>(o + B.pd);
         uint32_t* cw = reinterpret_cast<uint32_t*>(o + B.cw);
@@ -383,18 +481,23 @@ int build_blobs(sa_heom* h) {
             ph[j].G = H.G;
             ph[j].tier = H.tier;
             ph[j].islot = 0;
-            pattern_diag<V>(h, d.p0 + j, pd + size_t(2 * kPatDiag) * j);
+            pd[2 * j] = V(-h->gamma_d[2 * size_t(d.p0 + j)]);  // -Gamma_Lambda
+            pd[2 * j + 1] = V(-h->gamma_d[2 * size_t(d.p0 + j) + 1]);
             for (uint32_t cl = H.cat_off - d.c0; cl < h->hdr[d.p0 + j + 1].cat_off - d.c0; ++cl) cj[cl] = uint8_t(j);
         }
+        // multiplicities as the template holds them: M_0 - N = -r for the zero
+        // category, whose M_0 the kernel forms from the instance's N
+        const HostInstance& hr = h->inst[h->hdr[d.p0].inst];
+        const uint32_t cbase = h->hdr[h->instdev[h->hdr[d.p0].inst].pat_begin].cat_off;
         for (uint32_t cl = 0; cl < d.ncat; ++cl) {
             cw[cl] = h->cat_word[d.c0 + cl];
-            cM[cl] = V(h->catMd[d.c0 + cl]);
+            cM[cl] = V(tmpl_mult(hr, size_t(d.c0 + cl - cbase)));
         }
         const uint32_t nrounds = (d.nl + 31) / 32;
         for (uint32_t r = 0; d.nl && r <= nrounds; ++r) rb[r] = h->rbase[d.r0 + r];
         for (uint32_t i = 0; i < d.nl; ++i) {
-            lvd[i] = h->lvd[d.v0 + i];
-            lvj[i] = h->lvj[d.v0 + i];
+            lvd[i] = h->lvd[size_t(d.r0) * 32 + i];
+            lvj[i] = h->lvj[size_t(d.r0) * 32 + i];
         }
     }
     return SA_OK;
@@ -407,6 +510,7 @@ uint64_t list_item_rows(const ListItem& W) {
 }
 
 int build_lists(sa_heom* h) {
+    h->items = template_items(h);
     const size_t ni = h->items.size();
     std::vector<uint32_t> nrounds(ni + 1, 0);
     std::vector<uint64_t> nrows(ni + 1, 0);
@@ -436,8 +540,8 @@ int build_lists(sa_heom* h) {
     nrows[ni] = rw;
     h->list_rows = rw;
     try {
-        h->lvd.assign(size_t(h->nvar), 0u);
-        h->lvj.assign(size_t(h->nvar), 0);
+        h->lvd.assign(size_t(rr) * 32, 0u);  // lane words by round: lane i of an item at r0 * 32 + i
+        h->lvj.assign(size_t(rr) * 32, 0);
         h->rbase.assign(rr + 1, 0u);
         h->tidx.assign(rw * 32, 0u);
         h->tcid.assign(rw * 32, 0);
@@ -468,16 +572,16 @@ int build_lists(sa_heom* h) {
                     const uint32_t l = i < nlane ? W.order[i] : 0u;
                     const uint32_t n = i < nlane ? W.cnt[l] : 0u;
                     if (i < nlane) {
-                        h->lvd[d.v0 + i] = W.desc[l];
-                        h->lvj[d.v0 + i] = W.cls[l];
+                        h->lvd[size_t(d.r0) * 32 + i] = W.desc[l];
+                        h->lvj[size_t(d.r0) * 32 + i] = W.cls[l];
                     }
                     for (uint32_t t = 0; t < T; ++t) {
                         const size_t e = size_t(row + t) * 32 + u;
                         if (t < n) {
                             h->tidx[e] = W.tix[W.off[l] + t];
                             h->tcid[e] = W.tsl[W.off[l] + t];
-                        } else {
-                            h->tidx[e] = d.v0;
+                        } else {  // the item's first variable, with the zero slot
+                            h->tidx[e] = d.v0 - uint32_t(h->var_begin[h->hdr[d.p0].inst]);
                             h->tcid[e] = uint16_t(kListCoefZero);
                         }
                     }
@@ -488,8 +592,56 @@ int build_lists(sa_heom* h) {
     }
     const int rc = h->precision == SA_FP64 ? build_blobs<double>(h) : build_blobs<float>(h);
     if (rc) return rc;
+    // template items relative to their instance; work units instance by instance
+    std::vector<uint32_t> first(size_t(h->count) + 1, 0);  // first template item of each representative
+    {
+        std::vector<uint32_t> nit(size_t(h->count), 0);
+        for (ItemDesc& d : h->items) {
+            const int r = h->hdr[d.p0].inst;
+            ++nit[r];
+            d.p0 -= h->instdev[r].pat_begin;
+            d.v0 -= uint32_t(h->var_begin[r]);
+            d.c0 -= h->hdr[h->instdev[r].pat_begin].cat_off;
+        }
+        for (int r = 0; r < h->count; ++r) first[r + 1] = first[r] + nit[r];
+        // the instances of one template one after another, so that its lists
+        // are read while they are in L2; each instance's items in order, so
+        // that its tier +/-1 gathers stay near one another
+        std::vector<std::vector<int>> members(size_t(h->count));
+        for (int i = 0; i < h->count; ++i) members[size_t(h->tmpl[i])].push_back(i);
+        h->units.clear();
+        for (int r = 0; r < h->count; ++r)
+            for (int i : members[size_t(r)])
+                for (uint32_t c = first[r]; c < first[r + 1]; ++c) {
+                    h->units.push_back(c);
+                    h->units.push_back(uint32_t(i));
+                }
+        if (h->units.size() / 2 >= (size_t(1) << 32)) return fail(SA_ERR_UNSUPPORTED, "too many work units");
+    }
     h->list_items = h->items;
     return SA_OK;
+}
+
+// Per-instance constants of the list kernel.
+template <typename V>
+std::vector<InstK<V>> list_instk(const sa_heom* h) {
+    std::vector<InstK<V>> out(size_t(h->count));
+    const double lossf[5] = {0.0, 0.5, 0.5, 1.0, 0.0}, wt[5] = {2.0, 1.0, 1.0, 0.0, 0.0};
+    for (int i = 0; i < h->count; ++i) {
+        const sa_params& q = h->inst[i].p;
+        InstK<V>& k = out[size_t(i)];
+        k.var_base = uint32_t(h->var_begin[i]);
+        k.lcoef_base = h->instdev[i].lcoef_base;
+        k.N = double(h->inst[i].N);
+        k.g = V(q.g);
+        k.pad = V(0);
+        const double dim[5] = {0.0, -q.detuning, q.detuning, 0.0, 0.0};
+        for (int cl = 0; cl < 5; ++cl) {
+            k.cc[2 * cl] = V(-(lossf[cl] * q.kappa + wt[cl] * q.term));
+            k.cc[2 * cl + 1] = V(dim[cl]);
+        }
+    }
+    return out;
 }
 
 // ELL tables: warp w takes the variables 32 w .. 32 w + 31 in memory order.
@@ -640,7 +792,7 @@ std::vector<V> list_coefficients(const sa_heom* h) {
 }
 
 void free_lists(sa_heom* h) {
-    void** ptrs[] = {&h->d_lvd, &h->d_lvj, &h->d_rbase, &h->d_tidx, &h->d_tcid, &h->d_wpat, &h->d_blobs};
+    void** ptrs[] = {&h->d_lvd, &h->d_lvj, &h->d_rbase, &h->d_tidx, &h->d_tcid, &h->d_wpat, &h->d_blobs, &h->d_units};
     for (void** p : ptrs) {
         if (*p) cudaFree(*p);
         *p = nullptr;
@@ -671,6 +823,9 @@ int ensure_tables(sa_heom* h) {
                                          : upload(&h->d_lcoef, list_coefficients<float>(h));
 
         if (!rc && lists) rc = upload(&h->d_blobs, h->blobs);
+        if (!rc && lists) rc = upload(&h->d_units, h->units);
+        if (!rc && lists && !h->d_instk)
+            rc = h->precision == SA_FP64 ? upload(&h->d_instk, list_instk<double>(h)) : upload(&h->d_instk, list_instk<float>(h));
 
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_lvd, h->lvd);
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_wpat, h->wpat);
@@ -714,9 +869,10 @@ int apply_tuning(sa_heom* h) {
     h->cfg.chunk = h->chunk;
     h->cfg.use_queue = h->use_queue;
     h->cfg.kernel = h->kernel;
-    const uint32_t nchunks = uint32_t(h->items.size());
     int rc = ensure_tables(h);
     if (rc) return rc;
+    // work the grid shares out: the list kernel's units, the other kernels' items
+    const uint64_t nchunks = h->kernel == SA_KERNEL_LISTS ? h->units.size() / 2 : h->items.size();
     if (h->host_only) return SA_OK;
     if (h->d_chunk) cudaFree(h->d_chunk);
     if (h->d_vdesc) cudaFree(h->d_vdesc);
@@ -746,7 +902,7 @@ void free_device(sa_heom* h) {
                     h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0,
                     h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS, h->d_lvd, h->d_lvj, h->d_rbase,
                     h->d_tidx, h->d_tcid, h->d_lcoef, h->d_wpat, h->d_blobs, h->d_catpat, h->d_sums,
-                    h->d_rep_loc, h->d_recon_ws};
+                    h->d_rep_loc, h->d_recon_ws, h->d_units, h->d_instk};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -798,7 +954,9 @@ StageLaunch base_launch(const sa_heom* h) {
     s.npat = uint32_t(h->npat);
     s.sums = h->d_sums;
     s.nvar = uint32_t(h->nvar);
-    s.nchunks = uint32_t(h->items.size());
+    s.nchunks = uint32_t(h->kernel == SA_KERNEL_LISTS ? h->units.size() / 2 : h->items.size());
+    s.units = h->d_units;
+    s.instk = h->d_instk;
     s.err = h->d_err;
     s.debug = h->debug;
     s.ninst = h->count;
@@ -1067,6 +1225,7 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
         return fail(SA_ERR_UNSUPPORTED, "a pattern has more than 1024 unique variables");
     }
     decode_records(h);
+    assign_templates(h);
     // state layout
     if (precision == SA_FP64) {
         h->state_bytes = (size_t(h->nvar) * 16 + 255) / 256 * 256;
@@ -1253,8 +1412,8 @@ int sa_heom_dump_coefficients(const sa_heom* h, int inst, double* row, double* c
     return SA_OK;
 }
 
-int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* lvd, uint8_t* lvj,
-                       uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz) {
+int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* units, uint32_t* lvd,
+                       uint8_t* lvj, uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz) {
     if (!h || !sizes) return fail(SA_ERR_INVALID_ARG, "handle and sizes required");
     if (!h->host_only || h->tables != SA_KERNEL_LISTS)
         return fail(SA_ERR_STATE, "term lists are kept on the host only for host-only handles, after "
@@ -1262,13 +1421,15 @@ int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32
     sizes[0] = int64_t(h->items.size());
     sizes[1] = int64_t(h->rbase.size()) - 1;
     sizes[2] = int64_t(h->list_rows);
-    sizes[3] = h->nvar;
+    sizes[3] = int64_t(h->lvd.size());
+    sizes[4] = int64_t(h->units.size() / 2);
     if (items)
         for (size_t c = 0; c < h->items.size(); ++c) {
             const ItemDesc& d = h->items[c];
             const uint32_t f[8] = {d.p0, d.np, d.v0, d.nv, d.c0, d.ncat, d.r0, d.nl};
             std::memcpy(items + 8 * c, f, sizeof(f));
         }
+    if (units) std::copy(h->units.begin(), h->units.end(), units);
     if (lvd) std::copy(h->lvd.begin(), h->lvd.end(), lvd);
     if (lvj) std::copy(h->lvj.begin(), h->lvj.end(), lvj);
     if (rbase) std::copy(h->rbase.begin(), h->rbase.end(), rbase);

@@ -89,6 +89,8 @@ template <typename T> struct StageParams {
     const C* __restrict__ lcoef;            // per instance list_slots(m, L) slots from InstDev::lcoef_base
     // ELL kernel (lvd: per-variable word, rbase: per warp row, tidx / tcid as above)
     const unsigned char* __restrict__ blobs; // list kernel: per-item table blobs (16-byte aligned)
+    const uint2* __restrict__ units;         // list kernel: work units (template item, instance)
+    const InstK<T>* __restrict__ instk;      // list kernel: per-instance constants
     const uint32_t* __restrict__ wpat;      // first pattern of every warp row of 32 variables
     uint32_t nvar;
     const uint32_t* __restrict__ catpat;    // owning pattern of every category
@@ -602,6 +604,8 @@ template <typename T> struct ListSmem {
     using C = typename Cx<T>::t;
     uint64_t* bar;        // the warp's mbarrier
     C* op;                // skip + chunk + 2 nc + kItemPats + 1 entries (+ 2 spare)
+    T* mult;              // the item's multiplicities, M_0 = N - r included
+    C* diag;              // per pattern and variable class: -Gamma_Lambda plus the instance's part
     unsigned char* blob;  // the item's table blob
 };
 
@@ -614,10 +618,12 @@ __host__ __device__ __forceinline__ int list_opC(int item) { return item + 2 + l
 __host__ __device__ __forceinline__ int list_opZ(int item) { return item + 2 + 2 * list_ncat(item); }
 __host__ __device__ __forceinline__ int list_opZero(int item) { return item + 2 + 2 * list_ncat(item) + kItemPats; }
 
+// A warp's shared memory: mbarrier; operand area; multiplicities and the
+// diagonal table (written by the warp, never by a bulk copy); the blob.
 template <typename T>
 __host__ __device__ __forceinline__ size_t list_smem_bytes(int item) {
     const size_t cs = 2 * sizeof(T);
-    return 16 + al16(cs * (list_opZero(item) + 3)) +
+    return 16 + al16(cs * (list_opZero(item) + 3)) + al16(sizeof(T) * list_ncat(item)) + al16(cs * 5 * kItemPats) +
            blob_layout<T>(kItemPats, uint32_t(list_ncat(item)), uint32_t(item)).bytes;
 }
 
@@ -627,6 +633,8 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
     ListSmem<T> W;
     W.bar = reinterpret_cast<uint64_t*>(p);  p += 16;
     W.op = reinterpret_cast<C*>(p);          p += al16(sizeof(C) * (list_opZero(item) + 3));
+    W.mult = reinterpret_cast<T*>(p);        p += al16(sizeof(T) * list_ncat(item));
+    W.diag = reinterpret_cast<C*>(p);        p += al16(sizeof(C) * 5 * kItemPats);
     W.blob = p;
     return W;
 }
@@ -648,8 +656,10 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
 //    variable, with operands and the diagonal class chosen by the host.
 // A bounded wait that expires sets bit 0 of the error word; the warp then
 // waits (bounded again) for its copies and stops.
+// (a register budget instead of launch bounds: ptxas otherwise trades a few
+// spills for 32 resident warps, which measured slower)
 template <typename T, bool FP64SIDE>
-__global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
+__global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StageParams<T> P) {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -669,8 +679,12 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
     for (;;) {
         const unsigned int c = Q.next(P.queue, P.nchunks, lane);
         if (c >= P.nchunks) break;
-        const ItemDesc d = P.items[c];
-        const uint32_t v0 = d.v0, nv = d.nv;
+        // a work unit: a template item and the instance it is evaluated for
+        const uint2 un = P.units[c];
+        const ItemDesc d = P.items[un.x];
+        const InstK<T>* const ik = P.instk + un.y;
+        const uint32_t vbase = ik->var_base;
+        const uint32_t v0 = vbase + d.v0, nv = d.nv;  // the item's first variable in the batch
         // ---- bulk copies (lanes 0, 3) and L2 prefetches (lanes 1, 2, 4, 5) of the item
         const Span sx = span(P.x_in, v0, nv, sizeof(C));
         Span sp;
@@ -711,6 +725,22 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
         const T* const cM = reinterpret_cast<const T*>(S.blob + B.cM);
         const uint8_t* const cj = S.blob + B.cj;
         C* const op = S.op + sx.skip;
+        // the instance's multiplicities (the template stores -r for the zero
+        // category, whose M_0 = N - r) and its diagonal coefficient per pattern
+        // and variable class (0 S T, 1 X, 2 Y, 3 Z, 4 P): -Gamma_Lambda of the
+        // pattern plus the instance's loss, terminator and detuning
+        {
+            const T Nt = T(ik->N);
+            for (uint32_t cl = lane; cl < ncat; cl += 32) {
+                const T m = cM[cl];
+                S.mult[cl] = m > T(0) ? m : Nt + m;
+            }
+            const C* const pdg = reinterpret_cast<const C*>(S.blob + B.pd);
+            const C* const ccg = reinterpret_cast<const C*>(ik->cc);
+            for (int e = lane; e < 5 * np; e += 32) S.diag[e] = cadd(pdg[e / 5], ccg[e % 5]);
+            __syncwarp();
+        }
+        const T* const Mw = S.mult;
         C* const opR = op + list_opR(chunk);
         C* const opC = op + list_opC(chunk);
         C* const opZ = op + list_opZ(chunk);
@@ -723,13 +753,13 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
             const int cb = int(h.cat_rel);
             const int q = int(cl) - cb + 1;
             const C* xp = op + h.var_rel;
-            const T Mq = cM[cl];
+            const T Mq = Mw[cl];
             C Rs = xp[2 * G + q];
             if (Mq >= T(2)) Rs = caxpy(Mq - T(1), xp[(G + 1) * (G + 1) + ((cw[cl] >> 15) & 31)], Rs);
             C Cq = Rs;
             for (int e2 = 1; e2 <= G; ++e2) {
                 if (e2 == q) continue;
-                const T Mb = cM[cb + e2 - 1];
+                const T Mb = Mw[cb + e2 - 1];
                 Rs = caxpy(Mb, xp[loc_S_d(G, q, e2)], Rs);
                 Cq = caxpy(Mb, xp[loc_S_d(G, e2, q)], Cq);
             }
@@ -742,16 +772,17 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
             const int cb = int(h.cat_rel);
             const C* xp = op + h.var_rel;
             C zs = mk(T(0), T(0));
-            for (int q = 1; q <= G; ++q) zs = caxpy(cM[cb + q - 1], csub(xp[q], xp[G + q]), zs);
+            for (int q = 1; q <= G; ++q) zs = caxpy(Mw[cb + q - 1], csub(xp[q], xp[G + q]), zs);
             opZ[j] = zs;
         }
         __syncwarp();
         // ---- the lanes' variables, one round of 32 at a time.  The first four
         // term rows of every round are loaded one round ahead, so that a
         // round's gathers wait on one memory latency instead of two.
-        const C* __restrict__ X = P.x_in;
-        const C* __restrict__ cf = P.lcoef + *reinterpret_cast<const uint32_t*>(S.blob);
-        const C* const pd = reinterpret_cast<const C*>(S.blob + B.pd);
+        const C* __restrict__ X = P.x_in + vbase;  // targets are instance-relative
+        const C* __restrict__ cf = P.lcoef + ik->lcoef_base;
+        const C* const dg = S.diag;
+        const T g = ik->g;
         const uint32_t* const lvd = reinterpret_cast<const uint32_t*>(S.blob + B.lvd);
         const uint8_t* const lvj = S.blob + B.lvj;
         const uint32_t* const rb = reinterpret_cast<const uint32_t*>(S.blob + B.rb);
@@ -764,7 +795,7 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
             const uint16_t* __restrict__ tc = P.tcid + size_t(r0) * 32 + lane;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                nix[u] = uint32_t(u) < nt ? __ldcg(ti + u * 32) : v0;
+                nix[u] = uint32_t(u) < nt ? __ldcg(ti + u * 32) : d.v0;
                 ncx[u] = uint32_t(u) < nt ? uint32_t(__ldcg(tc + u * 32)) : 0u;
             }
         };
@@ -799,12 +830,12 @@ __global__ void __launch_bounds__(256) list_stage_kernel(StageParams<T> P) {
                 yv = __ldcg(P.y + v0 + l);
                 av = __ldcg(P.acc + v0 + l);
             }
-            // commutator and diagonal (classes: 0 S T, 1 X, 2 Y, 3 Z, 4 P)
-            const C* const pj = pd + kPatDiag * j;
-            const T g = pj[5].x;
+            // commutator and diagonal: -Gamma_Lambda of the pattern plus the
+            // instance's loss, terminator and detuning for the class (0 S T,
+            // 1 X, 2 Y, 3 Z, 4 P)
             const C t = csub(op[a], op[b]);
             C dv = mk(g * t.y, -g * t.x);
-            dv = cfma(pj[cls], v, dv);
+            dv = cfma(dg[5 * j + cls], v, dv);
             // hierarchy terms (Eqs. uvar-up, uvar-down); rows past the
             // round's end were loaded as the zero slot
 #pragma unroll
@@ -1255,6 +1286,8 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.sumC = p.sumR ? p.sumR + s.ncat : nullptr;
     p.sumZ = p.sumC ? p.sumC + s.ncat : nullptr;
     p.blobs = static_cast<const unsigned char*>(s.blobs);
+    p.units = static_cast<const uint2*>(s.units);
+    p.instk = static_cast<const InstK<T>*>(s.instk);
     p.nvar = s.nvar;
     p.nchunks = s.nchunks;
     p.chunk = cfg.chunk;

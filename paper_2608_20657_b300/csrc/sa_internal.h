@@ -139,6 +139,20 @@ struct ItemDesc {
     uint32_t blob_bytes;
 };
 
+// Per-instance constants of the list kernel (T = float or double): where the
+// instance's variables and coefficient table start, N (the zero category's
+// multiplicity is N - r; the template blob stores -r for it), the coupling g
+// and, per variable class (0 S T, 1 X, 2 Y, 3 Z, 4 P), the diagonal part that
+// does not depend on the pattern: -(cavity loss + terminator) and -/+ i
+// detuning, as (re, im) pairs.  The pattern's -Gamma_Lambda comes from the
+// blob.
+template <typename T> struct InstK {
+    uint32_t var_base, lcoef_base;
+    double N;
+    T g, pad;
+    T cc[10];
+};
+
 // per-pattern constants of the list kernel (T = float or double)
 template <typename T> struct PatConst {
     T g, det, kap;       // coupling, detuning, loss rate of the pattern's instance
@@ -157,18 +171,15 @@ struct ItemPat {
 constexpr int kItemInsts = 4;  // instances per work item
 
 // Byte offsets of the sections of a list-kernel item blob (every section
-// 16-byte aligned): a 16-byte header whose first word is the item's
-// coefficient base (its first instance's table; the item's term slots are
-// relative to it), patterns (ItemPat), per pattern kPatDiag complex T (the
-// diagonal coefficient of each variable class -- 0 S and T, 1 X, 2 Y, 3 Z,
-// 4 P: -Gamma_Lambda, the cavity loss, -/+ i detuning, the terminator -- and
-// the coupling g as (g, 0)), category words, multiplicities (T), owning
-// pattern of every category (u8), round table (first term row of every
-// round and the end), lane words, lane bytes.
+// 16-byte aligned): a 16-byte header (reserved), patterns (ItemPat), per pattern
+// -Gamma_Lambda (complex T), category words, multiplicities (T; the zero
+// category holds M_0 - N = -r, the instance adds its N), owning pattern of
+// every category (u8), round table (first term row of every round and the
+// end), lane words, lane bytes.
 struct BlobLayout {
     uint32_t pat, pd, cw, cM, cj, rb, lvd, lvj, bytes;
 };
-constexpr int kPatDiag = 6;  // complex entries per pattern in the pd section
+constexpr int kPatDiag = 1;  // complex entries per pattern in the pd section (-Gamma_Lambda)
 #if defined(__CUDACC__)
 #define SA_HOST_DEVICE __host__ __device__
 #else
@@ -222,6 +233,7 @@ struct StageLaunch {
     const void* lut; const void* lut_off;
     const void* lvd; const void* lvj; const void* rbase; const void* tidx; const void* tcid; const void* lcoef;
     const void* wpat; uint32_t nvar; const void* blobs;
+    const void* units; const void* instk;  // list kernel: work units (template item, instance), InstK<T>
     const void* catpat; uint32_t ncat, npat; void* sums;
     uint32_t nchunks;
     const void* x_in; void* x_out; const void* y; void* acc; void* y_out;

@@ -49,15 +49,6 @@ def _slot_coefficients(bath, L):
     return out
 
 
-def _global_coefficients(baths, sas):
-    """The instances' slot tables one after another (each padded to an even
-    length) and the first slot of each."""
-    tabs = [_slot_coefficients(b, sa.L) for b, sa in zip(baths, sas)]
-    tabs = [np.concatenate([t, np.zeros(t.size % 2, complex)]) for t in tabs]
-    base = np.concatenate([[0], np.cumsum([t.size for t in tabs])])
-    return np.concatenate(tabs), base
-
-
 def _layout(G, M):
     """Local indices of the canonical layout of a pattern with multiplicities M."""
     X = lambda q: q
@@ -70,43 +61,37 @@ def _layout(G, M):
 
 
 def _eval_lists(lib, sas, baths, x, insts):
-    """Right-hand side of the batch from the dumped lists; NaN where no lane
+    """Right-hand side of the batch from the dumped lists, work unit by work
+    unit (a template item evaluated for one instance); NaN where no lane
     writes (the physical representative in SA_FP32_AUX mode)."""
     L = lib.dump_lists()
     R0, C0, Z0, ZZ = (int(v) for v in L["opz"])
     out = np.full(x.size, np.nan, complex)
-    # batch pattern tables
     pats = [lib.dump_patterns(i) for i in range(len(sas))]
     voff = [lib.var_offset(i) for i in range(len(sas))]
-    gvar, gcat, ginst, gG, gM, ggam = [], [], [], [], [], []
-    cbase = 0
+    gams = []
     for i, (P, sa) in enumerate(zip(pats, sas)):
         vec = sa.vectors().astype(float)
         nu = np.asarray(baths[i]["nu"])
-        for p in range(P["G"].size):
-            gvar.append(voff[i] + P["var_off"][p])
-            gcat.append(cbase + P["cat_off"][p])
-            ginst.append(i)
-            gG.append(P["G"][p])
-            gM.append(P["cat_M"][P["cat_off"][p]:P["cat_off"][p + 1]])
-            ids = P["ids"][p]
-            ggam.append(sum(vec[v % len(vec)] @ nu for v in ids if v >= 0))  # molecule 1: ids V + v
-        cbase += P["cat_off"][-1]
-    coefs, cbase = _global_coefficients(baths, sas)
-    for it in L["items"]:
-        p0, np_, v0, nv, c0, ncat, r0, nl = (int(v) for v in it)
-        cf = coefs[cbase[ginst[p0]]:]  # term slots are relative to the item's first instance
+        gams.append([sum(vec[v % len(vec)] @ nu for v in P["ids"][p] if v >= 0)  # molecule 1: ids V + v
+                     for p in range(P["G"].size)])
+    coefs = [_slot_coefficients(b, sa.L) for b, sa in zip(baths, sas)]
+    covered = np.zeros(x.size, np.int64)
+    for c, inst in L["units"]:
+        p0, np_, v0, nv, c0, ncat, r0, nl = (int(v) for v in L["items"][c])
+        inst = int(inst)
+        P, vb, cf = pats[inst], voff[inst], coefs[inst]
         op = np.zeros(ZZ + 1, complex)
-        op[:nv] = x[v0:v0 + nv]
+        op[:nv] = x[vb + v0:vb + v0 + nv]
         for j in range(np_):
             p = p0 + j
-            G, M = gG[p], gM[p]
-            X, Y, P, Sv, T = _layout(G, M)
-            xp = x[gvar[p]:]
-            cb = gcat[p] - c0
+            G, M = int(P["G"][p]), P["cat_M"][P["cat_off"][p]:P["cat_off"][p + 1]]
+            X, Y, Pv, Sv, T = _layout(G, M)
+            xp = x[vb + P["var_off"][p]:]
+            cb = int(P["cat_off"][p]) - c0
             zs = 0
             for q in range(1, G + 1):
-                base = xp[P(q)] + ((M[q - 1] - 1) * xp[T(q)] if M[q - 1] >= 2 else 0)
+                base = xp[Pv(q)] + ((M[q - 1] - 1) * xp[T(q)] if M[q - 1] >= 2 else 0)
                 op[R0 + cb + q - 1] = base + sum(M[b - 1] * xp[Sv(q, b)] for b in range(1, G + 1) if b != q)
                 op[C0 + cb + q - 1] = base + sum(M[b - 1] * xp[Sv(b, q)] for b in range(1, G + 1) if b != q)
                 zs += M[q - 1] * (xp[X(q)] - xp[Y(q)])
@@ -127,27 +112,31 @@ def _eval_lists(lib, sas, baths, x, insts):
                     assert n == 0
                     continue
                 counts.append(n)
-                w0, w1 = int(L["lvd"][v0 + i0 + u]), int(L["lvj"][v0 + i0 + u])
+                w0, w1 = int(L["lvd"][32 * r0 + i0 + u]), int(L["lvj"][32 * r0 + i0 + u])
                 l, a, b = w0 & 1023, (w0 >> 10) & 2047, w0 >> 21
                 j, cls = w1 & 31, w1 >> 5
                 p = p0 + j
-                vg = v0 + l
-                assert gvar[p] <= vg < (gvar[p + 1] if p + 1 < len(gvar) else x.size)
-                inst = ginst[p]
+                vg = vb + v0 + l
+                assert P["var_off"][p] <= v0 + l < P["var_off"][p + 1]
                 sa_p = sas[inst].params
                 g, det, kap = sa_p.g, sa_p.detuning, sa_p.kappa
                 # classes: 0 S T, 1 X, 2 Y, 3 Z, 4 P
                 lossf = [0.0, 0.5, 0.5, 1.0, 0.0][cls]
                 dim = [0.0, -det, det, 0.0, 0.0][cls]
                 wt = [2.0, 1.0, 1.0, 0.0, 0.0][cls]  # terminator weight
-                diag = -(ggam[p].real + lossf * kap + wt * sa_p.term) + 1j * (dim - ggam[p].imag)
+                gam = gams[inst][p]
+                diag = -(gam.real + lossf * kap + wt * sa_p.term) + 1j * (dim - gam.imag)
                 dv = diag * op[l] - 1j * g * (op[a] - op[b])
-                dv += np.sum(cf[slot[:n]] * x[idx[:n]])
+                dv += np.sum(cf[slot[:n]] * x[vb + idx[:n]])
                 out[vg] = dv
+                covered[vg] += 1
                 seen.append(l)
             # a round is as long as its longest list, and lists are sorted
             assert counts and max(counts) == rb - ra and counts == sorted(counts, reverse=True)
         assert len(seen) == len(set(seen)) == nl
+    # every variable of every instance is written by exactly one lane, except
+    # the physical representatives the FP64 kernel integrates in SA_FP32_AUX
+    assert covered.max() <= 1
     return out
 
 
@@ -327,3 +316,39 @@ def test_lists_state_errors():
         lib.dump_lists()
     assert e.value.code == -7
     assert lib.dump_ell()["wpat"].size == (lib.n_vars + 31) // 32
+
+
+def test_lists_share_templates():
+    """Instances with identical tables -- the same m, L, d and decay rates, and
+    N >= L + d + 2 so that the hierarchy's structure no longer depends on N --
+    share one template: its items and lists are built once, and each instance
+    gets its own work units with its own N (zero-category multiplicity N - r),
+    g, detuning, loss, terminator and coefficients.  Instances below
+    saturation (N = 3 < L + 2 here) and other baths get templates of their
+    own.  Every instance's right-hand side matches the oracle's."""
+    specs = [(12, 0.10, 0.020), (30, 0.04, 0.000), (7, 0.15, 0.010), (3, 0.08, 0.030), (64, 0.02, 0.005)]
+    m, L = 2, 4
+    bath = _generic_bath(m, 99)
+    sas, baths, ps = [], [], []
+    for N, g, kap in specs:
+        kw = dict(detuning=0.3 * g, g=g, kappa=kap, term=0.7 * kap)
+        sas.append(oracle.SA(N, m, L, bath, **kw))
+        baths.append(bath)
+        ps.append(S.make_params(N, m, L, bath, **kw))
+    other = _generic_bath(m, 5)  # another bath: a template of its own
+    sas.append(oracle.SA(40, m, L, other, g=0.05))
+    baths.append(other)
+    ps.append(S.make_params(40, m, L, other, g=0.05))
+    for precision in (S.SA_FP64, S.SA_FP32_AUX):
+        lib = S.Heom(ps, precision=precision, host_only=True)
+        lib.set_kernel(S.SA_KERNEL_LISTS)
+        Ld = lib.dump_lists()
+        units = Ld["units"]
+        reps = {}
+        for c, inst in units:
+            reps.setdefault(int(inst), set()).add(int(c))
+        # the four saturated instances of the first bath read the same items
+        assert reps[0] == reps[1] == reps[2] == reps[4]
+        assert reps[3].isdisjoint(reps[0]) and reps[5].isdisjoint(reps[0])
+        assert len(Ld["items"]) == len(reps[0] | reps[3] | reps[5])
+        _case(ps, baths, sas, precision)
