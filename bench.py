@@ -267,7 +267,8 @@ def run_ours(args):
     ws, ps, precision, dt = _params(args.workload)
     if args.precision == "fp64":
         precision = S.SA_FP64
-    h = S.Heom(ps, precision=precision)
+    pack = args.layout == "packed"
+    h = S.Heom(ps, precision=precision, pack=pack)
     st = h.new_state()
     h.init_state(st, _rho0(ws))
     stream = torch.cuda.current_stream()
@@ -368,7 +369,7 @@ def run_ours(args):
                 "config": {"workload": _workload_name(args.workload),
                            "n_instances": h.count, "n_vars": n_vars, "n_patterns": h.n_patterns,
                            "state_bytes": h.state_bytes, "l2": "inputs larger than L2 (4 vectors)",
-                           "tuning": tuning,
+                           "tuning": tuning, "layout": args.layout,
                            "parallelism": f"replicas{world}"},
                 "roofline": roof, "gpu_launches": h.launches_per_step() * args.steps, "clocks": ck, "e2e": e2e}
         line.update(extra)
@@ -388,7 +389,7 @@ def _fp64_comparison(S, torch, stream, args, h32, ws, ps, dt, ms_step) -> dict:
     and CUDA graph, run one after another and scaled to the batch; w5 is one
     instance, so its FP64 path is that path already."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    h64 = S.Heom(ps, precision=S.SA_FP64)
+    h64 = S.Heom(ps, precision=S.SA_FP64, pack=args.layout == "packed")
     s64 = h64.new_state()
     if args.workload == "w4":
         h64.autotune(s64)
@@ -566,6 +567,9 @@ def main():
     ap.add_argument("--conv-n", default="2,4,6,8,10,12")
     ap.add_argument("--tune", default="", help="block,chunk,queue[,kernel] (skips the autotuner; kernel 0 = "
                                                 "connection records, 1 = term lists)")
+    ap.add_argument("--layout", default="canonical", choices=["packed", "canonical"],
+                    help="canonical: instance after instance (default, the faster on w4); packed: instances of "
+                         "repeated templates interleaved in packs of up to 32 (SA_BUILD_PACK_INSTANCES, the pack kernel)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -41,9 +41,20 @@
  *    kernels return INVALID_ARG otherwise.
  *  - SA_FP64 state buffers hold double2[n_vars_total] padded to 256 bytes.
  *    SA_FP32_AUX state buffers hold float2[n_vars_total], padded to 256
- *    bytes, followed by double2[8 * n_instances]: slot 8*i + j holds
+ *    bytes, followed by double2[32 * n_instances]: slot 32*i + j holds
  *    variable j of instance i's physical representative in FP64; the float2
  *    copy of those variables mirrors it for readers in FP32.
+ *  - Device state layout: the canonical layout, unless the handle was built
+ *    with SA_BUILD_PACK_INSTANCES.  Such a handle stores the instances of
+ *    every template (instances whose tables are identical: same m, L, d,
+ *    decay rates and hierarchy structure) that has at least 16 members in
+ *    packs of up to 32 instances (a remainder under 16 stays unpacked),
+ *    interleaved: variable l of the pack's lane j lies at element
+ *    base + l * n + j (n the pack's lanes); other instances are contiguous.  sa_heom_state_index gives every variable's
+ *    element.  The host arrays of sa_heom_state_upload / _download and the
+ *    observables stay canonical; a packed device state is meant to be
+ *    written and read through them (and sa_heom_init_*), and a checkpoint
+ *    records the layout in its hash.
  */
 #ifndef SA_HEOM_H
 #define SA_HEOM_H
@@ -75,6 +86,7 @@ enum {
 
 enum { SA_FP64 = 0, SA_FP32_AUX = 1 };                  /* precision */
 enum { SA_BUILD_DEVICE = 0, SA_BUILD_HOST_ONLY = 1 };   /* build flags */
+enum { SA_BUILD_PACK_INSTANCES = 4 };  /* build flag: interleave the instances of repeated templates (see above) */
 enum { SA_BUILD_ADJOINT_REPS = 2 };  /* sa_heom_build_representatives: the adjoint shortcut */
 enum { SA_BATH_HIGH_T = 0, SA_BATH_MATSUBARA = 1, SA_BATH_PADE = 2 };
 
@@ -181,8 +193,12 @@ int sa_heom_counts(const sa_params* p, sa_counts* out);
  * current CUDA device and allocate the RK4 work buffers (two stage vectors
  * and one accumulator, library-owned).  precision: SA_FP64 or SA_FP32_AUX.
  * The handle owns everything it allocates until sa_heom_destroy.
- * Errors: INVALID_ARG, UNSUPPORTED (more than 2^32 - 1 variables or records),
- * OOM, CUDA.
+ * flags: SA_BUILD_HOST_ONLY (tables on the host only, for the dumps), and
+ * SA_BUILD_PACK_INSTANCES (the packed device layout described at the top;
+ * the list kernel then evaluates one template item for all lanes of a pack
+ * at once, and sa_heom_set_kernel accepts SA_KERNEL_LISTS only).
+ * Errors: INVALID_ARG (unknown flag too), UNSUPPORTED (more than 2^32 - 1
+ * variables or records), OOM, CUDA.
  */
 int sa_heom_build(const sa_params* params, int count, int precision, int flags, sa_heom** out);
 
@@ -192,8 +208,40 @@ void sa_heom_destroy(sa_heom* h);
 /* sa_heom_info -- totals of the batch (inst = -1) or of instance inst. */
 int sa_heom_info(const sa_heom* h, int inst, sa_counts* out);
 
-/* sa_heom_var_offset -- first variable of instance inst in the batch vector. */
+/* sa_heom_var_offset -- first variable of instance inst in the batch vector
+ * (canonical layout: the host arrays of upload, download and the dumps). */
 int sa_heom_var_offset(const sa_heom* h, int inst, int64_t* out);
+
+/*
+ * sa_heom_state_index -- the element of a device state buffer (index into
+ * its double2 or float2 array) that holds variable `var` (canonical,
+ * instance-relative) of instance `inst`: var_offset + var unless the handle
+ * packs instances.  Pure host.  INVALID_ARG for an index out of range.
+ */
+int sa_heom_state_index(const sa_heom* h, int inst, int64_t var, int64_t* out);
+
+/*
+ * sa_heom_dump_packs -- the packs of a handle built with
+ * SA_BUILD_PACK_INSTANCES (none otherwise) and, after
+ * sa_heom_set_kernel(h, SA_KERNEL_LISTS) on a host-only handle, the table
+ * blobs of the pack items.  sizes[0..2] <- packs, pack lanes, blob bytes.
+ *   packs  uint32[4 * packs]: base element, lanes n, first element of the
+ *          interleaved coefficient tables (slot s of lane j at
+ *          cbase + s * n + j, slots as in sa_heom_dump_lists), first lane;
+ *   lanes  uint32[pack lanes]: the instance of every lane (first lane + j);
+ *   blobs  uint8[blob bytes]: every work item's table blob, at 16 times
+ *          its blob field (sa_heom_dump_lists items).  A pack item's blob
+ *          holds, each section starting on a 16-byte boundary after a
+ *          16-byte header: per pattern (var_rel u16, cat_rel u16, G u8,
+ *          tier u8, 0 u16); per pattern -Gamma_Lambda (re, im) in the
+ *          handle's auxiliary precision; per category the multiplicity in
+ *          that precision (-r for the zero category, whose M_0 = N - r);
+ *          per category its T-rank (u8, 31: no T variable); per item-local
+ *          variable the first of its terms (u16, variables + 1 entries); per
+ *          term the instance-relative target (u32), then per term the
+ *          coefficient slot (u16).
+ */
+int sa_heom_dump_packs(const sa_heom* h, int64_t* sizes, uint32_t* packs, uint32_t* lanes, uint8_t* blobs);
 
 /*
  * Table dumps of instance inst (host copies, canonical order), for checking
@@ -237,7 +285,6 @@ int sa_heom_dump_terms(const sa_heom* h, int inst, int64_t* var, int64_t* src, i
 int sa_heom_dump_coefficients(const sa_heom* h, int inst, double* row, double* col);
 
 /*
- * sa_heom_dump_lists/*
  * sa_heom_dump_lists -- the host copy of the SA_KERNEL_LISTS tables for the
  * current tuning (handles built with SA_BUILD_HOST_ONLY after
  * sa_heom_set_kernel(h, SA_KERNEL_LISTS); device handles keep them on the
@@ -248,12 +295,16 @@ int sa_heom_dump_coefficients(const sa_heom* h, int inst, double* row, double* c
  * slots relative to the instance, and a work unit pairs a template item with
  * an instance.  sizes[0..4] <- template items, rounds of 32 lanes, term rows,
  * lane slots (32 per round), work units.  Each non-NULL array receives:
- *   items  uint32[8 * items]: first pattern, patterns, first variable v0,
+ *   items  uint32[10 * items]: first pattern, patterns, first variable v0,
  *          variables, first category (relative to the template's
  *          representative instance), categories, first round r0, lane
- *          variables nl of every template item;
+ *          variables nl, blob offset (16-byte units) and blob bytes of
+ *          every template item; a pack item (packed handles) has
+ *          r0 = 0xffffffff and its hierarchy-term count in nl;
  *   units  uint32[2 * units]: template item, instance; the instances of a
- *          template one after another, each instance's items in order;
+ *          template one after another, each instance's items in order.  A
+ *          pack unit has bit 31 set on the item and a pack in place of the
+ *          instance;
  *   lvd    uint32[lane slots]: at 32 r0 + i, lane position i < nl of the
  *          item, l | a << 10 | b << 21 (item-local variable l; operand-area
  *          indices a, b of the term -i g (op[a] - op[b]));
@@ -500,9 +551,10 @@ int sa_heom_set_kernel(sa_heom* h, int kernel);
 int sa_heom_get_tuning(const sa_heom* h, int* out);
 
 /* Kernel launches one RK4 step issues: 4 stage kernels (SA_FP64), or 4 stage
- * kernels each followed by the FP64 physical-representative kernel
- * (SA_FP32_AUX); SA_KERNEL_ELL adds a grouped-sum kernel before each stage
- * kernel. */
+ * kernels each with the FP64 physical-representative kernel (SA_FP32_AUX);
+ * SA_KERNEL_ELL adds a grouped-sum kernel before each stage kernel, and a
+ * packed handle's stage is the pack kernel plus (when some instances are
+ * not packed) the list kernel. */
 int sa_heom_launches_per_step(const sa_heom* h);
 
 /*
@@ -527,8 +579,9 @@ int sa_heom_device_error(sa_heom* h, void* stream);
  * continues bit for bit: the kernels compute every variable in a fixed
  * order whatever the scheduling.
  *   sa_heom_config_hash      64-bit FNV-1a hash of the precision, every
- *                            instance's sa_params and the table layout
- *                            version.  Pure host.
+ *                            instance's sa_params, the table layout version
+ *                            and the device layout (where every instance's
+ *                            variables lie).  Pure host.
  *   sa_heom_checkpoint_save  d_state -> host_buf (caller-owned, at least
  *                            sa_heom_checkpoint_bytes); synchronous.
  *   sa_heom_checkpoint_load  host_buf -> d_state, *step (nullable) <- the

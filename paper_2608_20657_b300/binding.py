@@ -22,7 +22,7 @@ PHYS_SLOTS = 32  # SA_HEOM_PHYS_SLOTS
 NOALLOC_MAX_INSTANCES = 4096  # SA_HEOM_NOALLOC_MAX_INSTANCES
 
 SA_FP64, SA_FP32_AUX = 0, 1
-SA_BUILD_DEVICE, SA_BUILD_HOST_ONLY, SA_BUILD_ADJOINT_REPS = 0, 1, 2
+SA_BUILD_DEVICE, SA_BUILD_HOST_ONLY, SA_BUILD_ADJOINT_REPS, SA_BUILD_PACK_INSTANCES = 0, 1, 2, 4
 SA_KERNEL_RECORDS, SA_KERNEL_LISTS, SA_KERNEL_ELL = 0, 1, 2
 SA_DEBUG_EXPIRE_WAIT, SA_DEBUG_CORRUPT_RECORD = 1, 2
 INIT_KINDS = {"cavity": 0, "bright": 1, "up": 2, "lp": 3, "random": 4, "localised": 5, "superposed": 6}
@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
             "sa_heom_reconstruct_dense": [vp, vp, vp, vp, vp],
             "sa_heom_info": [vp, i32, P(Counts)],
             "sa_heom_var_offset": [vp, i32, P(i64)],
+            "sa_heom_state_index": [vp, i32, i64, P(i64)],
+            "sa_heom_dump_packs": [vp, vp, vp, vp, vp],
             "sa_heom_dump_vectors": [vp, i32, vp],
             "sa_heom_dump_patterns": [vp, i32, vp, vp, vp, vp, vp, vp, vp],
             "sa_heom_dump_categories": [vp, i32, vp, vp],
@@ -148,7 +150,7 @@ def exported_symbols() -> list[str]:
     return ["sa_bath_drude_lorentz", "sa_bath_terminator", "sa_heom_counts", "sa_heom_build",
             "sa_heom_build_representatives", "sa_heom_init_representatives", "sa_heom_reconstruct_dense",
             "sa_heom_destroy", "sa_heom_info",
-            "sa_heom_var_offset", "sa_heom_dump_vectors", "sa_heom_dump_patterns", "sa_heom_dump_categories",
+            "sa_heom_var_offset", "sa_heom_state_index", "sa_heom_dump_packs", "sa_heom_dump_vectors", "sa_heom_dump_patterns", "sa_heom_dump_categories",
             "sa_heom_dump_terms", "sa_heom_dump_coefficients", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_init_physical",
             "sa_heom_state_upload",
             "sa_heom_state_download", "sa_heom_rhs", "sa_heom_step", "sa_heom_propagate", "sa_heom_observables",
@@ -252,11 +254,15 @@ class Heom:
     """A built batch of instances (sa_heom handle)."""
 
     def __init__(self, params, precision: int = SA_FP64, host_only: bool = False, representatives: bool = False,
-                 adjoint: bool = False):
+                 adjoint: bool = False, pack: bool = False):
         """representatives: params is one d = 0 set; the handle is the batch of
         its representative propagations (sa_heom_build_representatives);
-        adjoint: leave out the |c><e_1| propagation (SA_BUILD_ADJOINT_REPS)."""
+        adjoint: leave out the |c><e_1| propagation (SA_BUILD_ADJOINT_REPS);
+        pack: the packed device layout (SA_BUILD_PACK_INSTANCES)."""
         flags = SA_BUILD_HOST_ONLY if host_only else SA_BUILD_DEVICE
+        if pack:
+            assert not representatives
+            flags |= SA_BUILD_PACK_INSTANCES
         h = ctypes.c_void_p()
         if representatives:
             p = params[0] if isinstance(params, (list, tuple)) else params
@@ -457,7 +463,7 @@ class Heom:
         _check(lib().sa_heom_dump_lists(self._h, _ptr(sizes), None, None, None, None, None, None, None, None),
                "sa_heom_dump_lists")
         ni, nr, rows, nlane, nu = (int(v) for v in sizes)
-        out = dict(items=np.zeros((ni, 8), np.uint32), units=np.zeros((nu, 2), np.uint32),
+        out = dict(items=np.zeros((ni, 10), np.uint32), units=np.zeros((nu, 2), np.uint32),
                    lvd=np.zeros(nlane, np.uint32), lvj=np.zeros(nlane, np.uint8),
                    rbase=np.zeros(nr + 1, np.uint32), tidx=np.zeros(32 * rows, np.uint32),
                    tcid=np.zeros(32 * rows, np.uint16), opz=np.zeros(4, np.int32))
@@ -465,6 +471,23 @@ class Heom:
                                                                 ("items", "units", "lvd", "lvj", "rbase", "tidx",
                                                                  "tcid", "opz"))), "sa_heom_dump_lists")
         return out
+
+    def dump_packs(self) -> dict:
+        """sa_heom_dump_packs: packs (base, n, cbase, lane0), lane instances
+        and (host-only handles with list tables) the item blobs."""
+        sizes = np.zeros(3, np.int64)
+        _check(lib().sa_heom_dump_packs(self._h, _ptr(sizes), None, None, None), "sa_heom_dump_packs")
+        npk, nl, nb = (int(v) for v in sizes)
+        out = dict(packs=np.zeros((npk, 4), np.uint32), lanes=np.zeros(nl, np.uint32), blobs=np.zeros(nb, np.uint8))
+        _check(lib().sa_heom_dump_packs(self._h, _ptr(sizes), _ptr(out["packs"]), _ptr(out["lanes"]),
+                                        _ptr(out["blobs"])), "sa_heom_dump_packs")
+        return out
+
+    def state_index(self, inst: int, var: int) -> int:
+        """sa_heom_state_index: element of the device state holding variable var of instance inst."""
+        out = ctypes.c_int64()
+        _check(lib().sa_heom_state_index(self._h, int(inst), int(var), ctypes.byref(out)), "sa_heom_state_index")
+        return int(out.value)
 
     def dump_ell(self) -> dict:
         """Host copy of the SA_KERNEL_ELL tables (host-only handles)."""

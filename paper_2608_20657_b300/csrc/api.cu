@@ -17,6 +17,7 @@
 namespace sa {
 cudaError_t launch_stage(const StageLaunch& s, const LaunchCfg& cfg, bool fp64, cudaStream_t st);
 cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm);
+cudaError_t pack_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm);
 void list_operand_layout(int item, int* opR, int* opC, int* opZ, int* opZero);
 cudaError_t launch_observables(const InstDev* inst, const double* theta, int ninst, const PatHdr* hdr,
                                const double* catMd, const uint32_t* cat_word, const void* main64, const void* side64,
@@ -24,8 +25,8 @@ cudaError_t launch_observables(const InstDev* inst, const double* theta, int nin
 cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0, int stride, void* main64,
                              void* main32, void* side64, cudaStream_t st);
 size_t recon_workspace_bytes(int64_t n);
-cudaError_t launch_marshal(const InstDev* inst, int ninst, uint64_t n0, uint64_t cnt, void* stage, void* main32,
-                           void* side64, int to_device, cudaStream_t st);
+cudaError_t launch_marshal(const InstDev* inst, int ninst, int packed, uint64_t n0, uint64_t cnt, void* stage,
+                           void* main, void* side64, int fp64, int to_device, cudaStream_t st);
 cudaError_t launch_reconstruct(const InstDev* inst, const RepSrc* src, const void* main64,
                                const void* side64, const void* rho0, int64_t n, void* rho_t, void* ws,
                                cudaStream_t st);
@@ -113,6 +114,23 @@ struct sa_heom {
     std::vector<uint32_t> units;       // per work unit: template item, instance
     void* d_units = nullptr;
     void* d_instk = nullptr;           // InstK<T> per instance
+    // SA_BUILD_PACK_INSTANCES: the instances of a template with at least
+    // kPackMin of them are stored in packs of up to 32, interleaved (PackDev);
+    // the list kernel evaluates a pack item for all lanes of a pack at once
+    bool packed = false;
+    std::vector<PackDev> packs;
+    std::vector<uint32_t> pk_inst;     // instance of every pack lane (PackDev::lane0 + j)
+    std::vector<int> pack_of;          // per instance: its pack, -1 if none
+    std::vector<std::vector<int>> tmpl_packs;  // per template representative: its packs
+    std::vector<char> tmpl_list;       // per template representative: some member is not packed
+    uint32_t pack_smem = 0;            // shared memory of a pack-kernel warp for the largest pack item
+    uint32_t pack_blob_off = 0;        // where the blob starts in it
+    uint64_t pcoef_total = 0;          // entries of the interleaved pack coefficient tables
+    void* d_packs = nullptr;
+    void* d_pkinst = nullptr;
+    void* d_pcoef = nullptr;
+    void* d_punits = nullptr;          // the pack units of `units`, in order (the list units go to d_units)
+    uint32_t n_list_units = 0, n_pack_units = 0;
     std::vector<uint8_t> blobs;        // SA_KERNEL_LISTS: per-item table blobs
     int tables = -1;              // variant whose term tables are current (-1: none)
     int tables_chunk = 0;         // item capacity they were built for (SA_KERNEL_LISTS)
@@ -301,13 +319,84 @@ void assign_templates(sa_heom* h) {
     }
 }
 
+// Packs (SA_BUILD_PACK_INSTANCES): the members of every template with at
+// least kPackMin instances, in instance order, in packs of 32 and one of the
+// remaining K mod 32 if that is at least kPackMin (fewer stay unpacked).
+// Then the device layout, instance by instance: a pack's
+// block (its n lanes interleaved over the template's variables) where its
+// first lane's instance stands, every other instance contiguous; likewise
+// the packs' interleaved coefficient tables.
+int assign_packs(sa_heom* h) {
+    const int nc = h->count;
+    h->pack_of.assign(size_t(nc), -1);
+    h->packs.clear();
+    h->pk_inst.clear();
+    h->tmpl_packs.assign(size_t(nc), {});
+    std::vector<int> lane(size_t(nc), 0);
+    if (h->packed) {
+        std::vector<std::vector<int>> members(static_cast<size_t>(nc));
+        for (int i = 0; i < nc; ++i) members[size_t(h->tmpl[i])].push_back(i);
+        for (int r = 0; r < nc; ++r) {
+            const int K = int(members[size_t(r)].size());
+            if (K < kPackMin) continue;
+            // full packs of 32, then the rest as one pack if it has kPackMin
+            // members (the others stay unpacked)
+            std::vector<uint32_t> sizes(size_t(K / kPackLanes), uint32_t(kPackLanes));
+            if (K % kPackLanes >= kPackMin) sizes.push_back(uint32_t(K % kPackLanes));
+            int at = 0;
+            for (uint32_t nk : sizes) {
+                PackDev pk{};
+                pk.n = nk;
+                pk.lane0 = uint32_t(h->pk_inst.size());
+                for (uint32_t j = 0; j < pk.n; ++j) {
+                    const int i = members[size_t(r)][size_t(at) + j];
+                    h->pk_inst.push_back(uint32_t(i));
+                    h->pack_of[size_t(i)] = int(h->packs.size());
+                    lane[size_t(i)] = int(j);
+                }
+                at += int(pk.n);
+                h->tmpl_packs[size_t(r)].push_back(int(h->packs.size()));
+                h->packs.push_back(pk);
+            }
+        }
+    }
+    h->tmpl_list.assign(size_t(nc), 0);
+    for (int i = 0; i < nc; ++i)
+        if (h->pack_of[size_t(i)] < 0) h->tmpl_list[size_t(h->tmpl[i])] = 1;
+    uint64_t cur = 0, cb = 0;
+    for (int i = 0; i < nc; ++i) {
+        InstDev& D = h->instdev[size_t(i)];
+        const uint64_t nv = h->var_begin[size_t(i) + 1] - h->var_begin[size_t(i)];
+        const int k = h->pack_of[size_t(i)];
+        if (k < 0) {
+            D.dev_base = uint32_t(cur);
+            D.dev_stride = 1;
+            cur += nv;
+            continue;
+        }
+        PackDev& pk = h->packs[size_t(k)];
+        if (lane[size_t(i)] == 0) {  // members are in instance order: lane 0 comes first
+            pk.base = uint32_t(cur);
+            pk.cbase = uint32_t(cb);
+            cur += nv * pk.n;
+            cb += uint64_t(list_slots(h->inst[size_t(i)].m, h->inst[size_t(i)].L)) * pk.n;
+        }
+        D.dev_base = pk.base + uint32_t(lane[size_t(i)]);
+        D.dev_stride = pk.n;
+    }
+    if (cur != uint64_t(h->nvar)) return fail(SA_ERR_STATE, "pack layout does not cover the batch");
+    if (cb >= (uint64_t(1) << 32)) return fail(SA_ERR_UNSUPPORTED, "pack coefficient tables exceed 32-bit indices");
+    h->pcoef_total = cb;
+    return SA_OK;
+}
+
 // The list kernel's work items: per template, runs of its representative's
 // consecutive patterns with at most `chunk` variables and kItemPats patterns
 // (batch-global p0, v0, c0 while the lists are built).
 std::vector<ItemDesc> template_items(const sa_heom* h) {
     std::vector<ItemDesc> out;
     for (int r = 0; r < h->count; ++r) {
-        if (h->tmpl[r] != r) continue;
+        if (h->tmpl[r] != r || !h->tmpl_list[size_t(r)]) continue;
         const int64_t pb = h->instdev[r].pat_begin, pe = pb + h->inst[r].P;
         int64_t p = pb;
         while (p < pe) {
@@ -441,19 +530,130 @@ void pattern_diag(const sa_heom* h, uint32_t p, V* e) {
     e[11] = V(0);
 }
 
+// a pack item (r0) rather than a list item of the work-item table
+constexpr uint32_t kPackItemMark = 0xffffffffu;
+
+// Blob of a pack item (PackLayout): patterns, -Gamma_Lambda per pattern, the
+// template's multiplicities, and per variable the warp updates a record --
+// commutator operands, class and pattern (as list_item resolves them,
+// renumbered for the pack kernel: R, C, Z sums and the zero after the item's
+// nv variables), its terms, and the grouped sums its value enters -- in the
+// three phases P/T/S, X/Y, Z.  Sets d.nl (variables updated), d.row0 (terms)
+// and d.row1 (the first two phases' lengths, 16 bits each).
+template <typename V>
+int pack_blob(const sa_heom* h, ItemDesc& d, uint8_t* o) {
+    ListItem W;
+    list_item(h, d, W);
+    const bool side64 = h->precision == SA_FP32_AUX;
+    // contribution word: sum slot, weight kind (1 one, 2 M_c, 3 M_c - 1, 4 -M_c), category c
+    auto cw = [](uint32_t slot, uint32_t kind, uint32_t c) { return slot | (kind << 11) | (c << 14); };
+    struct Rec {
+        uint32_t l, z, w;
+    };
+    std::vector<Rec> ph[3];
+    for (uint32_t j = 0; j < d.np; ++j) {
+        const PatHdr& H = h->hdr[d.p0 + j];
+        if (side64 && H.tier == 0) continue;  // integrated in FP64 by the side kernel
+        const int G = H.G;
+        const uint32_t pl = H.var_off - d.v0, cb = H.cat_off - d.c0;
+        ph[2].push_back({pl + uint32_t(loc_Z()), 0u, 0u});
+        for (int q = 1; q <= G; ++q) {
+            const uint32_t cq = cb + uint32_t(q) - 1;
+            ph[1].push_back({pl + uint32_t(loc_X(G, q)), cw(2 * d.ncat + j, 2, cq), 0u});
+            ph[1].push_back({pl + uint32_t(loc_Y(G, q)), cw(2 * d.ncat + j, 4, cq), 0u});
+            ph[0].push_back({pl + uint32_t(loc_P(G, q)), cw(cq, 1, cq), cw(d.ncat + cq, 1, cq)});
+            for (int r = 1; r <= G; ++r) {
+                if (r == q) continue;
+                const uint32_t cr = cb + uint32_t(r) - 1;
+                ph[0].push_back({pl + uint32_t(loc_S(G, q, r)), cw(cq, 2, cr), cw(d.ncat + cr, 2, cq)});
+            }
+            const int tr = (h->cat_word[H.cat_off + q - 1] >> 15) & 31;
+            if (tr != 31) ph[0].push_back({pl + uint32_t(loc_T(G, tr)), cw(cq, 3, cq), cw(d.ncat + cq, 3, cq)});
+        }
+    }
+    for (auto& v : ph) std::sort(v.begin(), v.end(), [](const Rec& x, const Rec& y) { return x.l < y.l; });
+    d.nl = uint32_t(ph[0].size() + ph[1].size() + ph[2].size());
+    d.row1 = uint32_t(ph[0].size()) | (uint32_t(ph[1].size()) << 16);
+    uint32_t nterm = 0;
+    for (auto& v : ph)
+        for (const Rec& e : v) nterm += W.cnt[e.l];
+    d.row0 = nterm;
+    if (ph[0].size() > 65535u || ph[1].size() > 65535u)
+        return fail(SA_ERR_UNSUPPORTED, "a pack item has too many variables");
+    const PackLayout B = pack_layout<V>(d.np, d.ncat, d.nl, nterm);
+    ItemPat* phd = reinterpret_cast<ItemPat*>(o + B.pat);
+    V* pd = reinterpret_cast<V*>(o + B.pd);
+    V* cM = reinterpret_cast<V*>(o + B.cM);
+    uint32_t* vrec = reinterpret_cast<uint32_t*>(o + B.vrec);
+    uint32_t* tgt = reinterpret_cast<uint32_t*>(o + B.tgt);
+    uint16_t* tsl = reinterpret_cast<uint16_t*>(o + B.tsl);
+    const HostInstance& hr = h->inst[h->hdr[d.p0].inst];
+    const uint32_t cbase = h->hdr[h->instdev[h->hdr[d.p0].inst].pat_begin].cat_off;
+    for (uint32_t j = 0; j < d.np; ++j) {
+        const PatHdr& H = h->hdr[d.p0 + j];
+        phd[j].var_rel = uint16_t(H.var_off - d.v0);
+        phd[j].cat_rel = uint16_t(H.cat_off - d.c0);
+        phd[j].G = H.G;
+        phd[j].tier = H.tier;
+        phd[j].islot = 0;
+        pd[2 * j] = V(-h->gamma_d[2 * size_t(d.p0 + j)]);
+        pd[2 * j + 1] = V(-h->gamma_d[2 * size_t(d.p0 + j) + 1]);
+    }
+    for (uint32_t cl = 0; cl < d.ncat; ++cl) cM[cl] = V(tmpl_mult(hr, size_t(d.c0 + cl - cbase)));
+    int opR, opC, opZ, opZero;
+    list_operand_layout(h->chunk, &opR, &opC, &opZ, &opZero);
+    auto code = [&](uint32_t a) -> uint32_t {
+        if (a < uint32_t(opR)) return a;                                     // an item variable
+        if (a < uint32_t(opC)) return d.nv + (a - uint32_t(opR));             // R of a category
+        if (a < uint32_t(opZ)) return d.nv + d.ncat + (a - uint32_t(opC));    // C of a category
+        if (a < uint32_t(opZero)) return d.nv + 2 * d.ncat + (a - uint32_t(opZ));  // Z of a pattern
+        return d.nv + 2 * d.ncat + d.np;                                      // zero
+    };
+    uint32_t u = 0, i = 0;
+    for (auto& v : ph)
+        for (const Rec& e : v) {
+            const uint32_t l = e.l;
+            const uint32_t w = W.desc[l];
+            const uint32_t a = (w >> 10) & 2047u, b = w >> 21;
+            const uint32_t j = W.cls[l] & 31u, cls = W.cls[l] >> 5;
+            const uint32_t cnt = W.cnt[l];
+            if (cnt > 63u || l > 1023u) return fail(SA_ERR_UNSUPPORTED, "a variable has more than 63 hierarchy terms");
+            vrec[4 * i] = code(a) | (code(b) << 11) | (cls << 22) | (j << 25);
+            vrec[4 * i + 1] = l | (u << 10) | (cnt << 26);
+            vrec[4 * i + 2] = e.z;
+            vrec[4 * i + 3] = e.w;
+            ++i;
+            for (uint32_t t = 0; t < cnt; ++t, ++u) {
+                tgt[u] = W.tix[W.off[l] + t];
+                tsl[u] = W.tsl[W.off[l] + t];
+            }
+        }
+    return SA_OK;
+}
+
 // Per-item table blobs of the list kernel (BlobLayout): everything the warp
 // stages for an item besides the state slices, contiguous and 16-byte
-// aligned so that one bulk copy brings it.
+// aligned so that one bulk copy brings it.  Pack items get a PackLayout blob;
+// pack_smem is the shared memory a warp needs for the largest.
 template <typename V>
 int build_blobs(sa_heom* h) {
     const size_t ni = h->items.size();
     uint64_t off16 = 0;
+    uint32_t max_sums = 0, max_blob = 0;
     for (size_t c = 0; c < ni; ++c) {
         ItemDesc& d = h->items[c];
-        const BlobLayout B = blob_layout<V>(d.np, d.ncat, d.nl);
+        const bool pk = d.r0 == kPackItemMark;
+        // (a pack blob is sized for all nv variables and row0 terms; the
+        // builder may update fewer)
+        const uint32_t bytes = pk ? pack_layout<V>(d.np, d.ncat, d.nv, d.row0).bytes
+                                  : blob_layout<V>(d.np, d.ncat, d.nl).bytes;
+        if (pk) {
+            max_sums = std::max(max_sums, pack_sums_bytes<V>(d.np, d.ncat));
+            max_blob = std::max(max_blob, bytes);
+        }
         d.blob16 = uint32_t(off16);
-        d.blob_bytes = B.bytes;
-        off16 += B.bytes / 16;
+        d.blob_bytes = bytes;
+        off16 += bytes / 16;
         if (off16 >= (uint64_t(1) << 32)) return fail(SA_ERR_UNSUPPORTED, "list-kernel blobs exceed 64 GB");
     }
     try {
@@ -461,9 +661,22 @@ int build_blobs(sa_heom* h) {
     } catch (const std::bad_alloc&) {
         return fail(SA_ERR_OOM, "host memory for the list-kernel blobs");
     }
+    // a pack-kernel warp: mbarrier, 5 x 32 per-lane diagonal parts, the
+    // largest item's sums, then its blob
+    h->pack_blob_off = max_blob ? 16u + uint32_t(5 * 32 * 2 * sizeof(V)) + max_sums : 0u;
+    h->pack_smem = max_blob ? h->pack_blob_off + max_blob : 0u;
+    int prc = SA_OK;
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t c = 0; c < int64_t(ni); ++c) {
-        const ItemDesc& d = h->items[c];
+        ItemDesc& d = h->items[c];
+        if (d.r0 == kPackItemMark) {
+            const int r = pack_blob<V>(h, d, &h->blobs[size_t(d.blob16) * 16]);
+            if (r) {
+#pragma omp critical
+                prc = r;
+            }
+            continue;
+        }
         const BlobLayout B = blob_layout<V>(d.np, d.ncat, d.nl);
         uint8_t* o = &h->blobs[size_t(d.blob16) * 16];
         ItemPat* ph = reinterpret_cast<ItemPat*>(o + B.pat);
@@ -500,7 +713,7 @@ int build_blobs(sa_heom* h) {
             lvj[i] = h->lvj[size_t(d.r0) * 32 + i];
         }
     }
-    return SA_OK;
+    return prc;
 }
 
 uint64_t list_item_rows(const ListItem& W) {
@@ -509,8 +722,80 @@ uint64_t list_item_rows(const ListItem& W) {
     return rows;
 }
 
+// Pack items (SA_KERNEL_LISTS on a packed handle): per packed template, runs
+// of its representative's consecutive patterns whose blob (PackLayout) and
+// grouped sums stay within kPackItemTarget bytes; a pattern larger than that
+// gets an item of its own.  nl holds the variables the warp updates, row0
+// the item's term count, r0 the pack-item mark.
+template <typename V>
+int pack_items(const sa_heom* h, std::vector<ItemDesc>& out) {
+    const bool side64 = h->precision == SA_FP32_AUX;
+    int opR, opC, opZ, opZero;
+    list_operand_layout(h->chunk, &opR, &opC, &opZ, &opZero);
+    const int ncat_cap = opC - opR;  // categories the list operand layout holds
+    for (int r = 0; r < h->count; ++r) {
+        if (h->tmpl[r] != r || h->tmpl_packs[size_t(r)].empty()) continue;
+        const HostInstance& hi = h->inst[r];
+        const int64_t pb = h->instdev[r].pat_begin, pe = pb + hi.P;
+        std::vector<uint32_t> nt(size_t(hi.P), 0u);  // hierarchy terms per pattern, as the lists count them
+        for (int64_t p = 0; p < hi.P; ++p) {
+            if (side64 && hi.tier[p] == 0) continue;
+            for_each_term(hi, p, [&](int64_t, int kind, int64_t, uint32_t, int side) {
+                if (!(kind == 3 && side == 1)) ++nt[size_t(p)];
+            });
+        }
+        int64_t p = pb;
+        while (p < pe) {
+            int64_t q = p;
+            uint32_t np = 0, ncat = 0, nv = 0, nterm = 0;
+            while (q < pe) {
+                const uint32_t u = h->hdr[q + 1].var_off - h->hdr[q].var_off;
+                const uint32_t c = h->hdr[q + 1].cat_off - h->hdr[q].cat_off;
+                const uint32_t t = nt[size_t(q - pb)];
+                const uint32_t bytes = pack_layout<V>(np + 1, ncat + c, nv + u, nterm + t).bytes +
+                                       pack_sums_bytes<V>(np + 1, ncat + c);
+                // operand codes below 2048, pattern index below 16, and the
+                // list kernel's operand layout for the item capacity (which
+                // list_item resolves the operands in)
+                if (q > p && (bytes > kPackItemTarget<V> || np + 1 > uint32_t(kItemPats) ||
+                              nv + u > uint32_t(h->chunk) || int(ncat + c) > ncat_cap))
+                    break;
+                ++np;
+                ncat += c;
+                nv += u;
+                nterm += t;
+                ++q;
+            }
+            if (nterm > 65535u || nv > uint32_t(h->chunk) || int(ncat) > ncat_cap ||
+                nv + 2 * ncat + np + 1 > 2048u)
+                return fail(SA_ERR_UNSUPPORTED, "a pattern is larger than a pack item holds");
+            ItemDesc d{};
+            d.p0 = uint32_t(p);
+            d.np = np;
+            d.v0 = h->hdr[p].var_off;
+            d.nv = nv;
+            d.c0 = h->hdr[p].cat_off;
+            d.ncat = ncat;
+            d.nl = nv;      // variables the warp updates (the blob builder leaves out integrated ones)
+            d.row0 = nterm;
+            d.r0 = kPackItemMark;
+            out.push_back(d);
+            p = q;
+        }
+    }
+    return SA_OK;
+}
+
 int build_lists(sa_heom* h) {
     h->items = template_items(h);
+    if (h->packed) {
+        const int rc0 = h->precision == SA_FP64 ? pack_items<double>(h, h->items) : pack_items<float>(h, h->items);
+        if (rc0) return rc0;
+        // items grouped by template, in the order of the representatives
+        std::stable_sort(h->items.begin(), h->items.end(), [&](const ItemDesc& a, const ItemDesc& b) {
+            return h->hdr[a.p0].inst < h->hdr[b.p0].inst;
+        });
+    }
     const size_t ni = h->items.size();
     std::vector<uint32_t> nrounds(ni + 1, 0);
     std::vector<uint64_t> nrows(ni + 1, 0);
@@ -519,6 +804,7 @@ int build_lists(sa_heom* h) {
         ListItem W;
 #pragma omp for schedule(dynamic, 64)
         for (int64_t c = 0; c < int64_t(ni); ++c) {
+            if (h->items[c].r0 == kPackItemMark) continue;
             list_item(h, h->items[c], W);
             nrounds[c] = uint32_t((W.order.size() + 31) / 32);
             nrows[c] = list_item_rows(W);
@@ -528,7 +814,7 @@ int build_lists(sa_heom* h) {
     uint64_t rr = 0, rw = 0;
     for (size_t c = 0; c < ni; ++c) {
         const uint64_t a = nrounds[c], b = nrows[c];
-        h->items[c].r0 = uint32_t(rr);
+        if (h->items[c].r0 != kPackItemMark) h->items[c].r0 = uint32_t(rr);
         nrounds[c] = uint32_t(rr);
         nrows[c] = rw;
         rr += a;
@@ -556,6 +842,7 @@ int build_lists(sa_heom* h) {
 #pragma omp for schedule(dynamic, 64)
         for (int64_t c = 0; c < int64_t(ni); ++c) {
             ItemDesc& d = h->items[c];
+            if (d.r0 == kPackItemMark) continue;
             list_item(h, d, W);
             const uint32_t nlane = uint32_t(W.order.size());
             d.nl = nlane;
@@ -592,7 +879,8 @@ int build_lists(sa_heom* h) {
     }
     const int rc = h->precision == SA_FP64 ? build_blobs<double>(h) : build_blobs<float>(h);
     if (rc) return rc;
-    // template items relative to their instance; work units instance by instance
+    // template items relative to their instance; work units: a template's
+    // items for one instance after another, or for one pack after another
     std::vector<uint32_t> first(size_t(h->count) + 1, 0);  // first template item of each representative
     {
         std::vector<uint32_t> nit(size_t(h->count), 0);
@@ -610,13 +898,24 @@ int build_lists(sa_heom* h) {
         std::vector<std::vector<int>> members(size_t(h->count));
         for (int i = 0; i < h->count; ++i) members[size_t(h->tmpl[i])].push_back(i);
         h->units.clear();
-        for (int r = 0; r < h->count; ++r)
-            for (int i : members[size_t(r)])
+        for (int r = 0; r < h->count; ++r) {
+            for (int k : h->tmpl_packs[size_t(r)])
                 for (uint32_t c = first[r]; c < first[r + 1]; ++c) {
+                    if (h->items[c].r0 != kPackItemMark) continue;
+                    h->units.push_back(c | kPackUnit);
+                    h->units.push_back(uint32_t(k));
+                }
+            for (int i : members[size_t(r)]) {
+                if (h->pack_of[size_t(i)] >= 0) continue;
+                for (uint32_t c = first[r]; c < first[r + 1]; ++c) {
+                    if (h->items[c].r0 == kPackItemMark) continue;
                     h->units.push_back(c);
                     h->units.push_back(uint32_t(i));
                 }
-        if (h->units.size() / 2 >= (size_t(1) << 32)) return fail(SA_ERR_UNSUPPORTED, "too many work units");
+            }
+        }
+        if (h->units.size() / 2 >= (size_t(1) << 32) || h->items.size() >= size_t(kPackUnit))
+            return fail(SA_ERR_UNSUPPORTED, "too many work units");
     }
     h->list_items = h->items;
     return SA_OK;
@@ -630,7 +929,7 @@ std::vector<InstK<V>> list_instk(const sa_heom* h) {
     for (int i = 0; i < h->count; ++i) {
         const sa_params& q = h->inst[i].p;
         InstK<V>& k = out[size_t(i)];
-        k.var_base = uint32_t(h->var_begin[i]);
+        k.var_base = h->instdev[i].dev_base;  // a list unit's instance is never packed: stride 1
         k.lcoef_base = h->instdev[i].lcoef_base;
         k.N = double(h->inst[i].N);
         k.g = V(q.g);
@@ -791,8 +1090,26 @@ std::vector<V> list_coefficients(const sa_heom* h) {
     return t;
 }
 
+// The packs' coefficient tables: slot s of lane j at cbase + s * n + j.
+template <typename V>
+std::vector<V> pack_coefficients(const sa_heom* h) {
+    const std::vector<V> lc = list_coefficients<V>(h);
+    std::vector<V> t(size_t(2) * h->pcoef_total, V(0));
+    for (const PackDev& pk : h->packs)
+        for (uint32_t j = 0; j < pk.n; ++j) {
+            const int i = int(h->pk_inst[pk.lane0 + j]);
+            const uint32_t ns = uint32_t(list_slots(h->inst[i].m, h->inst[i].L));
+            for (uint32_t sl = 0; sl < ns; ++sl)
+                for (int z = 0; z < 2; ++z)
+                    t[size_t(2) * (pk.cbase + size_t(sl) * pk.n + j) + z] =
+                        lc[size_t(2) * (h->instdev[i].lcoef_base + sl) + z];
+        }
+    return t;
+}
+
 void free_lists(sa_heom* h) {
-    void** ptrs[] = {&h->d_lvd, &h->d_lvj, &h->d_rbase, &h->d_tidx, &h->d_tcid, &h->d_wpat, &h->d_blobs, &h->d_units};
+    void** ptrs[] = {&h->d_lvd,   &h->d_lvj,   &h->d_rbase, &h->d_tidx,  &h->d_tcid,
+                     &h->d_wpat,  &h->d_blobs, &h->d_units, &h->d_punits};
     for (void** p : ptrs) {
         if (*p) cudaFree(*p);
         *p = nullptr;
@@ -823,9 +1140,28 @@ int ensure_tables(sa_heom* h) {
                                          : upload(&h->d_lcoef, list_coefficients<float>(h));
 
         if (!rc && lists) rc = upload(&h->d_blobs, h->blobs);
-        if (!rc && lists) rc = upload(&h->d_units, h->units);
+        if (!rc && lists) {
+            // list units and pack units apart, each in order
+            std::vector<uint32_t> lu, pu;
+            for (size_t u = 0; u < h->units.size(); u += 2) {
+                std::vector<uint32_t>& dst = (h->units[u] & kPackUnit) ? pu : lu;
+                dst.push_back(h->units[u]);
+                dst.push_back(h->units[u + 1]);
+            }
+            h->n_list_units = uint32_t(lu.size() / 2);
+            h->n_pack_units = uint32_t(pu.size() / 2);
+            rc = upload(&h->d_units, lu);
+            if (!rc) rc = upload(&h->d_punits, pu);
+        }
         if (!rc && lists && !h->d_instk)
             rc = h->precision == SA_FP64 ? upload(&h->d_instk, list_instk<double>(h)) : upload(&h->d_instk, list_instk<float>(h));
+        if (!rc && lists && h->packed && !h->packs.empty() && !h->d_pcoef) {
+            rc = upload(&h->d_packs, h->packs);
+            if (!rc) rc = upload(&h->d_pkinst, h->pk_inst);
+            if (!rc)
+                rc = h->precision == SA_FP64 ? upload(&h->d_pcoef, pack_coefficients<double>(h))
+                                             : upload(&h->d_pcoef, pack_coefficients<float>(h));
+        }
 
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_lvd, h->lvd);
         if (!rc && k == SA_KERNEL_ELL) rc = upload(&h->d_wpat, h->wpat);
@@ -864,6 +1200,8 @@ int apply_tuning(sa_heom* h) {
         const int rc0 = check_device(h);
         if (rc0) return rc0;
     }
+    if (h->packed && h->kernel != SA_KERNEL_LISTS)
+        return fail(SA_ERR_UNSUPPORTED, "a handle built with SA_BUILD_PACK_INSTANCES runs the list kernel only");
     build_items(h);
     h->cfg.block = h->block;
     h->cfg.chunk = h->chunk;
@@ -871,9 +1209,11 @@ int apply_tuning(sa_heom* h) {
     h->cfg.kernel = h->kernel;
     int rc = ensure_tables(h);
     if (rc) return rc;
+    h->cfg.pack_smem = h->kernel == SA_KERNEL_LISTS ? int(h->pack_smem) : 0;
+    h->cfg.pack_blob = int(h->pack_blob_off);
     // work the grid shares out: the list kernel's units, the other kernels' items
-    const uint64_t nchunks = h->kernel == SA_KERNEL_LISTS ? h->units.size() / 2 : h->items.size();
     if (h->host_only) return SA_OK;
+    const uint64_t nchunks = h->kernel == SA_KERNEL_LISTS ? h->n_list_units : h->items.size();
     if (h->d_chunk) cudaFree(h->d_chunk);
     if (h->d_vdesc) cudaFree(h->d_vdesc);
     h->d_chunk = h->d_vdesc = nullptr;
@@ -889,6 +1229,23 @@ int apply_tuning(sa_heom* h) {
     const bool persistent = h->use_queue || h->kernel == SA_KERNEL_LISTS;
     h->cfg.grid = persistent ? int(std::min<int64_t>(int64_t(h->num_sms) * occ, blocks_needed)) : int(blocks_needed);
     if (h->cfg.grid < 1) h->cfg.grid = 1;
+    h->cfg.pgrid = 0;
+    h->cfg.side_list = 0;
+    if (h->kernel == SA_KERNEL_LISTS && h->n_pack_units) {
+        int pocc = 0;
+        CK(pack_occupancy(h->cfg, h->precision == SA_FP64, &pocc));
+        if (pocc < 1) return fail(SA_ERR_UNSUPPORTED, "pack kernel does not fit on an SM with this tuning (shared memory)");
+        const int64_t need = (int64_t(h->n_pack_units) + wpb - 1) / wpb;
+        int per_sm = pocc;
+        if (h->n_list_units && h->side && pocc > 1) {
+            // the unpacked instances' list kernel beside it on the side
+            // stream: one CTA per SM for it, the rest for the pack kernel
+            h->cfg.side_list = 1;
+            h->cfg.grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(h->num_sms), blocks_needed)));
+            per_sm = pocc - 1;
+        }
+        h->cfg.pgrid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(h->num_sms) * per_sm, need)));
+    }
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
     return SA_OK;
@@ -902,7 +1259,7 @@ void free_device(sa_heom* h) {
                     h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0,
                     h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS, h->d_lvd, h->d_lvj, h->d_rbase,
                     h->d_tidx, h->d_tcid, h->d_lcoef, h->d_wpat, h->d_blobs, h->d_catpat, h->d_sums,
-                    h->d_rep_loc, h->d_recon_ws, h->d_units, h->d_instk};
+                    h->d_rep_loc, h->d_recon_ws, h->d_units, h->d_instk, h->d_packs, h->d_pkinst, h->d_pcoef};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -954,9 +1311,14 @@ StageLaunch base_launch(const sa_heom* h) {
     s.npat = uint32_t(h->npat);
     s.sums = h->d_sums;
     s.nvar = uint32_t(h->nvar);
-    s.nchunks = uint32_t(h->kernel == SA_KERNEL_LISTS ? h->units.size() / 2 : h->items.size());
+    s.nchunks = uint32_t(h->kernel == SA_KERNEL_LISTS ? h->n_list_units : h->items.size());
+    s.punits = h->d_punits;
+    s.npunits = h->kernel == SA_KERNEL_LISTS ? h->n_pack_units : 0u;
     s.units = h->d_units;
     s.instk = h->d_instk;
+    s.packs = h->d_packs;
+    s.pk_inst = h->d_pkinst;
+    s.pcoef = h->d_pcoef;
     s.err = h->d_err;
     s.debug = h->debug;
     s.ninst = h->count;
@@ -980,6 +1342,9 @@ cudaError_t observables_into(const sa_heom* h, const void* d_state, double* d_ou
 }
 
 // The four fused RK4 stage launches of one step; slot: first queue counter.
+// work counters of one RK4 step: stage s uses slot + s (list or record
+// kernel) and slot + 4 + s (pack kernel)
+constexpr int kQueuePerStep = 8;
 int enqueue_step(sa_heom* h, void* y, double dt, size_t slot, cudaStream_t st) {
     void* acc = h->d_work[0];
     void* xa = h->d_work[1];
@@ -1001,6 +1366,7 @@ int enqueue_step(sa_heom* h, void* y, double dt, size_t slot, cudaStream_t st) {
         L.dt = dt;
         L.stage = s;
         L.queue = h->d_queue + slot + s;
+        L.pqueue = h->d_queue + slot + 4 + s;
         CK(launch_stage(L, h->cfg, h->precision == SA_FP64, st));
     }
     return SA_OK;
@@ -1121,9 +1487,14 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     *out = nullptr;
     sa_heom* h = new (std::nothrow) sa_heom();
     if (!h) return fail(SA_ERR_OOM, "handle");
+    if (flags & ~(SA_BUILD_HOST_ONLY | SA_BUILD_PACK_INSTANCES)) {
+        delete h;
+        return fail(SA_ERR_INVALID_ARG, "unknown build flag");
+    }
     h->count = count;
     h->precision = precision;
     h->host_only = (flags & SA_BUILD_HOST_ONLY) != 0;
+    h->packed = (flags & SA_BUILD_PACK_INSTANCES) != 0;
     h->inst.resize(count);
     for (int i = 0; i < count; ++i) {
         std::string err;
@@ -1226,6 +1597,13 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     }
     decode_records(h);
     assign_templates(h);
+    {
+        const int rc = assign_packs(h);
+        if (rc) {
+            delete h;
+            return rc;
+        }
+    }
     // state layout
     if (precision == SA_FP64) {
         h->state_bytes = (size_t(h->nvar) * 16 + 255) / 256 * 256;
@@ -1287,7 +1665,7 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     }
     if (!rc) {
         e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
-        if (e == cudaSuccess && precision == SA_FP32_AUX) {
+        if (e == cudaSuccess && (precision == SA_FP32_AUX || h->packed)) {
             e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
@@ -1412,6 +1790,32 @@ int sa_heom_dump_coefficients(const sa_heom* h, int inst, double* row, double* c
     return SA_OK;
 }
 
+int sa_heom_state_index(const sa_heom* h, int inst, int64_t var, int64_t* out) {
+    if (!h || !out || inst < 0 || inst >= h->count) return fail(SA_ERR_INVALID_ARG, "handle, instance, out");
+    const uint64_t nv = h->var_begin[size_t(inst) + 1] - h->var_begin[size_t(inst)];
+    if (var < 0 || uint64_t(var) >= nv) return fail(SA_ERR_INVALID_ARG, "variable index out of range");
+    const InstDev& D = h->instdev[size_t(inst)];
+    *out = int64_t(D.dev_base) + var * int64_t(D.dev_stride);
+    return SA_OK;
+}
+
+int sa_heom_dump_packs(const sa_heom* h, int64_t* sizes, uint32_t* packs, uint32_t* lanes, uint8_t* blobs) {
+    if (!h || !sizes) return fail(SA_ERR_INVALID_ARG, "handle and sizes required");
+    const bool have_blobs = h->host_only && h->tables == SA_KERNEL_LISTS;
+    sizes[0] = int64_t(h->packs.size());
+    sizes[1] = int64_t(h->pk_inst.size());
+    sizes[2] = have_blobs ? int64_t(h->blobs.size()) : 0;
+    if (packs)
+        for (size_t k = 0; k < h->packs.size(); ++k) {
+            const PackDev& pk = h->packs[k];
+            const uint32_t f[4] = {pk.base, pk.n, pk.cbase, pk.lane0};
+            std::memcpy(packs + 4 * k, f, sizeof(f));
+        }
+    if (lanes) std::copy(h->pk_inst.begin(), h->pk_inst.end(), lanes);
+    if (blobs && have_blobs) std::copy(h->blobs.begin(), h->blobs.end(), blobs);
+    return SA_OK;
+}
+
 int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32_t* units, uint32_t* lvd,
                        uint8_t* lvj, uint32_t* rbase, uint32_t* tidx, uint16_t* tcid, int32_t* opz) {
     if (!h || !sizes) return fail(SA_ERR_INVALID_ARG, "handle and sizes required");
@@ -1426,8 +1830,8 @@ int sa_heom_dump_lists(const sa_heom* h, int64_t* sizes, uint32_t* items, uint32
     if (items)
         for (size_t c = 0; c < h->items.size(); ++c) {
             const ItemDesc& d = h->items[c];
-            const uint32_t f[8] = {d.p0, d.np, d.v0, d.nv, d.c0, d.ncat, d.r0, d.nl};
-            std::memcpy(items + 8 * c, f, sizeof(f));
+            const uint32_t f[10] = {d.p0, d.np, d.v0, d.nv, d.c0, d.ncat, d.r0, d.nl, d.blob16, d.blob_bytes};
+            std::memcpy(items + 10 * c, f, sizeof(f));
         }
     if (units) std::copy(h->units.begin(), h->units.end(), units);
     if (lvd) std::copy(h->lvd.begin(), h->lvd.end(), lvd);
@@ -1471,7 +1875,7 @@ int sa_heom_state_bytes(const sa_heom* h, size_t* bytes) {
 namespace {
 constexpr uint64_t kCkMagic = 0x4B434D4F45484153ull;  // "SAHEOMCK" in memory order
 constexpr uint32_t kCkVersion = 1;
-constexpr uint32_t kTableVersion = 2;  // bump when the canonical layout changes
+constexpr uint32_t kTableVersion = 3;  // bump when the canonical or device layout changes
 struct CkHeader {
     uint64_t magic;
     uint32_t version, precision;
@@ -1509,6 +1913,11 @@ uint64_t config_hash(const sa_heom* h) {
         x = fnv1a(x, p.cc_im, sizeof(double) * size_t(p.m));
         x = fnv1a(x, p.nu_re, sizeof(double) * size_t(p.m));
         x = fnv1a(x, p.nu_im, sizeof(double) * size_t(p.m));
+    }
+    // the device layout: where every instance's variables lie
+    for (const InstDev& D : h->instdev) {
+        x = fnv1a(x, &D.dev_base, sizeof(D.dev_base));
+        x = fnv1a(x, &D.dev_stride, sizeof(D.dev_stride));
     }
     return x;
 }
@@ -1748,21 +2157,22 @@ int sa_heom_state_upload(const sa_heom* h, const double* host_x, void* d_state, 
     if (rc) return rc;
     if (!host_x || !d_state) return fail(SA_ERR_INVALID_ARG, "host_x and d_state required");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (h->precision == SA_FP64) {
+    const bool f64 = h->precision == SA_FP64;
+    if (f64 && !h->packed) {
         CK(cudaMemcpyAsync(d_state, host_x, size_t(h->nvar) * 16, cudaMemcpyHostToDevice, st));
         CK(cudaStreamSynchronize(st));
         return SA_OK;
     }
-    // SA_FP32_AUX: the complex128 values go to the device as they are, in
-    // chunks through the two RK4 stage-input work vectors (scratch between
-    // steps), and a kernel narrows them there
+    // SA_FP32_AUX, or a packed layout: the complex128 values go to the device
+    // as they are, in chunks through the two RK4 stage-input work vectors
+    // (scratch between steps), and a kernel narrows or places them there
     const uint64_t per = h->state_bytes / 16;
     for (uint64_t n0 = 0, c = 0; n0 < uint64_t(h->nvar); n0 += per, ++c) {
         const uint64_t cnt = std::min<uint64_t>(per, uint64_t(h->nvar) - n0);
         void* stage = h->d_work[1 + (c & 1)];
         CK(cudaMemcpyAsync(stage, host_x + 2 * n0, cnt * 16, cudaMemcpyHostToDevice, st));
-        CK(launch_marshal(static_cast<const InstDev*>(h->d_inst), h->count, n0, cnt, stage, d_state,
-                          side(h, d_state), 1, st));
+        CK(launch_marshal(static_cast<const InstDev*>(h->d_inst), h->count, h->packed ? 1 : 0, n0, cnt, stage,
+                          d_state, f64 ? nullptr : side(h, d_state), f64 ? 1 : 0, 1, st));
     }
     CK(cudaStreamSynchronize(st));
     return SA_OK;
@@ -1773,19 +2183,22 @@ int sa_heom_state_download(const sa_heom* h, const void* d_state, double* host_x
     if (rc) return rc;
     if (!host_x || !d_state) return fail(SA_ERR_INVALID_ARG, "host_x and d_state required");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (h->precision == SA_FP64) {
+    const bool f64 = h->precision == SA_FP64;
+    if (f64 && !h->packed) {
         CK(cudaMemcpyAsync(host_x, d_state, size_t(h->nvar) * 16, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         return SA_OK;
     }
-    // SA_FP32_AUX: widened to complex128 on the device, chunk by chunk in the
-    // two RK4 stage-input work vectors, then copied to the caller's buffer
+    // SA_FP32_AUX, or a packed layout: widened (or gathered) to complex128 in
+    // canonical order on the device, chunk by chunk in the two RK4
+    // stage-input work vectors, then copied to the caller's buffer
     const uint64_t per = h->state_bytes / 16;
     for (uint64_t n0 = 0, c = 0; n0 < uint64_t(h->nvar); n0 += per, ++c) {
         const uint64_t cnt = std::min<uint64_t>(per, uint64_t(h->nvar) - n0);
         void* stage = h->d_work[1 + (c & 1)];
-        CK(launch_marshal(static_cast<const InstDev*>(h->d_inst), h->count, n0, cnt, stage,
-                          const_cast<void*>(d_state), side(h, d_state), 0, st));
+        CK(launch_marshal(static_cast<const InstDev*>(h->d_inst), h->count, h->packed ? 1 : 0, n0, cnt, stage,
+                          const_cast<void*>(d_state), f64 ? nullptr : side(h, const_cast<void*>(d_state)),
+                          f64 ? 1 : 0, 0, st));
         CK(cudaMemcpyAsync(host_x + 2 * n0, stage, cnt * 16, cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
@@ -1798,7 +2211,7 @@ int sa_heom_rhs(sa_heom* h, const void* d_x, void* d_dx, void* stream) {
     if (!d_x || !d_dx || d_x == d_dx) return fail(SA_ERR_INVALID_ARG, "distinct d_x and d_dx required");
     if (misaligned(d_x) || misaligned(d_dx)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CK(cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int), st));
+    CK(cudaMemsetAsync(h->d_queue, 0, 2 * sizeof(unsigned int), st));
     StageLaunch L = base_launch(h);
     L.x_in = d_x;
     L.x_out = d_dx;
@@ -1806,6 +2219,7 @@ int sa_heom_rhs(sa_heom* h, const void* d_x, void* d_dx, void* stream) {
     L.xs_out = side(h, d_dx);
     L.stage = -1;
     L.queue = h->d_queue;
+    L.pqueue = h->d_queue + 1;
     CK(launch_stage(L, h->cfg, h->precision == SA_FP64, st));
     return SA_OK;
 }
@@ -1816,7 +2230,7 @@ int sa_heom_step(sa_heom* h, void* d_state, double dt, void* stream) {
     if (!d_state || !std::isfinite(dt)) return fail(SA_ERR_INVALID_ARG, "d_state and finite dt required");
     if (misaligned(d_state)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    CK(cudaMemsetAsync(h->d_queue, 0, 4 * sizeof(unsigned int), st));
+    CK(cudaMemsetAsync(h->d_queue, 0, kQueuePerStep * sizeof(unsigned int), st));
     return enqueue_step(h, d_state, dt, 0, st);
 }
 
@@ -1829,11 +2243,12 @@ static int graph_for(sa_heom* h, void* d_state, double dt, int64_t steps, cudaGr
         *out = it->second;
         return SA_OK;
     }
-    int rc = ensure_queue(h, size_t(4 * steps));
+    int rc = ensure_queue(h, size_t(kQueuePerStep * steps));
     if (rc) return rc;
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int) * 4 * steps, h->cap);
-    for (int64_t s = 0; s < steps && e == cudaSuccess && rc == SA_OK; ++s) rc = enqueue_step(h, d_state, dt, 4 * s, h->cap);
+    cudaError_t e = cudaMemsetAsync(h->d_queue, 0, sizeof(unsigned int) * kQueuePerStep * steps, h->cap);
+    for (int64_t s = 0; s < steps && e == cudaSuccess && rc == SA_OK; ++s)
+        rc = enqueue_step(h, d_state, dt, size_t(kQueuePerStep * s), h->cap);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(queue) in capture");
@@ -2033,6 +2448,7 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
             for (int b : blocks)
                 for (int q = 0; q < 2; ++q) {
                     if (c < h->max_u) continue;
+                    if (h->packed && k != SA_KERNEL_LISTS) continue;  // a packed layout runs the list kernel only
                     // the ELL kernel has neither work items nor a queue
                     if (k == SA_KERNEL_ELL && (q != 0 || c != std::max(128, (h->max_u + 31) / 32 * 32))) continue;
                     h->kernel = k;
@@ -2073,8 +2489,11 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
 // stage in SA_FP32_AUX mode
 int sa_heom_launches_per_step(const sa_heom* h) {
     if (!h) return 0;
-    const int per_stage = 1 + (h->precision == SA_FP64 ? 0 : 1) + (h->kernel == SA_KERNEL_ELL ? 1 : 0);
-    return 4 * per_stage;
+    int main = 1;
+    if (h->kernel == SA_KERNEL_ELL) main = 2;  // grouped sums, then the ELL kernel
+    if (h->kernel == SA_KERNEL_LISTS && !h->host_only)
+        main = (h->n_list_units ? 1 : 0) + (h->n_pack_units ? 1 : 0);  // list kernel, pack kernel
+    return 4 * (main + (h->precision == SA_FP64 ? 0 : 1));
 }
 
 int sa_heom_set_debug(sa_heom* h, int flags) {

@@ -91,6 +91,14 @@ template <typename T> struct StageParams {
     const unsigned char* __restrict__ blobs; // list kernel: per-item table blobs (16-byte aligned)
     const uint2* __restrict__ units;         // list kernel: work units (template item, instance)
     const InstK<T>* __restrict__ instk;      // list kernel: per-instance constants
+    const PackDev* __restrict__ packs;       // pack kernel: instance packs
+    const uint32_t* __restrict__ pk_inst;    // pack kernel: instance of every pack lane
+    const C* __restrict__ pcoef;             // pack kernel: interleaved coefficient tables of the packs
+    const uint2* __restrict__ punits;        // pack kernel: work units (pack item | kPackUnit, pack)
+    uint32_t npunits;
+    uint32_t pack_smem;                      // pack kernel: shared-memory bytes per warp
+    uint32_t pack_blob;                      // pack kernel: offset of the item blob in a warp's shared memory
+    unsigned int* pqueue;                    // pack kernel: its work counter
     const uint32_t* __restrict__ wpat;      // first pattern of every warp row of 32 variables
     uint32_t nvar;
     const uint32_t* __restrict__ catpat;    // owning pattern of every category
@@ -639,6 +647,202 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
     return W;
 }
 
+// One pack unit: a pack item evaluated for the n <= 32 instances of a pack,
+// lane j taking the pack's instance j (lanes j >= n shadow lane 0 and store
+// nothing).  The pack's state is interleaved, so every access of the warp --
+// a variable of the item, a tier +/-1 target, a coefficient slot, y and the
+// accumulator -- is one contiguous run of n elements, and the item's tables
+// (one bulk copy into the warp's shared memory) are read by all lanes alike.
+//  * the item's variables one per round, in three phases (P, T, S; then X,
+//    Y; then Z): each adds its own value, weighted, to the grouped sums it
+//    enters (R_q and C_q of Eqs. grouped-row-sum, grouped-column-sum, the Z
+//    sum of Eq. HZ; in the warp's shared memory, one column per lane), which
+//    the next phase reads as operands; each gets its diagonal (-Gamma_Lambda
+//    plus the instance's loss, terminator and detuning), commutator
+//    -i g (op[a] - op[b]) with host-chosen operands, hierarchy terms (Eqs.
+//    uvar-up, uvar-down) and the fused RK4 update.  Within a phase the loads
+//    of the next variable (its value, operands, y, accumulator and first two
+//    terms) are issued before the current one is finished, so two
+//    variables' memory latencies overlap.
+// Returns false when the bounded wait for the tables expired (error bit set,
+// the copy drained).
+template <typename T, bool FP64SIDE>
+__device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDesc& d, uint32_t pkid,
+                                          unsigned char* wsm, uint64_t* bar, uint32_t& parity, int lane) {
+    using C = typename Cx<T>::t;
+    C* const ccs = reinterpret_cast<C*>(wsm + 16);            // 5 x 32 per-lane diagonal parts
+    C* const sums = ccs + 5 * 32;                             // grouped sums, 32 lanes per entry
+    unsigned char* const blob = wsm + P.pack_blob;
+    const PackDev pk = P.packs[pkid];
+    const uint32_t n = pk.n;
+    const bool act = uint32_t(lane) < n;
+    const uint32_t ll = act ? uint32_t(lane) : 0u;
+    if (lane == 0) {
+        // earlier units wrote this shared memory with ordinary stores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, d.blob_bytes);
+        bulk_g2s(blob, P.blobs + size_t(d.blob16) * 16, d.blob_bytes, bar);
+    } else if ((lane == 1 || lane == 2) && P.stage > 0) {
+        // the item's y and accumulator block (contiguous in the pack) into L2
+        const Span t = span(lane == 1 ? P.y : static_cast<const C*>(P.acc), size_t(pk.base) + size_t(d.v0) * n,
+                            d.nv * n, sizeof(C));
+        if (t.bytes) bulk_prefetch_l2(t.src, t.bytes);
+    }
+    // the lane's instance constants while the copy is in flight
+    const InstK<T>* const ik = P.instk + P.pk_inst[pk.lane0 + ll];
+    const T g = ik->g, Nt = T(ik->N);
+#pragma unroll
+    for (int cl = 0; cl < 5; ++cl) ccs[cl * 32 + lane] = mk(ik->cc[2 * cl], ik->cc[2 * cl + 1]);
+    if (!__all_sync(0xffffffffu, !P.expire_wait && mbar_wait(bar, parity))) {
+        if (lane == 0) atomicOr(P.err, 1u);
+        mbar_wait(bar, parity);
+        return false;
+    }
+    parity ^= 1u;
+    const uint32_t np = d.np, ncat = d.ncat, nv = d.nv, nl = d.nl;
+    const PackLayout B = pack_layout<T>(np, ncat, nl, d.row0);
+    const ItemPat* const ph = reinterpret_cast<const ItemPat*>(blob + B.pat);
+    const C* const pd = reinterpret_cast<const C*>(blob + B.pd);
+    const T* const cM = reinterpret_cast<const T*>(blob + B.cM);
+    const uint4* const vrec = reinterpret_cast<const uint4*>(blob + B.vrec);
+    const uint32_t* const tgt = reinterpret_cast<const uint32_t*>(blob + B.tgt);
+    const uint16_t* const tsl = reinterpret_cast<const uint16_t*>(blob + B.tsl);
+    (void)ph;
+    // lane base pointers; element offsets from them are 32-bit
+    const size_t lb = size_t(pk.base) + ll;
+    const C* __restrict__ X = P.x_in + lb;
+    const C* __restrict__ cf = P.pcoef + pk.cbase + ll;
+    const uint32_t iv0 = d.v0 * n;  // the item's variable 0
+    // the grouped sums start at zero; the zero operand stays zero
+    C* const sl = sums + lane;
+    const uint32_t nsums = 2 * ncat + np + 1;
+    for (uint32_t k = 0; k < nsums; ++k) sl[k * 32] = mk(T(0), T(0));
+    // weight of a contribution: kind 1 one, 2 M_c, 3 M_c - 1, 4 -M_c (the zero
+    // category's multiplicity is N - r, stored as -r)
+    auto weight = [&](uint32_t w) {
+        const T m = cM[(w >> 14) & 1023u];
+        const T M = m > T(0) ? m : Nt + m;
+        const uint32_t k = (w >> 11) & 7u;
+        return k == 1u ? T(1) : (k == 2u ? M : (k == 3u ? M - T(1) : -M));
+    };
+    const C* __restrict__ Yb = P.y + lb;
+    C* const Ab = P.acc + lb;
+    C* const XO = P.x_out + lb;
+    C* const YO = P.y_out + lb;
+    const int stage = P.stage;
+    const T dtT = T(P.dt);
+    const T aT = stage == 2 ? dtT : T(0.5) * dtT;
+    const C z = mk(T(0), T(0));
+    auto opnd = [&](uint32_t code) { return code < nv ? __ldg(X + (iv0 + code * n)) : sl[(code - nv) * 32]; };
+    // loads of variable i: value, operands, y, accumulator, first two terms
+    auto fetch = [&](uint32_t i, C& v, C& oa, C& ob, C& yv, C& av, C& x0, C& c0, C& x1, C& c1) {
+        const uint4 r = vrec[i];
+        const uint32_t off = iv0 + (r.y & 1023u) * n;
+        const uint32_t u0 = (r.y >> 10) & 65535u, cnt = r.y >> 26;
+        v = __ldg(X + off);
+        oa = opnd(r.x & 2047u);
+        ob = opnd((r.x >> 11) & 2047u);
+        yv = z;
+        av = z;
+        if (stage > 0) {
+            yv = __ldcg(Yb + off);
+            av = __ldcg(Ab + off);
+        }
+        x0 = c0 = x1 = c1 = z;
+        if (cnt > 0) {
+            x0 = __ldg(X + tgt[u0] * n);
+            c0 = __ldg(cf + uint32_t(tsl[u0]) * n);
+        }
+        if (cnt > 1) {
+            x1 = __ldg(X + tgt[u0 + 1] * n);
+            c1 = __ldg(cf + uint32_t(tsl[u0 + 1]) * n);
+        }
+    };
+    // the rest of variable i: its contributions to the grouped sums, then
+    // diagonal, commutator, terms and the RK4 update
+    auto finish = [&](uint32_t i, C v, C oa, C ob, C yv, C av, C x0, C c0, C x1, C c1) {
+        const uint4 r = vrec[i];
+        if (r.z & 0x3800u) sl[(r.z & 2047u) * 32] = caxpy(weight(r.z), v, sl[(r.z & 2047u) * 32]);
+        if (r.w & 0x3800u) sl[(r.w & 2047u) * 32] = caxpy(weight(r.w), v, sl[(r.w & 2047u) * 32]);
+        const uint32_t off = iv0 + (r.y & 1023u) * n;
+        const uint32_t u0 = (r.y >> 10) & 65535u, u1 = u0 + (r.y >> 26);
+        const C dgl = cadd(pd[(r.x >> 25) & 31u], ccs[((r.x >> 22) & 7u) * 32 + lane]);
+        const C t = csub(oa, ob);
+        C dv = mk(g * t.y, -g * t.x);
+        dv = cfma(dgl, v, dv);
+        dv = cfma(c0, x0, dv);
+        dv = cfma(c1, x1, dv);
+        uint32_t u = u0 + 2;
+        for (; u + 2 <= u1; u += 2) {
+            const C xa = __ldg(X + tgt[u] * n), ca = __ldg(cf + uint32_t(tsl[u]) * n);
+            const C xb = __ldg(X + tgt[u + 1] * n), cb = __ldg(cf + uint32_t(tsl[u + 1]) * n);
+            dv = cfma(ca, xa, dv);
+            dv = cfma(cb, xb, dv);
+        }
+        if (u < u1) dv = cfma(__ldg(cf + uint32_t(tsl[u]) * n), __ldg(X + tgt[u] * n), dv);
+        if (act) {
+            if (stage < 0) {
+                XO[off] = dv;
+            } else if (stage == 0) {
+                Ab[off] = dv;
+                XO[off] = caxpy(aT, dv, v);  // x_in is y in the first stage
+            } else if (stage == 3) {
+                YO[off] = caxpy(dtT / T(6), cadd(av, dv), yv);
+            } else {
+                Ab[off] = caxpy(T(2), dv, av);
+                XO[off] = caxpy(aT, dv, yv);
+            }
+        }
+    };
+    // the three phases, each with two register sets in turn: variable i + 1
+    // loads while variable i finishes
+    const uint32_t ph1 = d.row1 & 65535u, ph2 = ph1 + (d.row1 >> 16);
+    uint32_t i0 = 0;
+#pragma unroll 1
+    for (int phase = 0; phase < 3; ++phase) {
+        const uint32_t i1 = phase == 0 ? ph1 : (phase == 1 ? ph2 : nl);
+        C vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1;
+        C vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1;
+        if (i0 < i1) fetch(i0, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
+        for (uint32_t i = i0; i < i1; i += 2) {
+            if (i + 1 < i1) fetch(i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
+            finish(i, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
+            if (i + 1 >= i1) break;
+            if (i + 2 < i1) fetch(i + 2, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
+            finish(i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
+        }
+        i0 = i1;
+    }
+    __syncwarp();
+    return true;
+}
+
+// The pack kernel: persistent warps drawing pack units (static striding or
+// the atomic counter), each warp with an mbarrier and a blob buffer of
+// pack_smem bytes.  Registers are budgeted apart from the list kernel's.
+template <typename T, bool FP64SIDE>
+__global__ void __maxnreg__(sizeof(T) == 8 ? 128 : 80) pack_stage_kernel(StageParams<T> P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    unsigned char* const wsm = smem + size_t(wib) * P.pack_smem;
+    uint64_t* const bar = reinterpret_cast<uint64_t*>(wsm);
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    ItemQueue Q;
+    Q.init(P.use_queue, wib);
+    uint32_t parity = 0;
+    for (;;) {
+        const unsigned int c = Q.next(P.pqueue, P.npunits, lane);
+        if (c >= P.npunits) break;
+        const uint2 un = P.punits[c];
+        if (!pack_unit<T, FP64SIDE>(P, P.items[un.x & ~kPackUnit], un.y, wsm, bar, parity, lane)) return;
+    }
+}
+
 // One warp per work item, like stage_kernel, but
 //  * the item's stage-input slice and its table blob (instance constants,
 //    patterns, damping rates, category words, multiplicities and owners,
@@ -1053,13 +1257,18 @@ __global__ void __launch_bounds__(128) rho0_kernel(StageParams<T> P, int ninst) 
     }
     const double2* xsin = P.xs_in + I.side;
     auto own = [&](int ii) { return xsin[ii]; };
-    auto gath = [&](uint32_t ii) { const C t = __ldg(P.x_in + ii); return make_double2(t.x, t.y); };
+    // targets are batch-global canonical indices of the instance's tier-1
+    // variables; the device state may hold the instance strided (a pack lane)
+    auto gath = [&](uint32_t ii) {
+        const C t = __ldg(P.x_in + I.dev_base + size_t(ii - I.var_begin) * I.dev_stride);
+        return make_double2(t.x, t.y);
+    };
     const double2 k = var_rhs<double>(P, kind, q, r, G, P.cat_word + h.cat_off, P.cat_M + h.cat_off,
                                       reinterpret_cast<const uint2*>(P.rec) + h.rec_off, h, I,
                                       make_double2(0.0, 0.0), own, gath);
     const double dt = P.dt;
     const int si = int(I.side) + loc;
-    const uint32_t vg = h.var_off + loc;
+    const size_t vg = I.dev_base + size_t(loc) * I.dev_stride;  // the physical pattern starts the instance
     if (P.stage < 0) {
         P.xs_out[si] = k;
         P.x_out[vg] = mk(T(k.x), T(k.y));
@@ -1097,30 +1306,34 @@ __global__ void observables_kernel(const InstDev* __restrict__ inst, const doubl
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ninst) return;
     const InstDev I = inst[i];
-    const double2* v = side64 ? side64 + I.side : main64 + I.var_begin;
+    // the physical representative: FP64 side slots, or the FP64 state (where
+    // a packed instance's variables are dev_stride apart)
+    const double2* const vb = side64 ? side64 + I.side : main64 + I.dev_base;
+    const size_t vs = side64 ? 1 : I.dev_stride;
+    auto v = [&](int l) { return vb[size_t(l) * vs]; };
     const PatHdr h = hdr[I.pat_begin];
     const int G = h.G;
     const double* M = catMd + h.cat_off;
     const uint32_t* cw = cat_word + h.cat_off;
-    const double2 Z = v[0];
+    const double2 Z = v(0);
     double Pexc = 0.0, PBn = 0.0, XY = 0.0;
     double hd = fabs(Z.y);
     for (int q = 1; q <= G; ++q) {
         const double Mq = M[q - 1];
-        const double2 Xq = v[q], Yq = v[G + q], Pq = v[2 * G + q];
+        const double2 Xq = v(q), Yq = v(G + q), Pq = v(2 * G + q);
         Pexc += Mq * Pq.x;
         PBn += Mq * Pq.x;
         XY += Mq * (Xq.x + Yq.x);
         hd = fmax(hd, fabs(Pq.y));
         hd = fmax(hd, hypot(Xq.x - Yq.x, Xq.y + Yq.y));
         if (Mq >= 2.0) {
-            const double2 Tq = v[(G + 1) * (G + 1) + int((cw[q - 1] >> 15) & 31u)];
+            const double2 Tq = v((G + 1) * (G + 1) + int((cw[q - 1] >> 15) & 31u));
             PBn += Mq * (Mq - 1.0) * Tq.x;
             hd = fmax(hd, fabs(Tq.y));
         }
         for (int r = 1; r <= G; ++r) {
             if (r == q) continue;
-            const double2 Sqr = v[loc_S_d(G, q, r)], Srq = v[loc_S_d(G, r, q)];
+            const double2 Sqr = v(loc_S_d(G, q, r)), Srq = v(loc_S_d(G, r, q));
             PBn += Mq * M[r - 1] * Sqr.x;
             hd = fmax(hd, hypot(Sqr.x - Srq.x, Sqr.y + Srq.y));
         }
@@ -1150,8 +1363,9 @@ __global__ void init_rho0_kernel(const InstDev* __restrict__ inst, int ninst, co
     const InstDev I = inst[i];
     for (uint32_t j = 0; j < I.n_rho0; ++j) {
         const double re = rho0[size_t(stride) * i + 2 * j], im = rho0[size_t(stride) * i + 2 * j + 1];
-        if (main64) main64[I.var_begin + j] = make_double2(re, im);
-        if (main32) main32[I.var_begin + j] = make_float2(float(re), float(im));
+        const size_t e = I.dev_base + size_t(j) * I.dev_stride;
+        if (main64) main64[e] = make_double2(re, im);
+        if (main32) main32[e] = make_float2(float(re), float(im));
         if (side64) side64[I.side + j] = make_double2(re, im);
     }
 }
@@ -1162,18 +1376,33 @@ __global__ void init_rho0_kernel(const InstDev* __restrict__ inst, int ninst, co
 // physical representatives' variables exactly into their FP64 side slots
 // (narrow), or widen the float2 state into the staging buffer with the
 // physical representatives taken from their side slots (widen).
-__global__ void narrow_state_kernel(const double2* __restrict__ stage, uint64_t n0, uint64_t cnt,
-                                    float2* __restrict__ main32) {
-    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= cnt) return;
-    const double2 v = stage[i];
-    main32[n0 + i] = make_float2(float(v.x), float(v.y));
+// (packed handles: the element of canonical variable gv is found through
+// its instance, the last one whose var_begin <= gv)
+__device__ __forceinline__ uint64_t state_elem(const InstDev* __restrict__ inst, int ninst, int packed, uint64_t gv) {
+    if (!packed) return gv;
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (uint64_t(inst[mid].var_begin) <= gv) lo = mid;
+        else hi = mid - 1;
+    }
+    return uint64_t(inst[lo].dev_base) + (gv - inst[lo].var_begin) * inst[lo].dev_stride;
 }
-__global__ void widen_state_kernel(const float2* __restrict__ main32, uint64_t n0, uint64_t cnt,
-                                   double2* __restrict__ stage) {
+__device__ __forceinline__ float2 to_state(double2 v, float2*) { return make_float2(float(v.x), float(v.y)); }
+__device__ __forceinline__ double2 to_state(double2 v, double2*) { return v; }
+template <typename S>
+__global__ void to_device_kernel(const InstDev* __restrict__ inst, int ninst, int packed,
+                                 const double2* __restrict__ stage, uint64_t n0, uint64_t cnt, S* __restrict__ main) {
     const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= cnt) return;
-    const float2 v = main32[n0 + i];
+    main[state_elem(inst, ninst, packed, n0 + i)] = to_state(stage[i], (S*)nullptr);
+}
+template <typename S>
+__global__ void from_device_kernel(const InstDev* __restrict__ inst, int ninst, int packed,
+                                   const S* __restrict__ main, uint64_t n0, uint64_t cnt, double2* __restrict__ stage) {
+    const uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const S v = main[state_elem(inst, ninst, packed, n0 + i)];
     stage[i] = make_double2(double(v.x), double(v.y));
 }
 // one thread per side slot: the physical representative's variables that
@@ -1194,13 +1423,16 @@ __global__ void side_state_kernel(const InstDev* __restrict__ inst, int ninst, u
 
 // ---- host launch wrappers (called from api.cu) -----------------------------
 
-size_t stage_smem_bytes(int item, int block, bool fp64, int kernel) {
-    if (kernel == SA_KERNEL_ELL) return 0;
+// shared memory of one CTA of the stage kernel (the list kernel's layout for
+// the item capacity, or the record kernel's), and of the pack kernel
+static size_t stage_smem_bytes(const LaunchCfg& cfg, bool fp64) {
+    if (cfg.kernel == SA_KERNEL_ELL) return 0;
     size_t w;
-    if (kernel == SA_KERNEL_LISTS) w = fp64 ? list_smem_bytes<double>(item) : list_smem_bytes<float>(item);
-    else w = fp64 ? warp_smem_bytes<double>(item) : warp_smem_bytes<float>(item);
-    return w * size_t(block / 32);
+    if (cfg.kernel == SA_KERNEL_LISTS) w = fp64 ? list_smem_bytes<double>(cfg.chunk) : list_smem_bytes<float>(cfg.chunk);
+    else w = fp64 ? warp_smem_bytes<double>(cfg.chunk) : warp_smem_bytes<float>(cfg.chunk);
+    return w * size_t(cfg.block / 32);
 }
+static size_t pack_smem_bytes(const LaunchCfg& cfg) { return size_t(cfg.pack_smem + 15) / 16 * 16 * size_t(cfg.block / 32); }
 
 // operand-area offsets of the list kernel for a given item capacity
 void list_operand_layout(int item, int* opR, int* opC, int* opZ, int* opZero) {
@@ -1213,25 +1445,28 @@ void list_operand_layout(int item, int* opR, int* opC, int* opZ, int* opZero) {
 template <typename T, bool SIDE>
 static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int ninst, cudaStream_t st,
                             const StageLaunch& s) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, sizeof(T) == 8, cfg.kernel);
+    const size_t sm = stage_smem_bytes(cfg, sizeof(T) == 8);
     // the FP64 physical-representative kernel reads the same stage input and
-    // writes other variables: it overlaps the stage kernel on a side stream
+    // writes other variables: it overlaps the stage kernel on a side stream;
+    // so does the list kernel of a packed handle's unpacked instances, beside
+    // the pack kernel (a few CTAs per SM left to it)
     cudaStream_t side = static_cast<cudaStream_t>(s.side_stream);
-    const bool fork = SIDE && side && s.ev_fork && s.ev_join;
+    const bool have_side = side && s.ev_fork && s.ev_join;
+    const bool side_list = have_side && cfg.kernel == SA_KERNEL_LISTS && cfg.side_list && p.npunits && p.nchunks;
+    const bool fork = have_side && (SIDE || side_list);
+    if (fork) {
+        cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(s.ev_fork), st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, static_cast<cudaEvent_t>(s.ev_fork), 0);
+        if (e != cudaSuccess) return e;
+    }
     if (SIDE) {
-        cudaStream_t rs = st;
-        if (fork) {
-            cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(s.ev_fork), st);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, static_cast<cudaEvent_t>(s.ev_fork), 0);
-            if (e != cudaSuccess) return e;
-            rs = side;
-        }
         const int threads = ninst * kSideSlots;
-        rho0_kernel<T><<<(threads + 127) / 128, 128, 0, rs>>>(p, ninst);
-        if (fork) {
-            const cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(s.ev_join), side);
-            if (e != cudaSuccess) return e;
-        }
+        rho0_kernel<T><<<(threads + 127) / 128, 128, 0, fork ? side : st>>>(p, ninst);
+    }
+    if (side_list) list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, side>>>(p);
+    if (fork) {
+        const cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(s.ev_join), side);
+        if (e != cudaSuccess) return e;
     }
     if (cfg.kernel == SA_KERNEL_ELL) {
         const unsigned gs = unsigned((size_t(p.ncat) + p.npat + 255) / 256);
@@ -1239,7 +1474,8 @@ static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int n
         const unsigned grid = unsigned((size_t(p.nvar) + 31) / 32 * 32 + cfg.block - 1) / unsigned(cfg.block);
         if (grid > 0) ell_stage_kernel<T, SIDE><<<grid, cfg.block, 0, st>>>(p);
     } else if (cfg.kernel == SA_KERNEL_LISTS) {
-        list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+        if (p.npunits) pack_stage_kernel<T, SIDE><<<cfg.pgrid, cfg.block, pack_smem_bytes(cfg), st>>>(p);
+        if (p.nchunks && !side_list) list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
 
     } else {
         stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
@@ -1288,6 +1524,14 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.blobs = static_cast<const unsigned char*>(s.blobs);
     p.units = static_cast<const uint2*>(s.units);
     p.instk = static_cast<const InstK<T>*>(s.instk);
+    p.packs = static_cast<const PackDev*>(s.packs);
+    p.pk_inst = static_cast<const uint32_t*>(s.pk_inst);
+    p.pcoef = static_cast<const C*>(s.pcoef);
+    p.punits = static_cast<const uint2*>(s.punits);
+    p.npunits = s.npunits;
+    p.pack_smem = uint32_t((cfg.pack_smem + 15) / 16 * 16);
+    p.pack_blob = uint32_t(cfg.pack_blob);
+    p.pqueue = s.pqueue;
     p.nvar = s.nvar;
     p.nchunks = s.nchunks;
     p.chunk = cfg.chunk;
@@ -1324,8 +1568,23 @@ static cudaError_t occupancy_of(K kern, int block, size_t sm, int lim, int* bloc
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, block, sm);
 }
 
+// CTAs per SM of the pack kernel (0 if its shared memory does not fit)
+cudaError_t pack_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm) {
+    const size_t sm = pack_smem_bytes(cfg);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int lim = std::max(optin - 1024, 0);
+    if (sm > size_t(lim)) {
+        *blocks_per_sm = 0;
+        return cudaSuccess;
+    }
+    if (fp64) return occupancy_of(pack_stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
+    return occupancy_of(pack_stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
+}
+
 cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm) {
-    const size_t sm = stage_smem_bytes(cfg.chunk, cfg.block, fp64, cfg.kernel);
+    const size_t sm = stage_smem_bytes(cfg, fp64);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -1365,22 +1624,24 @@ cudaError_t launch_init_rho0(const InstDev* inst, int ninst, const double* rho0,
     return cudaGetLastError();
 }
 
-cudaError_t launch_marshal(const InstDev* inst, int ninst, uint64_t n0, uint64_t cnt, void* stage, void* main32,
-                           void* side64, int to_device, cudaStream_t st) {
+cudaError_t launch_marshal(const InstDev* inst, int ninst, int packed, uint64_t n0, uint64_t cnt, void* stage,
+                           void* main, void* side64, int fp64, int to_device, cudaStream_t st) {
     if (cnt == 0) return cudaSuccess;
     const unsigned grid = unsigned((cnt + 255) / 256);
     const unsigned sgrid = unsigned((size_t(ninst) * kSideSlots + 255) / 256);
+    const double2* sg = static_cast<const double2*>(stage);
+    double2* sd = static_cast<double2*>(stage);
     if (to_device) {
-        narrow_state_kernel<<<grid, 256, 0, st>>>(static_cast<const double2*>(stage), n0, cnt,
-                                                  static_cast<float2*>(main32));
-        side_state_kernel<<<sgrid, 256, 0, st>>>(inst, ninst, n0, cnt, static_cast<double2*>(stage),
-                                                 static_cast<double2*>(side64), 1);
+        if (fp64) to_device_kernel<<<grid, 256, 0, st>>>(inst, ninst, packed, sg, n0, cnt, static_cast<double2*>(main));
+        else to_device_kernel<<<grid, 256, 0, st>>>(inst, ninst, packed, sg, n0, cnt, static_cast<float2*>(main));
     } else {
-        widen_state_kernel<<<grid, 256, 0, st>>>(static_cast<const float2*>(main32), n0, cnt,
-                                                 static_cast<double2*>(stage));
-        side_state_kernel<<<sgrid, 256, 0, st>>>(inst, ninst, n0, cnt, static_cast<double2*>(stage),
-                                                 static_cast<double2*>(side64), 0);
+        if (fp64) from_device_kernel<<<grid, 256, 0, st>>>(inst, ninst, packed, static_cast<const double2*>(main), n0,
+                                                           cnt, sd);
+        else from_device_kernel<<<grid, 256, 0, st>>>(inst, ninst, packed, static_cast<const float2*>(main), n0, cnt,
+                                                      sd);
     }
+    if (side64)
+        side_state_kernel<<<sgrid, 256, 0, st>>>(inst, ninst, n0, cnt, sd, static_cast<double2*>(side64), to_device);
     return cudaGetLastError();
 }
 

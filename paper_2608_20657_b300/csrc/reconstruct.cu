@@ -64,7 +64,7 @@ __global__ void gather_responses_kernel(const InstDev* __restrict__ inst, const 
     double2 v = d2(0.0, 0.0);
     if (S.loc >= 0) {
         const InstDev I = inst[S.inst];
-        v = side64 ? side64[I.side + S.loc] : main64[I.var_begin + S.loc];
+        v = side64 ? side64[I.side + S.loc] : main64[I.dev_base + size_t(S.loc) * I.dev_stride];
         if (S.conj) v.y = -v.y;
     }
     resp[t] = v;

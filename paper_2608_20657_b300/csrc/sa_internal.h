@@ -86,7 +86,10 @@ struct InstDev {
     uint32_t n_rho0;     // variables of the physical representative (5 for d = 0, up to 26 for d = 3)
     uint32_t pat_begin;  // first pattern (the empty pattern)
     uint32_t lcoef_base; // first slot of the instance's list/ELL coefficient table
-    uint32_t pad2[2];
+    // where the instance's variable l lives in the device state: element
+    // dev_base + l * dev_stride (var_begin + l, stride 1, unless the handle
+    // packs instances; a packed instance is one lane of its pack)
+    uint32_t dev_base, dev_stride;
     double term;         // terminator strength Delta (0: off)
     double pad3;
 };
@@ -203,6 +206,67 @@ SA_HOST_DEVICE inline BlobLayout blob_layout(uint32_t np, uint32_t ncat, uint32_
 }
 constexpr int kItemPats = 16;     // patterns per work item (at most 31: 5-bit local index)
 constexpr int kMaxItemVars = 1024; // variables per work item (10-bit local index)
+// An instance pack (SA_BUILD_PACK_INSTANCES): n <= 32 instances of one
+// template stored interleaved, variable l of lane j at element
+// base + l * n + j of the device state; their list coefficient tables
+// interleaved the same way from element cbase (slot s of lane j at
+// cbase + s * n + j); lane j's instance is pk_inst[lane0 + j].
+struct PackDev {
+    uint32_t base, n, cbase, lane0;
+};
+constexpr int kPackMin = 16;   // fewer lanes than this go to the list kernel (a pack warp costs about as much per variable as 10-13 list lanes)
+constexpr int kPackLanes = 32; // instances per pack at most
+
+// Byte offsets of the sections of a pack item's table blob (every section
+// 16-byte aligned): a 16-byte header (reserved); patterns (ItemPat); per
+// pattern -Gamma_Lambda (complex T); per category the multiplicity (T, as in
+// the list blobs); per variable the warp updates a uint4 record; then per
+// term the target (instance-relative variable, u32), then per term the
+// coefficient slot (u16), the variables' terms one after another.
+// The records come in three phases -- the P, T and S variables, then the X
+// and Y variables, then the Z variables, each in canonical order (the
+// physical representative left out in SA_FP32_AUX mode) -- so that the
+// grouped sums a phase reads are complete: every variable adds its own value,
+// weighted, to the sums it enters (P_q, T_q and S_{q,b} to R_q and C of their
+// column category, Eqs. grouped-row-sum, grouped-column-sum; X_q and Y_q to
+// the Z sum of Eq. HZ).  A record:
+//   x: operand codes a (bits 0-10) and b (11-21) of the commutator term
+//      -i g (op[a] - op[b]), diagonal class (22-24: 0 S T, 1 X, 2 Y, 3 Z,
+//      4 P) and pattern (25-29);
+//   y: item-local index (bits 0-9), first term (10-25), number of terms (26-31);
+//   z, w: two contributions, each a sum slot (bits 0-10), a weight kind
+//      (11-13: 0 none, 1 one, 2 M_c, 3 M_c - 1, 4 -M_c) and the category c
+//      of that multiplicity (14-23).
+// Operand codes and sum slots: below nv an item variable; nv + c (slot c)
+// the row sum R of category c, nv + ncat + c its column sum C,
+// nv + 2 ncat + j the Z sum of pattern j, nv + 2 ncat + np zero.  The sums
+// live in the warp's shared memory, one column per lane.
+struct PackLayout {
+    uint32_t pat, pd, cM, vrec, tgt, tsl, bytes;
+};
+template <typename T>
+SA_HOST_DEVICE inline PackLayout pack_layout(uint32_t np, uint32_t ncat, uint32_t nl, uint32_t nterm) {
+    auto a16 = [](uint32_t b) { return (b + 15u) & ~15u; };
+    PackLayout L;
+    L.pat = 16;
+    L.pd = L.pat + a16(np * uint32_t(sizeof(ItemPat)));
+    L.cM = L.pd + a16(np * uint32_t(2 * sizeof(T)));
+    L.vrec = L.cM + a16(ncat * uint32_t(sizeof(T)));
+    L.tgt = L.vrec + nl * 16u;
+    L.tsl = L.tgt + a16(nterm * 4u);
+    L.bytes = L.tsl + a16(nterm * 2u);
+    return L;
+}
+// grouped sums of a pack item in the warp's shared memory: R and C per
+// category, Z per pattern and a zero, one complex T per lane each
+template <typename T> SA_HOST_DEVICE inline uint32_t pack_sums_bytes(uint32_t np, uint32_t ncat) {
+    return (2u * ncat + np + 1u) * 32u * uint32_t(2 * sizeof(T));
+}
+// pack items are cut so that their blob and sums stay below this many bytes
+// (a pattern that alone exceeds it gets an item of its own)
+template <typename T> constexpr uint32_t kPackItemTarget = sizeof(T) == 8 ? 12288u : 6144u;
+constexpr uint32_t kPackUnit = 0x80000000u;  // work-unit flag: (pack item, pack) rather than (item, instance)
+
 // List and ELL kernels: the coefficient table of one instance, compact so
 // that a warp's coefficient loads stay in a few cache lines.  Slot 0 is zero
 // (padded entries); then, for each channel k, occupation n = 0..L before the
@@ -224,6 +288,10 @@ struct LaunchCfg {
     int use_queue;  // 1: persistent grid + atomic work queue
     int grid;       // CTAs
     int kernel;     // SA_KERNEL_RECORDS, SA_KERNEL_LISTS or SA_KERNEL_ELL (include/sa_heom.h)
+    int pack_smem;  // pack kernel: shared-memory bytes of a warp (0: no packs)
+    int pack_blob;  // pack kernel: offset of the blob in a warp's shared memory (after mbarrier, diagonal parts, sums)
+    int pgrid;      // pack kernel: CTAs (persistent)
+    int side_list;  // 1: the list kernel runs on the side stream, beside the pack kernel
 };
 struct StageLaunch {
     const void* hdr; const void* cat_word; const void* cat_M; const void* gamma; const void* rec;
@@ -234,6 +302,8 @@ struct StageLaunch {
     const void* lvd; const void* lvj; const void* rbase; const void* tidx; const void* tcid; const void* lcoef;
     const void* wpat; uint32_t nvar; const void* blobs;
     const void* units; const void* instk;  // list kernel: work units (template item, instance), InstK<T>
+    const void* packs; const void* pk_inst; const void* pcoef;  // pack kernel: PackDev, lane instances, pack coefficients
+    const void* punits; uint32_t npunits; unsigned int* pqueue;  // pack kernel: its work units and counter
     const void* catpat; uint32_t ncat, npat; void* sums;
     uint32_t nchunks;
     const void* x_in; void* x_out; const void* y; void* acc; void* y_out;

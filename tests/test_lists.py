@@ -21,6 +21,7 @@ import paper_2608_20657_b300 as S
 import workloads as W
 
 ZERO_SLOT = 0
+PACK_UNIT = 0x80000000
 
 
 def _generic_bath(m, seed):
@@ -78,7 +79,9 @@ def _eval_lists(lib, sas, baths, x, insts):
     coefs = [_slot_coefficients(b, sa.L) for b, sa in zip(baths, sas)]
     covered = np.zeros(x.size, np.int64)
     for c, inst in L["units"]:
-        p0, np_, v0, nv, c0, ncat, r0, nl = (int(v) for v in L["items"][c])
+        if int(c) & PACK_UNIT:  # pack units: tests/test_packs.py
+            continue
+        p0, np_, v0, nv, c0, ncat, r0, nl = (int(v) for v in L["items"][c][:8])
         inst = int(inst)
         P, vb, cf = pats[inst], voff[inst], coefs[inst]
         op = np.zeros(ZZ + 1, complex)
