@@ -512,11 +512,13 @@ int sa_heom_observables(sa_heom* h, const void* d_state, double* out, void* stre
  * chunk: variables per warp work item (>= largest pattern, <= 1024, multiple
  * of 32); queue: 1 for the dynamic work queue over a persistent grid, 0 for
  * one work item per warp.  Any argument
- * <= 0 keeps its current value.  sa_heom_autotune times every variant,
- * block size (128, 256), item size (64 .. 256) and queue mode on d_state
- * (which it leaves changed) over four RK4 steps, times the four fastest again
- * over twelve and keeps the best; best[3] receives block, chunk, queue
- * (sa_heom_get_tuning also reports the kernel variant it chose).
+ * <= 0 keeps its current value.  sa_heom_autotune times every variant
+ * (the list kernel only on a packed handle), block size (128, 256), item
+ * size (64 .. 256) and queue mode on d_state (which it leaves changed) over
+ * four RK4 steps replayed as the CUDA graph sa_heom_propagate uses, times
+ * the four fastest again over twelve and keeps the best; best[3] receives
+ * block, chunk, queue (sa_heom_get_tuning also reports the kernel variant it
+ * chose).
  */
 int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue);
 int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best);

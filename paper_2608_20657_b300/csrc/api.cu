@@ -2425,16 +2425,14 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     // ms per RK4 step of the current tuning: two warm-up steps, then `reps`
+    // (through the CUDA graph of `reps` steps that sa_heom_propagate replays:
+    // the first run builds and warms it, the second is timed)
     auto time_steps = [&](int reps, float* ms) -> int {
-        for (int rep = 0; rep < 2; ++rep) {
-            const int r = sa_heom_step(h, d_state, 0.0, st);
-            if (r) return r;
-        }
+        int r = run_steps(h, d_state, 0.0, reps, st);
+        if (r) return r;
         CK(cudaEventRecord(e0, st));
-        for (int rep = 0; rep < reps; ++rep) {
-            const int r = sa_heom_step(h, d_state, 0.0, st);
-            if (r) return r;
-        }
+        r = run_steps(h, d_state, 0.0, reps, st);
+        if (r) return r;
         CK(cudaEventRecord(e1, st));
         CK(cudaEventSynchronize(e1));
         CK(cudaEventElapsedTime(ms, e0, e1));
