@@ -1230,21 +1230,12 @@ int apply_tuning(sa_heom* h) {
     h->cfg.grid = persistent ? int(std::min<int64_t>(int64_t(h->num_sms) * occ, blocks_needed)) : int(blocks_needed);
     if (h->cfg.grid < 1) h->cfg.grid = 1;
     h->cfg.pgrid = 0;
-    h->cfg.side_list = 0;
     if (h->kernel == SA_KERNEL_LISTS && h->n_pack_units) {
         int pocc = 0;
         CK(pack_occupancy(h->cfg, h->precision == SA_FP64, &pocc));
         if (pocc < 1) return fail(SA_ERR_UNSUPPORTED, "pack kernel does not fit on an SM with this tuning (shared memory)");
         const int64_t need = (int64_t(h->n_pack_units) + wpb - 1) / wpb;
-        int per_sm = pocc;
-        if (h->n_list_units && h->side && pocc > 1) {
-            // the unpacked instances' list kernel beside it on the side
-            // stream: one CTA per SM for it, the rest for the pack kernel
-            h->cfg.side_list = 1;
-            h->cfg.grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(h->num_sms), blocks_needed)));
-            per_sm = pocc - 1;
-        }
-        h->cfg.pgrid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(h->num_sms) * per_sm, need)));
+        h->cfg.pgrid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(h->num_sms) * pocc, need)));
     }
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
@@ -1665,7 +1656,7 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     }
     if (!rc) {
         e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
-        if (e == cudaSuccess && (precision == SA_FP32_AUX || h->packed)) {
+        if (e == cudaSuccess && precision == SA_FP32_AUX) {
             e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);

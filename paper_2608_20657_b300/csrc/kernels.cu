@@ -1447,26 +1447,23 @@ static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int n
                             const StageLaunch& s) {
     const size_t sm = stage_smem_bytes(cfg, sizeof(T) == 8);
     // the FP64 physical-representative kernel reads the same stage input and
-    // writes other variables: it overlaps the stage kernel on a side stream;
-    // so does the list kernel of a packed handle's unpacked instances, beside
-    // the pack kernel (a few CTAs per SM left to it)
+    // writes other variables: it overlaps the stage kernel on a side stream
     cudaStream_t side = static_cast<cudaStream_t>(s.side_stream);
-    const bool have_side = side && s.ev_fork && s.ev_join;
-    const bool side_list = have_side && cfg.kernel == SA_KERNEL_LISTS && cfg.side_list && p.npunits && p.nchunks;
-    const bool fork = have_side && (SIDE || side_list);
-    if (fork) {
-        cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(s.ev_fork), st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, static_cast<cudaEvent_t>(s.ev_fork), 0);
-        if (e != cudaSuccess) return e;
-    }
+    const bool fork = SIDE && side && s.ev_fork && s.ev_join;
     if (SIDE) {
+        cudaStream_t rs = st;
+        if (fork) {
+            cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(s.ev_fork), st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(side, static_cast<cudaEvent_t>(s.ev_fork), 0);
+            if (e != cudaSuccess) return e;
+            rs = side;
+        }
         const int threads = ninst * kSideSlots;
-        rho0_kernel<T><<<(threads + 127) / 128, 128, 0, fork ? side : st>>>(p, ninst);
-    }
-    if (side_list) list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, side>>>(p);
-    if (fork) {
-        const cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(s.ev_join), side);
-        if (e != cudaSuccess) return e;
+        rho0_kernel<T><<<(threads + 127) / 128, 128, 0, rs>>>(p, ninst);
+        if (fork) {
+            const cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(s.ev_join), side);
+            if (e != cudaSuccess) return e;
+        }
     }
     if (cfg.kernel == SA_KERNEL_ELL) {
         const unsigned gs = unsigned((size_t(p.ncat) + p.npat + 255) / 256);
@@ -1474,8 +1471,10 @@ static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int n
         const unsigned grid = unsigned((size_t(p.nvar) + 31) / 32 * 32 + cfg.block - 1) / unsigned(cfg.block);
         if (grid > 0) ell_stage_kernel<T, SIDE><<<grid, cfg.block, 0, st>>>(p);
     } else if (cfg.kernel == SA_KERNEL_LISTS) {
+        // a packed handle's pack units first, then the list units of its
+        // unpacked instances, each kernel with the whole GPU
         if (p.npunits) pack_stage_kernel<T, SIDE><<<cfg.pgrid, cfg.block, pack_smem_bytes(cfg), st>>>(p);
-        if (p.nchunks && !side_list) list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+        if (p.nchunks) list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
 
     } else {
         stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);

@@ -291,7 +291,6 @@ struct LaunchCfg {
     int pack_smem;  // pack kernel: shared-memory bytes of a warp (0: no packs)
     int pack_blob;  // pack kernel: offset of the blob in a warp's shared memory (after mbarrier, diagonal parts, sums)
     int pgrid;      // pack kernel: CTAs (persistent)
-    int side_list;  // 1: the list kernel runs on the side stream, beside the pack kernel
 };
 struct StageLaunch {
     const void* hdr; const void* cat_word; const void* cat_M; const void* gamma; const void* rec;
