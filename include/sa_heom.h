@@ -524,6 +524,33 @@ int sa_heom_set_tuning(sa_heom* h, int block, int chunk, int queue);
 int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best);
 
 /*
+ * Tuning cache.  sa_heom_autotune first looks its answer up in a process-wide
+ * cache keyed by sa_heom_tuning_key -- the device (name and SM count), the
+ * precision, the layout (packed or not), the largest pattern, the variable
+ * count rounded down to a power of two and the multiset of (m, L, d) of the
+ * instances -- and a hit applies the cached tuning without timing anything;
+ * after timing, the winner is stored under the key.
+ *   sa_heom_autotune_ex      as sa_heom_autotune; flags SA_TUNE_FORCE times
+ *                            afresh and replaces the entry.
+ *   sa_heom_tuning_key       the handle's key (pure host; without the device
+ *                            part for a host-only handle).
+ *   sa_heom_tuning_cache_save / _load   the cache as a text file, one entry
+ *                            per line: key (16 hex digits), block, chunk,
+ *                            queue, kernel.  Loading adds to the cache;
+ *                            INVALID_ARG, and nothing added, for a missing or
+ *                            malformed file.
+ *   sa_heom_tuning_cache_clear, _size   empty it, count its entries.
+ * The cache is shared by the threads of a process (guarded by a mutex).
+ */
+enum { SA_TUNE_FORCE = 1 };
+int sa_heom_autotune_ex(sa_heom* h, void* d_state, void* stream, int flags, int* best);
+int sa_heom_tuning_key(const sa_heom* h, uint64_t* out);
+int sa_heom_tuning_cache_save(const char* path);
+int sa_heom_tuning_cache_load(const char* path);
+int sa_heom_tuning_cache_clear(void);
+int sa_heom_tuning_cache_size(int64_t* out);
+
+/*
  * Stage-kernel variant.  Both evaluate the same right-hand side (Eqs.
  * uvar-up, uvar-down and the commutator of Eq. HS) and fuse the RK4 stage.
  *   SA_KERNEL_RECORDS  each lane walks the connection records of its

@@ -25,6 +25,7 @@ SA_FP64, SA_FP32_AUX = 0, 1
 SA_BUILD_DEVICE, SA_BUILD_HOST_ONLY, SA_BUILD_ADJOINT_REPS, SA_BUILD_PACK_INSTANCES = 0, 1, 2, 4
 SA_KERNEL_RECORDS, SA_KERNEL_LISTS, SA_KERNEL_ELL = 0, 1, 2
 SA_DEBUG_EXPIRE_WAIT, SA_DEBUG_CORRUPT_RECORD = 1, 2
+SA_TUNE_FORCE = 1
 INIT_KINDS = {"cavity": 0, "bright": 1, "up": 2, "lp": 3, "random": 4, "localised": 5, "superposed": 6}
 BATH_HIGH_T, BATH_MATSUBARA, BATH_PADE = 0, 1, 2
 ERRORS = {0: "SA_OK", -1: "SA_ERR_INVALID_ARG", -2: "SA_ERR_UNSUPPORTED", -3: "SA_ERR_OOM",
@@ -104,6 +105,12 @@ def lib() -> ctypes.CDLL:
             "sa_heom_observables": [vp, vp, vp, vp],
             "sa_heom_set_tuning": [vp, i32, i32, i32],
             "sa_heom_autotune": [vp, vp, vp, vp],
+            "sa_heom_autotune_ex": [vp, vp, vp, i32, vp],
+            "sa_heom_tuning_key": [vp, P(ctypes.c_uint64)],
+            "sa_heom_tuning_cache_save": [ctypes.c_char_p],
+            "sa_heom_tuning_cache_load": [ctypes.c_char_p],
+            "sa_heom_tuning_cache_clear": [],
+            "sa_heom_tuning_cache_size": [P(i64)],
             "sa_heom_set_kernel": [vp, i32],
             "sa_heom_dump_lists": [vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
             "sa_heom_dump_ell": [vp, vp, vp, vp, vp, vp, vp],
@@ -154,7 +161,9 @@ def exported_symbols() -> list[str]:
             "sa_heom_dump_terms", "sa_heom_dump_coefficients", "sa_heom_state_bytes", "sa_heom_init_state", "sa_heom_init_physical",
             "sa_heom_state_upload",
             "sa_heom_state_download", "sa_heom_rhs", "sa_heom_step", "sa_heom_propagate", "sa_heom_observables",
-            "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_set_kernel", "sa_heom_get_tuning", "sa_heom_prepare", "sa_heom_dump_lists", "sa_heom_dump_ell",
+            "sa_heom_set_tuning", "sa_heom_autotune", "sa_heom_autotune_ex", "sa_heom_tuning_key",
+            "sa_heom_tuning_cache_save", "sa_heom_tuning_cache_load", "sa_heom_tuning_cache_clear",
+            "sa_heom_tuning_cache_size", "sa_heom_set_kernel", "sa_heom_get_tuning", "sa_heom_prepare", "sa_heom_dump_lists", "sa_heom_dump_ell",
             "sa_heom_launches_per_step", "sa_heom_device_error",
             "sa_heom_observables_noalloc", "sa_heom_initial_vars", "sa_unit_cm_to_rad_fs", "sa_unit_kT_rad_fs",
             "sa_heom_validate", "sa_heom_set_debug", "sa_heom_config_hash",
@@ -242,6 +251,24 @@ def unit_kT_rad_fs(T_K: float) -> float:
     out = ctypes.c_double()
     _check(lib().sa_unit_kT_rad_fs(float(T_K), ctypes.byref(out)), "sa_unit_kT_rad_fs")
     return out.value
+
+
+def tuning_cache_save(path: str):
+    _check(lib().sa_heom_tuning_cache_save(str(path).encode()), "sa_heom_tuning_cache_save")
+
+
+def tuning_cache_load(path: str):
+    _check(lib().sa_heom_tuning_cache_load(str(path).encode()), "sa_heom_tuning_cache_load")
+
+
+def tuning_cache_clear():
+    _check(lib().sa_heom_tuning_cache_clear(), "sa_heom_tuning_cache_clear")
+
+
+def tuning_cache_size() -> int:
+    out = ctypes.c_int64()
+    _check(lib().sa_heom_tuning_cache_size(ctypes.byref(out)), "sa_heom_tuning_cache_size")
+    return int(out.value)
 
 
 def counts(p: Params) -> dict:
@@ -448,10 +475,18 @@ class Heom:
     def set_tuning(self, block=0, chunk=0, queue=-1):
         _check(lib().sa_heom_set_tuning(self._h, int(block), int(chunk), int(queue)), "sa_heom_set_tuning")
 
-    def autotune(self, state, stream=None):
+    def autotune(self, state, stream=None, force: bool = False):
+        """sa_heom_autotune_ex: the cached tuning for this handle's key, or
+        (force, or no entry) every variant timed and the winner cached."""
         best = (ctypes.c_int * 3)()
-        _check(lib().sa_heom_autotune(self._h, _dev(state), _stream(stream), best), "sa_heom_autotune")
+        _check(lib().sa_heom_autotune_ex(self._h, _dev(state), _stream(stream), SA_TUNE_FORCE if force else 0, best),
+               "sa_heom_autotune_ex")
         return tuple(best)
+
+    def tuning_key(self) -> int:
+        out = ctypes.c_uint64()
+        _check(lib().sa_heom_tuning_key(self._h, ctypes.byref(out)), "sa_heom_tuning_key")
+        return int(out.value)
 
     def set_kernel(self, kernel: int):
         """SA_KERNEL_RECORDS or SA_KERNEL_LISTS (rebuilds the launch tables)."""

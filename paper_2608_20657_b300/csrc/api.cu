@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -2397,11 +2399,127 @@ int sa_heom_get_tuning(const sa_heom* h, int* out) {
     return SA_OK;
 }
 
+// ---- tuning cache: key -> (block, chunk, queue, kernel), process-wide
+namespace {
+std::mutex g_tune_mu;
+std::map<uint64_t, std::array<int, 4>> g_tune;
+
+// The cache key of a handle: the device (name and SM count; none for a
+// host-only handle), precision, layout, the largest pattern, the variable
+// count rounded down to a power of two, and the multiset of (m, L, d) of its
+// instances.
+uint64_t tuning_key(const sa_heom* h) {
+    uint64_t x = 0xcbf29ce484222325ull;
+    if (!h->host_only) {
+        cudaDeviceProp prop{};
+        if (cudaGetDeviceProperties(&prop, h->device) == cudaSuccess)
+            x = fnv1a(x, prop.name, std::strlen(prop.name));
+        x = fnv1a(x, &h->num_sms, sizeof(h->num_sms));
+    }
+    const int v[4] = {h->precision, h->packed ? 1 : 0, h->max_u, int(std::floor(std::log2(double(h->nvar))))};
+    x = fnv1a(x, v, sizeof(v));
+    std::map<std::array<int, 3>, int> shapes;
+    for (const HostInstance& hi : h->inst) ++shapes[{hi.m, hi.L, hi.d}];
+    for (const auto& kv : shapes) {
+        x = fnv1a(x, kv.first.data(), sizeof(int) * 3);
+        x = fnv1a(x, &kv.second, sizeof(int));
+    }
+    return x;
+}
+}  // namespace
+
+int sa_heom_tuning_key(const sa_heom* h, uint64_t* out) {
+    if (!h || !out) return fail(SA_ERR_INVALID_ARG, "handle, out");
+    *out = tuning_key(h);
+    return SA_OK;
+}
+
+int sa_heom_tuning_cache_clear(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+    return SA_OK;
+}
+
+int sa_heom_tuning_cache_size(int64_t* out) {
+    if (!out) return fail(SA_ERR_INVALID_ARG, "out");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    *out = int64_t(g_tune.size());
+    return SA_OK;
+}
+
+int sa_heom_tuning_cache_save(const char* path) {
+    if (!path) return fail(SA_ERR_INVALID_ARG, "path");
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    FILE* f = std::fopen(path, "w");
+    if (!f) return fail(SA_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    for (const auto& kv : g_tune)
+        std::fprintf(f, "%016llx %d %d %d %d\n", static_cast<unsigned long long>(kv.first), kv.second[0],
+                     kv.second[1], kv.second[2], kv.second[3]);
+    const bool ok = std::fclose(f) == 0;
+    return ok ? SA_OK : fail(SA_ERR_INVALID_ARG, std::string("cannot write ") + path);
+}
+
+int sa_heom_tuning_cache_load(const char* path) {
+    if (!path) return fail(SA_ERR_INVALID_ARG, "path");
+    FILE* f = std::fopen(path, "r");
+    if (!f) return fail(SA_ERR_INVALID_ARG, std::string("cannot read ") + path);
+    std::map<uint64_t, std::array<int, 4>> got;
+    unsigned long long k = 0;
+    int b = 0, c = 0, q = 0, kern = 0, n = 0;
+    while ((n = std::fscanf(f, "%llx %d %d %d %d", &k, &b, &c, &q, &kern)) == 5) {
+        if (b < 64 || b > 256 || b % 32 || c < 32 || c > kMaxItemVars || c % 32 || (q != 0 && q != 1) ||
+            (kern != SA_KERNEL_RECORDS && kern != SA_KERNEL_LISTS && kern != SA_KERNEL_ELL)) {
+            std::fclose(f);
+            return fail(SA_ERR_INVALID_ARG, std::string("malformed tuning entry in ") + path);
+        }
+        got[uint64_t(k)] = {b, c, q, kern};
+    }
+    const bool eof = n == EOF;
+    std::fclose(f);
+    if (!eof) return fail(SA_ERR_INVALID_ARG, std::string("malformed tuning cache ") + path);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& kv : got) g_tune[kv.first] = kv.second;
+    return SA_OK;
+}
+
 int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
+    return sa_heom_autotune_ex(h, d_state, stream, 0, best);
+}
+
+int sa_heom_autotune_ex(sa_heom* h, void* d_state, void* stream, int flags, int* best) {
     int rc = check_device(h);
     if (rc) return rc;
     if (!d_state) return fail(SA_ERR_INVALID_ARG, "d_state required");
     if (misaligned(d_state)) return fail(SA_ERR_INVALID_ARG, "state buffers must be 16-byte aligned");
+    if (flags & ~SA_TUNE_FORCE) return fail(SA_ERR_INVALID_ARG, "unknown autotune flag");
+    const uint64_t key = tuning_key(h);
+    if (!(flags & SA_TUNE_FORCE)) {
+        std::array<int, 4> t{};
+        bool hit = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) {
+                t = it->second;
+                hit = true;
+            }
+        }
+        if (hit && !(h->packed && t[3] != SA_KERNEL_LISTS)) {
+            const int old = h->kernel;
+            h->kernel = t[3];
+            rc = sa_heom_set_tuning(h, t[0], t[1], t[2]);
+            if (!rc) {
+                if (best) {
+                    best[0] = t[0];
+                    best[1] = t[1];
+                    best[2] = t[2];
+                }
+                return SA_OK;
+            }
+            h->kernel = old;  // the cached tuning does not fit this handle: time afresh
+            apply_tuning(h);
+        }
+    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int blocks[] = {128, 256};
     const int chunks[] = {64, 96, 128, 160, 192, 224, 256};
@@ -2466,6 +2584,10 @@ int sa_heom_autotune(sa_heom* h, void* d_state, void* stream, int* best) {
     h->kernel = w.k;
     rc = sa_heom_set_tuning(h, w.b, w.c, w.q);
     if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = {w.b, w.c, w.q, w.k};
+    }
     if (best) {
         best[0] = w.b;
         best[1] = w.c;
