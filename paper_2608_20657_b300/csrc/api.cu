@@ -547,8 +547,22 @@ int pack_blob(const sa_heom* h, ItemDesc& d, uint8_t* o) {
     ListItem W;
     list_item(h, d, W);
     const bool side64 = h->precision == SA_FP32_AUX;
-    // contribution word: sum slot, weight kind (1 one, 2 M_c, 3 M_c - 1, 4 -M_c), category c
-    auto cw = [](uint32_t slot, uint32_t kind, uint32_t c) { return slot | (kind << 11) | (c << 14); };
+    // contribution word: sum slot and the weight a + b N (kind 1 one, 2 M_c,
+    // 3 M_c - 1, 4 -M_c of item category c; b = 1 or -1 only for the zero
+    // category, whose M_0 = N - r is stored as -r): slot | (b + 1) << 12 |
+    // (a + 32768) << 14
+    const HostInstance& hrw = h->inst[h->hdr[d.p0].inst];
+    const uint32_t cbw = h->hdr[h->instdev[h->hdr[d.p0].inst].pat_begin].cat_off;
+    auto cw = [&](uint32_t slot, uint32_t kind, uint32_t c) {
+        const size_t gc = size_t(d.c0 + c - cbw);
+        const int64_t mt = tmpl_mult(hrw, gc);  // M, or -r for the zero category
+        const int64_t zb = hrw.cat_vec[gc] == 0 ? 1 : 0;
+        int64_t a = 1, b = 0;
+        if (kind == 2) a = mt, b = zb;
+        if (kind == 3) a = mt - 1, b = zb;
+        if (kind == 4) a = -mt, b = -zb;
+        return slot | uint32_t(b + 1) << 12 | uint32_t(a + 32768) << 14;
+    };
     struct Rec {
         uint32_t l, z, w;
     };

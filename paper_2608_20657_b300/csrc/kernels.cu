@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "sa_internal.h"
 
@@ -717,14 +718,9 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
     C* const sl = sums + lane;
     const uint32_t nsums = 2 * ncat + np + 1;
     for (uint32_t k = 0; k < nsums; ++k) sl[k * 32] = mk(T(0), T(0));
-    // weight of a contribution: kind 1 one, 2 M_c, 3 M_c - 1, 4 -M_c (the zero
-    // category's multiplicity is N - r, stored as -r)
-    auto weight = [&](uint32_t w) {
-        const T m = cM[(w >> 14) & 1023u];
-        const T M = m > T(0) ? m : Nt + m;
-        const uint32_t k = (w >> 11) & 7u;
-        return k == 1u ? T(1) : (k == 2u ? M : (k == 3u ? M - T(1) : -M));
-    };
+    // weight of a grouped-sum contribution: a + b N (b = 0 but for the zero
+    // category, whose multiplicity is N - r)
+    auto weight = [&](uint32_t w) { return fma(T(int((w >> 12) & 3u) - 1), Nt, T(int((w >> 14) & 65535u) - 32768)); };
     const C* __restrict__ Yb = P.y + lb;
     C* const Ab = P.acc + lb;
     C* const XO = P.x_out + lb;
@@ -733,15 +729,26 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
     const T dtT = T(P.dt);
     const T aT = stage == 2 ? dtT : T(0.5) * dtT;
     const C z = mk(T(0), T(0));
-    auto opnd = [&](uint32_t code) { return code < nv ? __ldg(X + (iv0 + code * n)) : sl[(code - nv) * 32]; };
-    // loads of variable i: value, operands, y, accumulator, first two terms
-    auto fetch = [&](uint32_t i, C& v, C& oa, C& ob, C& yv, C& av, C& x0, C& c0, C& x1, C& c1) {
+    auto var = [&](uint32_t code) { return __ldg(X + (iv0 + code * n)); };
+    // loads of variable i in phase ph: value, operands (P, T, S: two item
+    // variables; X, Y: the Z variable and a sum; Z: its sum), y, accumulator,
+    // first two terms
+    auto fetch = [&](int ph, uint32_t i, C& v, C& oa, C& ob, C& yv, C& av, C& x0, C& c0, C& x1, C& c1) {
         const uint4 r = vrec[i];
         const uint32_t off = iv0 + (r.y & 1023u) * n;
         const uint32_t u0 = (r.y >> 10) & 65535u, cnt = r.y >> 26;
+        const uint32_t ca = r.x & 2047u, cb = (r.x >> 11) & 2047u;
         v = __ldg(X + off);
-        oa = opnd(r.x & 2047u);
-        ob = opnd((r.x >> 11) & 2047u);
+        if (ph == 0) {
+            oa = var(ca);
+            ob = var(cb);
+        } else if (ph == 1) {
+            oa = ca < nv ? var(ca) : sl[(ca - nv) * 32];
+            ob = cb < nv ? var(cb) : sl[(cb - nv) * 32];
+        } else {
+            oa = sl[(ca - nv) * 32];
+            ob = z;
+        }
         yv = z;
         av = z;
         if (stage > 0) {
@@ -758,12 +765,12 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
             c1 = __ldg(cf + uint32_t(tsl[u0 + 1]) * n);
         }
     };
-    // the rest of variable i: its contributions to the grouped sums, then
-    // diagonal, commutator, terms and the RK4 update
-    auto finish = [&](uint32_t i, C v, C oa, C ob, C yv, C av, C x0, C c0, C x1, C c1) {
+    // the rest of variable i: its contributions to the grouped sums (P, T, S:
+    // two; X, Y: one; Z: none), then diagonal, commutator, terms, RK4 update
+    auto finish = [&](int ph, uint32_t i, C v, C oa, C ob, C yv, C av, C x0, C c0, C x1, C c1) {
         const uint4 r = vrec[i];
-        if (r.z & 0x3800u) sl[(r.z & 2047u) * 32] = caxpy(weight(r.z), v, sl[(r.z & 2047u) * 32]);
-        if (r.w & 0x3800u) sl[(r.w & 2047u) * 32] = caxpy(weight(r.w), v, sl[(r.w & 2047u) * 32]);
+        if (ph < 2) sl[(r.z & 2047u) * 32] = caxpy(weight(r.z), v, sl[(r.z & 2047u) * 32]);
+        if (ph == 0) sl[(r.w & 2047u) * 32] = caxpy(weight(r.w), v, sl[(r.w & 2047u) * 32]);
         const uint32_t off = iv0 + (r.y & 1023u) * n;
         const uint32_t u0 = (r.y >> 10) & 65535u, u1 = u0 + (r.y >> 26);
         const C dgl = cadd(pd[(r.x >> 25) & 31u], ccs[((r.x >> 22) & 7u) * 32 + lane]);
@@ -794,22 +801,22 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
             }
         }
     };
-    // the three phases, each with two register sets in turn: variable i + 1
-    // loads while variable i finishes
+    // the three phases (P, T, S; X, Y; Z), each with two register sets in
+    // turn: variable i + 1 loads while variable i finishes
     const uint32_t ph1 = d.row1 & 65535u, ph2 = ph1 + (d.row1 >> 16);
     uint32_t i0 = 0;
 #pragma unroll 1
-    for (int phase = 0; phase < 3; ++phase) {
-        const uint32_t i1 = phase == 0 ? ph1 : (phase == 1 ? ph2 : nl);
+    for (int ph = 0; ph < 3; ++ph) {
+        const uint32_t i1 = ph == 0 ? ph1 : (ph == 1 ? ph2 : nl);
         C vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1;
         C vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1;
-        if (i0 < i1) fetch(i0, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
+        if (i0 < i1) fetch(ph, i0, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
         for (uint32_t i = i0; i < i1; i += 2) {
-            if (i + 1 < i1) fetch(i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
-            finish(i, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
+            if (i + 1 < i1) fetch(ph, i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
+            finish(ph, i, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
             if (i + 1 >= i1) break;
-            if (i + 2 < i1) fetch(i + 2, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
-            finish(i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
+            if (i + 2 < i1) fetch(ph, i + 2, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
+            finish(ph, i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
         }
         i0 = i1;
     }

@@ -234,9 +234,11 @@ constexpr int kPackLanes = 32; // instances per pack at most
 //      -i g (op[a] - op[b]), diagonal class (22-24: 0 S T, 1 X, 2 Y, 3 Z,
 //      4 P) and pattern (25-29);
 //   y: item-local index (bits 0-9), first term (10-25), number of terms (26-31);
-//   z, w: two contributions, each a sum slot (bits 0-10), a weight kind
-//      (11-13: 0 none, 1 one, 2 M_c, 3 M_c - 1, 4 -M_c) and the category c
-//      of that multiplicity (14-23).
+//   z, w: the contributions (two for P, T, S; one, in z, for X and Y; none
+//      for Z), each a sum slot (bits 0-10) and its weight a + b N (bits
+//      12-13: b + 1; bits 14-29: a + 32768), N the instance's molecule count:
+//      1 for P_q, M_q - 1 for T_q, M_b and M_q for S_{q,b}, M_q and -M_q for
+//      X_q and Y_q, where M of the zero category is N - r (b = 1).
 // Operand codes and sum slots: below nv an item variable; nv + c (slot c)
 // the row sum R of category c, nv + ncat + c its column sum C,
 // nv + 2 ncat + j the Z sum of pattern j, nv + 2 ncat + np zero.  The sums

@@ -158,14 +158,11 @@ def _eval_packs(h, specs, sas, x, out, precision):
             for idx, (w, w1, wz, ww) in enumerate(vrec):
                 w, l, u0, cnt = int(w), int(w1) & 1023, (int(w1) >> 10) & 65535, int(w1) >> 26
                 a, bo, cls, jj = w & 2047, (w >> 11) & 2047, (w >> 22) & 7, (w >> 25) & 31
-                for con in (int(wz), int(ww)):
-                    kind = (con >> 11) & 7
-                    if kind:
-                        slot, cc = con & 2047, (con >> 14) & 1023
-                        M = Mall[cc]
-                        wgt = {1: 1.0, 2: M, 3: M - 1, 4: -M}[kind]
-                        sums[slot] += wgt * xi[l]
-                        done[slot] = max(done[slot], phase[idx])
+                ncon = (2, 1, 0)[phase[idx]]  # P, T, S enter two sums, X and Y one, Z none
+                for con in (int(wz), int(ww))[:ncon]:
+                    slot, bb, aa = con & 2047, ((con >> 12) & 3) - 1, ((con >> 14) & 65535) - 32768
+                    sums[slot] += (aa + bb * N) * xi[l]
+                    done[slot] = max(done[slot], phase[idx])
                 for opc in (a, bo):
                     if opc >= nv:  # a sum read: written only in an earlier phase
                         assert done[opc - nv] < phase[idx] or opc - nv == nslot
