@@ -112,14 +112,18 @@ class Clocks:
 
 _PHYS_BEGIN = "// -- begin: physical-representative kernels (outside the stage kernels' code)\n"
 _PHYS_END = "// -- end: physical-representative kernels\n"
+_PACK_BEGIN = "// -- begin: pack kernel (the opt-in packed layout; no list-kernel code)\n"
+_PACK_END = "// -- end: pack kernel\n"
 
 
 def _stage_sha() -> str:
     """Hash of the stage kernels' source: kernels.cu less its marked
     physical-representative sections (the FP64 rho_0, observables and init
-    kernels and their launch wrappers), which no stage kernel calls."""
+    kernels and their launch wrappers) and its pack-kernel section, which no
+    other stage kernel calls."""
     src = open(os.path.join(ROOT, "paper_2608_20657_b300", "csrc", "kernels.cu"), encoding="utf-8").read()
-    src = re.sub(re.escape(_PHYS_BEGIN) + ".*?" + re.escape(_PHYS_END), "", src, flags=re.S)
+    for b, e in ((_PHYS_BEGIN, _PHYS_END), (_PACK_BEGIN, _PACK_END)):
+        src = re.sub(re.escape(b) + ".*?" + re.escape(e), "", src, flags=re.S)
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
@@ -565,6 +569,9 @@ def main():
     ap.add_argument("--conv-scaling", action="store_true",
                     help="time the conventional against the symmetry-adapted hierarchy over --conv-n, then exit")
     ap.add_argument("--conv-n", default="2,4,6,8,10,12")
+    ap.add_argument("--reconstruct-only", action="store_true",
+                    help="time only the dense reconstruction of arbitrary initial operators (N + 1 = 8192; "
+                         "--steps calls), then exit")
     ap.add_argument("--tune", default="", help="block,chunk,queue[,kernel] (skips the autotuner; kernel 0 = "
                                                 "connection records, 1 = term lists)")
     ap.add_argument("--layout", default="canonical", choices=["packed", "canonical"],
@@ -575,6 +582,13 @@ def main():
         args.warmup = 3
     if args.conv_scaling:
         return run_conv_scaling(args)
+    if args.reconstruct_only:
+        import torch
+
+        import paper_2608_20657_b300 as S
+
+        print(json.dumps({"reconstruct": _time_reconstruct(S, torch, torch.cuda.current_stream(), reps=args.steps)}))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -30,7 +30,6 @@
 
 #include <algorithm>
 #include <cstdint>
-#include <type_traits>
 
 #include "sa_internal.h"
 
@@ -648,6 +647,7 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
     return W;
 }
 
+// -- begin: pack kernel (the opt-in packed layout; no list-kernel code)
 // One pack unit: a pack item evaluated for the n <= 32 instances of a pack,
 // lane j taking the pack's instance j (lanes j >= n shadow lane 0 and store
 // nothing).  The pack's state is interleaved, so every access of the warp --
@@ -849,6 +849,8 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 128 : 80) pack_stage_kernel(StagePa
         if (!pack_unit<T, FP64SIDE>(P, P.items[un.x & ~kPackUnit], un.y, wsm, bar, parity, lane)) return;
     }
 }
+
+// -- end: pack kernel
 
 // One warp per work item, like stage_kernel, but
 //  * the item's stage-input slice and its table blob (instance constants,
