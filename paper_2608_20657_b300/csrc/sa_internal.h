@@ -163,15 +163,15 @@ template <typename T> struct PatConst {
     T term;              // terminator strength Delta
 };
 
-// A pattern as the list kernel's blob gives it (8 bytes): its first variable
-// and first category relative to the work item's, G, tier and the slot of its
-// instance among the item's instances.
+// A pattern as the list and pack kernels' blobs give it (8 bytes): its first
+// variable and first category relative to the work item's, G, tier, and a
+// reserved zero (a template item belongs to one instance at a time).
 struct ItemPat {
     uint16_t var_rel, cat_rel;
     uint8_t G, tier;
     uint16_t islot;
 };
-constexpr int kItemInsts = 4;  // instances per work item
+constexpr int kItemInsts = 4;  // record kernel: instances per work item
 
 // Byte offsets of the sections of a list-kernel item blob (every section
 // 16-byte aligned): a 16-byte header (reserved), patterns (ItemPat), per pattern
