@@ -589,8 +589,10 @@ int sa_heom_launches_per_step(const sa_heom* h);
 /*
  * sa_heom_device_error -- read the kernels' device error word (synchronises
  * `stream`).  Returns SA_ERR_TIMEOUT if a stage kernel gave up a bounded
- * wait on its bulk copies, SA_OK otherwise.  sa_heom_propagate with
- * observables checks it too.  Reading the word clears it.  After
+ * wait on its bulk copies, SA_ERR_STATE if a stage kernel checking its table
+ * indices (SA_DEBUG_CHECK_INDICES) found one out of range, SA_OK otherwise.
+ * sa_heom_propagate with observables checks it too.  Reading the word clears
+ * it.  After
  * SA_ERR_TIMEOUT the outputs of the affected launches, and so the caller's
  * state buffer, are undefined, and unless the expiry was injected
  * (SA_DEBUG_EXPIRE_WAIT) a copy the kernel gave up on may still land in
@@ -648,14 +650,26 @@ int sa_heom_checkpoint_load(const sa_heom* h, const void* host_buf, size_t bytes
  *                      (host-only handles; STATE otherwise) moves the target
  *                      of instance 0's first connection record off its
  *                      pattern, for which sa_heom_validate must fail; it
- *                      cannot be undone.  Other bits: INVALID_ARG.
+ *                      cannot be undone.  SA_DEBUG_CHECK_INDICES: the list
+ *                      and pack kernels check every hierarchy-term target
+ *                      and coefficient slot they read from their tables
+ *                      against the instance's variable and slot counts; an
+ *                      index out of range is replaced by 0 (no access outside
+ *                      the buffers) and sets the device error word, which
+ *                      sa_heom_device_error reports as SA_ERR_STATE; the
+ *                      launch's outputs are then wrong.  SA_DEBUG_CORRUPT_LIST
+ *                      (device handles running the list kernel, and only
+ *                      together with SA_DEBUG_CHECK_INDICES; INVALID_ARG
+ *                      otherwise) rebuilds the term lists with one target of
+ *                      the first term row out of range, for that check to
+ *                      find; turning it off rebuilds them correct.  Other
+ *                      bits: INVALID_ARG.
  */
-enum { SA_DEBUG_EXPIRE_WAIT = 1, SA_DEBUG_CORRUPT_RECORD = 2 };
+enum { SA_DEBUG_EXPIRE_WAIT = 1, SA_DEBUG_CORRUPT_RECORD = 2, SA_DEBUG_CHECK_INDICES = 4, SA_DEBUG_CORRUPT_LIST = 8 };
 int sa_heom_validate(const sa_heom* h);
 int sa_heom_set_debug(sa_heom* h, int flags);
 
 /*
- * sa_heom_observables_noalloc/*
  * sa_heom_observables_noalloc -- the same observables as sa_heom_observables
  * (same kernel, same out[8 * i ..] layout), for callers that may not call
  * cudaMalloc.  The paper has no counterpart to this entry point.

@@ -24,7 +24,7 @@ NOALLOC_MAX_INSTANCES = 4096  # SA_HEOM_NOALLOC_MAX_INSTANCES
 SA_FP64, SA_FP32_AUX = 0, 1
 SA_BUILD_DEVICE, SA_BUILD_HOST_ONLY, SA_BUILD_ADJOINT_REPS, SA_BUILD_PACK_INSTANCES = 0, 1, 2, 4
 SA_KERNEL_RECORDS, SA_KERNEL_LISTS, SA_KERNEL_ELL = 0, 1, 2
-SA_DEBUG_EXPIRE_WAIT, SA_DEBUG_CORRUPT_RECORD = 1, 2
+SA_DEBUG_EXPIRE_WAIT, SA_DEBUG_CORRUPT_RECORD, SA_DEBUG_CHECK_INDICES, SA_DEBUG_CORRUPT_LIST = 1, 2, 4, 8
 SA_TUNE_FORCE = 1
 INIT_KINDS = {"cavity": 0, "bright": 1, "up": 2, "lp": 3, "random": 4, "localised": 5, "superposed": 6}
 BATH_HIGH_T, BATH_MATSUBARA, BATH_PADE = 0, 1, 2

@@ -132,6 +132,8 @@ struct sa_heom {
     void* d_pkinst = nullptr;
     void* d_pcoef = nullptr;
     void* d_punits = nullptr;          // the pack units of `units`, in order (the list units go to d_units)
+    void* d_ilimit = nullptr;          // per instance: variables and list coefficient slots (index checks)
+    bool corrupt_list = false;         // SA_DEBUG_CORRUPT_LIST: the term lists carry one bad target
     uint32_t n_list_units = 0, n_pack_units = 0;
     std::vector<uint8_t> blobs;        // SA_KERNEL_LISTS: per-item table blobs
     int tables = -1;              // variant whose term tables are current (-1: none)
@@ -893,6 +895,17 @@ int build_lists(sa_heom* h) {
             }
         }
     }
+    if (h->corrupt_list) {
+        // SA_DEBUG_CORRUPT_LIST: the first real entry of the first term row
+        // names a target beyond every instance
+        bool done = false;
+        for (size_t e = 0; e < h->tcid.size() && !done; ++e)
+            if (h->tcid[e] != uint16_t(kListCoefZero)) {
+                h->tidx[e] = 0x7fffffffu;
+                done = true;
+            }
+        if (!done) return fail(SA_ERR_STATE, "SA_DEBUG_CORRUPT_LIST: no term row to corrupt");
+    }
     const int rc = h->precision == SA_FP64 ? build_blobs<double>(h) : build_blobs<float>(h);
     if (rc) return rc;
     // template items relative to their instance; work units: a template's
@@ -1266,7 +1279,8 @@ void free_device(sa_heom* h) {
                     h->d_chunk, h->d_work[0], h->d_work[1], h->d_work[2], h->d_queue, h->d_obs, h->d_rho0,
                     h->d_err, h->d_vdesc, h->d_drecA, h->d_drecS, h->d_lvd, h->d_lvj, h->d_rbase,
                     h->d_tidx, h->d_tcid, h->d_lcoef, h->d_wpat, h->d_blobs, h->d_catpat, h->d_sums,
-                    h->d_rep_loc, h->d_recon_ws, h->d_units, h->d_instk, h->d_packs, h->d_pkinst, h->d_pcoef};
+                    h->d_rep_loc, h->d_recon_ws, h->d_units, h->d_instk, h->d_packs, h->d_pkinst, h->d_pcoef,
+                    h->d_ilimit};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -1323,6 +1337,7 @@ StageLaunch base_launch(const sa_heom* h) {
     s.npunits = h->kernel == SA_KERNEL_LISTS ? h->n_pack_units : 0u;
     s.units = h->d_units;
     s.instk = h->d_instk;
+    s.ilimit = h->d_ilimit;
     s.packs = h->d_packs;
     s.pk_inst = h->d_pkinst;
     s.pcoef = h->d_pcoef;
@@ -1379,7 +1394,8 @@ int enqueue_step(sa_heom* h, void* y, double dt, size_t slot, cudaStream_t st) {
     return SA_OK;
 }
 
-// the kernels' error word: bit 0 = a bounded wait on a bulk copy expired;
+// the kernels' error word: bit 0 = a bounded wait on a bulk copy expired,
+// bit 1 = a table index out of range (SA_DEBUG_CHECK_INDICES);
 // reading it clears it
 int read_device_error(sa_heom* h, cudaStream_t st) {
     unsigned int w = 0;
@@ -1388,7 +1404,8 @@ int read_device_error(sa_heom* h, cudaStream_t st) {
     if (w) {
         CK(cudaMemsetAsync(h->d_err, 0, sizeof(w), st));
         CK(cudaStreamSynchronize(st));
-        return fail(SA_ERR_TIMEOUT, "a bounded device wait expired in the stage kernel");
+        if (w & 1u) return fail(SA_ERR_TIMEOUT, "a bounded device wait expired in the stage kernel");
+        return fail(SA_ERR_STATE, "a stage kernel found a table index out of range (SA_DEBUG_CHECK_INDICES)");
     }
     return SA_OK;
 }
@@ -1651,6 +1668,14 @@ int sa_heom_build(const sa_params* params, int count, int precision, int flags, 
     if (!rc) rc = upload(&h->d_drecA, h->drecA);
     if (!rc) rc = upload(&h->d_drecS, h->drecS);
     if (!rc) rc = upload(&h->d_lut_off, h->lut_off);
+    if (!rc) {
+        std::vector<uint32_t> lim(size_t(2) * count);
+        for (int i = 0; i < count; ++i) {
+            lim[size_t(2) * i] = uint32_t(h->var_begin[size_t(i) + 1] - h->var_begin[size_t(i)]);
+            lim[size_t(2) * i + 1] = uint32_t(list_slots(h->inst[i].m, h->inst[i].L));
+        }
+        rc = upload(&h->d_ilimit, lim);
+    }
     for (int w = 0; w < 3 && !rc; ++w) {
         e = cudaMalloc(&h->d_work[w], h->state_bytes);
         if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? fail(SA_ERR_OOM, "RK4 work buffers")
@@ -2623,20 +2648,33 @@ int sa_heom_launches_per_step(const sa_heom* h) {
 
 int sa_heom_set_debug(sa_heom* h, int flags) {
     if (!h) return fail(SA_ERR_INVALID_ARG, "null handle");
-    if (flags & ~(SA_DEBUG_EXPIRE_WAIT | SA_DEBUG_CORRUPT_RECORD)) return fail(SA_ERR_INVALID_ARG, "unknown flag");
+    if (flags & ~(SA_DEBUG_EXPIRE_WAIT | SA_DEBUG_CORRUPT_RECORD | SA_DEBUG_CHECK_INDICES | SA_DEBUG_CORRUPT_LIST))
+        return fail(SA_ERR_INVALID_ARG, "unknown flag");
+    if ((flags & SA_DEBUG_CORRUPT_LIST) &&
+        (!(flags & SA_DEBUG_CHECK_INDICES) || h->host_only || h->kernel != SA_KERNEL_LISTS))
+        return fail(SA_ERR_INVALID_ARG,
+                    "SA_DEBUG_CORRUPT_LIST needs SA_DEBUG_CHECK_INDICES on a device handle running the list kernel");
     if (flags & SA_DEBUG_CORRUPT_RECORD) {
         if (!h->host_only) return fail(SA_ERR_STATE, "SA_DEBUG_CORRUPT_RECORD needs a host-only handle");
         HostInstance& hi = h->inst[0];
         if (hi.rec.empty()) return fail(SA_ERR_STATE, "instance 0 has no connection record");
         hi.rec[0].target += 1;  // no longer the first variable of a pattern
     }
-    const int expire = flags & SA_DEBUG_EXPIRE_WAIT;
-    if (expire != (h->debug & SA_DEBUG_EXPIRE_WAIT)) {
-        // the step graphs hold the kernels' parameters: rebuild them
+    const int kept = flags & (SA_DEBUG_EXPIRE_WAIT | SA_DEBUG_CHECK_INDICES | SA_DEBUG_CORRUPT_LIST);
+    if (kept != h->debug) {
+        // the step graphs hold the kernels and their parameters: rebuild them
         for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
         h->graphs.clear();
     }
-    h->debug = expire;
+    const bool corrupt = (flags & SA_DEBUG_CORRUPT_LIST) != 0;
+    h->debug = kept;
+    if (corrupt != h->corrupt_list) {
+        // rebuild the term lists with (or, again, without) the bad target
+        h->corrupt_list = corrupt;
+        h->tables = -1;
+        const int rc = apply_tuning(h);
+        if (rc) return rc;
+    }
     return SA_OK;
 }
 

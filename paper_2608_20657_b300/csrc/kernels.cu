@@ -124,6 +124,7 @@ template <typename T> struct StageParams {
     unsigned int* queue;
     unsigned int* err;                      // device error word (bit 0: a bounded wait expired)
     int expire_wait;                        // SA_DEBUG_EXPIRE_WAIT: report the first bulk-copy wait as expired
+    const uint2* __restrict__ ilimit;       // SA_DEBUG_CHECK_INDICES: per instance its variables and list slots
 };
 
 enum { KZ = 0, KX = 1, KY = 2, KP = 3, KS = 4, KT = 5 };
@@ -667,7 +668,7 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
 //    variables' memory latencies overlap.
 // Returns false when the bounded wait for the tables expired (error bit set,
 // the copy drained).
-template <typename T, bool FP64SIDE>
+template <typename T, bool FP64SIDE, bool CHECK>
 __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDesc& d, uint32_t pkid,
                                           unsigned char* wsm, uint64_t* bar, uint32_t& parity, int lane) {
     using C = typename Cx<T>::t;
@@ -706,9 +707,30 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
     const C* const pd = reinterpret_cast<const C*>(blob + B.pd);
     const T* const cM = reinterpret_cast<const T*>(blob + B.cM);
     const uint4* const vrec = reinterpret_cast<const uint4*>(blob + B.vrec);
-    const uint32_t* const tgt = reinterpret_cast<const uint32_t*>(blob + B.tgt);
-    const uint16_t* const tsl = reinterpret_cast<const uint16_t*>(blob + B.tsl);
+    const uint32_t* const tgt0 = reinterpret_cast<const uint32_t*>(blob + B.tgt);
+    const uint16_t* const tsl0 = reinterpret_cast<const uint16_t*>(blob + B.tsl);
     (void)ph;
+    // SA_DEBUG_CHECK_INDICES: a target or slot out of the template's range
+    // reads index 0 instead and raises bit 1 of the error word
+    uint2 lim = make_uint2(0u, 0u);
+    if (CHECK) lim = P.ilimit[P.pk_inst[pk.lane0]];
+    bool bad = false;
+    auto tgtat = [&](uint32_t u) {
+        const uint32_t v = tgt0[u];
+        if (CHECK && v >= lim.x) {
+            bad = true;
+            return 0u;
+        }
+        return v;
+    };
+    auto tslat = [&](uint32_t u) {
+        const uint32_t v = tsl0[u];
+        if (CHECK && v >= lim.y) {
+            bad = true;
+            return 0u;
+        }
+        return v;
+    };
     // lane base pointers; element offsets from them are 32-bit
     const size_t lb = size_t(pk.base) + ll;
     const C* __restrict__ X = P.x_in + lb;
@@ -757,12 +779,12 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
         }
         x0 = c0 = x1 = c1 = z;
         if (cnt > 0) {
-            x0 = __ldg(X + tgt[u0] * n);
-            c0 = __ldg(cf + uint32_t(tsl[u0]) * n);
+            x0 = __ldg(X + tgtat(u0) * n);
+            c0 = __ldg(cf + tslat(u0) * n);
         }
         if (cnt > 1) {
-            x1 = __ldg(X + tgt[u0 + 1] * n);
-            c1 = __ldg(cf + uint32_t(tsl[u0 + 1]) * n);
+            x1 = __ldg(X + tgtat(u0 + 1) * n);
+            c1 = __ldg(cf + tslat(u0 + 1) * n);
         }
     };
     // the rest of variable i: its contributions to the grouped sums (P, T, S:
@@ -781,12 +803,12 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
         dv = cfma(c1, x1, dv);
         uint32_t u = u0 + 2;
         for (; u + 2 <= u1; u += 2) {
-            const C xa = __ldg(X + tgt[u] * n), ca = __ldg(cf + uint32_t(tsl[u]) * n);
-            const C xb = __ldg(X + tgt[u + 1] * n), cb = __ldg(cf + uint32_t(tsl[u + 1]) * n);
+            const C xa = __ldg(X + tgtat(u) * n), ca = __ldg(cf + tslat(u) * n);
+            const C xb = __ldg(X + tgtat(u + 1) * n), cb = __ldg(cf + tslat(u + 1) * n);
             dv = cfma(ca, xa, dv);
             dv = cfma(cb, xb, dv);
         }
-        if (u < u1) dv = cfma(__ldg(cf + uint32_t(tsl[u]) * n), __ldg(X + tgt[u] * n), dv);
+        if (u < u1) dv = cfma(__ldg(cf + tslat(u) * n), __ldg(X + tgtat(u) * n), dv);
         if (act) {
             if (stage < 0) {
                 XO[off] = dv;
@@ -820,6 +842,7 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
         }
         i0 = i1;
     }
+    if (CHECK && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.err, 2u);
     __syncwarp();
     return true;
 }
@@ -827,7 +850,7 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
 // The pack kernel: persistent warps drawing pack units (static striding or
 // the atomic counter), each warp with an mbarrier and a blob buffer of
 // pack_smem bytes.  Registers are budgeted apart from the list kernel's.
-template <typename T, bool FP64SIDE>
+template <typename T, bool FP64SIDE, bool CHECK>
 __global__ void __maxnreg__(sizeof(T) == 8 ? 128 : 80) pack_stage_kernel(StageParams<T> P) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -846,7 +869,7 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 128 : 80) pack_stage_kernel(StagePa
         const unsigned int c = Q.next(P.pqueue, P.npunits, lane);
         if (c >= P.npunits) break;
         const uint2 un = P.punits[c];
-        if (!pack_unit<T, FP64SIDE>(P, P.items[un.x & ~kPackUnit], un.y, wsm, bar, parity, lane)) return;
+        if (!pack_unit<T, FP64SIDE, CHECK>(P, P.items[un.x & ~kPackUnit], un.y, wsm, bar, parity, lane)) return;
     }
 }
 
@@ -871,7 +894,7 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 128 : 80) pack_stage_kernel(StagePa
 // waits (bounded again) for its copies and stops.
 // (a register budget instead of launch bounds: ptxas otherwise trades a few
 // spills for 32 resident warps, which measured slower)
-template <typename T, bool FP64SIDE>
+template <typename T, bool FP64SIDE, bool CHECK>
 __global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StageParams<T> P) {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -994,6 +1017,25 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StagePa
         // round's gathers wait on one memory latency instead of two.
         const C* __restrict__ X = P.x_in + vbase;  // targets are instance-relative
         const C* __restrict__ cf = P.lcoef + ik->lcoef_base;
+        // SA_DEBUG_CHECK_INDICES: a target or slot out of the instance's range
+        // reads index 0 instead and raises bit 1 of the error word
+        uint2 lim = make_uint2(0u, 0u);
+        if (CHECK) lim = P.ilimit[un.y];
+        bool bad = false;
+        auto ckx = [&](uint32_t v) {
+            if (CHECK && v >= lim.x) {
+                bad = true;
+                return 0u;
+            }
+            return v;
+        };
+        auto ckc = [&](uint32_t v) {
+            if (CHECK && v >= lim.y) {
+                bad = true;
+                return 0u;
+            }
+            return v;
+        };
         const C* const dg = S.diag;
         const T g = ik->g;
         const uint32_t* const lvd = reinterpret_cast<const uint32_t*>(S.blob + B.lvd);
@@ -1008,8 +1050,8 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StagePa
             const uint16_t* __restrict__ tc = P.tcid + size_t(r0) * 32 + lane;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                nix[u] = uint32_t(u) < nt ? __ldcg(ti + u * 32) : d.v0;
-                ncx[u] = uint32_t(u) < nt ? uint32_t(__ldcg(tc + u * 32)) : 0u;
+                nix[u] = uint32_t(u) < nt ? ckx(__ldcg(ti + u * 32)) : d.v0;
+                ncx[u] = uint32_t(u) < nt ? ckc(uint32_t(__ldcg(tc + u * 32))) : 0u;
             }
         };
         if (nrounds) first_rows(0);
@@ -1060,8 +1102,8 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StagePa
                 uint32_t jx[4], jc[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    jx[u] = __ldcg(ti + (t2 + u) * 32);
-                    jc[u] = __ldcg(tc + (t2 + u) * 32);
+                    jx[u] = ckx(__ldcg(ti + (t2 + u) * 32));
+                    jc[u] = ckc(__ldcg(tc + (t2 + u) * 32));
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -1071,7 +1113,7 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StagePa
 #pragma unroll
                 for (int u = 0; u < 4; ++u) dv = cfma(cv[u], xv[u], dv);
             }
-            for (; t2 < nt; ++t2) dv = cfma(__ldg(cf + __ldcg(tc + t2 * 32)), __ldg(X + __ldcg(ti + t2 * 32)), dv);
+            for (; t2 < nt; ++t2) dv = cfma(__ldg(cf + ckc(__ldcg(tc + t2 * 32))), __ldg(X + ckx(__ldcg(ti + t2 * 32))), dv);
             if (on) {
                 const uint32_t vg = v0 + l;
                 if (P.stage < 0) {
@@ -1087,6 +1129,7 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StagePa
                 }
             }
         }
+        if (CHECK && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.err, 2u);
         __syncwarp();
     }
 }
@@ -1482,8 +1525,13 @@ static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int n
     } else if (cfg.kernel == SA_KERNEL_LISTS) {
         // a packed handle's pack units first, then the list units of its
         // unpacked instances, each kernel with the whole GPU
-        if (p.npunits) pack_stage_kernel<T, SIDE><<<cfg.pgrid, cfg.block, pack_smem_bytes(cfg), st>>>(p);
-        if (p.nchunks) list_stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
+        if (s.debug & SA_DEBUG_CHECK_INDICES) {
+            if (p.npunits) pack_stage_kernel<T, SIDE, true><<<cfg.pgrid, cfg.block, pack_smem_bytes(cfg), st>>>(p);
+            if (p.nchunks) list_stage_kernel<T, SIDE, true><<<cfg.grid, cfg.block, sm, st>>>(p);
+        } else {
+            if (p.npunits) pack_stage_kernel<T, SIDE, false><<<cfg.pgrid, cfg.block, pack_smem_bytes(cfg), st>>>(p);
+            if (p.nchunks) list_stage_kernel<T, SIDE, false><<<cfg.grid, cfg.block, sm, st>>>(p);
+        }
 
     } else {
         stage_kernel<T, SIDE><<<cfg.grid, cfg.block, sm, st>>>(p);
@@ -1559,6 +1607,7 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.queue = s.queue;
     p.err = s.err;
     p.expire_wait = (s.debug & SA_DEBUG_EXPIRE_WAIT) ? 1 : 0;
+    p.ilimit = static_cast<const uint2*>(s.ilimit);
     return p;
 }
 
@@ -1587,8 +1636,13 @@ cudaError_t pack_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm) 
         *blocks_per_sm = 0;
         return cudaSuccess;
     }
-    if (fp64) return occupancy_of(pack_stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
-    return occupancy_of(pack_stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
+    // (the index-checking variant gets the same shared-memory limit)
+    int dummy = 0;
+    cudaError_t e = fp64 ? occupancy_of(pack_stage_kernel<double, false, true>, cfg.block, sm, lim, &dummy)
+                         : occupancy_of(pack_stage_kernel<float, true, true>, cfg.block, sm, lim, &dummy);
+    if (e != cudaSuccess) return e;
+    if (fp64) return occupancy_of(pack_stage_kernel<double, false, false>, cfg.block, sm, lim, blocks_per_sm);
+    return occupancy_of(pack_stage_kernel<float, true, false>, cfg.block, sm, lim, blocks_per_sm);
 }
 
 cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm) {
@@ -1608,8 +1662,13 @@ cudaError_t stage_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ell_stage_kernel<float, true>, cfg.block, 0);
     }
     if (cfg.kernel == SA_KERNEL_LISTS) {
-        if (fp64) return occupancy_of(list_stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
-        return occupancy_of(list_stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);
+        // (the index-checking variant gets the same shared-memory limit)
+        int dummy = 0;
+        cudaError_t e = fp64 ? occupancy_of(list_stage_kernel<double, false, true>, cfg.block, sm, lim, &dummy)
+                             : occupancy_of(list_stage_kernel<float, true, true>, cfg.block, sm, lim, &dummy);
+        if (e != cudaSuccess) return e;
+        if (fp64) return occupancy_of(list_stage_kernel<double, false, false>, cfg.block, sm, lim, blocks_per_sm);
+        return occupancy_of(list_stage_kernel<float, true, false>, cfg.block, sm, lim, blocks_per_sm);
     }
     if (fp64) return occupancy_of(stage_kernel<double, false>, cfg.block, sm, lim, blocks_per_sm);
     return occupancy_of(stage_kernel<float, true>, cfg.block, sm, lim, blocks_per_sm);

@@ -311,6 +311,7 @@ struct StageLaunch {
     const void* xs_in; void* xs_out; const void* ys; void* accs; void* ys_out;
     double dt; int stage; unsigned int* queue; unsigned int* err;
     int debug;  // SA_DEBUG_* flags (include/sa_heom.h)
+    const void* ilimit;  // SA_DEBUG_CHECK_INDICES: per instance (variables, list slots)
     int ninst;
     // SA_FP32_AUX: the FP64 physical-representative kernel runs on a side
     // stream, forked before and joined after the stage kernel

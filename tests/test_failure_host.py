@@ -46,4 +46,11 @@ def test_debug_flags_preconditions():
         h.set_debug(64)
     assert e.value.code == -1
     h.set_debug(S.SA_DEBUG_EXPIRE_WAIT)  # accepted; takes effect on a device handle
+    h.set_debug(S.SA_DEBUG_CHECK_INDICES)
     h.set_debug(0)
+    # a planted bad list index only ever comes with the kernels' index check,
+    # and only on a device handle
+    for flags in (S.SA_DEBUG_CORRUPT_LIST, S.SA_DEBUG_CORRUPT_LIST | S.SA_DEBUG_CHECK_INDICES):
+        with pytest.raises(S.SaHeomError) as e:
+            h.set_debug(flags)
+        assert e.value.code == -1
