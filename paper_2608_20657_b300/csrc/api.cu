@@ -126,7 +126,6 @@ struct sa_heom {
     std::vector<std::vector<int>> tmpl_packs;  // per template representative: its packs
     std::vector<char> tmpl_list;       // per template representative: some member is not packed
     uint32_t pack_smem = 0;            // shared memory of a pack-kernel warp for the largest pack item
-    uint32_t pack_blob_off = 0;        // where the blob starts in it
     uint64_t pcoef_total = 0;          // entries of the interleaved pack coefficient tables
     void* d_packs = nullptr;
     void* d_pkinst = nullptr;
@@ -657,7 +656,7 @@ template <typename V>
 int build_blobs(sa_heom* h) {
     const size_t ni = h->items.size();
     uint64_t off16 = 0;
-    uint32_t max_sums = 0, max_blob = 0;
+    uint32_t max_pack = 0;
     for (size_t c = 0; c < ni; ++c) {
         ItemDesc& d = h->items[c];
         const bool pk = d.r0 == kPackItemMark;
@@ -665,10 +664,7 @@ int build_blobs(sa_heom* h) {
         // builder may update fewer)
         const uint32_t bytes = pk ? pack_layout<V>(d.np, d.ncat, d.nv, d.row0).bytes
                                   : blob_layout<V>(d.np, d.ncat, d.nl).bytes;
-        if (pk) {
-            max_sums = std::max(max_sums, pack_sums_bytes<V>(d.np, d.ncat));
-            max_blob = std::max(max_blob, bytes);
-        }
+        if (pk) max_pack = std::max(max_pack, pack_sums_bytes<V>(d.np, d.ncat) + bytes);
         d.blob16 = uint32_t(off16);
         d.blob_bytes = bytes;
         off16 += bytes / 16;
@@ -679,10 +675,9 @@ int build_blobs(sa_heom* h) {
     } catch (const std::bad_alloc&) {
         return fail(SA_ERR_OOM, "host memory for the list-kernel blobs");
     }
-    // a pack-kernel warp: mbarrier, 5 x 32 per-lane diagonal parts, the
-    // largest item's sums, then its blob
-    h->pack_blob_off = max_blob ? 16u + uint32_t(5 * 32 * 2 * sizeof(V)) + max_sums : 0u;
-    h->pack_smem = max_blob ? h->pack_blob_off + max_blob : 0u;
+    // a pack-kernel warp: mbarrier, 5 x 32 per-lane diagonal parts, then the
+    // item's grouped sums followed by its blob (the largest item sets the size)
+    h->pack_smem = max_pack ? 16u + uint32_t(5 * 32 * 2 * sizeof(V)) + max_pack : 0u;
     int prc = SA_OK;
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t c = 0; c < int64_t(ni); ++c) {
@@ -1239,7 +1234,6 @@ int apply_tuning(sa_heom* h) {
     int rc = ensure_tables(h);
     if (rc) return rc;
     h->cfg.pack_smem = h->kernel == SA_KERNEL_LISTS ? int(h->pack_smem) : 0;
-    h->cfg.pack_blob = int(h->pack_blob_off);
     // work the grid shares out: the list kernel's units, the other kernels' items
     if (h->host_only) return SA_OK;
     const uint64_t nchunks = h->kernel == SA_KERNEL_LISTS ? h->n_list_units : h->items.size();

@@ -97,7 +97,6 @@ template <typename T> struct StageParams {
     const uint2* __restrict__ punits;        // pack kernel: work units (pack item | kPackUnit, pack)
     uint32_t npunits;
     uint32_t pack_smem;                      // pack kernel: shared-memory bytes per warp
-    uint32_t pack_blob;                      // pack kernel: offset of the item blob in a warp's shared memory
     unsigned int* pqueue;                    // pack kernel: its work counter
     const uint32_t* __restrict__ wpat;      // first pattern of every warp row of 32 variables
     uint32_t nvar;
@@ -665,7 +664,9 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
 //    uvar-up, uvar-down) and the fused RK4 update.  Within a phase the loads
 //    of the next variable (its value, operands, y, accumulator and first two
 //    terms) are issued before the current one is finished, so two
-//    variables' memory latencies overlap.
+//    variables' memory latencies overlap; the term targets of the two
+//    variables after those are prefetched into L2, and the item's value, y
+//    and accumulator blocks are prefetched into L2 when the unit starts.
 // Returns false when the bounded wait for the tables expired (error bit set,
 // the copy drained).
 template <typename T, bool FP64SIDE, bool CHECK>
@@ -674,7 +675,7 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
     using C = typename Cx<T>::t;
     C* const ccs = reinterpret_cast<C*>(wsm + 16);            // 5 x 32 per-lane diagonal parts
     C* const sums = ccs + 5 * 32;                             // grouped sums, 32 lanes per entry
-    unsigned char* const blob = wsm + P.pack_blob;
+    unsigned char* const blob = reinterpret_cast<unsigned char*>(sums + (2 * d.ncat + d.np + 1) * 32);  // after them
     const PackDev pk = P.packs[pkid];
     const uint32_t n = pk.n;
     const bool act = uint32_t(lane) < n;
@@ -684,10 +685,11 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, d.blob_bytes);
         bulk_g2s(blob, P.blobs + size_t(d.blob16) * 16, d.blob_bytes, bar);
-    } else if ((lane == 1 || lane == 2) && P.stage > 0) {
-        // the item's y and accumulator block (contiguous in the pack) into L2
-        const Span t = span(lane == 1 ? P.y : static_cast<const C*>(P.acc), size_t(pk.base) + size_t(d.v0) * n,
-                            d.nv * n, sizeof(C));
+    } else if (lane <= 3 && (lane == 3 || P.stage > 0)) {
+        // the item's y, accumulator and stage-input blocks (contiguous in the
+        // pack) into L2
+        const C* const src = lane == 1 ? P.y : (lane == 2 ? static_cast<const C*>(P.acc) : P.x_in);
+        const Span t = span(src, size_t(pk.base) + size_t(d.v0) * n, d.nv * n, sizeof(C));
         if (t.bytes) bulk_prefetch_l2(t.src, t.bytes);
     }
     // the lane's instance constants while the copy is in flight
@@ -823,6 +825,13 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
             }
         }
     };
+    // the term targets of variable k into L2 (two variables before its loads)
+    auto prefetch_targets = [&](uint32_t k) {
+        if (k >= nl) return;
+        const uint4 r = vrec[k];
+        const uint32_t u0 = (r.y >> 10) & 65535u, cnt = r.y >> 26;
+        for (uint32_t u = u0; u < u0 + cnt; ++u) asm volatile("prefetch.global.L2 [%0];" ::"l"(X + tgtat(u) * n));
+    };
     // the three phases (P, T, S; X, Y; Z), each with two register sets in
     // turn: variable i + 1 loads while variable i finishes
     const uint32_t ph1 = d.row1 & 65535u, ph2 = ph1 + (d.row1 >> 16);
@@ -834,6 +843,8 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
         C vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1;
         if (i0 < i1) fetch(ph, i0, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
         for (uint32_t i = i0; i < i1; i += 2) {
+            prefetch_targets(i + 2);
+            prefetch_targets(i + 3);
             if (i + 1 < i1) fetch(ph, i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
             finish(ph, i, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
             if (i + 1 >= i1) break;
@@ -1586,7 +1597,6 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.punits = static_cast<const uint2*>(s.punits);
     p.npunits = s.npunits;
     p.pack_smem = uint32_t((cfg.pack_smem + 15) / 16 * 16);
-    p.pack_blob = uint32_t(cfg.pack_blob);
     p.pqueue = s.pqueue;
     p.nvar = s.nvar;
     p.nchunks = s.nchunks;

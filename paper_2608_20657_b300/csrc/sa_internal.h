@@ -291,7 +291,6 @@ struct LaunchCfg {
     int grid;       // CTAs
     int kernel;     // SA_KERNEL_RECORDS, SA_KERNEL_LISTS or SA_KERNEL_ELL (include/sa_heom.h)
     int pack_smem;  // pack kernel: shared-memory bytes of a warp (0: no packs)
-    int pack_blob;  // pack kernel: offset of the blob in a warp's shared memory (after mbarrier, diagonal parts, sums)
     int pgrid;      // pack kernel: CTAs (persistent)
 };
 struct StageLaunch {
