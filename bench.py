@@ -116,13 +116,13 @@ _PACK_BEGIN = "// -- begin: pack kernel (the opt-in packed layout; no list-kerne
 _PACK_END = "// -- end: pack kernel\n"
 
 
-def _stage_sha() -> str:
+def _stage_sha(pack: bool = False) -> str:
     """Hash of the stage kernels' source: kernels.cu less its marked
     physical-representative sections (the FP64 rho_0, observables and init
-    kernels and their launch wrappers) and its pack-kernel section, which no
-    other stage kernel calls."""
+    kernels and their launch wrappers) and, unless the packed layout's stage
+    is meant, its pack-kernel section, which no other stage kernel calls."""
     src = open(os.path.join(ROOT, "paper_2608_20657_b300", "csrc", "kernels.cu"), encoding="utf-8").read()
-    for b, e in ((_PHYS_BEGIN, _PHYS_END), (_PACK_BEGIN, _PACK_END)):
+    for b, e in ((_PHYS_BEGIN, _PHYS_END),) + (() if pack else ((_PACK_BEGIN, _PACK_END),)):
         src = re.sub(re.escape(b) + ".*?" + re.escape(e), "", src, flags=re.S)
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
@@ -135,7 +135,7 @@ def _traffic(workload: str, kernel_name: str):
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("kernel_sha") != _stage_sha() or d.get("kernel") != kernel_name:
+    if d.get("kernel_sha") != _stage_sha(kernel_name.startswith("pack")) or d.get("kernel") != kernel_name:
         return None
     return d.get("dram_bytes_per_launch")
 
@@ -250,9 +250,13 @@ def run_reference(args):
 
 # ------------------------------------------------------------ GPU arm
 
-def _kernel_name(kernel, fp32):
-    base = {1: "list_stage_kernel", 2: "ell_stage_kernel"}.get(kernel, "stage_kernel")
-    return base + ("<float,true>" if fp32 else "<double,false>")
+def _kernel_name(kernel, fp32, packed=False):
+    """The stage kernel the step launches (the instantiation without index
+    checks); on a packed handle the pack kernel, then the list kernel for
+    the unpacked instances, make up one RK4 stage."""
+    args = "<float,true,false>" if fp32 else "<double,false,false>"
+    base = {1: "list_stage_kernel", 2: "ell_stage_kernel"}.get(kernel, "stage_kernel") + args
+    return "pack_stage_kernel" + args + "+" + base if packed else base
 
 
 def run_ours(args):
@@ -271,8 +275,10 @@ def run_ours(args):
     ws, ps, precision, dt = _params(args.workload)
     if args.precision == "fp64":
         precision = S.SA_FP64
-    pack = args.layout == "packed"
-    h = S.Heom(ps, precision=precision, pack=pack)
+    h = S.Heom(ps, precision=precision, pack=args.layout == "packed")
+    # a single instance, or a batch without a template of 16 members, has
+    # no pack: its layout stays the canonical one
+    pack = args.layout == "packed" and len(h.dump_packs()["packs"]) > 0
     st = h.new_state()
     h.init_state(st, _rho0(ws))
     stream = torch.cuda.current_stream()
@@ -314,13 +320,14 @@ def run_ours(args):
 
     # roofline of the stage kernel (4 launches per step; in FP32-aux mode the
     # small FP64 kernel of the physical density matrix overlaps each of them
-    # on a side stream)
+    # on a side stream; on a packed handle a "launch" is one RK4 stage, the
+    # pack kernel followed by the list kernel of the unpacked instances)
     launch_ms = ms_step / 4.0
     bytes_launch = FP32_BYTES_PER_VAR_STEP * n_vars / 4.0 if precision == S.SA_FP32_AUX else \
         FP64_BYTES_PER_VAR_STEP * n_vars / 4.0
     achieved = bytes_launch / (launch_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
-    kname = _kernel_name(tuning["kernel"], precision == S.SA_FP32_AUX)
+    kname = _kernel_name(tuning["kernel"], precision == S.SA_FP32_AUX, pack)
     traffic = _traffic(args.workload, kname)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs",
@@ -373,7 +380,7 @@ def run_ours(args):
                 "config": {"workload": _workload_name(args.workload),
                            "n_instances": h.count, "n_vars": n_vars, "n_patterns": h.n_patterns,
                            "state_bytes": h.state_bytes, "l2": "inputs larger than L2 (4 vectors)",
-                           "tuning": tuning, "layout": args.layout,
+                           "tuning": tuning, "layout": "packed" if pack else "canonical",
                            "parallelism": f"replicas{world}"},
                 "roofline": roof, "gpu_launches": h.launches_per_step() * args.steps, "clocks": ck, "e2e": e2e}
         line.update(extra)
@@ -574,9 +581,10 @@ def main():
                          "--steps calls), then exit")
     ap.add_argument("--tune", default="", help="block,chunk,queue[,kernel] (skips the autotuner; kernel 0 = "
                                                 "connection records, 1 = term lists)")
-    ap.add_argument("--layout", default="canonical", choices=["packed", "canonical"],
-                    help="canonical: instance after instance (default, the faster on w4); packed: instances of "
-                         "repeated templates interleaved in packs of up to 32 (SA_BUILD_PACK_INSTANCES, the pack kernel)")
+    ap.add_argument("--layout", default="packed", choices=["packed", "canonical"],
+                    help="packed (default, the faster on w4): instances of repeated templates interleaved in packs "
+                         "of up to 32 (SA_BUILD_PACK_INSTANCES, the pack kernel); canonical: instance after instance, "
+                         "the list kernel only")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
