@@ -2630,13 +2630,14 @@ int sa_heom_autotune_ex(sa_heom* h, void* d_state, void* stream, int flags, int*
 }
 
 // four stage kernels, plus the FP64 physical-representative kernel after each
-// stage in SA_FP32_AUX mode
+// stage in SA_FP32_AUX mode (on a packed handle the pack kernel runs the
+// list units too)
 int sa_heom_launches_per_step(const sa_heom* h) {
     if (!h) return 0;
     int main = 1;
     if (h->kernel == SA_KERNEL_ELL) main = 2;  // grouped sums, then the ELL kernel
     if (h->kernel == SA_KERNEL_LISTS && !h->host_only)
-        main = (h->n_list_units ? 1 : 0) + (h->n_pack_units ? 1 : 0);  // list kernel, pack kernel
+        main = (h->n_list_units || h->n_pack_units) ? 1 : 0;  // list kernel, or the pack kernel
     return 4 * (main + (h->precision == SA_FP64 ? 0 : 1));
 }
 

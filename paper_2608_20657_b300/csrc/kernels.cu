@@ -647,245 +647,6 @@ __device__ __forceinline__ ListSmem<T> carve_list(unsigned char* p, int item) {
     return W;
 }
 
-// -- begin: pack kernel (the opt-in packed layout; no list-kernel code)
-// One pack unit: a pack item evaluated for the n <= 32 instances of a pack,
-// lane j taking the pack's instance j (lanes j >= n shadow lane 0 and store
-// nothing).  The pack's state is interleaved, so every access of the warp --
-// a variable of the item, a tier +/-1 target, a coefficient slot, y and the
-// accumulator -- is one contiguous run of n elements, and the item's tables
-// (one bulk copy into the warp's shared memory) are read by all lanes alike.
-//  * the item's variables one per round, in three phases (P, T, S; then X,
-//    Y; then Z): each adds its own value, weighted, to the grouped sums it
-//    enters (R_q and C_q of Eqs. grouped-row-sum, grouped-column-sum, the Z
-//    sum of Eq. HZ; in the warp's shared memory, one column per lane), which
-//    the next phase reads as operands; each gets its diagonal (-Gamma_Lambda
-//    plus the instance's loss, terminator and detuning), commutator
-//    -i g (op[a] - op[b]) with host-chosen operands, hierarchy terms (Eqs.
-//    uvar-up, uvar-down) and the fused RK4 update.  Within a phase the loads
-//    of the next variable (its value, operands, y, accumulator and first two
-//    terms) are issued before the current one is finished, so two
-//    variables' memory latencies overlap; the term targets of the two
-//    variables after those are prefetched into L2, and the item's value, y
-//    and accumulator blocks are prefetched into L2 when the unit starts.
-// Returns false when the bounded wait for the tables expired (error bit set,
-// the copy drained).
-template <typename T, bool FP64SIDE, bool CHECK>
-__device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDesc& d, uint32_t pkid,
-                                          unsigned char* wsm, uint64_t* bar, uint32_t& parity, int lane) {
-    using C = typename Cx<T>::t;
-    C* const ccs = reinterpret_cast<C*>(wsm + 16);            // 5 x 32 per-lane diagonal parts
-    C* const sums = ccs + 5 * 32;                             // grouped sums, 32 lanes per entry
-    unsigned char* const blob = reinterpret_cast<unsigned char*>(sums + (2 * d.ncat + d.np + 1) * 32);  // after them
-    const PackDev pk = P.packs[pkid];
-    const uint32_t n = pk.n;
-    const bool act = uint32_t(lane) < n;
-    const uint32_t ll = act ? uint32_t(lane) : 0u;
-    if (lane == 0) {
-        // earlier units wrote this shared memory with ordinary stores
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(bar, d.blob_bytes);
-        bulk_g2s(blob, P.blobs + size_t(d.blob16) * 16, d.blob_bytes, bar);
-    } else if (lane <= 3 && (lane == 3 || P.stage > 0)) {
-        // the item's y, accumulator and stage-input blocks (contiguous in the
-        // pack) into L2
-        const C* const src = lane == 1 ? P.y : (lane == 2 ? static_cast<const C*>(P.acc) : P.x_in);
-        const Span t = span(src, size_t(pk.base) + size_t(d.v0) * n, d.nv * n, sizeof(C));
-        if (t.bytes) bulk_prefetch_l2(t.src, t.bytes);
-    }
-    // the lane's instance constants while the copy is in flight
-    const InstK<T>* const ik = P.instk + P.pk_inst[pk.lane0 + ll];
-    const T g = ik->g, Nt = T(ik->N);
-#pragma unroll
-    for (int cl = 0; cl < 5; ++cl) ccs[cl * 32 + lane] = mk(ik->cc[2 * cl], ik->cc[2 * cl + 1]);
-    if (!__all_sync(0xffffffffu, !P.expire_wait && mbar_wait(bar, parity))) {
-        if (lane == 0) atomicOr(P.err, 1u);
-        mbar_wait(bar, parity);
-        return false;
-    }
-    parity ^= 1u;
-    const uint32_t np = d.np, ncat = d.ncat, nv = d.nv, nl = d.nl;
-    const PackLayout B = pack_layout<T>(np, ncat, nl, d.row0);
-    const ItemPat* const ph = reinterpret_cast<const ItemPat*>(blob + B.pat);
-    const C* const pd = reinterpret_cast<const C*>(blob + B.pd);
-    const T* const cM = reinterpret_cast<const T*>(blob + B.cM);
-    const uint4* const vrec = reinterpret_cast<const uint4*>(blob + B.vrec);
-    const uint32_t* const tgt0 = reinterpret_cast<const uint32_t*>(blob + B.tgt);
-    const uint16_t* const tsl0 = reinterpret_cast<const uint16_t*>(blob + B.tsl);
-    (void)ph;
-    // SA_DEBUG_CHECK_INDICES: a target or slot out of the template's range
-    // reads index 0 instead and raises bit 1 of the error word
-    uint2 lim = make_uint2(0u, 0u);
-    if (CHECK) lim = P.ilimit[P.pk_inst[pk.lane0]];
-    bool bad = false;
-    auto tgtat = [&](uint32_t u) {
-        const uint32_t v = tgt0[u];
-        if (CHECK && v >= lim.x) {
-            bad = true;
-            return 0u;
-        }
-        return v;
-    };
-    auto tslat = [&](uint32_t u) {
-        const uint32_t v = tsl0[u];
-        if (CHECK && v >= lim.y) {
-            bad = true;
-            return 0u;
-        }
-        return v;
-    };
-    // lane base pointers; element offsets from them are 32-bit
-    const size_t lb = size_t(pk.base) + ll;
-    const C* __restrict__ X = P.x_in + lb;
-    const C* __restrict__ cf = P.pcoef + pk.cbase + ll;
-    const uint32_t iv0 = d.v0 * n;  // the item's variable 0
-    // the grouped sums start at zero; the zero operand stays zero
-    C* const sl = sums + lane;
-    const uint32_t nsums = 2 * ncat + np + 1;
-    for (uint32_t k = 0; k < nsums; ++k) sl[k * 32] = mk(T(0), T(0));
-    // weight of a grouped-sum contribution: a + b N (b = 0 but for the zero
-    // category, whose multiplicity is N - r)
-    auto weight = [&](uint32_t w) { return fma(T(int((w >> 12) & 3u) - 1), Nt, T(int((w >> 14) & 65535u) - 32768)); };
-    const C* __restrict__ Yb = P.y + lb;
-    C* const Ab = P.acc + lb;
-    C* const XO = P.x_out + lb;
-    C* const YO = P.y_out + lb;
-    const int stage = P.stage;
-    const T dtT = T(P.dt);
-    const T aT = stage == 2 ? dtT : T(0.5) * dtT;
-    const C z = mk(T(0), T(0));
-    auto var = [&](uint32_t code) { return __ldg(X + (iv0 + code * n)); };
-    // loads of variable i in phase ph: value, operands (P, T, S: two item
-    // variables; X, Y: the Z variable and a sum; Z: its sum), y, accumulator,
-    // first two terms
-    auto fetch = [&](int ph, uint32_t i, C& v, C& oa, C& ob, C& yv, C& av, C& x0, C& c0, C& x1, C& c1) {
-        const uint4 r = vrec[i];
-        const uint32_t off = iv0 + (r.y & 1023u) * n;
-        const uint32_t u0 = (r.y >> 10) & 65535u, cnt = r.y >> 26;
-        const uint32_t ca = r.x & 2047u, cb = (r.x >> 11) & 2047u;
-        v = __ldg(X + off);
-        if (ph == 0) {
-            oa = var(ca);
-            ob = var(cb);
-        } else if (ph == 1) {
-            oa = ca < nv ? var(ca) : sl[(ca - nv) * 32];
-            ob = cb < nv ? var(cb) : sl[(cb - nv) * 32];
-        } else {
-            oa = sl[(ca - nv) * 32];
-            ob = z;
-        }
-        yv = z;
-        av = z;
-        if (stage > 0) {
-            yv = __ldcg(Yb + off);
-            av = __ldcg(Ab + off);
-        }
-        x0 = c0 = x1 = c1 = z;
-        if (cnt > 0) {
-            x0 = __ldg(X + tgtat(u0) * n);
-            c0 = __ldg(cf + tslat(u0) * n);
-        }
-        if (cnt > 1) {
-            x1 = __ldg(X + tgtat(u0 + 1) * n);
-            c1 = __ldg(cf + tslat(u0 + 1) * n);
-        }
-    };
-    // the rest of variable i: its contributions to the grouped sums (P, T, S:
-    // two; X, Y: one; Z: none), then diagonal, commutator, terms, RK4 update
-    auto finish = [&](int ph, uint32_t i, C v, C oa, C ob, C yv, C av, C x0, C c0, C x1, C c1) {
-        const uint4 r = vrec[i];
-        if (ph < 2) sl[(r.z & 2047u) * 32] = caxpy(weight(r.z), v, sl[(r.z & 2047u) * 32]);
-        if (ph == 0) sl[(r.w & 2047u) * 32] = caxpy(weight(r.w), v, sl[(r.w & 2047u) * 32]);
-        const uint32_t off = iv0 + (r.y & 1023u) * n;
-        const uint32_t u0 = (r.y >> 10) & 65535u, u1 = u0 + (r.y >> 26);
-        const C dgl = cadd(pd[(r.x >> 25) & 31u], ccs[((r.x >> 22) & 7u) * 32 + lane]);
-        const C t = csub(oa, ob);
-        C dv = mk(g * t.y, -g * t.x);
-        dv = cfma(dgl, v, dv);
-        dv = cfma(c0, x0, dv);
-        dv = cfma(c1, x1, dv);
-        uint32_t u = u0 + 2;
-        for (; u + 2 <= u1; u += 2) {
-            const C xa = __ldg(X + tgtat(u) * n), ca = __ldg(cf + tslat(u) * n);
-            const C xb = __ldg(X + tgtat(u + 1) * n), cb = __ldg(cf + tslat(u + 1) * n);
-            dv = cfma(ca, xa, dv);
-            dv = cfma(cb, xb, dv);
-        }
-        if (u < u1) dv = cfma(__ldg(cf + tslat(u) * n), __ldg(X + tgtat(u) * n), dv);
-        if (act) {
-            if (stage < 0) {
-                XO[off] = dv;
-            } else if (stage == 0) {
-                Ab[off] = dv;
-                XO[off] = caxpy(aT, dv, v);  // x_in is y in the first stage
-            } else if (stage == 3) {
-                YO[off] = caxpy(dtT / T(6), cadd(av, dv), yv);
-            } else {
-                Ab[off] = caxpy(T(2), dv, av);
-                XO[off] = caxpy(aT, dv, yv);
-            }
-        }
-    };
-    // the term targets of variable k into L2 (two variables before its loads)
-    auto prefetch_targets = [&](uint32_t k) {
-        if (k >= nl) return;
-        const uint4 r = vrec[k];
-        const uint32_t u0 = (r.y >> 10) & 65535u, cnt = r.y >> 26;
-        for (uint32_t u = u0; u < u0 + cnt; ++u) asm volatile("prefetch.global.L2 [%0];" ::"l"(X + tgtat(u) * n));
-    };
-    // the three phases (P, T, S; X, Y; Z), each with two register sets in
-    // turn: variable i + 1 loads while variable i finishes
-    const uint32_t ph1 = d.row1 & 65535u, ph2 = ph1 + (d.row1 >> 16);
-    uint32_t i0 = 0;
-#pragma unroll 1
-    for (int ph = 0; ph < 3; ++ph) {
-        const uint32_t i1 = ph == 0 ? ph1 : (ph == 1 ? ph2 : nl);
-        C vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1;
-        C vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1;
-        if (i0 < i1) fetch(ph, i0, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
-        for (uint32_t i = i0; i < i1; i += 2) {
-            prefetch_targets(i + 2);
-            prefetch_targets(i + 3);
-            if (i + 1 < i1) fetch(ph, i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
-            finish(ph, i, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
-            if (i + 1 >= i1) break;
-            if (i + 2 < i1) fetch(ph, i + 2, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
-            finish(ph, i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
-        }
-        i0 = i1;
-    }
-    if (CHECK && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.err, 2u);
-    __syncwarp();
-    return true;
-}
-
-// The pack kernel: persistent warps drawing pack units (static striding or
-// the atomic counter), each warp with an mbarrier and a blob buffer of
-// pack_smem bytes.  Registers are budgeted apart from the list kernel's.
-template <typename T, bool FP64SIDE, bool CHECK>
-__global__ void __maxnreg__(sizeof(T) == 8 ? 128 : 80) pack_stage_kernel(StageParams<T> P) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    unsigned char* const wsm = smem + size_t(wib) * P.pack_smem;
-    uint64_t* const bar = reinterpret_cast<uint64_t*>(wsm);
-    if (lane == 0) {
-        mbar_init(bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    ItemQueue Q;
-    Q.init(P.use_queue, wib);
-    uint32_t parity = 0;
-    for (;;) {
-        const unsigned int c = Q.next(P.pqueue, P.npunits, lane);
-        if (c >= P.npunits) break;
-        const uint2 un = P.punits[c];
-        if (!pack_unit<T, FP64SIDE, CHECK>(P, P.items[un.x & ~kPackUnit], un.y, wsm, bar, parity, lane)) return;
-    }
-}
-
-// -- end: pack kernel
-
 // One warp per work item, like stage_kernel, but
 //  * the item's stage-input slice and its table blob (instance constants,
 //    patterns, damping rates, category words, multiplicities and owners,
@@ -903,29 +664,16 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 128 : 80) pack_stage_kernel(StagePa
 //    variable, with operands and the diagonal class chosen by the host.
 // A bounded wait that expires sets bit 0 of the error word; the warp then
 // waits (bounded again) for its copies and stops.
-// (a register budget instead of launch bounds: ptxas otherwise trades a few
-// spills for 32 resident warps, which measured slower)
+// list_unit is one work unit c in the warp's shared memory S; it returns
+// false when the bounded wait for its copies expired.
 template <typename T, bool FP64SIDE, bool CHECK>
-__global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StageParams<T> P) {
+__device__ __forceinline__ bool list_unit(const StageParams<T>& P, unsigned int c, const ListSmem<T>& S,
+                                          uint32_t& parity, int lane) {
     using C = typename Cx<T>::t;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
     const int chunk = P.chunk;
-    const ListSmem<T> S = carve_list<T>(smem + size_t(wib) * list_smem_bytes<T>(chunk), chunk);
-    if (lane == 0) {
-        mbar_init(S.bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    ItemQueue Q;
-    Q.init(P.use_queue, wib);
     const T dtT = T(P.dt);
     const T aT = P.stage == 2 ? dtT : T(0.5) * dtT;
-    uint32_t parity = 0;
-    for (;;) {
-        const unsigned int c = Q.next(P.queue, P.nchunks, lane);
-        if (c >= P.nchunks) break;
+    {
         // a work unit: a template item and the instance it is evaluated for
         const uint2 un = P.units[c];
         const ItemDesc d = P.items[un.x];
@@ -961,7 +709,7 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StagePa
         if (!__all_sync(0xffffffffu, !P.expire_wait && mbar_wait(S.bar, parity))) {
             if (lane == 0) atomicOr(P.err, 1u);
             mbar_wait(S.bar, parity);
-            return;
+            return false;
         }
         parity ^= 1u;
         const int np = int(d.np);
@@ -1143,7 +891,286 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StagePa
         if (CHECK && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.err, 2u);
         __syncwarp();
     }
+    return true;
 }
+
+// The list kernel: persistent warps drawing work units (static striding or
+// the atomic counter).  (A register budget instead of launch bounds: ptxas
+// otherwise trades a few spills for 32 resident warps, which measured
+// slower.)
+template <typename T, bool FP64SIDE, bool CHECK>
+__global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StageParams<T> P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const ListSmem<T> S = carve_list<T>(smem + size_t(wib) * list_smem_bytes<T>(P.chunk), P.chunk);
+    if (lane == 0) {
+        mbar_init(S.bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    ItemQueue Q;
+    Q.init(P.use_queue, wib);
+    uint32_t parity = 0;
+    for (;;) {
+        const unsigned int c = Q.next(P.queue, P.nchunks, lane);
+        if (c >= P.nchunks) break;
+        if (!list_unit<T, FP64SIDE, CHECK>(P, c, S, parity, lane)) return;
+    }
+}
+
+// -- begin: pack kernel (the opt-in packed layout; no list-kernel code)
+// One pack unit: a pack item evaluated for the n <= 32 instances of a pack,
+// lane j taking the pack's instance j (lanes j >= n shadow lane 0 and store
+// nothing).  The pack's state is interleaved, so every access of the warp --
+// a variable of the item, a tier +/-1 target, a coefficient slot, y and the
+// accumulator -- is one contiguous run of n elements, and the item's tables
+// (one bulk copy into the warp's shared memory) are read by all lanes alike.
+//  * the item's variables one per round, in three phases (P, T, S; then X,
+//    Y; then Z): each adds its own value, weighted, to the grouped sums it
+//    enters (R_q and C_q of Eqs. grouped-row-sum, grouped-column-sum, the Z
+//    sum of Eq. HZ; in the warp's shared memory, one column per lane), which
+//    the next phase reads as operands; each gets its diagonal (-Gamma_Lambda
+//    plus the instance's loss, terminator and detuning), commutator
+//    -i g (op[a] - op[b]) with host-chosen operands, hierarchy terms (Eqs.
+//    uvar-up, uvar-down) and the fused RK4 update.  Within a phase the loads
+//    of the next variable (its value, operands, y, accumulator and first two
+//    terms) are issued before the current one is finished, so two
+//    variables' memory latencies overlap; the term targets of the two
+//    variables after those are prefetched into L2, and the item's value, y
+//    and accumulator blocks are prefetched into L2 when the unit starts.
+// Returns false when the bounded wait for the tables expired (error bit set,
+// the copy drained).
+template <typename T, bool FP64SIDE, bool CHECK>
+__device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDesc& d, uint32_t pkid,
+                                          unsigned char* wsm, uint64_t* bar, uint32_t& parity, int lane) {
+    using C = typename Cx<T>::t;
+    C* const ccs = reinterpret_cast<C*>(wsm + 16);            // 5 x 32 per-lane diagonal parts
+    C* const sums = ccs + 5 * 32;                             // grouped sums, 32 lanes per entry
+    unsigned char* const blob = reinterpret_cast<unsigned char*>(sums + (2 * d.ncat + d.np + 1) * 32);  // after them
+    const PackDev pk = P.packs[pkid];
+    const uint32_t n = pk.n;
+    const bool act = uint32_t(lane) < n;
+    const uint32_t ll = act ? uint32_t(lane) : 0u;
+    if (lane == 0) {
+        // earlier units wrote this shared memory with ordinary stores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, d.blob_bytes);
+        bulk_g2s(blob, P.blobs + size_t(d.blob16) * 16, d.blob_bytes, bar);
+    } else if (lane <= 3 && (lane == 3 || P.stage > 0)) {
+        // the item's y, accumulator and stage-input blocks (contiguous in the
+        // pack) into L2
+        const C* const src = lane == 1 ? P.y : (lane == 2 ? static_cast<const C*>(P.acc) : P.x_in);
+        const Span t = span(src, size_t(pk.base) + size_t(d.v0) * n, d.nv * n, sizeof(C));
+        if (t.bytes) bulk_prefetch_l2(t.src, t.bytes);
+    }
+    // the lane's instance constants while the copy is in flight
+    const InstK<T>* const ik = P.instk + P.pk_inst[pk.lane0 + ll];
+    const T g = ik->g, Nt = T(ik->N);
+#pragma unroll
+    for (int cl = 0; cl < 5; ++cl) ccs[cl * 32 + lane] = mk(ik->cc[2 * cl], ik->cc[2 * cl + 1]);
+    if (!__all_sync(0xffffffffu, !P.expire_wait && mbar_wait(bar, parity))) {
+        if (lane == 0) atomicOr(P.err, 1u);
+        mbar_wait(bar, parity);
+        return false;
+    }
+    parity ^= 1u;
+    const uint32_t np = d.np, ncat = d.ncat, nv = d.nv, nl = d.nl;
+    const PackLayout B = pack_layout<T>(np, ncat, nl, d.row0);
+    const C* const pd = reinterpret_cast<const C*>(blob + B.pd);
+    const uint4* const vrec = reinterpret_cast<const uint4*>(blob + B.vrec);
+    const uint32_t* const tgt0 = reinterpret_cast<const uint32_t*>(blob + B.tgt);
+    const uint16_t* const tsl0 = reinterpret_cast<const uint16_t*>(blob + B.tsl);
+    // SA_DEBUG_CHECK_INDICES: a target or slot out of the template's range
+    // reads index 0 instead and raises bit 1 of the error word
+    uint2 lim = make_uint2(0u, 0u);
+    if (CHECK) lim = P.ilimit[P.pk_inst[pk.lane0]];
+    bool bad = false;
+    auto tgtat = [&](uint32_t u) {
+        const uint32_t v = tgt0[u];
+        if (CHECK && v >= lim.x) {
+            bad = true;
+            return 0u;
+        }
+        return v;
+    };
+    auto tslat = [&](uint32_t u) {
+        const uint32_t v = tsl0[u];
+        if (CHECK && v >= lim.y) {
+            bad = true;
+            return 0u;
+        }
+        return v;
+    };
+    // lane base pointers; element offsets from them are 32-bit
+    const size_t lb = size_t(pk.base) + ll;
+    const C* __restrict__ X = P.x_in + lb;
+    const C* __restrict__ cf = P.pcoef + pk.cbase + ll;
+    const uint32_t iv0 = d.v0 * n;  // the item's variable 0
+    // the grouped sums start at zero; the zero operand stays zero
+    C* const sl = sums + lane;
+    const uint32_t nsums = 2 * ncat + np + 1;
+    for (uint32_t k = 0; k < nsums; ++k) sl[k * 32] = mk(T(0), T(0));
+    // weight of a grouped-sum contribution: a + b N (b = 0 but for the zero
+    // category, whose multiplicity is N - r)
+    auto weight = [&](uint32_t w) { return fma(T(int((w >> 12) & 3u) - 1), Nt, T(int((w >> 14) & 65535u) - 32768)); };
+    const C* __restrict__ Yb = P.y + lb;
+    C* const Ab = P.acc + lb;
+    C* const XO = P.x_out + lb;
+    C* const YO = P.y_out + lb;
+    const int stage = P.stage;
+    const T dtT = T(P.dt);
+    const T aT = stage == 2 ? dtT : T(0.5) * dtT;
+    const C z = mk(T(0), T(0));
+    auto var = [&](uint32_t code) { return __ldg(X + (iv0 + code * n)); };
+    // loads of variable i in phase ph: value, operands (P, T, S: two item
+    // variables; X, Y: the Z variable and a sum; Z: its sum), y, accumulator,
+    // first two terms
+    auto fetch = [&](int ph, uint32_t i, C& v, C& oa, C& ob, C& yv, C& av, C& x0, C& c0, C& x1, C& c1) {
+        const uint4 r = vrec[i];
+        const uint32_t off = iv0 + (r.y & 1023u) * n;
+        const uint32_t u0 = (r.y >> 10) & 65535u, cnt = r.y >> 26;
+        const uint32_t ca = r.x & 2047u, cb = (r.x >> 11) & 2047u;
+        v = __ldg(X + off);
+        if (ph == 0) {
+            oa = var(ca);
+            ob = var(cb);
+        } else if (ph == 1) {
+            oa = ca < nv ? var(ca) : sl[(ca - nv) * 32];
+            ob = cb < nv ? var(cb) : sl[(cb - nv) * 32];
+        } else {
+            oa = sl[(ca - nv) * 32];
+            ob = z;
+        }
+        yv = z;
+        av = z;
+        if (stage > 0) {
+            yv = __ldcg(Yb + off);
+            av = __ldcg(Ab + off);
+        }
+        x0 = c0 = x1 = c1 = z;
+        if (cnt > 0) {
+            x0 = __ldg(X + tgtat(u0) * n);
+            c0 = __ldg(cf + tslat(u0) * n);
+        }
+        if (cnt > 1) {
+            x1 = __ldg(X + tgtat(u0 + 1) * n);
+            c1 = __ldg(cf + tslat(u0 + 1) * n);
+        }
+    };
+    // the rest of variable i: its contributions to the grouped sums (P, T, S:
+    // two; X, Y: one; Z: none), then diagonal, commutator, terms, RK4 update
+    auto finish = [&](int ph, uint32_t i, C v, C oa, C ob, C yv, C av, C x0, C c0, C x1, C c1) {
+        const uint4 r = vrec[i];
+        if (ph < 2) sl[(r.z & 2047u) * 32] = caxpy(weight(r.z), v, sl[(r.z & 2047u) * 32]);
+        if (ph == 0) sl[(r.w & 2047u) * 32] = caxpy(weight(r.w), v, sl[(r.w & 2047u) * 32]);
+        const uint32_t off = iv0 + (r.y & 1023u) * n;
+        const uint32_t u0 = (r.y >> 10) & 65535u, u1 = u0 + (r.y >> 26);
+        const C dgl = cadd(pd[(r.x >> 25) & 31u], ccs[((r.x >> 22) & 7u) * 32 + lane]);
+        const C t = csub(oa, ob);
+        C dv = mk(g * t.y, -g * t.x);
+        dv = cfma(dgl, v, dv);
+        dv = cfma(c0, x0, dv);
+        dv = cfma(c1, x1, dv);
+        uint32_t u = u0 + 2;
+        for (; u + 2 <= u1; u += 2) {
+            const C xa = __ldg(X + tgtat(u) * n), ca = __ldg(cf + tslat(u) * n);
+            const C xb = __ldg(X + tgtat(u + 1) * n), cb = __ldg(cf + tslat(u + 1) * n);
+            dv = cfma(ca, xa, dv);
+            dv = cfma(cb, xb, dv);
+        }
+        if (u < u1) dv = cfma(__ldg(cf + tslat(u) * n), __ldg(X + tgtat(u) * n), dv);
+        if (act) {
+            if (stage < 0) {
+                XO[off] = dv;
+            } else if (stage == 0) {
+                Ab[off] = dv;
+                XO[off] = caxpy(aT, dv, v);  // x_in is y in the first stage
+            } else if (stage == 3) {
+                YO[off] = caxpy(dtT / T(6), cadd(av, dv), yv);
+            } else {
+                Ab[off] = caxpy(T(2), dv, av);
+                XO[off] = caxpy(aT, dv, yv);
+            }
+        }
+    };
+    // the term targets of variable k into L2 (two variables before its loads)
+    auto prefetch_targets = [&](uint32_t k) {
+        if (k >= nl) return;
+        const uint4 r = vrec[k];
+        const uint32_t u0 = (r.y >> 10) & 65535u, cnt = r.y >> 26;
+        for (uint32_t u = u0; u < u0 + cnt; ++u) asm volatile("prefetch.global.L2 [%0];" ::"l"(X + tgtat(u) * n));
+    };
+    // the three phases (P, T, S; X, Y; Z), each with two register sets in
+    // turn: variable i + 1 loads while variable i finishes
+    const uint32_t ph1 = d.row1 & 65535u, ph2 = ph1 + (d.row1 >> 16);
+    uint32_t i0 = 0;
+#pragma unroll 1
+    for (int ph = 0; ph < 3; ++ph) {
+        const uint32_t i1 = ph == 0 ? ph1 : (ph == 1 ? ph2 : nl);
+        C vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1;
+        C vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1;
+        if (i0 < i1) fetch(ph, i0, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
+        for (uint32_t i = i0; i < i1; i += 2) {
+            prefetch_targets(i + 2);
+            prefetch_targets(i + 3);
+            if (i + 1 < i1) fetch(ph, i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
+            finish(ph, i, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
+            if (i + 1 >= i1) break;
+            if (i + 2 < i1) fetch(ph, i + 2, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
+            finish(ph, i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
+        }
+        i0 = i1;
+    }
+    if (CHECK && __any_sync(0xffffffffu, bad) && lane == 0) atomicOr(P.err, 2u);
+    __syncwarp();
+    return true;
+}
+
+// The pack kernel: persistent warps drawing pack units (static striding or
+// the atomic counter), each warp with an mbarrier and pack_smem bytes of
+// shared memory; then, in the same launch and shared memory, the list units
+// of the unpacked instances, so that warps done with the (long) pack units
+// fill the tail with (short) list units.  Registers are budgeted apart from
+// the list kernel's.
+template <typename T, bool FP64SIDE, bool CHECK>
+__global__ void __maxnreg__(sizeof(T) == 8 ? 128 : 80) pack_stage_kernel(StageParams<T> P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    unsigned char* const wsm = smem + size_t(wib) * P.pack_smem;
+    uint64_t* const bar = reinterpret_cast<uint64_t*>(wsm);
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    ItemQueue Q;
+    Q.init(P.use_queue, wib);
+    uint32_t parity = 0;
+    for (;;) {
+        const unsigned int c = Q.next(P.pqueue, P.npunits, lane);
+        if (c >= P.npunits) break;
+        const uint2 un = P.punits[c];
+        if (!pack_unit<T, FP64SIDE, CHECK>(P, P.items[un.x & ~kPackUnit], un.y, wsm, bar, parity, lane)) return;
+    }
+    if (P.nchunks == 0) return;
+    // the list units' bulk copies land where the pack units wrote with
+    // ordinary stores (the mbarrier stays where it is)
+    __syncwarp();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    const ListSmem<T> S = carve_list<T>(wsm, P.chunk);
+    ItemQueue L;
+    L.init(P.use_queue, wib);
+    for (;;) {
+        const unsigned int c = L.next(P.queue, P.nchunks, lane);
+        if (c >= P.nchunks) break;
+        if (!list_unit<T, FP64SIDE, CHECK>(P, c, S, parity, lane)) return;
+    }
+}
+
+// -- end: pack kernel
 
 // ---- ELL kernel ------------------------------------------------------------
 // Grouped sums of the stage input, one thread each: R_q and C_q of every
@@ -1495,7 +1522,13 @@ static size_t stage_smem_bytes(const LaunchCfg& cfg, bool fp64) {
     else w = fp64 ? warp_smem_bytes<double>(cfg.chunk) : warp_smem_bytes<float>(cfg.chunk);
     return w * size_t(cfg.block / 32);
 }
-static size_t pack_smem_bytes(const LaunchCfg& cfg) { return size_t(cfg.pack_smem + 15) / 16 * 16 * size_t(cfg.block / 32); }
+// a pack-kernel warp's shared memory: the largest pack item's, or the list
+// units' if that is larger
+static uint32_t pack_warp_smem(const LaunchCfg& cfg, bool fp64) {
+    const size_t l = fp64 ? list_smem_bytes<double>(cfg.chunk) : list_smem_bytes<float>(cfg.chunk);
+    return uint32_t(std::max(size_t(cfg.pack_smem + 15) / 16 * 16, (l + 15) / 16 * 16));
+}
+static size_t pack_smem_bytes(const LaunchCfg& cfg, bool fp64) { return size_t(pack_warp_smem(cfg, fp64)) * size_t(cfg.block / 32); }
 
 // operand-area offsets of the list kernel for a given item capacity
 void list_operand_layout(int item, int* opR, int* opC, int* opZ, int* opZero) {
@@ -1534,14 +1567,15 @@ static cudaError_t launch_t(const StageParams<T>& p, const LaunchCfg& cfg, int n
         const unsigned grid = unsigned((size_t(p.nvar) + 31) / 32 * 32 + cfg.block - 1) / unsigned(cfg.block);
         if (grid > 0) ell_stage_kernel<T, SIDE><<<grid, cfg.block, 0, st>>>(p);
     } else if (cfg.kernel == SA_KERNEL_LISTS) {
-        // a packed handle's pack units first, then the list units of its
-        // unpacked instances, each kernel with the whole GPU
+        // a packed handle's pack units, then in the same launch the list
+        // units of its unpacked instances; otherwise the list kernel
+        const size_t psm = pack_smem_bytes(cfg, sizeof(T) == 8);
         if (s.debug & SA_DEBUG_CHECK_INDICES) {
-            if (p.npunits) pack_stage_kernel<T, SIDE, true><<<cfg.pgrid, cfg.block, pack_smem_bytes(cfg), st>>>(p);
-            if (p.nchunks) list_stage_kernel<T, SIDE, true><<<cfg.grid, cfg.block, sm, st>>>(p);
+            if (p.npunits) pack_stage_kernel<T, SIDE, true><<<cfg.pgrid, cfg.block, psm, st>>>(p);
+            else if (p.nchunks) list_stage_kernel<T, SIDE, true><<<cfg.grid, cfg.block, sm, st>>>(p);
         } else {
-            if (p.npunits) pack_stage_kernel<T, SIDE, false><<<cfg.pgrid, cfg.block, pack_smem_bytes(cfg), st>>>(p);
-            if (p.nchunks) list_stage_kernel<T, SIDE, false><<<cfg.grid, cfg.block, sm, st>>>(p);
+            if (p.npunits) pack_stage_kernel<T, SIDE, false><<<cfg.pgrid, cfg.block, psm, st>>>(p);
+            else if (p.nchunks) list_stage_kernel<T, SIDE, false><<<cfg.grid, cfg.block, sm, st>>>(p);
         }
 
     } else {
@@ -1596,7 +1630,7 @@ static StageParams<T> make_params(const StageLaunch& s, const LaunchCfg& cfg) {
     p.pcoef = static_cast<const C*>(s.pcoef);
     p.punits = static_cast<const uint2*>(s.punits);
     p.npunits = s.npunits;
-    p.pack_smem = uint32_t((cfg.pack_smem + 15) / 16 * 16);
+    p.pack_smem = pack_warp_smem(cfg, sizeof(T) == 8);
     p.pqueue = s.pqueue;
     p.nvar = s.nvar;
     p.nchunks = s.nchunks;
@@ -1637,7 +1671,7 @@ static cudaError_t occupancy_of(K kern, int block, size_t sm, int lim, int* bloc
 
 // CTAs per SM of the pack kernel (0 if its shared memory does not fit)
 cudaError_t pack_occupancy(const LaunchCfg& cfg, bool fp64, int* blocks_per_sm) {
-    const size_t sm = pack_smem_bytes(cfg);
+    const size_t sm = pack_smem_bytes(cfg, fp64);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

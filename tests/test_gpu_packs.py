@@ -34,7 +34,7 @@ def _rand(h, seed):
 @pytest.mark.parametrize("precision", [S.SA_FP64, S.SA_FP32_AUX])
 def test_packed_rhs_against_oracle(precision):
     h, sas = _setup(precision)
-    assert h.launches_per_step() == 4 * (2 if precision == S.SA_FP64 else 3)  # pack + list (+ rho_0) kernels
+    assert h.launches_per_step() == 4 * (1 if precision == S.SA_FP64 else 2)  # pack kernel with list units (+ rho_0)
     x = _rand(h, 11)
     if precision == S.SA_FP32_AUX:
         x = x.astype(np.complex64).astype(np.complex128)
