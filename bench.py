@@ -252,11 +252,12 @@ def run_reference(args):
 
 def _kernel_name(kernel, fp32, packed=False):
     """The stage kernel the step launches (the instantiation without index
-    checks); on a packed handle the pack kernel, then the list kernel for
-    the unpacked instances, make up one RK4 stage."""
+    checks); on a packed handle the pack kernel, which also runs the list
+    units of the unpacked instances."""
     args = "<float,true,false>" if fp32 else "<double,false,false>"
-    base = {1: "list_stage_kernel", 2: "ell_stage_kernel"}.get(kernel, "stage_kernel") + args
-    return "pack_stage_kernel" + args + "+" + base if packed else base
+    if packed:
+        return "pack_stage_kernel" + args
+    return {1: "list_stage_kernel", 2: "ell_stage_kernel"}.get(kernel, "stage_kernel") + args
 
 
 def run_ours(args):
@@ -320,8 +321,8 @@ def run_ours(args):
 
     # roofline of the stage kernel (4 launches per step; in FP32-aux mode the
     # small FP64 kernel of the physical density matrix overlaps each of them
-    # on a side stream; on a packed handle a "launch" is one RK4 stage, the
-    # pack kernel followed by the list kernel of the unpacked instances)
+    # on a side stream; on a packed handle the stage kernel is the pack
+    # kernel, which runs the unpacked instances' list units after its packs)
     launch_ms = ms_step / 4.0
     bytes_launch = FP32_BYTES_PER_VAR_STEP * n_vars / 4.0 if precision == S.SA_FP32_AUX else \
         FP64_BYTES_PER_VAR_STEP * n_vars / 4.0

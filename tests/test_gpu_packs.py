@@ -68,6 +68,27 @@ def test_packed_rk4_against_unpacked_and_oracle():
 
 
 @pytest.mark.parametrize("precision", [S.SA_FP64, S.SA_FP32_AUX])
+def test_packed_tuning_invariance(precision):
+    """The pack kernel takes the list units of the unpacked instances after its
+    pack units, from the atomic counter or by static striding: every block
+    size, item size and queue mode gives the same bits (no sum depends on
+    which warp evaluates an item)."""
+    h, _ = _setup(precision)
+    x = _rand(h, 13)
+    out = []
+    for (b, c, q) in [(128, 192, 1), (128, 192, 0), (64, 160, 1), (256, 128, 0), (96, 96, 1)]:
+        h.set_tuning(b, c, q)
+        st = h.new_state()
+        h.upload(st, x)
+        h.propagate(st, 0.05, 6, observe=False)
+        torch.cuda.synchronize()
+        out.append(h.download(st))
+    h.device_error()  # raises if a wait expired or an index was out of range
+    for o in out[1:]:
+        assert np.array_equal(o, out[0])
+
+
+@pytest.mark.parametrize("precision", [S.SA_FP64, S.SA_FP32_AUX])
 def test_packed_marshalling_and_element_index(precision):
     h, _ = _setup(precision)
     x = _rand(h, 13)
