@@ -936,9 +936,9 @@ __global__ void __maxnreg__(sizeof(T) == 8 ? 104 : 80) list_stage_kernel(StagePa
 //    uvar-up, uvar-down) and the fused RK4 update.  Within a phase the loads
 //    of the next variable (its value, operands, y, accumulator and first two
 //    terms) are issued before the current one is finished, so two
-//    variables' memory latencies overlap; the term targets of the two
-//    variables after those are prefetched into L2, and the item's value, y
-//    and accumulator blocks are prefetched into L2 when the unit starts.
+//    variables' memory latencies overlap.  (L2 prefetches of the item's
+//    blocks or of the next variables' targets measured slower: with the
+//    list units in the same launch, L2 capacity is what they take.)
 // Returns false when the bounded wait for the tables expired (error bit set,
 // the copy drained).
 template <typename T, bool FP64SIDE, bool CHECK>
@@ -957,12 +957,6 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, d.blob_bytes);
         bulk_g2s(blob, P.blobs + size_t(d.blob16) * 16, d.blob_bytes, bar);
-    } else if (lane <= 3 && (lane == 3 || P.stage > 0)) {
-        // the item's y, accumulator and stage-input blocks (contiguous in the
-        // pack) into L2
-        const C* const src = lane == 1 ? P.y : (lane == 2 ? static_cast<const C*>(P.acc) : P.x_in);
-        const Span t = span(src, size_t(pk.base) + size_t(d.v0) * n, d.nv * n, sizeof(C));
-        if (t.bytes) bulk_prefetch_l2(t.src, t.bytes);
     }
     // the lane's instance constants while the copy is in flight
     const InstK<T>* const ik = P.instk + P.pk_inst[pk.lane0 + ll];
@@ -1094,13 +1088,6 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
             }
         }
     };
-    // the term targets of variable k into L2 (two variables before its loads)
-    auto prefetch_targets = [&](uint32_t k) {
-        if (k >= nl) return;
-        const uint4 r = vrec[k];
-        const uint32_t u0 = (r.y >> 10) & 65535u, cnt = r.y >> 26;
-        for (uint32_t u = u0; u < u0 + cnt; ++u) asm volatile("prefetch.global.L2 [%0];" ::"l"(X + tgtat(u) * n));
-    };
     // the three phases (P, T, S; X, Y; Z), each with two register sets in
     // turn: variable i + 1 loads while variable i finishes
     const uint32_t ph1 = d.row1 & 65535u, ph2 = ph1 + (d.row1 >> 16);
@@ -1112,8 +1099,6 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
         C vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1;
         if (i0 < i1) fetch(ph, i0, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
         for (uint32_t i = i0; i < i1; i += 2) {
-            prefetch_targets(i + 2);
-            prefetch_targets(i + 3);
             if (i + 1 < i1) fetch(ph, i + 1, vB, oaB, obB, yB, aB, xB0, cB0, xB1, cB1);
             finish(ph, i, vA, oaA, obA, yA, aA, xA0, cA0, xA1, cA1);
             if (i + 1 >= i1) break;
