@@ -195,8 +195,9 @@ int sa_heom_counts(const sa_params* p, sa_counts* out);
  * The handle owns everything it allocates until sa_heom_destroy.
  * flags: SA_BUILD_HOST_ONLY (tables on the host only, for the dumps), and
  * SA_BUILD_PACK_INSTANCES (the packed device layout described at the top;
- * the list kernel then evaluates one template item for all lanes of a pack
- * at once, and sa_heom_set_kernel accepts SA_KERNEL_LISTS only).
+ * the list kernel's launch then evaluates one template item for all lanes
+ * of a pack at once, followed in the same launch by the list units of the
+ * unpacked instances, and sa_heom_set_kernel accepts SA_KERNEL_LISTS only).
  * Errors: INVALID_ARG (unknown flag too), UNSUPPORTED (more than 2^32 - 1
  * variables or records), OOM, CUDA.
  */
@@ -581,9 +582,9 @@ int sa_heom_get_tuning(const sa_heom* h, int* out);
 
 /* Kernel launches one RK4 step issues: 4 stage kernels (SA_FP64), or 4 stage
  * kernels each with the FP64 physical-representative kernel (SA_FP32_AUX);
- * SA_KERNEL_ELL adds a grouped-sum kernel before each stage kernel, and a
- * packed handle's stage is the pack kernel plus (when some instances are
- * not packed) the list kernel. */
+ * SA_KERNEL_ELL adds a grouped-sum kernel before each stage kernel; a
+ * packed handle's stage kernel is the pack kernel, which also runs the list
+ * units of the instances left unpacked. */
 int sa_heom_launches_per_step(const sa_heom* h);
 
 /*

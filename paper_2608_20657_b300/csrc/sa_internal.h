@@ -214,7 +214,7 @@ constexpr int kMaxItemVars = 1024; // variables per work item (10-bit local inde
 struct PackDev {
     uint32_t base, n, cbase, lane0;
 };
-constexpr int kPackMin = 16;   // fewer lanes than this go to the list kernel (a pack warp costs about as much per variable as 10-13 list lanes)
+constexpr int kPackMin = 16;   // fewer lanes than this stay unpacked, for list units (packs from 8, 12 or 24 lanes measured no faster)
 constexpr int kPackLanes = 32; // instances per pack at most
 
 // Byte offsets of the sections of a pack item's table blob (every section
