@@ -233,14 +233,21 @@ int sa_heom_state_index(const sa_heom* h, int inst, int64_t var, int64_t* out);
  *   blobs  uint8[blob bytes]: every work item's table blob, at 16 times
  *          its blob field (sa_heom_dump_lists items).  A pack item's blob
  *          holds, each section starting on a 16-byte boundary after a
- *          16-byte header: per pattern (var_rel u16, cat_rel u16, G u8,
- *          tier u8, 0 u16); per pattern -Gamma_Lambda (re, im) in the
- *          handle's auxiliary precision; per category the multiplicity in
- *          that precision (-r for the zero category, whose M_0 = N - r);
- *          per category its T-rank (u8, 31: no T variable); per item-local
- *          variable the first of its terms (u16, variables + 1 entries); per
- *          term the instance-relative target (u32), then per term the
- *          coefficient slot (u16).
+ *          16-byte header (u32 nw, the number of weights; the rest
+ *          reserved): per pattern (var_rel u16, cat_rel u16, G u8, tier u8,
+ *          0 u16); per pattern -Gamma_Lambda (re, im) in the handle's
+ *          auxiliary precision; per category the multiplicity in that
+ *          precision (-r for the zero category, whose M_0 = N - r); per
+ *          variable the pack kernel updates a 16-byte record, in three
+ *          phases (P, T, S; X, Y; Z): x = operand codes a | b << 11 of
+ *          -i g (op[a] - op[b]) | diagonal class << 22 | pattern << 25,
+ *          y = item-local variable | first term << 10 | term count << 26,
+ *          z, w = grouped-sum contributions, each sum slot | weight index
+ *          << 11 (operand codes and slots: below nv an item variable, then
+ *          R and C per category, Z per pattern, zero); per term the
+ *          instance-relative target (u32), then per term the coefficient
+ *          slot (u16); then the nw distinct weights a + b N as int32 pairs
+ *          (a, b), N the lane's molecule count.
  */
 int sa_heom_dump_packs(const sa_heom* h, int64_t* sizes, uint32_t* packs, uint32_t* lanes, uint8_t* blobs);
 

@@ -536,6 +536,30 @@ void pattern_diag(const sa_heom* h, uint32_t p, V* e) {
 // a pack item (r0) rather than a list item of the work-item table
 constexpr uint32_t kPackItemMark = 0xffffffffu;
 
+// Grouped-sum weights a + b N of the patterns p0 .. p1 - 1 of template
+// representative r, appended to w where new: 1 (a = 1, b = 0) first, then per
+// category M_q, M_q - 1 and -M_q, the zero category's M_0 = N - r being
+// a = -r, b = 1.  The pack kernel evaluates each once per unit and lane.
+static void pack_weights(const sa_heom* h, int r, int64_t p0, int64_t p1,
+                         std::vector<std::pair<int64_t, int64_t>>& w) {
+    const HostInstance& hi = h->inst[r];
+    const uint32_t cb = h->hdr[h->instdev[r].pat_begin].cat_off;
+    auto add = [&](int64_t a, int64_t b) {
+        for (const auto& e : w)
+            if (e.first == a && e.second == b) return;
+        w.emplace_back(a, b);
+    };
+    add(1, 0);
+    for (int64_t p = p0; p < p1; ++p)
+        for (uint32_t c = h->hdr[p].cat_off; c < h->hdr[p + 1].cat_off; ++c) {
+            const size_t gc = size_t(c - cb);
+            const int64_t mt = tmpl_mult(hi, gc), zb = hi.cat_vec[gc] == 0 ? 1 : 0;
+            add(mt, zb);
+            add(mt - 1, zb);
+            add(-mt, -zb);
+        }
+}
+
 // Blob of a pack item (PackLayout): patterns, -Gamma_Lambda per pattern, the
 // template's multiplicities, and per variable the warp updates a record --
 // commutator operands, class and pattern (as list_item resolves them,
@@ -548,12 +572,16 @@ int pack_blob(const sa_heom* h, ItemDesc& d, uint8_t* o) {
     ListItem W;
     list_item(h, d, W);
     const bool side64 = h->precision == SA_FP32_AUX;
-    // contribution word: sum slot and the weight a + b N (kind 1 one, 2 M_c,
-    // 3 M_c - 1, 4 -M_c of item category c; b = 1 or -1 only for the zero
-    // category, whose M_0 = N - r is stored as -r): slot | (b + 1) << 12 |
-    // (a + 32768) << 14
-    const HostInstance& hrw = h->inst[h->hdr[d.p0].inst];
-    const uint32_t cbw = h->hdr[h->instdev[h->hdr[d.p0].inst].pat_begin].cat_off;
+    // contribution word: sum slot | the index of its weight a + b N in the
+    // item's weight list << 11 (kind 1 one, 2 M_c, 3 M_c - 1, 4 -M_c of item
+    // category c; b = 1 or -1 only for the zero category, whose M_0 = N - r
+    // is stored as -r)
+    const int rw = int(h->hdr[d.p0].inst);
+    const HostInstance& hrw = h->inst[rw];
+    const uint32_t cbw = h->hdr[h->instdev[rw].pat_begin].cat_off;
+    std::vector<std::pair<int64_t, int64_t>> wl;
+    pack_weights(h, rw, d.p0, int64_t(d.p0) + d.np, wl);
+    if (wl.size() != d.nw) return fail(SA_ERR_STATE, "pack item weights differ from its budget");
     auto cw = [&](uint32_t slot, uint32_t kind, uint32_t c) {
         const size_t gc = size_t(d.c0 + c - cbw);
         const int64_t mt = tmpl_mult(hrw, gc);  // M, or -r for the zero category
@@ -562,7 +590,9 @@ int pack_blob(const sa_heom* h, ItemDesc& d, uint8_t* o) {
         if (kind == 2) a = mt, b = zb;
         if (kind == 3) a = mt - 1, b = zb;
         if (kind == 4) a = -mt, b = -zb;
-        return slot | uint32_t(b + 1) << 12 | uint32_t(a + 32768) << 14;
+        uint32_t k = 0;
+        while (wl[k].first != a || wl[k].second != b) ++k;  // listed by pack_weights
+        return slot | k << 11;
     };
     struct Rec {
         uint32_t l, z, w;
@@ -597,7 +627,15 @@ int pack_blob(const sa_heom* h, ItemDesc& d, uint8_t* o) {
     d.row0 = nterm;
     if (ph[0].size() > 65535u || ph[1].size() > 65535u)
         return fail(SA_ERR_UNSUPPORTED, "a pack item has too many variables");
-    const PackLayout B = pack_layout<V>(d.np, d.ncat, d.nl, nterm);
+    const PackLayout B = pack_layout<V>(d.np, d.ncat, d.nl, nterm, d.nw);
+    reinterpret_cast<uint32_t*>(o)[0] = d.nw;
+    int32_t* wab = reinterpret_cast<int32_t*>(o + B.wab);
+    for (uint32_t k = 0; k < d.nw; ++k) {
+        if (wl[k].first < INT32_MIN || wl[k].first > INT32_MAX)
+            return fail(SA_ERR_UNSUPPORTED, "a grouped-sum weight is beyond 32 bits");
+        wab[2 * k] = int32_t(wl[k].first);
+        wab[2 * k + 1] = int32_t(wl[k].second);
+    }
     ItemPat* phd = reinterpret_cast<ItemPat*>(o + B.pat);
     V* pd = reinterpret_cast<V*>(o + B.pd);
     V* cM = reinterpret_cast<V*>(o + B.cM);
@@ -662,9 +700,9 @@ int build_blobs(sa_heom* h) {
         const bool pk = d.r0 == kPackItemMark;
         // (a pack blob is sized for all nv variables and row0 terms; the
         // builder may update fewer)
-        const uint32_t bytes = pk ? pack_layout<V>(d.np, d.ncat, d.nv, d.row0).bytes
+        const uint32_t bytes = pk ? pack_layout<V>(d.np, d.ncat, d.nv, d.row0, d.nw).bytes
                                   : blob_layout<V>(d.np, d.ncat, d.nl).bytes;
-        if (pk) max_pack = std::max(max_pack, pack_sums_bytes<V>(d.np, d.ncat) + bytes);
+        if (pk) max_pack = std::max(max_pack, pack_sums_bytes<V>(d.np, d.ncat) + bytes + pack_wtab_bytes<V>(d.nw));
         d.blob16 = uint32_t(off16);
         d.blob_bytes = bytes;
         off16 += bytes / 16;
@@ -676,7 +714,8 @@ int build_blobs(sa_heom* h) {
         return fail(SA_ERR_OOM, "host memory for the list-kernel blobs");
     }
     // a pack-kernel warp: mbarrier, 5 x 32 per-lane diagonal parts, then the
-    // item's grouped sums followed by its blob (the largest item sets the size)
+    // item's grouped sums, its blob and its per-lane weights (the largest item
+    // sets the size)
     h->pack_smem = max_pack ? 16u + uint32_t(5 * 32 * 2 * sizeof(V)) + max_pack : 0u;
     int prc = SA_OK;
 #pragma omp parallel for schedule(dynamic, 256)
@@ -736,10 +775,11 @@ uint64_t list_item_rows(const ListItem& W) {
 }
 
 // Pack items (SA_KERNEL_LISTS on a packed handle): per packed template, runs
-// of its representative's consecutive patterns whose blob (PackLayout) and
-// grouped sums stay within kPackItemTarget bytes; a pattern larger than that
-// gets an item of its own.  nl holds the variables the warp updates, row0
-// the item's term count, r0 the pack-item mark.
+// of its representative's consecutive patterns whose blob (PackLayout),
+// grouped sums and per-lane weights stay within kPackItemTarget bytes; a
+// pattern larger than that gets an item of its own.  nl holds the variables
+// the warp updates, row0 the item's term count, nw its weights, r0 the
+// pack-item mark.
 template <typename V>
 int pack_items(const sa_heom* h, std::vector<ItemDesc>& out) {
     const bool side64 = h->precision == SA_FP32_AUX;
@@ -761,12 +801,16 @@ int pack_items(const sa_heom* h, std::vector<ItemDesc>& out) {
         while (p < pe) {
             int64_t q = p;
             uint32_t np = 0, ncat = 0, nv = 0, nterm = 0;
+            std::vector<std::pair<int64_t, int64_t>> wl, wq;  // the item's weights, with pattern q
             while (q < pe) {
                 const uint32_t u = h->hdr[q + 1].var_off - h->hdr[q].var_off;
                 const uint32_t c = h->hdr[q + 1].cat_off - h->hdr[q].cat_off;
                 const uint32_t t = nt[size_t(q - pb)];
-                const uint32_t bytes = pack_layout<V>(np + 1, ncat + c, nv + u, nterm + t).bytes +
-                                       pack_sums_bytes<V>(np + 1, ncat + c);
+                wq = wl;
+                pack_weights(h, r, q, q + 1, wq);
+                const uint32_t nw = uint32_t(wq.size());
+                const uint32_t bytes = pack_layout<V>(np + 1, ncat + c, nv + u, nterm + t, nw).bytes +
+                                       pack_sums_bytes<V>(np + 1, ncat + c) + pack_wtab_bytes<V>(nw);
                 // operand codes below 2048, pattern index below 16, and the
                 // list kernel's operand layout for the item capacity (which
                 // list_item resolves the operands in)
@@ -777,6 +821,7 @@ int pack_items(const sa_heom* h, std::vector<ItemDesc>& out) {
                 ncat += c;
                 nv += u;
                 nterm += t;
+                wl.swap(wq);
                 ++q;
             }
             if (nterm > 65535u || nv > uint32_t(h->chunk) || int(ncat) > ncat_cap ||
@@ -791,6 +836,7 @@ int pack_items(const sa_heom* h, std::vector<ItemDesc>& out) {
             d.ncat = ncat;
             d.nl = nv;      // variables the warp updates (the blob builder leaves out integrated ones)
             d.row0 = nterm;
+            d.nw = uint32_t(wl.size());
             d.r0 = kPackItemMark;
             out.push_back(d);
             p = q;

@@ -970,7 +970,7 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
     }
     parity ^= 1u;
     const uint32_t np = d.np, ncat = d.ncat, nv = d.nv, nl = d.nl;
-    const PackLayout B = pack_layout<T>(np, ncat, nl, d.row0);
+    const PackLayout B = pack_layout<T>(np, ncat, nl, d.row0, d.nw);
     const C* const pd = reinterpret_cast<const C*>(blob + B.pd);
     const uint4* const vrec = reinterpret_cast<const uint4*>(blob + B.vrec);
     const uint32_t* const tgt0 = reinterpret_cast<const uint32_t*>(blob + B.tgt);
@@ -1005,9 +1005,20 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
     C* const sl = sums + lane;
     const uint32_t nsums = 2 * ncat + np + 1;
     for (uint32_t k = 0; k < nsums; ++k) sl[k * 32] = mk(T(0), T(0));
-    // weight of a grouped-sum contribution: a + b N (b = 0 but for the zero
-    // category, whose multiplicity is N - r)
-    auto weight = [&](uint32_t w) { return fma(T(int((w >> 12) & 3u) - 1), Nt, T(int((w >> 14) & 65535u) - 32768)); };
+    // the grouped-sum weight a + b N of a contribution for the lane's
+    // instance (b = 0 but for the zero category, whose multiplicity is
+    // N - r), named by its index in the item's weight list: in FP64 looked up
+    // in a per-lane table evaluated once per unit (one column per lane after
+    // the blob), in FP32 evaluated where it is used
+    const int2* const wab = reinterpret_cast<const int2*>(blob + B.wab);
+    T* const wt = reinterpret_cast<T*>(blob + d.blob_bytes) + lane;
+    if constexpr (sizeof(T) == 8)
+        for (uint32_t k = 0; k < d.nw; ++k) wt[k * 32] = fma(T(wab[k].y), Nt, T(wab[k].x));
+    auto weight = [&](uint32_t w) {
+        if constexpr (sizeof(T) == 8) return wt[(w >> 11) * 32];
+        const int2 e = wab[w >> 11];
+        return fma(T(e.y), Nt, T(e.x));
+    };
     const C* __restrict__ Yb = P.y + lb;
     C* const Ab = P.acc + lb;
     C* const XO = P.x_out + lb;

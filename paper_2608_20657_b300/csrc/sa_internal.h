@@ -140,6 +140,7 @@ struct ItemDesc {
     uint32_t row0, row1;  // list kernel: the item's term rows
     uint32_t blob16;      // list kernel: the item's table blob, in 16-byte units
     uint32_t blob_bytes;
+    uint32_t nw;          // pack items: distinct grouped-sum weights a + b N (0 otherwise)
 };
 
 // Per-instance constants of the list kernel (T = float or double): where the
@@ -218,11 +219,14 @@ constexpr int kPackMin = 16;   // fewer lanes than this stay unpacked, for list 
 constexpr int kPackLanes = 32; // instances per pack at most
 
 // Byte offsets of the sections of a pack item's table blob (every section
-// 16-byte aligned): a 16-byte header (reserved); patterns (ItemPat); per
+// 16-byte aligned): a 16-byte header (u32 nw, then reserved); patterns (ItemPat); per
 // pattern -Gamma_Lambda (complex T); per category the multiplicity (T, as in
 // the list blobs); per variable the warp updates a uint4 record; then per
 // term the target (instance-relative variable, u32), then per term the
-// coefficient slot (u16), the variables' terms one after another.
+// coefficient slot (u16), the variables' terms one after another; then the
+// item's nw distinct grouped-sum weights a + b N as (a, b) int32 pairs, N the
+// instance's molecule count: 1, M_q, M_q - 1 and -M_q of its categories, where
+// M of the zero category is N - r (a = -r, b = 1).
 // The records come in three phases -- the P, T and S variables, then the X
 // and Y variables, then the Z variables, each in canonical order (the
 // physical representative left out in SA_FP32_AUX mode) -- so that the
@@ -235,19 +239,18 @@ constexpr int kPackLanes = 32; // instances per pack at most
 //      4 P) and pattern (25-29);
 //   y: item-local index (bits 0-9), first term (10-25), number of terms (26-31);
 //   z, w: the contributions (two for P, T, S; one, in z, for X and Y; none
-//      for Z), each a sum slot (bits 0-10) and its weight a + b N (bits
-//      12-13: b + 1; bits 14-29: a + 32768), N the instance's molecule count:
-//      1 for P_q, M_q - 1 for T_q, M_b and M_q for S_{q,b}, M_q and -M_q for
-//      X_q and Y_q, where M of the zero category is N - r (b = 1).
+//      for Z), each a sum slot (bits 0-10) and the index of its weight
+//      (bits 11-31): 1 for P_q, M_q - 1 for T_q, M_b and M_q for S_{q,b},
+//      M_q and -M_q for X_q and Y_q.
 // Operand codes and sum slots: below nv an item variable; nv + c (slot c)
 // the row sum R of category c, nv + ncat + c its column sum C,
 // nv + 2 ncat + j the Z sum of pattern j, nv + 2 ncat + np zero.  The sums
 // live in the warp's shared memory, one column per lane.
 struct PackLayout {
-    uint32_t pat, pd, cM, vrec, tgt, tsl, bytes;
+    uint32_t pat, pd, cM, vrec, tgt, tsl, wab, bytes;
 };
 template <typename T>
-SA_HOST_DEVICE inline PackLayout pack_layout(uint32_t np, uint32_t ncat, uint32_t nl, uint32_t nterm) {
+SA_HOST_DEVICE inline PackLayout pack_layout(uint32_t np, uint32_t ncat, uint32_t nl, uint32_t nterm, uint32_t nw) {
     auto a16 = [](uint32_t b) { return (b + 15u) & ~15u; };
     PackLayout L;
     L.pat = 16;
@@ -256,15 +259,23 @@ SA_HOST_DEVICE inline PackLayout pack_layout(uint32_t np, uint32_t ncat, uint32_
     L.vrec = L.cM + a16(ncat * uint32_t(sizeof(T)));
     L.tgt = L.vrec + nl * 16u;
     L.tsl = L.tgt + a16(nterm * 4u);
-    L.bytes = L.tsl + a16(nterm * 2u);
+    L.wab = L.tsl + a16(nterm * 2u);
+    L.bytes = L.wab + a16(nw * 8u);
     return L;
+}
+// the per-lane values of a pack item's grouped-sum weights, after its blob
+// (FP64 only: there the two conversions and the multiply-add of a weight,
+// done per contribution, cost more of the FP64 pipe than the table's shared
+// memory; FP32 evaluates them per contribution and keeps its items larger)
+template <typename T> SA_HOST_DEVICE inline uint32_t pack_wtab_bytes(uint32_t nw) {
+    return sizeof(T) == 8 ? nw * 32u * uint32_t(sizeof(T)) : 0u;
 }
 // grouped sums of a pack item in the warp's shared memory: R and C per
 // category, Z per pattern and a zero, one complex T per lane each
 template <typename T> SA_HOST_DEVICE inline uint32_t pack_sums_bytes(uint32_t np, uint32_t ncat) {
     return (2u * ncat + np + 1u) * 32u * uint32_t(2 * sizeof(T));
 }
-// pack items are cut so that their blob and sums stay below this many bytes
+// pack items are cut so that their blob, sums and weights stay below this many bytes
 // (a pattern that alone exceeds it gets an item of its own)
 template <typename T> constexpr uint32_t kPackItemTarget = sizeof(T) == 8 ? 12288u : 6144u;
 constexpr uint32_t kPackUnit = 0x80000000u;  // work-unit flag: (pack item, pack) rather than (item, instance)

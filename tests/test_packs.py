@@ -77,14 +77,15 @@ def test_pack_layout_is_an_interleaved_bijection():
     assert u.config_hash() != h.config_hash()
 
 
-def _pack_layout(np_, ncat, nl, nterm, sz):
+def _pack_layout(np_, ncat, nl, nterm, nw, sz):
     L = {"pat": 16}
     L["pd"] = L["pat"] + A16(np_ * 8)
     L["cM"] = L["pd"] + A16(np_ * 2 * sz)
     L["vrec"] = L["cM"] + A16(ncat * sz)
     L["tgt"] = L["vrec"] + nl * 16
     L["tsl"] = L["tgt"] + A16(nterm * 4)
-    L["bytes"] = L["tsl"] + A16(nterm * 2)
+    L["wab"] = L["tsl"] + A16(nterm * 2)
+    L["bytes"] = L["wab"] + A16(nw * 8)
     return L
 
 
@@ -111,14 +112,17 @@ def _eval_packs(h, specs, sas, x, out, precision):
         p0, np_, v0, nv, c0, ncat, r0, nl, b16, bb = (int(v) for v in items[int(c) & ~PACK_UNIT])
         assert r0 == 0xffffffff
         blob = blobs[16 * b16:16 * b16 + bb]
-        B0 = _pack_layout(np_, ncat, nl, 0, sz)
+        nw = int(np.frombuffer(blob[:4].tobytes(), "<u4")[0])
+        B0 = _pack_layout(np_, ncat, nl, 0, 0, sz)
         vrec = np.frombuffer(blob[B0["vrec"]:B0["vrec"] + 16 * nl].tobytes(), "<u4").astype(np.int64).reshape(-1, 4)
         cnts = vrec[:, 1] >> 26
         starts = (vrec[:, 1] >> 10) & 65535
         nterm = int(cnts.sum())
         assert np.array_equal(starts, np.concatenate([[0], np.cumsum(cnts)[:-1]]))  # terms one variable after another
-        B = _pack_layout(np_, ncat, nl, nterm, sz)
+        B = _pack_layout(np_, ncat, nl, nterm, nw, sz)
         assert B["bytes"] <= bb
+        wab = np.frombuffer(blob[B["wab"]:B["wab"] + 8 * nw].tobytes(), "<i4").astype(np.int64).reshape(-1, 2)
+        assert len({(int(a_), int(b_)) for a_, b_ in wab}) == nw  # distinct weights
         ph = np.frombuffer(blob[B["pat"]:B["pat"] + 8 * np_].tobytes(), PAT)
         pd = np.frombuffer(blob[B["pd"]:B["pd"] + 2 * sz * np_].tobytes(), ft).astype(float).view(complex)
         cM = np.frombuffer(blob[B["cM"]:B["cM"] + sz * ncat].tobytes(), ft).astype(float)
@@ -160,7 +164,9 @@ def _eval_packs(h, specs, sas, x, out, precision):
                 a, bo, cls, jj = w & 2047, (w >> 11) & 2047, (w >> 22) & 7, (w >> 25) & 31
                 ncon = (2, 1, 0)[phase[idx]]  # P, T, S enter two sums, X and Y one, Z none
                 for con in (int(wz), int(ww))[:ncon]:
-                    slot, bb, aa = con & 2047, ((con >> 12) & 3) - 1, ((con >> 14) & 65535) - 32768
+                    slot, kw_ = con & 2047, con >> 11
+                    assert kw_ < nw
+                    aa, bb = (int(v_) for v_ in wab[kw_])
                     sums[slot] += (aa + bb * N) * xi[l]
                     done[slot] = max(done[slot], phase[idx])
                 for opc in (a, bo):
@@ -214,17 +220,23 @@ def test_packed_handle_refuses_other_kernels():
     h.set_kernel(S.SA_KERNEL_LISTS)  # still usable
 
 
-def test_pack_items_respect_the_budget():
-    """Every pack item's blob and grouped sums fit the per-warp budget (or the
-    item holds one pattern), with at most 16 patterns."""
-    h = _handle(_batch(), S.SA_FP32_AUX)
+@pytest.mark.parametrize("precision", [S.SA_FP32_AUX, S.SA_FP64])
+def test_pack_items_respect_the_budget(precision):
+    """Every pack item's blob, grouped sums and (FP64) per-lane weight table
+    fit the per-warp budget -- 6 KB in FP32, 12 KB in FP64 -- or the item
+    holds one pattern, with at most 16 patterns."""
+    h = _handle(_batch(), precision)
     h.set_kernel(S.SA_KERNEL_LISTS)
     L = h.dump_lists()
     n = 0
+    blobs = h.dump_packs()["blobs"]
+    cs, budget, wtab = (8, 6144, 0) if precision == S.SA_FP32_AUX else (16, 12288, 8)
     for it in L["items"]:
         if int(it[6]) == 0xffffffff:
             n += 1
-            sums = (2 * int(it[5]) + int(it[1]) + 1) * 32 * 8
-            assert int(it[9]) + sums <= 6144 or int(it[1]) == 1
+            sums = (2 * int(it[5]) + int(it[1]) + 1) * 32 * cs
+            nw = int(np.frombuffer(blobs[16 * int(it[8]):16 * int(it[8]) + 4].tobytes(), "<u4")[0])
+            assert nw >= 1
+            assert int(it[9]) + sums + nw * 32 * wtab <= budget or int(it[1]) == 1
             assert int(it[1]) <= 16
     assert n > 0
