@@ -702,7 +702,9 @@ int build_blobs(sa_heom* h) {
         // builder may update fewer)
         const uint32_t bytes = pk ? pack_layout<V>(d.np, d.ncat, d.nv, d.row0, d.nw).bytes
                                   : blob_layout<V>(d.np, d.ncat, d.nl).bytes;
-        if (pk) max_pack = std::max(max_pack, pack_sums_bytes<V>(d.np, d.ncat) + bytes + pack_wtab_bytes<V>(d.nw));
+        if (pk)
+            max_pack = std::max(max_pack, pack_sums_bytes<V>(d.np, d.ncat) + bytes + pack_wtab_bytes<V>(d.nw) +
+                                              pack_dtab_bytes<V>(d.np));
         d.blob16 = uint32_t(off16);
         d.blob_bytes = bytes;
         off16 += bytes / 16;
@@ -714,8 +716,8 @@ int build_blobs(sa_heom* h) {
         return fail(SA_ERR_OOM, "host memory for the list-kernel blobs");
     }
     // a pack-kernel warp: mbarrier, 5 x 32 per-lane diagonal parts, then the
-    // item's grouped sums, its blob and its per-lane weights (the largest item
-    // sets the size)
+    // item's grouped sums, its blob, its per-lane weights and diagonals (the
+    // largest item sets the size)
     h->pack_smem = max_pack ? 16u + uint32_t(5 * 32 * 2 * sizeof(V)) + max_pack : 0u;
     int prc = SA_OK;
 #pragma omp parallel for schedule(dynamic, 256)
@@ -810,7 +812,8 @@ int pack_items(const sa_heom* h, std::vector<ItemDesc>& out) {
                 pack_weights(h, r, q, q + 1, wq);
                 const uint32_t nw = uint32_t(wq.size());
                 const uint32_t bytes = pack_layout<V>(np + 1, ncat + c, nv + u, nterm + t, nw).bytes +
-                                       pack_sums_bytes<V>(np + 1, ncat + c) + pack_wtab_bytes<V>(nw);
+                                       pack_sums_bytes<V>(np + 1, ncat + c) + pack_wtab_bytes<V>(nw) +
+                                       pack_dtab_bytes<V>(np + 1);
                 // operand codes below 2048, pattern index below 16, and the
                 // list kernel's operand layout for the item capacity (which
                 // list_item resolves the operands in)

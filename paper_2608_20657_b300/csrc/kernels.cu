@@ -1019,6 +1019,16 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
         const int2 e = wab[w >> 11];
         return fma(T(e.y), Nt, T(e.x));
     };
+    // the diagonal coefficient of pattern j and class cl (-Gamma_Lambda plus
+    // the instance's part): in FP64 from a per-lane table after the weights,
+    // in FP32 added where it is used
+    C* const dtab = reinterpret_cast<C*>(blob + d.blob_bytes + pack_wtab_bytes<T>(d.nw)) + lane;
+    if constexpr (sizeof(T) == 8)
+        for (uint32_t e = 0; e < 5 * np; ++e) dtab[e * 32] = cadd(pd[e / 5], ccs[(e % 5) * 32 + lane]);
+    auto diag = [&](uint32_t j, uint32_t cl) {
+        if constexpr (sizeof(T) == 8) return dtab[(j * 5 + cl) * 32];
+        return cadd(pd[j], ccs[cl * 32 + lane]);
+    };
     const C* __restrict__ Yb = P.y + lb;
     C* const Ab = P.acc + lb;
     C* const XO = P.x_out + lb;
@@ -1071,7 +1081,7 @@ __device__ __forceinline__ bool pack_unit(const StageParams<T>& P, const ItemDes
         if (ph == 0) sl[(r.w & 2047u) * 32] = caxpy(weight(r.w), v, sl[(r.w & 2047u) * 32]);
         const uint32_t off = iv0 + (r.y & 1023u) * n;
         const uint32_t u0 = (r.y >> 10) & 65535u, u1 = u0 + (r.y >> 26);
-        const C dgl = cadd(pd[(r.x >> 25) & 31u], ccs[((r.x >> 22) & 7u) * 32 + lane]);
+        const C dgl = diag((r.x >> 25) & 31u, (r.x >> 22) & 7u);
         const C t = csub(oa, ob);
         C dv = mk(g * t.y, -g * t.x);
         dv = cfma(dgl, v, dv);

@@ -270,6 +270,12 @@ SA_HOST_DEVICE inline PackLayout pack_layout(uint32_t np, uint32_t ncat, uint32_
 template <typename T> SA_HOST_DEVICE inline uint32_t pack_wtab_bytes(uint32_t nw) {
     return sizeof(T) == 8 ? nw * 32u * uint32_t(sizeof(T)) : 0u;
 }
+// and, after those, the per-lane diagonal coefficient of every (pattern,
+// variable class) of the item, likewise FP64 only (the two additions of a
+// variable's diagonal, done once per unit)
+template <typename T> SA_HOST_DEVICE inline uint32_t pack_dtab_bytes(uint32_t np) {
+    return sizeof(T) == 8 ? np * 5u * 32u * uint32_t(2 * sizeof(T)) : 0u;
+}
 // grouped sums of a pack item in the warp's shared memory: R and C per
 // category, Z per pattern and a zero, one complex T per lane each
 template <typename T> SA_HOST_DEVICE inline uint32_t pack_sums_bytes(uint32_t np, uint32_t ncat) {

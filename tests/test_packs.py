@@ -222,8 +222,8 @@ def test_packed_handle_refuses_other_kernels():
 
 @pytest.mark.parametrize("precision", [S.SA_FP32_AUX, S.SA_FP64])
 def test_pack_items_respect_the_budget(precision):
-    """Every pack item's blob, grouped sums and (FP64) per-lane weight table
-    fit the per-warp budget -- 6 KB in FP32, 12 KB in FP64 -- or the item
+    """Every pack item's blob, grouped sums and (FP64) per-lane weight and
+    diagonal tables fit the per-warp budget -- 6 KB in FP32, 12 KB in FP64 -- or the item
     holds one pattern, with at most 16 patterns."""
     h = _handle(_batch(), precision)
     h.set_kernel(S.SA_KERNEL_LISTS)
@@ -237,6 +237,7 @@ def test_pack_items_respect_the_budget(precision):
             sums = (2 * int(it[5]) + int(it[1]) + 1) * 32 * cs
             nw = int(np.frombuffer(blobs[16 * int(it[8]):16 * int(it[8]) + 4].tobytes(), "<u4")[0])
             assert nw >= 1
-            assert int(it[9]) + sums + nw * 32 * wtab <= budget or int(it[1]) == 1
+            dtab = int(it[1]) * 5 * 32 * 2 * wtab  # (FP64) per-lane diagonal per pattern and class
+            assert int(it[9]) + sums + nw * 32 * wtab + dtab <= budget or int(it[1]) == 1
             assert int(it[1]) <= 16
     assert n > 0
