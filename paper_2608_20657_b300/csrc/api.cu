@@ -581,6 +581,7 @@ int pack_blob(const sa_heom* h, ItemDesc& d, uint8_t* o) {
     const uint32_t cbw = h->hdr[h->instdev[rw].pat_begin].cat_off;
     std::vector<std::pair<int64_t, int64_t>> wl;
     pack_weights(h, rw, d.p0, int64_t(d.p0) + d.np, wl);
+    bool missing = false;  // a contribution whose weight is not listed (never, by construction)
     if (wl.size() != d.nw) return fail(SA_ERR_STATE, "pack item weights differ from its budget");
     auto cw = [&](uint32_t slot, uint32_t kind, uint32_t c) {
         const size_t gc = size_t(d.c0 + c - cbw);
@@ -591,7 +592,8 @@ int pack_blob(const sa_heom* h, ItemDesc& d, uint8_t* o) {
         if (kind == 3) a = mt - 1, b = zb;
         if (kind == 4) a = -mt, b = -zb;
         uint32_t k = 0;
-        while (wl[k].first != a || wl[k].second != b) ++k;  // listed by pack_weights
+        while (k < wl.size() && (wl[k].first != a || wl[k].second != b)) ++k;  // listed by pack_weights
+        if (k == wl.size()) missing = true;
         return slot | k << 11;
     };
     struct Rec {
@@ -618,6 +620,7 @@ int pack_blob(const sa_heom* h, ItemDesc& d, uint8_t* o) {
             if (tr != 31) ph[0].push_back({pl + uint32_t(loc_T(G, tr)), cw(cq, 3, cq), cw(d.ncat + cq, 3, cq)});
         }
     }
+    if (missing) return fail(SA_ERR_STATE, "a pack item's grouped-sum weight is not in its list");
     for (auto& v : ph) std::sort(v.begin(), v.end(), [](const Rec& x, const Rec& y) { return x.l < y.l; });
     d.nl = uint32_t(ph[0].size() + ph[1].size() + ph[2].size());
     d.row1 = uint32_t(ph[0].size()) | (uint32_t(ph[1].size()) << 16);
