@@ -1309,7 +1309,8 @@ int apply_tuning(sa_heom* h) {
         int pocc = 0;
         CK(pack_occupancy(h->cfg, h->precision == SA_FP64, &pocc));
         if (pocc < 1) return fail(SA_ERR_UNSUPPORTED, "pack kernel does not fit on an SM with this tuning (shared memory)");
-        const int64_t need = (int64_t(h->n_pack_units) + wpb - 1) / wpb;
+        // (the pack kernel also runs the list units of the unpacked instances)
+        const int64_t need = (int64_t(h->n_pack_units) + int64_t(h->n_list_units) + wpb - 1) / wpb;
         h->cfg.pgrid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(h->num_sms) * pocc, need)));
     }
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
